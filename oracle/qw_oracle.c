@@ -34,15 +34,16 @@
  *   - A read outside its segment returns 0 (garbage subspaces reach l >= s
  *     and rows j >= N).
  *   - QBS output is the in-row index mid - offset (Def. 1 defines i(d) as the
- *     list index; Alg. 1 step 8 XORs mid); floor midpoint, right exclusive,
+ *     list index, while Alg. 1 XORs the absolute address mid); floor
+ *     midpoint, right end exclusive,
  *     ceil(log2 s)+1 probes, stop at the first equal element.
- *   - O_s' step 1 computes the address out of place (Eq. "Newprocess").
- *   - Conditional rotation (Alg. T~ step 5 and its footnote): for A's Q1.15
+ *   - O_s' computes the QRAM address out of place (Eq. "Newprocess").
+ *   - Conditional rotation (Alg. T~ and the footnote of Sec. IV): for A's Q1.15
  *     value a, g = sqrt(1-|a|); f = sqrt(a) if a >= 0, else i*sigma*sqrt(|a|)
  *     with sigma = +1 when j <= k and -1 when j > k; R = [[f, -g], [g, conj f]]
  *     acting on b2, R^dag its conjugate transpose.
  *   - P = 2 Pi - 1: the sign flips unless b1, k, b2, jc, kc are all zero
- *     (Alg. "Quantum walk operator", step 2; Eq. (impl)).
+ *     (Alg. "Quantum walk operator"; Eq. (impl)).
  *   - H of T~ acts on the low log2(s) bits of register k (Sec. IV, T~).
  */
 #include <complex.h>
@@ -147,23 +148,23 @@ static uint64_t qbs(oracle *o, uint64_t offset, uint64_t target, uint64_t out)
     int sp = 0;
     const int iters = (int)o->L + 1; /* for i = 0 : ceil(log s) */
 
-    /* step 1-3 */
+    /* allocate and initialise the search window and the loop flag */
     left ^= offset;
     right ^= left + (uint64_t)o->s;
     flag ^= 1;
     for (int it = 0; it < iters; ++it) {
-        if (flag) mid ^= (left + right) / 2;                 /* 5 */
-        if (flag) midval ^= qram(o, mid, o->col_base);       /* 6 */
-        if (flag) {                                          /* 7 */
+        if (flag) mid ^= (left + right) / 2;                 /* midpoint */
+        if (flag) midval ^= qram(o, mid, o->col_base);       /* QRAM probe */
+        if (flag) {                                          /* compare */
             cl ^= (midval < target);
             ce ^= (midval == target);
         }
-        if (ce) out ^= mid - offset;                         /* 8 */
-        if (ce) flag ^= 1;                                   /* 9 */
-        if (flag && cl) { uint64_t t = mid; mid = left; left = t; }   /* 10 */
-        if (flag) cl ^= 1;                                   /* 11 */
-        if (flag && cl) { uint64_t t = mid; mid = right; right = t; } /* 12 */
-        /* 13: push -- the variables move onto the stack, fresh zeros remain */
+        if (ce) out ^= mid - offset;                         /* found: write output */
+        if (ce) flag ^= 1;                                   /* found: stop */
+        if (flag && cl) { uint64_t t = mid; mid = left; left = t; }   /* go right */
+        if (flag) cl ^= 1;
+        if (flag && cl) { uint64_t t = mid; mid = right; right = t; } /* go left */
+        /* push: the loop variables move onto the garbage stack, zeros remain */
         stack[sp].mid = mid;
         stack[sp].midval = midval;
         stack[sp].cl = cl;
@@ -174,23 +175,23 @@ static uint64_t qbs(oracle *o, uint64_t offset, uint64_t target, uint64_t out)
         cl = 0;
         ce = 0;
     }
-    /* 15: uncompute everything except step 8, in reverse order */
+    /* uncompute every loop step except the output write, in reverse order */
     for (int it = iters - 1; it >= 0; --it) {
         sp--;
         mid = stack[sp].mid;
         midval = stack[sp].midval;
         cl = stack[sp].cl;
         ce = stack[sp].ce;
-        if (flag && cl) { uint64_t t = mid; mid = right; right = t; } /* 12^-1 */
-        if (flag) cl ^= 1;                                   /* 11^-1 */
-        if (flag && cl) { uint64_t t = mid; mid = left; left = t; }   /* 10^-1 */
-        if (ce) flag ^= 1;                                   /* 9^-1 */
-        if (flag) {                                          /* 7^-1 */
+        if (flag && cl) { uint64_t t = mid; mid = right; right = t; }
+        if (flag) cl ^= 1;
+        if (flag && cl) { uint64_t t = mid; mid = left; left = t; }
+        if (ce) flag ^= 1;
+        if (flag) {
             cl ^= (midval < target);
             ce ^= (midval == target);
         }
-        if (flag) midval ^= qram(o, mid, o->col_base);       /* 6^-1 */
-        if (flag) mid ^= (left + right) / 2;                 /* 5^-1 */
+        if (flag) midval ^= qram(o, mid, o->col_base);
+        if (flag) mid ^= (left + right) / 2;
         check(o, mid == 0 && midval == 0 && cl == 0 && ce == 0);
     }
     flag ^= 1;
@@ -307,7 +308,7 @@ static int interfere(oracle *o, int reg, int bitlo, int nbits, unitary_fn fn)
 {
     const int dim = 1 << nbits;
     const uint64_t mask = ((uint64_t)(dim - 1)) << bitlo;
-    /* 1. grouping */
+    /* grouping */
     g_sort_o = o;
     g_sort_reg = reg;
     g_sort_mask = mask;
@@ -322,7 +323,7 @@ static int interfere(oracle *o, int reg, int bitlo, int nbits, unitary_fn fn)
     while (i < o->m) {
         int64_t g = i + 1;
         while (g < o->m && same_group(&o->st[i], &o->st[g], reg, mask)) ++g;
-        /* 2. computing on the zero-filled group vector */
+        /* computing, on the zero-filled group vector */
         for (int t = 0; t < dim; ++t) v[t] = 0;
         for (int64_t q = i; q < g; ++q) v[(o->st[q].r[reg] & mask) >> bitlo] = o->st[q].a;
         fn(o, &o->st[i], dim, u);
@@ -336,7 +337,7 @@ static int interfere(oracle *o, int reg, int bitlo, int nbits, unitary_fn fn)
         for (int t = 0; t < dim; ++t) {
             double complex acc = 0;
             for (int q = 0; q < dim; ++q) acc += u[t * dim + q] * v[q];
-            /* 3. clearing zero elements */
+            /* clearing zero elements */
             if (creal(acc) * creal(acc) + cimag(acc) * cimag(acc) <= o->tau * o->tau) continue;
             branch e = o->st[i];
             e.r[reg] = (e.r[reg] & ~mask) | ((uint64_t)t << bitlo);
