@@ -1,0 +1,189 @@
+/*
+ * qwalk.h -- C ABI of the GB300 sparse-state quantum-walk simulator.
+ *
+ * The library simulates, on one GPU, the quantum walk on a sparse real
+ * symmetric matrix stored in QRAM in compressed-sparse-column form and the
+ * CKS quantum linear solver built on it (arXiv 2303.06890, Secs. II-V).  The
+ * quantum state is a list of branches: one packed register key and one complex
+ * amplitude each (Sec. V-A, "Main idea").
+ *
+ * Registers (Sec. IV, "Implementation of the quantum walk"): jc, j, b1, kc, k,
+ * b2 of widths nb, nb, 1, nb, nb, 1 with nb = ceil(log2 N) (the largest N of
+ * the simulation), plus the 16-bit element register A that is live only
+ * inside T~ and T~^dag.
+ *
+ * Conventions for every function:
+ *   - the return value is QW_OK (0) or a negative QW_ERR_* code; nothing
+ *     throws across the ABI; qw_last_error() gives a message for the last
+ *     failure on that simulator;
+ *   - host arrays belong to the caller and are copied during the call;
+ *     device memory belongs to the simulator and is freed by qw_sim_destroy;
+ *   - work is issued in order on the stream given at creation; functions that
+ *     return data to host arrays synchronise that stream before returning.
+ */
+#ifndef QWALK_H
+#define QWALK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QW_OK 0
+#define QW_ERR_ARG (-1)           /* bad argument (null pointer, size, index) */
+#define QW_ERR_CSC (-2)           /* matrix rejected, see qw_sim_create */
+#define QW_ERR_CAPACITY (-3)      /* a row or the on-chip row buffer overflowed */
+#define QW_ERR_CUDA (-4)          /* a CUDA runtime call failed */
+#define QW_ERR_DEVICE_STATUS (-5) /* a device-side self-check tripped */
+#define QW_ERR_STATE (-6)         /* call out of order (e.g. no state yet) */
+
+#define QW_FP64 0     /* complex128 amplitudes, FP64 arithmetic */
+#define QW_FP32_AMP 1 /* complex64 amplitudes in memory; merge, norm, renormalisation
+                         and success probability in FP64 */
+
+/* Register ids for qw_measure_register. */
+#define QW_REG_JC 0
+#define QW_REG_J 1
+#define QW_REG_B1 2
+#define QW_REG_KC 3
+#define QW_REG_K 4
+#define QW_REG_B2 5
+
+typedef struct qw_sim qw_sim; /* opaque; owns all device memory */
+
+/*
+ * One real symmetric matrix in CSC form (Sec. II-C).  Column c holds its
+ * non-zero rows rowidx[colptr[c] .. colptr[c+1]) in strictly increasing order
+ * with values val_q15[...] in Q1.15 two's complement (value = q / 32768).
+ * By symmetry column j is also row j, which is what the QRAM stores.
+ * s_pad: padded sparsity s, a power of two >= the largest column count and
+ * <= n; 0 selects the smallest such power of two (Table 1, note b).
+ */
+typedef struct {
+    int32_t n;
+    int32_t nnz;
+    const int32_t *colptr;  /* n + 1 entries, colptr[0] = 0, colptr[n] = nnz */
+    const int32_t *rowidx;  /* nnz entries */
+    const int16_t *val_q15; /* nnz entries */
+    int32_t s_pad;
+} qw_csc;
+
+typedef struct {
+    int32_t precision;       /* QW_FP64 (default) or QW_FP32_AMP */
+    int32_t fuse_reflection; /* 1 (default): H P H of one walk step as the per-group
+                                reflection 2|+><+| - 1; 0: H, P, H as three ops */
+    double prune_tau;        /* branches with |a| <= tau are removed after each
+                                interference op; 0 = 1e-13 (FP64), 2^-20 (FP32_AMP) */
+    int32_t row_capacity;    /* branches per (jc, j, b1) row between steps; 0 = auto (4 s) */
+    int32_t warp_capacity;   /* branches one warp holds on chip while it runs a row
+                                through a step; 0 = auto */
+    int32_t renorm;          /* -1 = default (on for FP32_AMP, off for FP64) */
+    void *stream;            /* cudaStream_t to issue on; NULL = the default stream */
+} qw_sim_opts;
+
+/* Fill *opts with the defaults above. */
+void qw_sim_opts_default(qw_sim_opts *opts);
+
+/*
+ * Create a simulator for num_instances independent walks, instance i on
+ * matrix mats[i] (batched form: every instance is advanced by each call of
+ * qw_apply_walk_step).  All instances must have the same padded sparsity s.
+ * The matrices are validated and copied to device memory as the padded QRAM
+ * image of Fig. 1: per row j, s (column, value) slots at j*s..j*s+s-1, sorted
+ * by column; a row with fewer than s non-zeros is completed with explicit
+ * zero elements at the first columns j+1, j+2, ... (cyclically) not already in
+ * the row.
+ * Errors: QW_ERR_ARG (null, num_instances < 1, n < 2, n > 65536);
+ * QW_ERR_CSC (unsorted or duplicate rows in a column, index out of range,
+ * column count > s_pad, s_pad not a power of two or > n, matrix not
+ * symmetric, negative diagonal element -- which the walk's isometry cannot
+ * encode, Eq. psi_j -- or instances with different s); QW_ERR_CUDA.
+ * On success *out owns the simulator; on failure *out is NULL.
+ */
+int qw_sim_create(const qw_csc *mats, int32_t num_instances, const qw_sim_opts *opts,
+                  qw_sim **out);
+
+/*
+ * Set instance inst to |b~> = sum_j b_j |jc=0, j, b1=0, kc=0, k=0, b2=0>
+ * (Sec. IV, |j~>), b = b_re + i b_im (b_im may be NULL), n = that instance's N;
+ * exact zeros are not stored.  With apply_T != 0 the state becomes T~|b~>
+ * (Alg. T~).  Other instances are not touched.
+ * Errors: QW_ERR_ARG, QW_ERR_CAPACITY, QW_ERR_CUDA.
+ */
+int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, const double *b_im, int32_t n,
+                  int32_t apply_T);
+
+/*
+ * Apply nsteps walk steps W = S T~ P T~^dag (Alg. "Quantum walk operator")
+ * to every instance.  Each step is one launch over all rows; no host
+ * synchronisation happens between steps.  The call synchronises once at the
+ * end to read the device status word.
+ * Errors: QW_ERR_STATE (no state), QW_ERR_CAPACITY (state kept at the last
+ * completed step), QW_ERR_DEVICE_STATUS, QW_ERR_CUDA.
+ */
+int qw_apply_walk_step(qw_sim *sim, int64_t nsteps);
+
+/*
+ * CKS coefficients of Eq. (fx): b = ceil(kappa^2 ln(kappa/eps)),
+ * j0 = ceil(sqrt(b ln(4 b / eps))), a_j = 4 (-1)^j sum_{i=j+1}^{b} C(2b, b+i) / 2^(2b)
+ * for j = 0..j0, computed in log space.  Writes min(j0+1, cap) coefficients;
+ * *j0_out and *b_out (nullable) receive j0 and b.
+ * Errors: QW_ERR_ARG (kappa < 1, eps not in (0, 1), coeffs NULL with cap > 0).
+ */
+int qw_cks_coefficients(double kappa, double eps, double *coeffs, int64_t cap, int64_t *j0_out,
+                        int64_t *b_out);
+
+/*
+ * CKS linear solver (Sec. IV, Eq. (fx); Sec. V-B).  Requires instance inst in
+ * state T~|b~> (qw_state_init with apply_T = 1) and a single-instance
+ * simulator.  Runs walk steps and, at every other step, reads the flag-0 block
+ * of tau_j = T~^dag W^(2j+1) T~ |b~> (whose value is T_{2j+1}(A/s) b) in FP64:
+ * Y += coeffs[j] * Pi_0 tau_j for j = 0..j0.  Outputs: y_out (2 N doubles,
+ * interleaved re/im) = Y; psucc_out (j0+1 doubles, nullable) =
+ * || Pi_0 sum_{k<=j} coeffs[k] tau_k ||^2 for each j.  2 j0 + 2 launches.
+ * Errors: QW_ERR_ARG, QW_ERR_STATE, QW_ERR_CAPACITY, QW_ERR_CUDA.
+ */
+int qw_apply_qls(qw_sim *sim, int32_t inst, const double *coeffs, int64_t j0, double *y_out,
+                 double *psucc_out);
+
+/*
+ * Marginal distribution of one register of instance inst:
+ * probs[v] = sum over branches with register value v of |a|^2, v < len.
+ * reg_id is one of QW_REG_*.  Errors: QW_ERR_ARG, QW_ERR_STATE, QW_ERR_CUDA.
+ */
+int qw_measure_register(qw_sim *sim, int32_t inst, int32_t reg_id, double *probs, int64_t len);
+
+/* Number of branches of instance inst (inst = -1: all instances). */
+int qw_state_size(qw_sim *sim, int32_t inst, int64_t *count);
+
+/*
+ * Export instance inst (-1: all) in canonical order: keys ascending.  Each
+ * key occupies key_words (1..10) uint64 words, least significant word first,
+ * zero-extended; the packed layout from bit 0 up is
+ *   b2 (1) | k (nb) | kc (nb) | b1 (1) | j (nb) | jc (nb) | A (16) | inst (16).
+ * amps receives 2 doubles (re, im) per branch.  Writes min(count, cap)
+ * branches; *count receives the total.  nb is reported by qw_sim_info.
+ * Errors: QW_ERR_ARG (key_words too small for the layout), QW_ERR_STATE, QW_ERR_CUDA.
+ */
+int qw_state_export(qw_sim *sim, int32_t inst, int32_t key_words, uint64_t *keys, double *amps,
+                    int64_t cap, int64_t *count);
+
+/* nb, s, number of instances, and the total device bytes held (all nullable). */
+int qw_sim_info(const qw_sim *sim, int32_t *nb, int32_t *s, int32_t *num_instances,
+                int64_t *device_bytes);
+
+/* Kernel launches issued by this simulator since creation (for accounting). */
+int64_t qw_launch_count(const qw_sim *sim);
+
+/* Free all device memory of the simulator.  Accepts NULL. */
+int qw_sim_destroy(qw_sim *sim);
+
+/* Message of the last failure on sim (a static string if sim is NULL). */
+const char *qw_last_error(const qw_sim *sim);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QWALK_H */

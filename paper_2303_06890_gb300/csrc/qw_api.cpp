@@ -1,0 +1,726 @@
+/*
+ * qw_api.cpp -- host side of the C ABI declared in include/qwalk.h.
+ *
+ * Validates the CSC input, builds the padded QRAM image of Fig. 1 and the
+ * rotation table, owns the device buffers, and issues the kernels of
+ * qw_kernels.cu in stream order.  No arithmetic of the walk runs here except
+ * the CKS coefficients of Eq. (fx), which are host-side parameters of the
+ * solver.
+ */
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/qwalk.h"
+#include "qw_internal.h"
+
+namespace {
+
+struct Scalars {
+    int32_t status;
+    int32_t pad0;
+    int64_t steps_done;
+    double norm[2];
+    double scale[2];
+    double renorm_target;
+    unsigned int done_ctr;
+    unsigned int pad1;
+    unsigned long long counter;
+};
+
+thread_local std::string g_create_error;
+
+int64_t next_pow2(int64_t x)
+{
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+int ceil_log2(int64_t x)
+{
+    int b = 0;
+    while (((int64_t)1 << b) < x) b++;
+    return b;
+}
+
+} // namespace
+
+struct qw_sim {
+    qw_sim_opts opts;
+    cudaStream_t stream = nullptr;
+    int fp32 = 0;
+    int renorm = 0;
+    int mode = QW_MODE_WALK_FUSED;
+    QwSimDev d{};
+    std::vector<int32_t> n_of;       /* N per instance */
+    std::vector<int64_t> bkt_of;     /* bucket base per instance (+1) */
+    std::vector<double> init_norm2;  /* ||b||^2 of each instance at its last init */
+    double host_target = 0.0;        /* staging for an async copy of the renorm target */
+    QwBufDev buf[3]{};
+    int cur = 0;                     /* buffer holding the state */
+    int scale_slot = 0;              /* Scalars.scale slot of the state's pending scale */
+    bool has_state = false;
+    bool fresh_T = false;            /* state is T~|b~> and untouched since */
+    int grid_walk = 1, grid_t = 1;
+    /* device allocations */
+    uint32_t *img = nullptr;
+    double2 *fg = nullptr;
+    int32_t *inst_n = nullptr;
+    int64_t *inst_img = nullptr, *inst_bkt = nullptr;
+    double *partials = nullptr;
+    Scalars *sc = nullptr;
+    double2 *qls_y = nullptr;
+    double *qls_p = nullptr;
+    int64_t qls_p_cap = 0;
+    int64_t device_bytes = 0;
+    int64_t launches = 0;
+    std::string err;
+};
+
+static int fail(qw_sim *sim, int code, const std::string &msg)
+{
+    if (sim) sim->err = msg;
+    return code;
+}
+
+static int cuda_fail(qw_sim *sim, cudaError_t e, const char *what)
+{
+    return fail(sim, QW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define QW_CUDA(sim, call)                                                                         \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return cuda_fail((sim), e_, #call);                                 \
+    } while (0)
+
+template <typename T> static cudaError_t dalloc(qw_sim *sim, T **p, size_t count)
+{
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T) + 16);
+    if (e == cudaSuccess) sim->device_bytes += (int64_t)(count * sizeof(T));
+    return e;
+}
+
+extern "C" void qw_sim_opts_default(qw_sim_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = QW_FP64;
+    o->fuse_reflection = 1;
+    o->prune_tau = 0.0;
+    o->row_capacity = 0;
+    o->warp_capacity = 0;
+    o->renorm = -1;
+    o->stream = nullptr;
+}
+
+/* Validate one CSC matrix; on success return its largest column count. */
+static int validate_csc(qw_sim *sim, const qw_csc &m, int idx, int32_t *maxcount)
+{
+    const std::string tag = "matrix " + std::to_string(idx) + ": ";
+    if (m.n < 2 || m.n > 65536) return fail(sim, QW_ERR_ARG, tag + "n must be in [2, 65536]");
+    if (!m.colptr || (m.nnz > 0 && (!m.rowidx || !m.val_q15)))
+        return fail(sim, QW_ERR_ARG, tag + "null CSC array");
+    if (m.colptr[0] != 0 || m.colptr[m.n] != m.nnz || m.nnz < 0)
+        return fail(sim, QW_ERR_CSC, tag + "colptr[0] must be 0 and colptr[n] = nnz");
+    int32_t mx = 0;
+    for (int32_t c = 0; c < m.n; ++c) {
+        const int32_t lo = m.colptr[c], hi = m.colptr[c + 1];
+        if (hi < lo) return fail(sim, QW_ERR_CSC, tag + "colptr decreases");
+        mx = std::max(mx, hi - lo);
+        for (int32_t t = lo; t < hi; ++t) {
+            const int32_t r = m.rowidx[t];
+            if (r < 0 || r >= m.n) return fail(sim, QW_ERR_CSC, tag + "row index out of range");
+            if (t > lo && m.rowidx[t - 1] >= r)
+                return fail(sim, QW_ERR_CSC, tag + "row indices unsorted or duplicate");
+            if (r == c && m.val_q15[t] < 0)
+                return fail(sim, QW_ERR_CSC, tag + "negative diagonal element");
+        }
+    }
+    /* symmetry: (r, c, v) present => (c, r, v) present */
+    for (int32_t c = 0; c < m.n; ++c) {
+        for (int32_t t = m.colptr[c]; t < m.colptr[c + 1]; ++t) {
+            const int32_t r = m.rowidx[t];
+            const int32_t *b = m.rowidx + m.colptr[r], *e = m.rowidx + m.colptr[r + 1];
+            const int32_t *p = std::lower_bound(b, e, c);
+            if (p == e || *p != c || m.val_q15[p - m.rowidx] != m.val_q15[t])
+                return fail(sim, QW_ERR_CSC, tag + "matrix is not symmetric");
+        }
+    }
+    *maxcount = mx;
+    return QW_OK;
+}
+
+/* Padded QRAM image of one matrix (Fig. 1): row j's s slots sorted by
+ * column; missing slots hold explicit zeros at the first free columns
+ * j+1, j+2, ... (cyclic). Word = column << 16 | Q1.15 value bits. */
+static void build_image(const qw_csc &m, int s, uint32_t *out)
+{
+    std::vector<char> used((size_t)m.n, 0);
+    std::vector<std::pair<int32_t, uint16_t>> slot;
+    slot.reserve((size_t)s);
+    for (int32_t j = 0; j < m.n; ++j) {
+        slot.clear();
+        for (int32_t t = m.colptr[j]; t < m.colptr[j + 1]; ++t) {
+            slot.emplace_back(m.rowidx[t], (uint16_t)m.val_q15[t]);
+            used[(size_t)m.rowidx[t]] = 1;
+        }
+        int32_t c = j;
+        while ((int)slot.size() < s) {
+            c = (c + 1) % m.n;
+            if (used[(size_t)c]) continue;
+            used[(size_t)c] = 1;
+            slot.emplace_back(c, (uint16_t)0);
+        }
+        std::sort(slot.begin(), slot.end());
+        for (int t = 0; t < s; ++t) {
+            out[(size_t)j * s + t] = ((uint32_t)slot[(size_t)t].first << 16) | slot[(size_t)t].second;
+            used[(size_t)slot[(size_t)t].first] = 0;
+        }
+    }
+}
+
+extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opts *opts_in,
+                             qw_sim **out)
+{
+    if (!out) return QW_ERR_ARG;
+    *out = nullptr;
+    if (!mats || ninst < 1 || ninst > 65535) {
+        g_create_error = "qw_sim_create: mats is NULL or num_instances out of [1, 65535]";
+        return QW_ERR_ARG;
+    }
+    qw_sim *sim = new (std::nothrow) qw_sim();
+    if (!sim) return QW_ERR_CUDA;
+    if (opts_in) sim->opts = *opts_in;
+    else qw_sim_opts_default(&sim->opts);
+    const qw_sim_opts &o = sim->opts;
+    int rc = QW_OK;
+    int32_t s = -1;
+    int32_t nmax = 0;
+    for (int i = 0; i < ninst && rc == QW_OK; ++i) {
+        int32_t mx = 0;
+        rc = validate_csc(sim, mats[i], i, &mx);
+        if (rc != QW_OK) break;
+        int32_t si = mats[i].s_pad ? mats[i].s_pad : (int32_t)next_pow2(std::max(mx, 1));
+        if ((si & (si - 1)) || si < mx || si > mats[i].n) {
+            rc = fail(sim, QW_ERR_CSC, "matrix " + std::to_string(i) +
+                                           ": s_pad must be a power of two in [max column count, n]");
+            break;
+        }
+        if (s >= 0 && si != s) {
+            rc = fail(sim, QW_ERR_CSC, "all instances must have the same padded sparsity s");
+            break;
+        }
+        s = si;
+        nmax = std::max(nmax, mats[i].n);
+    }
+    if (rc != QW_OK) {
+        g_create_error = "qw_sim_create: " + sim->err;
+        delete sim;
+        return rc;
+    }
+    if (o.precision != QW_FP64 && o.precision != QW_FP32_AMP) {
+        delete sim;
+        g_create_error = "qw_sim_create: unknown precision";
+        return QW_ERR_ARG;
+    }
+    sim->fp32 = o.precision == QW_FP32_AMP;
+    sim->renorm = o.renorm < 0 ? sim->fp32 : (o.renorm != 0);
+    sim->mode = o.fuse_reflection ? QW_MODE_WALK_FUSED : QW_MODE_WALK_LITERAL;
+    sim->stream = (cudaStream_t)o.stream;
+
+    QwSimDev &d = sim->d;
+    d.nb = std::max(1, ceil_log2(nmax));
+    d.s = s;
+    d.L = ceil_log2(s);
+    d.ninst = ninst;
+    const double tau = o.prune_tau > 0 ? o.prune_tau : (sim->fp32 ? std::ldexp(1.0, -20) : 1e-13);
+    d.tau2 = tau * tau;
+    d.inv_sqrt_s = 1.0 / std::sqrt((double)s);
+    d.two_over_s = 2.0 / (double)s;
+    d.cap_row = o.row_capacity > 0 ? o.row_capacity : std::max(8, 4 * s);
+    int64_t wc = o.warp_capacity;
+    if (wc <= 0) {
+        wc = sim->mode == QW_MODE_WALK_FUSED ? next_pow2(std::max<int64_t>(32, 4 * s))
+                                             : std::min<int64_t>(512, next_pow2(std::max<int64_t>(32, 4 * s * s)));
+    }
+    wc = std::max<int64_t>(wc, s);
+    wc = std::max<int64_t>(wc, d.cap_row);
+    d.warp_cap = (int)wc;
+    d.spill_slots = 4096;
+
+    /* per-instance tables and the QRAM image */
+    std::vector<int32_t> hn((size_t)ninst);
+    std::vector<int64_t> himg((size_t)ninst), hbkt((size_t)ninst + 1);
+    int64_t img_words = 0, buckets = 0;
+    for (int i = 0; i < ninst; ++i) {
+        hn[(size_t)i] = mats[i].n;
+        himg[(size_t)i] = img_words;
+        hbkt[(size_t)i] = buckets;
+        img_words += (int64_t)mats[i].n * s;
+        buckets += (int64_t)2 << ceil_log2(mats[i].n);
+    }
+    hbkt[(size_t)ninst] = buckets;
+    d.dense_buckets = buckets;
+    d.total_buckets = buckets + d.spill_slots;
+    sim->n_of = hn;
+    sim->bkt_of = hbkt;
+    std::vector<uint32_t> himage((size_t)img_words);
+    for (int i = 0; i < ninst; ++i) build_image(mats[i], s, himage.data() + himg[(size_t)i]);
+    std::vector<double2> hfg(65536);
+    for (int c = 0; c < 65536; ++c) {
+        const int16_t q = (int16_t)(uint16_t)c;
+        const double mag = std::fabs((double)q / 32768.0);
+        hfg[(size_t)c] = make_double2(std::sqrt(mag), std::sqrt(1.0 - mag));
+    }
+
+    auto bail = [&](cudaError_t e, const char *what) {
+        g_create_error = std::string("qw_sim_create: ") + what + ": " + cudaGetErrorString(e);
+        qw_sim_destroy(sim);
+        return QW_ERR_CUDA;
+    };
+    cudaError_t e;
+#define QW_TRY(call)                                                                               \
+    if ((e = (call)) != cudaSuccess) return bail(e, #call)
+    QW_TRY(dalloc(sim, &sim->img, (size_t)img_words));
+    QW_TRY(dalloc(sim, &sim->fg, 65536));
+    QW_TRY(dalloc(sim, &sim->inst_n, (size_t)ninst));
+    QW_TRY(dalloc(sim, &sim->inst_img, (size_t)ninst));
+    QW_TRY(dalloc(sim, &sim->inst_bkt, (size_t)ninst + 1));
+    QW_TRY(cudaMemcpy(sim->img, himage.data(), himage.size() * 4, cudaMemcpyHostToDevice));
+    QW_TRY(cudaMemcpy(sim->fg, hfg.data(), hfg.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    QW_TRY(cudaMemcpy(sim->inst_n, hn.data(), hn.size() * 4, cudaMemcpyHostToDevice));
+    QW_TRY(cudaMemcpy(sim->inst_img, himg.data(), himg.size() * 8, cudaMemcpyHostToDevice));
+    QW_TRY(cudaMemcpy(sim->inst_bkt, hbkt.data(), hbkt.size() * 8, cudaMemcpyHostToDevice));
+    d.img = sim->img;
+    d.fg = sim->fg;
+    d.inst_n = sim->inst_n;
+    d.inst_img = sim->inst_img;
+    d.inst_bkt = sim->inst_bkt;
+    const size_t amp_bytes = sim->fp32 ? sizeof(float2) : sizeof(double2);
+    const size_t slots = (size_t)d.total_buckets * (size_t)d.cap_row;
+    for (int bi = 0; bi < 3; ++bi) {
+        QwBufDev &b = sim->buf[bi];
+        QW_TRY(dalloc(sim, &b.key, slots));
+        QW_TRY(dalloc(sim, (unsigned char **)&b.amp, slots * amp_bytes));
+        QW_TRY(dalloc(sim, &b.count, (size_t)d.total_buckets));
+        QW_TRY(dalloc(sim, &b.spill, (size_t)d.spill_slots));
+        QW_TRY(cudaMemset(b.count, 0, (size_t)d.total_buckets * 4));
+        QW_TRY(cudaMemset(b.spill, 0xff, (size_t)d.spill_slots * 8));
+    }
+    sim->grid_walk = qw_step_grid(d, sim->fp32, sim->mode);
+    sim->grid_t = qw_step_grid(d, sim->fp32, QW_MODE_T);
+    const int gmax = std::max(sim->grid_walk, sim->grid_t);
+    QW_TRY(dalloc(sim, &sim->partials, (size_t)gmax));
+    QW_TRY(dalloc(sim, &sim->sc, 1));
+    Scalars z{};
+    z.scale[0] = z.scale[1] = 1.0;
+    z.renorm_target = 1.0;
+    QW_TRY(cudaMemcpy(sim->sc, &z, sizeof z, cudaMemcpyHostToDevice));
+    sim->init_norm2.assign((size_t)ninst, 0.0);
+    QW_TRY(dalloc(sim, &sim->qls_y, (size_t)nmax));
+    QW_TRY(cudaDeviceSynchronize());
+#undef QW_TRY
+    *out = sim;
+    return QW_OK;
+}
+
+extern "C" int qw_sim_destroy(qw_sim *sim)
+{
+    if (!sim) return QW_OK;
+    if (sim->stream) cudaStreamSynchronize(sim->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(sim->img);
+    cudaFree(sim->fg);
+    cudaFree(sim->inst_n);
+    cudaFree(sim->inst_img);
+    cudaFree(sim->inst_bkt);
+    for (auto &b : sim->buf) {
+        cudaFree(b.key);
+        cudaFree(b.amp);
+        cudaFree(b.count);
+        cudaFree(b.spill);
+    }
+    cudaFree(sim->partials);
+    cudaFree(sim->sc);
+    cudaFree(sim->qls_y);
+    cudaFree(sim->qls_p);
+    delete sim;
+    return QW_OK;
+}
+
+extern "C" const char *qw_last_error(const qw_sim *sim)
+{
+    if (!sim) return g_create_error.c_str();
+    return sim->err.c_str();
+}
+
+extern "C" int qw_sim_info(const qw_sim *sim, int32_t *nb, int32_t *s, int32_t *ninst,
+                           int64_t *bytes)
+{
+    if (!sim) return QW_ERR_ARG;
+    if (nb) *nb = sim->d.nb;
+    if (s) *s = sim->d.s;
+    if (ninst) *ninst = sim->d.ninst;
+    if (bytes) *bytes = sim->device_bytes;
+    return QW_OK;
+}
+
+extern "C" int64_t qw_launch_count(const qw_sim *sim) { return sim ? sim->launches : 0; }
+
+static const double *pending_scale(qw_sim *sim)
+{
+    return sim->renorm ? &sim->sc->scale[sim->scale_slot] : nullptr;
+}
+
+/* Read and clear the device status word; map it to an error code. */
+static int check_status(qw_sim *sim, const char *where)
+{
+    int32_t st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, &sim->sc->status, 4, cudaMemcpyDeviceToHost, sim->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
+    if (e != cudaSuccess) return cuda_fail(sim, e, where);
+    if (st == 0) return QW_OK;
+    const int32_t zero = 0;
+    cudaMemcpyAsync(&sim->sc->status, &zero, 4, cudaMemcpyHostToDevice, sim->stream);
+    cudaStreamSynchronize(sim->stream);
+    std::string m = std::string(where) + ": device status";
+    if (st & QW_ST_ROW_OVERFLOW) m += " [row bucket overflow: raise row_capacity]";
+    if (st & QW_ST_WARP_OVERFLOW) m += " [on-chip row buffer overflow: raise warp_capacity]";
+    if (st & QW_ST_SPILL_FULL) m += " [garbage-row table full]";
+    if (st & QW_ST_ANCILLA) m += " [register A not returned to zero]";
+    const int code = (st & (QW_ST_ROW_OVERFLOW | QW_ST_WARP_OVERFLOW | QW_ST_SPILL_FULL))
+                         ? QW_ERR_CAPACITY
+                         : QW_ERR_DEVICE_STATUS;
+    return fail(sim, code, m);
+}
+
+static QwStepArgs step_args(qw_sim *sim, int mode)
+{
+    QwStepArgs a{};
+    a.mode = mode;
+    a.renorm = sim->renorm;
+    a.scale_in = pending_scale(sim);
+    a.partials = sim->partials;
+    a.done_ctr = &sim->sc->done_ctr;
+    a.norm_out = &sim->sc->norm[sim->scale_slot ^ 1];
+    a.scale_out = &sim->sc->scale[sim->scale_slot ^ 1];
+    a.renorm_target = &sim->sc->renorm_target;
+    a.steps_done = &sim->sc->steps_done;
+    a.status = &sim->sc->status;
+    a.qls_y = sim->qls_y;
+    return a;
+}
+
+/* one walk step: X_cur -> X_cur+1, clearing X_cur+2 */
+static int launch_walk(qw_sim *sim, double coef, int readout)
+{
+    QwStepArgs a = step_args(sim, sim->mode);
+    a.qls_coef = coef;
+    a.qls_readout = readout;
+    const int nxt = (sim->cur + 1) % 3, clr = (sim->cur + 2) % 3;
+    cudaError_t e = qw_launch_step(sim->d, sim->buf[sim->cur], sim->buf[nxt], sim->buf[clr], a,
+                                   sim->fp32, sim->grid_walk, sim->stream);
+    sim->launches++;
+    if (e != cudaSuccess) return cuda_fail(sim, e, "walk step launch");
+    sim->cur = nxt;
+    sim->scale_slot ^= 1;
+    return QW_OK;
+}
+
+extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, const double *b_im,
+                             int32_t n, int32_t apply_T)
+{
+    if (!sim) return QW_ERR_ARG;
+    if (inst < 0 || inst >= sim->d.ninst) return fail(sim, QW_ERR_ARG, "instance out of range");
+    if (!b_re || n != sim->n_of[(size_t)inst]) return fail(sim, QW_ERR_ARG, "b must hold N values");
+    std::vector<double2> hb((size_t)n);
+    for (int j = 0; j < n; ++j) hb[(size_t)j] = make_double2(b_re[j], b_im ? b_im[j] : 0.0);
+    double2 *db = nullptr;
+    QW_CUDA(sim, cudaMallocAsync((void **)&db, hb.size() * sizeof(double2), sim->stream));
+    QW_CUDA(sim, cudaMemcpyAsync(db, hb.data(), hb.size() * sizeof(double2), cudaMemcpyHostToDevice,
+                                 sim->stream));
+    const int64_t lo = sim->bkt_of[(size_t)inst], hi = sim->bkt_of[(size_t)inst + 1];
+    const bool all = sim->d.ninst == 1;
+    /* clear the instance's rows in every buffer (the whole state for a single
+       instance, garbage-row table included) */
+    for (int bi = 0; bi < 3; ++bi) {
+        QW_CUDA(sim, qw_launch_clear(sim->d, sim->buf[bi], all ? 0 : lo,
+                                     all ? sim->d.total_buckets : hi, all ? 1 : 0, sim->stream));
+        sim->launches++;
+    }
+    double nb2 = 0.0;
+    for (int j = 0; j < n; ++j) nb2 += hb[(size_t)j].x * hb[(size_t)j].x + hb[(size_t)j].y * hb[(size_t)j].y;
+    sim->init_norm2[(size_t)inst] = nb2;
+    if (all) {
+        Scalars z{};
+        z.scale[0] = z.scale[1] = 1.0;
+        z.renorm_target = nb2;
+        QW_CUDA(sim, cudaMemcpyAsync(sim->sc, &z, sizeof z, cudaMemcpyHostToDevice, sim->stream));
+        sim->scale_slot = 0;
+        sim->cur = 0;
+    } else {
+        double target = 0.0;
+        for (double v : sim->init_norm2) target += v;
+        sim->host_target = target;
+        QW_CUDA(sim, cudaMemcpyAsync(&sim->sc->renorm_target, &sim->host_target, 8,
+                                     cudaMemcpyHostToDevice, sim->stream));
+    }
+    QW_CUDA(sim, qw_launch_init_b(sim->d, sim->buf[sim->cur], inst, db, n, sim->fp32,
+                                  all ? nullptr : pending_scale(sim), sim->stream));
+    sim->launches++;
+    if (apply_T) {
+        QwStepArgs a = step_args(sim, QW_MODE_T);
+        a.scale_in = nullptr;
+        a.norm_out = &sim->sc->norm[sim->scale_slot];
+        a.scale_out = nullptr;
+        a.bucket_lo = lo;
+        a.bucket_hi = hi;
+        QW_CUDA(sim, qw_launch_step(sim->d, sim->buf[sim->cur], sim->buf[sim->cur], sim->buf[sim->cur],
+                                    a, sim->fp32, sim->grid_t, sim->stream));
+        sim->launches++;
+    }
+    QW_CUDA(sim, cudaFreeAsync(db, sim->stream));
+    int rc = check_status(sim, "qw_state_init");
+    if (rc != QW_OK) return rc;
+    sim->has_state = true;
+    sim->fresh_T = apply_T != 0;
+    return QW_OK;
+}
+
+/* Run nsteps walk steps; on a device error, roll the host view back to the
+ * buffer of the last step that completed cleanly (steps after a failed one
+ * are no-ops on the device). */
+static int run_steps(qw_sim *sim, int64_t nsteps, const char *where)
+{
+    int64_t done0 = 0;
+    QW_CUDA(sim, cudaMemcpyAsync(&done0, &sim->sc->steps_done, 8, cudaMemcpyDeviceToHost, sim->stream));
+    QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
+    const int cur0 = sim->cur, slot0 = sim->scale_slot;
+    for (int64_t t = 0; t < nsteps; ++t) {
+        int rc = launch_walk(sim, 0.0, 0);
+        if (rc != QW_OK) return rc;
+    }
+    int rc = check_status(sim, where);
+    if (rc != QW_OK) {
+        int64_t done1 = 0;
+        cudaMemcpy(&done1, &sim->sc->steps_done, 8, cudaMemcpyDeviceToHost);
+        const int64_t good = done1 - done0;
+        sim->cur = (int)((cur0 + good) % 3);
+        sim->scale_slot = slot0 ^ (int)(good & 1);
+        sim->err += " (state kept after " + std::to_string(good) + " completed steps)";
+    }
+    return rc;
+}
+
+extern "C" int qw_apply_walk_step(qw_sim *sim, int64_t nsteps)
+{
+    if (!sim) return QW_ERR_ARG;
+    if (nsteps < 0) return fail(sim, QW_ERR_ARG, "nsteps < 0");
+    if (!sim->has_state) return fail(sim, QW_ERR_STATE, "no state: call qw_state_init first");
+    if (nsteps == 0) return QW_OK;
+    sim->fresh_T = false;
+    return run_steps(sim, nsteps, "qw_apply_walk_step");
+}
+
+extern "C" int qw_cks_coefficients(double kappa, double eps, double *coeffs, int64_t cap,
+                                   int64_t *j0_out, int64_t *b_out)
+{
+    if (!(kappa >= 1.0) || !(eps > 0.0 && eps < 1.0) || (cap > 0 && !coeffs)) return QW_ERR_ARG;
+    const double bd = std::ceil(kappa * kappa * std::log(kappa / eps));
+    if (!(bd < 4e9)) return QW_ERR_ARG;
+    const int64_t b = (int64_t)bd;
+    const int64_t j0 = (int64_t)std::ceil(std::sqrt(bd * std::log(4.0 * bd / eps)));
+    if (j0_out) *j0_out = j0;
+    if (b_out) *b_out = b;
+    if (cap <= 0) return QW_OK;
+    /* terms t_i = C(2b, b+i) / 4^b, i = 0..b.  t_0 = prod_{i<=b} (2i-1)/(2i) for
+       b <= 4096, else the asymptotic series of the central binomial coefficient
+       C(2b,b)/4^b = (pi b)^(-1/2) (1 - 1/(8b) + 1/(128b^2) + 5/(1024b^3)
+       - 21/(32768b^4)); then t_{i+1} / t_i = (b - i) / (b + i + 1); tails are
+       summed smallest term first. */
+    double t0;
+    if (b <= 4096) {
+        t0 = 1.0;
+        for (int64_t i = 1; i <= b; ++i) t0 *= (double)(2 * i - 1) / (double)(2 * i);
+    } else {
+        const double x = 1.0 / bd;
+        const double pi = 3.14159265358979323846;
+        t0 = (1.0 - x / 8.0 + x * x / 128.0 + 5.0 * x * x * x / 1024.0 - 21.0 * x * x * x * x / 32768.0) /
+             std::sqrt(pi * bd);
+    }
+    int64_t imax = 0;
+    std::vector<double> t;
+    double cur = t0;
+    t.push_back(cur);
+    while (imax < b && cur > 0.0) {
+        cur *= (double)(b - imax) / (double)(b + imax + 1);
+        t.push_back(cur);
+        imax++;
+    }
+    const int64_t count = std::min<int64_t>(j0 + 1, cap);
+    std::vector<double> tail((size_t)t.size() + 1, 0.0);
+    for (int64_t i = (int64_t)t.size() - 1; i >= 0; --i) tail[(size_t)i] = tail[(size_t)i + 1] + t[(size_t)i];
+    for (int64_t j = 0; j < count; ++j) {
+        const double tj = (j + 1 < (int64_t)tail.size()) ? tail[(size_t)j + 1] : 0.0;
+        coeffs[j] = 4.0 * ((j & 1) ? -tj : tj);
+    }
+    return QW_OK;
+}
+
+extern "C" int qw_apply_qls(qw_sim *sim, int32_t inst, const double *coeffs, int64_t j0,
+                            double *y_out, double *psucc_out)
+{
+    if (!sim) return QW_ERR_ARG;
+    if (sim->d.ninst != 1 || inst != 0) return fail(sim, QW_ERR_ARG, "QLS needs a single-instance simulator");
+    if (!coeffs || j0 < 0 || !y_out) return fail(sim, QW_ERR_ARG, "coeffs, j0 and y_out are required");
+    if (!sim->has_state || !sim->fresh_T)
+        return fail(sim, QW_ERR_STATE, "QLS needs the state T~|b~> (qw_state_init with apply_T = 1)");
+    const int n = sim->n_of[0];
+    if (sim->qls_p_cap < j0 + 1) {
+        cudaFree(sim->qls_p);
+        sim->qls_p = nullptr;
+        QW_CUDA(sim, cudaMalloc((void **)&sim->qls_p, (size_t)(j0 + 1) * sizeof(double)));
+        sim->qls_p_cap = j0 + 1;
+    }
+    QW_CUDA(sim, cudaMemsetAsync(sim->qls_y, 0, (size_t)n * sizeof(double2), sim->stream));
+    for (int64_t j = 0; j <= j0; ++j) {
+        int rc = launch_walk(sim, 0.0, 0);
+        if (rc == QW_OK) rc = launch_walk(sim, coeffs[j], 1);
+        if (rc != QW_OK) return rc;
+        QW_CUDA(sim, qw_launch_qls_norm(sim->qls_y, n, sim->qls_p + j, sim->stream));
+        sim->launches++;
+        if ((j & 1023) == 1023) {
+            int st = check_status(sim, "qw_apply_qls");
+            if (st != QW_OK) return st;
+        }
+    }
+    sim->fresh_T = false;
+    std::vector<double2> hy((size_t)n);
+    QW_CUDA(sim, cudaMemcpyAsync(hy.data(), sim->qls_y, (size_t)n * sizeof(double2),
+                                 cudaMemcpyDeviceToHost, sim->stream));
+    if (psucc_out)
+        QW_CUDA(sim, cudaMemcpyAsync(psucc_out, sim->qls_p, (size_t)(j0 + 1) * sizeof(double),
+                                     cudaMemcpyDeviceToHost, sim->stream));
+    int rc = check_status(sim, "qw_apply_qls");
+    if (rc != QW_OK) return rc;
+    for (int j = 0; j < n; ++j) {
+        y_out[2 * j] = hy[(size_t)j].x;
+        y_out[2 * j + 1] = hy[(size_t)j].y;
+    }
+    return QW_OK;
+}
+
+extern "C" int qw_measure_register(qw_sim *sim, int32_t inst, int32_t reg, double *probs, int64_t len)
+{
+    if (!sim) return QW_ERR_ARG;
+    if (inst < 0 || inst >= sim->d.ninst || reg < 0 || reg > 5 || !probs || len < 1)
+        return fail(sim, QW_ERR_ARG, "bad instance, register id or output");
+    if (!sim->has_state) return fail(sim, QW_ERR_STATE, "no state");
+    double *dp = nullptr;
+    QW_CUDA(sim, cudaMallocAsync((void **)&dp, (size_t)len * sizeof(double), sim->stream));
+    QW_CUDA(sim, cudaMemsetAsync(dp, 0, (size_t)len * sizeof(double), sim->stream));
+    QW_CUDA(sim, qw_launch_measure(sim->d, sim->buf[sim->cur], inst, sim->fp32, pending_scale(sim), reg,
+                                   dp, len, sim->stream));
+    sim->launches++;
+    QW_CUDA(sim, cudaMemcpyAsync(probs, dp, (size_t)len * sizeof(double), cudaMemcpyDeviceToHost,
+                                 sim->stream));
+    QW_CUDA(sim, cudaFreeAsync(dp, sim->stream));
+    return check_status(sim, "qw_measure_register");
+}
+
+extern "C" int qw_state_size(qw_sim *sim, int32_t inst, int64_t *count)
+{
+    if (!sim || !count) return QW_ERR_ARG;
+    if (inst < -1 || inst >= sim->d.ninst) return fail(sim, QW_ERR_ARG, "instance out of range");
+    if (!sim->has_state) return fail(sim, QW_ERR_STATE, "no state");
+    QW_CUDA(sim, cudaMemsetAsync(&sim->sc->counter, 0, 8, sim->stream));
+    QW_CUDA(sim, qw_launch_count(sim->d, sim->buf[sim->cur], inst, &sim->sc->counter, sim->stream));
+    sim->launches++;
+    unsigned long long c = 0;
+    QW_CUDA(sim, cudaMemcpyAsync(&c, &sim->sc->counter, 8, cudaMemcpyDeviceToHost, sim->stream));
+    QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
+    *count = (int64_t)c;
+    return QW_OK;
+}
+
+static void put_bits(uint64_t *w, int pos, uint64_t v, int width)
+{
+    for (int b = 0; b < width; ++b)
+        if ((v >> b) & 1ull) w[(pos + b) >> 6] |= 1ull << ((pos + b) & 63);
+}
+
+extern "C" int qw_state_export(qw_sim *sim, int32_t inst, int32_t key_words, uint64_t *keys,
+                               double *amps, int64_t cap, int64_t *count)
+{
+    if (!sim || !count) return QW_ERR_ARG;
+    const int nb = sim->d.nb;
+    const int bits = 4 * nb + 34;
+    if (key_words < 1 || key_words > 10 || key_words * 64 < bits)
+        return fail(sim, QW_ERR_ARG, "key_words too small for the packed register layout");
+    if (cap > 0 && (!keys || !amps)) return fail(sim, QW_ERR_ARG, "null output arrays");
+    int64_t total = 0;
+    int rc = qw_state_size(sim, inst, &total);
+    if (rc != QW_OK) return rc;
+    *count = total;
+    if (total == 0 || cap <= 0) return QW_OK;
+    uint64_t *drow = nullptr, *dloc = nullptr;
+    double2 *damp = nullptr;
+    QW_CUDA(sim, cudaMallocAsync((void **)&drow, (size_t)total * 8, sim->stream));
+    QW_CUDA(sim, cudaMallocAsync((void **)&dloc, (size_t)total * 8, sim->stream));
+    QW_CUDA(sim, cudaMallocAsync((void **)&damp, (size_t)total * 16, sim->stream));
+    QW_CUDA(sim, cudaMemsetAsync(&sim->sc->counter, 0, 8, sim->stream));
+    QW_CUDA(sim, qw_launch_export(sim->d, sim->buf[sim->cur], inst, sim->fp32, pending_scale(sim), drow,
+                                  dloc, damp, &sim->sc->counter, total, sim->stream));
+    sim->launches++;
+    std::vector<uint64_t> hrow((size_t)total), hloc((size_t)total);
+    std::vector<double2> hamp((size_t)total);
+    QW_CUDA(sim, cudaMemcpyAsync(hrow.data(), drow, (size_t)total * 8, cudaMemcpyDeviceToHost, sim->stream));
+    QW_CUDA(sim, cudaMemcpyAsync(hloc.data(), dloc, (size_t)total * 8, cudaMemcpyDeviceToHost, sim->stream));
+    QW_CUDA(sim, cudaMemcpyAsync(hamp.data(), damp, (size_t)total * 16, cudaMemcpyDeviceToHost, sim->stream));
+    QW_CUDA(sim, cudaFreeAsync(drow, sim->stream));
+    QW_CUDA(sim, cudaFreeAsync(dloc, sim->stream));
+    QW_CUDA(sim, cudaFreeAsync(damp, sim->stream));
+    rc = check_status(sim, "qw_state_export");
+    if (rc != QW_OK) return rc;
+    /* pack: b2 | k | kc | b1 | j | jc | A | inst */
+    const size_t W = (size_t)key_words;
+    std::vector<uint64_t> packed((size_t)total * W, 0ull);
+    const uint64_t m = (1ull << nb) - 1;
+    for (int64_t i = 0; i < total; ++i) {
+        const uint64_t rk = hrow[(size_t)i], lk = hloc[(size_t)i];
+        uint64_t *w = packed.data() + (size_t)i * W;
+        int p = 0;
+        put_bits(w, p, lk & 1ull, 1); p += 1;                      /* b2 */
+        put_bits(w, p, (lk >> 1) & m, nb); p += nb;                /* k */
+        put_bits(w, p, (lk >> (1 + nb)) & m, nb); p += nb;         /* kc */
+        put_bits(w, p, rk & 1ull, 1); p += 1;                      /* b1 */
+        put_bits(w, p, (rk >> 1) & 0x7ffffull, nb); p += nb;       /* j */
+        put_bits(w, p, (rk >> 20) & 0xfffffull, nb); p += nb;      /* jc */
+        put_bits(w, p, (lk >> (1 + 2 * nb)) & 0xffffull, 16); p += 16; /* A */
+        put_bits(w, p, rk >> 40, 16);                              /* inst */
+    }
+    std::vector<int64_t> order((size_t)total);
+    for (int64_t i = 0; i < total; ++i) order[(size_t)i] = i;
+    std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+        const uint64_t *a = packed.data() + (size_t)x * W, *b = packed.data() + (size_t)y * W;
+        for (size_t t = W; t-- > 0;)
+            if (a[t] != b[t]) return a[t] < b[t];
+        return false;
+    });
+    const int64_t nout = std::min(total, cap);
+    for (int64_t i = 0; i < nout; ++i) {
+        const int64_t src = order[(size_t)i];
+        std::memcpy(keys + (size_t)i * W, packed.data() + (size_t)src * W, W * 8);
+        amps[2 * i] = hamp[(size_t)src].x;
+        amps[2 * i + 1] = hamp[(size_t)src].y;
+    }
+    return QW_OK;
+}

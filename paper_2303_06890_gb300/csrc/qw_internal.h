@@ -1,0 +1,111 @@
+/*
+ * qw_internal.h -- device data layout shared by the kernels (qw_kernels.cu)
+ * and the host side of the C ABI (qw_api.cpp).
+ *
+ * Layout in HBM.  The state is bucketed by row: one bucket per (inst, jc, j, b1)
+ * value, i.e. per value of the registers that T~, P and T~^dag never change
+ * and that every QRAM access of those operators indexes (row j).  A bucket
+ * holds up to cap_row branches as
+ *   key[b * cap_row + i]  uint64, the "local" registers (k, kc, A, b2) packed
+ *                         in the R layout below,
+ *   amp[b * cap_row + i]  double2 or float2,
+ *   count[b]              int32 branches present.
+ * Rows with jc = 0 have dense buckets: inst_bkt[inst] + (j << 1 | b1).  Rows
+ * with jc != 0 (garbage subspace) go to spill buckets dense_buckets + slot,
+ * slot found by open addressing on the packed row key in spill[].
+ * Three such buffers rotate: a step reads X_t, writes X_{t+1} and clears
+ * X_{t+2}; X_t stays intact until the step after next.
+ *
+ * Local-key layouts (bit 0 first):
+ *   R layout: b2 | k (nb) | kc (nb) | A (16)            -- b2-pairs adjacent
+ *   H layout: k_low (L) | b2 | k_high (nb-L) | kc | A   -- Hadamard groups adjacent
+ * Both keep kc and A at bits 1+nb and above.
+ */
+#ifndef QW_INTERNAL_H
+#define QW_INTERNAL_H
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define QW_SPILL_EMPTY (~0ull)
+
+/* device status word bits */
+#define QW_ST_ROW_OVERFLOW 1   /* a bucket received more than cap_row branches */
+#define QW_ST_WARP_OVERFLOW 2  /* a row outgrew the on-chip row buffer */
+#define QW_ST_SPILL_FULL 4     /* no free spill slot for a jc != 0 row */
+#define QW_ST_ANCILLA 8        /* register A not zero where it must be */
+
+/* step kernel modes */
+#define QW_MODE_WALK_FUSED 0   /* T~^dag, (H P H as one reflection), T~, S */
+#define QW_MODE_WALK_LITERAL 1 /* T~^dag, H, P, H, T~, S */
+#define QW_MODE_T 2            /* T~ only, in place on a bucket range */
+
+struct QwSimDev {
+    int nb, s, L, ninst;
+    int cap_row;   /* branches per bucket */
+    int warp_cap;  /* on-chip branches per warp */
+    int spill_slots;          /* power of two */
+    int64_t dense_buckets;    /* sum over instances */
+    int64_t total_buckets;    /* dense + spill */
+    double tau2;              /* prune threshold squared */
+    double inv_sqrt_s;        /* 1 / sqrt(s) */
+    double two_over_s;        /* 2 / s */
+    const uint32_t *img;      /* QRAM words: column << 16 | Q1.15 value */
+    const double2 *fg;        /* per Q1.15 code: (sqrt|a|, sqrt(1-|a|)) */
+    const int32_t *inst_n;    /* N per instance */
+    const int64_t *inst_img;  /* image offset per instance */
+    const int64_t *inst_bkt;  /* first dense bucket per instance, ninst + 1 entries */
+};
+
+struct QwBufDev {
+    uint64_t *key;
+    void *amp;
+    int32_t *count;
+    uint64_t *spill;
+};
+
+struct QwStepArgs {
+    int mode;
+    int renorm;
+    int64_t bucket_lo, bucket_hi; /* bucket range processed (MODE_T) */
+    const double *scale_in;  /* amplitude scale of the input (renormalisation), nullable */
+    double *partials;        /* per-block norm partial sums */
+    unsigned int *done_ctr;  /* blocks finished (last block reduces partials) */
+    double *norm_out;        /* ||output||^2 */
+    double *scale_out;       /* sqrt(target / norm_out) when renorm, else 1 */
+    const double *renorm_target; /* sum of the instances' initial ||b||^2 */
+    int64_t *steps_done;     /* incremented by each step that completes cleanly */
+    int32_t *status;
+    double2 *qls_y;          /* flag-0 accumulator (nullable) */
+    double qls_coef;         /* Y += coef * Pi_0 tau at this step's midpoint */
+    int qls_readout;
+};
+
+/* launchers (qw_kernels.cu); all return cudaGetLastError() of the launch */
+int qw_sm_count(void);
+cudaError_t qw_launch_step(const QwSimDev &d, const QwBufDev &in, const QwBufDev &out,
+                           const QwBufDev &clear, const QwStepArgs &a, int fp32, int grid,
+                           cudaStream_t st);
+int qw_step_grid(const QwSimDev &d, int fp32, int mode);
+cudaError_t qw_launch_clear(const QwSimDev &d, const QwBufDev &buf, int64_t lo, int64_t hi,
+                            int clear_spill, cudaStream_t st);
+cudaError_t qw_launch_init_b(const QwSimDev &d, const QwBufDev &buf, int inst, const double2 *b,
+                             int n, int fp32, const double *scale, cudaStream_t st);
+cudaError_t qw_launch_export(const QwSimDev &d, const QwBufDev &buf, int inst, int fp32,
+                             const double *scale, uint64_t *rowkey, uint64_t *local, double2 *amp,
+                             unsigned long long *counter, int64_t cap, cudaStream_t st);
+cudaError_t qw_launch_measure(const QwSimDev &d, const QwBufDev &buf, int inst, int fp32,
+                              const double *scale, int reg, double *probs, int64_t len,
+                              cudaStream_t st);
+cudaError_t qw_launch_count(const QwSimDev &d, const QwBufDev &buf, int inst,
+                            unsigned long long *counter, cudaStream_t st);
+cudaError_t qw_launch_qls_norm(const double2 *y, int n, double *out, cudaStream_t st);
+
+/* packed row key: inst << 40 | jc << 20 | j << 1 | b1  (nb <= 19) */
+__host__ __device__ static inline uint64_t qw_rowkey(uint32_t inst, uint32_t jc, uint32_t j,
+                                                     uint32_t b1)
+{
+    return ((uint64_t)inst << 40) | ((uint64_t)jc << 20) | ((uint64_t)j << 1) | (uint64_t)b1;
+}
+
+#endif /* QW_INTERNAL_H */

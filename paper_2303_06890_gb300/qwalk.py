@@ -1,0 +1,233 @@
+"""Thin ctypes binding of the C ABI in include/qwalk.h (argument marshalling only).
+
+Every step of the walk runs in libqwalk.so's CUDA kernels; this module only
+converts numpy arrays to pointers and error codes to exceptions.  PyTorch, when
+present, supplies the CUDA stream.  Loading fails loudly when the library is
+missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+QW_OK = 0
+QW_ERR_ARG = -1
+QW_ERR_CSC = -2
+QW_ERR_CAPACITY = -3
+QW_ERR_CUDA = -4
+QW_ERR_DEVICE_STATUS = -5
+QW_ERR_STATE = -6
+QW_FP64 = 0
+QW_FP32_AMP = 1
+REGS = {"jc": 0, "j": 1, "b1": 2, "kc": 3, "k": 4, "b2": 5}
+
+EXPORTED = ("qw_sim_opts_default", "qw_sim_create", "qw_state_init", "qw_apply_walk_step",
+            "qw_cks_coefficients", "qw_apply_qls", "qw_measure_register", "qw_state_size",
+            "qw_state_export", "qw_sim_info", "qw_launch_count", "qw_sim_destroy", "qw_last_error")
+
+
+class QwError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"qwalk error {code}: {msg}")
+        self.code = code
+
+
+class CSC(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int32), ("colptr", ctypes.c_void_p),
+                ("rowidx", ctypes.c_void_p), ("val_q15", ctypes.c_void_p), ("s_pad", ctypes.c_int32)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("fuse_reflection", ctypes.c_int32),
+                ("prune_tau", ctypes.c_double), ("row_capacity", ctypes.c_int32),
+                ("warp_capacity", ctypes.c_int32), ("renorm", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libqwalk.so (building it first if asked); raise if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError(f"libqwalk.so not built: {path}")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.qw_sim_opts_default.argtypes = [P]
+    lib.qw_sim_opts_default.restype = None
+    lib.qw_sim_create.argtypes = [P, i32, P, P]
+    lib.qw_state_init.argtypes = [P, i32, P, P, i32, i32]
+    lib.qw_apply_walk_step.argtypes = [P, i64]
+    lib.qw_cks_coefficients.argtypes = [dbl, dbl, P, i64, P, P]
+    lib.qw_apply_qls.argtypes = [P, i32, P, i64, P, P]
+    lib.qw_measure_register.argtypes = [P, i32, i32, P, i64]
+    lib.qw_state_size.argtypes = [P, i32, P]
+    lib.qw_state_export.argtypes = [P, i32, i32, P, P, i64, P]
+    lib.qw_sim_info.argtypes = [P, P, P, P, P]
+    lib.qw_launch_count.argtypes = [P]
+    lib.qw_launch_count.restype = i64
+    lib.qw_sim_destroy.argtypes = [P]
+    lib.qw_last_error.argtypes = [P]
+    lib.qw_last_error.restype = ctypes.c_char_p
+    for name in ("qw_sim_create", "qw_state_init", "qw_apply_walk_step", "qw_cks_coefficients",
+                 "qw_apply_qls", "qw_measure_register", "qw_state_size", "qw_state_export",
+                 "qw_sim_info", "qw_sim_destroy"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def current_stream() -> int | None:
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+def cks_coefficients(kappa: float, eps: float = 1e-3) -> tuple[np.ndarray, int, int]:
+    """qw_cks_coefficients: (a_0..a_j0, j0, b) of Eq. (fx)."""
+    lib = load()
+    j0 = ctypes.c_int64()
+    b = ctypes.c_int64()
+    rc = lib.qw_cks_coefficients(float(kappa), float(eps), None, 0, ctypes.byref(j0), ctypes.byref(b))
+    if rc:
+        raise QwError(rc, "qw_cks_coefficients: bad kappa or eps")
+    out = np.zeros(j0.value + 1)
+    rc = lib.qw_cks_coefficients(float(kappa), float(eps), _p(out), out.size, None, None)
+    if rc:
+        raise QwError(rc, "qw_cks_coefficients")
+    return out, int(j0.value), int(b.value)
+
+
+class Sim:
+    """qw_sim_create ... qw_sim_destroy for one or several matrices."""
+
+    def __init__(self, matrices, s_pad: int = 0, precision: int = QW_FP64, fuse_reflection: bool = True,
+                 prune_tau: float = 0.0, row_capacity: int = 0, warp_capacity: int = 0,
+                 renorm: int = -1, stream: int | None = None):
+        lib = load()
+        if not isinstance(matrices, (list, tuple)):
+            matrices = [matrices]
+        self._keep = []
+        arr = (CSC * len(matrices))()
+        for i, m in enumerate(matrices):
+            cp = np.ascontiguousarray(m.colptr, dtype=np.int32)
+            ri = np.ascontiguousarray(m.rowidx, dtype=np.int32)
+            va = np.ascontiguousarray(m.val_q15, dtype=np.int16)
+            self._keep += [cp, ri, va]
+            arr[i] = CSC(int(m.n), int(ri.size), cp.ctypes.data, ri.ctypes.data, va.ctypes.data, int(s_pad))
+        opts = Opts()
+        lib.qw_sim_opts_default(ctypes.byref(opts))
+        opts.precision = precision
+        opts.fuse_reflection = int(bool(fuse_reflection))
+        opts.prune_tau = prune_tau
+        opts.row_capacity = row_capacity
+        opts.warp_capacity = warp_capacity
+        opts.renorm = renorm
+        opts.stream = current_stream() if stream is None else stream
+        h = ctypes.c_void_p()
+        rc = lib.qw_sim_create(arr, len(matrices), ctypes.byref(opts), ctypes.byref(h))
+        if rc:
+            raise QwError(rc, lib.qw_last_error(None).decode())
+        self._h = h
+        self.ns = [int(m.n) for m in matrices]
+        nb, s, ni, by = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        lib.qw_sim_info(h, ctypes.byref(nb), ctypes.byref(s), ctypes.byref(ni), ctypes.byref(by))
+        self.nb, self.s, self.num_instances, self.device_bytes = nb.value, s.value, ni.value, by.value
+
+    def _check(self, rc: int) -> None:
+        if rc:
+            raise QwError(rc, load().qw_last_error(self._h).decode())
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().qw_sim_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # --- the ABI calls ------------------------------------------------------
+    def state_init(self, b, inst: int = 0, apply_T: bool = True) -> None:
+        b = np.asarray(b)
+        re = np.ascontiguousarray(b.real, dtype=np.float64)
+        im = np.ascontiguousarray(b.imag, dtype=np.float64) if np.iscomplexobj(b) else None
+        self._check(load().qw_state_init(self._h, inst, _p(re), None if im is None else _p(im),
+                                         re.size, int(bool(apply_T))))
+
+    def apply_walk_step(self, nsteps: int = 1) -> None:
+        self._check(load().qw_apply_walk_step(self._h, int(nsteps)))
+
+    def apply_qls(self, coeffs: np.ndarray, inst: int = 0) -> tuple[np.ndarray, np.ndarray]:
+        coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
+        j0 = coeffs.size - 1
+        y = np.zeros(2 * self.ns[inst])
+        p = np.zeros(j0 + 1)
+        self._check(load().qw_apply_qls(self._h, inst, _p(coeffs), j0, _p(y), _p(p)))
+        return y[0::2] + 1j * y[1::2], p
+
+    def measure_register(self, reg: str, length: int, inst: int = 0) -> np.ndarray:
+        out = np.zeros(int(length))
+        self._check(load().qw_measure_register(self._h, inst, REGS[reg], _p(out), out.size))
+        return out
+
+    def state_size(self, inst: int = -1) -> int:
+        c = ctypes.c_int64()
+        self._check(load().qw_state_size(self._h, inst, ctypes.byref(c)))
+        return int(c.value)
+
+    def state_export(self, inst: int = -1, key_words: int = 2) -> tuple[np.ndarray, np.ndarray]:
+        """(keys [M, key_words] uint64, amps [M] complex128), keys ascending."""
+        n = self.state_size(inst)
+        keys = np.zeros((max(n, 1), key_words), dtype=np.uint64)
+        amps = np.zeros((max(n, 1), 2))
+        c = ctypes.c_int64()
+        self._check(load().qw_state_export(self._h, inst, key_words, _p(keys), _p(amps), n,
+                                           ctypes.byref(c)))
+        m = min(n, int(c.value))
+        return keys[:m], amps[:m, 0] + 1j * amps[:m, 1]
+
+    def launch_count(self) -> int:
+        return int(load().qw_launch_count(self._h))
+
+    def unpack(self, keys: np.ndarray) -> np.ndarray:
+        """Packed keys -> [M, 8] (jc, j, b1, kc, k, b2, A, inst) per the header's layout."""
+        nb = self.nb
+        widths = [("b2", 1), ("k", nb), ("kc", nb), ("b1", 1), ("j", nb), ("jc", nb), ("A", 16),
+                  ("inst", 16)]
+        big = [int(sum(int(w) << (64 * t) for t, w in enumerate(row))) for row in keys]
+        out = np.zeros((len(big), 8), dtype=np.uint64)
+        order = {"jc": 0, "j": 1, "b1": 2, "kc": 3, "k": 4, "b2": 5, "A": 6, "inst": 7}
+        for i, v in enumerate(big):
+            pos = 0
+            for name, w in widths:
+                out[i, order[name]] = (v >> pos) & ((1 << w) - 1)
+                pos += w
+        return out

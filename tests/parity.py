@@ -1,0 +1,38 @@
+"""Helpers that compare the CUDA path's state with the oracle's (test-only)."""
+from __future__ import annotations
+
+import numpy as np
+
+KEY_FIELDS = ("jc", "j", "b1", "kc", "k", "b2", "A")
+
+
+def gpu_state(sim, inst: int = 0) -> dict:
+    keys, amps = sim.state_export(inst=inst, key_words=2 if 4 * sim.nb + 34 <= 128 else 10)
+    regs = sim.unpack(keys)
+    assert np.all(regs[:, 7] == inst)
+    return {tuple(int(v) for v in r[:7]): complex(a) for r, a in zip(regs, amps)}
+
+
+def oracle_state(o) -> dict:
+    regs, amps = o.export()
+    return {tuple(int(v) for v in r[:7]): complex(a) for r, a in zip(regs, amps)}
+
+
+def compare(gpu: dict, ref: dict, tol: float, drop_below: float = 0.0) -> dict:
+    """Key sets equal (after dropping |a_ref| <= drop_below on both sides) and
+    max |delta a| <= tol.  Returns error statistics."""
+    if drop_below > 0:
+        small = {k for k, v in ref.items() if abs(v) <= drop_below}
+        ref = {k: v for k, v in ref.items() if k not in small}
+        gpu = {k: v for k, v in gpu.items() if k not in small and abs(v) > drop_below}
+    missing = set(ref) - set(gpu)
+    extra = set(gpu) - set(ref)
+    assert not missing and not extra, (
+        f"key sets differ: {len(missing)} missing (e.g. {sorted(missing)[:3]}), "
+        f"{len(extra)} extra (e.g. {sorted(extra)[:3]})")
+    if not ref:
+        return {"max_abs": 0.0, "l2": 0.0, "count": 0}
+    d = np.array([gpu[k] - ref[k] for k in ref])
+    stats = {"max_abs": float(np.abs(d).max()), "l2": float(np.linalg.norm(d)), "count": len(ref)}
+    assert stats["max_abs"] <= tol, stats
+    return stats

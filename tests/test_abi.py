@@ -1,0 +1,108 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every function that
+include/qwalk.h declares, validates its inputs before touching a GPU, and its
+host-only CKS coefficients agree with the oracle's."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2303_06890_gb300 import qwalk
+from paper_2303_06890_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "qwalk.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qw_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = qwalk.load()
+    names = declared_functions()
+    assert len(names) >= 13
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(qwalk.EXPORTED) == set(names)
+
+
+def _csc(matrix, **kw):
+    cp = np.ascontiguousarray(kw.get("colptr", matrix.colptr), dtype=np.int32)
+    ri = np.ascontiguousarray(kw.get("rowidx", matrix.rowidx), dtype=np.int32)
+    va = np.ascontiguousarray(kw.get("val", matrix.val_q15), dtype=np.int16)
+    c = qwalk.CSC(kw.get("n", matrix.n), ri.size, cp.ctypes.data, ri.ctypes.data, va.ctypes.data,
+                  kw.get("s_pad", 0))
+    return c, (cp, ri, va)
+
+
+def _create(csc):
+    lib = qwalk.load()
+    h = ctypes.c_void_p()
+    rc = lib.qw_sim_create(ctypes.byref(csc), 1, None, ctypes.byref(h))
+    return rc, lib.qw_last_error(None).decode()
+
+
+@pytest.mark.parametrize("case", ["unsorted", "duplicate", "range", "asym", "negdiag", "spad", "colptr", "n"])
+def test_create_rejects_bad_matrices_before_any_device_work(case):
+    m = wl.walk_n16().matrix
+    ri = m.rowidx.copy()
+    va = m.val_q15.copy()
+    cp = m.colptr.copy()
+    kw = {}
+    lo, hi = cp[0], cp[1]
+    if case == "unsorted":
+        ri[lo:hi] = ri[lo:hi][::-1]
+        kw = dict(rowidx=ri)
+    elif case == "duplicate":
+        ri[lo + 1] = ri[lo]
+        kw = dict(rowidx=ri)
+    elif case == "range":
+        ri[-1] = m.n
+        kw = dict(rowidx=ri)
+    elif case == "asym":
+        off = next(t for t in range(m.nnz) if ri[t] != np.searchsorted(cp, t, side="right") - 1)
+        va[off] = va[off] // 2 + 1
+        kw = dict(val=va)
+    elif case == "negdiag":
+        d = next(t for t in range(cp[0], cp[1]) if ri[t] == 0)
+        va[d] = -100
+        kw = dict(val=va)
+    elif case == "spad":
+        kw = dict(s_pad=3)
+    elif case == "colptr":
+        cp[-1] += 1
+        kw = dict(colptr=cp)
+    elif case == "n":
+        kw = dict(n=1)
+    csc, keep = _csc(m, **kw)
+    rc, msg = _create(csc)
+    want = qwalk.QW_ERR_ARG if case == "n" else qwalk.QW_ERR_CSC
+    assert rc == want, (rc, msg)
+    assert msg
+
+
+def test_cks_coefficients_match_oracle():
+    from oracle import dense
+    for kappa in (2.0, 10.0, 100.0, 403.9):
+        c, j0, b = qwalk.cks_coefficients(kappa, 1e-3)
+        assert (b, j0) == dense.cks_parameters(kappa, 1e-3)
+        ref = dense.cks_coefficients(b, j0)
+        assert np.abs(c - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_cks_rejects_bad_arguments():
+    lib = qwalk.load()
+    assert lib.qw_cks_coefficients(0.5, 1e-3, None, 0, None, None) == qwalk.QW_ERR_ARG
+    assert lib.qw_cks_coefficients(10.0, 0.0, None, 0, None, None) == qwalk.QW_ERR_ARG
+    assert lib.qw_cks_coefficients(10.0, 1e-3, None, 5, None, None) == qwalk.QW_ERR_ARG
+
+
+def test_null_and_destroy_are_safe():
+    lib = qwalk.load()
+    assert lib.qw_sim_destroy(None) == 0
+    assert lib.qw_state_size(None, 0, None) == qwalk.QW_ERR_ARG
+    assert lib.qw_apply_walk_step(None, 1) == qwalk.QW_ERR_ARG
+    assert lib.qw_launch_count(None) == 0

@@ -1,0 +1,298 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Keys (register values) must match exactly; amplitudes within 1e-12 in FP64.
+FP32-amplitude results are compared with the FP64 oracle after removing
+branches with |a| <= 10 tau32 on both sides; their error is reported."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import dense
+from paper_2303_06890_gb300 import qwalk
+from paper_2303_06890_gb300 import workloads as wl
+
+from parity import compare, gpu_state, oracle_state
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TAU32 = 2.0 ** -20
+
+
+def _sim(w, **kw):
+    return qwalk.Sim(w.matrix, s_pad=w.s, **kw)
+
+
+def _oracle(w):
+    o = oracle.Oracle(w.matrix, w.s)
+    o.init_b(w.b)
+    return o
+
+
+@pytest.mark.parametrize("apply_T", [False, True])
+def test_state_init(apply_T):
+    w = wl.walk_n16()
+    sim = _sim(w)
+    sim.state_init(w.b, apply_T=apply_T)
+    o = _oracle(w)
+    if apply_T:
+        o.apply("T")
+    compare(gpu_state(sim), oracle_state(o), TOL64)
+
+
+@pytest.mark.parametrize("fuse", [True, False])
+def test_walk_n16_every_step(fuse):
+    w = wl.walk_n16()
+    sim = _sim(w, fuse_reflection=fuse)
+    sim.state_init(w.b)
+    o = _oracle(w)
+    o.apply("T")
+    for m in range(w.steps):
+        sim.apply_walk_step(1)
+        o.apply("W")
+        compare(gpu_state(sim), oracle_state(o), TOL64)
+    assert o.violations == 0
+
+
+@pytest.mark.parametrize("n,smax,seed,band", [(24, 4, 1, 0), (48, 8, 2, 1), (100, 8, 3, 0),
+                                              (33, 4, 4, 1), (130, 16, 5, 0), (77, 2, 6, 0)])
+def test_walk_random_cases(n, smax, seed, band):
+    w = wl.small_random(n, smax, seed, band=band)
+    for fuse in (True, False):
+        sim = _sim(w, fuse_reflection=fuse)
+        sim.state_init(w.b)
+        o = _oracle(w)
+        o.apply("T")
+        for _ in range(5):
+            sim.apply_walk_step(1)
+            o.apply("W")
+            compare(gpu_state(sim), oracle_state(o), TOL64)
+
+
+def test_walk_n1024_fp64_100_steps():
+    w = wl.walk_n1024()
+    sim = _sim(w)
+    sim.state_init(w.b)
+    o = _oracle(w)
+    o.apply("T")
+    done = 0
+    for target in (1, 2, 10, 50, 100):
+        sim.apply_walk_step(target - done)
+        for _ in range(target - done):
+            o.apply("W")
+        done = target
+        compare(gpu_state(sim), oracle_state(o), TOL64)
+
+
+def test_walk_n16384_fp64_full_size():
+    w = wl.walk_n16384()
+    sim = _sim(w)
+    sim.state_init(w.b)
+    o = _oracle(w)
+    o.apply("T")
+    compare(gpu_state(sim), oracle_state(o), TOL64)
+    for _ in range(3):
+        sim.apply_walk_step(1)
+        o.apply("W")
+        compare(gpu_state(sim), oracle_state(o), TOL64)
+
+
+def test_fp32_amp_n1024_100_steps():
+    w = wl.walk_n1024()
+    sim = _sim(w, precision=qwalk.QW_FP32_AMP)
+    sim.state_init(w.b)
+    o = _oracle(w)
+    o.apply("T")
+    done = 0
+    for target in (10, 100):
+        sim.apply_walk_step(target - done)
+        for _ in range(target - done):
+            o.apply("W")
+        done = target
+        st = compare(gpu_state(sim), oracle_state(o), 1e-5, drop_below=10 * TAU32)
+        print(f"FP32-amp N=1024 step {target}: max|da| {st['max_abs']:.3e} ||da||_2 {st['l2']:.3e}")
+        assert st["l2"] <= 1e-5
+
+
+def test_fp32_amp_n16384_bench_config():
+    """The benchmarked configuration (N=16384, s=16, complex64 amplitudes with
+    FP64 merge, norm and renormalisation), 20 steps, against the FP64 oracle."""
+    w = wl.walk_n16384()
+    sim = _sim(w, precision=qwalk.QW_FP32_AMP)
+    sim.state_init(w.b)
+    sim.apply_walk_step(w.steps)
+    o = _oracle(w)
+    o.apply("T")
+    for _ in range(w.steps):
+        o.apply("W")
+    st = compare(gpu_state(sim), oracle_state(o), 1e-5, drop_below=10 * TAU32)
+    print(f"FP32-amp N=16384 step 20: max|da| {st['max_abs']:.3e} ||da||_2 {st['l2']:.3e}")
+    assert st["l2"] <= 1e-5
+
+
+def test_measure_register_matches_oracle():
+    w = wl.small_random(40, 8, 11)
+    sim = _sim(w)
+    sim.state_init(w.b)
+    sim.apply_walk_step(5)
+    o = _oracle(w)
+    o.apply("T")
+    for _ in range(5):
+        o.apply("W")
+    for reg in ("jc", "j", "b1", "kc", "k", "b2"):
+        length = 1 << sim.nb
+        got = sim.measure_register(reg, length)
+        want = o.marginal(reg, length)
+        assert np.abs(got - want).max() < 1e-12, reg
+    assert abs(sim.measure_register("j", 1 << sim.nb).sum() - 1.0) < 1e-12
+
+
+def test_chebyshev_identity_at_full_size_via_readout():
+    """Flag-0 blocks read by the QLS path equal T_{2j+1}(A/s) b from the dense
+    recurrence, at N = 16384 (a property that holds at any size)."""
+    w = wl.walk_n16384()
+    a = w.matrix.dense() if w.n <= 4096 else None
+    rng = np.random.default_rng(5)
+    coeffs = rng.standard_normal(4)
+    sim = _sim(w)
+    sim.state_init(w.b)
+    y, p = sim.apply_qls(coeffs)
+    # sparse A/s times vector, from the CSC arrays
+    m = w.matrix
+    cols = np.repeat(np.arange(m.n), np.diff(m.colptr))
+    vals = m.val_q15.astype(np.float64) / 32768.0 / w.s
+
+    def hv(v):
+        out = np.zeros(m.n, dtype=complex)
+        np.add.at(out, m.rowidx, vals * v[cols])
+        return out
+
+    t_prev, t_cur = w.b.astype(complex), hv(w.b.astype(complex))
+    cheb = [t_prev, t_cur]
+    for _ in range(2, 2 * len(coeffs)):
+        t_prev, t_cur = t_cur, 2 * hv(t_cur) - t_prev
+        cheb.append(t_cur)
+    want = sum(c * cheb[2 * j + 1] for j, c in enumerate(coeffs))
+    assert a is None
+    assert np.abs(y - want).max() < 1e-12
+    acc = np.zeros(m.n, dtype=complex)
+    for j, c in enumerate(coeffs):
+        acc += c * cheb[2 * j + 1]
+        assert abs(p[j] - np.vdot(acc, acc).real) < 1e-10 * max(1.0, p[j])
+
+
+def test_qls_n16_matches_oracle():
+    w = wl.walk_n16()
+    b_int, j0 = dense.cks_parameters(w.kappa, 1e-3)
+    coeffs = dense.cks_coefficients(b_int, j0)
+    sim = _sim(w)
+    sim.state_init(w.b)
+    y, p = sim.apply_qls(coeffs)
+    yo, ys, _ = oracle.qls(w.matrix, w.s, w.b, coeffs)
+    assert np.abs(y - yo).max() < 1e-9 * max(1.0, np.abs(yo).max())
+    x = dense.qls_reference(w.matrix.dense(), w.b)
+    assert dense.fidelity(x, y) > 0.999
+
+
+@pytest.mark.parametrize("precision", [qwalk.QW_FP64, qwalk.QW_FP32_AMP])
+def test_qls_n1024_fidelity(precision):
+    w = wl.qls_n1024()
+    coeffs, j0, b_int = qwalk.cks_coefficients(w.kappa, 1e-3)
+    sim = _sim(w, precision=precision)
+    sim.state_init(w.b)
+    y, p = sim.apply_qls(coeffs)
+    a = w.matrix.dense() / w.s
+    t_prev, t_cur = w.b.copy(), a @ w.b
+    want = coeffs[0] * t_cur
+    for j in range(1, j0 + 1):
+        for _ in range(2):
+            t_prev, t_cur = t_cur, 2 * (a @ t_cur) - t_prev
+        want = want + coeffs[j] * t_cur
+    x = dense.qls_reference(w.matrix.dense(), w.b)
+    f = dense.fidelity(x, y)
+    rel = np.linalg.norm(y - want) / np.linalg.norm(want)
+    print(f"QLS N=1024 precision={precision}: j0={j0} F={f:.8f} rel.err vs dense {rel:.3e}")
+    if precision == qwalk.QW_FP64:
+        assert rel < 1e-9
+    else:
+        assert rel < 1e-3
+    assert f > 0.999
+
+
+def test_batched_instances_match_their_oracles():
+    sizes = [(64, 1), (100, 2), (37, 3), (256, 4), (64, 5), (500, 6)]
+    ws = [wl.small_random(n, 8, 40 + seed, band=1) for n, seed in sizes]
+    ws = [w for w in ws if w.s == 8]
+    mats = [w.matrix for w in ws]
+    sim = qwalk.Sim(mats, s_pad=8)
+    for i, w in enumerate(ws):
+        sim.state_init(w.b, inst=i)
+    sim.apply_walk_step(5)
+    for i, w in enumerate(ws):
+        o = oracle.Oracle(w.matrix, 8)
+        o.init_b(w.b)
+        o.apply("T")
+        for _ in range(5):
+            o.apply("W")
+        compare(gpu_state(sim, inst=i), oracle_state(o), TOL64)
+
+
+def test_capacity_overflow_keeps_last_state():
+    w = wl.walk_n16()
+    sim = _sim(w, row_capacity=8, warp_capacity=8)
+    sim.state_init(w.b)
+    before = gpu_state(sim)
+    with pytest.raises(qwalk.QwError) as e:
+        sim.apply_walk_step(3)
+    assert e.value.code == qwalk.QW_ERR_CAPACITY
+    compare(gpu_state(sim), before, 0.0)
+
+
+def test_degenerate_inputs():
+    # all-zero b: empty state, steps are no-ops
+    w = wl.walk_n16()
+    sim = _sim(w)
+    sim.state_init(np.zeros(w.n))
+    assert sim.state_size() == 0
+    sim.apply_walk_step(2)
+    assert sim.state_size() == 0
+    # a single basis vector and a diagonal matrix (s = 1)
+    a = np.diag(np.linspace(0.1, 0.9, 8))
+    from test_oracle_pins import dense_to_matrix
+    m = dense_to_matrix(a)
+    wd = wl.Workload("diag", m, np.eye(8)[3], s=1, steps=3, cond=0, kappa=0)
+    for fuse in (True, False):
+        sim = _sim(wd, fuse_reflection=fuse)
+        sim.state_init(wd.b)
+        o = _oracle(wd)
+        o.apply("T")
+        for _ in range(3):
+            sim.apply_walk_step(1)
+            o.apply("W")
+            compare(gpu_state(sim), oracle_state(o), TOL64)
+    # N = 2 with a full row
+    m2 = dense_to_matrix(np.array([[0.5, -0.7], [-0.7, 0.2]]))
+    w2 = wl.Workload("n2", m2, np.array([0.6, 0.8]), s=2, steps=4, cond=0, kappa=0)
+    sim = _sim(w2)
+    sim.state_init(w2.b)
+    o = _oracle(w2)
+    o.apply("T")
+    for _ in range(4):
+        sim.apply_walk_step(1)
+        o.apply("W")
+        compare(gpu_state(sim), oracle_state(o), TOL64)
+
+
+def test_launch_count_and_reinit():
+    w = wl.walk_n16()
+    sim = _sim(w)
+    sim.state_init(w.b)
+    c0 = sim.launch_count()
+    sim.apply_walk_step(4)
+    assert sim.launch_count() - c0 == 4  # one launch per walk step
+    sim.state_init(w.b)
+    o = _oracle(w)
+    o.apply("T")
+    compare(gpu_state(sim), oracle_state(o), TOL64)
