@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of the sparse-state quantum walk (arXiv 2303.06890) on GB300.
+
+Workload: the quantum walk on a random symmetric N = 16384 matrix with at most
+16 non-zeros per column (s = 16), Q1.15 values, random normalised |b>,
+complex64 amplitudes with FP64 merge, norm and renormalisation -- the
+configuration the paper's headline walk (N = 16384, Table 1 row E) is quoted
+at.  One benchmark step = one walk step W = S T~ P T~^dag of the whole state.
+
+Prints one JSON line: walk steps/s (value), branch entries/s, the plain
+FP64-amplitude path on the same workload, the roofline of the step kernel,
+the end-to-end rate through the C ABI with host buffers, the CPU oracle's rate
+and the SM clocks seen during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own copy of the walk (weak
+scaling, no data exchange); the reported time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "walk steps/s and sparse-state entries/s at n=16384, FP32 vs FP64; HBM GB/s vs peak"
+UNIT = "walk steps/s"
+PROFILE = os.path.join(ROOT, "profiles", "k_step_walk_n16384_s16.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_2303_06890_gb300", "csrc", "qw_kernels.cu")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=4000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--fp64-steps", type=int, default=1000)
+    p.add_argument("--e2e-jobs", type=int, default=10)
+    p.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_hash() -> str:
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic(precision: str):
+    """DRAM bytes per launch of k_step from the committed ncu summary, or None
+    when the kernel source changed since the capture."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != kernel_hash():
+        return None
+    key = f"dram_bytes_per_launch_{precision}"
+    try:
+        return int(float(vals[key]))
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="qw_clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def timed_walk(sim, steps: int, torch, flush) -> tuple[float, list[float]]:
+    """Per-step device time (CUDA events on the simulator's stream) with an
+    untimed L2 flush (a 256 MiB write) before every timed step."""
+    stream = torch.cuda.current_stream()
+    evs = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.enqueue_walk_steps(1)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    sim.sync()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    return sum(ms) / 1000.0, ms
+
+
+def algorithmic_bytes(stats: dict, nb: int, amp_bytes: int) -> tuple[float, float]:
+    """Per step: the bytes the interference ops of the step stream if each
+    reads its input and writes its output once (R^dag, H P H, R), with
+    W_live = ceil((4 nb + 18) / 64) key words; and the bytes the fused kernel
+    must move at least (the state read once and written once)."""
+    steps = max(1, stats["steps"])
+    w_live = -(-(4 * nb + 18) // 64)
+    entry = 8 * w_live + amp_bytes
+    ops = [(stats["in"], stats["after_rdag"]), (stats["after_rdag"], stats["after_hph"]),
+           (stats["after_hph"], stats["out"])]
+    if stats["after_h1"]:
+        ops = [(stats["in"], stats["after_rdag"]), (stats["after_rdag"], stats["after_h1"]),
+               (stats["after_h1"], stats["after_hph"]), (stats["after_hph"], stats["out"])]
+    b_alg = sum(i + o for i, o in ops) * entry / steps
+    b_min = (stats["in"] + stats["out"]) * (8 + amp_bytes) / steps
+    return b_alg, b_min
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_2303_06890_gb300 import qwalk
+    from paper_2303_06890_gb300 import workloads as wl
+
+    w = wl.walk_n16384()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # --- the benchmarked path: complex64 amplitudes, FP64 merge/norm/renorm ---
+    sim = qwalk.Sim(w.matrix, s_pad=w.s, precision=qwalk.QW_FP32_AMP)
+    sim.state_init(w.b, apply_T=True)
+    sim.apply_walk_step(args.warmup)
+    sim.step_stats(reset=True)
+    launches0 = sim.launch_count()
+    clocks = ClockSampler(local_rank)
+    barrier()
+    t_dev, per_step = timed_walk(sim, args.steps, torch, flush)
+    barrier()
+    clk = clocks.stop()
+    gpu_launches = sim.launch_count() - launches0
+    stats = sim.step_stats(reset=True)
+    t_max = max_over_ranks(t_dev)
+    value = world * args.steps / t_max
+    ms_step = 1000.0 * t_max / args.steps
+    entries_per_step = (stats["in"] + stats["after_rdag"] + stats["after_hph"]) / max(1, stats["steps"])
+    b_alg, b_min = algorithmic_bytes(stats, sim.nb, 8)
+    mean_step_s = statistics.mean(per_step) / 1000.0
+    peak, peak_kind = peaks()
+    achieved = b_alg / mean_step_s / 1e9
+    traffic = profiled_traffic("fp32")
+    live_entries = stats["out"] / max(1, stats["steps"])
+    sim.close()
+
+    # --- the plain FP64 path on the same workload ---
+    sim64 = qwalk.Sim(w.matrix, s_pad=w.s, precision=qwalk.QW_FP64)
+    sim64.state_init(w.b, apply_T=True)
+    sim64.apply_walk_step(args.warmup)
+    sim64.step_stats(reset=True)
+    barrier()
+    t64, per64 = timed_walk(sim64, args.fp64_steps, torch, flush)
+    barrier()
+    t64 = max_over_ranks(t64)
+    stats64 = sim64.step_stats(reset=True)
+    b_alg64, _ = algorithmic_bytes(stats64, sim64.nb, 16)
+    fp64 = {"value": world * args.fp64_steps / t64, "unit": UNIT, "steps": args.fp64_steps,
+            "ms_per_step": 1000.0 * t64 / args.fp64_steps,
+            "entries_per_s": world * (stats64["in"] + stats64["after_rdag"] + stats64["after_hph"]) / t64,
+            "achieved_gbs": b_alg64 / statistics.mean(per64) * 1000.0 / 1e9,
+            "traffic": profiled_traffic("fp64")}
+    sim64.close()
+
+    # --- end to end through the C ABI with host buffers ---
+    import numpy as np
+    b_host = torch.from_numpy(np.ascontiguousarray(w.b)).pin_memory()
+    probs_host = torch.empty(w.n, dtype=torch.float64).pin_memory()
+    sim_e = qwalk.Sim(w.matrix, s_pad=w.s, precision=qwalk.QW_FP32_AMP)
+    steps_per_job = w.steps
+    sim_e.state_init(b_host.numpy(), apply_T=True)
+    sim_e.apply_walk_step(2)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_jobs):
+        sim_e.state_init(b_host.numpy(), apply_T=True)  # H2D of |b>
+        sim_e.apply_walk_step(steps_per_job)
+        probs_host.numpy()[:] = sim_e.measure_register("j", w.n)  # D2H of the marginal
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    sim_e.close()
+    e2e = {"value": world * args.e2e_jobs * steps_per_job / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": w.n * 8 / steps_per_job,
+           "d2h_bytes_per_step": w.n * 8 / steps_per_job,
+           "job": f"qw_state_init(|b> from pinned host memory, T~) + {steps_per_job} walk steps "
+                  f"+ qw_measure_register(j) to host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_budget)
+
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "s": w.s, "nnz": int(w.matrix.nnz),
+                   "amplitudes": "complex64 in HBM; FP64 merge, norm, renormalisation",
+                   "steps_per_walk": w.steps, "branches_per_step": live_entries,
+                   "l2": "flushed before every timed step (256 MiB write, untimed)",
+                   "parallelism": f"replicas x{world}"},
+        "entries_per_s": world * entries_per_step / (t_max / args.steps),
+        "fp64": fp64,
+        "fp32_speedup_vs_fp64": value / fp64["value"],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "k_step<float2, WALK_FUSED>",
+                     "algorithmic_bytes_per_launch": b_alg,
+                     "state_bytes_per_launch": b_min,
+                     "state_gbs": b_min / mean_step_s / 1e9},
+        "e2e": e2e,
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(w, budget: float) -> dict:
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    same workload: T~ then walk steps until about ``budget`` seconds pass."""
+    import oracle
+
+    o = oracle.Oracle(w.matrix, w.s)
+    o.init_b(w.b)
+    o.apply("T")
+    steps, t0 = 0, time.perf_counter()
+    while steps < 1 or (time.perf_counter() - t0 < budget and steps < 50):
+        o.apply("W")
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} walk steps of the same N=16384 walk after T~ ({dt:.1f} s, "
+                      f"{o.size()} branches), plain C FP64 register-level oracle"}
+
+
+def run_reference(args, rank, world):
+    """The oracle timed as the reference arm: rank 0 only, bounded sample."""
+    if rank != 0:
+        return
+    from paper_2303_06890_gb300 import workloads as wl
+    import oracle
+
+    w = wl.walk_n16384()
+    o = oracle.Oracle(w.matrix, w.s)
+    o.init_b(w.b)
+    o.apply("T")
+    for _ in range(min(args.warmup, 1)):
+        o.apply("W")
+    budget = 60.0
+    steps, t0 = 0, time.perf_counter()
+    while steps < max(1, args.steps) and (steps < 1 or time.perf_counter() - t0 < budget):
+        o.apply("W")
+        steps += 1
+    dt = time.perf_counter() - t0
+    v = steps / dt
+    sample = (f"{steps} of the requested {args.steps} walk steps (60 s budget) of the N=16384 walk, "
+              f"after T~ and {min(args.warmup, 1)} warm-up step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": min(args.warmup, 1), "ms_per_step": 1000.0 * dt / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w.name, "n": w.n, "s": w.s},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -74,7 +74,7 @@ typedef struct {
     int32_t fuse_reflection; /* 1 (default): H P H of one walk step as the per-group
                                 reflection 2|+><+| - 1; 0: H, P, H as three ops */
     double prune_tau;        /* branches with |a| <= tau are removed after each
-                                interference op; 0 = 1e-13 (FP64), 2^-20 (FP32_AMP) */
+                                interference op; 0 = 1e-13 (FP64), 2^-24 (FP32_AMP) */
     int32_t row_capacity;    /* branches per (jc, j, b1) row between steps; 0 = auto (4 s) */
     int32_t warp_capacity;   /* branches one warp holds on chip while it runs a row
                                 through a step; 0 = auto */
@@ -125,6 +125,23 @@ int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, const double *b
 int qw_apply_walk_step(qw_sim *sim, int64_t nsteps);
 
 /*
+ * Issue nsteps walk steps on the simulator's stream and return without
+ * synchronising (for pipelining, timing and stream capture).  Device errors
+ * of these steps are reported by the next call that synchronises (qw_sync,
+ * qw_apply_walk_step, the measurement and export calls).
+ * Errors: QW_ERR_ARG, QW_ERR_STATE, QW_ERR_CUDA (launch failure).
+ */
+int qw_enqueue_walk_steps(qw_sim *sim, int64_t nsteps);
+
+/*
+ * Synchronise the stream and read the device status word.  On a device
+ * error the state is the output of the last step that completed cleanly
+ * (later steps did nothing) and the error code is returned:
+ * QW_ERR_CAPACITY, QW_ERR_DEVICE_STATUS or QW_ERR_CUDA.
+ */
+int qw_sync(qw_sim *sim);
+
+/*
  * CKS coefficients of Eq. (fx): b = ceil(kappa^2 ln(kappa/eps)),
  * j0 = ceil(sqrt(b ln(4 b / eps))), a_j = 4 (-1)^j sum_{i=j+1}^{b} C(2b, b+i) / 2^(2b)
  * for j = 0..j0, computed in log space.  Writes min(j0+1, cap) coefficients;
@@ -172,6 +189,16 @@ int qw_state_export(qw_sim *sim, int32_t inst, int32_t key_words, uint64_t *keys
 /* nb, s, number of instances, and the total device bytes held (all nullable). */
 int qw_sim_info(const qw_sim *sim, int32_t *nb, int32_t *s, int32_t *num_instances,
                 int64_t *device_bytes);
+
+/*
+ * Branch counters of the walk steps run since creation or the last reset,
+ * summed over steps: out[0] rows processed, out[1] branches entering the
+ * steps (input of R^dag), out[2] after R^dag, out[3] after the first H (only
+ * with fuse_reflection = 0), out[4] after H P H, out[5] after R (branches
+ * written), out[6] steps counted.  Writes min(len, 8) values; reset != 0
+ * zeroes the counters afterwards.  Errors: QW_ERR_ARG, QW_ERR_CUDA.
+ */
+int qw_step_stats(qw_sim *sim, int64_t *out, int32_t len, int32_t reset);
 
 /* Kernel launches issued by this simulator since creation (for accounting). */
 int64_t qw_launch_count(const qw_sim *sim);

@@ -32,6 +32,7 @@ struct Scalars {
     unsigned int done_ctr;
     unsigned int pad1;
     unsigned long long counter;
+    unsigned long long stats[QW_NSTAT];
 };
 
 thread_local std::string g_create_error;
@@ -66,6 +67,8 @@ struct qw_sim {
     QwBufDev buf[3]{};
     int cur = 0;                     /* buffer holding the state */
     int scale_slot = 0;              /* Scalars.scale slot of the state's pending scale */
+    int sync_cur = 0, sync_slot = 0; /* cur / scale_slot at the last clean sync */
+    int64_t sync_done = 0;           /* device steps_done at the last clean sync */
     bool has_state = false;
     bool fresh_T = false;            /* state is T~|b~> and untouched since */
     int grid_walk = 1, grid_t = 1;
@@ -241,7 +244,7 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     d.s = s;
     d.L = ceil_log2(s);
     d.ninst = ninst;
-    const double tau = o.prune_tau > 0 ? o.prune_tau : (sim->fp32 ? std::ldexp(1.0, -20) : 1e-13);
+    const double tau = o.prune_tau > 0 ? o.prune_tau : (sim->fp32 ? std::ldexp(1.0, -24) : 1e-13);
     d.tau2 = tau * tau;
     d.inv_sqrt_s = 1.0 / std::sqrt((double)s);
     d.two_over_s = 2.0 / (double)s;
@@ -380,22 +383,38 @@ static const double *pending_scale(qw_sim *sim)
     return sim->renorm ? &sim->sc->scale[sim->scale_slot] : nullptr;
 }
 
-/* Read and clear the device status word; map it to an error code. */
+/* Synchronise, read the device status word and the clean-step counter.  On
+ * an error, steps issued after the failing one did nothing on the device, so
+ * the state is the output of the last clean step: move the host view there.
+ * Then clear the status and map it to an error code. */
 static int check_status(qw_sim *sim, const char *where)
 {
-    int32_t st = 0;
-    cudaError_t e = cudaMemcpyAsync(&st, &sim->sc->status, 4, cudaMemcpyDeviceToHost, sim->stream);
+    struct {
+        int32_t status, pad;
+        int64_t done;
+    } h{};
+    cudaError_t e = cudaMemcpyAsync(&h, &sim->sc->status, sizeof h, cudaMemcpyDeviceToHost, sim->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
     if (e != cudaSuccess) return cuda_fail(sim, e, where);
-    if (st == 0) return QW_OK;
+    const int64_t good = h.done - sim->sync_done;
+    if (h.status != 0) {
+        sim->cur = (int)((sim->sync_cur + good) % 3);
+        sim->scale_slot = sim->sync_slot ^ (int)(good & 1);
+    }
+    sim->sync_cur = sim->cur;
+    sim->sync_slot = sim->scale_slot;
+    sim->sync_done = h.done;
+    if (h.status == 0) return QW_OK;
     const int32_t zero = 0;
     cudaMemcpyAsync(&sim->sc->status, &zero, 4, cudaMemcpyHostToDevice, sim->stream);
     cudaStreamSynchronize(sim->stream);
+    const int32_t st = h.status;
     std::string m = std::string(where) + ": device status";
     if (st & QW_ST_ROW_OVERFLOW) m += " [row bucket overflow: raise row_capacity]";
     if (st & QW_ST_WARP_OVERFLOW) m += " [on-chip row buffer overflow: raise warp_capacity]";
     if (st & QW_ST_SPILL_FULL) m += " [garbage-row table full]";
     if (st & QW_ST_ANCILLA) m += " [register A not returned to zero]";
+    m += "; state kept after " + std::to_string(good) + " clean steps since the last sync";
     const int code = (st & (QW_ST_ROW_OVERFLOW | QW_ST_WARP_OVERFLOW | QW_ST_SPILL_FULL))
                          ? QW_ERR_CAPACITY
                          : QW_ERR_DEVICE_STATUS;
@@ -415,6 +434,7 @@ static QwStepArgs step_args(qw_sim *sim, int mode)
     a.renorm_target = &sim->sc->renorm_target;
     a.steps_done = &sim->sc->steps_done;
     a.status = &sim->sc->status;
+    a.stats = sim->sc->stats;
     a.qls_y = sim->qls_y;
     return a;
 }
@@ -464,8 +484,9 @@ extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, cons
         z.scale[0] = z.scale[1] = 1.0;
         z.renorm_target = nb2;
         QW_CUDA(sim, cudaMemcpyAsync(sim->sc, &z, sizeof z, cudaMemcpyHostToDevice, sim->stream));
-        sim->scale_slot = 0;
-        sim->cur = 0;
+        sim->scale_slot = sim->sync_slot = 0;
+        sim->cur = sim->sync_cur = 0;
+        sim->sync_done = 0;
     } else {
         double target = 0.0;
         for (double v : sim->init_norm2) target += v;
@@ -495,39 +516,30 @@ extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, cons
     return QW_OK;
 }
 
-/* Run nsteps walk steps; on a device error, roll the host view back to the
- * buffer of the last step that completed cleanly (steps after a failed one
- * are no-ops on the device). */
-static int run_steps(qw_sim *sim, int64_t nsteps, const char *where)
-{
-    int64_t done0 = 0;
-    QW_CUDA(sim, cudaMemcpyAsync(&done0, &sim->sc->steps_done, 8, cudaMemcpyDeviceToHost, sim->stream));
-    QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
-    const int cur0 = sim->cur, slot0 = sim->scale_slot;
-    for (int64_t t = 0; t < nsteps; ++t) {
-        int rc = launch_walk(sim, 0.0, 0);
-        if (rc != QW_OK) return rc;
-    }
-    int rc = check_status(sim, where);
-    if (rc != QW_OK) {
-        int64_t done1 = 0;
-        cudaMemcpy(&done1, &sim->sc->steps_done, 8, cudaMemcpyDeviceToHost);
-        const int64_t good = done1 - done0;
-        sim->cur = (int)((cur0 + good) % 3);
-        sim->scale_slot = slot0 ^ (int)(good & 1);
-        sim->err += " (state kept after " + std::to_string(good) + " completed steps)";
-    }
-    return rc;
-}
-
-extern "C" int qw_apply_walk_step(qw_sim *sim, int64_t nsteps)
+extern "C" int qw_enqueue_walk_steps(qw_sim *sim, int64_t nsteps)
 {
     if (!sim) return QW_ERR_ARG;
     if (nsteps < 0) return fail(sim, QW_ERR_ARG, "nsteps < 0");
     if (!sim->has_state) return fail(sim, QW_ERR_STATE, "no state: call qw_state_init first");
-    if (nsteps == 0) return QW_OK;
-    sim->fresh_T = false;
-    return run_steps(sim, nsteps, "qw_apply_walk_step");
+    if (nsteps > 0) sim->fresh_T = false;
+    for (int64_t t = 0; t < nsteps; ++t) {
+        int rc = launch_walk(sim, 0.0, 0);
+        if (rc != QW_OK) return rc;
+    }
+    return QW_OK;
+}
+
+extern "C" int qw_sync(qw_sim *sim)
+{
+    if (!sim) return QW_ERR_ARG;
+    return check_status(sim, "qw_sync");
+}
+
+extern "C" int qw_apply_walk_step(qw_sim *sim, int64_t nsteps)
+{
+    int rc = qw_enqueue_walk_steps(sim, nsteps);
+    if (rc != QW_OK) return rc;
+    return check_status(sim, "qw_apply_walk_step");
 }
 
 extern "C" int qw_cks_coefficients(double kappa, double eps, double *coeffs, int64_t cap,
@@ -722,5 +734,16 @@ extern "C" int qw_state_export(qw_sim *sim, int32_t inst, int32_t key_words, uin
         amps[2 * i] = hamp[(size_t)src].x;
         amps[2 * i + 1] = hamp[(size_t)src].y;
     }
+    return QW_OK;
+}
+
+extern "C" int qw_step_stats(qw_sim *sim, int64_t *out, int32_t len, int32_t reset)
+{
+    if (!sim || (len > 0 && !out)) return QW_ERR_ARG;
+    unsigned long long h[QW_NSTAT] = {0};
+    QW_CUDA(sim, cudaMemcpyAsync(h, sim->sc->stats, sizeof h, cudaMemcpyDeviceToHost, sim->stream));
+    if (reset) QW_CUDA(sim, cudaMemsetAsync(sim->sc->stats, 0, sizeof h, sim->stream));
+    QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
+    for (int i = 0; i < len && i < QW_NSTAT; ++i) out[i] = (int64_t)h[i];
     return QW_OK;
 }

@@ -35,6 +35,16 @@
 #define QW_ST_SPILL_FULL 4     /* no free spill slot for a jc != 0 row */
 #define QW_ST_ANCILLA 8        /* register A not zero where it must be */
 
+/* per-step branch counters (index into QwStepArgs.stats) */
+#define QW_STAT_ROWS 0      /* rows processed */
+#define QW_STAT_IN 1        /* branches entering the step (input of R^dag) */
+#define QW_STAT_RDAG 2      /* after R^dag (input of the H P H stage) */
+#define QW_STAT_H1 3        /* after the first H (literal mode only) */
+#define QW_STAT_HPH 4       /* after H P H (input of R) */
+#define QW_STAT_OUT 5       /* after R (branches written) */
+#define QW_STAT_STEPS 6     /* clean steps counted */
+#define QW_NSTAT 8
+
 /* step kernel modes */
 #define QW_MODE_WALK_FUSED 0   /* T~^dag, (H P H as one reflection), T~, S */
 #define QW_MODE_WALK_LITERAL 1 /* T~^dag, H, P, H, T~, S */
@@ -76,6 +86,7 @@ struct QwStepArgs {
     const double *renorm_target; /* sum of the instances' initial ||b||^2 */
     int64_t *steps_done;     /* incremented by each step that completes cleanly */
     int32_t *status;
+    unsigned long long *stats; /* QW_STAT_* counters, accumulated (nullable) */
     double2 *qls_y;          /* flag-0 accumulator (nullable) */
     double qls_coef;         /* Y += coef * Pi_0 tau at this step's midpoint */
     int qls_readout;

@@ -609,6 +609,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_step(QwSimDev d, QwBufDev in, Qw
     const int64_t blo = (MODE == QW_MODE_T) ? a.bucket_lo : 0;
     const int64_t bhi = skip ? blo : ((MODE == QW_MODE_T) ? a.bucket_hi : d.total_buckets);
     double nrm = 0.0;
+    unsigned long long st_rows = 0, st_in = 0, st_rdag = 0, st_h1 = 0, st_hph = 0, st_out = 0;
 
     for (int64_t b = blo + (int64_t)blockIdx.x * WARPS + warp; b < bhi;
          b += (int64_t)gridDim.x * WARPS) {
@@ -644,10 +645,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_step(QwSimDev d, QwBufDev in, Qw
             nrm += emit_row<AmpT>(d, r, kP, aP, n, in, false, a.status);
             continue;
         }
+        st_rows++;
+        st_in += n;
         /* T~^dag */
         chain<1>(d, r, kP, n);
         warp_sort(kP, aP, n, kQ, aQ);
         n = rot_op<true>(d, r, kQ, aQ, n, kP, aP, C, a.status);
+        st_rdag += n;
         chain<2>(d, r, kP, n);
         warp_sort(kP, aP, n, kQ, aQ);
         if (MODE == QW_MODE_WALK_FUSED) {
@@ -655,6 +659,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_step(QwSimDev d, QwBufDev in, Qw
             n = reflect_op(d, r, kQ, aQ, n, kP, aP, C, a.status, a);
         } else {
             n = hadamard_op(d, r, kQ, aQ, n, kP, aP, C, a.status, a, true);
+            st_h1 += n;
             phase_op(d, r, kP, aP, n);
             n = hadamard_op(d, r, kP, aP, n, kQ, aQ, C, a.status, a, false);
             for (int i = lane; i < n; i += 32) {
@@ -663,11 +668,21 @@ __global__ void __launch_bounds__(WARPS * 32) k_step(QwSimDev d, QwBufDev in, Qw
             }
             __syncwarp();
         }
+        st_hph += n;
         /* rest of T~, then S */
         chain<3>(d, r, kP, n);
         warp_sort(kP, aP, n, kQ, aQ);
         n = rot_op<false>(d, r, kQ, aQ, n, kP, aP, C, a.status);
+        st_out += n;
         nrm += emit_row<AmpT>(d, r, kP, aP, n, out, true, a.status);
+    }
+    if (a.stats && lane == 0 && st_rows) {
+        atomicAdd(a.stats + QW_STAT_ROWS, st_rows);
+        atomicAdd(a.stats + QW_STAT_IN, st_in);
+        atomicAdd(a.stats + QW_STAT_RDAG, st_rdag);
+        if (st_h1) atomicAdd(a.stats + QW_STAT_H1, st_h1);
+        atomicAdd(a.stats + QW_STAT_HPH, st_hph);
+        atomicAdd(a.stats + QW_STAT_OUT, st_out);
     }
 
     /* ||output||^2: block partial sums, reduced in block order by the last block */
@@ -693,6 +708,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_step(QwSimDev d, QwBufDev in, Qw
             if (a.scale_out)
                 *a.scale_out = (a.renorm && tot > 0.0) ? sqrt(*a.renorm_target / tot) : 1.0;
             if (a.steps_done) *a.steps_done += 1;
+            if (a.stats && MODE != QW_MODE_T) a.stats[QW_STAT_STEPS] += 1;
         }
         *a.done_ctr = 0u;
     }

@@ -26,8 +26,10 @@ QW_FP32_AMP = 1
 REGS = {"jc": 0, "j": 1, "b1": 2, "kc": 3, "k": 4, "b2": 5}
 
 EXPORTED = ("qw_sim_opts_default", "qw_sim_create", "qw_state_init", "qw_apply_walk_step",
+            "qw_enqueue_walk_steps", "qw_sync",
             "qw_cks_coefficients", "qw_apply_qls", "qw_measure_register", "qw_state_size",
-            "qw_state_export", "qw_sim_info", "qw_launch_count", "qw_sim_destroy", "qw_last_error")
+            "qw_state_export", "qw_sim_info", "qw_step_stats", "qw_launch_count", "qw_sim_destroy",
+            "qw_last_error")
 
 
 class QwError(RuntimeError):
@@ -72,20 +74,24 @@ def load(build_if_missing: bool = True):
     lib.qw_sim_create.argtypes = [P, i32, P, P]
     lib.qw_state_init.argtypes = [P, i32, P, P, i32, i32]
     lib.qw_apply_walk_step.argtypes = [P, i64]
+    lib.qw_enqueue_walk_steps.argtypes = [P, i64]
+    lib.qw_sync.argtypes = [P]
     lib.qw_cks_coefficients.argtypes = [dbl, dbl, P, i64, P, P]
     lib.qw_apply_qls.argtypes = [P, i32, P, i64, P, P]
     lib.qw_measure_register.argtypes = [P, i32, i32, P, i64]
     lib.qw_state_size.argtypes = [P, i32, P]
     lib.qw_state_export.argtypes = [P, i32, i32, P, P, i64, P]
     lib.qw_sim_info.argtypes = [P, P, P, P, P]
+    lib.qw_step_stats.argtypes = [P, P, i32, i32]
     lib.qw_launch_count.argtypes = [P]
     lib.qw_launch_count.restype = i64
     lib.qw_sim_destroy.argtypes = [P]
     lib.qw_last_error.argtypes = [P]
     lib.qw_last_error.restype = ctypes.c_char_p
-    for name in ("qw_sim_create", "qw_state_init", "qw_apply_walk_step", "qw_cks_coefficients",
+    for name in ("qw_sim_create", "qw_state_init", "qw_apply_walk_step", "qw_enqueue_walk_steps",
+                 "qw_sync", "qw_cks_coefficients",
                  "qw_apply_qls", "qw_measure_register", "qw_state_size", "qw_state_export",
-                 "qw_sim_info", "qw_sim_destroy"):
+                 "qw_sim_info", "qw_step_stats", "qw_sim_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -185,6 +191,12 @@ class Sim:
     def apply_walk_step(self, nsteps: int = 1) -> None:
         self._check(load().qw_apply_walk_step(self._h, int(nsteps)))
 
+    def enqueue_walk_steps(self, nsteps: int = 1) -> None:
+        self._check(load().qw_enqueue_walk_steps(self._h, int(nsteps)))
+
+    def sync(self) -> None:
+        self._check(load().qw_sync(self._h))
+
     def apply_qls(self, coeffs: np.ndarray, inst: int = 0) -> tuple[np.ndarray, np.ndarray]:
         coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
         j0 = coeffs.size - 1
@@ -213,6 +225,14 @@ class Sim:
                                            ctypes.byref(c)))
         m = min(n, int(c.value))
         return keys[:m], amps[:m, 0] + 1j * amps[:m, 1]
+
+    STAT_NAMES = ("rows", "in", "after_rdag", "after_h1", "after_hph", "out", "steps")
+
+    def step_stats(self, reset: bool = False) -> dict:
+        """qw_step_stats: per-op branch counters summed over the steps run."""
+        out = np.zeros(8, dtype=np.int64)
+        self._check(load().qw_step_stats(self._h, _p(out), 8, int(bool(reset))))
+        return dict(zip(self.STAT_NAMES, (int(v) for v in out[:7])))
 
     def launch_count(self) -> int:
         return int(load().qw_launch_count(self._h))

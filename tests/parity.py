@@ -36,3 +36,18 @@ def compare(gpu: dict, ref: dict, tol: float, drop_below: float = 0.0) -> dict:
     stats = {"max_abs": float(np.abs(d).max()), "l2": float(np.linalg.norm(d)), "count": len(ref)}
     assert stats["max_abs"] <= tol, stats
     return stats
+
+
+def compare_union(gpu: dict, ref: dict, max_tol: float, l2_tol: float) -> dict:
+    """Reduced-precision comparison: the difference over the union of keys
+    (a key missing on one side counts as amplitude 0) must satisfy both
+    bounds; so a branch kept on one side only is allowed exactly when its
+    amplitude is below max_tol."""
+    keys = set(gpu) | set(ref)
+    d = np.array([gpu.get(k, 0j) - ref.get(k, 0j) for k in keys]) if keys else np.zeros(1)
+    only = [abs(gpu.get(k, 0j)) + abs(ref.get(k, 0j)) for k in set(gpu) ^ set(ref)]
+    stats = {"max_abs": float(np.abs(d).max()), "l2": float(np.linalg.norm(d)),
+             "count": len(keys), "one_sided": len(only),
+             "one_sided_max": float(max(only)) if only else 0.0}
+    assert stats["max_abs"] <= max_tol and stats["l2"] <= l2_tol, stats
+    return stats
