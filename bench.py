@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "walk steps/s and sparse-state entries/s at n=16384, FP32 vs FP64; HBM GB/s vs peak"
 UNIT = "walk steps/s"
-PROFILE = os.path.join(ROOT, "profiles", "k_step_walk_n16384_s16.md")
+PROFILE = os.path.join(ROOT, "profiles", "k_walk_n16384_s16.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_2303_06890_gb300", "csrc", "qw_kernels.cu")
 L2_FLUSH_BYTES = 256 << 20
 
@@ -294,7 +294,7 @@ def run_ours(args, rank, world, local_rank):
         "fp32_speedup_vs_fp64": value / fp64["value"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "k_step<float2, WALK_FUSED>",
+                     "kernel": "k_walk<float2>",
                      "algorithmic_bytes_per_launch": b_alg,
                      "state_bytes_per_launch": b_min,
                      "state_gbs": b_min / mean_step_s / 1e9},

@@ -75,6 +75,7 @@ struct qw_sim {
     /* device allocations */
     uint32_t *img = nullptr;
     double2 *fg = nullptr;
+    float4 *fg32 = nullptr;
     int32_t *inst_n = nullptr;
     int64_t *inst_img = nullptr, *inst_bkt = nullptr;
     double *partials = nullptr;
@@ -246,6 +247,13 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     d.ninst = ninst;
     const double tau = o.prune_tau > 0 ? o.prune_tau : (sim->fp32 ? std::ldexp(1.0, -24) : 1e-13);
     d.tau2 = tau * tau;
+    {
+        const double hi = tau * (1.0 + std::ldexp(1.0, -30));
+        const double lo = tau * std::sqrt(0.5) * (1.0 - std::ldexp(1.0, -30));
+        std::memcpy(&d.tau_hi_bits, &hi, 8);
+        std::memcpy(&d.tau_lo_bits, &lo, 8);
+        d.tau2f = (float)(tau * tau);
+    }
     d.inv_sqrt_s = 1.0 / std::sqrt((double)s);
     d.two_over_s = 2.0 / (double)s;
     d.cap_row = o.row_capacity > 0 ? o.row_capacity : std::max(8, 4 * s);
@@ -278,10 +286,14 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     std::vector<uint32_t> himage((size_t)img_words);
     for (int i = 0; i < ninst; ++i) build_image(mats[i], s, himage.data() + himg[(size_t)i]);
     std::vector<double2> hfg(65536);
+    std::vector<float4> hfg32(65536);
     for (int c = 0; c < 65536; ++c) {
         const int16_t q = (int16_t)(uint16_t)c;
         const double mag = std::fabs((double)q / 32768.0);
-        hfg[(size_t)c] = make_double2(std::sqrt(mag), std::sqrt(1.0 - mag));
+        const double f = std::sqrt(mag), g = std::sqrt(1.0 - mag);
+        hfg[(size_t)c] = make_double2(f, g);
+        const float fh = (float)f, gh = (float)g;
+        hfg32[(size_t)c] = make_float4(fh, (float)(f - (double)fh), gh, (float)(g - (double)gh));
     }
 
     auto bail = [&](cudaError_t e, const char *what) {
@@ -294,16 +306,19 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     if ((e = (call)) != cudaSuccess) return bail(e, #call)
     QW_TRY(dalloc(sim, &sim->img, (size_t)img_words));
     QW_TRY(dalloc(sim, &sim->fg, 65536));
+    QW_TRY(dalloc(sim, &sim->fg32, 65536));
     QW_TRY(dalloc(sim, &sim->inst_n, (size_t)ninst));
     QW_TRY(dalloc(sim, &sim->inst_img, (size_t)ninst));
     QW_TRY(dalloc(sim, &sim->inst_bkt, (size_t)ninst + 1));
     QW_TRY(cudaMemcpy(sim->img, himage.data(), himage.size() * 4, cudaMemcpyHostToDevice));
     QW_TRY(cudaMemcpy(sim->fg, hfg.data(), hfg.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    QW_TRY(cudaMemcpy(sim->fg32, hfg32.data(), hfg32.size() * sizeof(float4), cudaMemcpyHostToDevice));
     QW_TRY(cudaMemcpy(sim->inst_n, hn.data(), hn.size() * 4, cudaMemcpyHostToDevice));
     QW_TRY(cudaMemcpy(sim->inst_img, himg.data(), himg.size() * 8, cudaMemcpyHostToDevice));
     QW_TRY(cudaMemcpy(sim->inst_bkt, hbkt.data(), hbkt.size() * 8, cudaMemcpyHostToDevice));
     d.img = sim->img;
     d.fg = sim->fg;
+    d.fg32 = sim->fg32;
     d.inst_n = sim->inst_n;
     d.inst_img = sim->inst_img;
     d.inst_bkt = sim->inst_bkt;
@@ -342,6 +357,7 @@ extern "C" int qw_sim_destroy(qw_sim *sim)
     else cudaDeviceSynchronize();
     cudaFree(sim->img);
     cudaFree(sim->fg);
+    cudaFree(sim->fg32);
     cudaFree(sim->inst_n);
     cudaFree(sim->inst_img);
     cudaFree(sim->inst_bkt);

@@ -58,10 +58,14 @@ struct QwSimDev {
     int64_t dense_buckets;    /* sum over instances */
     int64_t total_buckets;    /* dense + spill */
     double tau2;              /* prune threshold squared */
+    uint64_t tau_hi_bits;     /* bits of tau (1 + 2^-30): |x| above it => kept */
+    uint64_t tau_lo_bits;     /* bits of tau sqrt(1/2) (1 - 2^-30): |x|,|y| at most it => pruned */
+    float tau2f;              /* tau^2 as float (complex64 path) */
     double inv_sqrt_s;        /* 1 / sqrt(s) */
     double two_over_s;        /* 2 / s */
     const uint32_t *img;      /* QRAM words: column << 16 | Q1.15 value */
     const double2 *fg;        /* per Q1.15 code: (sqrt|a|, sqrt(1-|a|)) */
+    const float4 *fg32;       /* the same as float pairs: (hi, lo) of each, hi + lo ~ 48 bits */
     const int32_t *inst_n;    /* N per instance */
     const int64_t *inst_img;  /* image offset per instance */
     const int64_t *inst_bkt;  /* first dense bucket per instance, ninst + 1 entries */

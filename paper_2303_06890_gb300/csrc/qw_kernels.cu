@@ -297,80 +297,6 @@ __device__ int rot_op(const QwSimDev &d, const Row &r, const uint64_t *ks, const
     return out;
 }
 
-/* H P H of one walk step as one op (input sorted in the H layout).  Per
- * Hadamard group (all registers equal except the low L bits of k): P keeps
- * the sign of the all-zero branch (b1 = k = b2 = jc = kc = 0) and flips the
- * rest, so on a group whose other registers are zero H P H = 2|+><+| - 1,
- * i.e. a_u -> (2/s) sum_v a_v - a_u for all s values of u, and on every other
- * group H P H = -1.  Optionally reads the flag-0 amplitude of T~^dag's output,
- * (1/sqrt s) sum_v a_v of the group whose key is 0, into the QLS accumulator. */
-__device__ int reflect_op(const QwSimDev &d, const Row &r, const uint64_t *ks, const double2 *as,
-                          int n, uint64_t *kd, double2 *ad, int cap, int32_t *status,
-                          const QwStepArgs &a)
-{
-    const int lane = lane_id();
-    const int L = d.L, s = d.s;
-    const bool rowzero = (r.jc == 0 && r.b1 == 0);
-    const uint64_t zmask = (1ull << (1 + 2 * d.nb - L)) - 1; /* b2, k_high, kc */
-    const uint64_t umask = (uint64_t)s - 1;
-    int out = 0;
-    for (int base = 0; base < n; base += 32) {
-        const int i = base + lane;
-        const bool valid = i < n;
-        const uint64_t k = valid ? ks[i] : 0;
-        const uint64_t g = k >> L;
-        const bool zt = valid && rowzero && ((g & zmask) == 0);
-        const bool head = valid && (i == 0 || (ks[i - 1] >> L) != g);
-        int cnt = 0;
-        double2 sum = make_double2(0, 0);
-        int gend = i;
-        if (valid && !zt) cnt = keep(as[i], d.tau2) ? 1 : 0;
-        if (zt && head) {
-            while (gend < n && (ks[gend] >> L) == g) {
-                sum = cadd(sum, as[gend]);
-                gend++;
-            }
-            int m = i;
-            for (int u = 0; u < s; ++u) {
-                double2 au = make_double2(0, 0);
-                if (m < gend && (ks[m] & umask) == (uint64_t)u) au = as[m++];
-                cnt += keep(csub(cscale(d.two_over_s, sum), au), d.tau2) ? 1 : 0;
-            }
-            if (g == 0 && a.qls_readout && r.valid) {
-                const double2 y = cscale(d.inv_sqrt_s, sum);
-                double2 acc = a.qls_y[r.j];
-                acc.x += a.qls_coef * y.x;
-                acc.y += a.qls_coef * y.y;
-                a.qls_y[r.j] = acc;
-            }
-        }
-        int total;
-        int pos = out + warp_excl_scan(cnt, total);
-        if (valid && !zt && cnt) {
-            if (pos < cap) { kd[pos] = k; ad[pos] = cneg(as[i]); }
-        }
-        if (zt && head) {
-            int m = i;
-            for (int u = 0; u < s; ++u) {
-                double2 au = make_double2(0, 0);
-                if (m < gend && (ks[m] & umask) == (uint64_t)u) au = as[m++];
-                const double2 o = csub(cscale(d.two_over_s, sum), au);
-                if (keep(o, d.tau2)) {
-                    if (pos < cap) { kd[pos] = (g << L) | (uint64_t)u; ad[pos] = o; }
-                    pos++;
-                }
-            }
-        }
-        out += total;
-    }
-    __syncwarp();
-    if (out > cap) {
-        if (lane == 0) atomicOr(status, QW_ST_WARP_OVERFLOW);
-        out = cap;
-    }
-    return out;
-}
-
 /* Hadamard on the low L bits of k as a plain interference op (input sorted in
  * the H layout): each group emits the s outputs (1/sqrt s) sum_v (-1)^{u.v} a_v.
  * With readout set, the u = 0 output of the group whose key is 0 (the flag-0
@@ -577,6 +503,8 @@ __device__ void chain(const QwSimDev &d, const Row &r, uint64_t *ks, int n)
     __syncwarp();
 }
 
+/* Sort-based step kernel: T~ alone (MODE_T, in place on a bucket range) or a
+ * walk step with H, P and H as three interference ops (MODE_WALK_LITERAL). */
 template <typename AmpT, int MODE>
 __global__ void __launch_bounds__(WARPS * 32) k_step(QwSimDev d, QwBufDev in, QwBufDev out,
                                                      QwBufDev clr, QwStepArgs a)
@@ -654,20 +582,16 @@ __global__ void __launch_bounds__(WARPS * 32) k_step(QwSimDev d, QwBufDev in, Qw
         st_rdag += n;
         chain<2>(d, r, kP, n);
         warp_sort(kP, aP, n, kQ, aQ);
-        if (MODE == QW_MODE_WALK_FUSED) {
-            /* H (end of T~^dag), P, H (start of T~) */
-            n = reflect_op(d, r, kQ, aQ, n, kP, aP, C, a.status, a);
-        } else {
-            n = hadamard_op(d, r, kQ, aQ, n, kP, aP, C, a.status, a, true);
-            st_h1 += n;
-            phase_op(d, r, kP, aP, n);
-            n = hadamard_op(d, r, kP, aP, n, kQ, aQ, C, a.status, a, false);
-            for (int i = lane; i < n; i += 32) {
-                kP[i] = kQ[i];
-                aP[i] = aQ[i];
-            }
-            __syncwarp();
+        /* H (end of T~^dag), P, H (start of T~) as three interference ops */
+        n = hadamard_op(d, r, kQ, aQ, n, kP, aP, C, a.status, a, true);
+        st_h1 += n;
+        phase_op(d, r, kP, aP, n);
+        n = hadamard_op(d, r, kP, aP, n, kQ, aQ, C, a.status, a, false);
+        for (int i = lane; i < n; i += 32) {
+            kP[i] = kQ[i];
+            aP[i] = aQ[i];
         }
+        __syncwarp();
         st_hph += n;
         /* rest of T~, then S */
         chain<3>(d, r, kP, n);
@@ -709,6 +633,534 @@ __global__ void __launch_bounds__(WARPS * 32) k_step(QwSimDev d, QwBufDev in, Qw
                 *a.scale_out = (a.renorm && tot > 0.0) ? sqrt(*a.renorm_target / tot) : 1.0;
             if (a.steps_done) *a.steps_done += 1;
             if (a.stats && MODE != QW_MODE_T) a.stats[QW_STAT_STEPS] += 1;
+        }
+        *a.done_ctr = 0u;
+    }
+}
+
+template <typename AmpT>
+__host__ __device__ inline size_t walk_smem_per_warp(const QwSimDev &d)
+{
+    /* keys x2, amps x2, zero-group buffer, staged QRAM row, partner indices */
+    size_t b = (size_t)d.warp_cap * 2 * (sizeof(uint64_t) + sizeof(AmpT)) + (size_t)d.s * sizeof(AmpT) +
+               (size_t)d.s * sizeof(uint32_t) + (size_t)d.s * sizeof(int16_t);
+    return (b + 15) & ~(size_t)15;
+}
+
+/* ==== fused walk step: one sort per row, b2-pairs kept adjacent ============== */
+/*
+ * The register maps O_s', O_s'^dag and O_A' never read or write b2, so two
+ * branches that differ only in b2 before a map still differ only in b2 after
+ * it: b2-pairs are invariant.  The row is sorted once at load (R layout, b2 at
+ * bit 0, so pairs become adjacent); every later op keeps pairs adjacent with
+ * the b2 = 0 member first, and the rotations find their partner next to them.
+ * H P H needs no grouping at all: a branch outside the zero-type groups is
+ * only negated, and the zero-type groups are found by a predicate on the key.
+ */
+
+template <typename AmpT> struct Amp;
+
+/* complex128 path: FP64 arithmetic throughout */
+template <> struct Amp<double2> {
+    typedef double2 T;
+    struct Norm {
+        double v = 0.0;
+        __device__ void add(T a) { v = fma(a.x, a.x, fma(a.y, a.y, v)); }
+        __device__ double get() const { return v; }
+    };
+    __device__ static T zero() { return make_double2(0.0, 0.0); }
+    __device__ static T neg(T a) { return make_double2(-a.x, -a.y); }
+    __device__ static double2 to_d(T a) { return a; }
+    __device__ static T from_d(double2 a) { return a; }
+    /* |a|^2 > tau^2 exactly as the un-fused FP64 formula, decided from the
+       exponent bits except in a narrow band around tau */
+    __device__ static bool keep(const QwSimDev &d, T a)
+    {
+        const uint64_t ux = (uint64_t)__double_as_longlong(a.x) & 0x7fffffffffffffffull;
+        const uint64_t uy = (uint64_t)__double_as_longlong(a.y) & 0x7fffffffffffffffull;
+        const uint64_t um = ux > uy ? ux : uy;
+        if (um > d.tau_hi_bits) return true;
+        if (um <= d.tau_lo_bits) return false;
+        return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y)) > d.tau2;
+    }
+    struct Scale {
+        double s;
+        __device__ explicit Scale(double v) : s(v) {}
+        __device__ T apply(T a) const { return make_double2(a.x * s, a.y * s); }
+    };
+    /* (A x + B y) per component, FP64 */
+    __device__ static void rot(const QwSimDev &d, uint32_t A, bool dag, bool sneg, T a0, T a1, T &o0, T &o1);
+};
+
+/* complex64 path: amplitudes are float; each rotation output f a0 +- g a1 is
+   formed from error-free products and an error-free sum on the FP32 pipe
+   (f, g held as float pairs with ~48 significant bits) and rounded once. */
+template <> struct Amp<float2> {
+    typedef float2 T;
+    struct Norm { /* float-pair accumulator, exact up to ~2^-46 relative */
+        float hi = 0.f, lo = 0.f;
+        __device__ void add(T a)
+        {
+            const float v = __fadd_rn(__fmul_rn(a.x, a.x), __fmul_rn(a.y, a.y));
+            const float s = __fadd_rn(hi, v);
+            const float bp = __fsub_rn(s, hi);
+            lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(v, bp)));
+            hi = s;
+        }
+        __device__ double get() const { return (double)hi + (double)lo; }
+    };
+    __device__ static T zero() { return make_float2(0.f, 0.f); }
+    __device__ static T neg(T a) { return make_float2(-a.x, -a.y); }
+    __device__ static double2 to_d(T a) { return make_double2((double)a.x, (double)a.y); }
+    __device__ static T from_d(double2 a) { return make_float2((float)a.x, (float)a.y); }
+    __device__ static bool keep(const QwSimDev &d, T a)
+    {
+        return __fadd_rn(__fmul_rn(a.x, a.x), __fmul_rn(a.y, a.y)) > d.tau2f;
+    }
+    /* a * s with s = sh + sl, rounded once */
+    __device__ static float mul_split(float a, float sh, float sl)
+    {
+        const float p = __fmul_rn(sh, a);
+        float e = __fmaf_rn(sh, a, -p);
+        e = __fmaf_rn(sl, a, e);
+        return __fadd_rn(p, e);
+    }
+    struct Scale { /* the FP64 factor as a float pair, applied with one rounding */
+        float sh, sl;
+        __device__ explicit Scale(double v) : sh((float)v), sl((float)(v - (double)(float)v)) {}
+        __device__ T apply(T a) const { return make_float2(mul_split(a.x, sh, sl), mul_split(a.y, sh, sl)); }
+    };
+    /* round(A x + B y), A = ah + al, B = bh + bl: two error-free products and
+       an error-free sum, one final rounding */
+    __device__ static float dot2(float ah, float al, float x, float bh, float bl, float y)
+    {
+        const float p1 = __fmul_rn(ah, x);
+        float e1 = __fmaf_rn(ah, x, -p1);
+        e1 = __fmaf_rn(al, x, e1);
+        const float p2 = __fmul_rn(bh, y);
+        float e2 = __fmaf_rn(bh, y, -p2);
+        e2 = __fmaf_rn(bl, y, e2);
+        const float s = __fadd_rn(p1, p2);
+        const float bp = __fsub_rn(s, p1);
+        const float t = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bp)), __fsub_rn(p2, bp));
+        return __fadd_rn(s, __fadd_rn(t, __fadd_rn(e1, e2)));
+    }
+    __device__ static void rot(const QwSimDev &d, uint32_t A, bool dag, bool sneg, T a0, T a1, T &o0, T &o1);
+};
+
+/* multiply by 1 (real f) or by i*sigma (imaginary f), sigma = sneg ? -1 : 1 */
+template <typename T>
+__device__ __forceinline__ T rho(T a, bool imag, bool sneg)
+{
+    T r = a;
+    if (imag) {
+        r.x = sneg ? a.y : -a.y;
+        r.y = sneg ? -a.x : a.x;
+    }
+    return r;
+}
+
+/* R:    o0 = f a0 - g a1,        o1 = g a0 + conj(f) a1
+ * R^dag: o0 = conj(f) a0 + g a1, o1 = f a1 - g a0
+ * with f = fm (a >= 0) or i sigma fm (a < 0): f x = fm rho(x, sigma),
+ * conj(f) x = fm rho(x, -sigma). */
+__device__ void Amp<double2>::rot(const QwSimDev &d, uint32_t A, bool dag, bool sneg, T a0, T a1,
+                                  T &o0, T &o1)
+{
+    const double2 t = __ldg(d.fg + A);
+    const double fm = t.x, g = t.y;
+    const bool imag = (int16_t)(uint16_t)A < 0;
+    const double2 x0 = rho(a0, imag, dag ? !sneg : sneg);
+    const double2 x1 = rho(a1, imag, dag ? sneg : !sneg);
+    if (!dag) {
+        o0 = make_double2(fma(fm, x0.x, -g * a1.x), fma(fm, x0.y, -g * a1.y));
+        o1 = make_double2(fma(g, a0.x, fm * x1.x), fma(g, a0.y, fm * x1.y));
+    } else {
+        o0 = make_double2(fma(fm, x0.x, g * a1.x), fma(fm, x0.y, g * a1.y));
+        o1 = make_double2(fma(fm, x1.x, -g * a0.x), fma(fm, x1.y, -g * a0.y));
+    }
+}
+
+__device__ void Amp<float2>::rot(const QwSimDev &d, uint32_t A, bool dag, bool sneg, T a0, T a1,
+                                 T &o0, T &o1)
+{
+    const float4 t = __ldg(d.fg32 + A); /* fh, fl, gh, gl */
+    const bool imag = (int16_t)(uint16_t)A < 0;
+    const float2 x0 = rho(a0, imag, dag ? !sneg : sneg);
+    const float2 x1 = rho(a1, imag, dag ? sneg : !sneg);
+    if (!dag) {
+        o0 = make_float2(dot2(t.x, t.y, x0.x, -t.z, -t.w, a1.x), dot2(t.x, t.y, x0.y, -t.z, -t.w, a1.y));
+        o1 = make_float2(dot2(t.z, t.w, a0.x, t.x, t.y, x1.x), dot2(t.z, t.w, a0.y, t.x, t.y, x1.y));
+    } else {
+        o0 = make_float2(dot2(t.x, t.y, x0.x, t.z, t.w, a1.x), dot2(t.x, t.y, x0.y, t.z, t.w, a1.y));
+        o1 = make_float2(dot2(t.x, t.y, x1.x, -t.z, -t.w, a0.x), dot2(t.x, t.y, x1.y, -t.z, -t.w, a0.y));
+    }
+}
+
+/* Load-time grouping: put b2-pairs next to each other, b2 = 0 first.  A row
+ * that fits one warp pairs by a warp match on key >> 1; a longer row is
+ * sorted by key. */
+template <typename AmpT>
+__device__ void pair_up(const uint64_t *ks, const AmpT *as, int n, uint64_t *kd, AmpT *ad)
+{
+    const int lane = lane_id();
+    if (n <= 32) {
+        const bool valid = lane < n;
+        /* inactive lanes get keys whose k >> 1 are distinct and above every real key */
+        const uint64_t k = valid ? ks[lane] : (~0ull - 2ull * (uint64_t)lane);
+        const AmpT a = valid ? as[lane] : Amp<AmpT>::zero();
+        const unsigned m = __match_any_sync(FULL, k >> 1);
+        const unsigned other = m & ~(1u << lane);
+        const bool head = valid && ((k & 1) == 0 || other == 0);
+        const int cnt = head ? (other ? 2 : 1) : 0;
+        int total;
+        const int pos = warp_excl_scan(cnt, total);
+        const int src = other ? (__ffs(other) - 1) : lane;
+        const uint64_t pk = __shfl_sync(FULL, k, src);
+        AmpT pa;
+        pa.x = __shfl_sync(FULL, a.x, src);
+        pa.y = __shfl_sync(FULL, a.y, src);
+        if (head) {
+            kd[pos] = k;
+            ad[pos] = a;
+            if (cnt == 2) {
+                kd[pos + 1] = pk;
+                ad[pos + 1] = pa;
+            }
+        }
+        __syncwarp();
+        return;
+    }
+    for (int i = lane; i < n; i += 32) {
+        const uint64_t ki = ks[i];
+        int r = 0;
+        for (int t = 0; t < n; ++t) r += (ks[t] < ki);
+        kd[r] = ki;
+        ad[r] = as[i];
+    }
+    __syncwarp();
+}
+
+/* R or R^dag on adjacent b2-pairs (R layout); outputs stay pair-adjacent. */
+template <bool DAG, typename AmpT>
+__device__ int rot_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, const AmpT *as, int n,
+                         uint64_t *kd, AmpT *ad, int cap, int32_t *status)
+{
+    const int lane = lane_id();
+    const uint64_t kmask = (1ull << d.nb) - 1;
+    int out = 0;
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        const bool valid = i < n;
+        const uint64_t k = valid ? ks[i] : 0;
+        const bool is_end = valid && i > 0 && ks[i - 1] == (k ^ 1ull);
+        const bool head = valid && !is_end;
+        AmpT o0 = Amp<AmpT>::zero(), o1 = Amp<AmpT>::zero();
+        bool c0 = false, c1 = false;
+        if (head) {
+            AmpT a0 = Amp<AmpT>::zero(), a1 = Amp<AmpT>::zero();
+            if ((k & 1ull) == 0) {
+                a0 = as[i];
+                if (i + 1 < n && ks[i + 1] == (k | 1ull)) a1 = as[i + 1];
+            } else {
+                a1 = as[i];
+            }
+            const uint32_t A = (uint32_t)(k >> (1 + 2 * d.nb)) & 0xffffu;
+            const uint32_t kreg = (uint32_t)((k >> 1) & kmask);
+            Amp<AmpT>::rot(d, A, DAG, r.j > kreg, a0, a1, o0, o1);
+            c0 = Amp<AmpT>::keep(d, o0);
+            c1 = Amp<AmpT>::keep(d, o1);
+        }
+        int total;
+        int pos = out + warp_excl_scan((int)c0 + (int)c1, total);
+        if (c0) {
+            if (pos < cap) { kd[pos] = k & ~1ull; ad[pos] = o0; }
+            pos++;
+        }
+        if (c1) {
+            if (pos < cap) { kd[pos] = k | 1ull; ad[pos] = o1; }
+        }
+        out += total;
+    }
+    __syncwarp();
+    if (out > cap) {
+        if (lane == 0) atomicOr(status, QW_ST_WARP_OVERFLOW);
+        out = cap;
+    }
+    return out;
+}
+
+/* H P H of one walk step without sorting (R-layout keys, pairs adjacent).
+ * P keeps the sign of the all-zero branch only, so a Hadamard group (fixed
+ * registers except the low L bits of k) is either zero-type -- row jc = b1 = 0
+ * and kc = k_high = b2 = 0, any A -- where H P H = 2|+><+| - 1 maps
+ * a_u -> (2/s) sum_v a_v - a_u for all s values of u, or H P H = -1.  Output:
+ * the other branches negated in their order, then per zero-type group (by A)
+ * the s outputs (u, b2 = 0) each followed by its b2 = 1 partner.  The group
+ * sum is FP64.  With readout, (1/sqrt s) sum_v a_v of the A = 0 group -- the
+ * flag-0 amplitude of T~^dag's output -- goes into the QLS accumulator. */
+template <typename AmpT>
+__device__ int reflect_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, const AmpT *as,
+                             int n, uint64_t *kd, AmpT *ad, int cap, int32_t *status,
+                             const QwStepArgs &a, AmpT *zbuf, int16_t *pbuf)
+{
+    const int lane = lane_id();
+    const int s = d.s;
+    const int ash = 1 + 2 * d.nb; /* A field shift */
+    const uint64_t zm = ((1ull << ash) - 1) & ~((1ull << (d.L + 1)) - 1); /* k_high | kc */
+    const bool rowzero = (r.jc == 0 && r.b1 == 0);
+    int out = 0;
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        const bool valid = i < n;
+        const uint64_t k = valid ? ks[i] : 0;
+        const bool zp = rowzero && (k & zm) == 0;
+        const AmpT v = valid ? as[i] : Amp<AmpT>::zero();
+        const bool c = valid && !zp && Amp<AmpT>::keep(d, v);
+        int total;
+        const int pos = out + warp_excl_scan((int)c, total);
+        if (c && pos < cap) {
+            kd[pos] = k;
+            ad[pos] = Amp<AmpT>::neg(v);
+        }
+        out += total;
+    }
+    if (rowzero) {
+        int64_t prevA = -1;
+        for (;;) {
+            /* next group: the smallest A above the previous among zero-type keys */
+            uint32_t amin = 0xffffffffu;
+            for (int base = 0; base < n; base += 32) {
+                const int i = base + lane;
+                if (i < n) {
+                    const uint64_t k = ks[i];
+                    const uint32_t A = (uint32_t)(k >> ash);
+                    if ((k & zm) == 0 && (int64_t)A > prevA && A < amin) amin = A;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) amin = min(amin, __shfl_xor_sync(FULL, amin, o));
+            if (amin == 0xffffffffu) break;
+            for (int t = lane; t < s; t += 32) {
+                zbuf[t] = Amp<AmpT>::zero();
+                pbuf[t] = -1;
+            }
+            __syncwarp();
+            double2 part = make_double2(0.0, 0.0);
+            for (int base = 0; base < n; base += 32) {
+                const int i = base + lane;
+                if (i < n) {
+                    const uint64_t k = ks[i];
+                    if ((k & zm) == 0 && (uint32_t)(k >> ash) == amin) {
+                        const int u = (int)((k >> 1) & (uint64_t)(s - 1));
+                        if ((k & 1ull) == 0) {
+                            zbuf[u] = as[i];
+                            const double2 z = Amp<AmpT>::to_d(as[i]);
+                            part.x += z.x;
+                            part.y += z.y;
+                        } else {
+                            pbuf[u] = (int16_t)i;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            const double sx = warp_sum(part.x), sy = warp_sum(part.y);
+            const double cx = d.two_over_s * sx, cy = d.two_over_s * sy;
+            if (amin == 0 && a.qls_readout && r.valid && lane == 0) {
+                double2 acc = a.qls_y[r.j];
+                acc.x += a.qls_coef * (d.inv_sqrt_s * sx);
+                acc.y += a.qls_coef * (d.inv_sqrt_s * sy);
+                a.qls_y[r.j] = acc;
+            }
+            const uint64_t gkey = (uint64_t)amin << ash;
+            for (int ub = 0; ub < s; ub += 32) {
+                const int u = ub + lane;
+                const bool vu = u < s;
+                AmpT o0 = Amp<AmpT>::zero();
+                int p = -1;
+                if (vu) {
+                    const double2 au = Amp<AmpT>::to_d(zbuf[u]);
+                    o0 = Amp<AmpT>::from_d(make_double2(cx - au.x, cy - au.y));
+                    p = pbuf[u];
+                }
+                const bool c0 = vu && Amp<AmpT>::keep(d, o0);
+                const bool c1 = p >= 0;
+                int total;
+                int pos = out + warp_excl_scan((int)c0 + (int)c1, total);
+                const uint64_t k0 = gkey | ((uint64_t)u << 1);
+                if (c0) {
+                    if (pos < cap) { kd[pos] = k0; ad[pos] = o0; }
+                    pos++;
+                }
+                if (c1 && pos < cap) {
+                    kd[pos] = k0 | 1ull;
+                    ad[pos] = Amp<AmpT>::neg(as[p]);
+                }
+                out += total;
+            }
+            __syncwarp();
+            prevA = amin;
+        }
+    }
+    __syncwarp();
+    if (out > cap) {
+        if (lane == 0) atomicOr(status, QW_ST_WARP_OVERFLOW);
+        out = cap;
+    }
+    return out;
+}
+
+/* register maps in place, R layout */
+template <int CHAIN>
+__device__ void chain_r(const QwSimDev &d, const Row &r, uint64_t *ks, int n)
+{
+    for (int i = lane_id(); i < n; i += 32) {
+        Regs x = decode_r(ks[i], d.nb);
+        if (CHAIN == 1) { /* start of T~^dag */
+            op_osdag(d, r, x);
+            op_oa(d, r, x);
+            op_os(d, r, x);
+        } else if (CHAIN == 2) { /* after R^dag */
+            op_osdag(d, r, x);
+            op_oa(d, r, x);
+        } else { /* after H of T~ */
+            op_oa(d, r, x);
+            op_os(d, r, x);
+        }
+        ks[i] = encode_r(x, d.nb);
+    }
+    __syncwarp();
+}
+
+/* last register maps of T~, S, and the append to the new rows' buckets */
+template <typename AmpT>
+__device__ void emit_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, const AmpT *as, int n,
+                           const QwBufDev &out, int32_t *status, typename Amp<AmpT>::Norm &nrm)
+{
+    for (int i = lane_id(); i < n; i += 32) {
+        Regs x = decode_r(ks[i], d.nb);
+        op_osdag(d, r, x);
+        op_oa(d, r, x);
+        op_os(d, r, x);
+        if (x.A != 0) atomicOr(status, QW_ST_ANCILLA);
+        Regs y = x;
+        y.kc = r.jc;
+        y.k = r.j;
+        y.b2 = r.b1;
+        const int64_t b = bucket_of(d, out, r.inst, x.kc, x.k, x.b2, status);
+        if (b < 0) continue;
+        const int pos = atomicAdd(out.count + b, 1);
+        if (pos >= d.cap_row) {
+            atomicOr(status, QW_ST_ROW_OVERFLOW);
+            continue;
+        }
+        const int64_t slot = b * (int64_t)d.cap_row + pos;
+        out.key[slot] = encode_r(y, d.nb);
+        static_cast<AmpT *>(out.amp)[slot] = as[i];
+        nrm.add(as[i]);
+    }
+}
+
+template <typename AmpT>
+__global__ void __launch_bounds__(WARPS * 32, 4) k_walk(QwSimDev d, QwBufDev in, QwBufDev out,
+                                                     QwBufDev clr, QwStepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double block_part[WARPS];
+    __shared__ int is_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int C = d.warp_cap;
+    const size_t per_warp = walk_smem_per_warp<AmpT>(d);
+    unsigned char *base = smem + per_warp * warp;
+    uint64_t *kP = reinterpret_cast<uint64_t *>(base);
+    uint64_t *kQ = kP + C;
+    AmpT *aP = reinterpret_cast<AmpT *>(kQ + C);
+    AmpT *aQ = aP + C;
+    AmpT *zbuf = aQ + C;
+    uint32_t *simg = reinterpret_cast<uint32_t *>(zbuf + d.s);
+    int16_t *pbuf = reinterpret_cast<int16_t *>(simg + d.s);
+
+    const bool skip = *(volatile int32_t *)a.status != 0;
+    if (!skip) { /* clear X_{t+2} for the step after this one */
+        const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t b = tid; b < d.total_buckets; b += nthr) clr.count[b] = 0;
+        for (int64_t t = tid; t < d.spill_slots; t += nthr) clr.spill[t] = QW_SPILL_EMPTY;
+    }
+    const bool rescale = a.scale_in != nullptr;
+    const typename Amp<AmpT>::Scale scale(rescale ? *a.scale_in : 1.0);
+    const int64_t bhi = skip ? 0 : d.total_buckets;
+    typename Amp<AmpT>::Norm nrm;
+    unsigned long long st_rows = 0, st_in = 0, st_rdag = 0, st_hph = 0, st_out = 0;
+
+    for (int64_t b = (int64_t)blockIdx.x * WARPS + warp; b < bhi; b += (int64_t)gridDim.x * WARPS) {
+        int n = in.count[b];
+        if (n <= 0) continue;
+        if (n > d.cap_row) n = d.cap_row;
+        Row r;
+        if (!row_of(d, in, b, r)) continue;
+        if (n > C) {
+            if (lane == 0) atomicOr(a.status, QW_ST_WARP_OVERFLOW);
+            continue;
+        }
+        r.simg = simg;
+        for (int t = lane; t < d.s; t += 32)
+            simg[t] = r.valid ? __ldg(d.img + r.img_base + (int64_t)r.j * d.s + t) : 0u;
+        const int64_t row0 = b * (int64_t)d.cap_row;
+        const AmpT *src = static_cast<const AmpT *>(in.amp) + row0;
+        for (int i = lane; i < n; i += 32) {
+            kQ[i] = in.key[row0 + i];
+            AmpT v = src[i];
+            if (rescale) v = scale.apply(v);
+            aQ[i] = v;
+        }
+        __syncwarp();
+        st_rows++;
+        st_in += n;
+        pair_up<AmpT>(kQ, aQ, n, kP, aP);
+        chain_r<1>(d, r, kP, n);                                               /* T~^dag ... */
+        n = rot_pairs<true, AmpT>(d, r, kP, aP, n, kQ, aQ, C, a.status);       /* R^dag */
+        st_rdag += n;
+        chain_r<2>(d, r, kQ, n);
+        n = reflect_pairs<AmpT>(d, r, kQ, aQ, n, kP, aP, C, a.status, a, zbuf, pbuf); /* H P H */
+        st_hph += n;
+        chain_r<3>(d, r, kP, n);                                               /* ... T~ */
+        n = rot_pairs<false, AmpT>(d, r, kP, aP, n, kQ, aQ, C, a.status);      /* R */
+        st_out += n;
+        emit_pairs<AmpT>(d, r, kQ, aQ, n, out, a.status, nrm);                 /* S */
+        __syncwarp();
+    }
+    if (a.stats && lane == 0 && st_rows) {
+        atomicAdd(a.stats + QW_STAT_ROWS, st_rows);
+        atomicAdd(a.stats + QW_STAT_IN, st_in);
+        atomicAdd(a.stats + QW_STAT_RDAG, st_rdag);
+        atomicAdd(a.stats + QW_STAT_HPH, st_hph);
+        atomicAdd(a.stats + QW_STAT_OUT, st_out);
+    }
+    double nv = warp_sum(nrm.get());
+    if (lane == 0) block_part[warp] = nv;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < WARPS; ++w) sum += block_part[w];
+        a.partials[blockIdx.x] = sum;
+        __threadfence();
+        const unsigned prev = atomicAdd(a.done_ctr, 1u);
+        is_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (is_last && threadIdx.x == 0) {
+        __threadfence();
+        double tot = 0.0;
+        for (unsigned bb = 0; bb < gridDim.x; ++bb) tot += __ldcg(a.partials + bb);
+        const bool clean = *(volatile int32_t *)a.status == 0;
+        if (clean) {
+            *a.norm_out = tot;
+            if (a.scale_out)
+                *a.scale_out = (a.renorm && tot > 0.0) ? sqrt(*a.renorm_target / tot) : 1.0;
+            if (a.steps_done) *a.steps_done += 1;
+            if (a.stats) a.stats[QW_STAT_STEPS] += 1;
         }
         *a.done_ctr = 0u;
     }
@@ -848,6 +1300,29 @@ template <typename AmpT, int MODE> size_t step_smem(const QwSimDev &d)
                             (((size_t)d.s * sizeof(uint32_t) + 15) & ~(size_t)15));
 }
 
+template <typename AmpT>
+int walk_grid_t(const QwSimDev &d)
+{
+    const size_t sm = (size_t)WARPS * walk_smem_per_warp<AmpT>(d);
+    cudaFuncSetAttribute(k_walk<AmpT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<AmpT>, WARPS * 32, sm);
+    if (per_sm < 1) per_sm = 1;
+    int64_t want = (d.total_buckets + WARPS - 1) / WARPS;
+    int64_t g = (int64_t)per_sm * qw_sm_count();
+    if (want < g) g = want;
+    return (int)(g < 1 ? 1 : g);
+}
+
+template <typename AmpT>
+cudaError_t launch_walk_t(const QwSimDev &d, const QwBufDev &in, const QwBufDev &out,
+                          const QwBufDev &clr, const QwStepArgs &a, int grid, cudaStream_t st)
+{
+    const size_t sm = (size_t)WARPS * walk_smem_per_warp<AmpT>(d);
+    k_walk<AmpT><<<grid, WARPS * 32, sm, st>>>(d, in, out, clr, a);
+    return cudaGetLastError();
+}
+
 template <typename AmpT, int MODE>
 int step_grid_t(const QwSimDev &d)
 {
@@ -887,12 +1362,11 @@ int qw_sm_count(void)
 
 int qw_step_grid(const QwSimDev &d, int fp32, int mode)
 {
+    if (mode == QW_MODE_WALK_FUSED) return fp32 ? walk_grid_t<float2>(d) : walk_grid_t<double2>(d);
     if (fp32) {
-        if (mode == QW_MODE_WALK_FUSED) return step_grid_t<float2, QW_MODE_WALK_FUSED>(d);
         if (mode == QW_MODE_WALK_LITERAL) return step_grid_t<float2, QW_MODE_WALK_LITERAL>(d);
         return step_grid_t<float2, QW_MODE_T>(d);
     }
-    if (mode == QW_MODE_WALK_FUSED) return step_grid_t<double2, QW_MODE_WALK_FUSED>(d);
     if (mode == QW_MODE_WALK_LITERAL) return step_grid_t<double2, QW_MODE_WALK_LITERAL>(d);
     return step_grid_t<double2, QW_MODE_T>(d);
 }
@@ -901,15 +1375,14 @@ cudaError_t qw_launch_step(const QwSimDev &d, const QwBufDev &in, const QwBufDev
                            const QwBufDev &clr, const QwStepArgs &a, int fp32, int grid,
                            cudaStream_t st)
 {
+    if (a.mode == QW_MODE_WALK_FUSED)
+        return fp32 ? launch_walk_t<float2>(d, in, out, clr, a, grid, st)
+                    : launch_walk_t<double2>(d, in, out, clr, a, grid, st);
     if (fp32) {
-        if (a.mode == QW_MODE_WALK_FUSED)
-            return launch_step_t<float2, QW_MODE_WALK_FUSED>(d, in, out, clr, a, grid, st);
         if (a.mode == QW_MODE_WALK_LITERAL)
             return launch_step_t<float2, QW_MODE_WALK_LITERAL>(d, in, out, clr, a, grid, st);
         return launch_step_t<float2, QW_MODE_T>(d, in, out, clr, a, grid, st);
     }
-    if (a.mode == QW_MODE_WALK_FUSED)
-        return launch_step_t<double2, QW_MODE_WALK_FUSED>(d, in, out, clr, a, grid, st);
     if (a.mode == QW_MODE_WALK_LITERAL)
         return launch_step_t<double2, QW_MODE_WALK_LITERAL>(d, in, out, clr, a, grid, st);
     return launch_step_t<double2, QW_MODE_T>(d, in, out, clr, a, grid, st);
