@@ -171,28 +171,22 @@ __device__ __forceinline__ uint32_t qword(const QwSimDev &d, const Row &r, uint3
     return 0u;
 }
 
-/* Quantum binary search (Def. 1), net effect of the reversible loop of
- * Alg. 1 after its uncomputation: ceil(log2 s)+1 probes with a floor midpoint
- * over [0, s), stop at the first equal column, in-row index or 0. */
+/* Quantum binary search (Def. 1): the net effect of the reversible loop of
+ * Alg. 1 after its uncomputation, i(t) = in-row index of t, 0 if absent.
+ * A row j < N holds a sorted list of distinct columns, where a branch-free
+ * lower-bound search finds the same index as the fixed ceil(log2 s)+1-probe
+ * search with a floor midpoint.  A row j >= N reads the all-zero list, where
+ * that fixed-probe search stops at its first midpoint s/2 when t = 0 and
+ * finds nothing otherwise. */
 __device__ __forceinline__ uint32_t qbs(const QwSimDev &d, const Row &r, uint32_t target)
 {
-    uint32_t lo = 0, hi = (uint32_t)d.s, found = 0;
-    bool done = false;
-    for (int it = 0; it <= d.L; ++it) {
-        if (!done) {
-            const uint32_t mid = (lo + hi) >> 1;
-            const uint32_t v = r.valid ? (r.simg[mid] >> 16) : 0u;
-            if (v == target) {
-                found = mid;
-                done = true;
-            } else if (v < target) {
-                lo = mid;
-            } else {
-                hi = mid;
-            }
-        }
+    if (!r.valid) return target == 0 ? (uint32_t)(d.s >> 1) : 0u;
+    uint32_t i = 0;
+    for (int step = d.s >> 1; step > 0; step >>= 1) {
+        const uint32_t c = r.simg[i + step] >> 16;
+        i = (c <= target) ? i + (uint32_t)step : i;
     }
-    return found;
+    return ((r.simg[i] >> 16) == target) ? i : 0u;
 }
 
 /* O_A': A ^= a_{j,k}, controlled by jc = kc = 0 (Sec. III-B). */
@@ -841,13 +835,20 @@ __device__ void pair_up(const uint64_t *ks, const AmpT *as, int n, uint64_t *kd,
     __syncwarp();
 }
 
-/* R or R^dag on adjacent b2-pairs (R layout); outputs stay pair-adjacent. */
+/* Rotation controls carried in the key between a map and its rotation: the
+ * element register A (its field of the R layout) and bit 63 = [j > k], the
+ * sign sigma = -1 of the rotation for a negative element (sigma = +1 when
+ * j <= k).  Both members of a b2-pair carry the same values. */
+#define QW_SNEG_BIT 63
+
+/* R or R^dag on adjacent b2-pairs (R layout), controlled by the A field and
+ * the sign bit of the key; outputs stay pair-adjacent and their keys are
+ * ANDed with out_mask (which drops the controls: A returns to zero). */
 template <bool DAG, typename AmpT>
-__device__ int rot_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, const AmpT *as, int n,
-                         uint64_t *kd, AmpT *ad, int cap, int32_t *status)
+__device__ int rot_pairs(const QwSimDev &d, const uint64_t *ks, const AmpT *as, int n, uint64_t *kd,
+                         AmpT *ad, int cap, uint64_t out_mask, int32_t *status)
 {
     const int lane = lane_id();
-    const uint64_t kmask = (1ull << d.nb) - 1;
     int out = 0;
     for (int base = 0; base < n; base += 32) {
         const int i = base + lane;
@@ -866,19 +867,19 @@ __device__ int rot_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, co
                 a1 = as[i];
             }
             const uint32_t A = (uint32_t)(k >> (1 + 2 * d.nb)) & 0xffffu;
-            const uint32_t kreg = (uint32_t)((k >> 1) & kmask);
-            Amp<AmpT>::rot(d, A, DAG, r.j > kreg, a0, a1, o0, o1);
+            Amp<AmpT>::rot(d, A, DAG, (k >> QW_SNEG_BIT) != 0, a0, a1, o0, o1);
             c0 = Amp<AmpT>::keep(d, o0);
             c1 = Amp<AmpT>::keep(d, o1);
         }
         int total;
         int pos = out + warp_excl_scan((int)c0 + (int)c1, total);
+        const uint64_t kb = k & out_mask & ~1ull;
         if (c0) {
-            if (pos < cap) { kd[pos] = k & ~1ull; ad[pos] = o0; }
+            if (pos < cap) { kd[pos] = kb; ad[pos] = o0; }
             pos++;
         }
         if (c1) {
-            if (pos < cap) { kd[pos] = k | 1ull; ad[pos] = o1; }
+            if (pos < cap) { kd[pos] = kb | 1ull; ad[pos] = o1; }
         }
         out += total;
     }
@@ -890,15 +891,16 @@ __device__ int rot_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, co
     return out;
 }
 
-/* H P H of one walk step without sorting (R-layout keys, pairs adjacent).
- * P keeps the sign of the all-zero branch only, so a Hadamard group (fixed
- * registers except the low L bits of k) is either zero-type -- row jc = b1 = 0
- * and kc = k_high = b2 = 0, any A -- where H P H = 2|+><+| - 1 maps
- * a_u -> (2/s) sum_v a_v - a_u for all s values of u, or H P H = -1.  Output:
- * the other branches negated in their order, then per zero-type group (by A)
- * the s outputs (u, b2 = 0) each followed by its b2 = 1 partner.  The group
- * sum is FP64.  With readout, (1/sqrt s) sum_v a_v of the A = 0 group -- the
- * flag-0 amplitude of T~^dag's output -- goes into the QLS accumulator. */
+/* H P H of one walk step without sorting (keys (l, z, A = 0, b2), pairs
+ * adjacent).  P keeps the sign of the all-zero branch only, so a Hadamard
+ * group (registers fixed except the low L bits of k) is either zero-type --
+ * row jc = b1 = 0 and kc = k_high = b2 = 0 -- where H P H = 2|+><+| - 1 maps
+ * a_u -> (2/s) sum_v a_v - a_u for all s values of u, or H P H = -1.  Since A
+ * is zero here, a row has at most one zero-type group.  Output: the other
+ * branches negated in their order, then the s outputs (u, b2 = 0), each
+ * followed by its b2 = 1 partner.  The group sum is FP64.  With readout,
+ * (1/sqrt s) sum_v a_v -- the flag-0 amplitude of T~^dag's output -- goes into
+ * the QLS accumulator. */
 template <typename AmpT>
 __device__ int reflect_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, const AmpT *as,
                              int n, uint64_t *kd, AmpT *ad, int cap, int32_t *status,
@@ -906,16 +908,34 @@ __device__ int reflect_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
 {
     const int lane = lane_id();
     const int s = d.s;
-    const int ash = 1 + 2 * d.nb; /* A field shift */
-    const uint64_t zm = ((1ull << ash) - 1) & ~((1ull << (d.L + 1)) - 1); /* k_high | kc */
+    const uint64_t zm = ((1ull << (1 + 2 * d.nb)) - 1) & ~((1ull << (d.L + 1)) - 1); /* k_high|kc */
     const bool rowzero = (r.jc == 0 && r.b1 == 0);
+    if (rowzero) {
+        for (int t = lane; t < s; t += 32) {
+            zbuf[t] = Amp<AmpT>::zero();
+            pbuf[t] = -1;
+        }
+        __syncwarp();
+    }
     int out = 0;
+    double px = 0.0, py = 0.0;
     for (int base = 0; base < n; base += 32) {
         const int i = base + lane;
         const bool valid = i < n;
         const uint64_t k = valid ? ks[i] : 0;
-        const bool zp = rowzero && (k & zm) == 0;
+        const bool zp = valid && rowzero && (k & zm) == 0;
         const AmpT v = valid ? as[i] : Amp<AmpT>::zero();
+        if (zp) {
+            const int u = (int)((k >> 1) & (uint64_t)(s - 1));
+            if ((k & 1ull) == 0) {
+                zbuf[u] = v;
+                const double2 z = Amp<AmpT>::to_d(v);
+                px += z.x;
+                py += z.y;
+            } else {
+                pbuf[u] = (int16_t)i;
+            }
+        }
         const bool c = valid && !zp && Amp<AmpT>::keep(d, v);
         int total;
         const int pos = out + warp_excl_scan((int)c, total);
@@ -926,81 +946,39 @@ __device__ int reflect_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
         out += total;
     }
     if (rowzero) {
-        int64_t prevA = -1;
-        for (;;) {
-            /* next group: the smallest A above the previous among zero-type keys */
-            uint32_t amin = 0xffffffffu;
-            for (int base = 0; base < n; base += 32) {
-                const int i = base + lane;
-                if (i < n) {
-                    const uint64_t k = ks[i];
-                    const uint32_t A = (uint32_t)(k >> ash);
-                    if ((k & zm) == 0 && (int64_t)A > prevA && A < amin) amin = A;
-                }
+        __syncwarp();
+        const double sx = warp_sum(px), sy = warp_sum(py);
+        const double cx = d.two_over_s * sx, cy = d.two_over_s * sy;
+        if (a.qls_readout && r.valid && lane == 0) {
+            double2 acc = a.qls_y[r.j];
+            acc.x += a.qls_coef * (d.inv_sqrt_s * sx);
+            acc.y += a.qls_coef * (d.inv_sqrt_s * sy);
+            a.qls_y[r.j] = acc;
+        }
+        for (int ub = 0; ub < s; ub += 32) {
+            const int u = ub + lane;
+            const bool vu = u < s;
+            AmpT o0 = Amp<AmpT>::zero();
+            int p = -1;
+            if (vu) {
+                const double2 au = Amp<AmpT>::to_d(zbuf[u]);
+                o0 = Amp<AmpT>::from_d(make_double2(cx - au.x, cy - au.y));
+                p = pbuf[u];
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) amin = min(amin, __shfl_xor_sync(FULL, amin, o));
-            if (amin == 0xffffffffu) break;
-            for (int t = lane; t < s; t += 32) {
-                zbuf[t] = Amp<AmpT>::zero();
-                pbuf[t] = -1;
+            const bool c0 = vu && Amp<AmpT>::keep(d, o0);
+            const bool c1 = p >= 0;
+            int total;
+            int pos = out + warp_excl_scan((int)c0 + (int)c1, total);
+            const uint64_t k0 = (uint64_t)u << 1;
+            if (c0) {
+                if (pos < cap) { kd[pos] = k0; ad[pos] = o0; }
+                pos++;
             }
-            __syncwarp();
-            double2 part = make_double2(0.0, 0.0);
-            for (int base = 0; base < n; base += 32) {
-                const int i = base + lane;
-                if (i < n) {
-                    const uint64_t k = ks[i];
-                    if ((k & zm) == 0 && (uint32_t)(k >> ash) == amin) {
-                        const int u = (int)((k >> 1) & (uint64_t)(s - 1));
-                        if ((k & 1ull) == 0) {
-                            zbuf[u] = as[i];
-                            const double2 z = Amp<AmpT>::to_d(as[i]);
-                            part.x += z.x;
-                            part.y += z.y;
-                        } else {
-                            pbuf[u] = (int16_t)i;
-                        }
-                    }
-                }
+            if (c1 && pos < cap) {
+                kd[pos] = k0 | 1ull;
+                ad[pos] = Amp<AmpT>::neg(as[p]);
             }
-            __syncwarp();
-            const double sx = warp_sum(part.x), sy = warp_sum(part.y);
-            const double cx = d.two_over_s * sx, cy = d.two_over_s * sy;
-            if (amin == 0 && a.qls_readout && r.valid && lane == 0) {
-                double2 acc = a.qls_y[r.j];
-                acc.x += a.qls_coef * (d.inv_sqrt_s * sx);
-                acc.y += a.qls_coef * (d.inv_sqrt_s * sy);
-                a.qls_y[r.j] = acc;
-            }
-            const uint64_t gkey = (uint64_t)amin << ash;
-            for (int ub = 0; ub < s; ub += 32) {
-                const int u = ub + lane;
-                const bool vu = u < s;
-                AmpT o0 = Amp<AmpT>::zero();
-                int p = -1;
-                if (vu) {
-                    const double2 au = Amp<AmpT>::to_d(zbuf[u]);
-                    o0 = Amp<AmpT>::from_d(make_double2(cx - au.x, cy - au.y));
-                    p = pbuf[u];
-                }
-                const bool c0 = vu && Amp<AmpT>::keep(d, o0);
-                const bool c1 = p >= 0;
-                int total;
-                int pos = out + warp_excl_scan((int)c0 + (int)c1, total);
-                const uint64_t k0 = gkey | ((uint64_t)u << 1);
-                if (c0) {
-                    if (pos < cap) { kd[pos] = k0; ad[pos] = o0; }
-                    pos++;
-                }
-                if (c1 && pos < cap) {
-                    kd[pos] = k0 | 1ull;
-                    ad[pos] = Amp<AmpT>::neg(as[p]);
-                }
-                out += total;
-            }
-            __syncwarp();
-            prevA = amin;
+            out += total;
         }
     }
     __syncwarp();
@@ -1011,52 +989,84 @@ __device__ int reflect_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
     return out;
 }
 
-/* register maps in place, R layout */
-template <int CHAIN>
-__device__ void chain_r(const QwSimDev &d, const Row &r, uint64_t *ks, int n)
+/* Register maps of T~^dag before R^dag.  T~^dag applies O_s'^dag, O_A', O_s',
+ * R^dag, O_s'^dag, O_A': O_s' R^dag O_s'^dag is R^dag in the coordinates
+ * (l, z) = O_s'^dag(k, kc), controlled by A and by the input column k, and the
+ * second O_A' undoes the first.  So each branch moves to (l, z) and carries
+ * A = [jc = 0, z = 0] a_{j,l} and sigma(j, k) for the rotation; after R^dag the
+ * controls are dropped (A = 0).  Input A must be 0 (T~ and T~^dag return it
+ * to 0 at the end of every step). */
+__device__ __forceinline__ uint64_t map_tdag(const QwSimDev &d, const Row &r, uint64_t key,
+                                            int32_t *status)
 {
-    for (int i = lane_id(); i < n; i += 32) {
-        Regs x = decode_r(ks[i], d.nb);
-        if (CHAIN == 1) { /* start of T~^dag */
-            op_osdag(d, r, x);
-            op_oa(d, r, x);
-            op_os(d, r, x);
-        } else if (CHAIN == 2) { /* after R^dag */
-            op_osdag(d, r, x);
-            op_oa(d, r, x);
-        } else { /* after H of T~ */
-            op_oa(d, r, x);
-            op_os(d, r, x);
-        }
-        ks[i] = encode_r(x, d.nb);
-    }
+    const Regs x = decode_r(key, d.nb);
+    if (x.A != 0) atomicOr(status, QW_ST_ANCILLA);
+    const uint32_t l = x.kc ^ qbs(d, r, x.k);
+    const uint32_t w = qword(d, r, l);
+    Regs y;
+    y.k = l;
+    y.kc = x.k ^ (w >> 16);
+    y.A = (r.jc == 0 && y.kc == 0) ? (w & 0xffffu) : 0u;
+    y.b2 = x.b2;
+    return encode_r(y, d.nb) | ((uint64_t)(r.j > x.k) << QW_SNEG_BIT);
+}
+
+/* Register maps of T~ after H: O_A', O_s', R, O_s'^dag, O_A', O_s'.  From
+ * (l, z): A = [jc = 0, z = 0] a_{j,l}, then O_s' gives (k, kc) =
+ * (z ^ K(j,l), l ^ I(j, k)); R is controlled by A and sigma(j, k); the last
+ * three maps only return A to 0. */
+__device__ __forceinline__ uint64_t map_t(const QwSimDev &d, const Row &r, uint64_t key)
+{
+    const Regs x = decode_r(key, d.nb);
+    const uint32_t w = qword(d, r, x.k);
+    Regs y;
+    y.A = (r.jc == 0 && x.kc == 0) ? (w & 0xffffu) : 0u;
+    y.k = x.kc ^ (w >> 16);
+    y.kc = x.k ^ qbs(d, r, y.k);
+    y.b2 = x.b2;
+    return encode_r(y, d.nb) | ((uint64_t)(r.j > y.k) << QW_SNEG_BIT);
+}
+
+template <int WHICH>
+__device__ void map_row(const QwSimDev &d, const Row &r, uint64_t *ks, int n, int32_t *status)
+{
+    for (int i = lane_id(); i < n; i += 32) ks[i] = (WHICH == 0) ? map_tdag(d, r, ks[i], status)
+                                                                : map_t(d, r, ks[i]);
     __syncwarp();
 }
 
-/* last register maps of T~, S, and the append to the new rows' buckets */
+/* S, and the append of every branch to the bucket of its new row. */
 template <typename AmpT>
 __device__ void emit_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, const AmpT *as, int n,
                            const QwBufDev &out, int32_t *status, typename Amp<AmpT>::Norm &nrm)
 {
+    const int64_t blo = d.inst_bkt[r.inst], bhi = d.inst_bkt[r.inst + 1];
+    Regs y;
+    y.kc = r.jc;
+    y.k = r.j;
+    y.b2 = r.b1;
+    y.A = 0;
+    const uint64_t local = encode_r(y, d.nb);
     for (int i = lane_id(); i < n; i += 32) {
-        Regs x = decode_r(ks[i], d.nb);
-        op_osdag(d, r, x);
-        op_oa(d, r, x);
-        op_os(d, r, x);
-        if (x.A != 0) atomicOr(status, QW_ST_ANCILLA);
-        Regs y = x;
-        y.kc = r.jc;
-        y.k = r.j;
-        y.b2 = r.b1;
-        const int64_t b = bucket_of(d, out, r.inst, x.kc, x.k, x.b2, status);
-        if (b < 0) continue;
+        const Regs x = decode_r(ks[i], d.nb);
+        int64_t b;
+        if (x.kc == 0) {
+            b = blo + (((int64_t)x.k << 1) | (int64_t)x.b2);
+            if (b >= bhi) {
+                atomicOr(status, QW_ST_SPILL_FULL);
+                continue;
+            }
+        } else {
+            b = bucket_of(d, out, r.inst, x.kc, x.k, x.b2, status);
+            if (b < 0) continue;
+        }
         const int pos = atomicAdd(out.count + b, 1);
         if (pos >= d.cap_row) {
             atomicOr(status, QW_ST_ROW_OVERFLOW);
             continue;
         }
         const int64_t slot = b * (int64_t)d.cap_row + pos;
-        out.key[slot] = encode_r(y, d.nb);
+        out.key[slot] = local;
         static_cast<AmpT *>(out.amp)[slot] = as[i];
         nrm.add(as[i]);
     }
@@ -1119,14 +1129,14 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk(QwSimDev d, QwBufDev in,
         st_rows++;
         st_in += n;
         pair_up<AmpT>(kQ, aQ, n, kP, aP);
-        chain_r<1>(d, r, kP, n);                                               /* T~^dag ... */
-        n = rot_pairs<true, AmpT>(d, r, kP, aP, n, kQ, aQ, C, a.status);       /* R^dag */
+        const uint64_t drop = (1ull << (1 + 2 * d.nb)) - 1; /* keep b2, k, kc; A = 0 */
+        map_row<0>(d, r, kP, n, a.status);                                     /* T~^dag: maps */
+        n = rot_pairs<true, AmpT>(d, kP, aP, n, kQ, aQ, C, drop, a.status);    /* R^dag */
         st_rdag += n;
-        chain_r<2>(d, r, kQ, n);
         n = reflect_pairs<AmpT>(d, r, kQ, aQ, n, kP, aP, C, a.status, a, zbuf, pbuf); /* H P H */
         st_hph += n;
-        chain_r<3>(d, r, kP, n);                                               /* ... T~ */
-        n = rot_pairs<false, AmpT>(d, r, kP, aP, n, kQ, aQ, C, a.status);      /* R */
+        map_row<1>(d, r, kP, n, a.status);                                     /* T~: maps */
+        n = rot_pairs<false, AmpT>(d, kP, aP, n, kQ, aQ, C, drop, a.status);   /* R */
         st_out += n;
         emit_pairs<AmpT>(d, r, kQ, aQ, n, out, a.status, nrm);                 /* S */
         __syncwarp();
