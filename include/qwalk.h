@@ -171,6 +171,37 @@ int qw_apply_qls(qw_sim *sim, int32_t inst, const double *coeffs, int64_t j0, do
  */
 int qw_measure_register(qw_sim *sim, int32_t inst, int32_t reg_id, double *probs, int64_t len);
 
+/*
+ * Largest len accepted by qw_measure_register_noalloc: 65536 bins, enough for
+ * any register of a simulator (N <= 65536).
+ */
+#define QW_MEASURE_NOALLOC_MAX_LEN 65536
+
+/*
+ * qw_measure_register without any device allocation.  No counterpart in the
+ * paper: this is a service of the library, for callers that cannot call
+ * cudaMalloc or cudaMallocAsync at this point -- for instance code running
+ * while its stream is being captured into a CUDA graph, a runtime whose
+ * memory is owned by another allocator with no headroom left, or a loop that
+ * must not touch the allocator for latency reasons.  qw_measure_register
+ * obtains a temporary device histogram per call; this entry point
+ * accumulates into a fixed 512 KiB array of the library's device image
+ * instead, which every GPU that loads the library keeps until the process
+ * exits.  Same arguments and result (probs is a host array of len doubles).
+ * Limits and caveats:
+ *   - len must be <= QW_MEASURE_NOALLOC_MAX_LEN, else QW_ERR_ARG;
+ *   - the first call on a device looks up the array's device address once
+ *     (cudaGetSymbolAddress); make that first call before any stream
+ *     capture begins;
+ *   - all calls share the one array: each call zeroes the bins it uses before
+ *     accumulating, but calls whose GPU work overlaps (issued on different
+ *     streams with no ordering between them) race and give wrong results;
+ *   - like qw_measure_register it synchronises the simulator's stream.
+ * Errors: QW_ERR_ARG, QW_ERR_STATE, QW_ERR_CUDA.
+ */
+int qw_measure_register_noalloc(qw_sim *sim, int32_t inst, int32_t reg_id, double *probs,
+                                int64_t len);
+
 /* Number of branches of instance inst (inst = -1: all instances). */
 int qw_state_size(qw_sim *sim, int32_t inst, int64_t *count);
 

@@ -56,6 +56,7 @@ int ceil_log2(int64_t x)
 struct qw_sim {
     qw_sim_opts opts;
     cudaStream_t stream = nullptr;
+    int device = 0;                  /* CUDA device current at creation */
     int fp32 = 0;
     int renorm = 0;
     int mode = QW_MODE_WALK_FUSED;
@@ -235,6 +236,7 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
         g_create_error = "qw_sim_create: unknown precision";
         return QW_ERR_ARG;
     }
+    cudaGetDevice(&sim->device);
     sim->fp32 = o.precision == QW_FP32_AMP;
     sim->renorm = o.renorm < 0 ? sim->fp32 : (o.renorm != 0);
     sim->mode = o.fuse_reflection ? QW_MODE_WALK_FUSED : QW_MODE_WALK_LITERAL;
@@ -662,6 +664,26 @@ extern "C" int qw_measure_register(qw_sim *sim, int32_t inst, int32_t reg, doubl
                                  sim->stream));
     QW_CUDA(sim, cudaFreeAsync(dp, sim->stream));
     return check_status(sim, "qw_measure_register");
+}
+
+/* Same result as qw_measure_register, for callers that must not allocate
+ * device memory: the histogram lives in a fixed scratch array of the library
+ * (see qw_kernels.cu) instead of a per-call cudaMallocAsync buffer. */
+extern "C" int qw_measure_register_noalloc(qw_sim *sim, int32_t inst, int32_t reg, double *probs,
+                                           int64_t len)
+{
+    if (!sim) return QW_ERR_ARG;
+    if (inst < 0 || inst >= sim->d.ninst || reg < 0 || reg > 5 || !probs || len < 1)
+        return fail(sim, QW_ERR_ARG, "bad instance, register id or output");
+    if (len > QW_MEASURE_NOALLOC_MAX_LEN)
+        return fail(sim, QW_ERR_ARG,
+                    "qw_measure_register_noalloc: len " + std::to_string(len) + " exceeds the fixed scratch of " +
+                        std::to_string(QW_MEASURE_NOALLOC_MAX_LEN) + " bins; use qw_measure_register");
+    if (!sim->has_state) return fail(sim, QW_ERR_STATE, "no state");
+    QW_CUDA(sim, qw_launch_measure_noalloc(sim->d, sim->buf[sim->cur], inst, sim->fp32, pending_scale(sim),
+                                           reg, probs, len, sim->device, sim->stream));
+    sim->launches++;
+    return check_status(sim, "qw_measure_register_noalloc");
 }
 
 extern "C" int qw_state_size(qw_sim *sim, int32_t inst, int64_t *count)

@@ -112,6 +112,9 @@ cudaError_t qw_launch_export(const QwSimDev &d, const QwBufDev &buf, int inst, i
 cudaError_t qw_launch_measure(const QwSimDev &d, const QwBufDev &buf, int inst, int fp32,
                               const double *scale, int reg, double *probs, int64_t len,
                               cudaStream_t st);
+cudaError_t qw_launch_measure_noalloc(const QwSimDev &d, const QwBufDev &buf, int inst, int fp32,
+                                      const double *scale, int reg, double *host_probs,
+                                      int64_t len, int device, cudaStream_t st);
 cudaError_t qw_launch_count(const QwSimDev &d, const QwBufDev &buf, int inst,
                             unsigned long long *counter, cudaStream_t st);
 cudaError_t qw_launch_qls_norm(const double2 *y, int n, double *out, cudaStream_t st);

@@ -20,6 +20,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
+#include "../../include/qwalk.h"
 #include "qw_internal.h"
 
 namespace {
@@ -1453,4 +1456,57 @@ cudaError_t qw_launch_qls_norm(const double2 *y, int n, double *out, cudaStream_
 {
     k_qls_norm<<<1, 1024, 0, st>>>(y, n, out);
     return cudaGetLastError();
+}
+
+/* ---- measurement without device allocation ------------------------------------ */
+/*
+ * Histogram scratch of qw_measure_register_noalloc, a fixed array in the
+ * library's device image instead of a cudaMallocAsync buffer.  Every GPU that
+ * loads the library holds it (QW_MEASURE_NOALLOC_MAX_LEN doubles, 512 KiB)
+ * until the process exits.  All calls share it: each call zeroes the bins it
+ * uses before the kernel accumulates into them, and two calls whose work
+ * overlaps on the GPU (different streams, no ordering between them) race on it.
+ * Host code may not pass the symbol itself to a kernel -- on the host it
+ * names a shadow variable, not device memory -- so the device address is
+ * looked up with cudaGetSymbolAddress, once per device, with that device
+ * current, and cached.
+ */
+static __device__ __align__(256) double g_measure_scratch[QW_MEASURE_NOALLOC_MAX_LEN];
+
+namespace {
+constexpr int kMaxDevices = 128;
+std::mutex g_scratch_mu;
+double *g_scratch_addr[kMaxDevices] = {nullptr};
+} // namespace
+
+cudaError_t qw_launch_measure_noalloc(const QwSimDev &d, const QwBufDev &buf, int inst, int fp32,
+                                      const double *scale, int reg, double *host_probs,
+                                      int64_t len, int device, cudaStream_t st)
+{
+    if (device < 0 || device >= kMaxDevices || len < 1 || len > QW_MEASURE_NOALLOC_MAX_LEN)
+        return cudaErrorInvalidValue;
+    double *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_mu);
+        if (!g_scratch_addr[device]) {
+            int prev = -1;
+            cudaError_t e = cudaGetDevice(&prev);
+            if (e != cudaSuccess) return e;
+            if (prev != device && (e = cudaSetDevice(device)) != cudaSuccess) return e;
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_measure_scratch);
+            if (prev != device) cudaSetDevice(prev);
+            if (e != cudaSuccess) return e;
+            g_scratch_addr[device] = static_cast<double *>(p);
+        }
+        scratch = g_scratch_addr[device];
+    }
+    cudaError_t e = cudaMemsetAsync(scratch, 0, (size_t)len * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const int grid = 4 * qw_sm_count();
+    if (fp32) k_measure<float2><<<grid, 256, 0, st>>>(d, buf, inst, scale, reg, scratch, len);
+    else k_measure<double2><<<grid, 256, 0, st>>>(d, buf, inst, scale, reg, scratch, len);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(host_probs, scratch, (size_t)len * sizeof(double), cudaMemcpyDeviceToHost, st);
 }

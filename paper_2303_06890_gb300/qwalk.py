@@ -29,7 +29,8 @@ EXPORTED = ("qw_sim_opts_default", "qw_sim_create", "qw_state_init", "qw_apply_w
             "qw_enqueue_walk_steps", "qw_sync",
             "qw_cks_coefficients", "qw_apply_qls", "qw_measure_register", "qw_state_size",
             "qw_state_export", "qw_sim_info", "qw_step_stats", "qw_launch_count", "qw_sim_destroy",
-            "qw_last_error")
+            "qw_last_error", "qw_measure_register_noalloc")
+MEASURE_NOALLOC_MAX_LEN = 65536
 
 
 class QwError(RuntimeError):
@@ -79,6 +80,7 @@ def load(build_if_missing: bool = True):
     lib.qw_cks_coefficients.argtypes = [dbl, dbl, P, i64, P, P]
     lib.qw_apply_qls.argtypes = [P, i32, P, i64, P, P]
     lib.qw_measure_register.argtypes = [P, i32, i32, P, i64]
+    lib.qw_measure_register_noalloc.argtypes = [P, i32, i32, P, i64]
     lib.qw_state_size.argtypes = [P, i32, P]
     lib.qw_state_export.argtypes = [P, i32, i32, P, P, i64, P]
     lib.qw_sim_info.argtypes = [P, P, P, P, P]
@@ -90,7 +92,8 @@ def load(build_if_missing: bool = True):
     lib.qw_last_error.restype = ctypes.c_char_p
     for name in ("qw_sim_create", "qw_state_init", "qw_apply_walk_step", "qw_enqueue_walk_steps",
                  "qw_sync", "qw_cks_coefficients",
-                 "qw_apply_qls", "qw_measure_register", "qw_state_size", "qw_state_export",
+                 "qw_apply_qls", "qw_measure_register", "qw_measure_register_noalloc",
+                 "qw_state_size", "qw_state_export",
                  "qw_sim_info", "qw_step_stats", "qw_sim_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -208,6 +211,13 @@ class Sim:
     def measure_register(self, reg: str, length: int, inst: int = 0) -> np.ndarray:
         out = np.zeros(int(length))
         self._check(load().qw_measure_register(self._h, inst, REGS[reg], _p(out), out.size))
+        return out
+
+    def measure_register_noalloc(self, reg: str, length: int, inst: int = 0) -> np.ndarray:
+        """qw_measure_register_noalloc: the same marginal without any device
+        allocation (fixed scratch in the library; length <= 65536)."""
+        out = np.zeros(int(length))
+        self._check(load().qw_measure_register_noalloc(self._h, inst, REGS[reg], _p(out), out.size))
         return out
 
     def state_size(self, inst: int = -1) -> int:
