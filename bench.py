@@ -208,6 +208,7 @@ def run_ours(args, rank, world, local_rank):
     # --- the benchmarked path: complex64 amplitudes, FP64 merge/norm/renorm ---
     sim = qwalk.Sim(w.matrix, s_pad=w.s, precision=qwalk.QW_FP32_AMP)
     sim.state_init(w.b, apply_T=True)
+    variant, tune_us = sim.autotune(max(2, args.warmup // 2))  # warm-up steps, both variants
     sim.apply_walk_step(args.warmup)
     sim.step_stats(reset=True)
     launches0 = sim.launch_count()
@@ -233,6 +234,7 @@ def run_ours(args, rank, world, local_rank):
     # --- the plain FP64 path on the same workload ---
     sim64 = qwalk.Sim(w.matrix, s_pad=w.s, precision=qwalk.QW_FP64)
     sim64.state_init(w.b, apply_T=True)
+    variant64, tune64 = sim64.autotune(max(2, args.warmup // 2))
     sim64.apply_walk_step(args.warmup)
     sim64.step_stats(reset=True)
     barrier()
@@ -242,6 +244,7 @@ def run_ours(args, rank, world, local_rank):
     stats64 = sim64.step_stats(reset=True)
     b_alg64, _ = algorithmic_bytes(stats64, sim64.nb, 16)
     fp64 = {"value": world * args.fp64_steps / t64, "unit": UNIT, "steps": args.fp64_steps,
+            "variant": variant64, "autotune_us_per_step": tune64,
             "ms_per_step": 1000.0 * t64 / args.fp64_steps,
             "entries_per_s": world * (stats64["in"] + stats64["after_rdag"] + stats64["after_hph"]) / t64,
             "achieved_gbs": b_alg64 / statistics.mean(per64) * 1000.0 / 1e9,
@@ -252,7 +255,7 @@ def run_ours(args, rank, world, local_rank):
     import numpy as np
     b_host = torch.from_numpy(np.ascontiguousarray(w.b)).pin_memory()
     probs_host = torch.empty(w.n, dtype=torch.float64).pin_memory()
-    sim_e = qwalk.Sim(w.matrix, s_pad=w.s, precision=qwalk.QW_FP32_AMP)
+    sim_e = qwalk.Sim(w.matrix, s_pad=w.s, precision=qwalk.QW_FP32_AMP, walk_variant=variant)
     steps_per_job = w.steps
     sim_e.state_init(b_host.numpy(), apply_T=True)
     sim_e.apply_walk_step(2)
@@ -294,7 +297,8 @@ def run_ours(args, rank, world, local_rank):
         "fp32_speedup_vs_fp64": value / fp64["value"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "k_walk<float2>",
+                     "kernel": f"k_walk<float2, {'pipelined' if variant else 'row-at-a-time'}>",
+                     "autotune_us_per_step": tune_us,
                      "algorithmic_bytes_per_launch": b_alg,
                      "state_bytes_per_launch": b_min,
                      "state_gbs": b_min / mean_step_s / 1e9},

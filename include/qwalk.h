@@ -80,6 +80,9 @@ typedef struct {
                                 through a step; 0 = auto */
     int32_t renorm;          /* -1 = default (on for FP32_AMP, off for FP64) */
     void *stream;            /* cudaStream_t to issue on; NULL = the default stream */
+    int32_t walk_variant;    /* step kernel with fuse_reflection = 1: 0 = one row at a
+                                time (default), 1 = software-pipelined row loop; see
+                                qw_autotune */
 } qw_sim_opts;
 
 /* Fill *opts with the defaults above. */
@@ -140,6 +143,19 @@ int qw_enqueue_walk_steps(qw_sim *sim, int64_t nsteps);
  * QW_ERR_CAPACITY, QW_ERR_DEVICE_STATUS or QW_ERR_CUDA.
  */
 int qw_sync(qw_sim *sim);
+
+/*
+ * Autotuner of the fused step kernel: runs steps_per_candidate walk steps with
+ * each variant of the kernel (0: rows processed one at a time, 4 blocks per
+ * SM; 1: row loop software-pipelined, 3 blocks per SM), times them with CUDA
+ * events on the simulator's stream, and keeps the faster one for all later
+ * steps.  The state advances by 2 * steps_per_candidate walk steps (the
+ * variants give identical results).  *choice (nullable) receives the variant,
+ * *us_per_step (nullable, 2 doubles) the measured times.  Synchronises.
+ * Has no effect with fuse_reflection = 0.  Errors: QW_ERR_ARG, QW_ERR_STATE,
+ * QW_ERR_CAPACITY, QW_ERR_CUDA.
+ */
+int qw_autotune(qw_sim *sim, int32_t steps_per_candidate, int32_t *choice, double *us_per_step);
 
 /*
  * CKS coefficients of Eq. (fx): b = ceil(kappa^2 ln(kappa/eps)),

@@ -33,6 +33,8 @@ struct Scalars {
     unsigned int pad1;
     unsigned long long counter;
     unsigned long long stats[QW_NSTAT];
+    int32_t tinit_fallback;
+    int32_t pad2;
 };
 
 thread_local std::string g_create_error;
@@ -124,6 +126,7 @@ extern "C" void qw_sim_opts_default(qw_sim_opts *o)
     o->warp_capacity = 0;
     o->renorm = -1;
     o->stream = nullptr;
+    o->walk_variant = 0;
 }
 
 /* Validate one CSC matrix; on success return its largest column count. */
@@ -239,7 +242,8 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     cudaGetDevice(&sim->device);
     sim->fp32 = o.precision == QW_FP32_AMP;
     sim->renorm = o.renorm < 0 ? sim->fp32 : (o.renorm != 0);
-    sim->mode = o.fuse_reflection ? QW_MODE_WALK_FUSED : QW_MODE_WALK_LITERAL;
+    sim->mode = o.fuse_reflection ? (o.walk_variant == 1 ? QW_MODE_WALK_FUSED_PF : QW_MODE_WALK_FUSED)
+                                  : QW_MODE_WALK_LITERAL;
     sim->stream = (cudaStream_t)o.stream;
 
     QwSimDev &d = sim->d;
@@ -337,7 +341,11 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     }
     sim->grid_walk = qw_step_grid(d, sim->fp32, sim->mode);
     sim->grid_t = qw_step_grid(d, sim->fp32, QW_MODE_T);
-    const int gmax = std::max(sim->grid_walk, sim->grid_t);
+    int gmax = std::max(sim->grid_walk, sim->grid_t);
+    if (sim->mode != QW_MODE_WALK_LITERAL) {
+        gmax = std::max(gmax, qw_step_grid(d, sim->fp32, QW_MODE_WALK_FUSED));
+        gmax = std::max(gmax, qw_step_grid(d, sim->fp32, QW_MODE_WALK_FUSED_PF));
+    }
     QW_TRY(dalloc(sim, &sim->partials, (size_t)gmax));
     QW_TRY(dalloc(sim, &sim->sc, 1));
     Scalars z{};
@@ -516,17 +524,32 @@ extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, cons
                                   all ? nullptr : pending_scale(sim), sim->stream));
     sim->launches++;
     if (apply_T) {
-        QwStepArgs a = step_args(sim, QW_MODE_T);
-        a.scale_in = nullptr;
-        a.norm_out = &sim->sc->norm[sim->scale_slot];
-        a.scale_out = nullptr;
-        a.bucket_lo = lo;
-        a.bucket_hi = hi;
-        QW_CUDA(sim, qw_launch_step(sim->d, sim->buf[sim->cur], sim->buf[sim->cur], sim->buf[sim->cur],
-                                    a, sim->fp32, sim->grid_t, sim->stream));
-        sim->launches++;
+        /* T~ on |b~>: the one-branch-per-row kernel, or the literal sort-based
+           schedule when that was asked for */
+        if (sim->mode != QW_MODE_WALK_LITERAL) {
+            int32_t fb = 0;
+            QW_CUDA(sim, cudaMemsetAsync(&sim->sc->tinit_fallback, 0, 4, sim->stream));
+            QW_CUDA(sim, qw_launch_tinit(sim->d, sim->buf[sim->cur], lo, hi, sim->fp32, &sim->sc->status,
+                                         &sim->sc->tinit_fallback, sim->stream));
+            sim->launches++;
+            QW_CUDA(sim, cudaMemcpyAsync(&fb, &sim->sc->tinit_fallback, 4, cudaMemcpyDeviceToHost, sim->stream));
+            QW_CUDA(sim, cudaFreeAsync(db, sim->stream));
+            db = nullptr;
+            QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
+            if (fb) return fail(sim, QW_ERR_DEVICE_STATUS, "qw_state_init: a row was not |b~> before T~");
+        } else {
+            QwStepArgs a = step_args(sim, QW_MODE_T);
+            a.scale_in = nullptr;
+            a.norm_out = &sim->sc->norm[sim->scale_slot];
+            a.scale_out = nullptr;
+            a.bucket_lo = lo;
+            a.bucket_hi = hi;
+            QW_CUDA(sim, qw_launch_step(sim->d, sim->buf[sim->cur], sim->buf[sim->cur], sim->buf[sim->cur],
+                                        a, sim->fp32, sim->grid_t, sim->stream));
+            sim->launches++;
+        }
     }
-    QW_CUDA(sim, cudaFreeAsync(db, sim->stream));
+    if (db) QW_CUDA(sim, cudaFreeAsync(db, sim->stream));
     int rc = check_status(sim, "qw_state_init");
     if (rc != QW_OK) return rc;
     sim->has_state = true;
@@ -558,6 +581,43 @@ extern "C" int qw_apply_walk_step(qw_sim *sim, int64_t nsteps)
     int rc = qw_enqueue_walk_steps(sim, nsteps);
     if (rc != QW_OK) return rc;
     return check_status(sim, "qw_apply_walk_step");
+}
+
+extern "C" int qw_autotune(qw_sim *sim, int32_t steps, int32_t *choice, double *us_per_step)
+{
+    if (!sim || steps < 1) return QW_ERR_ARG;
+    if (!sim->has_state) return fail(sim, QW_ERR_STATE, "no state: call qw_state_init first");
+    if (sim->mode == QW_MODE_WALK_LITERAL) {
+        if (choice) *choice = -1;
+        return QW_OK;
+    }
+    const int modes[2] = {QW_MODE_WALK_FUSED, QW_MODE_WALK_FUSED_PF};
+    double us[2] = {0.0, 0.0};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    QW_CUDA(sim, cudaEventCreate(&e0));
+    QW_CUDA(sim, cudaEventCreate(&e1));
+    int rc = QW_OK;
+    for (int v = 0; v < 2 && rc == QW_OK; ++v) {
+        sim->mode = modes[v];
+        sim->grid_walk = qw_step_grid(sim->d, sim->fp32, sim->mode);
+        cudaEventRecord(e0, sim->stream);
+        rc = qw_enqueue_walk_steps(sim, steps);
+        cudaEventRecord(e1, sim->stream);
+        if (rc == QW_OK) rc = check_status(sim, "qw_autotune");
+        float ms = 0.f;
+        if (rc == QW_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) us[v] = 1000.0 * ms / steps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const int best = (us[1] > 0.0 && us[1] < us[0]) ? 1 : 0;
+    sim->mode = modes[best];
+    sim->grid_walk = qw_step_grid(sim->d, sim->fp32, sim->mode);
+    if (choice) *choice = best;
+    if (us_per_step) {
+        us_per_step[0] = us[0];
+        us_per_step[1] = us[1];
+    }
+    return rc;
 }
 
 extern "C" int qw_cks_coefficients(double kappa, double eps, double *coeffs, int64_t cap,

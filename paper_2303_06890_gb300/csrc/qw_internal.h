@@ -49,6 +49,7 @@
 #define QW_MODE_WALK_FUSED 0   /* T~^dag, (H P H as one reflection), T~, S */
 #define QW_MODE_WALK_LITERAL 1 /* T~^dag, H, P, H, T~, S */
 #define QW_MODE_T 2            /* T~ only, in place on a bucket range */
+#define QW_MODE_WALK_FUSED_PF 3 /* fused step, row loop software-pipelined */
 
 struct QwSimDev {
     int nb, s, L, ninst;
@@ -106,6 +107,8 @@ cudaError_t qw_launch_clear(const QwSimDev &d, const QwBufDev &buf, int64_t lo, 
                             int clear_spill, cudaStream_t st);
 cudaError_t qw_launch_init_b(const QwSimDev &d, const QwBufDev &buf, int inst, const double2 *b,
                              int n, int fp32, const double *scale, cudaStream_t st);
+cudaError_t qw_launch_tinit(const QwSimDev &d, const QwBufDev &buf, int64_t lo, int64_t hi, int fp32,
+                            int32_t *status, int32_t *fallback, cudaStream_t st);
 cudaError_t qw_launch_export(const QwSimDev &d, const QwBufDev &buf, int inst, int fp32,
                              const double *scale, uint64_t *rowkey, uint64_t *local, double2 *amp,
                              unsigned long long *counter, int64_t cap, cudaStream_t st);

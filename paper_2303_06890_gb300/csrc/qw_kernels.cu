@@ -665,6 +665,15 @@ template <> struct Amp<double2> {
         __device__ void add(T a) { v = fma(a.x, a.x, fma(a.y, a.y, v)); }
         __device__ double get() const { return v; }
     };
+    /* sum of a zero-type Hadamard group (FP64) */
+    struct Sum {
+        double x = 0.0, y = 0.0;
+        __device__ void add(T a) { x += a.x; y += a.y; }
+        __device__ void reduce() { x = warp_sum(x); y = warp_sum(y); }
+        __device__ void scale_pow2(double f) { x *= f; y *= f; }
+        __device__ T minus(T a) const { return make_double2(x - a.x, y - a.y); }
+        __device__ double2 value() const { return make_double2(x, y); }
+    };
     __device__ static T zero() { return make_double2(0.0, 0.0); }
     __device__ static T neg(T a) { return make_double2(-a.x, -a.y); }
     __device__ static double2 to_d(T a) { return a; }
@@ -705,6 +714,58 @@ template <> struct Amp<float2> {
             hi = s;
         }
         __device__ double get() const { return (double)hi + (double)lo; }
+    };
+    /* float-pair (hi + lo) accumulator: error-free two-sums, ~48 bits */
+    struct DF {
+        float h = 0.f, l = 0.f;
+        __device__ void add(float v)
+        {
+            const float s = __fadd_rn(h, v);
+            const float bp = __fsub_rn(s, h);
+            const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(v, bp));
+            h = s;
+            l = __fadd_rn(l, e);
+        }
+        __device__ void add(float vh, float vl)
+        {
+            add(vh);
+            l = __fadd_rn(l, vl);
+            const float s = __fadd_rn(h, l); /* renormalise: |l| small */
+            l = __fsub_rn(l, __fsub_rn(s, h));
+            h = s;
+        }
+        __device__ void reduce()
+        {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float oh = __shfl_xor_sync(FULL, h, o), ol = __shfl_xor_sync(FULL, l, o);
+                add(oh, ol);
+            }
+        }
+        /* round(h + l - v) */
+        __device__ float minus(float v) const
+        {
+            const float s = __fsub_rn(h, v);
+            const float bp = __fsub_rn(s, h);
+            const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(-v, bp));
+            return __fadd_rn(s, __fadd_rn(e, l));
+        }
+    };
+    /* sum of a zero-type Hadamard group, exact to ~2^-46 relative */
+    struct Sum {
+        DF x, y;
+        __device__ void add(T a) { x.add(a.x); y.add(a.y); }
+        __device__ void reduce() { x.reduce(); y.reduce(); }
+        __device__ void scale_pow2(double f)
+        {
+            const float g = (float)f; /* 2/s: a power of two, exact */
+            x.h *= g; x.l *= g; y.h *= g; y.l *= g;
+        }
+        __device__ T minus(T a) const { return make_float2(x.minus(a.x), y.minus(a.y)); }
+        __device__ double2 value() const
+        {
+            return make_double2((double)x.h + (double)x.l, (double)y.h + (double)y.l);
+        }
     };
     __device__ static T zero() { return make_float2(0.f, 0.f); }
     __device__ static T neg(T a) { return make_float2(-a.x, -a.y); }
@@ -794,18 +855,26 @@ __device__ void Amp<float2>::rot(const QwSimDev &d, uint32_t A, bool dag, bool s
     }
 }
 
-/* Load-time grouping: put b2-pairs next to each other, b2 = 0 first.  A row
- * that fits one warp pairs by a warp match on key >> 1; a longer row is
- * sorted by key. */
+/* Load the row and group it: b2-pairs next to each other, b2 = 0 first.  A
+ * row that fits one warp is loaded straight into registers and paired by a
+ * warp match on key >> 1; a longer row goes through shared memory and is
+ * sorted by key (rank of each key among the row's). */
 template <typename AmpT>
-__device__ void pair_up(const uint64_t *ks, const AmpT *as, int n, uint64_t *kd, AmpT *ad)
+__device__ void load_pairs(const uint64_t *gkey, const AmpT *gamp, int n, bool rescale,
+                           const typename Amp<AmpT>::Scale &scale, uint64_t *kd, AmpT *ad,
+                           uint64_t *ktmp, AmpT *atmp, bool have, uint64_t hk, AmpT ha)
 {
     const int lane = lane_id();
     if (n <= 32) {
         const bool valid = lane < n;
         /* inactive lanes get keys whose k >> 1 are distinct and above every real key */
-        const uint64_t k = valid ? ks[lane] : (~0ull - 2ull * (uint64_t)lane);
-        const AmpT a = valid ? as[lane] : Amp<AmpT>::zero();
+        uint64_t k = ~0ull - 2ull * (uint64_t)lane;
+        AmpT a = Amp<AmpT>::zero();
+        if (valid) {
+            k = have ? hk : gkey[lane];
+            a = have ? ha : gamp[lane];
+            if (rescale) a = scale.apply(a);
+        }
         const unsigned m = __match_any_sync(FULL, k >> 1);
         const unsigned other = m & ~(1u << lane);
         const bool head = valid && ((k & 1) == 0 || other == 0);
@@ -829,11 +898,18 @@ __device__ void pair_up(const uint64_t *ks, const AmpT *as, int n, uint64_t *kd,
         return;
     }
     for (int i = lane; i < n; i += 32) {
-        const uint64_t ki = ks[i];
+        ktmp[i] = gkey[i];
+        AmpT v = gamp[i];
+        if (rescale) v = scale.apply(v);
+        atmp[i] = v;
+    }
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+        const uint64_t ki = ktmp[i];
         int r = 0;
-        for (int t = 0; t < n; ++t) r += (ks[t] < ki);
+        for (int t = 0; t < n; ++t) r += (ktmp[t] < ki);
         kd[r] = ki;
-        ad[r] = as[i];
+        ad[r] = atmp[i];
     }
     __syncwarp();
 }
@@ -844,14 +920,22 @@ __device__ void pair_up(const uint64_t *ks, const AmpT *as, int n, uint64_t *kd,
  * j <= k).  Both members of a b2-pair carry the same values. */
 #define QW_SNEG_BIT 63
 
-/* R or R^dag on adjacent b2-pairs (R layout), controlled by the A field and
- * the sign bit of the key; outputs stay pair-adjacent and their keys are
- * ANDed with out_mask (which drops the controls: A returns to zero). */
-template <bool DAG, typename AmpT>
-__device__ int rot_pairs(const QwSimDev &d, const uint64_t *ks, const AmpT *as, int n, uint64_t *kd,
-                         AmpT *ad, int cap, uint64_t out_mask, int32_t *status)
+__device__ __forceinline__ uint64_t map_tdag(const QwSimDev &d, const Row &r, uint64_t key,
+                                            int32_t *status);
+__device__ __forceinline__ uint64_t map_t(const QwSimDev &d, const Row &r, uint64_t key);
+
+/* The register maps of one half-step followed by R^dag (WHICH = 0, T~^dag) or
+ * R (WHICH = 1, T~) on the adjacent b2-pairs.  The maps never read b2, so the
+ * pair head maps the key once for both members; the rotation is controlled
+ * by the A field and the sign bit of the mapped key, and the outputs (pair-
+ * adjacent) keep only b2, k and kc: A is back to 0. */
+template <int WHICH, typename AmpT>
+__device__ int map_rot_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, const AmpT *as,
+                             int n, uint64_t *kd, AmpT *ad, int cap, int32_t *status)
 {
     const int lane = lane_id();
+    const int ash = 1 + 2 * d.nb;
+    const uint64_t keep_mask = (1ull << ash) - 1; /* b2 | k | kc */
     int out = 0;
     for (int base = 0; base < n; base += 32) {
         const int i = base + lane;
@@ -861,6 +945,7 @@ __device__ int rot_pairs(const QwSimDev &d, const uint64_t *ks, const AmpT *as, 
         const bool head = valid && !is_end;
         AmpT o0 = Amp<AmpT>::zero(), o1 = Amp<AmpT>::zero();
         bool c0 = false, c1 = false;
+        uint64_t kb = 0;
         if (head) {
             AmpT a0 = Amp<AmpT>::zero(), a1 = Amp<AmpT>::zero();
             if ((k & 1ull) == 0) {
@@ -869,14 +954,15 @@ __device__ int rot_pairs(const QwSimDev &d, const uint64_t *ks, const AmpT *as, 
             } else {
                 a1 = as[i];
             }
-            const uint32_t A = (uint32_t)(k >> (1 + 2 * d.nb)) & 0xffffu;
-            Amp<AmpT>::rot(d, A, DAG, (k >> QW_SNEG_BIT) != 0, a0, a1, o0, o1);
+            const uint64_t mk = (WHICH == 0) ? map_tdag(d, r, k & ~1ull, status) : map_t(d, r, k & ~1ull);
+            const uint32_t A = (uint32_t)(mk >> ash) & 0xffffu;
+            Amp<AmpT>::rot(d, A, WHICH == 0, (mk >> QW_SNEG_BIT) != 0, a0, a1, o0, o1);
             c0 = Amp<AmpT>::keep(d, o0);
             c1 = Amp<AmpT>::keep(d, o1);
+            kb = mk & keep_mask;
         }
         int total;
         int pos = out + warp_excl_scan((int)c0 + (int)c1, total);
-        const uint64_t kb = k & out_mask & ~1ull;
         if (c0) {
             if (pos < cap) { kd[pos] = kb; ad[pos] = o0; }
             pos++;
@@ -901,7 +987,8 @@ __device__ int rot_pairs(const QwSimDev &d, const uint64_t *ks, const AmpT *as, 
  * a_u -> (2/s) sum_v a_v - a_u for all s values of u, or H P H = -1.  Since A
  * is zero here, a row has at most one zero-type group.  Output: the other
  * branches negated in their order, then the s outputs (u, b2 = 0), each
- * followed by its b2 = 1 partner.  The group sum is FP64.  With readout,
+ * followed by its b2 = 1 partner.  The group sum is FP64 for complex128 and
+ * a float pair (error-free two-sums, ~48 bits) for complex64.  With readout,
  * (1/sqrt s) sum_v a_v -- the flag-0 amplitude of T~^dag's output -- goes into
  * the QLS accumulator. */
 template <typename AmpT>
@@ -921,7 +1008,7 @@ __device__ int reflect_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
         __syncwarp();
     }
     int out = 0;
-    double px = 0.0, py = 0.0;
+    typename Amp<AmpT>::Sum sum;
     for (int base = 0; base < n; base += 32) {
         const int i = base + lane;
         const bool valid = i < n;
@@ -932,9 +1019,7 @@ __device__ int reflect_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
             const int u = (int)((k >> 1) & (uint64_t)(s - 1));
             if ((k & 1ull) == 0) {
                 zbuf[u] = v;
-                const double2 z = Amp<AmpT>::to_d(v);
-                px += z.x;
-                py += z.y;
+                sum.add(v);
             } else {
                 pbuf[u] = (int16_t)i;
             }
@@ -950,22 +1035,22 @@ __device__ int reflect_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
     }
     if (rowzero) {
         __syncwarp();
-        const double sx = warp_sum(px), sy = warp_sum(py);
-        const double cx = d.two_over_s * sx, cy = d.two_over_s * sy;
+        sum.reduce();
         if (a.qls_readout && r.valid && lane == 0) {
+            const double2 sv = sum.value();
             double2 acc = a.qls_y[r.j];
-            acc.x += a.qls_coef * (d.inv_sqrt_s * sx);
-            acc.y += a.qls_coef * (d.inv_sqrt_s * sy);
+            acc.x += a.qls_coef * (d.inv_sqrt_s * sv.x);
+            acc.y += a.qls_coef * (d.inv_sqrt_s * sv.y);
             a.qls_y[r.j] = acc;
         }
+        sum.scale_pow2(d.two_over_s);
         for (int ub = 0; ub < s; ub += 32) {
             const int u = ub + lane;
             const bool vu = u < s;
             AmpT o0 = Amp<AmpT>::zero();
             int p = -1;
             if (vu) {
-                const double2 au = Amp<AmpT>::to_d(zbuf[u]);
-                o0 = Amp<AmpT>::from_d(make_double2(cx - au.x, cy - au.y));
+                o0 = sum.minus(zbuf[u]);
                 p = pbuf[u];
             }
             const bool c0 = vu && Amp<AmpT>::keep(d, o0);
@@ -1030,14 +1115,6 @@ __device__ __forceinline__ uint64_t map_t(const QwSimDev &d, const Row &r, uint6
     return encode_r(y, d.nb) | ((uint64_t)(r.j > y.k) << QW_SNEG_BIT);
 }
 
-template <int WHICH>
-__device__ void map_row(const QwSimDev &d, const Row &r, uint64_t *ks, int n, int32_t *status)
-{
-    for (int i = lane_id(); i < n; i += 32) ks[i] = (WHICH == 0) ? map_tdag(d, r, ks[i], status)
-                                                                : map_t(d, r, ks[i]);
-    __syncwarp();
-}
-
 /* S, and the append of every branch to the bucket of its new row. */
 template <typename AmpT>
 __device__ void emit_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, const AmpT *as, int n,
@@ -1075,9 +1152,13 @@ __device__ void emit_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, 
     }
 }
 
-template <typename AmpT>
-__global__ void __launch_bounds__(WARPS * 32, 4) k_walk(QwSimDev d, QwBufDev in, QwBufDev out,
-                                                     QwBufDev clr, QwStepArgs a)
+/* One walk step.  PF = false: 4 blocks per SM, each row loaded when its turn
+ * comes.  PF = true: 3 blocks per SM (more registers), the row loop software-
+ * pipelined -- counts read two rows ahead, the next row's keys and amplitudes
+ * (first 32) loaded into registers while the current row is processed. */
+template <typename AmpT, bool PF>
+__global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwBufDev in, QwBufDev out,
+                                                                 QwBufDev clr, QwStepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double block_part[WARPS];
@@ -1107,12 +1188,55 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk(QwSimDev d, QwBufDev in,
     typename Amp<AmpT>::Norm nrm;
     unsigned long long st_rows = 0, st_in = 0, st_rdag = 0, st_hph = 0, st_out = 0;
 
-    for (int64_t b = (int64_t)blockIdx.x * WARPS + warp; b < bhi; b += (int64_t)gridDim.x * WARPS) {
-        int n = in.count[b];
+    /* Static balanced schedule: a warp takes both rows (b1 = 0 and 1) of a j
+       as one unit -- the b1 = 0 row is about twice the b1 = 1 row and holds
+       the zero-type reflection, so a plain stride over buckets (an even
+       number of warps) would hand half the warps only heavy rows -- and
+       strides over units; spill buckets are one unit each.  PF: the next
+       bucket's count and entries are read ahead. */
+    const int64_t nwarps = (int64_t)gridDim.x * WARPS;
+    const int64_t d2 = d.dense_buckets >> 1;
+    auto first_of = [&](int64_t u) -> int64_t { return u < d2 ? 2 * u : d.dense_buckets + (u - d2); };
+    auto next_of = [&](int64_t bb) -> int64_t {
+        int64_t u;
+        if (bb < d.dense_buckets) {
+            if ((bb & 1) == 0) return bb + 1;
+            u = (bb >> 1) + nwarps;
+        } else {
+            u = d2 + (bb - d.dense_buckets) + nwarps;
+        }
+        return first_of(u);
+    };
+    int64_t b = first_of((int64_t)blockIdx.x * WARPS + warp);
+    if (bhi == 0) b = bhi;
+    int n_nxt = 0;
+    bool have = false;
+    uint64_t pk = 0;
+    AmpT pa = Amp<AmpT>::zero();
+    int64_t bn = bhi;
+    if (PF && b < bhi) n_nxt = in.count[b];
+    while (b < bhi) {
+        int n;
+        bool have_cur = false;
+        uint64_t hk = 0;
+        AmpT ha = Amp<AmpT>::zero();
+        bn = next_of(b);
+        if (PF) {
+            n = n_nxt;
+            have_cur = have;
+            hk = pk;
+            ha = pa;
+            n_nxt = (bn < bhi) ? in.count[bn] : 0;
+            have = false;
+        } else {
+            n = in.count[b];
+        }
+        const int64_t bcur = b;
+        b = bn;
         if (n <= 0) continue;
         if (n > d.cap_row) n = d.cap_row;
         Row r;
-        if (!row_of(d, in, b, r)) continue;
+        if (!row_of(d, in, bcur, r)) continue;
         if (n > C) {
             if (lane == 0) atomicOr(a.status, QW_ST_WARP_OVERFLOW);
             continue;
@@ -1120,26 +1244,25 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk(QwSimDev d, QwBufDev in,
         r.simg = simg;
         for (int t = lane; t < d.s; t += 32)
             simg[t] = r.valid ? __ldg(d.img + r.img_base + (int64_t)r.j * d.s + t) : 0u;
-        const int64_t row0 = b * (int64_t)d.cap_row;
-        const AmpT *src = static_cast<const AmpT *>(in.amp) + row0;
-        for (int i = lane; i < n; i += 32) {
-            kQ[i] = in.key[row0 + i];
-            AmpT v = src[i];
-            if (rescale) v = scale.apply(v);
-            aQ[i] = v;
-        }
-        __syncwarp();
+        const int64_t row0 = bcur * (int64_t)d.cap_row;
         st_rows++;
         st_in += n;
-        pair_up<AmpT>(kQ, aQ, n, kP, aP);
-        const uint64_t drop = (1ull << (1 + 2 * d.nb)) - 1; /* keep b2, k, kc; A = 0 */
-        map_row<0>(d, r, kP, n, a.status);                                     /* T~^dag: maps */
-        n = rot_pairs<true, AmpT>(d, kP, aP, n, kQ, aQ, C, drop, a.status);    /* R^dag */
+        load_pairs<AmpT>(in.key + row0, static_cast<const AmpT *>(in.amp) + row0, n, rescale, scale,
+                         kP, aP, kQ, aQ, have_cur, hk, ha);
+        if (PF) { /* the next row's entries, while this row is processed */
+            const int mn = min(n_nxt, d.cap_row);
+            have = bn < bhi && mn > 0 && mn <= 32;
+            if (have && lane < mn) {
+                const int64_t slot = bn * (int64_t)d.cap_row + lane;
+                pk = in.key[slot];
+                pa = static_cast<const AmpT *>(in.amp)[slot];
+            }
+        }
+        n = map_rot_pairs<0, AmpT>(d, r, kP, aP, n, kQ, aQ, C, a.status);      /* T~^dag */
         st_rdag += n;
         n = reflect_pairs<AmpT>(d, r, kQ, aQ, n, kP, aP, C, a.status, a, zbuf, pbuf); /* H P H */
         st_hph += n;
-        map_row<1>(d, r, kP, n, a.status);                                     /* T~: maps */
-        n = rot_pairs<false, AmpT>(d, kP, aP, n, kQ, aQ, C, drop, a.status);   /* R */
+        n = map_rot_pairs<1, AmpT>(d, r, kP, aP, n, kQ, aQ, C, a.status);      /* T~ */
         st_out += n;
         emit_pairs<AmpT>(d, r, kQ, aQ, n, out, a.status, nrm);                 /* S */
         __syncwarp();
@@ -1176,6 +1299,63 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk(QwSimDev d, QwBufDev in,
             if (a.stats) a.stats[QW_STAT_STEPS] += 1;
         }
         *a.done_ctr = 0u;
+    }
+}
+
+/* T~ on |b~> (qw_state_init): every row (jc = 0, j, b1 = 0) of the range
+ * holds at most the one branch k = kc = b2 = A = 0.  T~'s Hadamard turns it
+ * into the s branches (l, z = 0) with amplitude a / sqrt(s) (a group with a
+ * single member at u = 0); then the maps and R of T~ as in the step kernel;
+ * the row does not change (no S).  A row holding anything else is left to the
+ * general sort-based kernel (flagged by *fallback). */
+template <typename AmpT>
+__global__ void __launch_bounds__(WARPS * 32) k_tinit(QwSimDev d, QwBufDev buf, int64_t lo, int64_t hi,
+                                                      int32_t *status, int32_t *fallback)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int C = d.warp_cap;
+    unsigned char *base = smem + walk_smem_per_warp<AmpT>(d) * warp;
+    uint64_t *kP = reinterpret_cast<uint64_t *>(base);
+    uint64_t *kQ = kP + C;
+    AmpT *aP = reinterpret_cast<AmpT *>(kQ + C);
+    AmpT *aQ = aP + C;
+    AmpT *zbuf = aQ + C;
+    uint32_t *simg = reinterpret_cast<uint32_t *>(zbuf + d.s);
+    for (int64_t b = lo + (int64_t)blockIdx.x * WARPS + warp; b < hi; b += (int64_t)gridDim.x * WARPS) {
+        const int n = buf.count[b];
+        if (n <= 0) continue;
+        const int64_t row0 = b * (int64_t)d.cap_row;
+        if (n != 1 || buf.key[row0] != 0ull) {
+            if (lane == 0) atomicOr(fallback, 1);
+            continue;
+        }
+        Row r;
+        if (!row_of(d, buf, b, r)) continue;
+        r.simg = simg;
+        for (int t = lane; t < d.s; t += 32)
+            simg[t] = r.valid ? __ldg(d.img + r.img_base + (int64_t)r.j * d.s + t) : 0u;
+        const double2 a = Amp<AmpT>::to_d(static_cast<const AmpT *>(buf.amp)[row0]);
+        const AmpT h = Amp<AmpT>::from_d(make_double2(d.inv_sqrt_s * a.x, d.inv_sqrt_s * a.y));
+        const bool kept = Amp<AmpT>::keep(d, h);
+        int m = 0;
+        if (kept) {
+            for (int u = lane; u < d.s; u += 32) {
+                kP[u] = (uint64_t)u << 1;
+                aP[u] = h;
+            }
+            m = d.s;
+        }
+        __syncwarp();
+        m = map_rot_pairs<1, AmpT>(d, r, kP, aP, m, kQ, aQ, C, status);
+        /* write back in place: the row keeps its registers (jc, j, b1) */
+        for (int i = lane; i < m && i < d.cap_row; i += 32) {
+            buf.key[row0 + i] = kQ[i];
+            static_cast<AmpT *>(buf.amp)[row0 + i] = aQ[i];
+        }
+        if (m > d.cap_row && lane == 0) atomicOr(status, QW_ST_ROW_OVERFLOW);
+        __syncwarp();
+        if (lane == 0) buf.count[b] = m < d.cap_row ? m : d.cap_row;
     }
 }
 
@@ -1313,13 +1493,13 @@ template <typename AmpT, int MODE> size_t step_smem(const QwSimDev &d)
                             (((size_t)d.s * sizeof(uint32_t) + 15) & ~(size_t)15));
 }
 
-template <typename AmpT>
+template <typename AmpT, bool PF>
 int walk_grid_t(const QwSimDev &d)
 {
     const size_t sm = (size_t)WARPS * walk_smem_per_warp<AmpT>(d);
-    cudaFuncSetAttribute(k_walk<AmpT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_walk<AmpT, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<AmpT>, WARPS * 32, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<AmpT, PF>, WARPS * 32, sm);
     if (per_sm < 1) per_sm = 1;
     int64_t want = (d.total_buckets + WARPS - 1) / WARPS;
     int64_t g = (int64_t)per_sm * qw_sm_count();
@@ -1327,12 +1507,12 @@ int walk_grid_t(const QwSimDev &d)
     return (int)(g < 1 ? 1 : g);
 }
 
-template <typename AmpT>
+template <typename AmpT, bool PF>
 cudaError_t launch_walk_t(const QwSimDev &d, const QwBufDev &in, const QwBufDev &out,
                           const QwBufDev &clr, const QwStepArgs &a, int grid, cudaStream_t st)
 {
     const size_t sm = (size_t)WARPS * walk_smem_per_warp<AmpT>(d);
-    k_walk<AmpT><<<grid, WARPS * 32, sm, st>>>(d, in, out, clr, a);
+    k_walk<AmpT, PF><<<grid, WARPS * 32, sm, st>>>(d, in, out, clr, a);
     return cudaGetLastError();
 }
 
@@ -1375,7 +1555,10 @@ int qw_sm_count(void)
 
 int qw_step_grid(const QwSimDev &d, int fp32, int mode)
 {
-    if (mode == QW_MODE_WALK_FUSED) return fp32 ? walk_grid_t<float2>(d) : walk_grid_t<double2>(d);
+    if (mode == QW_MODE_WALK_FUSED)
+        return fp32 ? walk_grid_t<float2, false>(d) : walk_grid_t<double2, false>(d);
+    if (mode == QW_MODE_WALK_FUSED_PF)
+        return fp32 ? walk_grid_t<float2, true>(d) : walk_grid_t<double2, true>(d);
     if (fp32) {
         if (mode == QW_MODE_WALK_LITERAL) return step_grid_t<float2, QW_MODE_WALK_LITERAL>(d);
         return step_grid_t<float2, QW_MODE_T>(d);
@@ -1389,8 +1572,11 @@ cudaError_t qw_launch_step(const QwSimDev &d, const QwBufDev &in, const QwBufDev
                            cudaStream_t st)
 {
     if (a.mode == QW_MODE_WALK_FUSED)
-        return fp32 ? launch_walk_t<float2>(d, in, out, clr, a, grid, st)
-                    : launch_walk_t<double2>(d, in, out, clr, a, grid, st);
+        return fp32 ? launch_walk_t<float2, false>(d, in, out, clr, a, grid, st)
+                    : launch_walk_t<double2, false>(d, in, out, clr, a, grid, st);
+    if (a.mode == QW_MODE_WALK_FUSED_PF)
+        return fp32 ? launch_walk_t<float2, true>(d, in, out, clr, a, grid, st)
+                    : launch_walk_t<double2, true>(d, in, out, clr, a, grid, st);
     if (fp32) {
         if (a.mode == QW_MODE_WALK_LITERAL)
             return launch_step_t<float2, QW_MODE_WALK_LITERAL>(d, in, out, clr, a, grid, st);
@@ -1509,4 +1695,23 @@ cudaError_t qw_launch_measure_noalloc(const QwSimDev &d, const QwBufDev &buf, in
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(host_probs, scratch, (size_t)len * sizeof(double), cudaMemcpyDeviceToHost, st);
+}
+
+cudaError_t qw_launch_tinit(const QwSimDev &d, const QwBufDev &buf, int64_t lo, int64_t hi, int fp32,
+                            int32_t *status, int32_t *fallback, cudaStream_t st)
+{
+    int64_t rows = hi - lo;
+    int grid = (int)((rows + WARPS - 1) / WARPS);
+    if (grid > 8 * qw_sm_count()) grid = 8 * qw_sm_count();
+    if (grid < 1) grid = 1;
+    if (fp32) {
+        const size_t sm = (size_t)WARPS * walk_smem_per_warp<float2>(d);
+        cudaFuncSetAttribute(k_tinit<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_tinit<float2><<<grid, WARPS * 32, sm, st>>>(d, buf, lo, hi, status, fallback);
+    } else {
+        const size_t sm = (size_t)WARPS * walk_smem_per_warp<double2>(d);
+        cudaFuncSetAttribute(k_tinit<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_tinit<double2><<<grid, WARPS * 32, sm, st>>>(d, buf, lo, hi, status, fallback);
+    }
+    return cudaGetLastError();
 }

@@ -29,7 +29,7 @@ EXPORTED = ("qw_sim_opts_default", "qw_sim_create", "qw_state_init", "qw_apply_w
             "qw_enqueue_walk_steps", "qw_sync",
             "qw_cks_coefficients", "qw_apply_qls", "qw_measure_register", "qw_state_size",
             "qw_state_export", "qw_sim_info", "qw_step_stats", "qw_launch_count", "qw_sim_destroy",
-            "qw_last_error", "qw_measure_register_noalloc")
+            "qw_last_error", "qw_measure_register_noalloc", "qw_autotune")
 MEASURE_NOALLOC_MAX_LEN = 65536
 
 
@@ -48,7 +48,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("fuse_reflection", ctypes.c_int32),
                 ("prune_tau", ctypes.c_double), ("row_capacity", ctypes.c_int32),
                 ("warp_capacity", ctypes.c_int32), ("renorm", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("walk_variant", ctypes.c_int32)]
 
 
 _lib = None
@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True):
     lib.qw_state_export.argtypes = [P, i32, i32, P, P, i64, P]
     lib.qw_sim_info.argtypes = [P, P, P, P, P]
     lib.qw_step_stats.argtypes = [P, P, i32, i32]
+    lib.qw_autotune.argtypes = [P, i32, P, P]
     lib.qw_launch_count.argtypes = [P]
     lib.qw_launch_count.restype = i64
     lib.qw_sim_destroy.argtypes = [P]
@@ -94,7 +95,7 @@ def load(build_if_missing: bool = True):
                  "qw_sync", "qw_cks_coefficients",
                  "qw_apply_qls", "qw_measure_register", "qw_measure_register_noalloc",
                  "qw_state_size", "qw_state_export",
-                 "qw_sim_info", "qw_step_stats", "qw_sim_destroy"):
+                 "qw_sim_info", "qw_step_stats", "qw_autotune", "qw_sim_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -134,7 +135,7 @@ class Sim:
 
     def __init__(self, matrices, s_pad: int = 0, precision: int = QW_FP64, fuse_reflection: bool = True,
                  prune_tau: float = 0.0, row_capacity: int = 0, warp_capacity: int = 0,
-                 renorm: int = -1, stream: int | None = None):
+                 renorm: int = -1, stream: int | None = None, walk_variant: int = 0):
         lib = load()
         if not isinstance(matrices, (list, tuple)):
             matrices = [matrices]
@@ -155,6 +156,7 @@ class Sim:
         opts.warp_capacity = warp_capacity
         opts.renorm = renorm
         opts.stream = current_stream() if stream is None else stream
+        opts.walk_variant = walk_variant
         h = ctypes.c_void_p()
         rc = lib.qw_sim_create(arr, len(matrices), ctypes.byref(opts), ctypes.byref(h))
         if rc:
@@ -193,6 +195,13 @@ class Sim:
 
     def apply_walk_step(self, nsteps: int = 1) -> None:
         self._check(load().qw_apply_walk_step(self._h, int(nsteps)))
+
+    def autotune(self, steps_per_candidate: int = 8) -> tuple[int, list[float]]:
+        """qw_autotune: (chosen variant, [us/step of variant 0, variant 1])."""
+        choice = ctypes.c_int32()
+        us = np.zeros(2)
+        self._check(load().qw_autotune(self._h, int(steps_per_candidate), ctypes.byref(choice), _p(us)))
+        return int(choice.value), [float(us[0]), float(us[1])]
 
     def enqueue_walk_steps(self, nsteps: int = 1) -> None:
         self._check(load().qw_enqueue_walk_steps(self._h, int(nsteps)))

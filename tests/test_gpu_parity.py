@@ -43,10 +43,10 @@ def test_state_init(apply_T):
     compare(gpu_state(sim), oracle_state(o), TOL64)
 
 
-@pytest.mark.parametrize("fuse", [True, False])
-def test_walk_n16_every_step(fuse):
+@pytest.mark.parametrize("fuse,variant", [(True, 0), (True, 1), (False, 0)])
+def test_walk_n16_every_step(fuse, variant):
     w = wl.walk_n16()
-    sim = _sim(w, fuse_reflection=fuse)
+    sim = _sim(w, fuse_reflection=fuse, walk_variant=variant)
     sim.state_init(w.b)
     o = _oracle(w)
     o.apply("T")
@@ -87,9 +87,10 @@ def test_walk_n1024_fp64_100_steps():
         compare(gpu_state(sim), oracle_state(o), TOL64)
 
 
-def test_walk_n16384_fp64_full_size():
+@pytest.mark.parametrize("variant", [0, 1])
+def test_walk_n16384_fp64_full_size(variant):
     w = wl.walk_n16384()
-    sim = _sim(w)
+    sim = _sim(w, walk_variant=variant)
     sim.state_init(w.b)
     o = _oracle(w)
     o.apply("T")
@@ -118,11 +119,15 @@ def test_fp32_amp_n1024_100_steps():
 
 def test_fp32_amp_n16384_bench_config():
     """The benchmarked configuration (N=16384, s=16, complex64 amplitudes with
-    FP64 merge, norm and renormalisation), 20 steps, against the FP64 oracle."""
+    FP64 merge, norm and renormalisation), 20 steps -- 4 of them by each
+    variant inside the autotuner, as bench.py runs it -- against the FP64
+    oracle."""
     w = wl.walk_n16384()
     sim = _sim(w, precision=qwalk.QW_FP32_AMP)
     sim.state_init(w.b)
-    sim.apply_walk_step(w.steps)
+    choice, us = sim.autotune(4)
+    assert choice in (0, 1) and min(us) > 0
+    sim.apply_walk_step(w.steps - 8)
     o = _oracle(w)
     o.apply("T")
     for _ in range(w.steps):
