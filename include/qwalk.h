@@ -83,6 +83,8 @@ typedef struct {
     int32_t walk_variant;    /* step kernel with fuse_reflection = 1: 0 = one row at a
                                 time (default), 1 = software-pipelined row loop; see
                                 qw_autotune */
+    int32_t graphs;          /* 1 (default): runs of >= 6 walk steps are issued as replays
+                                of a captured 6-step CUDA graph; 0: one launch per step */
 } qw_sim_opts;
 
 /* Fill *opts with the defaults above. */

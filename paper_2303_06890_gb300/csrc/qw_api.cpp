@@ -88,8 +88,23 @@ struct qw_sim {
     int64_t qls_p_cap = 0;
     int64_t device_bytes = 0;
     int64_t launches = 0;
+    /* captured 6-step graphs, one per (buffer, scale slot) phase */
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
     std::string err;
 };
+
+static const int kGraphSteps = 6; /* a multiple of the 3-buffer and 2-slot periods */
+
+static void drop_graphs(qw_sim *sim)
+{
+    for (auto &row : sim->gexec)
+        for (auto &g : row)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+}
 
 static int fail(qw_sim *sim, int code, const std::string &msg)
 {
@@ -127,6 +142,7 @@ extern "C" void qw_sim_opts_default(qw_sim_opts *o)
     o->renorm = -1;
     o->stream = nullptr;
     o->walk_variant = 0;
+    o->graphs = 1;
 }
 
 /* Validate one CSC matrix; on success return its largest column count. */
@@ -377,6 +393,8 @@ extern "C" int qw_sim_destroy(qw_sim *sim)
         cudaFree(b.count);
         cudaFree(b.spill);
     }
+    drop_graphs(sim);
+    if (sim->cap_stream) cudaStreamDestroy(sim->cap_stream);
     cudaFree(sim->partials);
     cudaFree(sim->sc);
     cudaFree(sim->qls_y);
@@ -557,13 +575,58 @@ extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, cons
     return QW_OK;
 }
 
+/* Capture kGraphSteps walk steps starting at the current (buffer, slot)
+ * phase on a private stream; the sequence of kernel arguments repeats with
+ * that period, so the graph can be replayed whenever the phase recurs. */
+static int capture_graph(qw_sim *sim, cudaGraphExec_t *out)
+{
+    if (!sim->cap_stream) QW_CUDA(sim, cudaStreamCreateWithFlags(&sim->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = sim->stream;
+    const int cur = sim->cur, slot = sim->scale_slot;
+    const int64_t launches = sim->launches;
+    sim->stream = sim->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(sim->cap_stream, cudaStreamCaptureModeThreadLocal);
+    int rc = QW_OK;
+    for (int t = 0; t < kGraphSteps && e == cudaSuccess && rc == QW_OK; ++t) rc = launch_walk(sim, 0.0, 0);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(sim->cap_stream, &g);
+    sim->stream = user;
+    sim->cur = cur;
+    sim->scale_slot = slot;
+    sim->launches = launches;
+    if (e != cudaSuccess) return cuda_fail(sim, e, "cudaStreamBeginCapture");
+    if (rc != QW_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e2 != cudaSuccess) return cuda_fail(sim, e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(sim, e, "cudaGraphInstantiate");
+    return QW_OK;
+}
+
 extern "C" int qw_enqueue_walk_steps(qw_sim *sim, int64_t nsteps)
 {
     if (!sim) return QW_ERR_ARG;
     if (nsteps < 0) return fail(sim, QW_ERR_ARG, "nsteps < 0");
     if (!sim->has_state) return fail(sim, QW_ERR_STATE, "no state: call qw_state_init first");
     if (nsteps > 0) sim->fresh_T = false;
-    for (int64_t t = 0; t < nsteps; ++t) {
+    int64_t t = 0;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (sim->opts.graphs && nsteps >= kGraphSteps &&
+        cudaStreamIsCapturing(sim->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+        cudaGraphExec_t &g = sim->gexec[sim->cur][sim->scale_slot];
+        if (!g) {
+            int rc = capture_graph(sim, &g);
+            if (rc != QW_OK) return rc;
+        }
+        for (; t + kGraphSteps <= nsteps; t += kGraphSteps) {
+            QW_CUDA(sim, cudaGraphLaunch(g, sim->stream));
+            sim->launches += kGraphSteps; /* one k_walk launch per step inside the graph */
+        }
+    }
+    for (; t < nsteps; ++t) {
         int rc = launch_walk(sim, 0.0, 0);
         if (rc != QW_OK) return rc;
     }
@@ -597,6 +660,8 @@ extern "C" int qw_autotune(qw_sim *sim, int32_t steps, int32_t *choice, double *
     QW_CUDA(sim, cudaEventCreate(&e0));
     QW_CUDA(sim, cudaEventCreate(&e1));
     int rc = QW_OK;
+    const int graphs = sim->opts.graphs;
+    sim->opts.graphs = 0; /* time the kernels themselves */
     for (int v = 0; v < 2 && rc == QW_OK; ++v) {
         sim->mode = modes[v];
         sim->grid_walk = qw_step_grid(sim->d, sim->fp32, sim->mode);
@@ -607,11 +672,13 @@ extern "C" int qw_autotune(qw_sim *sim, int32_t steps, int32_t *choice, double *
         float ms = 0.f;
         if (rc == QW_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) us[v] = 1000.0 * ms / steps;
     }
+    sim->opts.graphs = graphs;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     const int best = (us[1] > 0.0 && us[1] < us[0]) ? 1 : 0;
     sim->mode = modes[best];
     sim->grid_walk = qw_step_grid(sim->d, sim->fp32, sim->mode);
+    drop_graphs(sim);
     if (choice) *choice = best;
     if (us_per_step) {
         us_per_step[0] = us[0];

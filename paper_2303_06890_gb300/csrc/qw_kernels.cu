@@ -1019,7 +1019,6 @@ __device__ int reflect_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
             const int u = (int)((k >> 1) & (uint64_t)(s - 1));
             if ((k & 1ull) == 0) {
                 zbuf[u] = v;
-                sum.add(v);
             } else {
                 pbuf[u] = (int16_t)i;
             }
@@ -1034,7 +1033,9 @@ __device__ int reflect_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
         out += total;
     }
     if (rowzero) {
+        /* sum by u in a fixed order, whatever order the row's branches came in */
         __syncwarp();
+        for (int t = lane; t < s; t += 32) sum.add(zbuf[t]);
         sum.reduce();
         if (a.qls_readout && r.valid && lane == 0) {
             const double2 sv = sum.value();

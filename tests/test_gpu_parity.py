@@ -320,3 +320,32 @@ def test_launch_count_and_reinit():
     o = _oracle(w)
     o.apply("T")
     compare(gpu_state(sim), oracle_state(o), TOL64)
+
+
+@pytest.mark.parametrize("precision", [qwalk.QW_FP64, qwalk.QW_FP32_AMP])
+def test_graph_replay_equals_direct_launches(precision):
+    """Runs issued as replays of the captured 6-step graph give the same state
+    as one launch per step, from every (buffer, slot) phase: bit for bit in
+    FP64; in FP32 up to the renormalisation factor, whose FP64 norm sums the
+    branches in their (atomic, run-dependent) arrival order."""
+    w = wl.walk_n1024()
+    a = _sim(w, precision=precision, graphs=True)
+    b = _sim(w, precision=precision, graphs=False)
+    for sim in (a, b):
+        sim.state_init(w.b)
+    for n in (7, 6, 13, 1, 12):
+        a.apply_walk_step(n)
+        b.apply_walk_step(n)
+        ka, va = a.state_export()
+        kb, vb = b.state_export()
+        assert np.array_equal(ka, kb), n
+        if precision == qwalk.QW_FP64:
+            assert np.array_equal(va, vb), n
+        else:
+            assert np.abs(va - vb).max() <= 1e-6 * np.abs(vb).max(), n
+    o = _oracle(w)
+    o.apply("T")
+    for _ in range(39):
+        o.apply("W")
+    if precision == qwalk.QW_FP64:
+        compare(gpu_state(a), oracle_state(o), TOL64)
