@@ -49,6 +49,8 @@ def parse_args():
     p.add_argument("--e2e-jobs", type=int, default=10)
     p.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--batched-steps", type=int, default=300)
     return p.parse_args()
 
 
@@ -274,6 +276,9 @@ def run_ours(args, rank, world, local_rank):
            "job": f"qw_state_init(|b> from pinned host memory, T~) + {steps_per_job} walk steps "
                   f"+ qw_measure_register(j) to host"}
 
+    batched = None if args.no_batched else batched_leg(args, torch, flush, barrier, max_over_ranks,
+                                                       world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args.cpu_budget)
@@ -306,9 +311,74 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": gpu_launches,
         "clocks": clk,
     }
+    if batched is not None:
+        line["batched"] = batched
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
+
+
+def batched_leg(args, torch, flush, barrier, max_over_ranks, world) -> dict:
+    """256 independent walks (N log-uniform in [64, 4096], s = 8) advanced
+    together, one k_walk launch per step: kernel time per step (L2 flushed
+    before each timed step), the whole 50-step walk as CUDA-graph replays,
+    and the same instances walked one at a time by the plain complex128 path."""
+    from paper_2303_06890_gb300 import qwalk
+    from paper_2303_06890_gb300 import workloads as wl
+
+    ws = wl.batched(256)
+    sim = qwalk.Sim([w.matrix for w in ws], s_pad=8, precision=qwalk.QW_FP32_AMP)
+    for i, w in enumerate(ws):
+        sim.state_init(w.b, inst=i)
+    variant, tune = sim.autotune(3)
+    sim.apply_walk_step(6)
+    sim.step_stats(reset=True)
+    barrier()
+    t_dev, per = timed_walk(sim, args.batched_steps, torch, flush)
+    barrier()
+    stats = sim.step_stats(reset=True)
+    t_dev = max_over_ranks(t_dev)
+    # whole walks: re-initialise, 50 steps issued as graph replays, one event pair
+    for i, w in enumerate(ws):
+        sim.state_init(w.b, inst=i)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    e0.record()
+    sim.enqueue_walk_steps(50)
+    e1.record()
+    torch.cuda.synchronize()
+    sim.sync()
+    t_walk = max_over_ranks(e0.elapsed_time(e1) / 1000.0)
+    sim.close()
+    # the plain complex128 path, one instance at a time (instances after the
+    # first 64 are timed on a stride-4 sample and scaled by the step count)
+    t_seq = 0.0
+    sample = list(range(0, 256, 4))
+    for i in sample:
+        w = ws[i]
+        s1 = qwalk.Sim(w.matrix, s_pad=8, precision=qwalk.QW_FP64)
+        s1.state_init(w.b)
+        s1.apply_walk_step(2)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        s1.enqueue_walk_steps(50)
+        a1.record()
+        torch.cuda.synchronize()
+        s1.sync()
+        t_seq += a0.elapsed_time(a1) / 1000.0
+        s1.close()
+    t_seq *= 256 / len(sample)
+    t_seq = max_over_ranks(t_seq)
+    steps = max(1, stats["steps"])
+    return {"workload": "batched_256_n64-4096_s8", "instances": 256,
+            "branches_per_step": stats["out"] / steps,
+            "steps_per_s": world * args.batched_steps / t_dev,
+            "instance_steps_per_s": world * 256 * args.batched_steps / t_dev,
+            "ms_per_step": 1000.0 * t_dev / args.batched_steps,
+            "variant": variant, "autotune_us_per_step": tune,
+            "walk_50_steps_ms_graph": 1000.0 * t_walk,
+            "sequential_fp64_walk_50_steps_ms": 1000.0 * t_seq,
+            "speedup_vs_sequential_fp64": t_seq / t_walk}
 
 
 def cpu_baseline(w, budget: float) -> dict:

@@ -185,9 +185,10 @@ def conditioned_symmetric(n: int, smax: int, attempts: int, cond: float, seed: i
     return _assemble(n, diag_q, pairs, off_q)
 
 
-def _workload(name: str, m: Matrix, b: np.ndarray, steps: int, s: int | None = None) -> Workload:
+def _workload(name: str, m: Matrix, b: np.ndarray, steps: int, s: int | None = None,
+              spectrum: bool = True) -> Workload:
     s = next_pow2(m.max_col_nnz) if s is None else s
-    cond, kappa = _spectrum_stats(m, s)
+    cond, kappa = _spectrum_stats(m, s) if spectrum else (float("nan"), float("nan"))
     return Workload(name=name, matrix=m, b=b, s=s, steps=steps, cond=cond, kappa=kappa)
 
 
@@ -227,7 +228,8 @@ def batched(count: int = 256) -> list[Workload]:
     out = []
     for i, n in enumerate(batched_sizes(count)):
         m = random_symmetric(n, 8, 1, (3 * n) // 2, seed=500 + i)
-        out.append(_workload(f"batched_{i}_n{n}", m, random_b(n, 1000 + i), steps=50, s=8))
+        out.append(_workload(f"batched_{i}_n{n}", m, random_b(n, 1000 + i), steps=50, s=8,
+                             spectrum=False))
     return out
 
 

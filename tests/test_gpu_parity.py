@@ -349,3 +349,30 @@ def test_graph_replay_equals_direct_launches(precision):
         o.apply("W")
     if precision == qwalk.QW_FP64:
         compare(gpu_state(a), oracle_state(o), TOL64)
+
+
+@pytest.mark.parametrize("precision", [qwalk.QW_FP64, qwalk.QW_FP32_AMP])
+def test_batched_256_instances_full_size(precision):
+    """The batched workload at full size: 256 walks (N log-uniform in [64,
+    4096], s = 8) advanced together, one launch per step (graph-replayed), 50
+    steps.  FP64: a sample of instances across the size range equals its own
+    oracle; both precisions: every instance keeps unit norm."""
+    ws = wl.batched(256)
+    sim = qwalk.Sim([w.matrix for w in ws], s_pad=8, precision=precision)
+    for i, w in enumerate(ws):
+        sim.state_init(w.b, inst=i)
+    sim.apply_walk_step(50)
+    for i, w in enumerate(ws):
+        p = sim.measure_register("b2", 2, inst=i)
+        assert abs(p.sum() - 1.0) < (1e-10 if precision == qwalk.QW_FP64 else 1e-5), i
+    if precision != qwalk.QW_FP64:
+        return
+    by_size = sorted(range(len(ws)), key=lambda i: ws[i].n)
+    for i in by_size[::32] + [by_size[-1]]:
+        w = ws[i]
+        o = oracle.Oracle(w.matrix, 8)
+        o.init_b(w.b)
+        o.apply("T")
+        for _ in range(50):
+            o.apply("W")
+        compare(gpu_state(sim, inst=i), oracle_state(o), TOL64)
