@@ -55,8 +55,8 @@ def parse_args():
 
 
 def dist_env():
-    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
-            int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_2303_06890_gb300 import ranks
+    return ranks.env()
 
 
 def peaks():
@@ -195,17 +195,14 @@ def run_ours(args, rank, world, local_rank):
     w = wl.walk_n16384()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
+    from paper_2303_06890_gb300 import ranks
+
     def barrier():
         torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
+        ranks.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return ranks.max_over_ranks(x, device="cuda")
 
     # --- the benchmarked path: complex64 amplitudes, FP64 merge/norm/renorm ---
     sim = qwalk.Sim(w.matrix, s_pad=w.s, precision=qwalk.QW_FP32_AMP)
@@ -277,7 +274,7 @@ def run_ours(args, rank, world, local_rank):
                   f"+ qw_measure_register(j) to host"}
 
     batched = None if args.no_batched else batched_leg(args, torch, flush, barrier, max_over_ranks,
-                                                       world)
+                                                       world, rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -318,15 +315,17 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
-def batched_leg(args, torch, flush, barrier, max_over_ranks, world) -> dict:
+def batched_leg(args, torch, flush, barrier, max_over_ranks, world, rank) -> dict:
     """256 independent walks (N log-uniform in [64, 4096], s = 8) advanced
     together, one k_walk launch per step: kernel time per step (L2 flushed
     before each timed step), the whole 50-step walk as CUDA-graph replays,
-    and the same instances walked one at a time by the plain complex128 path."""
+    and the same instances walked one at a time by the plain complex128 path.
+    Each rank runs its own 256 instances (weak scaling)."""
     from paper_2303_06890_gb300 import qwalk
+    from paper_2303_06890_gb300 import ranks
     from paper_2303_06890_gb300 import workloads as wl
 
-    ws = wl.batched(256)
+    ws = wl.batched(256, first=ranks.instance_seed_offset(rank, 256))
     sim = qwalk.Sim([w.matrix for w in ws], s_pad=8, precision=qwalk.QW_FP32_AMP)
     for i, w in enumerate(ws):
         sim.state_init(w.b, inst=i)

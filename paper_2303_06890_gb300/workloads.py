@@ -223,13 +223,18 @@ def batched_sizes(count: int = 256, seed: int = 500) -> list[int]:
     return [int(round(2.0 ** x)) for x in rng.uniform(6.0, 12.0, count)]
 
 
-def batched(count: int = 256) -> list[Workload]:
-    """``count`` walks, N log-uniform in [64, 4096], <=8 nnz/column, 50 steps."""
+def batched(count: int = 256, first: int = 0) -> list[Workload]:
+    """``count`` walks, N log-uniform in [64, 4096], <=8 nnz/column, 50 steps.
+
+    Instance ``first + i`` uses matrix seed 500 + first + i and |b> seed
+    1000 + first + i (``first`` > 0 gives another rank its own instances).
+    """
     out = []
-    for i, n in enumerate(batched_sizes(count)):
-        m = random_symmetric(n, 8, 1, (3 * n) // 2, seed=500 + i)
-        out.append(_workload(f"batched_{i}_n{n}", m, random_b(n, 1000 + i), steps=50, s=8,
-                             spectrum=False))
+    sizes = batched_sizes(count, seed=500 + first)
+    for i, n in enumerate(sizes):
+        m = random_symmetric(n, 8, 1, (3 * n) // 2, seed=500 + first + i)
+        out.append(_workload(f"batched_{first + i}_n{n}", m, random_b(n, 1000 + first + i), steps=50,
+                             s=8, spectrum=False))
     return out
 
 
