@@ -100,6 +100,17 @@ __device__ __forceinline__ int warp_excl_scan(int v, int &total)
     return x - v;
 }
 
+/* Compaction for per-lane emit flags c0, c1 in {0, 1}, emitted in lane
+ * order as (c0 item, c1 item): the lane's first output position among the
+ * warp's outputs, and the warp total, from two ballots. */
+__device__ __forceinline__ int warp_compact2(bool c0, bool c1, int &total)
+{
+    const unsigned lt = (1u << lane_id()) - 1u;
+    const unsigned b0 = __ballot_sync(FULL, c0), b1 = __ballot_sync(FULL, c1);
+    total = __popc(b0) + __popc(b1);
+    return __popc(b0 & lt) + __popc(b1 & lt);
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -880,7 +891,7 @@ __device__ void load_pairs(const uint64_t *gkey, const AmpT *gamp, int n, bool r
         const bool head = valid && ((k & 1) == 0 || other == 0);
         const int cnt = head ? (other ? 2 : 1) : 0;
         int total;
-        const int pos = warp_excl_scan(cnt, total);
+        const int pos = warp_compact2(head, cnt == 2, total);
         const int src = other ? (__ffs(other) - 1) : lane;
         const uint64_t pk = __shfl_sync(FULL, k, src);
         AmpT pa;
@@ -962,7 +973,7 @@ __device__ int map_rot_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
             kb = mk & keep_mask;
         }
         int total;
-        int pos = out + warp_excl_scan((int)c0 + (int)c1, total);
+        int pos = out + warp_compact2(c0, c1, total);
         if (c0) {
             if (pos < cap) { kd[pos] = kb; ad[pos] = o0; }
             pos++;
@@ -1025,7 +1036,7 @@ __device__ int reflect_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
         }
         const bool c = valid && !zp && Amp<AmpT>::keep(d, v);
         int total;
-        const int pos = out + warp_excl_scan((int)c, total);
+        const int pos = out + warp_compact2(c, false, total);
         if (c && pos < cap) {
             kd[pos] = k;
             ad[pos] = Amp<AmpT>::neg(v);
@@ -1057,7 +1068,7 @@ __device__ int reflect_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
             const bool c0 = vu && Amp<AmpT>::keep(d, o0);
             const bool c1 = p >= 0;
             int total;
-            int pos = out + warp_excl_scan((int)c0 + (int)c1, total);
+            int pos = out + warp_compact2(c0, c1, total);
             const uint64_t k0 = (uint64_t)u << 1;
             if (c0) {
                 if (pos < cap) { kd[pos] = k0; ad[pos] = o0; }
@@ -1216,6 +1227,7 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
     AmpT pa = Amp<AmpT>::zero();
     int64_t bn = bhi;
     if (PF && b < bhi) n_nxt = in.count[b];
+    int64_t staged = -1; /* (inst, j) of the QRAM row held in simg */
     while (b < bhi) {
         int n;
         bool have_cur = false;
@@ -1243,8 +1255,11 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
             continue;
         }
         r.simg = simg;
-        for (int t = lane; t < d.s; t += 32)
-            simg[t] = r.valid ? __ldg(d.img + r.img_base + (int64_t)r.j * d.s + t) : 0u;
+        const int64_t want = ((int64_t)r.inst << 32) | (int64_t)r.j;
+        if (r.valid && want != staged) { /* rows b1 = 0, 1 of one j come in a row */
+            for (int t = lane; t < d.s; t += 32) simg[t] = __ldg(d.img + r.img_base + (int64_t)r.j * d.s + t);
+            staged = want;
+        }
         const int64_t row0 = bcur * (int64_t)d.cap_row;
         st_rows++;
         st_in += n;
