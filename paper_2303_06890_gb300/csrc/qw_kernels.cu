@@ -36,6 +36,7 @@ struct Row {
     int64_t img_base;
     bool valid; /* j < N: the row has a QRAM image */
     const uint32_t *simg;
+    const void *sfg; /* rotation values of the row's s slots (fused kernel), or null */
 };
 
 struct Regs {
@@ -646,13 +647,21 @@ __global__ void __launch_bounds__(WARPS * 32) k_step(QwSimDev d, QwBufDev in, Qw
     }
 }
 
+/* per-warp shared memory of the fused kernels: keys x2, amps x2, zero-group
+ * buffer, staged QRAM row, partner indices, then (16-byte aligned) the
+ * staged rotation values of the row's s slots */
 template <typename AmpT>
-__host__ __device__ inline size_t walk_smem_per_warp(const QwSimDev &d)
+__host__ __device__ inline size_t walk_smem_head(const QwSimDev &d)
 {
-    /* keys x2, amps x2, zero-group buffer, staged QRAM row, partner indices */
     size_t b = (size_t)d.warp_cap * 2 * (sizeof(uint64_t) + sizeof(AmpT)) + (size_t)d.s * sizeof(AmpT) +
                (size_t)d.s * sizeof(uint32_t) + (size_t)d.s * sizeof(int16_t);
     return (b + 15) & ~(size_t)15;
+}
+
+template <typename AmpT>
+__host__ __device__ inline size_t walk_smem_per_warp(const QwSimDev &d)
+{
+    return walk_smem_head<AmpT>(d) + (size_t)d.s * 16;
 }
 
 /* ==== fused walk step: one sort per row, b2-pairs kept adjacent ============== */
@@ -705,8 +714,10 @@ template <> struct Amp<double2> {
         __device__ explicit Scale(double v) : s(v) {}
         __device__ T apply(T a) const { return make_double2(a.x * s, a.y * s); }
     };
-    /* (A x + B y) per component, FP64 */
-    __device__ static void rot(const QwSimDev &d, uint32_t A, bool dag, bool sneg, T a0, T a1, T &o0, T &o1);
+    typedef double2 RotVal; /* (sqrt|a|, sqrt(1-|a|)) */
+    __device__ static RotVal rot_table(const QwSimDev &d, uint32_t A) { return __ldg(d.fg + A); }
+    __device__ static RotVal rot_zero() { return make_double2(0.0, 1.0); }
+    __device__ static void rot(RotVal t, uint32_t A, bool dag, bool sneg, T a0, T a1, T &o0, T &o1);
 };
 
 /* complex64 path: amplitudes are float; each rotation output f a0 +- g a1 is
@@ -814,7 +825,10 @@ template <> struct Amp<float2> {
         const float t = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bp)), __fsub_rn(p2, bp));
         return __fadd_rn(s, __fadd_rn(t, __fadd_rn(e1, e2)));
     }
-    __device__ static void rot(const QwSimDev &d, uint32_t A, bool dag, bool sneg, T a0, T a1, T &o0, T &o1);
+    typedef float4 RotVal; /* (sqrt|a|, sqrt(1-|a|)) as float pairs */
+    __device__ static RotVal rot_table(const QwSimDev &d, uint32_t A) { return __ldg(d.fg32 + A); }
+    __device__ static RotVal rot_zero() { return make_float4(0.f, 0.f, 1.f, 0.f); }
+    __device__ static void rot(RotVal t, uint32_t A, bool dag, bool sneg, T a0, T a1, T &o0, T &o1);
 };
 
 /* multiply by 1 (real f) or by i*sigma (imaginary f), sigma = sneg ? -1 : 1 */
@@ -833,10 +847,8 @@ __device__ __forceinline__ T rho(T a, bool imag, bool sneg)
  * R^dag: o0 = conj(f) a0 + g a1, o1 = f a1 - g a0
  * with f = fm (a >= 0) or i sigma fm (a < 0): f x = fm rho(x, sigma),
  * conj(f) x = fm rho(x, -sigma). */
-__device__ void Amp<double2>::rot(const QwSimDev &d, uint32_t A, bool dag, bool sneg, T a0, T a1,
-                                  T &o0, T &o1)
+__device__ void Amp<double2>::rot(RotVal t, uint32_t A, bool dag, bool sneg, T a0, T a1, T &o0, T &o1)
 {
-    const double2 t = __ldg(d.fg + A);
     const double fm = t.x, g = t.y;
     const bool imag = (int16_t)(uint16_t)A < 0;
     const double2 x0 = rho(a0, imag, dag ? !sneg : sneg);
@@ -850,10 +862,9 @@ __device__ void Amp<double2>::rot(const QwSimDev &d, uint32_t A, bool dag, bool 
     }
 }
 
-__device__ void Amp<float2>::rot(const QwSimDev &d, uint32_t A, bool dag, bool sneg, T a0, T a1,
-                                 T &o0, T &o1)
+__device__ void Amp<float2>::rot(RotVal t, uint32_t A, bool dag, bool sneg, T a0, T a1, T &o0, T &o1)
 {
-    const float4 t = __ldg(d.fg32 + A); /* fh, fl, gh, gl */
+    /* t = (fh, fl, gh, gl) */
     const bool imag = (int16_t)(uint16_t)A < 0;
     const float2 x0 = rho(a0, imag, dag ? !sneg : sneg);
     const float2 x1 = rho(a1, imag, dag ? sneg : !sneg);
@@ -932,8 +943,8 @@ __device__ void load_pairs(const uint64_t *gkey, const AmpT *gamp, int n, bool r
 #define QW_SNEG_BIT 63
 
 __device__ __forceinline__ uint64_t map_tdag(const QwSimDev &d, const Row &r, uint64_t key,
-                                            int32_t *status);
-__device__ __forceinline__ uint64_t map_t(const QwSimDev &d, const Row &r, uint64_t key);
+                                            int32_t *status, uint32_t &slot);
+__device__ __forceinline__ uint64_t map_t(const QwSimDev &d, const Row &r, uint64_t key, uint32_t &slot);
 
 /* The register maps of one half-step followed by R^dag (WHICH = 0, T~^dag) or
  * R (WHICH = 1, T~) on the adjacent b2-pairs.  The maps never read b2, so the
@@ -965,9 +976,17 @@ __device__ int map_rot_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
             } else {
                 a1 = as[i];
             }
-            const uint64_t mk = (WHICH == 0) ? map_tdag(d, r, k & ~1ull, status) : map_t(d, r, k & ~1ull);
+            uint32_t slot;
+            const uint64_t mk = (WHICH == 0) ? map_tdag(d, r, k & ~1ull, status, slot)
+                                             : map_t(d, r, k & ~1ull, slot);
             const uint32_t A = (uint32_t)(mk >> ash) & 0xffffu;
-            Amp<AmpT>::rot(d, A, WHICH == 0, (mk >> QW_SNEG_BIT) != 0, a0, a1, o0, o1);
+            /* A is 0 or the value of slot `slot` of row j: staged rotation
+               values for a slot of this row, the per-code table otherwise */
+            typename Amp<AmpT>::RotVal t;
+            if (A == 0) t = Amp<AmpT>::rot_zero();
+            else if (slot < (uint32_t)d.s && r.sfg) t = static_cast<const typename Amp<AmpT>::RotVal *>(r.sfg)[slot];
+            else t = Amp<AmpT>::rot_table(d, A);
+            Amp<AmpT>::rot(t, A, WHICH == 0, (mk >> QW_SNEG_BIT) != 0, a0, a1, o0, o1);
             c0 = Amp<AmpT>::keep(d, o0);
             c1 = Amp<AmpT>::keep(d, o1);
             kb = mk & keep_mask;
@@ -1097,7 +1116,7 @@ __device__ int reflect_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
  * controls are dropped (A = 0).  Input A must be 0 (T~ and T~^dag return it
  * to 0 at the end of every step). */
 __device__ __forceinline__ uint64_t map_tdag(const QwSimDev &d, const Row &r, uint64_t key,
-                                            int32_t *status)
+                                            int32_t *status, uint32_t &slot)
 {
     const Regs x = decode_r(key, d.nb);
     if (x.A != 0) atomicOr(status, QW_ST_ANCILLA);
@@ -1107,6 +1126,7 @@ __device__ __forceinline__ uint64_t map_tdag(const QwSimDev &d, const Row &r, ui
     y.k = l;
     y.kc = x.k ^ (w >> 16);
     y.A = (r.jc == 0 && y.kc == 0) ? (w & 0xffffu) : 0u;
+    slot = r.valid ? l : 0xffffffffu;
     y.b2 = x.b2;
     return encode_r(y, d.nb) | ((uint64_t)(r.j > x.k) << QW_SNEG_BIT);
 }
@@ -1115,10 +1135,11 @@ __device__ __forceinline__ uint64_t map_tdag(const QwSimDev &d, const Row &r, ui
  * (l, z): A = [jc = 0, z = 0] a_{j,l}, then O_s' gives (k, kc) =
  * (z ^ K(j,l), l ^ I(j, k)); R is controlled by A and sigma(j, k); the last
  * three maps only return A to 0. */
-__device__ __forceinline__ uint64_t map_t(const QwSimDev &d, const Row &r, uint64_t key)
+__device__ __forceinline__ uint64_t map_t(const QwSimDev &d, const Row &r, uint64_t key, uint32_t &slot)
 {
     const Regs x = decode_r(key, d.nb);
     const uint32_t w = qword(d, r, x.k);
+    slot = r.valid ? x.k : 0xffffffffu;
     Regs y;
     y.A = (r.jc == 0 && x.kc == 0) ? (w & 0xffffu) : 0u;
     y.k = x.kc ^ (w >> 16);
@@ -1186,6 +1207,8 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
     AmpT *zbuf = aQ + C;
     uint32_t *simg = reinterpret_cast<uint32_t *>(zbuf + d.s);
     int16_t *pbuf = reinterpret_cast<int16_t *>(simg + d.s);
+    typedef typename Amp<AmpT>::RotVal RotVal;
+    RotVal *sfg = reinterpret_cast<RotVal *>(base + walk_smem_head<AmpT>(d));
 
     const bool skip = *(volatile int32_t *)a.status != 0;
     if (!skip) { /* clear X_{t+2} for the step after this one */
@@ -1255,9 +1278,14 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
             continue;
         }
         r.simg = simg;
+        r.sfg = sfg;
         const int64_t want = ((int64_t)r.inst << 32) | (int64_t)r.j;
         if (r.valid && want != staged) { /* rows b1 = 0, 1 of one j come in a row */
-            for (int t = lane; t < d.s; t += 32) simg[t] = __ldg(d.img + r.img_base + (int64_t)r.j * d.s + t);
+            for (int t = lane; t < d.s; t += 32) {
+                const uint32_t w = __ldg(d.img + r.img_base + (int64_t)r.j * d.s + t);
+                simg[t] = w;
+                sfg[t] = Amp<AmpT>::rot_table(d, w & 0xffffu);
+            }
             staged = want;
         }
         const int64_t row0 = bcur * (int64_t)d.cap_row;
@@ -1349,6 +1377,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_tinit(QwSimDev d, QwBufDev buf, 
         Row r;
         if (!row_of(d, buf, b, r)) continue;
         r.simg = simg;
+        r.sfg = nullptr;
         for (int t = lane; t < d.s; t += 32)
             simg[t] = r.valid ? __ldg(d.img + r.img_base + (int64_t)r.j * d.s + t) : 0u;
         const double2 a = Amp<AmpT>::to_d(static_cast<const AmpT *>(buf.amp)[row0]);
