@@ -675,6 +675,17 @@ __host__ __device__ inline size_t walk_smem_per_warp(const QwSimDev &d)
  * only negated, and the zero-type groups are found by a predicate on the key.
  */
 
+/* sign flips as integer operations on the sign bit (keeps FP64 negations
+ * and selects off GB300's slow FP64 pipe) */
+__device__ __forceinline__ double flip_if(double x, bool neg)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ ((long long)neg << 63));
+}
+__device__ __forceinline__ float flip_if(float x, bool neg)
+{
+    return __int_as_float(__float_as_int(x) ^ ((int)neg << 31));
+}
+
 template <typename AmpT> struct Amp;
 
 /* complex128 path: FP64 arithmetic throughout */
@@ -689,13 +700,27 @@ template <> struct Amp<double2> {
     struct Sum {
         double x = 0.0, y = 0.0;
         __device__ void add(T a) { x += a.x; y += a.y; }
-        __device__ void reduce() { x = warp_sum(x); y = warp_sum(y); }
+        /* lanes 0..s-1 hold the values (s a power of two, <= 32 here) */
+        __device__ void reduce(int s)
+        {
+            if (s >= 32) {
+                x = warp_sum(x);
+                y = warp_sum(y);
+                return;
+            }
+            for (int o = s >> 1; o > 0; o >>= 1) {
+                x += __shfl_xor_sync(FULL, x, o);
+                y += __shfl_xor_sync(FULL, y, o);
+            }
+            x = __shfl_sync(FULL, x, 0);
+            y = __shfl_sync(FULL, y, 0);
+        }
         __device__ void scale_pow2(double f) { x *= f; y *= f; }
         __device__ T minus(T a) const { return make_double2(x - a.x, y - a.y); }
         __device__ double2 value() const { return make_double2(x, y); }
     };
     __device__ static T zero() { return make_double2(0.0, 0.0); }
-    __device__ static T neg(T a) { return make_double2(-a.x, -a.y); }
+    __device__ static T neg(T a) { return make_double2(flip_if(a.x, true), flip_if(a.y, true)); }
     __device__ static double2 to_d(T a) { return a; }
     __device__ static T from_d(double2 a) { return a; }
     /* |a|^2 > tau^2 exactly as the un-fused FP64 formula, decided from the
@@ -777,7 +802,7 @@ template <> struct Amp<float2> {
     struct Sum {
         DF x, y;
         __device__ void add(T a) { x.add(a.x); y.add(a.y); }
-        __device__ void reduce() { x.reduce(); y.reduce(); }
+        __device__ void reduce(int s) { (void)s; x.reduce(); y.reduce(); }
         __device__ void scale_pow2(double f)
         {
             const float g = (float)f; /* 2/s: a power of two, exact */
@@ -831,15 +856,14 @@ template <> struct Amp<float2> {
     __device__ static void rot(RotVal t, uint32_t A, bool dag, bool sneg, T a0, T a1, T &o0, T &o1);
 };
 
-/* multiply by 1 (real f) or by i*sigma (imaginary f), sigma = sneg ? -1 : 1 */
+/* multiply by 1 (real f) or by i*sigma (imaginary f), sigma = sneg ? -1 : 1:
+ * i sigma (x + i y) = -sigma y + i sigma x */
 template <typename T>
 __device__ __forceinline__ T rho(T a, bool imag, bool sneg)
 {
-    T r = a;
-    if (imag) {
-        r.x = sneg ? a.y : -a.y;
-        r.y = sneg ? -a.x : a.x;
-    }
+    T r;
+    r.x = imag ? flip_if(a.y, !sneg) : a.x;
+    r.y = imag ? flip_if(a.x, sneg) : a.y;
     return r;
 }
 
@@ -1066,7 +1090,7 @@ __device__ int reflect_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
         /* sum by u in a fixed order, whatever order the row's branches came in */
         __syncwarp();
         for (int t = lane; t < s; t += 32) sum.add(zbuf[t]);
-        sum.reduce();
+        sum.reduce(s);
         if (a.qls_readout && r.valid && lane == 0) {
             const double2 sv = sum.value();
             double2 acc = a.qls_y[r.j];
