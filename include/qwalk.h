@@ -235,6 +235,20 @@ int qw_state_size(qw_sim *sim, int32_t inst, int64_t *count);
 int qw_state_export(qw_sim *sim, int32_t inst, int32_t key_words, uint64_t *keys, double *amps,
                     int64_t cap, int64_t *count);
 
+/*
+ * Replace the whole state (every instance) by the count branches given in the
+ * packed layout of qw_state_export (key_words words per key, the instance
+ * field included) with amplitudes amps (2 doubles each): checkpoint / resume,
+ * or any state of the register space.  Keys must be distinct, name existing
+ * instances, and hold A = 0 (A is zero between walk steps).  The
+ * renormalisation target becomes the imported norm.
+ * Errors: QW_ERR_ARG (layout, duplicate key, A != 0, instance out of range),
+ * QW_ERR_CAPACITY (a row exceeds row_capacity or the garbage-row table),
+ * QW_ERR_CUDA.
+ */
+int qw_state_import(qw_sim *sim, int32_t key_words, const uint64_t *keys, const double *amps,
+                    int64_t count);
+
 /* nb, s, number of instances, and the total device bytes held (all nullable). */
 int qw_sim_info(const qw_sim *sim, int32_t *nb, int32_t *s, int32_t *num_instances,
                 int64_t *device_bytes);

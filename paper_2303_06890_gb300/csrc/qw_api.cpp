@@ -828,6 +828,14 @@ extern "C" int qw_state_size(qw_sim *sim, int32_t inst, int64_t *count)
     return QW_OK;
 }
 
+static uint64_t get_bits(const uint64_t *w, int pos, int width)
+{
+    uint64_t v = 0;
+    for (int b = 0; b < width; ++b)
+        if ((w[(pos + b) >> 6] >> ((pos + b) & 63)) & 1ull) v |= 1ull << b;
+    return v;
+}
+
 static void put_bits(uint64_t *w, int pos, uint64_t v, int width)
 {
     for (int b = 0; b < width; ++b)
@@ -910,5 +918,85 @@ extern "C" int qw_step_stats(qw_sim *sim, int64_t *out, int32_t len, int32_t res
     if (reset) QW_CUDA(sim, cudaMemsetAsync(sim->sc->stats, 0, sizeof h, sim->stream));
     QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
     for (int i = 0; i < len && i < QW_NSTAT; ++i) out[i] = (int64_t)h[i];
+    return QW_OK;
+}
+
+extern "C" int qw_state_import(qw_sim *sim, int32_t key_words, const uint64_t *keys, const double *amps,
+                               int64_t count)
+{
+    if (!sim) return QW_ERR_ARG;
+    const int nb = sim->d.nb;
+    if (key_words < 1 || key_words > 10 || key_words * 64 < 4 * nb + 34)
+        return fail(sim, QW_ERR_ARG, "key_words too small for the packed register layout");
+    if (count < 0 || (count > 0 && (!keys || !amps))) return fail(sim, QW_ERR_ARG, "bad arrays");
+    const size_t W = (size_t)key_words;
+    /* distinct keys */
+    std::vector<int64_t> order((size_t)count);
+    for (int64_t i = 0; i < count; ++i) order[(size_t)i] = i;
+    std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+        const uint64_t *a = keys + (size_t)x * W, *b = keys + (size_t)y * W;
+        for (size_t t = W; t-- > 0;)
+            if (a[t] != b[t]) return a[t] < b[t];
+        return false;
+    });
+    for (int64_t i = 1; i < count; ++i)
+        if (std::memcmp(keys + (size_t)order[(size_t)i] * W, keys + (size_t)order[(size_t)i - 1] * W, W * 8) == 0)
+            return fail(sim, QW_ERR_ARG, "qw_state_import: duplicate key");
+    std::vector<uint64_t> hrow((size_t)count), hloc((size_t)count);
+    std::vector<double2> hamp((size_t)count);
+    double norm2 = 0.0;
+    for (int64_t i = 0; i < count; ++i) {
+        const uint64_t *w = keys + (size_t)i * W;
+        int p = 0;
+        const uint64_t b2 = get_bits(w, p, 1); p += 1;
+        const uint64_t k = get_bits(w, p, nb); p += nb;
+        const uint64_t kc = get_bits(w, p, nb); p += nb;
+        const uint64_t b1 = get_bits(w, p, 1); p += 1;
+        const uint64_t j = get_bits(w, p, nb); p += nb;
+        const uint64_t jc = get_bits(w, p, nb); p += nb;
+        const uint64_t A = get_bits(w, p, 16); p += 16;
+        const uint64_t inst = get_bits(w, p, 16); p += 16;
+        for (int t = p; t < (int)W * 64; ++t)
+            if ((w[t >> 6] >> (t & 63)) & 1ull) return fail(sim, QW_ERR_ARG, "qw_state_import: bits above the layout");
+        if (A != 0) return fail(sim, QW_ERR_ARG, "qw_state_import: register A must be 0");
+        if ((int64_t)inst >= sim->d.ninst) return fail(sim, QW_ERR_ARG, "qw_state_import: instance out of range");
+        hrow[(size_t)i] = qw_rowkey((uint32_t)inst, (uint32_t)jc, (uint32_t)j, (uint32_t)b1);
+        hloc[(size_t)i] = b2 | (k << 1) | (kc << (1 + nb));
+        hamp[(size_t)i] = make_double2(amps[2 * i], amps[2 * i + 1]);
+        norm2 += amps[2 * i] * amps[2 * i] + amps[2 * i + 1] * amps[2 * i + 1];
+    }
+    for (int bi = 0; bi < 3; ++bi) {
+        QW_CUDA(sim, qw_launch_clear(sim->d, sim->buf[bi], 0, sim->d.total_buckets, 1, sim->stream));
+        sim->launches++;
+    }
+    Scalars z{};
+    z.scale[0] = z.scale[1] = 1.0;
+    z.renorm_target = norm2;
+    QW_CUDA(sim, cudaMemcpyAsync(sim->sc, &z, sizeof z, cudaMemcpyHostToDevice, sim->stream));
+    sim->scale_slot = sim->sync_slot = 0;
+    sim->cur = sim->sync_cur = 0;
+    sim->sync_done = 0;
+    drop_graphs(sim);
+    if (count > 0) {
+        uint64_t *drow = nullptr, *dloc = nullptr;
+        double2 *damp = nullptr;
+        QW_CUDA(sim, cudaMallocAsync((void **)&drow, (size_t)count * 8, sim->stream));
+        QW_CUDA(sim, cudaMallocAsync((void **)&dloc, (size_t)count * 8, sim->stream));
+        QW_CUDA(sim, cudaMallocAsync((void **)&damp, (size_t)count * 16, sim->stream));
+        QW_CUDA(sim, cudaMemcpyAsync(drow, hrow.data(), (size_t)count * 8, cudaMemcpyHostToDevice, sim->stream));
+        QW_CUDA(sim, cudaMemcpyAsync(dloc, hloc.data(), (size_t)count * 8, cudaMemcpyHostToDevice, sim->stream));
+        QW_CUDA(sim, cudaMemcpyAsync(damp, hamp.data(), (size_t)count * 16, cudaMemcpyHostToDevice, sim->stream));
+        QW_CUDA(sim, qw_launch_import(sim->d, sim->buf[sim->cur], drow, dloc, damp, count, sim->fp32,
+                                      &sim->sc->status, sim->stream));
+        sim->launches++;
+        QW_CUDA(sim, cudaFreeAsync(drow, sim->stream));
+        QW_CUDA(sim, cudaFreeAsync(dloc, sim->stream));
+        QW_CUDA(sim, cudaFreeAsync(damp, sim->stream));
+    }
+    int rc = check_status(sim, "qw_state_import");
+    if (rc != QW_OK) return rc;
+    sim->has_state = true;
+    sim->fresh_T = false;
+    for (auto &v : sim->init_norm2) v = 0.0;
     return QW_OK;
 }

@@ -109,6 +109,9 @@ cudaError_t qw_launch_init_b(const QwSimDev &d, const QwBufDev &buf, int inst, c
                              int n, int fp32, const double *scale, cudaStream_t st);
 cudaError_t qw_launch_tinit(const QwSimDev &d, const QwBufDev &buf, int64_t lo, int64_t hi, int fp32,
                             int32_t *status, int32_t *fallback, cudaStream_t st);
+cudaError_t qw_launch_import(const QwSimDev &d, const QwBufDev &buf, const uint64_t *rowkey,
+                             const uint64_t *local, const double2 *amp, int64_t count, int fp32,
+                             int32_t *status, cudaStream_t st);
 cudaError_t qw_launch_export(const QwSimDev &d, const QwBufDev &buf, int inst, int fp32,
                              const double *scale, uint64_t *rowkey, uint64_t *local, double2 *amp,
                              unsigned long long *counter, int64_t cap, cudaStream_t st);

@@ -1457,6 +1457,28 @@ __global__ void k_init_b(QwSimDev d, QwBufDev buf, int inst, const double2 *bvec
     buf.count[b] = 1;
 }
 
+/* Append imported branches (row key, local key, amplitude) to their rows. */
+template <typename AmpT>
+__global__ void k_import(QwSimDev d, QwBufDev buf, const uint64_t *rowkey, const uint64_t *local,
+                         const double2 *amp, int64_t count, int32_t *status)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const uint64_t rk = rowkey[i];
+    const uint32_t inst = (uint32_t)(rk >> 40), jc = (uint32_t)((rk >> 20) & 0xfffffu);
+    const uint32_t j = (uint32_t)((rk >> 1) & 0x7ffffu), b1 = (uint32_t)(rk & 1);
+    const int64_t b = bucket_of(d, buf, inst, jc, j, b1, status);
+    if (b < 0) return;
+    const int pos = atomicAdd(buf.count + b, 1);
+    if (pos >= d.cap_row) {
+        atomicOr(status, QW_ST_ROW_OVERFLOW);
+        return;
+    }
+    const int64_t slot = b * (int64_t)d.cap_row + pos;
+    buf.key[slot] = local[i];
+    store_amp<AmpT>(buf.amp, slot, amp[i]);
+}
+
 /* Every branch of instance inst (-1: all) to flat (row key, local key, amp). */
 template <typename AmpT>
 __global__ void k_export(QwSimDev d, QwBufDev buf, int inst, const double *scale, uint64_t *rowkey,
@@ -1782,5 +1804,16 @@ cudaError_t qw_launch_tinit(const QwSimDev &d, const QwBufDev &buf, int64_t lo, 
         cudaFuncSetAttribute(k_tinit<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_tinit<double2><<<grid, WARPS * 32, sm, st>>>(d, buf, lo, hi, status, fallback);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t qw_launch_import(const QwSimDev &d, const QwBufDev &buf, const uint64_t *rowkey,
+                             const uint64_t *local, const double2 *amp, int64_t count, int fp32,
+                             int32_t *status, cudaStream_t st)
+{
+    const int64_t grid = (count + 255) / 256;
+    if (grid < 1) return cudaSuccess;
+    if (fp32) k_import<float2><<<(unsigned)grid, 256, 0, st>>>(d, buf, rowkey, local, amp, count, status);
+    else k_import<double2><<<(unsigned)grid, 256, 0, st>>>(d, buf, rowkey, local, amp, count, status);
     return cudaGetLastError();
 }

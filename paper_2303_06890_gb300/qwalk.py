@@ -29,7 +29,7 @@ EXPORTED = ("qw_sim_opts_default", "qw_sim_create", "qw_state_init", "qw_apply_w
             "qw_enqueue_walk_steps", "qw_sync",
             "qw_cks_coefficients", "qw_apply_qls", "qw_measure_register", "qw_state_size",
             "qw_state_export", "qw_sim_info", "qw_step_stats", "qw_launch_count", "qw_sim_destroy",
-            "qw_last_error", "qw_measure_register_noalloc", "qw_autotune")
+            "qw_last_error", "qw_measure_register_noalloc", "qw_autotune", "qw_state_import")
 MEASURE_NOALLOC_MAX_LEN = 65536
 
 
@@ -87,6 +87,7 @@ def load(build_if_missing: bool = True):
     lib.qw_sim_info.argtypes = [P, P, P, P, P]
     lib.qw_step_stats.argtypes = [P, P, i32, i32]
     lib.qw_autotune.argtypes = [P, i32, P, P]
+    lib.qw_state_import.argtypes = [P, i32, P, P, i64]
     lib.qw_launch_count.argtypes = [P]
     lib.qw_launch_count.restype = i64
     lib.qw_sim_destroy.argtypes = [P]
@@ -96,7 +97,7 @@ def load(build_if_missing: bool = True):
                  "qw_sync", "qw_cks_coefficients",
                  "qw_apply_qls", "qw_measure_register", "qw_measure_register_noalloc",
                  "qw_state_size", "qw_state_export",
-                 "qw_sim_info", "qw_step_stats", "qw_autotune", "qw_sim_destroy"):
+                 "qw_sim_info", "qw_step_stats", "qw_autotune", "qw_state_import", "qw_sim_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -255,6 +256,28 @@ class Sim:
         out = np.zeros(8, dtype=np.int64)
         self._check(load().qw_step_stats(self._h, _p(out), 8, int(bool(reset))))
         return dict(zip(self.STAT_NAMES, (int(v) for v in out[:7])))
+
+    def state_import(self, keys: np.ndarray, amps: np.ndarray) -> None:
+        """qw_state_import: replace the state by packed keys [M, W] and amplitudes."""
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        a = np.ascontiguousarray(np.stack([np.real(amps), np.imag(amps)], axis=1), dtype=np.float64)
+        self._check(load().qw_state_import(self._h, keys.shape[1], _p(keys), _p(a), keys.shape[0]))
+
+    def pack(self, regs: np.ndarray, key_words: int = 2) -> np.ndarray:
+        """[M, 8] (jc, j, b1, kc, k, b2, A, inst) -> packed keys [M, key_words]."""
+        nb = self.nb
+        widths = [("b2", 1), ("k", nb), ("kc", nb), ("b1", 1), ("j", nb), ("jc", nb), ("A", 16),
+                  ("inst", 16)]
+        order = {"jc": 0, "j": 1, "b1": 2, "kc": 3, "k": 4, "b2": 5, "A": 6, "inst": 7}
+        out = np.zeros((len(regs), key_words), dtype=np.uint64)
+        for i, r in enumerate(regs):
+            v, pos = 0, 0
+            for name, w in widths:
+                v |= int(r[order[name]]) << pos
+                pos += w
+            for t in range(key_words):
+                out[i, t] = (v >> (64 * t)) & ((1 << 64) - 1)
+        return out
 
     def launch_count(self) -> int:
         return int(load().qw_launch_count(self._h))

@@ -376,3 +376,50 @@ def test_batched_256_instances_full_size(precision):
         for _ in range(50):
             o.apply("W")
         compare(gpu_state(sim, inst=i), oracle_state(o), TOL64)
+
+
+def test_checkpoint_round_trip():
+    """qw_state_export then qw_state_import reproduces the state, and the
+    resumed walk equals the uninterrupted one."""
+    w = wl.walk_n1024()
+    a = _sim(w)
+    a.state_init(w.b)
+    a.apply_walk_step(5)
+    keys, amps = a.state_export()
+    b = _sim(w)
+    b.state_import(keys, amps)
+    k2, a2 = b.state_export()
+    assert np.array_equal(keys, k2) and np.array_equal(amps, a2)
+    a.apply_walk_step(3)
+    b.apply_walk_step(3)
+    compare(gpu_state(b), gpu_state(a), 0.0)
+
+
+@pytest.mark.parametrize("fuse,variant", [(True, 0), (True, 1), (False, 0)])
+def test_garbage_subspace_states_match_oracle(fuse, variant):
+    """Random states over the whole register space -- rows with jc != 0 (the
+    garbage-row table), rows j >= N (N = 12, so the all-zero QRAM list), kc != 0
+    and k >= s (QRAM reads outside the row) -- walked by the GPU and by the
+    oracle from the same imported state."""
+    w = wl.small_random(12, 4, 17)
+    rng = np.random.default_rng(99)
+    sim = _sim(w, fuse_reflection=fuse, walk_variant=variant, row_capacity=96, warp_capacity=128)
+    nb = sim.nb
+    keys = set()
+    while len(keys) < 400:
+        keys.add((int(rng.integers(0, 4)), int(rng.integers(0, 1 << nb)), int(rng.integers(0, 2)),
+                  int(rng.integers(0, 4)), int(rng.integers(0, 1 << nb)), int(rng.integers(0, 2))))
+    regs = np.array(sorted(keys), dtype=np.uint64)
+    amps = rng.standard_normal(len(regs)) + 1j * rng.standard_normal(len(regs))
+    amps /= np.linalg.norm(amps)
+    assert (regs[:, 0] != 0).sum() > 100 and (regs[:, 1] >= w.n).sum() > 50
+    full = np.zeros((len(regs), 8), dtype=np.uint64)
+    full[:, :6] = regs
+    sim.state_import(sim.pack(full), amps)
+    o = oracle.Oracle(w.matrix, w.s)
+    o.set_state(regs, amps)
+    compare(gpu_state(sim), oracle_state(o), 0.0)
+    for _ in range(4):
+        sim.apply_walk_step(1)
+        o.apply("W")
+        compare(gpu_state(sim), oracle_state(o), TOL64)
