@@ -73,8 +73,11 @@ def kernel_hash() -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
+VARIANTS = ("rows", "rows, pipelined", "segments", "segments, pipelined")
+
+
 def profiled_traffic(precision: str):
-    """DRAM bytes per launch of k_step from the committed ncu summary, or None
+    """DRAM bytes per launch of k_walk from the committed ncu summary, or None
     when the kernel source changed since the capture."""
     try:
         text = open(PROFILE).read()
@@ -207,7 +210,7 @@ def run_ours(args, rank, world, local_rank):
     # --- the benchmarked path: complex64 amplitudes, FP64 merge/norm/renorm ---
     sim = qwalk.Sim(w.matrix, s_pad=w.s, precision=qwalk.QW_FP32_AMP)
     sim.state_init(w.b, apply_T=True)
-    variant, tune_us = sim.autotune(max(2, args.warmup // 2))  # warm-up steps, both variants
+    variant, tune_us = sim.autotune(max(2, args.warmup // 2))  # warm-up steps, all variants
     sim.apply_walk_step(args.warmup)
     sim.step_stats(reset=True)
     launches0 = sim.launch_count()
@@ -299,7 +302,7 @@ def run_ours(args, rank, world, local_rank):
         "fp32_speedup_vs_fp64": value / fp64["value"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": f"k_walk<float2, {'pipelined' if variant else 'row-at-a-time'}>",
+                     "kernel": f"k_walk<float2, {VARIANTS[variant]}>",
                      "autotune_us_per_step": tune_us,
                      "algorithmic_bytes_per_launch": b_alg,
                      "state_bytes_per_launch": b_min,

@@ -77,12 +77,15 @@ typedef struct {
                                 interference op; 0 = 1e-13 (FP64), 2^-24 (FP32_AMP) */
     int32_t row_capacity;    /* branches per (jc, j, b1) row between steps; 0 = auto (4 s) */
     int32_t warp_capacity;   /* branches one warp holds on chip while it runs a row
-                                through a step; 0 = auto */
+                                (or a segment of two rows) through a step; 0 = auto
+                                (2 row_capacity rounded up to a power of two, at
+                                least 64, for fuse_reflection = 1) */
     int32_t renorm;          /* -1 = default (on for FP32_AMP, off for FP64) */
     void *stream;            /* cudaStream_t to issue on; NULL = the default stream */
-    int32_t walk_variant;    /* step kernel with fuse_reflection = 1: 0 = one row at a
-                                time (default), 1 = software-pipelined row loop; see
-                                qw_autotune */
+    int32_t walk_variant;    /* step kernel with fuse_reflection = 1 (see qw_autotune):
+                                0 = one row at a time (default), 1 = rows with a
+                                software-pipelined loop, 2 = the two rows of a j as one
+                                segment, 3 = segments, software-pipelined */
     int32_t graphs;          /* 1 (default): runs of >= 6 walk steps are issued as replays
                                 of a captured 6-step CUDA graph; 0: one launch per step */
 } qw_sim_opts;
@@ -148,12 +151,14 @@ int qw_sync(qw_sim *sim);
 
 /*
  * Autotuner of the fused step kernel: runs steps_per_candidate walk steps with
- * each variant of the kernel (0: rows processed one at a time, 4 blocks per
- * SM; 1: row loop software-pipelined, 3 blocks per SM), times them with CUDA
- * events on the simulator's stream, and keeps the faster one for all later
- * steps.  The state advances by 2 * steps_per_candidate walk steps (the
- * variants give identical results).  *choice (nullable) receives the variant,
- * *us_per_step (nullable, 2 doubles) the measured times.  Synchronises.
+ * each of the four variants of walk_variant (rows or segments of two rows,
+ * plain or software-pipelined), times them with CUDA events on the
+ * simulator's stream, and keeps the fastest for all later steps.  Segments
+ * are tried only when warp_capacity >= 2 row_capacity (true by default);
+ * otherwise variants 2, 3 are skipped and reported as 0 us.  The state
+ * advances by steps_per_candidate walk steps per variant tried (the variants
+ * give the same results).  *choice (nullable) receives the variant,
+ * *us_per_step (nullable, 4 doubles) the measured times.  Synchronises.
  * Has no effect with fuse_reflection = 0.  Errors: QW_ERR_ARG, QW_ERR_STATE,
  * QW_ERR_CAPACITY, QW_ERR_CUDA.
  */
@@ -255,7 +260,8 @@ int qw_sim_info(const qw_sim *sim, int32_t *nb, int32_t *s, int32_t *num_instanc
 
 /*
  * Branch counters of the walk steps run since creation or the last reset,
- * summed over steps: out[0] rows processed, out[1] branches entering the
+ * summed over steps: out[0] row items processed (a row, or the two rows of a j
+ * run as one segment), out[1] branches entering the
  * steps (input of R^dag), out[2] after R^dag, out[3] after the first H (only
  * with fuse_reflection = 0), out[4] after H P H, out[5] after R (branches
  * written), out[6] steps counted.  Writes min(len, 8) values; reset != 0

@@ -258,8 +258,14 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     cudaGetDevice(&sim->device);
     sim->fp32 = o.precision == QW_FP32_AMP;
     sim->renorm = o.renorm < 0 ? sim->fp32 : (o.renorm != 0);
-    sim->mode = o.fuse_reflection ? (o.walk_variant == 1 ? QW_MODE_WALK_FUSED_PF : QW_MODE_WALK_FUSED)
-                                  : QW_MODE_WALK_LITERAL;
+    static const int kVariantMode[4] = {QW_MODE_WALK_FUSED, QW_MODE_WALK_FUSED_PF, QW_MODE_WALK_SEG,
+                                        QW_MODE_WALK_SEG_PF};
+    if (o.walk_variant < 0 || o.walk_variant > 3) {
+        delete sim;
+        g_create_error = "qw_sim_create: walk_variant must be 0..3";
+        return QW_ERR_ARG;
+    }
+    sim->mode = o.fuse_reflection ? kVariantMode[o.walk_variant] : QW_MODE_WALK_LITERAL;
     sim->stream = (cudaStream_t)o.stream;
 
     QwSimDev &d = sim->d;
@@ -281,7 +287,7 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     d.cap_row = o.row_capacity > 0 ? o.row_capacity : std::max(8, 4 * s);
     int64_t wc = o.warp_capacity;
     if (wc <= 0) {
-        wc = sim->mode == QW_MODE_WALK_FUSED ? next_pow2(std::max<int64_t>(32, 4 * s))
+        wc = sim->mode != QW_MODE_WALK_LITERAL ? next_pow2(std::max<int64_t>(64, 2 * (int64_t)d.cap_row))
                                              : std::min<int64_t>(512, next_pow2(std::max<int64_t>(32, 4 * s * s)));
     }
     wc = std::max<int64_t>(wc, s);
@@ -359,8 +365,8 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     sim->grid_t = qw_step_grid(d, sim->fp32, QW_MODE_T);
     int gmax = std::max(sim->grid_walk, sim->grid_t);
     if (sim->mode != QW_MODE_WALK_LITERAL) {
-        gmax = std::max(gmax, qw_step_grid(d, sim->fp32, QW_MODE_WALK_FUSED));
-        gmax = std::max(gmax, qw_step_grid(d, sim->fp32, QW_MODE_WALK_FUSED_PF));
+        for (int m : {QW_MODE_WALK_FUSED, QW_MODE_WALK_FUSED_PF, QW_MODE_WALK_SEG, QW_MODE_WALK_SEG_PF})
+            gmax = std::max(gmax, qw_step_grid(d, sim->fp32, m));
     }
     QW_TRY(dalloc(sim, &sim->partials, (size_t)gmax));
     QW_TRY(dalloc(sim, &sim->sc, 1));
@@ -654,15 +660,17 @@ extern "C" int qw_autotune(qw_sim *sim, int32_t steps, int32_t *choice, double *
         if (choice) *choice = -1;
         return QW_OK;
     }
-    const int modes[2] = {QW_MODE_WALK_FUSED, QW_MODE_WALK_FUSED_PF};
-    double us[2] = {0.0, 0.0};
+    const int modes[4] = {QW_MODE_WALK_FUSED, QW_MODE_WALK_FUSED_PF, QW_MODE_WALK_SEG, QW_MODE_WALK_SEG_PF};
+    double us[4] = {0.0, 0.0, 0.0, 0.0};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     QW_CUDA(sim, cudaEventCreate(&e0));
     QW_CUDA(sim, cudaEventCreate(&e1));
     int rc = QW_OK;
     const int graphs = sim->opts.graphs;
     sim->opts.graphs = 0; /* time the kernels themselves */
-    for (int v = 0; v < 2 && rc == QW_OK; ++v) {
+    /* a segment holds two rows on chip: only tried when the warp buffer fits them */
+    const int nvar = sim->d.warp_cap >= 2 * sim->d.cap_row ? 4 : 2;
+    for (int v = 0; v < nvar && rc == QW_OK; ++v) {
         sim->mode = modes[v];
         sim->grid_walk = qw_step_grid(sim->d, sim->fp32, sim->mode);
         cudaEventRecord(e0, sim->stream);
@@ -675,15 +683,15 @@ extern "C" int qw_autotune(qw_sim *sim, int32_t steps, int32_t *choice, double *
     sim->opts.graphs = graphs;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    const int best = (us[1] > 0.0 && us[1] < us[0]) ? 1 : 0;
+    int best = 0;
+    for (int v = 1; v < nvar; ++v)
+        if (us[v] > 0.0 && us[v] < us[best]) best = v;
     sim->mode = modes[best];
     sim->grid_walk = qw_step_grid(sim->d, sim->fp32, sim->mode);
     drop_graphs(sim);
     if (choice) *choice = best;
-    if (us_per_step) {
-        us_per_step[0] = us[0];
-        us_per_step[1] = us[1];
-    }
+    if (us_per_step)
+        for (int v = 0; v < 4; ++v) us_per_step[v] = us[v];
     return rc;
 }
 

@@ -50,6 +50,8 @@
 #define QW_MODE_WALK_LITERAL 1 /* T~^dag, H, P, H, T~, S */
 #define QW_MODE_T 2            /* T~ only, in place on a bucket range */
 #define QW_MODE_WALK_FUSED_PF 3 /* fused step, row loop software-pipelined */
+#define QW_MODE_WALK_SEG 4      /* fused step, both rows of a j as one segment */
+#define QW_MODE_WALK_SEG_PF 5   /* segments, software-pipelined */
 
 struct QwSimDev {
     int nb, s, L, ninst;

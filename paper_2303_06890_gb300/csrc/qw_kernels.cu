@@ -25,6 +25,16 @@
 #include "../../include/qwalk.h"
 #include "qw_internal.h"
 
+/* Rotation controls carried in the key between a map and its rotation: the
+ * element register A (its field of the R layout) and bit 63 = [j > k], the
+ * sign sigma = -1 of the rotation for a negative element (sigma = +1 when
+ * j <= k).  Both members of a b2-pair carry the same values. */
+#define QW_SNEG_BIT 63
+/* In the fused kernel a warp runs the rows (jc, j, b1 = 0) and (jc, j, b1 = 1)
+ * together -- they read the same QRAM row and nothing before S reads or
+ * changes b1 -- with b1 held in this bit of each branch's key. */
+#define QW_B1_BIT 52
+
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -901,24 +911,36 @@ __device__ void Amp<float2>::rot(RotVal t, uint32_t A, bool dag, bool sneg, T a0
     }
 }
 
-/* Load the row and group it: b2-pairs next to each other, b2 = 0 first.  A
- * row that fits one warp is loaded straight into registers and paired by a
- * warp match on key >> 1; a longer row goes through shared memory and is
- * sorted by key (rank of each key among the row's). */
+/* Load a segment -- the n0 branches of bucket A (b1 = tagA) and the n1 of
+ * bucket B (b1 = 1) -- and group it: b2-pairs next to each other, b2 = 0
+ * first.  A segment that fits one warp goes straight into registers and is
+ * paired by a warp match on key >> 1; a longer one goes through shared memory
+ * and is sorted by key (rank of each key among the segment's). */
 template <typename AmpT>
-__device__ void load_pairs(const uint64_t *gkey, const AmpT *gamp, int n, bool rescale,
-                           const typename Amp<AmpT>::Scale &scale, uint64_t *kd, AmpT *ad,
-                           uint64_t *ktmp, AmpT *atmp, bool have, uint64_t hk, AmpT ha)
+__device__ void load_seg(const QwBufDev &in, int64_t bA, int n0, uint64_t tagA, int64_t bB, int n1,
+                         int cap_row, bool rescale, const typename Amp<AmpT>::Scale &scale,
+                         uint64_t *kd, AmpT *ad, uint64_t *ktmp, AmpT *atmp, bool have, uint64_t hk, AmpT ha)
 {
     const int lane = lane_id();
+    const int n = n0 + n1;
+    const AmpT *amp = static_cast<const AmpT *>(in.amp);
+    auto fetch = [&](int i, uint64_t &k, AmpT &a) {
+        const int64_t slot = (i < n0) ? bA * (int64_t)cap_row + i : bB * (int64_t)cap_row + (i - n0);
+        k = in.key[slot] | ((i < n0) ? tagA : (1ull << QW_B1_BIT));
+        a = amp[slot];
+    };
     if (n <= 32) {
         const bool valid = lane < n;
         /* inactive lanes get keys whose k >> 1 are distinct and above every real key */
         uint64_t k = ~0ull - 2ull * (uint64_t)lane;
         AmpT a = Amp<AmpT>::zero();
         if (valid) {
-            k = have ? hk : gkey[lane];
-            a = have ? ha : gamp[lane];
+            if (have) {
+                k = hk;
+                a = ha;
+            } else {
+                fetch(lane, k, a);
+            }
             if (rescale) a = scale.apply(a);
         }
         const unsigned m = __match_any_sync(FULL, k >> 1);
@@ -944,9 +966,11 @@ __device__ void load_pairs(const uint64_t *gkey, const AmpT *gamp, int n, bool r
         return;
     }
     for (int i = lane; i < n; i += 32) {
-        ktmp[i] = gkey[i];
-        AmpT v = gamp[i];
+        uint64_t k;
+        AmpT v;
+        fetch(i, k, v);
         if (rescale) v = scale.apply(v);
+        ktmp[i] = k;
         atmp[i] = v;
     }
     __syncwarp();
@@ -960,11 +984,6 @@ __device__ void load_pairs(const uint64_t *gkey, const AmpT *gamp, int n, bool r
     __syncwarp();
 }
 
-/* Rotation controls carried in the key between a map and its rotation: the
- * element register A (its field of the R layout) and bit 63 = [j > k], the
- * sign sigma = -1 of the rotation for a negative element (sigma = +1 when
- * j <= k).  Both members of a b2-pair carry the same values. */
-#define QW_SNEG_BIT 63
 
 __device__ __forceinline__ uint64_t map_tdag(const QwSimDev &d, const Row &r, uint64_t key,
                                             int32_t *status, uint32_t &slot);
@@ -1001,8 +1020,9 @@ __device__ int map_rot_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
                 a1 = as[i];
             }
             uint32_t slot;
-            const uint64_t mk = (WHICH == 0) ? map_tdag(d, r, k & ~1ull, status, slot)
-                                             : map_t(d, r, k & ~1ull, slot);
+            const uint64_t b1bit = k & (1ull << QW_B1_BIT);
+            const uint64_t mk = (WHICH == 0) ? map_tdag(d, r, k & ~(1ull | b1bit), status, slot)
+                                             : map_t(d, r, k & ~(1ull | b1bit), slot);
             const uint32_t A = (uint32_t)(mk >> ash) & 0xffffu;
             /* A is 0 or the value of slot `slot` of row j: staged rotation
                values for a slot of this row, the per-code table otherwise */
@@ -1013,7 +1033,7 @@ __device__ int map_rot_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
             Amp<AmpT>::rot(t, A, WHICH == 0, (mk >> QW_SNEG_BIT) != 0, a0, a1, o0, o1);
             c0 = Amp<AmpT>::keep(d, o0);
             c1 = Amp<AmpT>::keep(d, o1);
-            kb = mk & keep_mask;
+            kb = (mk & keep_mask) | b1bit;
         }
         int total;
         int pos = out + warp_compact2(c0, c1, total);
@@ -1052,8 +1072,9 @@ __device__ int reflect_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
 {
     const int lane = lane_id();
     const int s = d.s;
-    const uint64_t zm = ((1ull << (1 + 2 * d.nb)) - 1) & ~((1ull << (d.L + 1)) - 1); /* k_high|kc */
-    const bool rowzero = (r.jc == 0 && r.b1 == 0);
+    const uint64_t zm = (((1ull << (1 + 2 * d.nb)) - 1) & ~((1ull << (d.L + 1)) - 1)) |
+                        (1ull << QW_B1_BIT); /* k_high | kc | b1 */
+    const bool rowzero = (r.jc == 0);
     if (rowzero) {
         for (int t = lane; t < s; t += 32) {
             zbuf[t] = Amp<AmpT>::zero();
@@ -1181,11 +1202,12 @@ __device__ void emit_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, 
     Regs y;
     y.kc = r.jc;
     y.k = r.j;
-    y.b2 = r.b1;
+    y.b2 = 0;
     y.A = 0;
-    const uint64_t local = encode_r(y, d.nb);
+    const uint64_t local0 = encode_r(y, d.nb);
     for (int i = lane_id(); i < n; i += 32) {
         const Regs x = decode_r(ks[i], d.nb);
+        const uint64_t local = local0 | ((ks[i] >> QW_B1_BIT) & 1ull); /* new b2 = old b1 */
         int64_t b;
         if (x.kc == 0) {
             b = blo + (((int64_t)x.k << 1) | (int64_t)x.b2);
@@ -1209,11 +1231,13 @@ __device__ void emit_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, 
     }
 }
 
-/* One walk step.  PF = false: 4 blocks per SM, each row loaded when its turn
- * comes.  PF = true: 3 blocks per SM (more registers), the row loop software-
- * pipelined -- counts read two rows ahead, the next row's keys and amplitudes
- * (first 32) loaded into registers while the current row is processed. */
-template <typename AmpT, bool PF>
+/* One walk step.  SEG = false: the two rows (jc = 0, j, b1 = 0 / 1) of a j
+ * are processed one after the other by the same warp; SEG = true: together,
+ * as one segment.  PF = false: 4 blocks per SM, each item loaded when its
+ * turn comes; PF = true: 3 blocks per SM (more registers), the item loop
+ * software-pipelined -- the next item's counts read at the start of the
+ * current one, its first 32 branches loaded while the current one runs. */
+template <typename AmpT, bool PF, bool SEG>
 __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwBufDev in, QwBufDev out,
                                                                  QwBufDev clr, QwStepArgs a)
 {
@@ -1247,56 +1271,77 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
     typename Amp<AmpT>::Norm nrm;
     unsigned long long st_rows = 0, st_in = 0, st_rdag = 0, st_hph = 0, st_out = 0;
 
-    /* Static balanced schedule: a warp takes both rows (b1 = 0 and 1) of a j
-       as one unit -- the b1 = 0 row is about twice the b1 = 1 row and holds
-       the zero-type reflection, so a plain stride over buckets (an even
-       number of warps) would hand half the warps only heavy rows -- and
-       strides over units; spill buckets are one unit each.  PF: the next
-       bucket's count and entries are read ahead. */
+    /* Units: a dense unit u holds the rows (jc = 0, j) with b1 = 0 and 1
+       (buckets 2u and 2u + 1); a garbage-row bucket (jc != 0) is a unit of
+       its own.  Warps stride over units (a b1 = 0 row is about twice a b1 = 1
+       row, so keeping both rows of a j on one warp balances the warps).  An
+       item is what one pass of the row pipeline runs: a whole dense unit
+       (SEG) or one of its rows. */
     const int64_t nwarps = (int64_t)gridDim.x * WARPS;
     const int64_t d2 = d.dense_buckets >> 1;
-    auto first_of = [&](int64_t u) -> int64_t { return u < d2 ? 2 * u : d.dense_buckets + (u - d2); };
-    auto next_of = [&](int64_t bb) -> int64_t {
-        int64_t u;
-        if (bb < d.dense_buckets) {
-            if ((bb & 1) == 0) return bb + 1;
-            u = (bb >> 1) + nwarps;
-        } else {
-            u = d2 + (bb - d.dense_buckets) + nwarps;
-        }
-        return first_of(u);
+    const int64_t units = skip ? 0 : d2 + d.spill_slots;
+    struct Item {
+        int64_t bA, bB;
+        int n0, n1;
+        uint64_t tagA;
+        bool valid;
     };
-    int64_t b = first_of((int64_t)blockIdx.x * WARPS + warp);
-    if (bhi == 0) b = bhi;
-    int n_nxt = 0;
+    auto item_of = [&](int64_t uu, int part, Item &it) {
+        it.valid = uu < units;
+        it.n0 = it.n1 = 0;
+        it.tagA = 0;
+        it.bB = -1;
+        if (!it.valid) return;
+        if (uu < d2) {
+            if (SEG) {
+                it.bA = 2 * uu;
+                it.bB = it.bA + 1;
+                it.n1 = min(in.count[it.bB], d.cap_row);
+            } else {
+                it.bA = 2 * uu + part;
+                it.tagA = (uint64_t)part << QW_B1_BIT;
+            }
+            it.n0 = min(in.count[it.bA], d.cap_row);
+        } else {
+            it.bA = d.dense_buckets + (uu - d2);
+            it.n0 = min(in.count[it.bA], d.cap_row);
+            if (it.n0 > 0) it.tagA = (uint64_t)(in.spill[uu - d2] & 1ull) << QW_B1_BIT;
+        }
+    };
+    auto advance = [&](int64_t &uu, int &part) {
+        if (!SEG && uu < d2 && part == 0) {
+            part = 1;
+        } else {
+            part = 0;
+            uu += nwarps;
+        }
+    };
+    int64_t u = (int64_t)blockIdx.x * WARPS + warp;
+    int part = 0;
+    Item cur, nxt;
+    item_of(u, part, cur);
     bool have = false;
     uint64_t pk = 0;
     AmpT pa = Amp<AmpT>::zero();
-    int64_t bn = bhi;
-    if (PF && b < bhi) n_nxt = in.count[b];
     int64_t staged = -1; /* (inst, j) of the QRAM row held in simg */
-    while (b < bhi) {
-        int n;
-        bool have_cur = false;
-        uint64_t hk = 0;
-        AmpT ha = Amp<AmpT>::zero();
-        bn = next_of(b);
-        if (PF) {
-            n = n_nxt;
-            have_cur = have;
-            hk = pk;
-            ha = pa;
-            n_nxt = (bn < bhi) ? in.count[bn] : 0;
-            have = false;
-        } else {
-            n = in.count[b];
-        }
-        const int64_t bcur = b;
-        b = bn;
+    while (cur.valid) {
+        int64_t un = u;
+        int pn = part;
+        advance(un, pn);
+        const bool have_cur = have;
+        const uint64_t hk = pk;
+        const AmpT ha = pa;
+        have = false;
+        if (PF) item_of(un, pn, nxt);
+        const Item it = cur;
+        u = un;
+        part = pn;
+        if (!PF) item_of(u, part, cur);
+        else cur = nxt;
+        int n = it.n0 + it.n1;
         if (n <= 0) continue;
-        if (n > d.cap_row) n = d.cap_row;
         Row r;
-        if (!row_of(d, in, bcur, r)) continue;
+        if (!row_of(d, in, it.bA, r)) continue;
         if (n > C) {
             if (lane == 0) atomicOr(a.status, QW_ST_WARP_OVERFLOW);
             continue;
@@ -1304,7 +1349,7 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
         r.simg = simg;
         r.sfg = sfg;
         const int64_t want = ((int64_t)r.inst << 32) | (int64_t)r.j;
-        if (r.valid && want != staged) { /* rows b1 = 0, 1 of one j come in a row */
+        if (r.valid && want != staged) {
             for (int t = lane; t < d.s; t += 32) {
                 const uint32_t w = __ldg(d.img + r.img_base + (int64_t)r.j * d.s + t);
                 simg[t] = w;
@@ -1312,17 +1357,18 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
             }
             staged = want;
         }
-        const int64_t row0 = bcur * (int64_t)d.cap_row;
         st_rows++;
         st_in += n;
-        load_pairs<AmpT>(in.key + row0, static_cast<const AmpT *>(in.amp) + row0, n, rescale, scale,
-                         kP, aP, kQ, aQ, have_cur, hk, ha);
-        if (PF) { /* the next row's entries, while this row is processed */
-            const int mn = min(n_nxt, d.cap_row);
-            have = bn < bhi && mn > 0 && mn <= 32;
-            if (have && lane < mn) {
-                const int64_t slot = bn * (int64_t)d.cap_row + lane;
-                pk = in.key[slot];
+        load_seg<AmpT>(in, it.bA, it.n0, it.tagA, it.bB, it.n1, d.cap_row, rescale, scale, kP, aP, kQ, aQ,
+                       have_cur, hk, ha);
+        if (PF && cur.valid) { /* the next item's branches, while this one is processed */
+            const int nn = cur.n0 + cur.n1;
+            have = nn > 0 && nn <= 32;
+            if (have && lane < nn) {
+                const bool fromA = lane < cur.n0;
+                const int64_t slot = fromA ? cur.bA * (int64_t)d.cap_row + lane
+                                           : cur.bB * (int64_t)d.cap_row + (lane - cur.n0);
+                pk = in.key[slot] | (fromA ? cur.tagA : (1ull << QW_B1_BIT));
                 pa = static_cast<const AmpT *>(in.amp)[slot];
             }
         }
@@ -1584,13 +1630,13 @@ template <typename AmpT, int MODE> size_t step_smem(const QwSimDev &d)
                             (((size_t)d.s * sizeof(uint32_t) + 15) & ~(size_t)15));
 }
 
-template <typename AmpT, bool PF>
+template <typename AmpT, bool PF, bool SEG>
 int walk_grid_t(const QwSimDev &d)
 {
     const size_t sm = (size_t)WARPS * walk_smem_per_warp<AmpT>(d);
-    cudaFuncSetAttribute(k_walk<AmpT, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_walk<AmpT, PF, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<AmpT, PF>, WARPS * 32, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<AmpT, PF, SEG>, WARPS * 32, sm);
     if (per_sm < 1) per_sm = 1;
     int64_t want = (d.total_buckets + WARPS - 1) / WARPS;
     int64_t g = (int64_t)per_sm * qw_sm_count();
@@ -1598,12 +1644,12 @@ int walk_grid_t(const QwSimDev &d)
     return (int)(g < 1 ? 1 : g);
 }
 
-template <typename AmpT, bool PF>
+template <typename AmpT, bool PF, bool SEG>
 cudaError_t launch_walk_t(const QwSimDev &d, const QwBufDev &in, const QwBufDev &out,
                           const QwBufDev &clr, const QwStepArgs &a, int grid, cudaStream_t st)
 {
     const size_t sm = (size_t)WARPS * walk_smem_per_warp<AmpT>(d);
-    k_walk<AmpT, PF><<<grid, WARPS * 32, sm, st>>>(d, in, out, clr, a);
+    k_walk<AmpT, PF, SEG><<<grid, WARPS * 32, sm, st>>>(d, in, out, clr, a);
     return cudaGetLastError();
 }
 
@@ -1647,9 +1693,13 @@ int qw_sm_count(void)
 int qw_step_grid(const QwSimDev &d, int fp32, int mode)
 {
     if (mode == QW_MODE_WALK_FUSED)
-        return fp32 ? walk_grid_t<float2, false>(d) : walk_grid_t<double2, false>(d);
+        return fp32 ? walk_grid_t<float2, false, false>(d) : walk_grid_t<double2, false, false>(d);
     if (mode == QW_MODE_WALK_FUSED_PF)
-        return fp32 ? walk_grid_t<float2, true>(d) : walk_grid_t<double2, true>(d);
+        return fp32 ? walk_grid_t<float2, true, false>(d) : walk_grid_t<double2, true, false>(d);
+    if (mode == QW_MODE_WALK_SEG)
+        return fp32 ? walk_grid_t<float2, false, true>(d) : walk_grid_t<double2, false, true>(d);
+    if (mode == QW_MODE_WALK_SEG_PF)
+        return fp32 ? walk_grid_t<float2, true, true>(d) : walk_grid_t<double2, true, true>(d);
     if (fp32) {
         if (mode == QW_MODE_WALK_LITERAL) return step_grid_t<float2, QW_MODE_WALK_LITERAL>(d);
         return step_grid_t<float2, QW_MODE_T>(d);
@@ -1663,11 +1713,17 @@ cudaError_t qw_launch_step(const QwSimDev &d, const QwBufDev &in, const QwBufDev
                            cudaStream_t st)
 {
     if (a.mode == QW_MODE_WALK_FUSED)
-        return fp32 ? launch_walk_t<float2, false>(d, in, out, clr, a, grid, st)
-                    : launch_walk_t<double2, false>(d, in, out, clr, a, grid, st);
+        return fp32 ? launch_walk_t<float2, false, false>(d, in, out, clr, a, grid, st)
+                    : launch_walk_t<double2, false, false>(d, in, out, clr, a, grid, st);
     if (a.mode == QW_MODE_WALK_FUSED_PF)
-        return fp32 ? launch_walk_t<float2, true>(d, in, out, clr, a, grid, st)
-                    : launch_walk_t<double2, true>(d, in, out, clr, a, grid, st);
+        return fp32 ? launch_walk_t<float2, true, false>(d, in, out, clr, a, grid, st)
+                    : launch_walk_t<double2, true, false>(d, in, out, clr, a, grid, st);
+    if (a.mode == QW_MODE_WALK_SEG)
+        return fp32 ? launch_walk_t<float2, false, true>(d, in, out, clr, a, grid, st)
+                    : launch_walk_t<double2, false, true>(d, in, out, clr, a, grid, st);
+    if (a.mode == QW_MODE_WALK_SEG_PF)
+        return fp32 ? launch_walk_t<float2, true, true>(d, in, out, clr, a, grid, st)
+                    : launch_walk_t<double2, true, true>(d, in, out, clr, a, grid, st);
     if (fp32) {
         if (a.mode == QW_MODE_WALK_LITERAL)
             return launch_step_t<float2, QW_MODE_WALK_LITERAL>(d, in, out, clr, a, grid, st);

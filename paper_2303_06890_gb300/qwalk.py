@@ -201,11 +201,11 @@ class Sim:
         self._check(load().qw_apply_walk_step(self._h, int(nsteps)))
 
     def autotune(self, steps_per_candidate: int = 8) -> tuple[int, list[float]]:
-        """qw_autotune: (chosen variant, [us/step of variant 0, variant 1])."""
+        """qw_autotune: (chosen variant, [us/step of variants 0..3])."""
         choice = ctypes.c_int32()
-        us = np.zeros(2)
+        us = np.zeros(4)
         self._check(load().qw_autotune(self._h, int(steps_per_candidate), ctypes.byref(choice), _p(us)))
-        return int(choice.value), [float(us[0]), float(us[1])]
+        return int(choice.value), [float(v) for v in us]
 
     def enqueue_walk_steps(self, nsteps: int = 1) -> None:
         self._check(load().qw_enqueue_walk_steps(self._h, int(nsteps)))

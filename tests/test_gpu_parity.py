@@ -43,7 +43,7 @@ def test_state_init(apply_T):
     compare(gpu_state(sim), oracle_state(o), TOL64)
 
 
-@pytest.mark.parametrize("fuse,variant", [(True, 0), (True, 1), (False, 0)])
+@pytest.mark.parametrize("fuse,variant", [(True, 0), (True, 1), (True, 2), (True, 3), (False, 0)])
 def test_walk_n16_every_step(fuse, variant):
     w = wl.walk_n16()
     sim = _sim(w, fuse_reflection=fuse, walk_variant=variant)
@@ -87,7 +87,7 @@ def test_walk_n1024_fp64_100_steps():
         compare(gpu_state(sim), oracle_state(o), TOL64)
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_walk_n16384_fp64_full_size(variant):
     w = wl.walk_n16384()
     sim = _sim(w, walk_variant=variant)
@@ -126,8 +126,8 @@ def test_fp32_amp_n16384_bench_config():
     sim = _sim(w, precision=qwalk.QW_FP32_AMP)
     sim.state_init(w.b)
     choice, us = sim.autotune(4)
-    assert choice in (0, 1) and min(us) > 0
-    sim.apply_walk_step(w.steps - 8)
+    assert choice in (0, 1, 2, 3) and min(us) > 0
+    sim.apply_walk_step(w.steps - 16)
     o = _oracle(w)
     o.apply("T")
     for _ in range(w.steps):
@@ -395,7 +395,7 @@ def test_checkpoint_round_trip():
     compare(gpu_state(b), gpu_state(a), 0.0)
 
 
-@pytest.mark.parametrize("fuse,variant", [(True, 0), (True, 1), (False, 0)])
+@pytest.mark.parametrize("fuse,variant", [(True, 0), (True, 1), (True, 2), (True, 3), (False, 0)])
 def test_garbage_subspace_states_match_oracle(fuse, variant):
     """Random states over the whole register space -- rows with jc != 0 (the
     garbage-row table), rows j >= N (N = 12, so the all-zero QRAM list), kc != 0
