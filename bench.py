@@ -3,9 +3,9 @@
 
 Workload: the quantum walk on a random symmetric N = 16384 matrix with at most
 16 non-zeros per column (s = 16), Q1.15 values, random normalised |b>,
-complex64 amplitudes with FP64 merge, norm and renormalisation -- the
-configuration the paper's headline walk (N = 16384, Table 1 row E) is quoted
-at.  One benchmark step = one walk step W = S T~ P T~^dag of the whole state.
+complex64 amplitudes with FP64 merge, norm and renormalisation, at the size
+of the paper's largest walk (Table 1 row E, N = 16384).  One benchmark step
+= one walk step W = S T~ P T~^dag of the whole state.
 
 Prints one JSON line: walk steps/s (value), branch entries/s, the plain
 FP64-amplitude path on the same workload, the roofline of the step kernel,
@@ -51,6 +51,8 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batched-steps", type=int, default=300)
+    p.add_argument("--no-table1", action="store_true")
+    p.add_argument("--no-qls", action="store_true")
     return p.parse_args()
 
 
@@ -279,6 +281,9 @@ def run_ours(args, rank, world, local_rank):
     batched = None if args.no_batched else batched_leg(args, torch, flush, barrier, max_over_ranks,
                                                        world, rank)
 
+    table1 = None if args.no_table1 else table1_leg(torch, barrier, max_over_ranks)
+    qls = None if args.no_qls else qls_leg(torch, barrier, max_over_ranks)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args.cpu_budget)
@@ -313,6 +318,10 @@ def run_ours(args, rank, world, local_rank):
     }
     if batched is not None:
         line["batched"] = batched
+    if table1 is not None:
+        line["table1"] = table1
+    if qls is not None:
+        line["qls"] = qls
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -381,6 +390,94 @@ def batched_leg(args, torch, flush, barrier, max_over_ranks, world, rank) -> dic
             "walk_50_steps_ms_graph": 1000.0 * t_walk,
             "sequential_fp64_walk_50_steps_ms": 1000.0 * t_seq,
             "speedup_vs_sequential_fp64": t_seq / t_walk}
+
+
+# Table 1: average time per walk step of the paper's simulator on one core of
+# a Xeon E5-2680 (context only: another machine, and the paper's matrices).
+TABLE1_PAPER_S_PER_STEP = {"A": 1.1e-3, "B": 12e-3, "C": 1.2, "D": 14.0, "E": 66.0}
+
+
+def _events_time(torch, fn) -> float:
+    """Device seconds of the work ``fn`` enqueues on the current stream."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1000.0
+
+
+def table1_leg(torch, barrier, max_over_ranks) -> dict:
+    """Walk steps on the band matrices shaped like Table 1 (A..E, Sec. V-B),
+    complex128 and complex64, autotuned, steps issued back to back as graph
+    replays (the state stays resident; no L2 flush: consecutive steps of one
+    walk), beside the paper's single-core time per step."""
+    from paper_2303_06890_gb300 import qwalk
+    from paper_2303_06890_gb300 import workloads as wl
+
+    out = {}
+    for name in "ABCDE":
+        w = wl.table1(name)
+        steps = 600 if w.n <= 1024 else 60
+        row = {"n": w.n, "s": w.s, "word": wl.TABLE1[name][1], "nnz": int(w.matrix.nnz),
+               "paper_s_per_step": TABLE1_PAPER_S_PER_STEP[name]}
+        for label, prec in (("fp64", qwalk.QW_FP64), ("fp32", qwalk.QW_FP32_AMP)):
+            sim = qwalk.Sim(w.matrix, s_pad=w.s, precision=prec)
+            sim.state_init(w.b)
+            variant, _ = sim.autotune(2 if w.n > 1024 else 6)
+            sim.apply_walk_step(6)
+            sim.step_stats(reset=True)
+            barrier()
+            t = max_over_ranks(_events_time(torch, lambda: sim.enqueue_walk_steps(steps)))
+            sim.sync()
+            st = sim.step_stats(reset=True)
+            sim.close()
+            row[label] = {"us_per_step": 1e6 * t / steps, "variant": variant,
+                          "branches_per_step": st["out"] / max(1, st["steps"]),
+                          "entries_per_s": (st["in"] + st["after_rdag"] + st["after_hph"]) / t}
+        row["paper_over_fp64"] = row["paper_s_per_step"] / (row["fp64"]["us_per_step"] * 1e-6)
+        out[name] = row
+    return out
+
+
+def qls_leg(torch, barrier, max_over_ranks) -> dict:
+    """The CKS solver (Sec. IV, Eq. (fx)) end to end through qw_apply_qls:
+    * the cond(A) = 100 N = 1024 system with complex64 amplitudes, at its own
+      j0 and at Table 1 C's kappa = 5000 (j0 = 106122, the 212245 walk steps
+      the paper ran for 70 h on one core); the wider interval [1/5000, 1]
+      still covers the spectrum, so the solution stays accurate;
+    * matrix C of Table 1 (N = 1024, s = 32, kappa 4907) in complex128 at its
+      own j0.
+    Fidelity |<x|y>|^2 / ||y||^2 against x = A^-1 b / ||A^-1 b|| from a dense
+    FP64 solve (numpy); p_succ = ||Y||^2 / (sum |a_j|)^2."""
+    import numpy as np
+    from paper_2303_06890_gb300 import qwalk
+    from paper_2303_06890_gb300 import workloads as wl
+
+    runs = [("qls_n1024_own_j0", wl.qls_n1024(), None, qwalk.QW_FP32_AMP),
+            ("qls_n1024_kappa5000", wl.qls_n1024(), 5000.0, qwalk.QW_FP32_AMP),
+            ("table1_C_own_j0", wl.table1("C", steps=0), None, qwalk.QW_FP64)]
+    out = {}
+    for label, w, kappa, prec in runs:
+        kappa = w.kappa if kappa is None else kappa
+        coeffs, j0, _ = qwalk.cks_coefficients(kappa, 1e-3)
+        sim = qwalk.Sim(w.matrix, s_pad=w.s, precision=prec)
+        barrier()
+        t0 = time.perf_counter()
+        sim.state_init(w.b)
+        y, p = sim.apply_qls(coeffs)
+        t = max_over_ranks(time.perf_counter() - t0)
+        sim.close()
+        x = np.linalg.solve(w.matrix.dense(), w.b)
+        x /= np.linalg.norm(x)
+        fid = float(abs(np.vdot(x, y)) ** 2 / np.vdot(y, y).real)
+        out[label] = {"n": w.n, "s": w.s, "kappa_walk": w.kappa, "kappa_coefficients": kappa,
+                      "j0": j0, "walk_steps": 2 * (j0 + 1),
+                      "precision": "complex64" if prec == qwalk.QW_FP32_AMP else "complex128",
+                      "seconds": t, "walk_steps_per_s": 2 * (j0 + 1) / t,
+                      "fidelity": fid,
+                      "p_succ": float(p[-1] / np.abs(coeffs).sum() ** 2)}
+    return out
 
 
 def cpu_baseline(w, budget: float) -> dict:

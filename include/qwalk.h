@@ -102,7 +102,9 @@ void qw_sim_opts_default(qw_sim_opts *opts);
  * by column; a row with fewer than s non-zeros is completed with explicit
  * zero elements at the first columns j+1, j+2, ... (cyclically) not already in
  * the row.
- * Errors: QW_ERR_ARG (null, num_instances < 1, n < 2, n > 65536);
+ * Errors: QW_ERR_ARG (null, num_instances < 1, n < 2, n > 65536, or row
+ * buffers -- 8 warps x 2 x warp_capacity branches -- larger than the
+ * device's shared memory per block);
  * QW_ERR_CSC (unsorted or duplicate rows in a column, index out of range,
  * column count > s_pad, s_pad not a power of two or > n, matrix not
  * symmetric, negative diagonal element -- which the walk's isometry cannot
@@ -181,7 +183,9 @@ int qw_cks_coefficients(double kappa, double eps, double *coeffs, int64_t cap, i
  * of tau_j = T~^dag W^(2j+1) T~ |b~> (whose value is T_{2j+1}(A/s) b) in FP64:
  * Y += coeffs[j] * Pi_0 tau_j for j = 0..j0.  Outputs: y_out (2 N doubles,
  * interleaved re/im) = Y; psucc_out (j0+1 doubles, nullable) =
- * || Pi_0 sum_{k<=j} coeffs[k] tau_k ||^2 for each j.  2 j0 + 2 launches.
+ * || Pi_0 sum_{k<=j} coeffs[k] tau_k ||^2 for each j.  Three launches per
+ * term (two walk steps, one norm); with opts.graphs, runs of 3 terms replay a
+ * captured CUDA graph (the coefficient index lives on the device).
  * Errors: QW_ERR_ARG, QW_ERR_STATE, QW_ERR_CAPACITY, QW_ERR_CUDA.
  */
 int qw_apply_qls(qw_sim *sim, int32_t inst, const double *coeffs, int64_t j0, double *y_out,

@@ -35,6 +35,7 @@ struct Scalars {
     unsigned long long stats[QW_NSTAT];
     int32_t tinit_fallback;
     int32_t pad2;
+    int64_t qls_j; /* current QLS term */
 };
 
 thread_local std::string g_create_error;
@@ -84,26 +85,31 @@ struct qw_sim {
     double *partials = nullptr;
     Scalars *sc = nullptr;
     double2 *qls_y = nullptr;
-    double *qls_p = nullptr;
+    double *qls_p = nullptr; /* p_j, j = 0..j0 */
+    double *qls_c = nullptr; /* coefficients a_j, j = 0..j0 */
     int64_t qls_p_cap = 0;
     int64_t device_bytes = 0;
     int64_t launches = 0;
     /* captured 6-step graphs, one per (buffer, scale slot) phase */
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    /* captured 3-term QLS graphs (6 walk steps, 3 norms), one per phase */
+    cudaGraphExec_t qexec[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
     std::string err;
 };
 
 static const int kGraphSteps = 6; /* a multiple of the 3-buffer and 2-slot periods */
+static const int kGraphTerms = 3;  /* QLS terms per graph: 2 walk steps each */
 
 static void drop_graphs(qw_sim *sim)
 {
-    for (auto &row : sim->gexec)
-        for (auto &g : row)
-            if (g) {
-                cudaGraphExecDestroy(g);
-                g = nullptr;
-            }
+    for (auto *set : {&sim->gexec, &sim->qexec})
+        for (auto &row : *set)
+            for (auto &g : row)
+                if (g) {
+                    cudaGraphExecDestroy(g);
+                    g = nullptr;
+                }
 }
 
 static int fail(qw_sim *sim, int code, const std::string &msg)
@@ -332,6 +338,19 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     cudaError_t e;
 #define QW_TRY(call)                                                                               \
     if ((e = (call)) != cudaSuccess) return bail(e, #call)
+    {
+        /* one block holds 8 warps' row buffers (2 x warp_capacity branches each) */
+        int optin = 0;
+        QW_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, sim->device));
+        const size_t need = qw_step_smem_bytes(d, sim->fp32, sim->mode);
+        if (need > (size_t)optin) {
+            g_create_error = "qw_sim_create: the step kernel needs " + std::to_string(need) +
+                             " bytes of shared memory per block, the device allows " + std::to_string(optin) +
+                             ": lower warp_capacity or row_capacity";
+            qw_sim_destroy(sim);
+            return QW_ERR_ARG;
+        }
+    }
     QW_TRY(dalloc(sim, &sim->img, (size_t)img_words));
     QW_TRY(dalloc(sim, &sim->fg, 65536));
     QW_TRY(dalloc(sim, &sim->fg32, 65536));
@@ -405,6 +424,7 @@ extern "C" int qw_sim_destroy(qw_sim *sim)
     cudaFree(sim->sc);
     cudaFree(sim->qls_y);
     cudaFree(sim->qls_p);
+    cudaFree(sim->qls_c);
     delete sim;
     return QW_OK;
 }
@@ -486,14 +506,15 @@ static QwStepArgs step_args(qw_sim *sim, int mode)
     a.status = &sim->sc->status;
     a.stats = sim->sc->stats;
     a.qls_y = sim->qls_y;
+    a.qls_coefs = sim->qls_c;
+    a.qls_j = &sim->sc->qls_j;
     return a;
 }
 
 /* one walk step: X_cur -> X_cur+1, clearing X_cur+2 */
-static int launch_walk(qw_sim *sim, double coef, int readout)
+static int launch_walk(qw_sim *sim, int readout)
 {
     QwStepArgs a = step_args(sim, sim->mode);
-    a.qls_coef = coef;
     a.qls_readout = readout;
     const int nxt = (sim->cur + 1) % 3, clr = (sim->cur + 2) % 3;
     cudaError_t e = qw_launch_step(sim->d, sim->buf[sim->cur], sim->buf[nxt], sim->buf[clr], a,
@@ -584,7 +605,19 @@ extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, cons
 /* Capture kGraphSteps walk steps starting at the current (buffer, slot)
  * phase on a private stream; the sequence of kernel arguments repeats with
  * that period, so the graph can be replayed whenever the phase recurs. */
-static int capture_graph(qw_sim *sim, cudaGraphExec_t *out)
+/* One QLS term: T~^dag W^2 T~ as two walk steps, the second reading out
+ * Y += a_j Pi_0 tau_j, then p_j = ||Y||^2 and j += 1 on the device. */
+static int launch_qls_term(qw_sim *sim)
+{
+    int rc = launch_walk(sim, 0);
+    if (rc == QW_OK) rc = launch_walk(sim, 1);
+    if (rc != QW_OK) return rc;
+    QW_CUDA(sim, qw_launch_qls_norm(sim->qls_y, sim->n_of[0], sim->qls_p, &sim->sc->qls_j, sim->stream));
+    sim->launches++;
+    return QW_OK;
+}
+
+static int capture_graph(qw_sim *sim, cudaGraphExec_t *out, bool qls)
 {
     if (!sim->cap_stream) QW_CUDA(sim, cudaStreamCreateWithFlags(&sim->cap_stream, cudaStreamNonBlocking));
     cudaStream_t user = sim->stream;
@@ -593,7 +626,11 @@ static int capture_graph(qw_sim *sim, cudaGraphExec_t *out)
     sim->stream = sim->cap_stream;
     cudaError_t e = cudaStreamBeginCapture(sim->cap_stream, cudaStreamCaptureModeThreadLocal);
     int rc = QW_OK;
-    for (int t = 0; t < kGraphSteps && e == cudaSuccess && rc == QW_OK; ++t) rc = launch_walk(sim, 0.0, 0);
+    if (qls) {
+        for (int t = 0; t < kGraphTerms && e == cudaSuccess && rc == QW_OK; ++t) rc = launch_qls_term(sim);
+    } else {
+        for (int t = 0; t < kGraphSteps && e == cudaSuccess && rc == QW_OK; ++t) rc = launch_walk(sim, 0);
+    }
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(sim->cap_stream, &g);
     sim->stream = user;
@@ -624,7 +661,7 @@ extern "C" int qw_enqueue_walk_steps(qw_sim *sim, int64_t nsteps)
         cudaStreamIsCapturing(sim->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
         cudaGraphExec_t &g = sim->gexec[sim->cur][sim->scale_slot];
         if (!g) {
-            int rc = capture_graph(sim, &g);
+            int rc = capture_graph(sim, &g, false);
             if (rc != QW_OK) return rc;
         }
         for (; t + kGraphSteps <= nsteps; t += kGraphSteps) {
@@ -633,7 +670,7 @@ extern "C" int qw_enqueue_walk_steps(qw_sim *sim, int64_t nsteps)
         }
     }
     for (; t < nsteps; ++t) {
-        int rc = launch_walk(sim, 0.0, 0);
+        int rc = launch_walk(sim, 0);
         if (rc != QW_OK) return rc;
     }
     return QW_OK;
@@ -750,19 +787,40 @@ extern "C" int qw_apply_qls(qw_sim *sim, int32_t inst, const double *coeffs, int
         return fail(sim, QW_ERR_STATE, "QLS needs the state T~|b~> (qw_state_init with apply_T = 1)");
     const int n = sim->n_of[0];
     if (sim->qls_p_cap < j0 + 1) {
+        drop_graphs(sim); /* the QLS graphs hold the old arrays */
         cudaFree(sim->qls_p);
-        sim->qls_p = nullptr;
+        cudaFree(sim->qls_c);
+        sim->qls_p = sim->qls_c = nullptr;
+        sim->qls_p_cap = 0;
         QW_CUDA(sim, cudaMalloc((void **)&sim->qls_p, (size_t)(j0 + 1) * sizeof(double)));
+        QW_CUDA(sim, cudaMalloc((void **)&sim->qls_c, (size_t)(j0 + 1) * sizeof(double)));
         sim->qls_p_cap = j0 + 1;
     }
+    QW_CUDA(sim, cudaMemcpyAsync(sim->qls_c, coeffs, (size_t)(j0 + 1) * sizeof(double), cudaMemcpyHostToDevice,
+                                 sim->stream));
     QW_CUDA(sim, cudaMemsetAsync(sim->qls_y, 0, (size_t)n * sizeof(double2), sim->stream));
-    for (int64_t j = 0; j <= j0; ++j) {
-        int rc = launch_walk(sim, 0.0, 0);
-        if (rc == QW_OK) rc = launch_walk(sim, coeffs[j], 1);
-        if (rc != QW_OK) return rc;
-        QW_CUDA(sim, qw_launch_qls_norm(sim->qls_y, n, sim->qls_p + j, sim->stream));
-        sim->launches++;
-        if ((j & 1023) == 1023) {
+    QW_CUDA(sim, cudaMemsetAsync(&sim->sc->qls_j, 0, sizeof(int64_t), sim->stream));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool graphs = sim->opts.graphs && cudaStreamIsCapturing(sim->stream, &cs) == cudaSuccess &&
+                        cs == cudaStreamCaptureStatusNone;
+    int64_t j = 0, next_check = 1024;
+    while (j <= j0) {
+        if (graphs && j0 + 1 - j >= kGraphTerms) {
+            cudaGraphExec_t &g = sim->qexec[sim->cur][sim->scale_slot];
+            if (!g) {
+                int rc = capture_graph(sim, &g, true);
+                if (rc != QW_OK) return rc;
+            }
+            QW_CUDA(sim, cudaGraphLaunch(g, sim->stream));
+            sim->launches += 3 * kGraphTerms;
+            j += kGraphTerms;
+        } else {
+            int rc = launch_qls_term(sim);
+            if (rc != QW_OK) return rc;
+            j += 1;
+        }
+        if (j >= next_check) { /* stop early on a device error */
+            next_check += 1024;
             int st = check_status(sim, "qw_apply_qls");
             if (st != QW_OK) return st;
         }

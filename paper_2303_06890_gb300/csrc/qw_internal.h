@@ -95,7 +95,8 @@ struct QwStepArgs {
     int32_t *status;
     unsigned long long *stats; /* QW_STAT_* counters, accumulated (nullable) */
     double2 *qls_y;          /* flag-0 accumulator (nullable) */
-    double qls_coef;         /* Y += coef * Pi_0 tau at this step's midpoint */
+    const double *qls_coefs; /* Y += qls_coefs[*qls_j] * Pi_0 tau at this step's midpoint */
+    const int64_t *qls_j;    /* index of the current QLS term (advanced by k_qls_norm) */
     int qls_readout;
 };
 
@@ -104,6 +105,8 @@ int qw_sm_count(void);
 cudaError_t qw_launch_step(const QwSimDev &d, const QwBufDev &in, const QwBufDev &out,
                            const QwBufDev &clear, const QwStepArgs &a, int fp32, int grid,
                            cudaStream_t st);
+/* dynamic shared memory per block of the step kernel of `mode` */
+size_t qw_step_smem_bytes(const QwSimDev &d, int fp32, int mode);
 int qw_step_grid(const QwSimDev &d, int fp32, int mode);
 cudaError_t qw_launch_clear(const QwSimDev &d, const QwBufDev &buf, int64_t lo, int64_t hi,
                             int clear_spill, cudaStream_t st);
@@ -125,7 +128,7 @@ cudaError_t qw_launch_measure_noalloc(const QwSimDev &d, const QwBufDev &buf, in
                                       int64_t len, int device, cudaStream_t st);
 cudaError_t qw_launch_count(const QwSimDev &d, const QwBufDev &buf, int inst,
                             unsigned long long *counter, cudaStream_t st);
-cudaError_t qw_launch_qls_norm(const double2 *y, int n, double *out, cudaStream_t st);
+cudaError_t qw_launch_qls_norm(const double2 *y, int n, double *p, int64_t *jctr, cudaStream_t st);
 
 /* packed row key: inst << 40 | jc << 20 | j << 1 | b1  (nb <= 19) */
 __host__ __device__ static inline uint64_t qw_rowkey(uint32_t inst, uint32_t jc, uint32_t j,

@@ -348,9 +348,10 @@ __device__ int hadamard_op(const QwSimDev &d, const Row &r, const uint64_t *ks, 
                 cnt += keep(o, d.tau2) ? 1 : 0;
                 if (u == 0 && g == 0 && readout && a.qls_readout && r.valid && r.jc == 0 &&
                     r.b1 == 0) {
+                    const double coef = a.qls_coefs[*a.qls_j];
                     double2 acc = a.qls_y[r.j];
-                    acc.x += a.qls_coef * o.x;
-                    acc.y += a.qls_coef * o.y;
+                    acc.x += coef * o.x;
+                    acc.y += coef * o.y;
                     a.qls_y[r.j] = acc;
                 }
             }
@@ -524,6 +525,49 @@ __device__ void chain(const QwSimDev &d, const Row &r, uint64_t *ks, int n)
 
 /* Sort-based step kernel: T~ alone (MODE_T, in place on a bucket range) or a
  * walk step with H, P and H as three interference ops (MODE_WALK_LITERAL). */
+/* End of a step: the norm of the output from per-block partial sums.  Every
+ * block stores its partial; the last block to finish sums them all -- each
+ * thread a fixed strided subset, then a fixed-shape warp and block reduction,
+ * so the result does not depend on the order blocks finish -- and publishes
+ * the norm, the next step's renormalisation factor and the clean-step count.
+ * nv: this warp's partial (any lane); block-uniform control flow. */
+__device__ void finish_step(const QwStepArgs &a, double nv, double *block_part, int *is_last, bool count_step)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    nv = warp_sum(nv);
+    if (lane == 0) block_part[warp] = nv;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < WARPS; ++w) sum += block_part[w];
+        a.partials[blockIdx.x] = sum;
+        __threadfence();
+        const unsigned prev = atomicAdd(a.done_ctr, 1u);
+        *is_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!*is_last) return;
+    __threadfence();
+    double v = 0.0;
+    for (unsigned bb = threadIdx.x; bb < gridDim.x; bb += blockDim.x) v += __ldcg(a.partials + bb);
+    v = warp_sum(v);
+    if (lane == 0) block_part[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < WARPS; ++w) tot += block_part[w];
+        const bool clean = *(volatile int32_t *)a.status == 0;
+        if (clean) {
+            *a.norm_out = tot;
+            if (a.scale_out)
+                *a.scale_out = (a.renorm && tot > 0.0) ? sqrt(*a.renorm_target / tot) : 1.0;
+            if (a.steps_done) *a.steps_done += 1;
+            if (a.stats && count_step) a.stats[QW_STAT_STEPS] += 1;
+        }
+        *a.done_ctr = 0u;
+    }
+}
+
 template <typename AmpT, int MODE>
 __global__ void __launch_bounds__(WARPS * 32) k_step(QwSimDev d, QwBufDev in, QwBufDev out,
                                                      QwBufDev clr, QwStepArgs a)
@@ -628,33 +672,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_step(QwSimDev d, QwBufDev in, Qw
         atomicAdd(a.stats + QW_STAT_OUT, st_out);
     }
 
-    /* ||output||^2: block partial sums, reduced in block order by the last block */
-    nrm = warp_sum(nrm);
-    if (lane == 0) block_part[warp] = nrm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < WARPS; ++w) s += block_part[w];
-        a.partials[blockIdx.x] = s;
-        __threadfence();
-        const unsigned prev = atomicAdd(a.done_ctr, 1u);
-        is_last = (prev == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (is_last && threadIdx.x == 0) {
-        __threadfence();
-        double tot = 0.0;
-        for (unsigned bb = 0; bb < gridDim.x; ++bb) tot += __ldcg(a.partials + bb);
-        const bool clean = *(volatile int32_t *)a.status == 0;
-        if (clean) {
-            *a.norm_out = tot;
-            if (a.scale_out)
-                *a.scale_out = (a.renorm && tot > 0.0) ? sqrt(*a.renorm_target / tot) : 1.0;
-            if (a.steps_done) *a.steps_done += 1;
-            if (a.stats && MODE != QW_MODE_T) a.stats[QW_STAT_STEPS] += 1;
-        }
-        *a.done_ctr = 0u;
-    }
+    /* ||output||^2 */
+    finish_step(a, nrm, block_part, &is_last, MODE != QW_MODE_T);
 }
 
 /* per-warp shared memory of the fused kernels: keys x2, amps x2, zero-group
@@ -1114,9 +1133,10 @@ __device__ int reflect_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
         sum.reduce(s);
         if (a.qls_readout && r.valid && lane == 0) {
             const double2 sv = sum.value();
+            const double coef = a.qls_coefs[*a.qls_j];
             double2 acc = a.qls_y[r.j];
-            acc.x += a.qls_coef * (d.inv_sqrt_s * sv.x);
-            acc.y += a.qls_coef * (d.inv_sqrt_s * sv.y);
+            acc.x += coef * (d.inv_sqrt_s * sv.x);
+            acc.y += coef * (d.inv_sqrt_s * sv.y);
             a.qls_y[r.j] = acc;
         }
         sum.scale_pow2(d.two_over_s);
@@ -1267,7 +1287,6 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
     }
     const bool rescale = a.scale_in != nullptr;
     const typename Amp<AmpT>::Scale scale(rescale ? *a.scale_in : 1.0);
-    const int64_t bhi = skip ? 0 : d.total_buckets;
     typename Amp<AmpT>::Norm nrm;
     unsigned long long st_rows = 0, st_in = 0, st_rdag = 0, st_hph = 0, st_out = 0;
 
@@ -1388,32 +1407,7 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
         atomicAdd(a.stats + QW_STAT_HPH, st_hph);
         atomicAdd(a.stats + QW_STAT_OUT, st_out);
     }
-    double nv = warp_sum(nrm.get());
-    if (lane == 0) block_part[warp] = nv;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double sum = 0.0;
-        for (int w = 0; w < WARPS; ++w) sum += block_part[w];
-        a.partials[blockIdx.x] = sum;
-        __threadfence();
-        const unsigned prev = atomicAdd(a.done_ctr, 1u);
-        is_last = (prev == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (is_last && threadIdx.x == 0) {
-        __threadfence();
-        double tot = 0.0;
-        for (unsigned bb = 0; bb < gridDim.x; ++bb) tot += __ldcg(a.partials + bb);
-        const bool clean = *(volatile int32_t *)a.status == 0;
-        if (clean) {
-            *a.norm_out = tot;
-            if (a.scale_out)
-                *a.scale_out = (a.renorm && tot > 0.0) ? sqrt(*a.renorm_target / tot) : 1.0;
-            if (a.steps_done) *a.steps_done += 1;
-            if (a.stats) a.stats[QW_STAT_STEPS] += 1;
-        }
-        *a.done_ctr = 0u;
-    }
+    finish_step(a, nrm.get(), block_part, &is_last, true);
 }
 
 /* T~ on |b~> (qw_state_init): every row (jc = 0, j, b1 = 0) of the range
@@ -1609,7 +1603,8 @@ __global__ void k_count(QwSimDev d, QwBufDev buf, int inst, unsigned long long *
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(counter, c);
 }
 
-__global__ void k_qls_norm(const double2 *y, int n, double *out)
+/* p[j] = ||Y||^2 for the current term j = *jctr, then advance the term. */
+__global__ void k_qls_norm(const double2 *y, int n, double *p, int64_t *jctr)
 {
     __shared__ double part[32];
     double acc = 0.0;
@@ -1620,7 +1615,9 @@ __global__ void k_qls_norm(const double2 *y, int n, double *out)
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
-        *out = t;
+        const int64_t j = *jctr;
+        p[j] = t;
+        *jctr = j + 1;
     }
 }
 
@@ -1688,6 +1685,13 @@ int qw_sm_count(void)
         if (n < 1) n = 1;
     }
     return n;
+}
+
+size_t qw_step_smem_bytes(const QwSimDev &d, int fp32, int mode)
+{
+    if (mode == QW_MODE_WALK_LITERAL || mode == QW_MODE_T)
+        return fp32 ? step_smem<float2, QW_MODE_T>(d) : step_smem<double2, QW_MODE_T>(d);
+    return (size_t)WARPS * (fp32 ? walk_smem_per_warp<float2>(d) : walk_smem_per_warp<double2>(d));
 }
 
 int qw_step_grid(const QwSimDev &d, int fp32, int mode)
@@ -1785,9 +1789,9 @@ cudaError_t qw_launch_count(const QwSimDev &d, const QwBufDev &buf, int inst,
     return cudaGetLastError();
 }
 
-cudaError_t qw_launch_qls_norm(const double2 *y, int n, double *out, cudaStream_t st)
+cudaError_t qw_launch_qls_norm(const double2 *y, int n, double *p, int64_t *jctr, cudaStream_t st)
 {
-    k_qls_norm<<<1, 1024, 0, st>>>(y, n, out);
+    k_qls_norm<<<1, 1024, 0, st>>>(y, n, p, jctr);
     return cudaGetLastError();
 }
 

@@ -132,6 +132,46 @@ def cks_coefficients(kappa: float, eps: float = 1e-3) -> tuple[np.ndarray, int, 
     return out, int(j0.value), int(b.value)
 
 
+_FIELD_ORDER = {"jc": 0, "j": 1, "b1": 2, "kc": 3, "k": 4, "b2": 5, "A": 6, "inst": 7}
+
+
+def _fields(nb: int) -> list[tuple[str, int]]:
+    """Packed key layout of qw_state_export, from bit 0 up."""
+    return [("b2", 1), ("k", nb), ("kc", nb), ("b1", 1), ("j", nb), ("jc", nb), ("A", 16), ("inst", 16)]
+
+
+def pack_keys(regs: np.ndarray, nb: int, key_words: int = 2) -> np.ndarray:
+    """[M, 8] (jc, j, b1, kc, k, b2, A, inst) -> packed keys [M, key_words]."""
+    regs = np.asarray(regs, dtype=np.uint64).reshape(len(regs), -1)
+    out = np.zeros((len(regs), key_words), dtype=np.uint64)
+    pos = 0
+    for name, w in _fields(nb):
+        v = regs[:, _FIELD_ORDER[name]] & np.uint64((1 << w) - 1)
+        word, off = divmod(pos, 64)
+        if word < key_words:
+            out[:, word] |= v << np.uint64(off)
+        if off + w > 64 and word + 1 < key_words:  # the field continues in the next word
+            out[:, word + 1] |= v >> np.uint64(64 - off)
+        pos += w
+    return out
+
+
+def unpack_keys(keys: np.ndarray, nb: int) -> np.ndarray:
+    """Packed keys [M, key_words] -> [M, 8] (jc, j, b1, kc, k, b2, A, inst)."""
+    keys = np.asarray(keys, dtype=np.uint64).reshape(len(keys), -1)
+    out = np.zeros((len(keys), 8), dtype=np.uint64)
+    pos = 0
+    for name, w in _fields(nb):
+        word, off = divmod(pos, 64)
+        if word < keys.shape[1]:
+            v = keys[:, word] >> np.uint64(off)
+            if off + w > 64 and word + 1 < keys.shape[1]:
+                v = v | (keys[:, word + 1] << np.uint64(64 - off))
+            out[:, _FIELD_ORDER[name]] = v & np.uint64((1 << w) - 1)
+        pos += w
+    return out
+
+
 class Sim:
     """qw_sim_create ... qw_sim_destroy for one or several matrices."""
 
@@ -265,34 +305,11 @@ class Sim:
 
     def pack(self, regs: np.ndarray, key_words: int = 2) -> np.ndarray:
         """[M, 8] (jc, j, b1, kc, k, b2, A, inst) -> packed keys [M, key_words]."""
-        nb = self.nb
-        widths = [("b2", 1), ("k", nb), ("kc", nb), ("b1", 1), ("j", nb), ("jc", nb), ("A", 16),
-                  ("inst", 16)]
-        order = {"jc": 0, "j": 1, "b1": 2, "kc": 3, "k": 4, "b2": 5, "A": 6, "inst": 7}
-        out = np.zeros((len(regs), key_words), dtype=np.uint64)
-        for i, r in enumerate(regs):
-            v, pos = 0, 0
-            for name, w in widths:
-                v |= int(r[order[name]]) << pos
-                pos += w
-            for t in range(key_words):
-                out[i, t] = (v >> (64 * t)) & ((1 << 64) - 1)
-        return out
+        return pack_keys(regs, self.nb, key_words)
 
     def launch_count(self) -> int:
         return int(load().qw_launch_count(self._h))
 
     def unpack(self, keys: np.ndarray) -> np.ndarray:
         """Packed keys -> [M, 8] (jc, j, b1, kc, k, b2, A, inst) per the header's layout."""
-        nb = self.nb
-        widths = [("b2", 1), ("k", nb), ("kc", nb), ("b1", 1), ("j", nb), ("jc", nb), ("A", 16),
-                  ("inst", 16)]
-        big = [int(sum(int(w) << (64 * t) for t, w in enumerate(row))) for row in keys]
-        out = np.zeros((len(big), 8), dtype=np.uint64)
-        order = {"jc": 0, "j": 1, "b1": 2, "kc": 3, "k": 4, "b2": 5, "A": 6, "inst": 7}
-        for i, v in enumerate(big):
-            pos = 0
-            for name, w in widths:
-                out[i, order[name]] = (v >> pos) & ((1 << w) - 1)
-                pos += w
-        return out
+        return unpack_keys(keys, self.nb)

@@ -246,6 +246,74 @@ def small_random(n: int, smax: int, seed: int, band: int = 0, attempts: int | No
     return _workload(f"random_n{n}_s{smax}_seed{seed}", m, random_b(n, seed + 7), steps=steps)
 
 
+# --- matrices shaped like the paper's Table 1 (Sec. V-B) ----------------------
+
+TABLE1 = {  # name: (N, word length w, s) as printed in Table 1
+    "A": (16, 8, 8),
+    "B": (128, 8, 16),
+    "C": (1024, 8, 32),
+    "D": (8192, 16, 32),
+    "E": (16384, 32, 64),
+}
+
+
+def band_positive(n: int, bandwidth: int, word: int, seed: int) -> Matrix:
+    """Positive symmetric band matrix of Sec. V-B: every entry with
+    |i - j| <= bandwidth is a w-bit fixed-point number in (0, 1).
+
+    Entries are drawn as uniform integers m in [1, 2^w - 1], value m / 2^w (0
+    is excluded so the band is full).  For w <= 15 the value is exact in
+    Q1.15; for w > 15 it is rounded half to even to 15 fractional bits and
+    kept in [2^-15, 1 - 2^-15] (positive, like the w-bit value).
+    """
+    rng = np.random.default_rng(seed)
+    rows, cols, vals = [], [], []
+    for dist in range(bandwidth + 1):
+        m = rng.integers(1, 1 << word, n - dist, dtype=np.int64)
+        if word <= 15:
+            q = m << (15 - word)
+        else:
+            q = np.rint(m.astype(np.float64) / float(1 << (word - 15))).astype(np.int64)
+        q = np.clip(q, 1, 32767)
+        i = np.arange(n - dist)
+        rows.append(i)
+        cols.append(i + dist)
+        vals.append(q)
+        if dist:
+            rows.append(i + dist)
+            cols.append(i)
+            vals.append(q)
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    v = np.concatenate(vals).astype(np.int16)
+    order = np.lexsort((r, c))
+    r, c, v = r[order], c[order], v[order]
+    colptr = np.zeros(n + 1, dtype=np.int32)
+    np.add.at(colptr, c + 1, 1)
+    return Matrix(n=n, colptr=np.cumsum(colptr).astype(np.int32), rowidx=r.astype(np.int32), val_q15=v)
+
+
+# Matrix seeds: for A, B, C (whose kappa Table 1 prints: 1.0e2, 6.6e2, 5.0e3)
+# the first seed from 600 on whose kappa = s / min|lambda(A)| is within 5 % of
+# the printed value (103.0, 665.3, 4906.6); D and E print none.
+TABLE1_SEEDS = {"A": 631, "B": 612, "C": 733, "D": 603, "E": 604}
+
+
+def table1(name: str, steps: int = 50, seed: int | None = None) -> Workload:
+    """Matrix ``name`` of Table 1 (A..E): N and w as printed, the widest band
+    whose row count 2 bandwidth + 1 rounds up to the printed s (footnote b),
+    |b> uniform random in [0, 1) normalised (Sec. V-B), seed 700 + i for
+    i = 0..4 (A..E)."""
+    n, word, s = TABLE1[name]
+    i = "ABCDE".index(name)
+    bw = s // 2 - 1
+    m = band_positive(n, bw, word, seed=TABLE1_SEEDS[name] if seed is None else seed)
+    rng = np.random.default_rng(700 + i)
+    b = rng.uniform(0.0, 1.0, n)
+    b /= np.linalg.norm(b)
+    return _workload(f"table1_{name}_n{n}_w{word}_s{s}", m, b, steps=steps, s=s, spectrum=n <= 4096)
+
+
 CONFIGS = {
     "walk_n16": walk_n16,
     "walk_n1024": walk_n1024,

@@ -106,3 +106,22 @@ def test_null_and_destroy_are_safe():
     assert lib.qw_state_size(None, 0, None) == qwalk.QW_ERR_ARG
     assert lib.qw_apply_walk_step(None, 1) == qwalk.QW_ERR_ARG
     assert lib.qw_launch_count(None) == 0
+
+
+@pytest.mark.parametrize("nb", [4, 14, 16])
+@pytest.mark.parametrize("key_words", [2, 10])
+def test_key_pack_unpack_follow_the_header_layout(nb, key_words):
+    """pack_keys / unpack_keys against the layout written out as one big
+    integer: b2 | k | kc | b1 | j | jc | A(16) | inst(16) from bit 0."""
+    rng = np.random.default_rng(nb)
+    widths = {"jc": nb, "j": nb, "b1": 1, "kc": nb, "k": nb, "b2": 1, "A": 16, "inst": 16}
+    names = ["jc", "j", "b1", "kc", "k", "b2", "A", "inst"]
+    regs = np.stack([rng.integers(0, 1 << widths[f], 500, dtype=np.uint64) for f in names], axis=1)
+    keys = qwalk.pack_keys(regs, nb, key_words)
+    for row, key in zip(regs, keys):
+        v, pos = 0, 0
+        for f in ["b2", "k", "kc", "b1", "j", "jc", "A", "inst"]:
+            v |= int(row[names.index(f)]) << pos
+            pos += widths[f]
+        assert [int(x) for x in key] == [(v >> (64 * t)) & ((1 << 64) - 1) for t in range(key_words)]
+    assert np.array_equal(qwalk.unpack_keys(keys, nb), regs)
