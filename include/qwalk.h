@@ -88,6 +88,10 @@ typedef struct {
                                 segment, 3 = segments, software-pipelined */
     int32_t graphs;          /* 1 (default): runs of >= 6 walk steps are issued as replays
                                 of a captured 6-step CUDA graph; 0: one launch per step */
+    int32_t spill_rows;      /* slots of the table holding rows with jc != 0 (reached only
+                                from states outside the walk's physical subspace, e.g. by
+                                qw_state_import); a power of two, 0 = auto (2N/8 over all
+                                instances, clamped to [256, 4096]) */
 } qw_sim_opts;
 
 /* Fill *opts with the defaults above. */

@@ -299,7 +299,11 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     wc = std::max<int64_t>(wc, s);
     wc = std::max<int64_t>(wc, d.cap_row);
     d.warp_cap = (int)wc;
-    d.spill_slots = 4096;
+    if (o.spill_rows < 0 || (o.spill_rows & (o.spill_rows - 1)) != 0 || o.spill_rows > (1 << 24)) {
+        g_create_error = "qw_sim_create: spill_rows must be 0 or a power of two <= 2^24";
+        qw_sim_destroy(sim);
+        return QW_ERR_ARG;
+    }
 
     /* per-instance tables and the QRAM image */
     std::vector<int32_t> hn((size_t)ninst);
@@ -313,6 +317,8 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
         buckets += (int64_t)2 << ceil_log2(mats[i].n);
     }
     hbkt[(size_t)ninst] = buckets;
+    d.spill_slots = o.spill_rows > 0 ? o.spill_rows
+                                     : (int)std::min<int64_t>(4096, std::max<int64_t>(256, next_pow2(buckets / 8)));
     d.dense_buckets = buckets;
     d.total_buckets = buckets + d.spill_slots;
     sim->n_of = hn;

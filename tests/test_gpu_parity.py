@@ -423,3 +423,34 @@ def test_garbage_subspace_states_match_oracle(fuse, variant):
         sim.apply_walk_step(1)
         o.apply("W")
         compare(gpu_state(sim), oracle_state(o), TOL64)
+
+
+def test_garbage_row_table_size_is_an_option_and_overflow_is_reported():
+    """The rows with jc != 0 live in a hash table of spill_rows slots: a state
+    with more such rows than slots is refused with QW_ERR_CAPACITY; one table
+    slot per row suffices."""
+    w = wl.small_random(12, 4, 17)
+    rng = np.random.default_rng(7)
+    keys = set()
+    while len(keys) < 200:
+        keys.add((int(rng.integers(1, 4)), int(rng.integers(0, 16)), int(rng.integers(0, 2)),
+                  0, int(rng.integers(0, 16)), int(rng.integers(0, 2))))
+    regs = np.array(sorted(keys), dtype=np.uint64)
+    rows = len({tuple(r[:3]) for r in regs.tolist()})
+    amps = rng.standard_normal(len(regs)) + 0j
+    amps /= np.linalg.norm(amps)
+    full = np.zeros((len(regs), 8), dtype=np.uint64)
+    full[:, :6] = regs
+    small = _sim(w, spill_rows=16)
+    with pytest.raises(qwalk.QwError) as err:
+        small.state_import(small.pack(full), amps)
+    assert err.value.code == qwalk.QW_ERR_CAPACITY and "garbage-row table full" in str(err.value)
+    small.close()
+    fit = _sim(w, spill_rows=int(wl.next_pow2(rows)))
+    fit.state_import(fit.pack(full), amps)
+    o = oracle.Oracle(w.matrix, w.s)
+    o.set_state(regs, amps)
+    compare(gpu_state(fit), oracle_state(o), 0.0)
+    fit.close()
+    with pytest.raises(qwalk.QwError):
+        _sim(w, spill_rows=100)  # not a power of two
