@@ -320,6 +320,7 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     d.spill_slots = o.spill_rows > 0 ? o.spill_rows
                                      : (int)std::min<int64_t>(4096, std::max<int64_t>(256, next_pow2(buckets / 8)));
     d.dense_buckets = buckets;
+    d.n_single = ninst == 1 ? mats[0].n : 0;
     d.total_buckets = buckets + d.spill_slots;
     sim->n_of = hn;
     sim->bkt_of = hbkt;

@@ -55,6 +55,7 @@
 
 struct QwSimDev {
     int nb, s, L, ninst;
+    int n_single;  /* N of the instance when ninst == 1 (tables not read then) */
     int cap_row;   /* branches per bucket */
     int warp_cap;  /* on-chip branches per warp */
     int spill_slots;          /* power of two */

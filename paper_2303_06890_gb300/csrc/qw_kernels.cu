@@ -410,7 +410,8 @@ __device__ int64_t bucket_of(const QwSimDev &d, const QwBufDev &out, uint32_t in
                              uint32_t j, uint32_t b1, int32_t *status)
 {
     if (jc == 0) {
-        const int64_t lo = d.inst_bkt[inst], hi = d.inst_bkt[inst + 1];
+        const int64_t lo = d.ninst == 1 ? 0 : d.inst_bkt[inst];
+        const int64_t hi = d.ninst == 1 ? d.dense_buckets : d.inst_bkt[inst + 1];
         const int64_t b = lo + (((int64_t)j << 1) | (int64_t)b1);
         if (b < hi) return b;
         atomicOr(status, QW_ST_SPILL_FULL);
@@ -431,6 +432,25 @@ __device__ int64_t bucket_of(const QwSimDev &d, const QwBufDev &out, uint32_t in
 
 __device__ bool row_of(const QwSimDev &d, const QwBufDev &in, int64_t b, Row &r)
 {
+    if (d.ninst == 1) { /* one instance: everything from the kernel parameters */
+        if (b < d.dense_buckets) {
+            r.inst = 0;
+            r.jc = 0;
+            r.j = (uint32_t)(b >> 1);
+            r.b1 = (uint32_t)(b & 1);
+        } else {
+            const uint64_t rk = in.spill[b - d.dense_buckets];
+            if (rk == QW_SPILL_EMPTY) return false;
+            r.inst = (uint32_t)(rk >> 40);
+            r.jc = (uint32_t)((rk >> 20) & 0xfffffu);
+            r.j = (uint32_t)((rk >> 1) & 0x7ffffu);
+            r.b1 = (uint32_t)(rk & 1);
+        }
+        r.n_inst = (uint32_t)d.n_single;
+        r.img_base = 0;
+        r.valid = r.j < r.n_inst;
+        return true;
+    }
     if (b < d.dense_buckets) {
         int lo = 0, hi = d.ninst;
         while (hi - lo > 1) {
@@ -682,8 +702,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_step(QwSimDev d, QwBufDev in, Qw
 template <typename AmpT>
 __host__ __device__ inline size_t walk_smem_head(const QwSimDev &d)
 {
-    size_t b = (size_t)d.warp_cap * 2 * (sizeof(uint64_t) + sizeof(AmpT)) + (size_t)d.s * sizeof(AmpT) +
-               (size_t)d.s * sizeof(uint32_t) + (size_t)d.s * sizeof(int16_t);
+    size_t b = (size_t)d.warp_cap * 2 * (sizeof(uint64_t) + sizeof(AmpT)) + (size_t)d.s * 2 * sizeof(AmpT) +
+               (size_t)d.s * sizeof(uint32_t) + (size_t)(d.s + 64) * sizeof(int16_t);
     return (b + 15) & ~(size_t)15;
 }
 
@@ -720,6 +740,7 @@ template <typename AmpT> struct Amp;
 /* complex128 path: FP64 arithmetic throughout */
 template <> struct Amp<double2> {
     typedef double2 T;
+    static constexpr bool kHeadLanes = true; /* rotate with one lane per pair head */
     struct Norm {
         double v = 0.0;
         __device__ void add(T a) { v = fma(a.x, a.x, fma(a.y, a.y, v)); }
@@ -779,6 +800,7 @@ template <> struct Amp<double2> {
    (f, g held as float pairs with ~48 significant bits) and rounded once. */
 template <> struct Amp<float2> {
     typedef float2 T;
+    static constexpr bool kHeadLanes = false;
     struct Norm { /* float-pair accumulator, exact up to ~2^-46 relative */
         float hi = 0.f, lo = 0.f;
         __device__ void add(T a)
@@ -930,77 +952,169 @@ __device__ void Amp<float2>::rot(RotVal t, uint32_t A, bool dag, bool sneg, T a0
     }
 }
 
-/* Load a segment -- the n0 branches of bucket A (b1 = tagA) and the n1 of
- * bucket B (b1 = 1) -- and group it: b2-pairs next to each other, b2 = 0
- * first.  A segment that fits one warp goes straight into registers and is
- * paired by a warp match on key >> 1; a longer one goes through shared memory
- * and is sorted by key (rank of each key among the segment's). */
+/* Pair up to 32 branches held one per lane (valid lanes carry distinct keys):
+ * b2-partners (keys equal but for bit 0) become adjacent, b2 = 0 first, in
+ * kd/ad from position base on.  Returns the number of valid branches. */
 template <typename AmpT>
-__device__ void load_seg(const QwBufDev &in, int64_t bA, int n0, uint64_t tagA, int64_t bB, int n1,
-                         int cap_row, bool rescale, const typename Amp<AmpT>::Scale &scale,
-                         uint64_t *kd, AmpT *ad, uint64_t *ktmp, AmpT *atmp, bool have, uint64_t hk, AmpT ha)
+__device__ int pair32(uint64_t k, AmpT a, bool valid, uint64_t *kd, AmpT *ad, int base)
 {
     const int lane = lane_id();
-    const int n = n0 + n1;
-    const AmpT *amp = static_cast<const AmpT *>(in.amp);
-    auto fetch = [&](int i, uint64_t &k, AmpT &a) {
-        const int64_t slot = (i < n0) ? bA * (int64_t)cap_row + i : bB * (int64_t)cap_row + (i - n0);
-        k = in.key[slot] | ((i < n0) ? tagA : (1ull << QW_B1_BIT));
-        a = amp[slot];
-    };
-    if (n <= 32) {
-        const bool valid = lane < n;
-        /* inactive lanes get keys whose k >> 1 are distinct and above every real key */
-        uint64_t k = ~0ull - 2ull * (uint64_t)lane;
-        AmpT a = Amp<AmpT>::zero();
-        if (valid) {
-            if (have) {
-                k = hk;
-                a = ha;
-            } else {
-                fetch(lane, k, a);
-            }
-            if (rescale) a = scale.apply(a);
+    /* inactive lanes get keys whose k >> 1 are distinct and above every real key */
+    if (!valid) k = ~0ull - 2ull * (uint64_t)lane;
+    const unsigned m = __match_any_sync(FULL, k >> 1);
+    const unsigned other = m & ~(1u << lane);
+    const bool head = valid && ((k & 1) == 0 || other == 0);
+    const int cnt = head ? (other ? 2 : 1) : 0;
+    int total;
+    const int pos = base + warp_compact2(head, cnt == 2, total);
+    const int src = other ? (__ffs(other) - 1) : lane;
+    const uint64_t pk = __shfl_sync(FULL, k, src);
+    AmpT pa;
+    pa.x = __shfl_sync(FULL, a.x, src);
+    pa.y = __shfl_sync(FULL, a.y, src);
+    if (head) {
+        kd[pos] = k;
+        ad[pos] = a;
+        if (cnt == 2) {
+            kd[pos + 1] = pk;
+            ad[pos + 1] = pa;
         }
-        const unsigned m = __match_any_sync(FULL, k >> 1);
-        const unsigned other = m & ~(1u << lane);
-        const bool head = valid && ((k & 1) == 0 || other == 0);
-        const int cnt = head ? (other ? 2 : 1) : 0;
-        int total;
-        const int pos = warp_compact2(head, cnt == 2, total);
-        const int src = other ? (__ffs(other) - 1) : lane;
-        const uint64_t pk = __shfl_sync(FULL, k, src);
-        AmpT pa;
-        pa.x = __shfl_sync(FULL, a.x, src);
-        pa.y = __shfl_sync(FULL, a.y, src);
-        if (head) {
-            kd[pos] = k;
-            ad[pos] = a;
-            if (cnt == 2) {
-                kd[pos + 1] = pk;
-                ad[pos + 1] = pa;
-            }
-        }
-        __syncwarp();
-        return;
     }
-    for (int i = lane; i < n; i += 32) {
+    return total;
+}
+
+/* Load the nr branches of bucket b (b1 tag `tag`) and pair them into kd/ad
+ * from position base on.  nr <= 32: one warp match.  nr <= 64 (and a scratch
+ * of >= 64 entries): split the row in two halves of <= 32 by one key bit
+ * above b2 (partners share every such bit), then one match per half.
+ * Otherwise (or if no bit splits the row evenly enough) sort by key: the rank
+ * of each key among the row's. */
+template <typename AmpT>
+__device__ void pair_row(const QwBufDev &in, int64_t b, int nr, uint64_t tag, int cap_row, bool rescale,
+                         const typename Amp<AmpT>::Scale &scale, uint64_t *kd, AmpT *ad, int base,
+                         uint64_t *ktmp, AmpT *atmp, int cap, bool have, uint64_t hk, AmpT ha)
+{
+    const int lane = lane_id();
+    const AmpT *amp = static_cast<const AmpT *>(in.amp);
+    const int64_t row0 = b * (int64_t)cap_row;
+    auto fetch = [&](int i, uint64_t &k, AmpT &a) {
+        k = in.key[row0 + i] | tag;
+        a = amp[row0 + i];
+        if (rescale) a = scale.apply(a);
+    };
+    if (nr <= 32 || (nr <= 64 && cap >= 64)) {
+        uint64_t k0 = 0, k1 = 0;
+        AmpT a0 = Amp<AmpT>::zero(), a1 = Amp<AmpT>::zero();
+        const bool v0 = lane < nr, v1 = lane + 32 < nr;
+        if (v0) {
+            if (have) {
+                k0 = hk;
+                a0 = rescale ? scale.apply(ha) : ha;
+            } else {
+                fetch(lane, k0, a0);
+            }
+        }
+        if (v1) fetch(lane + 32, k1, a1);
+        if (nr <= 32) {
+            pair32<AmpT>(k0, a0, v0, kd, ad, base);
+            __syncwarp();
+            return;
+        }
+        int t = 1;
+        int c0 = 0;
+        for (; t < 63; ++t) {
+            const bool z0 = v0 && ((k0 >> t) & 1ull) == 0;
+            const bool z1 = v1 && ((k1 >> t) & 1ull) == 0;
+            c0 = __popc(__ballot_sync(FULL, z0)) + __popc(__ballot_sync(FULL, z1));
+            if (c0 <= 32 && nr - c0 <= 32) break;
+        }
+        if (t < 63) {
+            /* halves: bit t = 0 to ktmp[0, c0), bit t = 1 to ktmp[32, 32 + nr - c0) */
+            const bool z0 = ((k0 >> t) & 1ull) == 0, z1 = ((k1 >> t) & 1ull) == 0;
+            const unsigned lt = (1u << lane) - 1u;
+            const unsigned bz0 = __ballot_sync(FULL, v0 && z0), bz1 = __ballot_sync(FULL, v1 && z1);
+            const unsigned bo0 = __ballot_sync(FULL, v0 && !z0), bo1 = __ballot_sync(FULL, v1 && !z1);
+            if (v0) {
+                const int q = z0 ? __popc(bz0 & lt) : 32 + __popc(bo0 & lt);
+                ktmp[q] = k0;
+                atmp[q] = a0;
+            }
+            if (v1) {
+                const int q = z1 ? __popc(bz0) + __popc(bz1 & lt) : 32 + __popc(bo0) + __popc(bo1 & lt);
+                ktmp[q] = k1;
+                atmp[q] = a1;
+            }
+            __syncwarp();
+            const bool w0 = lane < c0, w1 = lane < nr - c0;
+            const uint64_t h0 = w0 ? ktmp[lane] : 0ull, h1 = w1 ? ktmp[32 + lane] : 0ull;
+            const AmpT g0 = w0 ? atmp[lane] : Amp<AmpT>::zero();
+            const AmpT g1 = w1 ? atmp[32 + lane] : Amp<AmpT>::zero();
+            __syncwarp();
+            const int m0 = pair32<AmpT>(h0, g0, w0, kd, ad, base);
+            pair32<AmpT>(h1, g1, w1, kd, ad, base + m0);
+            __syncwarp();
+            return;
+        }
+        /* no balanced bit: fall through to the sort (the row reloads) */
+    }
+    for (int i = lane; i < nr; i += 32) {
         uint64_t k;
         AmpT v;
         fetch(i, k, v);
-        if (rescale) v = scale.apply(v);
         ktmp[i] = k;
         atmp[i] = v;
     }
     __syncwarp();
-    for (int i = lane; i < n; i += 32) {
+    for (int i = lane; i < nr; i += 32) {
         const uint64_t ki = ktmp[i];
         int r = 0;
-        for (int t = 0; t < n; ++t) r += (ktmp[t] < ki);
-        kd[r] = ki;
-        ad[r] = atmp[i];
+        for (int t = 0; t < nr; ++t) r += (ktmp[t] < ki);
+        kd[base + r] = ki;
+        ad[base + r] = atmp[i];
     }
     __syncwarp();
+}
+
+/* Load a segment -- the n0 branches of bucket A (b1 = tagA) and the n1 of
+ * bucket B (b1 = 1) -- and group it: b2-pairs next to each other, b2 = 0
+ * first.  Partners never straddle the two rows (they differ in b2 only), so
+ * each row is paired on its own; (have, hk, ha) are A's first 32 branches,
+ * loaded ahead by the pipelined loop. */
+template <typename AmpT>
+__device__ void load_seg(const QwBufDev &in, int64_t bA, int n0, uint64_t tagA, int64_t bB, int n1,
+                         int cap_row, bool rescale, const typename Amp<AmpT>::Scale &scale,
+                         uint64_t *kd, AmpT *ad, uint64_t *ktmp, AmpT *atmp, int cap, bool have, uint64_t hk,
+                         AmpT ha)
+{
+    const int n = n0 + n1;
+    if (n <= 32) { /* both rows in one warp match (the b1 tag keeps them apart) */
+        const int lane = lane_id();
+        uint64_t k = 0;
+        AmpT a = Amp<AmpT>::zero();
+        if (lane < n0) {
+            if (have) {
+                k = hk;
+                a = ha;
+            } else {
+                const int64_t slot = bA * (int64_t)cap_row + lane;
+                k = in.key[slot] | tagA;
+                a = static_cast<const AmpT *>(in.amp)[slot];
+            }
+        } else if (lane < n) {
+            const int64_t slot = bB * (int64_t)cap_row + (lane - n0);
+            k = in.key[slot] | (1ull << QW_B1_BIT);
+            a = static_cast<const AmpT *>(in.amp)[slot];
+        }
+        if (rescale && lane < n) a = scale.apply(a);
+        pair32<AmpT>(k, a, lane < n, kd, ad, 0);
+        __syncwarp();
+        return;
+    }
+    if (n0 > 0)
+        pair_row<AmpT>(in, bA, n0, tagA, cap_row, rescale, scale, kd, ad, 0, ktmp, atmp, cap, have, hk, ha);
+    if (n1 > 0)
+        pair_row<AmpT>(in, bB, n1, 1ull << QW_B1_BIT, cap_row, rescale, scale, kd, ad, n0, ktmp, atmp, cap,
+                       false, 0ull, Amp<AmpT>::zero());
 }
 
 
@@ -1013,24 +1127,29 @@ __device__ __forceinline__ uint64_t map_t(const QwSimDev &d, const Row &r, uint6
  * pair head maps the key once for both members; the rotation is controlled
  * by the A field and the sign bit of the mapped key, and the outputs (pair-
  * adjacent) keep only b2, k and kc: A is back to 0. */
-template <int WHICH, typename AmpT>
+template <int WHICH, typename AmpT, bool REFL = false>
 __device__ int map_rot_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, const AmpT *as,
-                             int n, uint64_t *kd, AmpT *ad, int cap, int32_t *status)
+                             int n, uint64_t *kd, AmpT *ad, int cap, int32_t *status, int16_t *hidx,
+                             AmpT *zbuf = nullptr, AmpT *z1buf = nullptr, int16_t *pbuf = nullptr,
+                             int *diverted = nullptr)
 {
     const int lane = lane_id();
     const int ash = 1 + 2 * d.nb;
     const uint64_t keep_mask = (1ull << ash) - 1; /* b2 | k | kc */
-    int out = 0;
-    for (int base = 0; base < n; base += 32) {
-        const int i = base + lane;
-        const bool valid = i < n;
-        const uint64_t k = valid ? ks[i] : 0;
-        const bool is_end = valid && i > 0 && ks[i - 1] == (k ^ 1ull);
-        const bool head = valid && !is_end;
+    /* H P H folded in (REFL): k_high | kc | b1 all zero in a row with jc = 0
+       marks the zero-type Hadamard groups (b2 = 0: the reflected group;
+       b2 = 1: negated, kept beside it); every other branch is negated here */
+    const uint64_t zm = (((1ull << ash) - 1) & ~((1ull << (d.L + 1)) - 1)) | (1ull << QW_B1_BIT);
+    const bool rowzero = REFL && r.jc == 0;
+    int out = 0, div = 0;
+    /* branch i heads its pair (a b2 = 0 branch, or a b2 = 1 one without its
+       partner): map the key once, rotate both members, append the kept ones */
+    auto pair_at = [&](int i, bool head) {
         AmpT o0 = Amp<AmpT>::zero(), o1 = Amp<AmpT>::zero();
         bool c0 = false, c1 = false;
         uint64_t kb = 0;
         if (head) {
+            const uint64_t k = ks[i];
             AmpT a0 = Amp<AmpT>::zero(), a1 = Amp<AmpT>::zero();
             if ((k & 1ull) == 0) {
                 a0 = as[i];
@@ -1054,6 +1173,22 @@ __device__ int map_rot_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
             c1 = Amp<AmpT>::keep(d, o1);
             kb = (mk & keep_mask) | b1bit;
         }
+        if (REFL) {
+            const bool zt = head && rowzero && (kb & zm) == 0;
+            div += __popc(__ballot_sync(FULL, zt && c0)) + __popc(__ballot_sync(FULL, zt && c1));
+            if (zt) {
+                const int u = (int)((kb >> 1) & (uint64_t)(d.s - 1));
+                if (c0) zbuf[u] = o0;
+                if (c1) {
+                    z1buf[u] = Amp<AmpT>::neg(o1);
+                    pbuf[u] = 1;
+                }
+                c0 = c1 = false;
+            } else {
+                o0 = Amp<AmpT>::neg(o0);
+                o1 = Amp<AmpT>::neg(o1);
+            }
+        }
         int total;
         int pos = out + warp_compact2(c0, c1, total);
         if (c0) {
@@ -1064,8 +1199,35 @@ __device__ int map_rot_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
             if (pos < cap) { kd[pos] = kb | 1ull; ad[pos] = o1; }
         }
         out += total;
+    };
+    auto is_head = [&](int i) {
+        return i < n && !(i > 0 && ks[i - 1] == (ks[i] ^ 1ull));
+    };
+    if (Amp<AmpT>::kHeadLanes) {
+        /* blocks of 64 branches: list the heads, then one lane per head, so no
+           lane idles through the (FP64) rotation for a pair's second member */
+        const unsigned lt = (1u << lane) - 1u;
+        for (int base = 0; base < n; base += 64) {
+            int nh = 0;
+            for (int half = 0; half < 64; half += 32) {
+                const int i = base + half + lane;
+                const bool head = is_head(i);
+                const unsigned hm = __ballot_sync(FULL, head);
+                if (head) hidx[nh + __popc(hm & lt)] = (int16_t)i;
+                nh += __popc(hm);
+            }
+            __syncwarp();
+            for (int hb = 0; hb < nh; hb += 32) {
+                const bool head = hb + lane < nh;
+                pair_at(head ? hidx[hb + lane] : 0, head);
+            }
+            __syncwarp();
+        }
+    } else {
+        for (int base = 0; base < n; base += 32) pair_at(base + lane, is_head(base + lane));
+        __syncwarp();
     }
-    __syncwarp();
+    if (REFL) *diverted = div;
     if (out > cap) {
         if (lane == 0) atomicOr(status, QW_ST_WARP_OVERFLOW);
         out = cap;
@@ -1073,97 +1235,58 @@ __device__ int map_rot_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
     return out;
 }
 
-/* H P H of one walk step without sorting (keys (l, z, A = 0, b2), pairs
- * adjacent).  P keeps the sign of the all-zero branch only, so a Hadamard
- * group (registers fixed except the low L bits of k) is either zero-type --
- * row jc = b1 = 0 and kc = k_high = b2 = 0 -- where H P H = 2|+><+| - 1 maps
- * a_u -> (2/s) sum_v a_v - a_u for all s values of u, or H P H = -1.  Since A
- * is zero here, a row has at most one zero-type group.  Output: the other
- * branches negated in their order, then the s outputs (u, b2 = 0), each
- * followed by its b2 = 1 partner.  The group sum is FP64 for complex128 and
- * a float pair (error-free two-sums, ~48 bits) for complex64.  With readout,
- * (1/sqrt s) sum_v a_v -- the flag-0 amplitude of T~^dag's output -- goes into
- * the QLS accumulator. */
+/* The zero-type Hadamard group of H P H, after T~^dag's rotation has negated
+ * every other branch and set the group aside (map_rot_pairs with REFL): in a
+ * row with jc = b1 = 0, the group (kc = k_high = b2 = 0) maps a_u ->
+ * (2/s) sum_v a_v - a_u for all s values of u (H P H = 2|+><+| - 1 there).
+ * Appends the s outputs (u, b2 = 0), each followed by its negated b2 = 1
+ * partner when present, to kd/ad after the n branches already there.  The
+ * sum is taken by u in a fixed order (FP64 for complex128, a float pair for
+ * complex64); with readout, (1/sqrt s) sum_v a_v -- the flag-0 amplitude of
+ * T~^dag's output -- goes into the QLS accumulator. */
 template <typename AmpT>
-__device__ int reflect_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, const AmpT *as,
-                             int n, uint64_t *kd, AmpT *ad, int cap, int32_t *status,
-                             const QwStepArgs &a, AmpT *zbuf, int16_t *pbuf)
+__device__ int reflect_zero(const QwSimDev &d, const Row &r, uint64_t *kd, AmpT *ad, int n, int cap,
+                            int32_t *status, const QwStepArgs &a, const AmpT *zbuf, const AmpT *z1buf,
+                            const int16_t *pbuf)
 {
+    if (r.jc != 0) return n;
     const int lane = lane_id();
     const int s = d.s;
-    const uint64_t zm = (((1ull << (1 + 2 * d.nb)) - 1) & ~((1ull << (d.L + 1)) - 1)) |
-                        (1ull << QW_B1_BIT); /* k_high | kc | b1 */
-    const bool rowzero = (r.jc == 0);
-    if (rowzero) {
-        for (int t = lane; t < s; t += 32) {
-            zbuf[t] = Amp<AmpT>::zero();
-            pbuf[t] = -1;
-        }
-        __syncwarp();
-    }
-    int out = 0;
     typename Amp<AmpT>::Sum sum;
-    for (int base = 0; base < n; base += 32) {
-        const int i = base + lane;
-        const bool valid = i < n;
-        const uint64_t k = valid ? ks[i] : 0;
-        const bool zp = valid && rowzero && (k & zm) == 0;
-        const AmpT v = valid ? as[i] : Amp<AmpT>::zero();
-        if (zp) {
-            const int u = (int)((k >> 1) & (uint64_t)(s - 1));
-            if ((k & 1ull) == 0) {
-                zbuf[u] = v;
-            } else {
-                pbuf[u] = (int16_t)i;
-            }
+    for (int t = lane; t < s; t += 32) sum.add(zbuf[t]);
+    sum.reduce(s);
+    if (a.qls_readout && r.valid && lane == 0) {
+        const double2 sv = sum.value();
+        const double coef = a.qls_coefs[*a.qls_j];
+        double2 acc = a.qls_y[r.j];
+        acc.x += coef * (d.inv_sqrt_s * sv.x);
+        acc.y += coef * (d.inv_sqrt_s * sv.y);
+        a.qls_y[r.j] = acc;
+    }
+    sum.scale_pow2(d.two_over_s);
+    int out = n;
+    for (int ub = 0; ub < s; ub += 32) {
+        const int u = ub + lane;
+        const bool vu = u < s;
+        AmpT o0 = Amp<AmpT>::zero();
+        bool c1 = false;
+        if (vu) {
+            o0 = sum.minus(zbuf[u]);
+            c1 = pbuf[u] > 0;
         }
-        const bool c = valid && !zp && Amp<AmpT>::keep(d, v);
+        const bool c0 = vu && Amp<AmpT>::keep(d, o0);
         int total;
-        const int pos = out + warp_compact2(c, false, total);
-        if (c && pos < cap) {
-            kd[pos] = k;
-            ad[pos] = Amp<AmpT>::neg(v);
+        int pos = out + warp_compact2(c0, c1, total);
+        const uint64_t k0 = (uint64_t)u << 1;
+        if (c0) {
+            if (pos < cap) { kd[pos] = k0; ad[pos] = o0; }
+            pos++;
+        }
+        if (c1 && pos < cap) {
+            kd[pos] = k0 | 1ull;
+            ad[pos] = z1buf[u];
         }
         out += total;
-    }
-    if (rowzero) {
-        /* sum by u in a fixed order, whatever order the row's branches came in */
-        __syncwarp();
-        for (int t = lane; t < s; t += 32) sum.add(zbuf[t]);
-        sum.reduce(s);
-        if (a.qls_readout && r.valid && lane == 0) {
-            const double2 sv = sum.value();
-            const double coef = a.qls_coefs[*a.qls_j];
-            double2 acc = a.qls_y[r.j];
-            acc.x += coef * (d.inv_sqrt_s * sv.x);
-            acc.y += coef * (d.inv_sqrt_s * sv.y);
-            a.qls_y[r.j] = acc;
-        }
-        sum.scale_pow2(d.two_over_s);
-        for (int ub = 0; ub < s; ub += 32) {
-            const int u = ub + lane;
-            const bool vu = u < s;
-            AmpT o0 = Amp<AmpT>::zero();
-            int p = -1;
-            if (vu) {
-                o0 = sum.minus(zbuf[u]);
-                p = pbuf[u];
-            }
-            const bool c0 = vu && Amp<AmpT>::keep(d, o0);
-            const bool c1 = p >= 0;
-            int total;
-            int pos = out + warp_compact2(c0, c1, total);
-            const uint64_t k0 = (uint64_t)u << 1;
-            if (c0) {
-                if (pos < cap) { kd[pos] = k0; ad[pos] = o0; }
-                pos++;
-            }
-            if (c1 && pos < cap) {
-                kd[pos] = k0 | 1ull;
-                ad[pos] = Amp<AmpT>::neg(as[p]);
-            }
-            out += total;
-        }
     }
     __syncwarp();
     if (out > cap) {
@@ -1218,36 +1341,45 @@ template <typename AmpT>
 __device__ void emit_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, const AmpT *as, int n,
                            const QwBufDev &out, int32_t *status, typename Amp<AmpT>::Norm &nrm)
 {
-    const int64_t blo = d.inst_bkt[r.inst], bhi = d.inst_bkt[r.inst + 1];
+    const int64_t blo = d.ninst == 1 ? 0 : d.inst_bkt[r.inst];
+    const int64_t bhi = d.ninst == 1 ? d.dense_buckets : d.inst_bkt[r.inst + 1];
     Regs y;
     y.kc = r.jc;
     y.k = r.j;
     y.b2 = 0;
     y.A = 0;
     const uint64_t local0 = encode_r(y, d.nb);
-    for (int i = lane_id(); i < n; i += 32) {
+    /* destination bucket of branch i (-1: dropped with a status bit) */
+    auto dest = [&](int i) -> int64_t {
         const Regs x = decode_r(ks[i], d.nb);
-        const uint64_t local = local0 | ((ks[i] >> QW_B1_BIT) & 1ull); /* new b2 = old b1 */
-        int64_t b;
         if (x.kc == 0) {
-            b = blo + (((int64_t)x.k << 1) | (int64_t)x.b2);
-            if (b >= bhi) {
-                atomicOr(status, QW_ST_SPILL_FULL);
-                continue;
-            }
-        } else {
-            b = bucket_of(d, out, r.inst, x.kc, x.k, x.b2, status);
-            if (b < 0) continue;
+            const int64_t b = blo + (((int64_t)x.k << 1) | (int64_t)x.b2);
+            if (b < bhi) return b;
+            atomicOr(status, QW_ST_SPILL_FULL);
+            return -1;
         }
-        const int pos = atomicAdd(out.count + b, 1);
+        return bucket_of(d, out, r.inst, x.kc, x.k, x.b2, status);
+    };
+    auto put = [&](int i, int64_t b, int pos) {
         if (pos >= d.cap_row) {
             atomicOr(status, QW_ST_ROW_OVERFLOW);
-            continue;
+            return;
         }
         const int64_t slot = b * (int64_t)d.cap_row + pos;
-        out.key[slot] = local;
+        out.key[slot] = local0 | ((ks[i] >> QW_B1_BIT) & 1ull); /* new b2 = old b1 */
         static_cast<AmpT *>(out.amp)[slot] = as[i];
         nrm.add(as[i]);
+    };
+    /* two branches per lane per pass: both slot claims are in flight before
+       either store waits on its claim */
+    for (int i0 = lane_id(); i0 < n; i0 += 64) {
+        const int i1 = i0 + 32;
+        const int64_t b0 = dest(i0);
+        const int64_t b1 = i1 < n ? dest(i1) : -1;
+        const int p0 = b0 >= 0 ? atomicAdd(out.count + b0, 1) : 0;
+        const int p1 = b1 >= 0 ? atomicAdd(out.count + b1, 1) : 0;
+        if (b0 >= 0) put(i0, b0, p0);
+        if (b1 >= 0) put(i1, b1, p1);
     }
 }
 
@@ -1273,8 +1405,10 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
     AmpT *aP = reinterpret_cast<AmpT *>(kQ + C);
     AmpT *aQ = aP + C;
     AmpT *zbuf = aQ + C;
-    uint32_t *simg = reinterpret_cast<uint32_t *>(zbuf + d.s);
+    AmpT *z1buf = zbuf + d.s;
+    uint32_t *simg = reinterpret_cast<uint32_t *>(z1buf + d.s);
     int16_t *pbuf = reinterpret_cast<int16_t *>(simg + d.s);
+    int16_t *hidx = pbuf + d.s;
     typedef typename Amp<AmpT>::RotVal RotVal;
     RotVal *sfg = reinterpret_cast<RotVal *>(base + walk_smem_head<AmpT>(d));
 
@@ -1378,26 +1512,32 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
         }
         st_rows++;
         st_in += n;
-        load_seg<AmpT>(in, it.bA, it.n0, it.tagA, it.bB, it.n1, d.cap_row, rescale, scale, kP, aP, kQ, aQ,
+        load_seg<AmpT>(in, it.bA, it.n0, it.tagA, it.bB, it.n1, d.cap_row, rescale, scale, kP, aP, kQ, aQ, C,
                        have_cur, hk, ha);
         if (PF && cur.valid) { /* the next item's branches, while this one is processed */
-            const int nn = cur.n0 + cur.n1;
-            have = nn > 0 && nn <= 32;
-            if (have && lane < nn) {
-                const bool fromA = lane < cur.n0;
-                const int64_t slot = fromA ? cur.bA * (int64_t)d.cap_row + lane
-                                           : cur.bB * (int64_t)d.cap_row + (lane - cur.n0);
-                pk = in.key[slot] | (fromA ? cur.tagA : (1ull << QW_B1_BIT));
+            have = cur.n0 > 0;
+            if (have && lane < cur.n0) { /* the first 32 of the next item's row A */
+                const int64_t slot = cur.bA * (int64_t)d.cap_row + lane;
+                pk = in.key[slot] | cur.tagA;
                 pa = static_cast<const AmpT *>(in.amp)[slot];
             }
         }
-        n = map_rot_pairs<0, AmpT>(d, r, kP, aP, n, kQ, aQ, C, a.status);      /* T~^dag */
-        st_rdag += n;
-        n = reflect_pairs<AmpT>(d, r, kQ, aQ, n, kP, aP, C, a.status, a, zbuf, pbuf); /* H P H */
+        if (r.jc == 0) { /* the zero-type group's slots, filled by T~^dag */
+            for (int t = lane; t < d.s; t += 32) {
+                zbuf[t] = Amp<AmpT>::zero();
+                pbuf[t] = -1;
+            }
+            __syncwarp();
+        }
+        int nz = 0;
+        n = map_rot_pairs<0, AmpT, true>(d, r, kP, aP, n, kQ, aQ, C, a.status, hidx, zbuf, z1buf, pbuf,
+                                         &nz);                                 /* T~^dag, H P H signs */
+        st_rdag += n + nz;
+        n = reflect_zero<AmpT>(d, r, kQ, aQ, n, C, a.status, a, zbuf, z1buf, pbuf); /* H P H */
         st_hph += n;
-        n = map_rot_pairs<1, AmpT>(d, r, kP, aP, n, kQ, aQ, C, a.status);      /* T~ */
+        n = map_rot_pairs<1, AmpT>(d, r, kQ, aQ, n, kP, aP, C, a.status, hidx); /* T~ */
         st_out += n;
-        emit_pairs<AmpT>(d, r, kQ, aQ, n, out, a.status, nrm);                 /* S */
+        emit_pairs<AmpT>(d, r, kP, aP, n, out, a.status, nrm);                 /* S */
         __syncwarp();
     }
     if (a.stats && lane == 0 && st_rows) {
@@ -1429,7 +1569,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_tinit(QwSimDev d, QwBufDev buf, 
     AmpT *aP = reinterpret_cast<AmpT *>(kQ + C);
     AmpT *aQ = aP + C;
     AmpT *zbuf = aQ + C;
-    uint32_t *simg = reinterpret_cast<uint32_t *>(zbuf + d.s);
+    AmpT *z1buf = zbuf + d.s;
+    uint32_t *simg = reinterpret_cast<uint32_t *>(z1buf + d.s);
+    int16_t *hidx = reinterpret_cast<int16_t *>(simg + d.s) + d.s;
     for (int64_t b = lo + (int64_t)blockIdx.x * WARPS + warp; b < hi; b += (int64_t)gridDim.x * WARPS) {
         const int n = buf.count[b];
         if (n <= 0) continue;
@@ -1456,7 +1598,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_tinit(QwSimDev d, QwBufDev buf, 
             m = d.s;
         }
         __syncwarp();
-        m = map_rot_pairs<1, AmpT>(d, r, kP, aP, m, kQ, aQ, C, status);
+        m = map_rot_pairs<1, AmpT>(d, r, kP, aP, m, kQ, aQ, C, status, hidx);
         /* write back in place: the row keeps its registers (jc, j, b1) */
         for (int i = lane; i < m && i < d.cap_row; i += 32) {
             buf.key[row0 + i] = kQ[i];
