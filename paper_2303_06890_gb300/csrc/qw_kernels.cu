@@ -699,18 +699,46 @@ __global__ void __launch_bounds__(WARPS * 32) k_step(QwSimDev d, QwBufDev in, Qw
 /* per-warp shared memory of the fused kernels: keys x2, amps x2, zero-group
  * buffer, staged QRAM row, partner indices, then (16-byte aligned) the
  * staged rotation values of the row's s slots */
-template <typename AmpT>
-__host__ __device__ inline size_t walk_smem_head(const QwSimDev &d)
-{
-    size_t b = (size_t)d.warp_cap * 2 * (sizeof(uint64_t) + sizeof(AmpT)) + (size_t)d.s * 2 * sizeof(AmpT) +
-               (size_t)d.s * sizeof(uint32_t) + (size_t)(d.s + 64) * sizeof(int16_t);
-    return (b + 15) & ~(size_t)15;
-}
+/* In-kernel key of the fused step: b2 (bit 0) | k (nb bits) | kc (nb bits),
+ * and the row's b1 as a tag bit; the A register is never held in it (0
+ * between steps; the maps return it beside the key).  32-bit keys whenever
+ * 1 + 2 nb <= 29 (N <= 16384), which halves the key traffic on chip and keeps
+ * the key arithmetic on 32-bit operations; 64-bit keys otherwise. */
+template <typename KeyT> struct KeyB1;
+template <> struct KeyB1<uint64_t> { static constexpr int bit = QW_B1_BIT; };
+template <> struct KeyB1<uint32_t> { static constexpr int bit = 31; };
 
-template <typename AmpT>
-__host__ __device__ inline size_t walk_smem_per_warp(const QwSimDev &d)
+__host__ __device__ inline bool key32_fits(const QwSimDev &d) { return 1 + 2 * d.nb <= 29; }
+
+/* per-warp shared memory of the fused kernels (byte offsets, 16-byte aligned):
+ * keys x2, amplitudes x2, the zero-type group (b2 = 0 values, b2 = 1 values,
+ * presence), the staged QRAM row, pair-head indices, the row's rotation values */
+struct WalkLayout {
+    size_t kP, kQ, aP, aQ, zbuf, z1buf, simg, pbuf, hidx, sfg, per_warp;
+};
+
+template <typename AmpT, typename KeyT>
+__host__ __device__ inline WalkLayout walk_layout(const QwSimDev &d)
 {
-    return walk_smem_head<AmpT>(d) + (size_t)d.s * 16;
+    WalkLayout o;
+    size_t p = 0;
+    const size_t C = (size_t)d.warp_cap, s = (size_t)d.s;
+#define QW_TAKE(field, bytes)                                                                      \
+    o.field = p;                                                                                   \
+    p = (p + (bytes) + 15) & ~(size_t)15
+    QW_TAKE(kP, C * sizeof(KeyT));
+    QW_TAKE(kQ, C * sizeof(KeyT));
+    QW_TAKE(aP, C * sizeof(AmpT));
+    QW_TAKE(aQ, C * sizeof(AmpT));
+    QW_TAKE(zbuf, s * sizeof(AmpT));
+    QW_TAKE(z1buf, s * sizeof(AmpT));
+    QW_TAKE(simg, s * sizeof(uint32_t));
+    QW_TAKE(pbuf, s * sizeof(int16_t));
+    QW_TAKE(hidx, 64 * sizeof(int16_t));
+    QW_TAKE(sfg, s * 16);
+#undef QW_TAKE
+    o.per_warp = p;
+    return o;
 }
 
 /* ==== fused walk step: one sort per row, b2-pairs kept adjacent ============== */
@@ -955,20 +983,21 @@ __device__ void Amp<float2>::rot(RotVal t, uint32_t A, bool dag, bool sneg, T a0
 /* Pair up to 32 branches held one per lane (valid lanes carry distinct keys):
  * b2-partners (keys equal but for bit 0) become adjacent, b2 = 0 first, in
  * kd/ad from position base on.  Returns the number of valid branches. */
-template <typename AmpT>
-__device__ int pair32(uint64_t k, AmpT a, bool valid, uint64_t *kd, AmpT *ad, int base)
+template <typename AmpT, typename KeyT>
+__device__ int pair32(KeyT k, AmpT a, bool valid, KeyT *kd, AmpT *ad, int base)
 {
     const int lane = lane_id();
-    /* inactive lanes get keys whose k >> 1 are distinct and above every real key */
-    if (!valid) k = ~0ull - 2ull * (uint64_t)lane;
-    const unsigned m = __match_any_sync(FULL, k >> 1);
+    /* inactive lanes get keys whose k >> 1 are distinct and above every real
+       key (real keys stay below the b1 tag bit plus 2^(1 + 2 nb)) */
+    if (!valid) k = (KeyT)~(KeyT)0 - (KeyT)(2 * lane);
+    const unsigned m = __match_any_sync(FULL, (KeyT)(k >> 1));
     const unsigned other = m & ~(1u << lane);
     const bool head = valid && ((k & 1) == 0 || other == 0);
     const int cnt = head ? (other ? 2 : 1) : 0;
     int total;
     const int pos = base + warp_compact2(head, cnt == 2, total);
     const int src = other ? (__ffs(other) - 1) : lane;
-    const uint64_t pk = __shfl_sync(FULL, k, src);
+    const KeyT pk = __shfl_sync(FULL, k, src);
     AmpT pa;
     pa.x = __shfl_sync(FULL, a.x, src);
     pa.y = __shfl_sync(FULL, a.y, src);
@@ -983,32 +1012,42 @@ __device__ int pair32(uint64_t k, AmpT a, bool valid, uint64_t *kd, AmpT *ad, in
     return total;
 }
 
+/* A stored branch (R layout, 64 bits) as an in-kernel key: b2 | k | kc plus
+ * the b1 tag; A (bits ash..) must be 0 and is reported through anc if not. */
+template <typename KeyT>
+__device__ __forceinline__ KeyT in_key(uint64_t raw, int ash, KeyT tag, uint64_t &anc)
+{
+    anc |= raw >> ash;
+    return (KeyT)(raw & ((1ull << ash) - 1)) | tag;
+}
+
 /* Load the nr branches of bucket b (b1 tag `tag`) and pair them into kd/ad
  * from position base on.  nr <= 32: one warp match.  nr <= 64 (and a scratch
  * of >= 64 entries): split the row in two halves of <= 32 by one key bit
  * above b2 (partners share every such bit), then one match per half.
  * Otherwise (or if no bit splits the row evenly enough) sort by key: the rank
- * of each key among the row's. */
-template <typename AmpT>
-__device__ void pair_row(const QwBufDev &in, int64_t b, int nr, uint64_t tag, int cap_row, bool rescale,
-                         const typename Amp<AmpT>::Scale &scale, uint64_t *kd, AmpT *ad, int base,
-                         uint64_t *ktmp, AmpT *atmp, int cap, bool have, uint64_t hk, AmpT ha)
+ * of each key among the row's.  (have, hraw, ha): the row's first 32 stored
+ * branches, loaded ahead. */
+template <typename AmpT, typename KeyT>
+__device__ void pair_row(const QwBufDev &in, int64_t b, int nr, KeyT tag, int cap_row, int ash, bool rescale,
+                         const typename Amp<AmpT>::Scale &scale, KeyT *kd, AmpT *ad, int base, KeyT *ktmp,
+                         AmpT *atmp, int cap, bool have, uint64_t hraw, AmpT ha, uint64_t &anc)
 {
     const int lane = lane_id();
     const AmpT *amp = static_cast<const AmpT *>(in.amp);
     const int64_t row0 = b * (int64_t)cap_row;
-    auto fetch = [&](int i, uint64_t &k, AmpT &a) {
-        k = in.key[row0 + i] | tag;
+    auto fetch = [&](int i, KeyT &k, AmpT &a) {
+        k = in_key<KeyT>(in.key[row0 + i], ash, tag, anc);
         a = amp[row0 + i];
         if (rescale) a = scale.apply(a);
     };
     if (nr <= 32 || (nr <= 64 && cap >= 64)) {
-        uint64_t k0 = 0, k1 = 0;
+        KeyT k0 = 0, k1 = 0;
         AmpT a0 = Amp<AmpT>::zero(), a1 = Amp<AmpT>::zero();
         const bool v0 = lane < nr, v1 = lane + 32 < nr;
         if (v0) {
             if (have) {
-                k0 = hk;
+                k0 = in_key<KeyT>(hraw, ash, tag, anc);
                 a0 = rescale ? scale.apply(ha) : ha;
             } else {
                 fetch(lane, k0, a0);
@@ -1016,21 +1055,22 @@ __device__ void pair_row(const QwBufDev &in, int64_t b, int nr, uint64_t tag, in
         }
         if (v1) fetch(lane + 32, k1, a1);
         if (nr <= 32) {
-            pair32<AmpT>(k0, a0, v0, kd, ad, base);
+            pair32<AmpT, KeyT>(k0, a0, v0, kd, ad, base);
             __syncwarp();
             return;
         }
+        constexpr int KB = 8 * (int)sizeof(KeyT);
         int t = 1;
         int c0 = 0;
-        for (; t < 63; ++t) {
-            const bool z0 = v0 && ((k0 >> t) & 1ull) == 0;
-            const bool z1 = v1 && ((k1 >> t) & 1ull) == 0;
+        for (; t < KB - 1; ++t) {
+            const bool z0 = v0 && ((k0 >> t) & 1) == 0;
+            const bool z1 = v1 && ((k1 >> t) & 1) == 0;
             c0 = __popc(__ballot_sync(FULL, z0)) + __popc(__ballot_sync(FULL, z1));
             if (c0 <= 32 && nr - c0 <= 32) break;
         }
-        if (t < 63) {
+        if (t < KB - 1) {
             /* halves: bit t = 0 to ktmp[0, c0), bit t = 1 to ktmp[32, 32 + nr - c0) */
-            const bool z0 = ((k0 >> t) & 1ull) == 0, z1 = ((k1 >> t) & 1ull) == 0;
+            const bool z0 = ((k0 >> t) & 1) == 0, z1 = ((k1 >> t) & 1) == 0;
             const unsigned lt = (1u << lane) - 1u;
             const unsigned bz0 = __ballot_sync(FULL, v0 && z0), bz1 = __ballot_sync(FULL, v1 && z1);
             const unsigned bo0 = __ballot_sync(FULL, v0 && !z0), bo1 = __ballot_sync(FULL, v1 && !z1);
@@ -1046,19 +1086,19 @@ __device__ void pair_row(const QwBufDev &in, int64_t b, int nr, uint64_t tag, in
             }
             __syncwarp();
             const bool w0 = lane < c0, w1 = lane < nr - c0;
-            const uint64_t h0 = w0 ? ktmp[lane] : 0ull, h1 = w1 ? ktmp[32 + lane] : 0ull;
+            const KeyT h0 = w0 ? ktmp[lane] : (KeyT)0, h1 = w1 ? ktmp[32 + lane] : (KeyT)0;
             const AmpT g0 = w0 ? atmp[lane] : Amp<AmpT>::zero();
             const AmpT g1 = w1 ? atmp[32 + lane] : Amp<AmpT>::zero();
             __syncwarp();
-            const int m0 = pair32<AmpT>(h0, g0, w0, kd, ad, base);
-            pair32<AmpT>(h1, g1, w1, kd, ad, base + m0);
+            const int m0 = pair32<AmpT, KeyT>(h0, g0, w0, kd, ad, base);
+            pair32<AmpT, KeyT>(h1, g1, w1, kd, ad, base + m0);
             __syncwarp();
             return;
         }
         /* no balanced bit: fall through to the sort (the row reloads) */
     }
     for (int i = lane; i < nr; i += 32) {
-        uint64_t k;
+        KeyT k;
         AmpT v;
         fetch(i, k, v);
         ktmp[i] = k;
@@ -1066,7 +1106,7 @@ __device__ void pair_row(const QwBufDev &in, int64_t b, int nr, uint64_t tag, in
     }
     __syncwarp();
     for (int i = lane; i < nr; i += 32) {
-        const uint64_t ki = ktmp[i];
+        const KeyT ki = ktmp[i];
         int r = 0;
         for (int t = 0; t < nr; ++t) r += (ktmp[t] < ki);
         kd[base + r] = ki;
@@ -1077,69 +1117,72 @@ __device__ void pair_row(const QwBufDev &in, int64_t b, int nr, uint64_t tag, in
 
 /* Load a segment -- the n0 branches of bucket A (b1 = tagA) and the n1 of
  * bucket B (b1 = 1) -- and group it: b2-pairs next to each other, b2 = 0
- * first.  Partners never straddle the two rows (they differ in b2 only), so
- * each row is paired on its own; (have, hk, ha) are A's first 32 branches,
- * loaded ahead by the pipelined loop. */
-template <typename AmpT>
-__device__ void load_seg(const QwBufDev &in, int64_t bA, int n0, uint64_t tagA, int64_t bB, int n1,
-                         int cap_row, bool rescale, const typename Amp<AmpT>::Scale &scale,
-                         uint64_t *kd, AmpT *ad, uint64_t *ktmp, AmpT *atmp, int cap, bool have, uint64_t hk,
-                         AmpT ha)
+ * first.  Partners never straddle the two rows (they differ in b2 only), so a
+ * segment that fits one warp is matched at once and a longer one row by row;
+ * (have, hraw, ha) are A's first 32 stored branches, loaded ahead by the
+ * pipelined loop.  A stored key with A != 0 sets the ancilla status bit. */
+template <typename AmpT, typename KeyT>
+__device__ void load_seg(const QwSimDev &d, const QwBufDev &in, int64_t bA, int n0, KeyT tagA, int64_t bB,
+                         int n1, bool rescale, const typename Amp<AmpT>::Scale &scale, KeyT *kd, AmpT *ad,
+                         KeyT *ktmp, AmpT *atmp, int cap, bool have, uint64_t hraw, AmpT ha, int32_t *status)
 {
+    const int lane = lane_id();
+    const int ash = 1 + 2 * d.nb;
+    const KeyT tagB = (KeyT)1 << KeyB1<KeyT>::bit;
     const int n = n0 + n1;
+    uint64_t anc = 0;
     if (n <= 32) { /* both rows in one warp match (the b1 tag keeps them apart) */
-        const int lane = lane_id();
-        uint64_t k = 0;
+        KeyT k = 0;
         AmpT a = Amp<AmpT>::zero();
         if (lane < n0) {
-            if (have) {
-                k = hk;
-                a = ha;
-            } else {
-                const int64_t slot = bA * (int64_t)cap_row + lane;
-                k = in.key[slot] | tagA;
-                a = static_cast<const AmpT *>(in.amp)[slot];
-            }
+            const int64_t slot = bA * (int64_t)d.cap_row + lane;
+            k = in_key<KeyT>(have ? hraw : in.key[slot], ash, tagA, anc);
+            a = have ? ha : static_cast<const AmpT *>(in.amp)[slot];
         } else if (lane < n) {
-            const int64_t slot = bB * (int64_t)cap_row + (lane - n0);
-            k = in.key[slot] | (1ull << QW_B1_BIT);
+            const int64_t slot = bB * (int64_t)d.cap_row + (lane - n0);
+            k = in_key<KeyT>(in.key[slot], ash, tagB, anc);
             a = static_cast<const AmpT *>(in.amp)[slot];
         }
         if (rescale && lane < n) a = scale.apply(a);
-        pair32<AmpT>(k, a, lane < n, kd, ad, 0);
+        pair32<AmpT, KeyT>(k, a, lane < n, kd, ad, 0);
         __syncwarp();
-        return;
+    } else {
+        if (n0 > 0)
+            pair_row<AmpT, KeyT>(in, bA, n0, tagA, d.cap_row, ash, rescale, scale, kd, ad, 0, ktmp, atmp, cap,
+                                 have, hraw, ha, anc);
+        if (n1 > 0)
+            pair_row<AmpT, KeyT>(in, bB, n1, tagB, d.cap_row, ash, rescale, scale, kd, ad, n0, ktmp, atmp, cap,
+                                 false, 0ull, Amp<AmpT>::zero(), anc);
     }
-    if (n0 > 0)
-        pair_row<AmpT>(in, bA, n0, tagA, cap_row, rescale, scale, kd, ad, 0, ktmp, atmp, cap, have, hk, ha);
-    if (n1 > 0)
-        pair_row<AmpT>(in, bB, n1, 1ull << QW_B1_BIT, cap_row, rescale, scale, kd, ad, n0, ktmp, atmp, cap,
-                       false, 0ull, Amp<AmpT>::zero());
+    if (__any_sync(FULL, anc != 0) && lane == 0) atomicOr(status, QW_ST_ANCILLA);
 }
 
 
-__device__ __forceinline__ uint64_t map_tdag(const QwSimDev &d, const Row &r, uint64_t key,
-                                            int32_t *status, uint32_t &slot);
-__device__ __forceinline__ uint64_t map_t(const QwSimDev &d, const Row &r, uint64_t key, uint32_t &slot);
+template <typename KeyT>
+__device__ __forceinline__ KeyT map_tdag(const QwSimDev &d, const Row &r, KeyT key, uint32_t &slot, uint32_t &A,
+                                         bool &sneg);
+template <typename KeyT>
+__device__ __forceinline__ KeyT map_t(const QwSimDev &d, const Row &r, KeyT key, uint32_t &slot, uint32_t &A,
+                                      bool &sneg);
 
 /* The register maps of one half-step followed by R^dag (WHICH = 0, T~^dag) or
  * R (WHICH = 1, T~) on the adjacent b2-pairs.  The maps never read b2, so the
  * pair head maps the key once for both members; the rotation is controlled
  * by the A field and the sign bit of the mapped key, and the outputs (pair-
  * adjacent) keep only b2, k and kc: A is back to 0. */
-template <int WHICH, typename AmpT, bool REFL = false>
-__device__ int map_rot_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, const AmpT *as,
-                             int n, uint64_t *kd, AmpT *ad, int cap, int32_t *status, int16_t *hidx,
+template <int WHICH, typename AmpT, typename KeyT, bool REFL = false>
+__device__ int map_rot_pairs(const QwSimDev &d, const Row &r, const KeyT *ks, const AmpT *as,
+                             int n, KeyT *kd, AmpT *ad, int cap, int32_t *status, int16_t *hidx,
                              AmpT *zbuf = nullptr, AmpT *z1buf = nullptr, int16_t *pbuf = nullptr,
                              int *diverted = nullptr)
 {
     const int lane = lane_id();
     const int ash = 1 + 2 * d.nb;
-    const uint64_t keep_mask = (1ull << ash) - 1; /* b2 | k | kc */
+    const KeyT b1m = (KeyT)1 << KeyB1<KeyT>::bit;
     /* H P H folded in (REFL): k_high | kc | b1 all zero in a row with jc = 0
        marks the zero-type Hadamard groups (b2 = 0: the reflected group;
        b2 = 1: negated, kept beside it); every other branch is negated here */
-    const uint64_t zm = (((1ull << ash) - 1) & ~((1ull << (d.L + 1)) - 1)) | (1ull << QW_B1_BIT);
+    const KeyT zm = ((((KeyT)1 << ash) - 1) & ~(((KeyT)1 << (d.L + 1)) - 1)) | b1m;
     const bool rowzero = REFL && r.jc == 0;
     int out = 0, div = 0;
     /* branch i heads its pair (a b2 = 0 branch, or a b2 = 1 one without its
@@ -1147,37 +1190,38 @@ __device__ int map_rot_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
     auto pair_at = [&](int i, bool head) {
         AmpT o0 = Amp<AmpT>::zero(), o1 = Amp<AmpT>::zero();
         bool c0 = false, c1 = false;
-        uint64_t kb = 0;
+        KeyT kb = 0;
         if (head) {
-            const uint64_t k = ks[i];
+            const KeyT k = ks[i];
             AmpT a0 = Amp<AmpT>::zero(), a1 = Amp<AmpT>::zero();
-            if ((k & 1ull) == 0) {
+            if ((k & (KeyT)1) == 0) {
                 a0 = as[i];
-                if (i + 1 < n && ks[i + 1] == (k | 1ull)) a1 = as[i + 1];
+                if (i + 1 < n && ks[i + 1] == (k | (KeyT)1)) a1 = as[i + 1];
             } else {
                 a1 = as[i];
             }
-            uint32_t slot;
-            const uint64_t b1bit = k & (1ull << QW_B1_BIT);
-            const uint64_t mk = (WHICH == 0) ? map_tdag(d, r, k & ~(1ull | b1bit), status, slot)
-                                             : map_t(d, r, k & ~(1ull | b1bit), slot);
-            const uint32_t A = (uint32_t)(mk >> ash) & 0xffffu;
+            uint32_t slot, A;
+            bool sneg;
+            const KeyT b1bit = k & b1m;
+            const KeyT key = k & ~((KeyT)1 | b1bit);
+            const KeyT mk = (WHICH == 0) ? map_tdag<KeyT>(d, r, key, slot, A, sneg)
+                                         : map_t<KeyT>(d, r, key, slot, A, sneg);
             /* A is 0 or the value of slot `slot` of row j: staged rotation
                values for a slot of this row, the per-code table otherwise */
             typename Amp<AmpT>::RotVal t;
             if (A == 0) t = Amp<AmpT>::rot_zero();
             else if (slot < (uint32_t)d.s && r.sfg) t = static_cast<const typename Amp<AmpT>::RotVal *>(r.sfg)[slot];
             else t = Amp<AmpT>::rot_table(d, A);
-            Amp<AmpT>::rot(t, A, WHICH == 0, (mk >> QW_SNEG_BIT) != 0, a0, a1, o0, o1);
+            Amp<AmpT>::rot(t, A, WHICH == 0, sneg, a0, a1, o0, o1);
             c0 = Amp<AmpT>::keep(d, o0);
             c1 = Amp<AmpT>::keep(d, o1);
-            kb = (mk & keep_mask) | b1bit;
+            kb = mk | b1bit;
         }
         if (REFL) {
             const bool zt = head && rowzero && (kb & zm) == 0;
             div += __popc(__ballot_sync(FULL, zt && c0)) + __popc(__ballot_sync(FULL, zt && c1));
             if (zt) {
-                const int u = (int)((kb >> 1) & (uint64_t)(d.s - 1));
+                const int u = (int)((kb >> 1) & (KeyT)(d.s - 1));
                 if (c0) zbuf[u] = o0;
                 if (c1) {
                     z1buf[u] = Amp<AmpT>::neg(o1);
@@ -1196,12 +1240,12 @@ __device__ int map_rot_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
             pos++;
         }
         if (c1) {
-            if (pos < cap) { kd[pos] = kb | 1ull; ad[pos] = o1; }
+            if (pos < cap) { kd[pos] = kb | (KeyT)1; ad[pos] = o1; }
         }
         out += total;
     };
     auto is_head = [&](int i) {
-        return i < n && !(i > 0 && ks[i - 1] == (ks[i] ^ 1ull));
+        return i < n && !(i > 0 && ks[i - 1] == (ks[i] ^ (KeyT)1));
     };
     if (Amp<AmpT>::kHeadLanes) {
         /* blocks of 64 branches: list the heads, then one lane per head, so no
@@ -1244,8 +1288,8 @@ __device__ int map_rot_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks
  * sum is taken by u in a fixed order (FP64 for complex128, a float pair for
  * complex64); with readout, (1/sqrt s) sum_v a_v -- the flag-0 amplitude of
  * T~^dag's output -- goes into the QLS accumulator. */
-template <typename AmpT>
-__device__ int reflect_zero(const QwSimDev &d, const Row &r, uint64_t *kd, AmpT *ad, int n, int cap,
+template <typename AmpT, typename KeyT>
+__device__ int reflect_zero(const QwSimDev &d, const Row &r, KeyT *kd, AmpT *ad, int n, int cap,
                             int32_t *status, const QwStepArgs &a, const AmpT *zbuf, const AmpT *z1buf,
                             const int16_t *pbuf)
 {
@@ -1277,13 +1321,13 @@ __device__ int reflect_zero(const QwSimDev &d, const Row &r, uint64_t *kd, AmpT 
         const bool c0 = vu && Amp<AmpT>::keep(d, o0);
         int total;
         int pos = out + warp_compact2(c0, c1, total);
-        const uint64_t k0 = (uint64_t)u << 1;
+        const KeyT k0 = (KeyT)u << 1;
         if (c0) {
             if (pos < cap) { kd[pos] = k0; ad[pos] = o0; }
             pos++;
         }
         if (c1 && pos < cap) {
-            kd[pos] = k0 | 1ull;
+            kd[pos] = k0 | (KeyT)1;
             ad[pos] = z1buf[u];
         }
         out += total;
@@ -1301,46 +1345,48 @@ __device__ int reflect_zero(const QwSimDev &d, const Row &r, uint64_t *kd, AmpT 
  * (l, z) = O_s'^dag(k, kc), controlled by A and by the input column k, and the
  * second O_A' undoes the first.  So each branch moves to (l, z) and carries
  * A = [jc = 0, z = 0] a_{j,l} and sigma(j, k) for the rotation; after R^dag the
- * controls are dropped (A = 0).  Input A must be 0 (T~ and T~^dag return it
- * to 0 at the end of every step). */
-__device__ __forceinline__ uint64_t map_tdag(const QwSimDev &d, const Row &r, uint64_t key,
-                                            int32_t *status, uint32_t &slot)
+ * controls are dropped (A = 0).  Input A is 0 (T~ and T~^dag return it to 0
+ * at the end of every step; the loader checks it). */
+template <typename KeyT>
+__device__ __forceinline__ KeyT map_tdag(const QwSimDev &d, const Row &r, KeyT key, uint32_t &slot, uint32_t &A,
+                                         bool &sneg)
 {
-    const Regs x = decode_r(key, d.nb);
-    if (x.A != 0) atomicOr(status, QW_ST_ANCILLA);
-    const uint32_t l = x.kc ^ qbs(d, r, x.k);
+    const uint32_t m = (1u << d.nb) - 1u;
+    const uint32_t k = (uint32_t)(key >> 1) & m, kc = (uint32_t)(key >> (1 + d.nb)) & m;
+    const uint32_t l = kc ^ qbs(d, r, k);
     const uint32_t w = qword(d, r, l);
-    Regs y;
-    y.k = l;
-    y.kc = x.k ^ (w >> 16);
-    y.A = (r.jc == 0 && y.kc == 0) ? (w & 0xffffu) : 0u;
+    const uint32_t z = k ^ (w >> 16);
+    A = (r.jc == 0 && z == 0) ? (w & 0xffffu) : 0u;
     slot = r.valid ? l : 0xffffffffu;
-    y.b2 = x.b2;
-    return encode_r(y, d.nb) | ((uint64_t)(r.j > x.k) << QW_SNEG_BIT);
+    sneg = r.j > k;
+    return (key & (KeyT)1) | ((KeyT)l << 1) | ((KeyT)z << (1 + d.nb));
 }
 
 /* Register maps of T~ after H: O_A', O_s', R, O_s'^dag, O_A', O_s'.  From
  * (l, z): A = [jc = 0, z = 0] a_{j,l}, then O_s' gives (k, kc) =
  * (z ^ K(j,l), l ^ I(j, k)); R is controlled by A and sigma(j, k); the last
  * three maps only return A to 0. */
-__device__ __forceinline__ uint64_t map_t(const QwSimDev &d, const Row &r, uint64_t key, uint32_t &slot)
+template <typename KeyT>
+__device__ __forceinline__ KeyT map_t(const QwSimDev &d, const Row &r, KeyT key, uint32_t &slot, uint32_t &A,
+                                      bool &sneg)
 {
-    const Regs x = decode_r(key, d.nb);
-    const uint32_t w = qword(d, r, x.k);
-    slot = r.valid ? x.k : 0xffffffffu;
-    Regs y;
-    y.A = (r.jc == 0 && x.kc == 0) ? (w & 0xffffu) : 0u;
-    y.k = x.kc ^ (w >> 16);
-    y.kc = x.k ^ qbs(d, r, y.k);
-    y.b2 = x.b2;
-    return encode_r(y, d.nb) | ((uint64_t)(r.j > y.k) << QW_SNEG_BIT);
+    const uint32_t m = (1u << d.nb) - 1u;
+    const uint32_t l = (uint32_t)(key >> 1) & m, z = (uint32_t)(key >> (1 + d.nb)) & m;
+    const uint32_t w = qword(d, r, l);
+    slot = r.valid ? l : 0xffffffffu;
+    A = (r.jc == 0 && z == 0) ? (w & 0xffffu) : 0u;
+    const uint32_t k = z ^ (w >> 16);
+    const uint32_t kc = l ^ qbs(d, r, k);
+    sneg = r.j > k;
+    return (key & (KeyT)1) | ((KeyT)k << 1) | ((KeyT)kc << (1 + d.nb));
 }
 
 /* S, and the append of every branch to the bucket of its new row. */
-template <typename AmpT>
-__device__ void emit_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, const AmpT *as, int n,
+template <typename AmpT, typename KeyT>
+__device__ void emit_pairs(const QwSimDev &d, const Row &r, const KeyT *ks, const AmpT *as, int n,
                            const QwBufDev &out, int32_t *status, typename Amp<AmpT>::Norm &nrm)
 {
+    const uint32_t m = (1u << d.nb) - 1u;
     const int64_t blo = d.ninst == 1 ? 0 : d.inst_bkt[r.inst];
     const int64_t bhi = d.ninst == 1 ? d.dense_buckets : d.inst_bkt[r.inst + 1];
     Regs y;
@@ -1351,14 +1397,16 @@ __device__ void emit_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, 
     const uint64_t local0 = encode_r(y, d.nb);
     /* destination bucket of branch i (-1: dropped with a status bit) */
     auto dest = [&](int i) -> int64_t {
-        const Regs x = decode_r(ks[i], d.nb);
-        if (x.kc == 0) {
-            const int64_t b = blo + (((int64_t)x.k << 1) | (int64_t)x.b2);
+        const KeyT key = ks[i];
+        const uint32_t b2 = (uint32_t)(key & (KeyT)1), k = (uint32_t)(key >> 1) & m;
+        const uint32_t kc = (uint32_t)(key >> (1 + d.nb)) & m;
+        if (kc == 0) {
+            const int64_t b = blo + (((int64_t)k << 1) | (int64_t)b2);
             if (b < bhi) return b;
             atomicOr(status, QW_ST_SPILL_FULL);
             return -1;
         }
-        return bucket_of(d, out, r.inst, x.kc, x.k, x.b2, status);
+        return bucket_of(d, out, r.inst, kc, k, b2, status);
     };
     auto put = [&](int i, int64_t b, int pos) {
         if (pos >= d.cap_row) {
@@ -1366,7 +1414,7 @@ __device__ void emit_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, 
             return;
         }
         const int64_t slot = b * (int64_t)d.cap_row + pos;
-        out.key[slot] = local0 | ((ks[i] >> QW_B1_BIT) & 1ull); /* new b2 = old b1 */
+        out.key[slot] = local0 | (uint64_t)((ks[i] >> KeyB1<KeyT>::bit) & (KeyT)1); /* new b2 = old b1 */
         static_cast<AmpT *>(out.amp)[slot] = as[i];
         nrm.add(as[i]);
     };
@@ -1389,7 +1437,7 @@ __device__ void emit_pairs(const QwSimDev &d, const Row &r, const uint64_t *ks, 
  * turn comes; PF = true: 3 blocks per SM (more registers), the item loop
  * software-pipelined -- the next item's counts read at the start of the
  * current one, its first 32 branches loaded while the current one runs. */
-template <typename AmpT, bool PF, bool SEG>
+template <typename AmpT, bool PF, bool SEG, typename KeyT>
 __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwBufDev in, QwBufDev out,
                                                                  QwBufDev clr, QwStepArgs a)
 {
@@ -1398,19 +1446,19 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
     __shared__ int is_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int C = d.warp_cap;
-    const size_t per_warp = walk_smem_per_warp<AmpT>(d);
-    unsigned char *base = smem + per_warp * warp;
-    uint64_t *kP = reinterpret_cast<uint64_t *>(base);
-    uint64_t *kQ = kP + C;
-    AmpT *aP = reinterpret_cast<AmpT *>(kQ + C);
-    AmpT *aQ = aP + C;
-    AmpT *zbuf = aQ + C;
-    AmpT *z1buf = zbuf + d.s;
-    uint32_t *simg = reinterpret_cast<uint32_t *>(z1buf + d.s);
-    int16_t *pbuf = reinterpret_cast<int16_t *>(simg + d.s);
-    int16_t *hidx = pbuf + d.s;
+    const WalkLayout lay = walk_layout<AmpT, KeyT>(d);
+    unsigned char *base = smem + lay.per_warp * warp;
+    KeyT *kP = reinterpret_cast<KeyT *>(base + lay.kP);
+    KeyT *kQ = reinterpret_cast<KeyT *>(base + lay.kQ);
+    AmpT *aP = reinterpret_cast<AmpT *>(base + lay.aP);
+    AmpT *aQ = reinterpret_cast<AmpT *>(base + lay.aQ);
+    AmpT *zbuf = reinterpret_cast<AmpT *>(base + lay.zbuf);
+    AmpT *z1buf = reinterpret_cast<AmpT *>(base + lay.z1buf);
+    uint32_t *simg = reinterpret_cast<uint32_t *>(base + lay.simg);
+    int16_t *pbuf = reinterpret_cast<int16_t *>(base + lay.pbuf);
+    int16_t *hidx = reinterpret_cast<int16_t *>(base + lay.hidx);
     typedef typename Amp<AmpT>::RotVal RotVal;
-    RotVal *sfg = reinterpret_cast<RotVal *>(base + walk_smem_head<AmpT>(d));
+    RotVal *sfg = reinterpret_cast<RotVal *>(base + lay.sfg);
 
     const bool skip = *(volatile int32_t *)a.status != 0;
     if (!skip) { /* clear X_{t+2} for the step after this one */
@@ -1436,9 +1484,10 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
     struct Item {
         int64_t bA, bB;
         int n0, n1;
-        uint64_t tagA;
+        KeyT tagA;
         bool valid;
     };
+    constexpr int B1 = KeyB1<KeyT>::bit;
     auto item_of = [&](int64_t uu, int part, Item &it) {
         it.valid = uu < units;
         it.n0 = it.n1 = 0;
@@ -1452,13 +1501,13 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
                 it.n1 = min(in.count[it.bB], d.cap_row);
             } else {
                 it.bA = 2 * uu + part;
-                it.tagA = (uint64_t)part << QW_B1_BIT;
+                it.tagA = (KeyT)part << B1;
             }
             it.n0 = min(in.count[it.bA], d.cap_row);
         } else {
             it.bA = d.dense_buckets + (uu - d2);
             it.n0 = min(in.count[it.bA], d.cap_row);
-            if (it.n0 > 0) it.tagA = (uint64_t)(in.spill[uu - d2] & 1ull) << QW_B1_BIT;
+            if (it.n0 > 0) it.tagA = (KeyT)(in.spill[uu - d2] & 1ull) << B1;
         }
     };
     auto advance = [&](int64_t &uu, int &part) {
@@ -1512,13 +1561,13 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
         }
         st_rows++;
         st_in += n;
-        load_seg<AmpT>(in, it.bA, it.n0, it.tagA, it.bB, it.n1, d.cap_row, rescale, scale, kP, aP, kQ, aQ, C,
-                       have_cur, hk, ha);
+        load_seg<AmpT, KeyT>(d, in, it.bA, it.n0, it.tagA, it.bB, it.n1, rescale, scale, kP, aP, kQ, aQ, C,
+                             have_cur, hk, ha, a.status);
         if (PF && cur.valid) { /* the next item's branches, while this one is processed */
             have = cur.n0 > 0;
             if (have && lane < cur.n0) { /* the first 32 of the next item's row A */
                 const int64_t slot = cur.bA * (int64_t)d.cap_row + lane;
-                pk = in.key[slot] | cur.tagA;
+                pk = in.key[slot];
                 pa = static_cast<const AmpT *>(in.amp)[slot];
             }
         }
@@ -1530,14 +1579,14 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
             __syncwarp();
         }
         int nz = 0;
-        n = map_rot_pairs<0, AmpT, true>(d, r, kP, aP, n, kQ, aQ, C, a.status, hidx, zbuf, z1buf, pbuf,
-                                         &nz);                                 /* T~^dag, H P H signs */
+        n = map_rot_pairs<0, AmpT, KeyT, true>(d, r, kP, aP, n, kQ, aQ, C, a.status, hidx, zbuf, z1buf, pbuf,
+                                               &nz);                           /* T~^dag, H P H signs */
         st_rdag += n + nz;
-        n = reflect_zero<AmpT>(d, r, kQ, aQ, n, C, a.status, a, zbuf, z1buf, pbuf); /* H P H */
+        n = reflect_zero<AmpT, KeyT>(d, r, kQ, aQ, n, C, a.status, a, zbuf, z1buf, pbuf); /* H P H */
         st_hph += n;
-        n = map_rot_pairs<1, AmpT>(d, r, kQ, aQ, n, kP, aP, C, a.status, hidx); /* T~ */
+        n = map_rot_pairs<1, AmpT, KeyT>(d, r, kQ, aQ, n, kP, aP, C, a.status, hidx); /* T~ */
         st_out += n;
-        emit_pairs<AmpT>(d, r, kP, aP, n, out, a.status, nrm);                 /* S */
+        emit_pairs<AmpT, KeyT>(d, r, kP, aP, n, out, a.status, nrm);           /* S */
         __syncwarp();
     }
     if (a.stats && lane == 0 && st_rows) {
@@ -1556,22 +1605,21 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
  * single member at u = 0); then the maps and R of T~ as in the step kernel;
  * the row does not change (no S).  A row holding anything else is left to the
  * general sort-based kernel (flagged by *fallback). */
-template <typename AmpT>
+template <typename AmpT, typename KeyT>
 __global__ void __launch_bounds__(WARPS * 32) k_tinit(QwSimDev d, QwBufDev buf, int64_t lo, int64_t hi,
                                                       int32_t *status, int32_t *fallback)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int C = d.warp_cap;
-    unsigned char *base = smem + walk_smem_per_warp<AmpT>(d) * warp;
-    uint64_t *kP = reinterpret_cast<uint64_t *>(base);
-    uint64_t *kQ = kP + C;
-    AmpT *aP = reinterpret_cast<AmpT *>(kQ + C);
-    AmpT *aQ = aP + C;
-    AmpT *zbuf = aQ + C;
-    AmpT *z1buf = zbuf + d.s;
-    uint32_t *simg = reinterpret_cast<uint32_t *>(z1buf + d.s);
-    int16_t *hidx = reinterpret_cast<int16_t *>(simg + d.s) + d.s;
+    const WalkLayout lay = walk_layout<AmpT, KeyT>(d);
+    unsigned char *base = smem + lay.per_warp * warp;
+    KeyT *kP = reinterpret_cast<KeyT *>(base + lay.kP);
+    KeyT *kQ = reinterpret_cast<KeyT *>(base + lay.kQ);
+    AmpT *aP = reinterpret_cast<AmpT *>(base + lay.aP);
+    AmpT *aQ = reinterpret_cast<AmpT *>(base + lay.aQ);
+    uint32_t *simg = reinterpret_cast<uint32_t *>(base + lay.simg);
+    int16_t *hidx = reinterpret_cast<int16_t *>(base + lay.hidx);
     for (int64_t b = lo + (int64_t)blockIdx.x * WARPS + warp; b < hi; b += (int64_t)gridDim.x * WARPS) {
         const int n = buf.count[b];
         if (n <= 0) continue;
@@ -1592,16 +1640,16 @@ __global__ void __launch_bounds__(WARPS * 32) k_tinit(QwSimDev d, QwBufDev buf, 
         int m = 0;
         if (kept) {
             for (int u = lane; u < d.s; u += 32) {
-                kP[u] = (uint64_t)u << 1;
+                kP[u] = (KeyT)u << 1;
                 aP[u] = h;
             }
             m = d.s;
         }
         __syncwarp();
-        m = map_rot_pairs<1, AmpT>(d, r, kP, aP, m, kQ, aQ, C, status, hidx);
+        m = map_rot_pairs<1, AmpT, KeyT>(d, r, kP, aP, m, kQ, aQ, C, status, hidx);
         /* write back in place: the row keeps its registers (jc, j, b1) */
         for (int i = lane; i < m && i < d.cap_row; i += 32) {
-            buf.key[row0 + i] = kQ[i];
+            buf.key[row0 + i] = (uint64_t)kQ[i]; /* b2 | k | kc, A = 0, no b1 tag */
             static_cast<AmpT *>(buf.amp)[row0 + i] = aQ[i];
         }
         if (m > d.cap_row && lane == 0) atomicOr(status, QW_ST_ROW_OVERFLOW);
@@ -1769,13 +1817,13 @@ template <typename AmpT, int MODE> size_t step_smem(const QwSimDev &d)
                             (((size_t)d.s * sizeof(uint32_t) + 15) & ~(size_t)15));
 }
 
-template <typename AmpT, bool PF, bool SEG>
-int walk_grid_t(const QwSimDev &d)
+template <typename AmpT, bool PF, bool SEG, typename KeyT>
+int walk_grid_k(const QwSimDev &d)
 {
-    const size_t sm = (size_t)WARPS * walk_smem_per_warp<AmpT>(d);
-    cudaFuncSetAttribute(k_walk<AmpT, PF, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const size_t sm = (size_t)WARPS * walk_layout<AmpT, KeyT>(d).per_warp;
+    cudaFuncSetAttribute(k_walk<AmpT, PF, SEG, KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<AmpT, PF, SEG>, WARPS * 32, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<AmpT, PF, SEG, KeyT>, WARPS * 32, sm);
     if (per_sm < 1) per_sm = 1;
     int64_t want = (d.total_buckets + WARPS - 1) / WARPS;
     int64_t g = (int64_t)per_sm * qw_sm_count();
@@ -1784,12 +1832,39 @@ int walk_grid_t(const QwSimDev &d)
 }
 
 template <typename AmpT, bool PF, bool SEG>
+int walk_grid_t(const QwSimDev &d)
+{
+    return key32_fits(d) ? walk_grid_k<AmpT, PF, SEG, uint32_t>(d) : walk_grid_k<AmpT, PF, SEG, uint64_t>(d);
+}
+
+template <typename AmpT, bool PF, bool SEG>
 cudaError_t launch_walk_t(const QwSimDev &d, const QwBufDev &in, const QwBufDev &out,
                           const QwBufDev &clr, const QwStepArgs &a, int grid, cudaStream_t st)
 {
-    const size_t sm = (size_t)WARPS * walk_smem_per_warp<AmpT>(d);
-    k_walk<AmpT, PF, SEG><<<grid, WARPS * 32, sm, st>>>(d, in, out, clr, a);
+    if (key32_fits(d)) {
+        const size_t sm = (size_t)WARPS * walk_layout<AmpT, uint32_t>(d).per_warp;
+        k_walk<AmpT, PF, SEG, uint32_t><<<grid, WARPS * 32, sm, st>>>(d, in, out, clr, a);
+    } else {
+        const size_t sm = (size_t)WARPS * walk_layout<AmpT, uint64_t>(d).per_warp;
+        k_walk<AmpT, PF, SEG, uint64_t><<<grid, WARPS * 32, sm, st>>>(d, in, out, clr, a);
+    }
     return cudaGetLastError();
+}
+
+template <typename AmpT>
+size_t walk_smem_bytes(const QwSimDev &d)
+{
+    return (size_t)WARPS * (key32_fits(d) ? walk_layout<AmpT, uint32_t>(d).per_warp
+                                          : walk_layout<AmpT, uint64_t>(d).per_warp);
+}
+
+template <typename AmpT, typename KeyT>
+void launch_tinit_k(const QwSimDev &d, const QwBufDev &buf, int64_t lo, int64_t hi, int grid, int32_t *status,
+                    int32_t *fallback, cudaStream_t st)
+{
+    const size_t sm = (size_t)WARPS * walk_layout<AmpT, KeyT>(d).per_warp;
+    cudaFuncSetAttribute(k_tinit<AmpT, KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_tinit<AmpT, KeyT><<<grid, WARPS * 32, sm, st>>>(d, buf, lo, hi, status, fallback);
 }
 
 template <typename AmpT, int MODE>
@@ -1833,7 +1908,7 @@ size_t qw_step_smem_bytes(const QwSimDev &d, int fp32, int mode)
 {
     if (mode == QW_MODE_WALK_LITERAL || mode == QW_MODE_T)
         return fp32 ? step_smem<float2, QW_MODE_T>(d) : step_smem<double2, QW_MODE_T>(d);
-    return (size_t)WARPS * (fp32 ? walk_smem_per_warp<float2>(d) : walk_smem_per_warp<double2>(d));
+    return fp32 ? walk_smem_bytes<float2>(d) : walk_smem_bytes<double2>(d);
 }
 
 int qw_step_grid(const QwSimDev &d, int fp32, int mode)
@@ -1997,14 +2072,13 @@ cudaError_t qw_launch_tinit(const QwSimDev &d, const QwBufDev &buf, int64_t lo, 
     int grid = (int)((rows + WARPS - 1) / WARPS);
     if (grid > 8 * qw_sm_count()) grid = 8 * qw_sm_count();
     if (grid < 1) grid = 1;
+    const bool k32 = key32_fits(d);
     if (fp32) {
-        const size_t sm = (size_t)WARPS * walk_smem_per_warp<float2>(d);
-        cudaFuncSetAttribute(k_tinit<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_tinit<float2><<<grid, WARPS * 32, sm, st>>>(d, buf, lo, hi, status, fallback);
+        if (k32) launch_tinit_k<float2, uint32_t>(d, buf, lo, hi, grid, status, fallback, st);
+        else launch_tinit_k<float2, uint64_t>(d, buf, lo, hi, grid, status, fallback, st);
     } else {
-        const size_t sm = (size_t)WARPS * walk_smem_per_warp<double2>(d);
-        cudaFuncSetAttribute(k_tinit<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_tinit<double2><<<grid, WARPS * 32, sm, st>>>(d, buf, lo, hi, status, fallback);
+        if (k32) launch_tinit_k<double2, uint32_t>(d, buf, lo, hi, grid, status, fallback, st);
+        else launch_tinit_k<double2, uint64_t>(d, buf, lo, hi, grid, status, fallback, st);
     }
     return cudaGetLastError();
 }

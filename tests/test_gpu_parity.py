@@ -454,3 +454,24 @@ def test_garbage_row_table_size_is_an_option_and_overflow_is_reported():
     fit.close()
     with pytest.raises(qwalk.QwError):
         _sim(w, spill_rows=100)  # not a power of two
+
+
+@pytest.mark.parametrize("n", [20000, 40000])
+@pytest.mark.parametrize("variant", [0, 3])
+def test_walk_with_64bit_in_kernel_keys_matches_oracle(n, variant):
+    """N > 16384 (nb = 15, 16): the step kernel holds its keys in 64 bits
+    instead of 32; walked against the oracle element by element."""
+    from parity import compare_arrays, gpu_arrays, oracle_arrays
+    w = wl.small_random(n, 4, 23, band=1, attempts=n)
+    sim = _sim(w, walk_variant=variant)
+    assert sim.nb >= 15
+    sim.state_init(w.b)
+    o = _oracle(w)
+    o.apply("T")
+    compare_arrays(gpu_arrays(sim), oracle_arrays(o), TOL64)
+    for _ in range(3):
+        sim.apply_walk_step(1)
+        o.apply("W")
+    st = compare_arrays(gpu_arrays(sim), oracle_arrays(o), TOL64)
+    print(f"N={n} variant {variant}: {st}")
+    sim.close()
