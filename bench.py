@@ -266,17 +266,17 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.e2e_jobs):
-        sim_e.state_init(b_host.numpy(), apply_T=True)  # H2D of |b>
-        sim_e.apply_walk_step(steps_per_job)
-        probs_host.numpy()[:] = sim_e.measure_register("j", w.n)  # D2H of the marginal
+        sim_e.state_init(b_host.numpy(), apply_T=True)  # H2D of |b> from pinned memory
+        sim_e.enqueue_walk_steps(steps_per_job)
+        sim_e.measure_register("j", w.n, out=probs_host.numpy())  # D2H of the marginal, synchronises
     torch.cuda.synchronize()
     t_e2e = max_over_ranks(time.perf_counter() - t0)
     sim_e.close()
     e2e = {"value": world * args.e2e_jobs * steps_per_job / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": w.n * 8 / steps_per_job,
            "d2h_bytes_per_step": w.n * 8 / steps_per_job,
-           "job": f"qw_state_init(|b> from pinned host memory, T~) + {steps_per_job} walk steps "
-                  f"+ qw_measure_register(j) to host"}
+           "job": f"qw_state_init(|b> from pinned host memory, T~) + qw_enqueue_walk_steps({steps_per_job}) "
+                  f"+ qw_measure_register(j) into pinned host memory"}
 
     batched = None if args.no_batched else batched_leg(args, torch, flush, barrier, max_over_ranks,
                                                        world, rank)

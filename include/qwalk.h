@@ -122,8 +122,12 @@ int qw_sim_create(const qw_csc *mats, int32_t num_instances, const qw_sim_opts *
  * Set instance inst to |b~> = sum_j b_j |jc=0, j, b1=0, kc=0, k=0, b2=0>
  * (Sec. IV, |j~>), b = b_re + i b_im (b_im may be NULL), n = that instance's N;
  * exact zeros are not stored.  With apply_T != 0 the state becomes T~|b~>
- * (Alg. T~).  Other instances are not touched.
- * Errors: QW_ERR_ARG, QW_ERR_CAPACITY, QW_ERR_CUDA.
+ * (Alg. T~).  Other instances are not touched.  b_re and b_im are copied to
+ * the device directly (an asynchronous copy when they are pinned); the call
+ * synchronises the simulator's stream before it returns, so they may be
+ * reused afterwards.
+ * Errors: QW_ERR_ARG, QW_ERR_CAPACITY, QW_ERR_CUDA, QW_ERR_DEVICE_STATUS (T~
+ * met a row of the instance that was not |b~>).
  */
 int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, const double *b_im, int32_t n,
                   int32_t apply_T);
@@ -198,7 +202,11 @@ int qw_apply_qls(qw_sim *sim, int32_t inst, const double *coeffs, int64_t j0, do
 /*
  * Marginal distribution of one register of instance inst:
  * probs[v] = sum over branches with register value v of |a|^2, v < len.
- * reg_id is one of QW_REG_*.  Errors: QW_ERR_ARG, QW_ERR_STATE, QW_ERR_CUDA.
+ * reg_id is one of QW_REG_*.  The histogram is accumulated in a device
+ * scratch array that the simulator keeps for later calls (allocated when len
+ * exceeds every earlier len) and copied straight into probs (asynchronous
+ * when probs is pinned); the call synchronises before it returns.
+ * Errors: QW_ERR_ARG, QW_ERR_STATE, QW_ERR_CUDA.
  */
 int qw_measure_register(qw_sim *sim, int32_t inst, int32_t reg_id, double *probs, int64_t len);
 

@@ -33,10 +33,15 @@ struct Scalars {
     unsigned int pad1;
     unsigned long long counter;
     unsigned long long stats[QW_NSTAT];
-    int32_t tinit_fallback;
-    int32_t pad2;
     int64_t qls_j; /* current QLS term */
 };
+
+/* the head of Scalars the host reads at every synchronising call */
+struct StatusView {
+    int32_t status, pad;
+    int64_t done;
+};
+static_assert(offsetof(Scalars, steps_done) == offsetof(StatusView, done), "Scalars head layout");
 
 thread_local std::string g_create_error;
 
@@ -88,6 +93,12 @@ struct qw_sim {
     double *qls_p = nullptr; /* p_j, j = 0..j0 */
     double *qls_c = nullptr; /* coefficients a_j, j = 0..j0 */
     int64_t qls_p_cap = 0;
+    double *b_dev = nullptr;     /* |b> staging: re then im, b_stride doubles each */
+    int64_t b_stride = 0;
+    double *meas_dev = nullptr;  /* register marginal scratch */
+    int64_t meas_cap = 0;
+    Scalars *h_sc = nullptr;     /* pinned host copies: Scalars reset, status read */
+    StatusView *h_st = nullptr;
     int64_t device_bytes = 0;
     int64_t launches = 0;
     /* captured 6-step graphs, one per (buffer, scale slot) phase */
@@ -402,6 +413,10 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     QW_TRY(cudaMemcpy(sim->sc, &z, sizeof z, cudaMemcpyHostToDevice));
     sim->init_norm2.assign((size_t)ninst, 0.0);
     QW_TRY(dalloc(sim, &sim->qls_y, (size_t)nmax));
+    QW_TRY(dalloc(sim, &sim->b_dev, 2 * (size_t)nmax));
+    sim->b_stride = nmax;
+    QW_TRY(cudaMallocHost((void **)&sim->h_sc, sizeof(Scalars)));
+    QW_TRY(cudaMallocHost((void **)&sim->h_st, sizeof(StatusView)));
     QW_TRY(cudaDeviceSynchronize());
 #undef QW_TRY
     *out = sim;
@@ -432,6 +447,10 @@ extern "C" int qw_sim_destroy(qw_sim *sim)
     cudaFree(sim->qls_y);
     cudaFree(sim->qls_p);
     cudaFree(sim->qls_c);
+    cudaFree(sim->b_dev);
+    cudaFree(sim->meas_dev);
+    cudaFreeHost(sim->h_sc);
+    cudaFreeHost(sim->h_st);
     delete sim;
     return QW_OK;
 }
@@ -466,13 +485,11 @@ static const double *pending_scale(qw_sim *sim)
  * Then clear the status and map it to an error code. */
 static int check_status(qw_sim *sim, const char *where)
 {
-    struct {
-        int32_t status, pad;
-        int64_t done;
-    } h{};
-    cudaError_t e = cudaMemcpyAsync(&h, &sim->sc->status, sizeof h, cudaMemcpyDeviceToHost, sim->stream);
+    cudaError_t e = cudaMemcpyAsync(sim->h_st, &sim->sc->status, sizeof(StatusView), cudaMemcpyDeviceToHost,
+                                    sim->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
     if (e != cudaSuccess) return cuda_fail(sim, e, where);
+    const StatusView h = *sim->h_st;
     const int64_t good = h.done - sim->sync_done;
     if (h.status != 0) {
         sim->cur = (int)((sim->sync_cur + good) % 3);
@@ -491,6 +508,7 @@ static int check_status(qw_sim *sim, const char *where)
     if (st & QW_ST_WARP_OVERFLOW) m += " [on-chip row buffer overflow: raise warp_capacity]";
     if (st & QW_ST_SPILL_FULL) m += " [garbage-row table full]";
     if (st & QW_ST_ANCILLA) m += " [register A not returned to zero]";
+    if (st & QW_ST_NOT_BTILDE) m += " [a row was not |b~> before T~]";
     m += "; state kept after " + std::to_string(good) + " clean steps since the last sync";
     const int code = (st & (QW_ST_ROW_OVERFLOW | QW_ST_WARP_OVERFLOW | QW_ST_SPILL_FULL))
                          ? QW_ERR_CAPACITY
@@ -539,12 +557,12 @@ extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, cons
     if (!sim) return QW_ERR_ARG;
     if (inst < 0 || inst >= sim->d.ninst) return fail(sim, QW_ERR_ARG, "instance out of range");
     if (!b_re || n != sim->n_of[(size_t)inst]) return fail(sim, QW_ERR_ARG, "b must hold N values");
-    std::vector<double2> hb((size_t)n);
-    for (int j = 0; j < n; ++j) hb[(size_t)j] = make_double2(b_re[j], b_im ? b_im[j] : 0.0);
-    double2 *db = nullptr;
-    QW_CUDA(sim, cudaMallocAsync((void **)&db, hb.size() * sizeof(double2), sim->stream));
-    QW_CUDA(sim, cudaMemcpyAsync(db, hb.data(), hb.size() * sizeof(double2), cudaMemcpyHostToDevice,
-                                 sim->stream));
+    /* |b> goes straight from the caller's arrays to the device (asynchronous
+       when they are pinned); the previous call's copies ended at its sync */
+    double *dre = sim->b_dev, *dim = b_im ? sim->b_dev + sim->b_stride : nullptr;
+    QW_CUDA(sim, cudaMemcpyAsync(dre, b_re, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, sim->stream));
+    if (b_im)
+        QW_CUDA(sim, cudaMemcpyAsync(dim, b_im, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, sim->stream));
     const int64_t lo = sim->bkt_of[(size_t)inst], hi = sim->bkt_of[(size_t)inst + 1];
     const bool all = sim->d.ninst == 1;
     /* clear the instance's rows in every buffer (the whole state for a single
@@ -555,13 +573,14 @@ extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, cons
         sim->launches++;
     }
     double nb2 = 0.0;
-    for (int j = 0; j < n; ++j) nb2 += hb[(size_t)j].x * hb[(size_t)j].x + hb[(size_t)j].y * hb[(size_t)j].y;
+    for (int j = 0; j < n; ++j) nb2 += b_re[j] * b_re[j] + (b_im ? b_im[j] * b_im[j] : 0.0);
     sim->init_norm2[(size_t)inst] = nb2;
     if (all) {
-        Scalars z{};
+        Scalars &z = *sim->h_sc;
+        z = Scalars{};
         z.scale[0] = z.scale[1] = 1.0;
         z.renorm_target = nb2;
-        QW_CUDA(sim, cudaMemcpyAsync(sim->sc, &z, sizeof z, cudaMemcpyHostToDevice, sim->stream));
+        QW_CUDA(sim, cudaMemcpyAsync(sim->sc, sim->h_sc, sizeof(Scalars), cudaMemcpyHostToDevice, sim->stream));
         sim->scale_slot = sim->sync_slot = 0;
         sim->cur = sim->sync_cur = 0;
         sim->sync_done = 0;
@@ -572,23 +591,17 @@ extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, cons
         QW_CUDA(sim, cudaMemcpyAsync(&sim->sc->renorm_target, &sim->host_target, 8,
                                      cudaMemcpyHostToDevice, sim->stream));
     }
-    QW_CUDA(sim, qw_launch_init_b(sim->d, sim->buf[sim->cur], inst, db, n, sim->fp32,
+    QW_CUDA(sim, qw_launch_init_b(sim->d, sim->buf[sim->cur], inst, dre, dim, n, sim->fp32,
                                   all ? nullptr : pending_scale(sim), sim->stream));
     sim->launches++;
     if (apply_T) {
-        /* T~ on |b~>: the one-branch-per-row kernel, or the literal sort-based
-           schedule when that was asked for */
+        /* T~ on |b~>: the one-branch-per-row kernel (a row that is not |b~>
+           sets a status bit), or the literal sort-based schedule when that
+           was asked for */
         if (sim->mode != QW_MODE_WALK_LITERAL) {
-            int32_t fb = 0;
-            QW_CUDA(sim, cudaMemsetAsync(&sim->sc->tinit_fallback, 0, 4, sim->stream));
             QW_CUDA(sim, qw_launch_tinit(sim->d, sim->buf[sim->cur], lo, hi, sim->fp32, &sim->sc->status,
-                                         &sim->sc->tinit_fallback, sim->stream));
+                                         sim->stream));
             sim->launches++;
-            QW_CUDA(sim, cudaMemcpyAsync(&fb, &sim->sc->tinit_fallback, 4, cudaMemcpyDeviceToHost, sim->stream));
-            QW_CUDA(sim, cudaFreeAsync(db, sim->stream));
-            db = nullptr;
-            QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
-            if (fb) return fail(sim, QW_ERR_DEVICE_STATUS, "qw_state_init: a row was not |b~> before T~");
         } else {
             QwStepArgs a = step_args(sim, QW_MODE_T);
             a.scale_in = nullptr;
@@ -601,7 +614,6 @@ extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, cons
             sim->launches++;
         }
     }
-    if (db) QW_CUDA(sim, cudaFreeAsync(db, sim->stream));
     int rc = check_status(sim, "qw_state_init");
     if (rc != QW_OK) return rc;
     sim->has_state = true;
@@ -854,15 +866,21 @@ extern "C" int qw_measure_register(qw_sim *sim, int32_t inst, int32_t reg, doubl
     if (inst < 0 || inst >= sim->d.ninst || reg < 0 || reg > 5 || !probs || len < 1)
         return fail(sim, QW_ERR_ARG, "bad instance, register id or output");
     if (!sim->has_state) return fail(sim, QW_ERR_STATE, "no state");
-    double *dp = nullptr;
-    QW_CUDA(sim, cudaMallocAsync((void **)&dp, (size_t)len * sizeof(double), sim->stream));
+    if (sim->meas_cap < len) { /* kept for later calls */
+        QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
+        cudaFree(sim->meas_dev);
+        sim->meas_dev = nullptr;
+        sim->meas_cap = 0;
+        QW_CUDA(sim, cudaMalloc((void **)&sim->meas_dev, (size_t)len * sizeof(double)));
+        sim->meas_cap = len;
+    }
+    double *dp = sim->meas_dev;
     QW_CUDA(sim, cudaMemsetAsync(dp, 0, (size_t)len * sizeof(double), sim->stream));
     QW_CUDA(sim, qw_launch_measure(sim->d, sim->buf[sim->cur], inst, sim->fp32, pending_scale(sim), reg,
                                    dp, len, sim->stream));
     sim->launches++;
     QW_CUDA(sim, cudaMemcpyAsync(probs, dp, (size_t)len * sizeof(double), cudaMemcpyDeviceToHost,
                                  sim->stream));
-    QW_CUDA(sim, cudaFreeAsync(dp, sim->stream));
     return check_status(sim, "qw_measure_register");
 }
 

@@ -34,6 +34,7 @@
 #define QW_ST_WARP_OVERFLOW 2  /* a row outgrew the on-chip row buffer */
 #define QW_ST_SPILL_FULL 4     /* no free spill slot for a jc != 0 row */
 #define QW_ST_ANCILLA 8        /* register A not zero where it must be */
+#define QW_ST_NOT_BTILDE 16    /* T~ at initialisation met a row that was not |b~> */
 
 /* per-step branch counters (index into QwStepArgs.stats) */
 #define QW_STAT_ROWS 0      /* rows processed */
@@ -111,10 +112,10 @@ size_t qw_step_smem_bytes(const QwSimDev &d, int fp32, int mode);
 int qw_step_grid(const QwSimDev &d, int fp32, int mode);
 cudaError_t qw_launch_clear(const QwSimDev &d, const QwBufDev &buf, int64_t lo, int64_t hi,
                             int clear_spill, cudaStream_t st);
-cudaError_t qw_launch_init_b(const QwSimDev &d, const QwBufDev &buf, int inst, const double2 *b,
-                             int n, int fp32, const double *scale, cudaStream_t st);
+cudaError_t qw_launch_init_b(const QwSimDev &d, const QwBufDev &buf, int inst, const double *b_re,
+                             const double *b_im, int n, int fp32, const double *scale, cudaStream_t st);
 cudaError_t qw_launch_tinit(const QwSimDev &d, const QwBufDev &buf, int64_t lo, int64_t hi, int fp32,
-                            int32_t *status, int32_t *fallback, cudaStream_t st);
+                            int32_t *status, cudaStream_t st);
 cudaError_t qw_launch_import(const QwSimDev &d, const QwBufDev &buf, const uint64_t *rowkey,
                              const uint64_t *local, const double2 *amp, int64_t count, int fp32,
                              int32_t *status, cudaStream_t st);

@@ -1603,11 +1603,11 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
  * holds at most the one branch k = kc = b2 = A = 0.  T~'s Hadamard turns it
  * into the s branches (l, z = 0) with amplitude a / sqrt(s) (a group with a
  * single member at u = 0); then the maps and R of T~ as in the step kernel;
- * the row does not change (no S).  A row holding anything else is left to the
- * general sort-based kernel (flagged by *fallback). */
+ * the row does not change (no S).  A row holding anything else sets the
+ * status bit QW_ST_NOT_BTILDE (the state was not |b~>). */
 template <typename AmpT, typename KeyT>
 __global__ void __launch_bounds__(WARPS * 32) k_tinit(QwSimDev d, QwBufDev buf, int64_t lo, int64_t hi,
-                                                      int32_t *status, int32_t *fallback)
+                                                      int32_t *status)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1625,7 +1625,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_tinit(QwSimDev d, QwBufDev buf, 
         if (n <= 0) continue;
         const int64_t row0 = b * (int64_t)d.cap_row;
         if (n != 1 || buf.key[row0] != 0ull) {
-            if (lane == 0) atomicOr(fallback, 1);
+            if (lane == 0) atomicOr(status, QW_ST_NOT_BTILDE);
             continue;
         }
         Row r;
@@ -1672,12 +1672,12 @@ __global__ void k_clear(QwBufDev buf, int64_t lo, int64_t hi, int spill_slots, i
 /* |b~>: branch (jc=0, j, b1=0, kc=0, k=0, b2=0) with amplitude b_j, stored in
  * the units of the pending renormalisation scale (amplitude / scale). */
 template <typename AmpT>
-__global__ void k_init_b(QwSimDev d, QwBufDev buf, int inst, const double2 *bvec, int n,
+__global__ void k_init_b(QwSimDev d, QwBufDev buf, int inst, const double *b_re, const double *b_im, int n,
                          const double *scale)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    double2 v = bvec[j];
+    double2 v = make_double2(b_re[j], b_im ? b_im[j] : 0.0);
     if (v.x == 0.0 && v.y == 0.0) return;
     if (scale) v = make_double2(v.x / *scale, v.y / *scale);
     const int64_t b = d.inst_bkt[inst] + ((int64_t)j << 1);
@@ -1860,11 +1860,11 @@ size_t walk_smem_bytes(const QwSimDev &d)
 
 template <typename AmpT, typename KeyT>
 void launch_tinit_k(const QwSimDev &d, const QwBufDev &buf, int64_t lo, int64_t hi, int grid, int32_t *status,
-                    int32_t *fallback, cudaStream_t st)
+                    cudaStream_t st)
 {
     const size_t sm = (size_t)WARPS * walk_layout<AmpT, KeyT>(d).per_warp;
     cudaFuncSetAttribute(k_tinit<AmpT, KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_tinit<AmpT, KeyT><<<grid, WARPS * 32, sm, st>>>(d, buf, lo, hi, status, fallback);
+    k_tinit<AmpT, KeyT><<<grid, WARPS * 32, sm, st>>>(d, buf, lo, hi, status);
 }
 
 template <typename AmpT, int MODE>
@@ -1967,12 +1967,12 @@ cudaError_t qw_launch_clear(const QwSimDev &d, const QwBufDev &buf, int64_t lo, 
     return cudaGetLastError();
 }
 
-cudaError_t qw_launch_init_b(const QwSimDev &d, const QwBufDev &buf, int inst, const double2 *b,
-                             int n, int fp32, const double *scale, cudaStream_t st)
+cudaError_t qw_launch_init_b(const QwSimDev &d, const QwBufDev &buf, int inst, const double *b_re,
+                             const double *b_im, int n, int fp32, const double *scale, cudaStream_t st)
 {
     const int grid = (n + 255) / 256;
-    if (fp32) k_init_b<float2><<<grid, 256, 0, st>>>(d, buf, inst, b, n, scale);
-    else k_init_b<double2><<<grid, 256, 0, st>>>(d, buf, inst, b, n, scale);
+    if (fp32) k_init_b<float2><<<grid, 256, 0, st>>>(d, buf, inst, b_re, b_im, n, scale);
+    else k_init_b<double2><<<grid, 256, 0, st>>>(d, buf, inst, b_re, b_im, n, scale);
     return cudaGetLastError();
 }
 
@@ -2066,7 +2066,7 @@ cudaError_t qw_launch_measure_noalloc(const QwSimDev &d, const QwBufDev &buf, in
 }
 
 cudaError_t qw_launch_tinit(const QwSimDev &d, const QwBufDev &buf, int64_t lo, int64_t hi, int fp32,
-                            int32_t *status, int32_t *fallback, cudaStream_t st)
+                            int32_t *status, cudaStream_t st)
 {
     int64_t rows = hi - lo;
     int grid = (int)((rows + WARPS - 1) / WARPS);
@@ -2074,11 +2074,11 @@ cudaError_t qw_launch_tinit(const QwSimDev &d, const QwBufDev &buf, int64_t lo, 
     if (grid < 1) grid = 1;
     const bool k32 = key32_fits(d);
     if (fp32) {
-        if (k32) launch_tinit_k<float2, uint32_t>(d, buf, lo, hi, grid, status, fallback, st);
-        else launch_tinit_k<float2, uint64_t>(d, buf, lo, hi, grid, status, fallback, st);
+        if (k32) launch_tinit_k<float2, uint32_t>(d, buf, lo, hi, grid, status, st);
+        else launch_tinit_k<float2, uint64_t>(d, buf, lo, hi, grid, status, st);
     } else {
-        if (k32) launch_tinit_k<double2, uint32_t>(d, buf, lo, hi, grid, status, fallback, st);
-        else launch_tinit_k<double2, uint64_t>(d, buf, lo, hi, grid, status, fallback, st);
+        if (k32) launch_tinit_k<double2, uint32_t>(d, buf, lo, hi, grid, status, st);
+        else launch_tinit_k<double2, uint64_t>(d, buf, lo, hi, grid, status, st);
     }
     return cudaGetLastError();
 }

@@ -262,8 +262,13 @@ class Sim:
         self._check(load().qw_apply_qls(self._h, inst, _p(coeffs), j0, _p(y), _p(p)))
         return y[0::2] + 1j * y[1::2], p
 
-    def measure_register(self, reg: str, length: int, inst: int = 0) -> np.ndarray:
-        out = np.zeros(int(length))
+    def measure_register(self, reg: str, length: int, inst: int = 0, out: np.ndarray | None = None) -> np.ndarray:
+        """qw_measure_register into ``out`` (float64, contiguous; e.g. a view of
+        pinned host memory) or a new array."""
+        if out is None:
+            out = np.zeros(int(length))
+        if out.dtype != np.float64 or not out.flags.c_contiguous or out.size != int(length):
+            raise ValueError("out must be a contiguous float64 array of the given length")
         self._check(load().qw_measure_register(self._h, inst, REGS[reg], _p(out), out.size))
         return out
 
