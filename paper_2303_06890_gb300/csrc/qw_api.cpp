@@ -87,6 +87,8 @@ struct qw_sim {
     float4 *fg32 = nullptr;
     int32_t *inst_n = nullptr;
     int64_t *inst_img = nullptr, *inst_bkt = nullptr;
+    uint16_t *unit_inst = nullptr;
+    void *slot_rot = nullptr;
     double *partials = nullptr;
     Scalars *sc = nullptr;
     double2 *qls_y = nullptr;
@@ -378,15 +380,38 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     QW_TRY(cudaMemcpy(sim->img, himage.data(), himage.size() * 4, cudaMemcpyHostToDevice));
     QW_TRY(cudaMemcpy(sim->fg, hfg.data(), hfg.size() * sizeof(double2), cudaMemcpyHostToDevice));
     QW_TRY(cudaMemcpy(sim->fg32, hfg32.data(), hfg32.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    { /* rotation values per QRAM slot, in the step kernel's precision (16 bytes either way) */
+        std::vector<float4> hs((size_t)img_words);
+        for (size_t w = 0; w < himage.size(); ++w) {
+            const uint32_t code = himage[w] & 0xffffu;
+            if (sim->fp32) {
+                hs[w] = hfg32[code];
+            } else {
+                static_assert(sizeof(float4) == sizeof(double2), "16-byte slot entries");
+                std::memcpy(&hs[w], &hfg[code], sizeof(double2));
+            }
+        }
+        QW_TRY(dalloc(sim, (float4 **)&sim->slot_rot, hs.size()));
+        QW_TRY(cudaMemcpy(sim->slot_rot, hs.data(), hs.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    }
     QW_TRY(cudaMemcpy(sim->inst_n, hn.data(), hn.size() * 4, cudaMemcpyHostToDevice));
     QW_TRY(cudaMemcpy(sim->inst_img, himg.data(), himg.size() * 8, cudaMemcpyHostToDevice));
     QW_TRY(cudaMemcpy(sim->inst_bkt, hbkt.data(), hbkt.size() * 8, cudaMemcpyHostToDevice));
+    if (ninst > 1) { /* instance of each dense bucket pair (2 j, 2 j + 1) */
+        std::vector<uint16_t> hu((size_t)(buckets / 2));
+        for (int i = 0; i < ninst; ++i)
+            for (int64_t u = hbkt[(size_t)i] / 2; u < hbkt[(size_t)i + 1] / 2; ++u) hu[(size_t)u] = (uint16_t)i;
+        QW_TRY(dalloc(sim, &sim->unit_inst, hu.size()));
+        QW_TRY(cudaMemcpy(sim->unit_inst, hu.data(), hu.size() * 2, cudaMemcpyHostToDevice));
+    }
     d.img = sim->img;
     d.fg = sim->fg;
     d.fg32 = sim->fg32;
     d.inst_n = sim->inst_n;
     d.inst_img = sim->inst_img;
     d.inst_bkt = sim->inst_bkt;
+    d.unit_inst = sim->unit_inst;
+    d.slot_rot = sim->slot_rot;
     const size_t amp_bytes = sim->fp32 ? sizeof(float2) : sizeof(double2);
     const size_t slots = (size_t)d.total_buckets * (size_t)d.cap_row;
     for (int bi = 0; bi < 3; ++bi) {
@@ -434,6 +459,8 @@ extern "C" int qw_sim_destroy(qw_sim *sim)
     cudaFree(sim->inst_n);
     cudaFree(sim->inst_img);
     cudaFree(sim->inst_bkt);
+    cudaFree(sim->unit_inst);
+    cudaFree(sim->slot_rot);
     for (auto &b : sim->buf) {
         cudaFree(b.key);
         cudaFree(b.amp);

@@ -71,9 +71,11 @@ struct QwSimDev {
     const uint32_t *img;      /* QRAM words: column << 16 | Q1.15 value */
     const double2 *fg;        /* per Q1.15 code: (sqrt|a|, sqrt(1-|a|)) */
     const float4 *fg32;       /* the same as float pairs: (hi, lo) of each, hi + lo ~ 48 bits */
+    const void *slot_rot;     /* per QRAM slot: its code's entry of fg (FP64) or fg32 (FP32) */
     const int32_t *inst_n;    /* N per instance */
     const int64_t *inst_img;  /* image offset per instance */
     const int64_t *inst_bkt;  /* first dense bucket per instance, ninst + 1 entries */
+    const uint16_t *unit_inst; /* instance of dense bucket pair u (buckets 2u, 2u + 1); ninst > 1 */
 };
 
 struct QwBufDev {

@@ -452,12 +452,7 @@ __device__ bool row_of(const QwSimDev &d, const QwBufDev &in, int64_t b, Row &r)
         return true;
     }
     if (b < d.dense_buckets) {
-        int lo = 0, hi = d.ninst;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (d.inst_bkt[mid] <= b) lo = mid;
-            else hi = mid;
-        }
+        const int lo = d.unit_inst[b >> 1];
         const int64_t idx = b - d.inst_bkt[lo];
         r.inst = (uint32_t)lo;
         r.jc = 0;
@@ -1119,8 +1114,9 @@ __device__ void pair_row(const QwBufDev &in, int64_t b, int nr, KeyT tag, int ca
  * bucket B (b1 = 1) -- and group it: b2-pairs next to each other, b2 = 0
  * first.  Partners never straddle the two rows (they differ in b2 only), so a
  * segment that fits one warp is matched at once and a longer one row by row;
- * (have, hraw, ha) are A's first 32 stored branches, loaded ahead by the
- * pipelined loop.  A stored key with A != 0 sets the ancilla status bit. */
+ * (have, hraw, ha) are the segment's first 32 stored branches (A's, then
+ * B's), loaded ahead by the pipelined loop.  A stored key with A != 0 sets
+ * the ancilla status bit. */
 template <typename AmpT, typename KeyT>
 __device__ void load_seg(const QwSimDev &d, const QwBufDev &in, int64_t bA, int n0, KeyT tagA, int64_t bB,
                          int n1, bool rescale, const typename Amp<AmpT>::Scale &scale, KeyT *kd, AmpT *ad,
@@ -1140,8 +1136,8 @@ __device__ void load_seg(const QwSimDev &d, const QwBufDev &in, int64_t bA, int 
             a = have ? ha : static_cast<const AmpT *>(in.amp)[slot];
         } else if (lane < n) {
             const int64_t slot = bB * (int64_t)d.cap_row + (lane - n0);
-            k = in_key<KeyT>(in.key[slot], ash, tagB, anc);
-            a = static_cast<const AmpT *>(in.amp)[slot];
+            k = in_key<KeyT>(have ? hraw : in.key[slot], ash, tagB, anc);
+            a = have ? ha : static_cast<const AmpT *>(in.amp)[slot];
         }
         if (rescale && lane < n) a = scale.apply(a);
         pair32<AmpT, KeyT>(k, a, lane < n, kd, ad, 0);
@@ -1552,10 +1548,10 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
         r.sfg = sfg;
         const int64_t want = ((int64_t)r.inst << 32) | (int64_t)r.j;
         if (r.valid && want != staged) {
+            const int64_t w0 = r.img_base + (int64_t)r.j * d.s;
             for (int t = lane; t < d.s; t += 32) {
-                const uint32_t w = __ldg(d.img + r.img_base + (int64_t)r.j * d.s + t);
-                simg[t] = w;
-                sfg[t] = Amp<AmpT>::rot_table(d, w & 0xffffu);
+                simg[t] = __ldg(d.img + w0 + t);
+                sfg[t] = __ldg(static_cast<const RotVal *>(d.slot_rot) + w0 + t);
             }
             staged = want;
         }
@@ -1563,10 +1559,12 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
         st_in += n;
         load_seg<AmpT, KeyT>(d, in, it.bA, it.n0, it.tagA, it.bB, it.n1, rescale, scale, kP, aP, kQ, aQ, C,
                              have_cur, hk, ha, a.status);
-        if (PF && cur.valid) { /* the next item's branches, while this one is processed */
-            have = cur.n0 > 0;
-            if (have && lane < cur.n0) { /* the first 32 of the next item's row A */
-                const int64_t slot = cur.bA * (int64_t)d.cap_row + lane;
+        if (PF && cur.valid) { /* the next item's first 32 branches (row A, then row B) */
+            const int nn = cur.n0 + cur.n1;
+            have = nn > 0;
+            if (lane < nn) {
+                const int64_t slot = lane < cur.n0 ? cur.bA * (int64_t)d.cap_row + lane
+                                                   : cur.bB * (int64_t)d.cap_row + (lane - cur.n0);
                 pk = in.key[slot];
                 pa = static_cast<const AmpT *>(in.amp)[slot];
             }
