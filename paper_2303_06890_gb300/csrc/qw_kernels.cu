@@ -1372,7 +1372,10 @@ __device__ __forceinline__ KeyT map_t(const QwSimDev &d, const Row &r, KeyT key,
     slot = r.valid ? l : 0xffffffffu;
     A = (r.jc == 0 && z == 0) ? (w & 0xffffu) : 0u;
     const uint32_t k = z ^ (w >> 16);
-    const uint32_t kc = l ^ qbs(d, r, k);
+    /* z = 0 and l a slot of a row j < N: k is the column of slot l, whose
+       in-row index in the unique sorted list is l itself, so kc = l ^ l = 0
+       without the search */
+    const uint32_t kc = (z == 0 && l < (uint32_t)d.s && r.valid) ? 0u : l ^ qbs(d, r, k);
     sneg = r.j > k;
     return (key & (KeyT)1) | ((KeyT)k << 1) | ((KeyT)kc << (1 + d.nb));
 }
