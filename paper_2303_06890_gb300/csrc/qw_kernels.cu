@@ -206,12 +206,14 @@ __device__ __forceinline__ uint32_t qword(const QwSimDev &d, const Row &r, uint3
 __device__ __forceinline__ uint32_t qbs(const QwSimDev &d, const Row &r, uint32_t target)
 {
     if (!r.valid) return target == 0 ? (uint32_t)(d.s >> 1) : 0u;
-    uint32_t i = 0;
+    uint32_t i = 0, ci = r.simg[0] >> 16; /* ci: the column at i */
     for (int step = d.s >> 1; step > 0; step >>= 1) {
         const uint32_t c = r.simg[i + step] >> 16;
-        i = (c <= target) ? i + (uint32_t)step : i;
+        const bool up = c <= target;
+        i = up ? i + (uint32_t)step : i;
+        ci = up ? c : ci;
     }
-    return ((r.simg[i] >> 16) == target) ? i : 0u;
+    return ci == target ? i : 0u;
 }
 
 /* O_A': A ^= a_{j,k}, controlled by jc = kc = 0 (Sec. III-B). */
@@ -1161,63 +1163,64 @@ template <typename KeyT>
 __device__ __forceinline__ KeyT map_t(const QwSimDev &d, const Row &r, KeyT key, uint32_t &slot, uint32_t &A,
                                       bool &sneg);
 
-/* The register maps of one half-step followed by R^dag (WHICH = 0, T~^dag) or
- * R (WHICH = 1, T~) on the adjacent b2-pairs.  The maps never read b2, so the
- * pair head maps the key once for both members; the rotation is controlled
- * by the A field and the sign bit of the mapped key, and the outputs (pair-
- * adjacent) keep only b2, k and kc: A is back to 0. */
-template <int WHICH, typename AmpT, typename KeyT, bool REFL = false>
-__device__ int map_rot_pairs(const QwSimDev &d, const Row &r, const KeyT *ks, const AmpT *as,
-                             int n, KeyT *kd, AmpT *ad, int cap, int32_t *status, int16_t *hidx,
-                             AmpT *zbuf = nullptr, AmpT *z1buf = nullptr, int16_t *pbuf = nullptr,
-                             int *diverted = nullptr)
+/* The pair headed by key k (b2 = 0 member amplitude a0, b2 = 1 member a1,
+ * zero where absent): the register maps of one half-step on the key, then
+ * R^dag (WHICH = 0, T~^dag) or R (WHICH = 1, T~).  The maps never read b2,
+ * so the head maps the key once for both members; the rotation is controlled
+ * by A and sigma, which the maps return beside the key.  Outputs o0 (b2 = 0)
+ * and o1 (b2 = 1) under kb (b2 = 0, the b1 tag kept), and whether each is
+ * kept by the pruning rule. */
+template <int WHICH, typename AmpT, typename KeyT>
+__device__ __forceinline__ void rot_head(const QwSimDev &d, const Row &r, KeyT k, AmpT a0, AmpT a1, AmpT &o0,
+                                         AmpT &o1, bool &c0, bool &c1, KeyT &kb)
 {
-    const int lane = lane_id();
-    const int ash = 1 + 2 * d.nb;
-    const KeyT b1m = (KeyT)1 << KeyB1<KeyT>::bit;
-    /* H P H folded in (REFL): k_high | kc | b1 all zero in a row with jc = 0
-       marks the zero-type Hadamard groups (b2 = 0: the reflected group;
-       b2 = 1: negated, kept beside it); every other branch is negated here */
-    const KeyT zm = ((((KeyT)1 << ash) - 1) & ~(((KeyT)1 << (d.L + 1)) - 1)) | b1m;
-    const bool rowzero = REFL && r.jc == 0;
-    int out = 0, div = 0;
-    /* branch i heads its pair (a b2 = 0 branch, or a b2 = 1 one without its
-       partner): map the key once, rotate both members, append the kept ones */
-    auto pair_at = [&](int i, bool head) {
-        AmpT o0 = Amp<AmpT>::zero(), o1 = Amp<AmpT>::zero();
-        bool c0 = false, c1 = false;
-        KeyT kb = 0;
-        if (head) {
-            const KeyT k = ks[i];
-            AmpT a0 = Amp<AmpT>::zero(), a1 = Amp<AmpT>::zero();
-            if ((k & (KeyT)1) == 0) {
-                a0 = as[i];
-                if (i + 1 < n && ks[i + 1] == (k | (KeyT)1)) a1 = as[i + 1];
-            } else {
-                a1 = as[i];
-            }
-            uint32_t slot, A;
-            bool sneg;
-            const KeyT b1bit = k & b1m;
-            const KeyT key = k & ~((KeyT)1 | b1bit);
-            const KeyT mk = (WHICH == 0) ? map_tdag<KeyT>(d, r, key, slot, A, sneg)
-                                         : map_t<KeyT>(d, r, key, slot, A, sneg);
-            /* A is 0 or the value of slot `slot` of row j: staged rotation
-               values for a slot of this row, the per-code table otherwise */
-            typename Amp<AmpT>::RotVal t;
-            if (A == 0) t = Amp<AmpT>::rot_zero();
-            else if (slot < (uint32_t)d.s && r.sfg) t = static_cast<const typename Amp<AmpT>::RotVal *>(r.sfg)[slot];
-            else t = Amp<AmpT>::rot_table(d, A);
-            Amp<AmpT>::rot(t, A, WHICH == 0, sneg, a0, a1, o0, o1);
-            c0 = Amp<AmpT>::keep(d, o0);
-            c1 = Amp<AmpT>::keep(d, o1);
-            kb = mk | b1bit;
-        }
+    const KeyT b1bit = k & ((KeyT)1 << KeyB1<KeyT>::bit);
+    const KeyT key = k & ~((KeyT)1 | b1bit);
+    uint32_t slot, A;
+    bool sneg;
+    const KeyT mk = (WHICH == 0) ? map_tdag<KeyT>(d, r, key, slot, A, sneg) : map_t<KeyT>(d, r, key, slot, A, sneg);
+    /* A is 0 or the value of slot `slot` of row j: staged rotation values for
+       a slot of this row, the per-code table otherwise */
+    typename Amp<AmpT>::RotVal t;
+    if (A == 0) t = Amp<AmpT>::rot_zero();
+    else if (slot < (uint32_t)d.s && r.sfg) t = static_cast<const typename Amp<AmpT>::RotVal *>(r.sfg)[slot];
+    else t = Amp<AmpT>::rot_table(d, A);
+    Amp<AmpT>::rot(t, A, WHICH == 0, sneg, a0, a1, o0, o1);
+    c0 = Amp<AmpT>::keep(d, o0);
+    c1 = Amp<AmpT>::keep(d, o1);
+    kb = mk | b1bit;
+}
+
+/* Appends rotated pairs to a warp buffer, pair-adjacent (b2 = 0 first), kept
+ * outputs only.  REFL: H P H folded in -- k_high | kc | b1 all zero in a row
+ * with jc = 0 marks the zero-type Hadamard group (b2 = 0: set aside in zbuf
+ * for the reflection; b2 = 1: negated, set aside beside it); every other
+ * output is negated here.  Called by all lanes of the warp together. */
+template <typename AmpT, typename KeyT, bool REFL>
+struct PairSink {
+    KeyT *kd;
+    AmpT *ad;
+    int cap, out, div;
+    KeyT zm;
+    bool rowzero;
+    int smask;
+    AmpT *zbuf, *z1buf;
+    int16_t *pbuf;
+    __device__ PairSink(const QwSimDev &d, const Row &r, KeyT *kd_, AmpT *ad_, int cap_, AmpT *zb, AmpT *z1b,
+                        int16_t *pb)
+        : kd(kd_), ad(ad_), cap(cap_), out(0), div(0), smask(d.s - 1), zbuf(zb), z1buf(z1b), pbuf(pb)
+    {
+        const int ash = 1 + 2 * d.nb;
+        zm = ((((KeyT)1 << ash) - 1) & ~(((KeyT)1 << (d.L + 1)) - 1)) | ((KeyT)1 << KeyB1<KeyT>::bit);
+        rowzero = REFL && r.jc == 0;
+    }
+    __device__ __forceinline__ void put(bool head, KeyT kb, AmpT o0, AmpT o1, bool c0, bool c1)
+    {
         if (REFL) {
             const bool zt = head && rowzero && (kb & zm) == 0;
             div += __popc(__ballot_sync(FULL, zt && c0)) + __popc(__ballot_sync(FULL, zt && c1));
             if (zt) {
-                const int u = (int)((kb >> 1) & (KeyT)(d.s - 1));
+                const int u = (int)((kb >> 1) & (KeyT)smask);
                 if (c0) zbuf[u] = o0;
                 if (c1) {
                     z1buf[u] = Amp<AmpT>::neg(o1);
@@ -1239,6 +1242,33 @@ __device__ int map_rot_pairs(const QwSimDev &d, const Row &r, const KeyT *ks, co
             if (pos < cap) { kd[pos] = kb | (KeyT)1; ad[pos] = o1; }
         }
         out += total;
+    }
+};
+
+/* One half-step (maps + rotation) over a warp buffer of n branches with
+ * b2-pairs adjacent: each pair head (a b2 = 0 branch, or a b2 = 1 one
+ * without its partner) rotates both members; the outputs go to the sink. */
+template <int WHICH, typename AmpT, typename KeyT, typename Sink>
+__device__ void map_rot_pairs(const QwSimDev &d, const Row &r, const KeyT *ks, const AmpT *as, int n, Sink &sink,
+                              int16_t *hidx)
+{
+    const int lane = lane_id();
+    auto pair_at = [&](int i, bool head) {
+        AmpT o0 = Amp<AmpT>::zero(), o1 = Amp<AmpT>::zero();
+        bool c0 = false, c1 = false;
+        KeyT kb = 0;
+        if (head) {
+            const KeyT k = ks[i];
+            AmpT a0 = Amp<AmpT>::zero(), a1 = Amp<AmpT>::zero();
+            if ((k & (KeyT)1) == 0) {
+                a0 = as[i];
+                if (i + 1 < n && ks[i + 1] == (k | (KeyT)1)) a1 = as[i + 1];
+            } else {
+                a1 = as[i];
+            }
+            rot_head<WHICH, AmpT, KeyT>(d, r, k, a0, a1, o0, o1, c0, c1, kb);
+        }
+        sink.put(head, kb, o0, o1, c0, c1);
     };
     auto is_head = [&](int i) {
         return i < n && !(i > 0 && ks[i - 1] == (ks[i] ^ (KeyT)1));
@@ -1267,12 +1297,45 @@ __device__ int map_rot_pairs(const QwSimDev &d, const Row &r, const KeyT *ks, co
         for (int base = 0; base < n; base += 32) pair_at(base + lane, is_head(base + lane));
         __syncwarp();
     }
-    if (REFL) *diverted = div;
-    if (out > cap) {
-        if (lane == 0) atomicOr(status, QW_ST_WARP_OVERFLOW);
-        out = cap;
+}
+
+/* T~^dag on up to 32 loaded branches held one per lane (valid lanes carry
+ * distinct keys): b2-partners found by a warp match on key >> 1, the head of
+ * each pair takes its partner's amplitude by a shuffle and rotates both. */
+template <typename AmpT, typename KeyT, typename Sink>
+__device__ __forceinline__ void rot0_chunk(const QwSimDev &d, const Row &r, KeyT k, AmpT a, bool valid, Sink &sink)
+{
+    const int lane = lane_id();
+    if (!valid) k = (KeyT)~(KeyT)0 - (KeyT)(2 * lane); /* distinct k >> 1 above every real key */
+    const unsigned m = __match_any_sync(FULL, (KeyT)(k >> 1));
+    const unsigned other = m & ~(1u << lane);
+    const bool b2one = (k & (KeyT)1) != 0;
+    const bool head = valid && (!b2one || other == 0);
+    const int src = other ? (__ffs(other) - 1) : lane;
+    AmpT pa;
+    pa.x = __shfl_sync(FULL, a.x, src);
+    pa.y = __shfl_sync(FULL, a.y, src);
+    AmpT o0 = Amp<AmpT>::zero(), o1 = Amp<AmpT>::zero();
+    bool c0 = false, c1 = false;
+    KeyT kb = 0;
+    if (head) {
+        const AmpT a0 = b2one ? Amp<AmpT>::zero() : a;
+        const AmpT a1 = b2one ? a : (other ? pa : Amp<AmpT>::zero());
+        rot_head<0, AmpT, KeyT>(d, r, k, a0, a1, o0, o1, c0, c1, kb);
     }
-    return out;
+    sink.put(head, kb, o0, o1, c0, c1);
+}
+
+/* Close a sink: its branch count, capped at the buffer (overflow flagged). */
+template <typename Sink>
+__device__ int sink_count(Sink &sink, int32_t *status)
+{
+    __syncwarp();
+    if (sink.out > sink.cap) {
+        if (lane_id() == 0) atomicOr(status, QW_ST_WARP_OVERFLOW);
+        return sink.cap;
+    }
+    return sink.out;
 }
 
 /* The zero-type Hadamard group of H P H, after T~^dag's rotation has negated
@@ -1560,8 +1623,55 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
         }
         st_rows++;
         st_in += n;
-        load_seg<AmpT, KeyT>(d, in, it.bA, it.n0, it.tagA, it.bB, it.n1, rescale, scale, kP, aP, kQ, aQ, C,
-                             have_cur, hk, ha, a.status);
+        if (r.jc == 0) { /* the zero-type group's slots, filled by T~^dag */
+            for (int t = lane; t < d.s; t += 32) {
+                zbuf[t] = Amp<AmpT>::zero();
+                pbuf[t] = -1;
+            }
+            __syncwarp();
+        }
+        PairSink<AmpT, KeyT, true> s0(d, r, kQ, aQ, C, zbuf, z1buf, pbuf);
+        if (!Amp<AmpT>::kHeadLanes && it.n0 <= 32 && it.n1 <= 32) {
+            /* rows of <= 32: T~^dag straight from the loaded registers, the
+               pairs found by one warp match per chunk of <= 32 */
+            const int ash = 1 + 2 * d.nb;
+            const KeyT tagB = (KeyT)1 << B1;
+            uint64_t anc = 0;
+            const AmpT *amp = static_cast<const AmpT *>(in.amp);
+            auto get = [&](int64_t slot, bool pre, uint64_t praw, AmpT pamp, KeyT tag, KeyT &k, AmpT &v) {
+                k = in_key<KeyT>(pre ? praw : in.key[slot], ash, tag, anc);
+                v = pre ? pamp : amp[slot];
+                if (rescale) v = scale.apply(v);
+            };
+            if (n <= 32) {
+                KeyT k = 0;
+                AmpT v = Amp<AmpT>::zero();
+                if (lane < it.n0) get(it.bA * (int64_t)d.cap_row + lane, have_cur, hk, ha, it.tagA, k, v);
+                else if (lane < n) get(it.bB * (int64_t)d.cap_row + (lane - it.n0), have_cur, hk, ha, tagB, k, v);
+                rot0_chunk<AmpT, KeyT>(d, r, k, v, lane < n, s0);
+            } else {
+                KeyT k = 0;
+                AmpT v = Amp<AmpT>::zero();
+                if (lane < it.n0) get(it.bA * (int64_t)d.cap_row + lane, have_cur, hk, ha, it.tagA, k, v);
+                rot0_chunk<AmpT, KeyT>(d, r, k, v, lane < it.n0, s0);
+                /* row B: its first 32 - n0 branches were loaded ahead into lanes n0.. */
+                const int src = (it.n0 + lane) & 31;
+                const uint64_t bh = __shfl_sync(FULL, hk, src);
+                AmpT ba;
+                ba.x = __shfl_sync(FULL, ha.x, src);
+                ba.y = __shfl_sync(FULL, ha.y, src);
+                KeyT kB = 0;
+                AmpT vB = Amp<AmpT>::zero();
+                if (lane < it.n1)
+                    get(it.bB * (int64_t)d.cap_row + lane, have_cur && it.n0 + lane < 32, bh, ba, tagB, kB, vB);
+                rot0_chunk<AmpT, KeyT>(d, r, kB, vB, lane < it.n1, s0);
+            }
+            if (__any_sync(FULL, anc != 0) && lane == 0) atomicOr(a.status, QW_ST_ANCILLA);
+        } else {
+            load_seg<AmpT, KeyT>(d, in, it.bA, it.n0, it.tagA, it.bB, it.n1, rescale, scale, kP, aP, kQ, aQ, C,
+                                 have_cur, hk, ha, a.status);
+            map_rot_pairs<0, AmpT, KeyT>(d, r, kP, aP, n, s0, hidx);
+        }
         if (PF && cur.valid) { /* the next item's first 32 branches (row A, then row B) */
             const int nn = cur.n0 + cur.n1;
             have = nn > 0;
@@ -1572,20 +1682,13 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
                 pa = static_cast<const AmpT *>(in.amp)[slot];
             }
         }
-        if (r.jc == 0) { /* the zero-type group's slots, filled by T~^dag */
-            for (int t = lane; t < d.s; t += 32) {
-                zbuf[t] = Amp<AmpT>::zero();
-                pbuf[t] = -1;
-            }
-            __syncwarp();
-        }
-        int nz = 0;
-        n = map_rot_pairs<0, AmpT, KeyT, true>(d, r, kP, aP, n, kQ, aQ, C, a.status, hidx, zbuf, z1buf, pbuf,
-                                               &nz);                           /* T~^dag, H P H signs */
-        st_rdag += n + nz;
+        n = sink_count(s0, a.status);                                          /* T~^dag, H P H signs */
+        st_rdag += n + s0.div;
         n = reflect_zero<AmpT, KeyT>(d, r, kQ, aQ, n, C, a.status, a, zbuf, z1buf, pbuf); /* H P H */
         st_hph += n;
-        n = map_rot_pairs<1, AmpT, KeyT>(d, r, kQ, aQ, n, kP, aP, C, a.status, hidx); /* T~ */
+        PairSink<AmpT, KeyT, false> s1(d, r, kP, aP, C, nullptr, nullptr, nullptr);
+        map_rot_pairs<1, AmpT, KeyT>(d, r, kQ, aQ, n, s1, hidx);
+        n = sink_count(s1, a.status);                                          /* T~ */
         st_out += n;
         emit_pairs<AmpT, KeyT>(d, r, kP, aP, n, out, a.status, nrm);           /* S */
         __syncwarp();
@@ -1647,7 +1750,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_tinit(QwSimDev d, QwBufDev buf, 
             m = d.s;
         }
         __syncwarp();
-        m = map_rot_pairs<1, AmpT, KeyT>(d, r, kP, aP, m, kQ, aQ, C, status, hidx);
+        PairSink<AmpT, KeyT, false> s1(d, r, kQ, aQ, C, nullptr, nullptr, nullptr);
+        map_rot_pairs<1, AmpT, KeyT>(d, r, kP, aP, m, s1, hidx);
+        m = sink_count(s1, status);
         /* write back in place: the row keeps its registers (jc, j, b1) */
         for (int i = lane; i < m && i < d.cap_row; i += 32) {
             buf.key[row0 + i] = (uint64_t)kQ[i]; /* b2 | k | kc, A = 0, no b1 tag */
