@@ -751,9 +751,15 @@ __host__ __device__ inline WalkLayout walk_layout(const QwSimDev &d)
 
 /* sign flips as integer operations on the sign bit (keeps FP64 negations
  * and selects off GB300's slow FP64 pipe) */
+/* sign flip of an FP64 value as an integer XOR on its high word, kept opaque
+   (inline PTX) so that it stays on the integer pipe: an FP64 negation would
+   take a slot of GB300's 1/64-rate FP64 pipe */
 __device__ __forceinline__ double flip_if(double x, bool neg)
 {
-    return __longlong_as_double(__double_as_longlong(x) ^ ((long long)neg << 63));
+    const int m = (int)((unsigned)neg << 31);
+    int hi = __double2hiint(x);
+    asm("xor.b32 %0, %0, %1;" : "+r"(hi) : "r"(m));
+    return __hiloint2double(hi, __double2loint(x));
 }
 __device__ __forceinline__ float flip_if(float x, bool neg)
 {
