@@ -781,20 +781,24 @@ template <> struct Amp<double2> {
     struct Sum {
         double x = 0.0, y = 0.0;
         __device__ void add(T a) { x += a.x; y += a.y; }
-        /* lanes 0..s-1 hold the values (s a power of two, <= 32 here) */
+        /* lane t < min(s, 32) holds the partial sums of the values t, t + 32, ...
+           (s a power of two).  Butterfly over the w = min(s, 32) lanes, x on
+           lanes t < w/2 and y on lanes t >= w/2 after the first level, so one
+           FP64 add serves both components; the same pairs and order as a
+           butterfly over each component alone (FP64 addition commutes). */
         __device__ void reduce(int s)
         {
-            if (s >= 32) {
-                x = warp_sum(x);
-                y = warp_sum(y);
-                return;
-            }
-            for (int o = s >> 1; o > 0; o >>= 1) {
-                x += __shfl_xor_sync(FULL, x, o);
-                y += __shfl_xor_sync(FULL, y, o);
+            const int w = s < 32 ? s : 32, h = w >> 1;
+            if (h > 0) {
+                const bool hy = (lane_id() & h) != 0;
+                const double recv = __shfl_xor_sync(FULL, hy ? x : y, h);
+                double v = (hy ? y : x) + recv;
+                for (int o = h >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+                x = v;
+                y = v;
             }
             x = __shfl_sync(FULL, x, 0);
-            y = __shfl_sync(FULL, y, 0);
+            y = __shfl_sync(FULL, y, h);
         }
         __device__ void scale_pow2(double f) { x *= f; y *= f; }
         __device__ T minus(T a) const { return make_double2(x - a.x, y - a.y); }
@@ -863,14 +867,7 @@ template <> struct Amp<float2> {
             l = __fsub_rn(l, __fsub_rn(s, h));
             h = s;
         }
-        __device__ void reduce()
-        {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float oh = __shfl_xor_sync(FULL, h, o), ol = __shfl_xor_sync(FULL, l, o);
-                add(oh, ol);
-            }
-        }
+
         /* round(h + l - v) */
         __device__ float minus(float v) const
         {
@@ -884,7 +881,39 @@ template <> struct Amp<float2> {
     struct Sum {
         DF x, y;
         __device__ void add(T a) { x.add(a.x); y.add(a.y); }
-        __device__ void reduce(int s) { (void)s; x.reduce(); y.reduce(); }
+        /* lane t < min(s, 32) holds the partial sums of the values t, t + 32, ...
+           (s a power of two).  Butterfly over the w = min(s, 32) lanes, x on
+           lanes t < w/2 and y on lanes t >= w/2 after the first level (where a
+           y lane adds its own pair to its partner's, the order the partner
+           would use), so one float-pair add serves both components. */
+        __device__ void reduce(int s)
+        {
+            const int w = s < 32 ? s : 32, h = w >> 1;
+            if (h > 0) {
+                const bool hy = (lane_id() & h) != 0;
+                const float rh = __shfl_xor_sync(FULL, hy ? x.h : y.h, h);
+                const float rl = __shfl_xor_sync(FULL, hy ? x.l : y.l, h);
+                DF v;
+                if (hy) { /* partner's y, then own y */
+                    v.h = rh;
+                    v.l = rl;
+                    v.add(y.h, y.l);
+                } else {
+                    v = x;
+                    v.add(rh, rl);
+                }
+                for (int o = h >> 1; o > 0; o >>= 1) {
+                    const float oh = __shfl_xor_sync(FULL, v.h, o), ol = __shfl_xor_sync(FULL, v.l, o);
+                    v.add(oh, ol);
+                }
+                x = v;
+                y = v;
+            }
+            x.h = __shfl_sync(FULL, x.h, 0);
+            x.l = __shfl_sync(FULL, x.l, 0);
+            y.h = __shfl_sync(FULL, y.h, h);
+            y.l = __shfl_sync(FULL, y.l, h);
+        }
         __device__ void scale_pow2(double f)
         {
             const float g = (float)f; /* 2/s: a power of two, exact */
