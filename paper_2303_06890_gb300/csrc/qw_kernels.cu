@@ -769,6 +769,12 @@ __device__ __forceinline__ float flip_if(float x, bool neg)
 template <typename AmpT> struct Amp;
 
 /* complex128 path: FP64 arithmetic throughout */
+/* the pruning decision inside the band around tau (rarely reached) */
+__device__ __noinline__ bool keep_band(double x, double y, double tau2)
+{
+    return __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)) > tau2;
+}
+
 template <> struct Amp<double2> {
     typedef double2 T;
     static constexpr bool kHeadLanes = true; /* rotate with one lane per pair head */
@@ -809,7 +815,10 @@ template <> struct Amp<double2> {
     __device__ static double2 to_d(T a) { return a; }
     __device__ static T from_d(double2 a) { return a; }
     /* |a|^2 > tau^2 exactly as the un-fused FP64 formula, decided from the
-       exponent bits except in a narrow band around tau */
+       exponent bits except in a narrow band around tau; the band's FP64
+       arithmetic sits in a call of its own, so that it is not if-converted
+       into every call (a predicated-off FP64 instruction still takes its
+       slot of the 1/64-rate FP64 pipe) */
     __device__ static bool keep(const QwSimDev &d, T a)
     {
         const uint64_t ux = (uint64_t)__double_as_longlong(a.x) & 0x7fffffffffffffffull;
@@ -817,7 +826,7 @@ template <> struct Amp<double2> {
         const uint64_t um = ux > uy ? ux : uy;
         if (um > d.tau_hi_bits) return true;
         if (um <= d.tau_lo_bits) return false;
-        return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y)) > d.tau2;
+        return keep_band(a.x, a.y, d.tau2);
     }
     struct Scale {
         double s;
