@@ -769,6 +769,8 @@ __device__ __forceinline__ float flip_if(float x, bool neg)
 template <typename AmpT> struct Amp;
 
 /* complex128 path: FP64 arithmetic throughout */
+__device__ __noinline__ double2 scale_c128(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+
 /* the pruning decision inside the band around tau (rarely reached) */
 __device__ __noinline__ bool keep_band(double x, double y, double tau2)
 {
@@ -828,10 +830,12 @@ template <> struct Amp<double2> {
         if (um <= d.tau_lo_bits) return false;
         return keep_band(a.x, a.y, d.tau2);
     }
-    struct Scale {
+    struct Scale { /* the renormalisation (off by default for complex128): out of
+                      line, so its FP64 products are not if-converted into the
+                      loads that do not rescale */
         double s;
         __device__ explicit Scale(double v) : s(v) {}
-        __device__ T apply(T a) const { return make_double2(a.x * s, a.y * s); }
+        __device__ T apply(T a) const { return scale_c128(a, s); }
     };
     typedef double2 RotVal; /* (sqrt|a|, sqrt(1-|a|)) */
     __device__ static RotVal rot_table(const QwSimDev &d, uint32_t A) { return __ldg(d.fg + A); }
