@@ -76,10 +76,12 @@ typedef struct {
     double prune_tau;        /* branches with |a| <= tau are removed after each
                                 interference op; 0 = 1e-13 (FP64), 2^-24 (FP32_AMP) */
     int32_t row_capacity;    /* branches per (jc, j, b1) row between steps; 0 = auto (4 s) */
-    int32_t warp_capacity;   /* branches one warp holds on chip while it runs a row
-                                (or a segment of two rows) through a step; 0 = auto
-                                (2 row_capacity rounded up to a power of two, at
-                                least 64, for fuse_reflection = 1) */
+    int32_t warp_capacity;   /* entries of a warp's on-chip buffers while it runs a row
+                                (or a segment of two rows) through a step: branches at
+                                load and after T~, b2-pairs between T~^dag and T~; 0 = auto:
+                                2 row_capacity rounded up to a power of two, at least 64
+                                (fuse_reflection = 1), halved while the buffers do not
+                                fit the device's shared memory per block */
     int32_t renorm;          /* -1 = default (on for FP32_AMP, off for FP64) */
     void *stream;            /* cudaStream_t to issue on; NULL = the default stream */
     int32_t walk_variant;    /* step kernel with fuse_reflection = 1 (see qw_autotune):

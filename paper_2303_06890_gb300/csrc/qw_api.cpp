@@ -359,9 +359,14 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
 #define QW_TRY(call)                                                                               \
     if ((e = (call)) != cudaSuccess) return bail(e, #call)
     {
-        /* one block holds 8 warps' row buffers (2 x warp_capacity branches each) */
+        /* one block holds its warps' row buffers (a few times warp_capacity
+           entries each); an automatic warp_capacity halves until they fit,
+           down to what a row needs (segments of two rows then stay off) */
         int optin = 0;
         QW_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, sim->device));
+        while (o.warp_capacity <= 0 && qw_step_smem_bytes(d, sim->fp32, sim->mode) > (size_t)optin &&
+               d.warp_cap / 2 >= std::max(d.s, d.cap_row))
+            d.warp_cap /= 2;
         const size_t need = qw_step_smem_bytes(d, sim->fp32, sim->mode);
         if (need > (size_t)optin) {
             g_create_error = "qw_sim_create: the step kernel needs " + std::to_string(need) +

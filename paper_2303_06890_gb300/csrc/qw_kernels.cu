@@ -708,10 +708,10 @@ template <> struct KeyB1<uint32_t> { static constexpr int bit = 31; };
 __host__ __device__ inline bool key32_fits(const QwSimDev &d) { return 1 + 2 * d.nb <= 29; }
 
 /* per-warp shared memory of the fused kernels (byte offsets, 16-byte aligned):
- * keys x2, amplitudes x2, the zero-type group (b2 = 0 values, b2 = 1 values,
+ * keys x2, amplitudes x3 (a pair list holds two per key), the zero-type group (b2 = 0 values, b2 = 1 values,
  * presence), the staged QRAM row, pair-head indices, the row's rotation values */
 struct WalkLayout {
-    size_t kP, kQ, aP, aQ, zbuf, z1buf, simg, pbuf, hidx, sfg, per_warp;
+    size_t kP, kQ, aP, aQ, aX, zbuf, z1buf, simg, pbuf, hidx, sfg, per_warp;
 };
 
 template <typename AmpT, typename KeyT>
@@ -727,6 +727,7 @@ __host__ __device__ inline WalkLayout walk_layout(const QwSimDev &d)
     QW_TAKE(kQ, C * sizeof(KeyT));
     QW_TAKE(aP, C * sizeof(AmpT));
     QW_TAKE(aQ, C * sizeof(AmpT));
+    QW_TAKE(aX, C * sizeof(AmpT));
     QW_TAKE(zbuf, s * sizeof(AmpT));
     QW_TAKE(z1buf, s * sizeof(AmpT));
     QW_TAKE(simg, s * sizeof(uint32_t));
@@ -1293,6 +1294,79 @@ struct PairSink {
     }
 };
 
+/* The same outputs as PairSink, as a pair list: one entry per pair with a
+ * kept member -- key kb (b2 = 0), the b2 = 0 and b2 = 1 amplitudes, zero for a
+ * member that is absent (a kept amplitude is never zero: it exceeds tau).
+ * elems counts the kept branches. */
+template <typename AmpT, typename KeyT, bool REFL>
+struct PairListSink {
+    KeyT *kd;
+    AmpT *a0d, *a1d;
+    int cap, out, div, elems;
+    KeyT zm;
+    bool rowzero;
+    int smask;
+    AmpT *zbuf, *z1buf;
+    int16_t *pbuf;
+    __device__ PairListSink(const QwSimDev &d, const Row &r, KeyT *kd_, AmpT *a0_, AmpT *a1_, int cap_, AmpT *zb,
+                            AmpT *z1b, int16_t *pb)
+        : kd(kd_), a0d(a0_), a1d(a1_), cap(cap_), out(0), div(0), elems(0), smask(d.s - 1), zbuf(zb), z1buf(z1b),
+          pbuf(pb)
+    {
+        const int ash = 1 + 2 * d.nb;
+        zm = ((((KeyT)1 << ash) - 1) & ~(((KeyT)1 << (d.L + 1)) - 1)) | ((KeyT)1 << KeyB1<KeyT>::bit);
+        rowzero = REFL && r.jc == 0;
+    }
+    __device__ __forceinline__ void put(bool head, KeyT kb, AmpT o0, AmpT o1, bool c0, bool c1)
+    {
+        if (REFL) {
+            const bool zt = head && rowzero && (kb & zm) == 0;
+            div += __popc(__ballot_sync(FULL, zt && c0)) + __popc(__ballot_sync(FULL, zt && c1));
+            if (zt) {
+                const int u = (int)((kb >> 1) & (KeyT)smask);
+                if (c0) zbuf[u] = o0;
+                if (c1) {
+                    z1buf[u] = Amp<AmpT>::neg(o1);
+                    pbuf[u] = 1;
+                }
+                c0 = c1 = false;
+            } else {
+                o0 = Amp<AmpT>::neg(o0);
+                o1 = Amp<AmpT>::neg(o1);
+            }
+        }
+        const bool any = c0 || c1;
+        const unsigned m = __ballot_sync(FULL, any);
+        elems += __popc(__ballot_sync(FULL, c0)) + __popc(__ballot_sync(FULL, c1));
+        if (any) {
+            const int pos = out + __popc(m & ((1u << lane_id()) - 1u));
+            if (pos < cap) {
+                kd[pos] = kb;
+                a0d[pos] = c0 ? o0 : Amp<AmpT>::zero();
+                a1d[pos] = c1 ? o1 : Amp<AmpT>::zero();
+            }
+        }
+        out += __popc(m);
+    }
+};
+
+/* One half-step over a pair list of np entries: one lane per pair. */
+template <int WHICH, typename AmpT, typename KeyT, typename Sink>
+__device__ void map_rot_list(const QwSimDev &d, const Row &r, const KeyT *ks, const AmpT *a0s, const AmpT *a1s,
+                             int np, Sink &sink)
+{
+    for (int base = 0; base < np; base += 32) {
+        const int p = base + lane_id();
+        const bool head = p < np;
+        AmpT o0 = Amp<AmpT>::zero(), o1 = Amp<AmpT>::zero();
+        bool c0 = false, c1 = false;
+        KeyT kb = 0;
+        if (head) rot_head<WHICH, AmpT, KeyT>(d, r, ks[p], a0s[p], a1s[p], o0, o1, c0, c1, kb);
+        sink.put(head, kb, o0, o1, c0, c1);
+    }
+    __syncwarp();
+}
+
 /* One half-step (maps + rotation) over a warp buffer of n branches with
  * b2-pairs adjacent: each pair head (a b2 = 0 branch, or a b2 = 1 one
  * without its partner) rotates both members; the outputs go to the sink. */
@@ -1386,21 +1460,24 @@ __device__ int sink_count(Sink &sink, int32_t *status)
     return sink.out;
 }
 
+
 /* The zero-type Hadamard group of H P H, after T~^dag's rotation has negated
- * every other branch and set the group aside (map_rot_pairs with REFL): in a
+ * every other branch and set the group aside (PairListSink with REFL): in a
  * row with jc = b1 = 0, the group (kc = k_high = b2 = 0) maps a_u ->
  * (2/s) sum_v a_v - a_u for all s values of u (H P H = 2|+><+| - 1 there).
- * Appends the s outputs (u, b2 = 0), each followed by its negated b2 = 1
- * partner when present, to kd/ad after the n branches already there.  The
- * sum is taken by u in a fixed order (FP64 for complex128, a float pair for
- * complex64); with readout, (1/sqrt s) sum_v a_v -- the flag-0 amplitude of
- * T~^dag's output -- goes into the QLS accumulator. */
+ * Appends the s pairs (u: the reflected b2 = 0 value, and the set-aside
+ * negated b2 = 1 partner) to the np entries of the pair list; elems receives
+ * the number of branches appended.  The sum is taken by u in a fixed order
+ * (FP64 for complex128, a float pair for complex64); with readout,
+ * (1/sqrt s) sum_v a_v -- the flag-0 amplitude of T~^dag's output -- goes into
+ * the QLS accumulator. */
 template <typename AmpT, typename KeyT>
-__device__ int reflect_zero(const QwSimDev &d, const Row &r, KeyT *kd, AmpT *ad, int n, int cap,
-                            int32_t *status, const QwStepArgs &a, const AmpT *zbuf, const AmpT *z1buf,
-                            const int16_t *pbuf)
+__device__ int reflect_zero_list(const QwSimDev &d, const Row &r, KeyT *kd, AmpT *a0d, AmpT *a1d, int np, int cap,
+                                 int32_t *status, const QwStepArgs &a, const AmpT *zbuf, const AmpT *z1buf,
+                                 const int16_t *pbuf, int &elems)
 {
-    if (r.jc != 0) return n;
+    elems = 0;
+    if (r.jc != 0) return np;
     const int lane = lane_id();
     const int s = d.s;
     typename Amp<AmpT>::Sum sum;
@@ -1415,7 +1492,7 @@ __device__ int reflect_zero(const QwSimDev &d, const Row &r, KeyT *kd, AmpT *ad,
         a.qls_y[r.j] = acc;
     }
     sum.scale_pow2(d.two_over_s);
-    int out = n;
+    int out = np;
     for (int ub = 0; ub < s; ub += 32) {
         const int u = ub + lane;
         const bool vu = u < s;
@@ -1426,18 +1503,18 @@ __device__ int reflect_zero(const QwSimDev &d, const Row &r, KeyT *kd, AmpT *ad,
             c1 = pbuf[u] > 0;
         }
         const bool c0 = vu && Amp<AmpT>::keep(d, o0);
-        int total;
-        int pos = out + warp_compact2(c0, c1, total);
-        const KeyT k0 = (KeyT)u << 1;
-        if (c0) {
-            if (pos < cap) { kd[pos] = k0; ad[pos] = o0; }
-            pos++;
+        const bool any = c0 || c1;
+        const unsigned m = __ballot_sync(FULL, any);
+        elems += __popc(__ballot_sync(FULL, c0)) + __popc(__ballot_sync(FULL, c1));
+        if (any) {
+            const int pos = out + __popc(m & ((1u << lane) - 1u));
+            if (pos < cap) {
+                kd[pos] = (KeyT)u << 1;
+                a0d[pos] = c0 ? o0 : Amp<AmpT>::zero();
+                a1d[pos] = c1 ? z1buf[u] : Amp<AmpT>::zero();
+            }
         }
-        if (c1 && pos < cap) {
-            kd[pos] = k0 | (KeyT)1;
-            ad[pos] = z1buf[u];
-        }
-        out += total;
+        out += __popc(m);
     }
     __syncwarp();
     if (out > cap) {
@@ -1562,6 +1639,7 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
     KeyT *kQ = reinterpret_cast<KeyT *>(base + lay.kQ);
     AmpT *aP = reinterpret_cast<AmpT *>(base + lay.aP);
     AmpT *aQ = reinterpret_cast<AmpT *>(base + lay.aQ);
+    AmpT *aX = reinterpret_cast<AmpT *>(base + lay.aX);
     AmpT *zbuf = reinterpret_cast<AmpT *>(base + lay.zbuf);
     AmpT *z1buf = reinterpret_cast<AmpT *>(base + lay.z1buf);
     uint32_t *simg = reinterpret_cast<uint32_t *>(base + lay.simg);
@@ -1678,7 +1756,7 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
             }
             __syncwarp();
         }
-        PairSink<AmpT, KeyT, true> s0(d, r, kQ, aQ, C, zbuf, z1buf, pbuf);
+        PairListSink<AmpT, KeyT, true> s0(d, r, kQ, aQ, aX, C, zbuf, z1buf, pbuf);
         if (!Amp<AmpT>::kHeadLanes && it.n0 <= 32 && it.n1 <= 32) {
             /* rows of <= 32: T~^dag straight from the loaded registers, the
                pairs found by one warp match per chunk of <= 32 */
@@ -1730,12 +1808,13 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
                 pa = static_cast<const AmpT *>(in.amp)[slot];
             }
         }
-        n = sink_count(s0, a.status);                                          /* T~^dag, H P H signs */
-        st_rdag += n + s0.div;
-        n = reflect_zero<AmpT, KeyT>(d, r, kQ, aQ, n, C, a.status, a, zbuf, z1buf, pbuf); /* H P H */
-        st_hph += n;
+        int np = sink_count(s0, a.status);                                     /* T~^dag, H P H signs */
+        st_rdag += s0.elems + s0.div;
+        int ez = 0;
+        np = reflect_zero_list<AmpT, KeyT>(d, r, kQ, aQ, aX, np, C, a.status, a, zbuf, z1buf, pbuf, ez); /* H P H */
+        st_hph += s0.elems + ez;
         PairSink<AmpT, KeyT, false> s1(d, r, kP, aP, C, nullptr, nullptr, nullptr);
-        map_rot_pairs<1, AmpT, KeyT>(d, r, kQ, aQ, n, s1, hidx);
+        map_rot_list<1, AmpT, KeyT>(d, r, kQ, aQ, aX, np, s1);
         n = sink_count(s1, a.status);                                          /* T~ */
         st_out += n;
         emit_pairs<AmpT, KeyT>(d, r, kP, aP, n, out, a.status, nrm);           /* S */

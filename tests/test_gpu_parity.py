@@ -245,11 +245,13 @@ def test_batched_instances_match_their_oracles():
 
 @pytest.mark.parametrize("enqueue", [False, True])
 def test_capacity_overflow_keeps_last_clean_state(enqueue):
-    """A row that outgrows its buffer fails the call with QW_ERR_CAPACITY; the
-    steps issued after the failing one do nothing, and the state is the output
-    of the last clean step, equal to the oracle's after that many steps."""
+    """A segment that outgrows the warp's on-chip buffer fails the call with
+    QW_ERR_CAPACITY (two rows of up to 8 branches against a buffer of 8, once
+    the b1 = 1 rows fill); the steps issued after the failing one do nothing,
+    and the state is the output of the last clean step, equal to the oracle's
+    after that many steps."""
     w = wl.walk_n16()
-    sim = _sim(w, row_capacity=8, warp_capacity=8)
+    sim = _sim(w, row_capacity=8, warp_capacity=8, walk_variant=2)
     sim.state_init(w.b)
     o = _oracle(w)
     o.apply("T")
