@@ -53,6 +53,7 @@ def parse_args():
     p.add_argument("--batched-steps", type=int, default=300)
     p.add_argument("--no-table1", action="store_true")
     p.add_argument("--no-qls", action="store_true")
+    p.add_argument("--no-mmax", action="store_true")
     return p.parse_args()
 
 
@@ -283,6 +284,7 @@ def run_ours(args, rank, world, local_rank):
 
     table1 = None if args.no_table1 else table1_leg(torch, barrier, max_over_ranks)
     qls = None if args.no_qls else qls_leg(torch, barrier, max_over_ranks)
+    mmax = None if args.no_mmax else mmax_leg()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -322,6 +324,8 @@ def run_ours(args, rank, world, local_rank):
         line["table1"] = table1
     if qls is not None:
         line["qls"] = qls
+    if mmax is not None:
+        line["mmax"] = mmax
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -405,6 +409,45 @@ def _events_time(torch, fn) -> float:
     e1.record()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / 1000.0
+
+
+def mmax_leg(steps: int = 12) -> dict:
+    """The largest number of branches M_max the walk reaches (the state after
+    T~ and after each interference op of every step, counted on the device),
+    against N at fixed s and against s at fixed N, on full positive band
+    matrices (Sec. V-B), complex128 -- the scan of Fig. 10 -- with the log-log
+    slopes between the ends of each scan."""
+    import math
+    import numpy as np
+    from paper_2303_06890_gb300 import qwalk
+    from paper_2303_06890_gb300 import workloads as wl
+
+    def m_max(n: int, s: int) -> int:
+        m = wl.band_positive(n, s // 2 - 1, 8, seed=900 + n + s)
+        b = np.random.default_rng(901 + n).uniform(0.0, 1.0, n)
+        sim = qwalk.Sim(m, s_pad=s)
+        sim.state_init(b / np.linalg.norm(b))
+        best = sim.state_size()
+        sim.step_stats(reset=True)
+        for _ in range(steps):
+            sim.apply_walk_step(1)
+            st = sim.step_stats(reset=True)
+            best = max(best, st["in"], st["after_rdag"], st["after_hph"], st["out"])
+        sim.close()
+        return int(best)
+
+    def slope(xs, ys):
+        return math.log(ys[-1] / ys[0]) / math.log(xs[-1] / xs[0])
+
+    out = {"steps": steps, "versus_n": {}, "versus_s": {}}
+    for s in (4, 8):
+        ns = [256, 1024, 4096, 16384]
+        ms = [m_max(n, s) for n in ns]
+        out["versus_n"][f"s={s}"] = {"n": ns, "m_max": ms, "slope": slope(ns, ms)}
+    ss = [4, 8, 16, 32, 64]
+    ms = [m_max(4096, s) for s in ss]
+    out["versus_s"]["n=4096"] = {"s": ss, "m_max": ms, "slope": slope(ss, ms)}
+    return out
 
 
 def table1_leg(torch, barrier, max_over_ranks) -> dict:
