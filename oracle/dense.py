@@ -72,3 +72,22 @@ def fidelity(x: np.ndarray, y: np.ndarray) -> float:
     """|<x|y>|^2 / ||y||^2 for unit x."""
     ny = np.linalg.norm(y)
     return float(abs(np.vdot(x, y)) ** 2 / (ny * ny)) if ny > 0 else 0.0
+
+
+def intuitive_os(cols, l: int) -> int:
+    """App. B's intuitive sparsity oracle on one row: k(j, l) for 0 <= l < N.
+    cols are the row's s column indices, sorted.  l < s: the l-th column of
+    the row ("sparsity mapping"); l >= s: the (l - s)-th column that is not in
+    the row ("bijection filler"), found by walking the sorted columns upward
+    from l - s and stepping over each one that is not above the running
+    index (Alg. "Find k from input l >= s", with the comparison strict: the
+    reading that reproduces the example of Sec. III-B)."""
+    s = len(cols)
+    if l < s:
+        return int(cols[l])
+    k = l - s
+    for c in cols:
+        if c > k:
+            return k
+        k += 1
+    return k

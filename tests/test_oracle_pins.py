@@ -403,3 +403,34 @@ def test_qls_matches_dense_chebyshev_sum_and_solve(oracle_mod):
     x = dense.qls_reference(ad, rhs)
     assert dense.fidelity(x, Y) > 1 - 1e-5
     assert o.violations == 0
+
+
+def test_intuitive_os_of_appendix_b_example_bijection_and_agreement_with_os_prime(oracle_mod):
+    """App. B's intuitive O_s: the example the text of Sec. III-B prints
+    (golden), a bijection of [0, N) on every row (brute force), and on the
+    valid inputs (l < s) the same map as the QBS-based O_s' of the oracle."""
+    from oracle import dense
+    lines = [x.split() for x in open(os.path.join(GOLDEN, "appb_intuitive_os.txt")) if x.strip()
+             and not x.startswith("#")]
+    for cols_s, l, k in lines:
+        cols = [int(c) for c in cols_s.split(",")]
+        assert dense.intuitive_os(cols, int(l)) == int(k)
+    # the comparison as printed (">=") sends l = 6 to column 2 of the row
+    # itself, against the example: the strict reading is the one taken
+    def as_printed(cols, l):
+        k = l - len(cols)
+        for c in cols:
+            if c >= k:
+                return k
+            k += 1
+        return k
+    assert as_printed([2, 5, 8, 10], 6) == 2 != dense.intuitive_os([2, 5, 8, 10], 6)
+    m = random_signed(24, 4, 33)
+    s = wl.next_pow2(m.max_col_nnz)
+    o = oracle_mod.Oracle(m, s)
+    for j, (cols, _) in enumerate(padded_rows(m, s)):
+        image = [dense.intuitive_os(list(cols), l) for l in range(m.n)]
+        assert sorted(image) == list(range(m.n))          # a bijection of [0, N)
+        assert image[s:] == sorted(set(range(m.n)) - set(cols))  # free columns, in order
+        for l in range(s):                                 # valid inputs: O_s' agrees
+            assert o.os_single(j, l, 0) == (image[l], 0)
