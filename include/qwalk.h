@@ -94,6 +94,12 @@ typedef struct {
                                 from states outside the walk's physical subspace, e.g. by
                                 qw_state_import); a power of two, 0 = auto (2N/8 over all
                                 instances, clamped to [256, 4096]) */
+    int32_t rot_bits;        /* 0 (default): the rotation's f = sqrt(|a|), g = sqrt(1 - |a|)
+                                in FP64; 1..52: the angle theta = arccos(sqrt(|a|)) held
+                                in a fixed-point register of rot_bits bits over [0, pi/2]
+                                (rounded half to even), f = cos, g = sin of it -- the
+                                square-root and arccos registers Table 2 lists for the
+                                conditional rotation */
 } qw_sim_opts;
 
 /* Fill *opts with the defaults above. */

@@ -51,6 +51,7 @@ def _load():
         getattr(lib, name).restype = i64
         getattr(lib, name).argtypes = [P]
     lib.or_set_tau.argtypes = [P, dbl]
+    lib.or_set_rot_bits.argtypes = [P, ctypes.c_int]
     lib.or_image.argtypes = [P, i64, i64, P, P]
     lib.or_init_b.argtypes = [P, P, P]
     lib.or_import.argtypes = [P, P, P, i64]
@@ -75,7 +76,7 @@ def _ptr(a: np.ndarray):
 class Oracle:
     """One register-level sparse state over the QRAM image of one matrix."""
 
-    def __init__(self, matrix, s: int, tau: float = TAU64):
+    def __init__(self, matrix, s: int, tau: float = TAU64, rot_bits: int = 0):
         lib = _load()
         self._colptr = np.ascontiguousarray(matrix.colptr, dtype=np.int32)
         self._rowidx = np.ascontiguousarray(matrix.rowidx, dtype=np.int32)
@@ -87,6 +88,8 @@ class Oracle:
         if not self._h:
             raise ValueError("oracle: invalid matrix or sparsity")
         self.nb = int(lib.or_nb(self._h))
+        if rot_bits:
+            lib.or_set_rot_bits(self._h, int(rot_bits))
 
     def __del__(self):
         if getattr(self, "_h", None):

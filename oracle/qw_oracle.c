@@ -73,6 +73,7 @@ typedef struct oracle {
     branch *st;         /* state */
     int64_t m, cap;
     double tau;
+    int rot_bits; /* 0: exact f, g; > 0: the rotation angle held in rot_bits bits */
     reg_meta meta[NREG];
     int64_t live_bits, max_live_bits;
     int64_t violations; /* ancilla-not-zero and other self-check failures */
@@ -366,18 +367,32 @@ static void u_hadamard(const oracle *o, const branch *idle, int dim, double comp
             u[t * dim + q] = (__builtin_popcount((unsigned)(t & q)) & 1) ? -h : h;
 }
 
-/* f and g of the conditional rotation from A's Q1.15 code and (j, k). */
-static void rotation_fg(const branch *e, double complex *f, double *g)
+/* f and g of the conditional rotation from A's Q1.15 code and (j, k).
+ * Exact (rot_bits = 0): |f| = sqrt(|a|), g = sqrt(1 - |a|).  With the angle in
+ * a fixed-point register (the square root and arccos registers that Table 2
+ * lists for the conditional rotation): theta = arccos(sqrt(|a|)) in [0, pi/2]
+ * rounded to a multiple of (pi/2) / 2^rot_bits (half to even), |f| = cos,
+ * g = sin of the rounded angle. */
+static void rotation_fg(const oracle *o, const branch *e, double complex *f, double *g)
 {
     int16_t q = (int16_t)(uint16_t)e->r[R_A];
     double a = (double)q / 32768.0;
     double mag = fabs(a);
-    *g = sqrt(1.0 - mag);
+    double fm;
+    if (o->rot_bits > 0) {
+        double step = ldexp(1.5707963267948966, -o->rot_bits);
+        double th = nearbyint(acos(sqrt(mag)) / step) * step;
+        fm = cos(th);
+        *g = sin(th);
+    } else {
+        fm = sqrt(mag);
+        *g = sqrt(1.0 - mag);
+    }
     if (q >= 0) {
-        *f = sqrt(mag);
+        *f = fm;
     } else {
         double sigma = (e->r[R_J] <= e->r[R_K]) ? 1.0 : -1.0;
-        *f = I * (sigma * sqrt(mag));
+        *f = I * (sigma * fm);
     }
 }
 
@@ -387,7 +402,7 @@ static void u_rot(const oracle *o, const branch *idle, int dim, double complex *
     (void)dim;
     double complex f;
     double g;
-    rotation_fg(idle, &f, &g);
+    rotation_fg(o, idle, &f, &g);
     u[0] = f;  u[1] = -g;       /* R|0> = f|0> + g|1> */
     u[2] = g;  u[3] = conj(f);  /* R|1> = -g|0> + conj(f)|1> */
 }
@@ -398,7 +413,7 @@ static void u_rotdag(const oracle *o, const branch *idle, int dim, double comple
     (void)dim;
     double complex f;
     double g;
-    rotation_fg(idle, &f, &g);
+    rotation_fg(o, idle, &f, &g);
     u[0] = conj(f); u[1] = g;
     u[2] = -g;      u[3] = f;
 }
@@ -570,6 +585,7 @@ int64_t or_size(const oracle *o) { return o->m; }
 int64_t or_violations(const oracle *o) { return o->violations; }
 int64_t or_max_live_bits(const oracle *o) { return o->max_live_bits; }
 void or_set_tau(oracle *o, double tau) { o->tau = tau; }
+void or_set_rot_bits(oracle *o, int bits) { o->rot_bits = bits; }
 
 /* QRAM image readback (value word, column word) of row j, slot l. */
 void or_image(const oracle *o, int64_t j, int64_t l, uint32_t *val, uint32_t *col)

@@ -312,6 +312,11 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     wc = std::max<int64_t>(wc, s);
     wc = std::max<int64_t>(wc, d.cap_row);
     d.warp_cap = (int)wc;
+    if (o.rot_bits < 0 || o.rot_bits > 52) {
+        g_create_error = "qw_sim_create: rot_bits must be in [0, 52]";
+        qw_sim_destroy(sim);
+        return QW_ERR_ARG;
+    }
     if (o.spill_rows < 0 || (o.spill_rows & (o.spill_rows - 1)) != 0 || o.spill_rows > (1 << 24)) {
         g_create_error = "qw_sim_create: spill_rows must be 0 or a power of two <= 2^24";
         qw_sim_destroy(sim);
@@ -344,7 +349,13 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     for (int c = 0; c < 65536; ++c) {
         const int16_t q = (int16_t)(uint16_t)c;
         const double mag = std::fabs((double)q / 32768.0);
-        const double f = std::sqrt(mag), g = std::sqrt(1.0 - mag);
+        double f = std::sqrt(mag), g = std::sqrt(1.0 - mag);
+        if (o.rot_bits > 0) { /* the angle in a fixed-point register of rot_bits bits */
+            const double step = std::ldexp(1.5707963267948966, -o.rot_bits);
+            const double th = std::nearbyint(std::acos(std::sqrt(mag)) / step) * step;
+            f = std::cos(th);
+            g = std::sin(th);
+        }
         hfg[(size_t)c] = make_double2(f, g);
         const float fh = (float)f, gh = (float)g;
         hfg32[(size_t)c] = make_float4(fh, (float)(f - (double)fh), gh, (float)(g - (double)gh));

@@ -49,7 +49,7 @@ class Opts(ctypes.Structure):
                 ("prune_tau", ctypes.c_double), ("row_capacity", ctypes.c_int32),
                 ("warp_capacity", ctypes.c_int32), ("renorm", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("walk_variant", ctypes.c_int32),
-                ("graphs", ctypes.c_int32), ("spill_rows", ctypes.c_int32)]
+                ("graphs", ctypes.c_int32), ("spill_rows", ctypes.c_int32), ("rot_bits", ctypes.c_int32)]
 
 
 _lib = None
@@ -178,7 +178,7 @@ class Sim:
     def __init__(self, matrices, s_pad: int = 0, precision: int = QW_FP64, fuse_reflection: bool = True,
                  prune_tau: float = 0.0, row_capacity: int = 0, warp_capacity: int = 0,
                  renorm: int = -1, stream: int | None = None, walk_variant: int = 0,
-                 graphs: bool = True, spill_rows: int = 0):
+                 graphs: bool = True, spill_rows: int = 0, rot_bits: int = 0):
         lib = load()
         if not isinstance(matrices, (list, tuple)):
             matrices = [matrices]
@@ -202,6 +202,7 @@ class Sim:
         opts.walk_variant = walk_variant
         opts.graphs = int(bool(graphs))
         opts.spill_rows = int(spill_rows)
+        opts.rot_bits = int(rot_bits)
         h = ctypes.c_void_p()
         rc = lib.qw_sim_create(arr, len(matrices), ctypes.byref(opts), ctypes.byref(h))
         if rc:

@@ -477,3 +477,41 @@ def test_walk_with_64bit_in_kernel_keys_matches_oracle(n, variant):
     st = compare_arrays(gpu_arrays(sim), oracle_arrays(o), TOL64)
     print(f"N={n} variant {variant}: {st}")
     sim.close()
+
+
+@pytest.mark.parametrize("fuse", [True, False])
+def test_fixed_point_rotation_angle_matches_oracle(fuse):
+    """rot_bits = 8: the rotation angle in an 8-bit fixed-point register (the
+    square-root and arccos registers of Table 2); the GPU walk equals the
+    oracle run with the same register, keys exactly, amplitudes to 1e-12."""
+    w = wl.walk_n16()
+    sim = _sim(w, rot_bits=8, fuse_reflection=fuse)
+    sim.state_init(w.b)
+    o = oracle.Oracle(w.matrix, w.s, rot_bits=8)
+    o.init_b(w.b)
+    o.apply("T")
+    compare(gpu_state(sim), oracle_state(o), TOL64)
+    for _ in range(5):
+        sim.apply_walk_step(1)
+        o.apply("W")
+        compare(gpu_state(sim), oracle_state(o), TOL64)
+    sim.close()
+
+
+def test_qls_fidelity_against_the_width_of_the_angle_register():
+    """The CKS solve of Table 1's matrix A (kappa 103) with the rotation angle
+    held in b bits: the fidelity to the exact solution approaches the
+    exact-rotation value as b grows (printed for b = 6 .. 16)."""
+    w = wl.table1("A", steps=0)
+    coeffs, _, _ = qwalk.cks_coefficients(w.kappa, 1e-3)
+    x = dense.qls_reference(w.matrix.dense(), w.b)
+    fid = {}
+    for bits in (6, 8, 10, 12, 16, 0):
+        sim = _sim(w, rot_bits=bits)
+        sim.state_init(w.b)
+        y, _ = sim.apply_qls(coeffs)
+        fid[bits] = dense.fidelity(x, y)
+        sim.close()
+    print("QLS fidelity by angle-register bits:", {k: round(v, 8) for k, v in fid.items()})
+    assert fid[0] > 0.999 and fid[16] > 0.999
+    assert fid[6] < fid[16]

@@ -162,9 +162,9 @@ def test_qram_image_layout(oracle_mod):
 
 # --- unitarity, ancilla hygiene, the block encoding and the Chebyshev identity -------
 
-def _flag0_after_tdag(oracle_mod, o, m, s):
+def _flag0_after_tdag(oracle_mod, o, m, s, rot_bits=0):
     regs, amps = o.export()
-    o2 = oracle_mod.Oracle(m, s)
+    o2 = oracle_mod.Oracle(m, s, rot_bits=rot_bits)
     o2.set_state(regs[:, :6], amps)
     o2.apply("TDAG")
     return o2.flag0()
@@ -434,3 +434,44 @@ def test_intuitive_os_of_appendix_b_example_bijection_and_agreement_with_os_prim
         assert image[s:] == sorted(set(range(m.n)) - set(cols))  # free columns, in order
         for l in range(s):                                 # valid inputs: O_s' agrees
             assert o.os_single(j, l, 0) == (image[l], 0)
+
+
+def _quantised_matrix(a: np.ndarray, bits: int) -> np.ndarray:
+    """sign(a) cos^2(theta_q): theta = arccos(sqrt|a|) rounded half to even to a
+    multiple of (pi/2) / 2^bits -- the matrix the walk encodes when its
+    rotation angle is held in a fixed-point register of `bits` bits."""
+    step = (np.pi / 2) / 2.0 ** bits
+    th = np.rint(np.arccos(np.sqrt(np.abs(a))) / step) * step
+    return np.sign(a) * np.cos(th) ** 2
+
+
+@pytest.mark.parametrize("bits", [4, 10])
+def test_fixed_point_rotation_angle_block_encoding_and_chebyshev(oracle_mod, bits):
+    """With the angle of the conditional rotation in a register of `bits` bits
+    (Table 2's square-root and arccos registers), T~^dag S T~ encodes the
+    matrix sign(A) cos^2(theta_q) / s, and the walk's flag-0 blocks follow its
+    Chebyshev polynomials; 4 bits leave A visibly changed."""
+    from oracle import dense
+    w = wl.walk_n16()
+    a = w.matrix.dense()
+    aq = _quantised_matrix(a, bits)
+    o = oracle_mod.Oracle(w.matrix, w.s, rot_bits=bits)
+    got = np.zeros((w.n, w.n), dtype=complex)
+    for k in range(w.n):
+        e = np.zeros(w.n)
+        e[k] = 1.0
+        o.init_b(e)
+        o.apply("T", "S", "TDAG")
+        got[:, k] = o.flag0()
+    assert np.abs(got - aq / w.s).max() < 1e-14
+    if bits == 4:
+        assert np.abs(aq - a).max() > 1e-3
+    ref = dense.chebyshev(aq / w.s, w.b, 6)
+    o = oracle_mod.Oracle(w.matrix, w.s, rot_bits=bits)
+    o.init_b(w.b)
+    o.apply("T")
+    for mstep in range(1, 7):
+        o.apply("W")
+        y = _flag0_after_tdag(oracle_mod, o, w.matrix, w.s, rot_bits=bits)
+        assert np.abs(y - ref[mstep]).max() < 1e-12, mstep
+    assert o.violations == 0
