@@ -496,6 +496,8 @@ def test_fixed_point_rotation_angle_matches_oracle(fuse):
         o.apply("W")
         compare(gpu_state(sim), oracle_state(o), TOL64)
     sim.close()
+    with pytest.raises(qwalk.QwError):
+        _sim(w, rot_bits=53)  # wider than an FP64 mantissa
 
 
 def test_qls_fidelity_against_the_width_of_the_angle_register():
