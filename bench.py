@@ -3,7 +3,8 @@
 
 Workload: the quantum walk on a random symmetric N = 16384 matrix with at most
 16 non-zeros per column (s = 16), Q1.15 values, random normalised |b>,
-complex64 amplitudes with FP64 merge, norm and renormalisation, at the size
+complex64 amplitudes (FP32 arithmetic with error-free products and sums in
+the merges; FP64 norm and renormalisation), at the size
 of the paper's largest walk (Table 1 row E, N = 16384).  One benchmark step
 = one walk step W = S T~ P T~^dag of the whole state.
 
@@ -298,9 +299,11 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "n": w.n, "s": w.s, "nnz": int(w.matrix.nnz),
-                   "amplitudes": "complex64 in HBM; FP64 merge, norm, renormalisation",
+                   "amplitudes": "complex64 in HBM; FP32 arithmetic with error-free products and "
+                                 "sums (~48-bit float pairs) in the rotations and the reflection sum; "
+                                 "FP64 norm and renormalisation",
                    "steps_per_walk": w.steps, "branches_per_step": live_entries,
                    "l2": "flushed before every timed step (256 MiB write, untimed)",
                    "parallelism": f"replicas x{world}"},
