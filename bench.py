@@ -338,7 +338,8 @@ def batched_leg(args, torch, flush, barrier, max_over_ranks, world, rank) -> dic
     """256 independent walks (N log-uniform in [64, 4096], s = 8) advanced
     together, one k_walk launch per step: kernel time per step (L2 flushed
     before each timed step), the whole 50-step walk as CUDA-graph replays,
-    and the same instances walked one at a time by the plain complex128 path.
+    and the same instances walked one at a time by the plain complex128 path
+    and by the complex64 path (the gain of batching alone).
     Each rank runs its own 256 instances (weak scaling)."""
     from paper_2303_06890_gb300 import qwalk
     from paper_2303_06890_gb300 import ranks
@@ -368,25 +369,29 @@ def batched_leg(args, torch, flush, barrier, max_over_ranks, world, rank) -> dic
     sim.sync()
     t_walk = max_over_ranks(e0.elapsed_time(e1) / 1000.0)
     sim.close()
-    # the plain complex128 path, one instance at a time (instances after the
-    # first 64 are timed on a stride-4 sample and scaled by the step count)
-    t_seq = 0.0
-    sample = list(range(0, 256, 4))
-    for i in sample:
-        w = ws[i]
-        s1 = qwalk.Sim(w.matrix, s_pad=8, precision=qwalk.QW_FP64)
-        s1.state_init(w.b)
-        s1.apply_walk_step(2)
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record()
-        s1.enqueue_walk_steps(50)
-        a1.record()
-        torch.cuda.synchronize()
-        s1.sync()
-        t_seq += a0.elapsed_time(a1) / 1000.0
-        s1.close()
-    t_seq *= 256 / len(sample)
-    t_seq = max_over_ranks(t_seq)
+    # the same instances walked one at a time, by the plain complex128 path and
+    # by the complex64 path (instances after the first 64 are timed on a
+    # stride-4 sample and scaled by the instance count)
+    def sequential(precision) -> float:
+        t = 0.0
+        sample = list(range(0, 256, 4))
+        for i in sample:
+            w = ws[i]
+            s1 = qwalk.Sim(w.matrix, s_pad=8, precision=precision)
+            s1.state_init(w.b)
+            s1.apply_walk_step(2)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            s1.enqueue_walk_steps(50)
+            a1.record()
+            torch.cuda.synchronize()
+            s1.sync()
+            t += a0.elapsed_time(a1) / 1000.0
+            s1.close()
+        return max_over_ranks(t * 256 / len(sample))
+
+    t_seq = sequential(qwalk.QW_FP64)
+    t_seq32 = sequential(qwalk.QW_FP32_AMP)
     steps = max(1, stats["steps"])
     return {"workload": "batched_256_n64-4096_s8", "instances": 256,
             "branches_per_step": stats["out"] / steps,
@@ -396,7 +401,9 @@ def batched_leg(args, torch, flush, barrier, max_over_ranks, world, rank) -> dic
             "variant": variant, "autotune_us_per_step": tune,
             "walk_50_steps_ms_graph": 1000.0 * t_walk,
             "sequential_fp64_walk_50_steps_ms": 1000.0 * t_seq,
-            "speedup_vs_sequential_fp64": t_seq / t_walk}
+            "speedup_vs_sequential_fp64": t_seq / t_walk,
+            "sequential_fp32_walk_50_steps_ms": 1000.0 * t_seq32,
+            "speedup_vs_sequential_same_precision": t_seq32 / t_walk}
 
 
 # Table 1: average time per walk step of the paper's simulator on one core of
