@@ -16,7 +16,9 @@
  *   - the return value is QW_OK (0) or a negative QW_ERR_* code; nothing
  *     throws across the ABI; qw_last_error() gives a message for the last
  *     failure on that simulator;
- *   - host arrays belong to the caller and are copied during the call;
+ *   - host arrays belong to the caller and are copied during the call (the
+ *     copy may be asynchronous from pinned memory; the call still returns
+ *     only when it no longer reads them);
  *     device memory belongs to the simulator and is freed by qw_sim_destroy;
  *   - work is issued in order on the stream given at creation; functions that
  *     return data to host arrays synchronise that stream before returning.
@@ -39,8 +41,10 @@ extern "C" {
 #define QW_ERR_STATE (-6)         /* call out of order (e.g. no state yet) */
 
 #define QW_FP64 0     /* complex128 amplitudes, FP64 arithmetic */
-#define QW_FP32_AMP 1 /* complex64 amplitudes in memory; merge, norm, renormalisation
-                         and success probability in FP64 */
+#define QW_FP32_AMP 1 /* complex64 amplitudes in memory; rotations and the reflection
+                         sum from error-free FP32 products and sums (~48-bit float
+                         pairs); norm, renormalisation, QLS read-out and success
+                         probability in FP64 */
 
 /* Register ids for qw_measure_register. */
 #define QW_REG_JC 0
