@@ -202,6 +202,10 @@ def test_qls_n16_matches_oracle():
 
 @pytest.mark.parametrize("precision", [qwalk.QW_FP64, qwalk.QW_FP32_AMP])
 def test_qls_n1024_fidelity(precision):
+    """The CKS solve of the cond(A) = 100 N = 1024 system against the dense
+    FP64 theory: Y = sum_j a_j T_{2j+1}(A/s) b, p_j = ||Y_j||^2 at every j, and
+    the fidelity to the dense solve.  complex128: 1e-9 relative; complex64:
+    |dp_j| / p_j <= 1e-4 and |dF| <= 1e-4 (the reduced-precision targets)."""
     w = wl.qls_n1024()
     coeffs, j0, b_int = qwalk.cks_coefficients(w.kappa, 1e-3)
     sim = _sim(w, precision=precision)
@@ -210,18 +214,23 @@ def test_qls_n1024_fidelity(precision):
     a = w.matrix.dense() / w.s
     t_prev, t_cur = w.b.copy(), a @ w.b
     want = coeffs[0] * t_cur
+    want_p = [float(want @ want)]
     for j in range(1, j0 + 1):
         for _ in range(2):
             t_prev, t_cur = t_cur, 2 * (a @ t_cur) - t_prev
         want = want + coeffs[j] * t_cur
+        want_p.append(float(want @ want))
     x = dense.qls_reference(w.matrix.dense(), w.b)
     f = dense.fidelity(x, y)
+    df = abs(f - dense.fidelity(x, want))
     rel = np.linalg.norm(y - want) / np.linalg.norm(want)
-    print(f"QLS N=1024 precision={precision}: j0={j0} F={f:.8f} rel.err vs dense {rel:.3e}")
+    rel_p = float(np.max(np.abs(p - np.array(want_p)) / np.array(want_p)))
+    print(f"QLS N=1024 precision={precision}: j0={j0} F={f:.8f} |dF|={df:.2e} "
+          f"rel.err vs dense {rel:.3e} max |dp|/p {rel_p:.2e}")
     if precision == qwalk.QW_FP64:
-        assert rel < 1e-9
+        assert rel < 1e-9 and rel_p < 1e-9
     else:
-        assert rel < 1e-3
+        assert rel < 1e-3 and rel_p <= 1e-4 and df <= 1e-4
     assert f > 0.999
 
 
