@@ -44,7 +44,16 @@
  *     acting on b2, R^dag its conjugate transpose.
  *   - P = 2 Pi - 1: the sign flips unless b1, k, b2, jc, kc are all zero
  *     (Alg. "Quantum walk operator"; Eq. (impl)).
+ *     Optionally (or_set_rot_bits) the angle arccos(sqrt|a|) is first rounded
+ *     to a multiple of (pi/2) / 2^bits, a fixed-point angle register as in
+ *     Table 2, and f, g are its cosine and sine.
  *   - H of T~ acts on the low log2(s) bits of register k (Sec. IV, T~).
+ *
+ * Pins: the test-suite checks this oracle against closed forms, brute force
+ * and the paper's printed examples.  Parity unpinned: the amplitudes of
+ * garbage branches (jc or kc != 0, rows j >= N) follow only from the readings
+ * above -- no closed form of the paper reaches them -- and are compared with
+ * the CUDA path as they stand.
  */
 #include <complex.h>
 #include <math.h>
