@@ -526,3 +526,20 @@ def test_qls_fidelity_against_the_width_of_the_angle_register():
     print("QLS fidelity by angle-register bits:", {k: round(v, 8) for k, v in fid.items()})
     assert fid[0] > 0.999 and fid[16] > 0.999
     assert fid[6] < fid[16]
+
+
+def test_complex64_with_64bit_in_kernel_keys_against_fp64_oracle():
+    """N = 20000 (64-bit in-kernel keys) in complex64, pipelined segments,
+    against the FP64 oracle over the union of keys after 4 steps."""
+    from parity import compare_union_arrays, gpu_arrays, oracle_arrays
+    w = wl.small_random(20000, 4, 23, band=1, attempts=20000)
+    sim = _sim(w, precision=qwalk.QW_FP32_AMP, walk_variant=3)
+    sim.state_init(w.b)
+    sim.apply_walk_step(4)
+    o = _oracle(w)
+    o.apply("T")
+    for _ in range(4):
+        o.apply("W")
+    st = compare_union_arrays(gpu_arrays(sim), oracle_arrays(o), 2e-6, 1e-5)
+    print(f"complex64 N=20000 step 4: {st}")
+    sim.close()
