@@ -43,8 +43,9 @@ extern "C" {
 #define QW_FP64 0     /* complex128 amplitudes, FP64 arithmetic */
 #define QW_FP32_AMP 1 /* complex64 amplitudes in memory; rotations and the reflection
                          sum from error-free FP32 products and sums (~48-bit float
-                         pairs); norm, renormalisation, QLS read-out and success
-                         probability in FP64 */
+                         pairs); each thread's share of the norm as a float pair,
+                         its reductions, the renormalisation factor, the QLS
+                         read-out and the success probability in FP64 */
 
 /* Register ids for qw_measure_register. */
 #define QW_REG_JC 0
@@ -212,12 +213,15 @@ int qw_apply_qls(qw_sim *sim, int32_t inst, const double *coeffs, int64_t j0, do
                  double *psucc_out);
 
 /*
- * Marginal distribution of one register of instance inst:
+ * Marginal distribution of one register of instance inst (the read-out of
+ * Sec. V-B: the success probability p_j of the post-selection is the weight
+ * of the flag registers' zero value, a marginal of the state):
  * probs[v] = sum over branches with register value v of |a|^2, v < len.
  * reg_id is one of QW_REG_*.  The histogram is accumulated in a device
- * scratch array that the simulator keeps for later calls (allocated when len
- * exceeds every earlier len) and copied straight into probs (asynchronous
- * when probs is pinned); the call synchronises before it returns.
+ * scratch array that the simulator keeps for later calls; the call allocates
+ * it with cudaMalloc when len exceeds every earlier len of this simulator.
+ * The result is copied straight into probs (asynchronous when probs is
+ * pinned); the call synchronises before it returns.
  * Errors: QW_ERR_ARG, QW_ERR_STATE, QW_ERR_CUDA.
  */
 int qw_measure_register(qw_sim *sim, int32_t inst, int32_t reg_id, double *probs, int64_t len);
@@ -230,23 +234,25 @@ int qw_measure_register(qw_sim *sim, int32_t inst, int32_t reg_id, double *probs
 
 /*
  * qw_measure_register without any device allocation.  No counterpart in the
- * paper: this is a service of the library, for callers that cannot call
- * cudaMalloc or cudaMallocAsync at this point -- for instance code running
- * while its stream is being captured into a CUDA graph, a runtime whose
- * memory is owned by another allocator with no headroom left, or a loop that
- * must not touch the allocator for latency reasons.  qw_measure_register
- * obtains a temporary device histogram per call; this entry point
- * accumulates into a fixed 512 KiB array of the library's device image
- * instead, which every GPU that loads the library keeps until the process
- * exits.  Same arguments and result (probs is a host array of len doubles).
+ * paper: a service of the library for callers that cannot call cudaMalloc or
+ * cudaMallocAsync when they measure -- a runtime whose device memory is owned
+ * by another allocator that has no headroom left (a cudaMalloc there fails,
+ * or evicts the owner's cached blocks), or a loop that must not enter the
+ * allocator for latency reasons (a cudaMalloc may synchronise the device).
+ * qw_measure_register may allocate its histogram (the first time a len is
+ * larger than every earlier one); this entry point never allocates: it
+ * accumulates into a fixed 512 KiB array of the library's device image,
+ * which every GPU that loads the library keeps until the process exits.  Same
+ * arguments and result (probs is a host array of len doubles).
  * Limits and caveats:
  *   - len must be <= QW_MEASURE_NOALLOC_MAX_LEN, else QW_ERR_ARG;
  *   - the first call on a device looks up the array's device address once
- *     (cudaGetSymbolAddress); make that first call before any stream
- *     capture begins;
- *   - all calls share the one array: each call zeroes the bins it uses before
- *     accumulating, but calls whose GPU work overlaps (issued on different
- *     streams with no ordering between them) race and give wrong results;
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture begins;
+ *   - all calls share the one array and it keeps the last call's contents:
+ *     each call zeroes the bins it uses before accumulating, but calls whose
+ *     GPU work overlaps (issued on different streams with no ordering between
+ *     them) race on it and give wrong results;
  *   - like qw_measure_register it synchronises the simulator's stream.
  * Errors: QW_ERR_ARG, QW_ERR_STATE, QW_ERR_CUDA.
  */
@@ -257,7 +263,10 @@ int qw_measure_register_noalloc(qw_sim *sim, int32_t inst, int32_t reg_id, doubl
 int qw_state_size(qw_sim *sim, int32_t inst, int64_t *count);
 
 /*
- * Export instance inst (-1: all) in canonical order: keys ascending.  Each
+ * Export instance inst (-1: all): the simulator's state array -- the list of
+ * (register key, amplitude) branches of Sec. V-A ("Main idea": the packed
+ * registers of a basis state, and its complex amplitude) -- in canonical
+ * order, keys ascending.  Each
  * key occupies key_words (1..10) uint64 words, least significant word first,
  * zero-extended; the packed layout from bit 0 up is
  *   b2 (1) | k (nb) | kc (nb) | b1 (1) | j (nb) | jc (nb) | A (16) | inst (16).
@@ -269,8 +278,8 @@ int qw_state_export(qw_sim *sim, int32_t inst, int32_t key_words, uint64_t *keys
                     int64_t cap, int64_t *count);
 
 /*
- * Replace the whole state (every instance) by the count branches given in the
- * packed layout of qw_state_export (key_words words per key, the instance
+ * Replace the whole state (every instance) -- the branch list of Sec. V-A --
+ * by the count branches given in the packed layout of qw_state_export (key_words words per key, the instance
  * field included) with amplitudes amps (2 doubles each): checkpoint / resume,
  * or any state of the register space.  Keys must be distinct, name existing
  * instances, and hold A = 0 (A is zero between walk steps).  The

@@ -929,7 +929,9 @@ extern "C" int qw_measure_register(qw_sim *sim, int32_t inst, int32_t reg, doubl
 
 /* Same result as qw_measure_register, for callers that must not allocate
  * device memory: the histogram lives in a fixed scratch array of the library
- * (see qw_kernels.cu) instead of a per-call cudaMallocAsync buffer. */
+ * (qw_kernels.cu) instead of the simulator's histogram, which
+ * qw_measure_register allocates with cudaMalloc when a len exceeds every
+ * earlier one.  This call never allocates. */
 extern "C" int qw_measure_register_noalloc(qw_sim *sim, int32_t inst, int32_t reg, double *probs,
                                            int64_t len)
 {

@@ -1,21 +1,31 @@
 /*
  * qw_kernels.cu -- sm_103a kernels of the sparse-state quantum walk.
  *
- * One walk step W = S T~ P T~^dag (Alg. "Quantum walk operator") is one launch
- * of k_step.  T~^dag, P and T~ never change the registers (jc, j, b1) and every
- * QRAM read they make (O_A', O_s', QBS) indexes row j, so each (jc, j, b1) row
- * of the state evolves independently until S.  One warp takes one row: it
- * loads the row's branches into its slice of shared memory together with the
- * row's s QRAM words, runs the whole T~^dag P T~ on chip -- the per-branch
- * register maps (semi-quantum ops, Sec. V-A), and the interference ops R^dag,
- * H P H and R as sort + per-group transform + pruning (Sec. V-A, interference
- * paragraph) -- then applies S and appends every branch to the bucket of its
- * new row with one atomic per branch.  The HBM traffic of a step is one read
- * and one write of the state.
+ * The product's walk step W = S T~ P T~^dag (Alg. "Quantum walk operator") is
+ * one launch of k_walk.  T~^dag, P and T~ never change the registers
+ * (jc, j, b1) and every QRAM read they make (O_A', O_s', QBS) indexes row j,
+ * so each (jc, j, b1) row of the state evolves independently until S.  One
+ * warp takes the two rows (jc, j, b1 = 0 / 1) of a j: it loads their branches
+ * with the row's s QRAM words, runs T~^dag P T~ on chip -- the register maps
+ * (semi-quantum ops, Sec. V-A) and the interference ops R^dag, H P H and R
+ * (the interference paragraph of Sec. V-A: grouping, per-group transform,
+ * pruning), with b2-pairs found by warp matching instead of a sort and H P H
+ * folded into R^dag's pass -- then applies S and appends every branch to the
+ * bucket of its new row with one atomic per branch.  The HBM traffic of a
+ * step is one read and one write of the state.  k_step runs the same step in
+ * the paper's literal schedule (every map, H, P, H as three interference ops,
+ * a rank sort before each); it is the plain reference schedule on the GPU.
  *
- * Arithmetic: register maps are exact integer work; amplitudes are combined in
- * FP64 whatever the storage type; the prune decision |a|^2 <= tau^2 is taken
- * with un-fused FP64 multiplies and adds.
+ * Arithmetic: register maps are exact integer work; the prune decision
+ * |a|^2 <= tau^2 is taken with un-fused multiplies and adds.  complex128
+ * amplitudes: FP64 throughout.  complex64 amplitudes: each rotation output
+ * f a0 +- g a1 is formed from error-free products (the FMA-based TwoProduct)
+ * and Knuth's error-free TwoSum on the FP32 pipe, with f and g held as float
+ * pairs (~48 significant bits), and rounded to FP32 once; the zero-type
+ * group sum of H P H is a float-pair accumulation by TwoSum; each lane's norm
+ * share adds the FP32-rounded |a|^2 by TwoSum, and the block and grid
+ * reductions of the norm, the renormalisation factor, the QLS read-out and
+ * p_j are FP64.
  */
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -850,7 +860,9 @@ template <> struct Amp<double2> {
 template <> struct Amp<float2> {
     typedef float2 T;
     static constexpr bool kHeadLanes = false;
-    struct Norm { /* float-pair accumulator, exact up to ~2^-46 relative */
+    struct Norm { /* |a|^2 rounded to FP32 once per branch (relative 2^-24), then
+                     summed by TwoSum into a float pair, so the sum adds no
+                     rounding error of note beyond those per-term roundings */
         float hi = 0.f, lo = 0.f;
         __device__ void add(T a)
         {
@@ -862,7 +874,8 @@ template <> struct Amp<float2> {
         }
         __device__ double get() const { return (double)hi + (double)lo; }
     };
-    /* float-pair (hi + lo) accumulator: error-free two-sums, ~48 bits */
+    /* float-pair (hi + lo) accumulator built from Knuth's TwoSum (the sum and
+       its exact rounding error), ~48 significant bits */
     struct DF {
         float h = 0.f, l = 0.f;
         __device__ void add(float v)
@@ -960,8 +973,9 @@ template <> struct Amp<float2> {
         __device__ explicit Scale(double v) : sh((float)v), sl((float)(v - (double)(float)v)) {}
         __device__ T apply(T a) const { return make_float2(mul_split(a.x, sh, sl), mul_split(a.y, sh, sl)); }
     };
-    /* round(A x + B y), A = ah + al, B = bh + bl: two error-free products and
-       an error-free sum, one final rounding */
+    /* round(A x + B y), A = ah + al, B = bh + bl: the products by the FMA-based
+       TwoProduct (p = fl(a b), e = fma(a, b, -p) exact), their sum by Knuth's
+       TwoSum, the low parts added to the error term, one final rounding */
     __device__ static float dot2(float ah, float al, float x, float bh, float bl, float y)
     {
         const float p1 = __fmul_rn(ah, x);
@@ -2125,14 +2139,18 @@ cudaError_t launch_step_t(const QwSimDev &d, const QwBufDev &in, const QwBufDev 
 
 } // namespace
 
+/* SM count of the current device, cached per device (launch shapes follow
+   the device the simulator issues on) */
 int qw_sm_count(void)
 {
-    static int n = 0;
+    constexpr int kDevs = 128;
+    static int cache[kDevs] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+    int n = dev < kDevs ? cache[dev] : 0;
     if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n < 1) n = 1;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+        if (dev < kDevs) cache[dev] = n;
     }
     return n;
 }
@@ -2248,7 +2266,7 @@ cudaError_t qw_launch_qls_norm(const double2 *y, int n, double *p, int64_t *jctr
 /* ---- measurement without device allocation ------------------------------------ */
 /*
  * Histogram scratch of qw_measure_register_noalloc, a fixed array in the
- * library's device image instead of a cudaMallocAsync buffer.  Every GPU that
+ * library's device image instead of an allocated buffer.  Every GPU that
  * loads the library holds it (QW_MEASURE_NOALLOC_MAX_LEN doubles, 512 KiB)
  * until the process exits.  All calls share it: each call zeroes the bins it
  * uses before the kernel accumulates into them, and two calls whose work

@@ -366,8 +366,10 @@ def test_graph_replay_equals_direct_launches(precision):
 def test_batched_256_instances_full_size(precision):
     """The batched workload at full size: 256 walks (N log-uniform in [64,
     4096], s = 8) advanced together, one launch per step (graph-replayed), 50
-    steps.  FP64: a sample of instances across the size range equals its own
-    oracle; both precisions: every instance keeps unit norm."""
+    steps.  A sample of instances across the size range equals its own FP64
+    oracle: complex128 keys exactly and amplitudes to 1e-12; complex64 over the
+    union of keys within the reduced-precision bounds (max |da| <= 2e-6,
+    ||da||_2 <= 1e-5).  Every instance keeps unit norm."""
     ws = wl.batched(256)
     sim = qwalk.Sim([w.matrix for w in ws], s_pad=8, precision=precision)
     for i, w in enumerate(ws):
@@ -376,9 +378,8 @@ def test_batched_256_instances_full_size(precision):
     for i, w in enumerate(ws):
         p = sim.measure_register("b2", 2, inst=i)
         assert abs(p.sum() - 1.0) < (1e-10 if precision == qwalk.QW_FP64 else 1e-5), i
-    if precision != qwalk.QW_FP64:
-        return
     by_size = sorted(range(len(ws)), key=lambda i: ws[i].n)
+    worst = {"max_abs": 0.0, "l2": 0.0}
     for i in by_size[::32] + [by_size[-1]]:
         w = ws[i]
         o = oracle.Oracle(w.matrix, 8)
@@ -386,7 +387,13 @@ def test_batched_256_instances_full_size(precision):
         o.apply("T")
         for _ in range(50):
             o.apply("W")
-        compare(gpu_state(sim, inst=i), oracle_state(o), TOL64)
+        if precision == qwalk.QW_FP64:
+            compare(gpu_state(sim, inst=i), oracle_state(o), TOL64)
+        else:
+            st = compare_union(gpu_state(sim, inst=i), oracle_state(o), 2e-6, 1e-5)
+            worst = {k: max(worst[k], st[k]) for k in worst}
+    if precision != qwalk.QW_FP64:
+        print(f"complex64 batched, 50 steps, worst sampled instance: {worst}")
 
 
 def test_checkpoint_round_trip():

@@ -475,3 +475,56 @@ def test_fixed_point_rotation_angle_block_encoding_and_chebyshev(oracle_mod, bit
         y = _flag0_after_tdag(oracle_mod, o, w.matrix, w.s, rot_bits=bits)
         assert np.abs(y - ref[mstep]).max() < 1e-12, mstep
     assert o.violations == 0
+
+
+# --- register marginals (the read-out behind qw_measure_register) ---------------------
+
+def test_marginal_of_hand_built_state_against_dense_tensor(oracle_mod):
+    """or_marginal on a state imported branch by branch equals the marginal of
+    the dense probability tensor over (jc, j, b1, kc, k, b2), summed over the
+    other five axes; every register's marginal sums to the norm."""
+    w = wl.small_random(4, 2, 5)  # N = 4: nb = 2, a 4*4*2*4*4*2 = 1024-state space
+    o = oracle_mod.Oracle(w.matrix, w.s)
+    dims = (1 << o.nb, 1 << o.nb, 2, 1 << o.nb, 1 << o.nb, 2)
+    rng = np.random.default_rng(31)
+    flat = rng.choice(int(np.prod(dims)), size=60, replace=False)
+    regs = np.stack(np.unravel_index(flat, dims), axis=1).astype(np.uint64)
+    amps = rng.standard_normal(60) + 1j * rng.standard_normal(60)
+    o.set_state(regs, amps)
+    psi = np.zeros(dims, dtype=complex)
+    psi[tuple(regs.astype(np.int64).T)] = amps
+    prob = np.abs(psi) ** 2
+    names = ("jc", "j", "b1", "kc", "k", "b2")
+    for axis, name in enumerate(names):
+        others = tuple(a for a in range(6) if a != axis)
+        want = prob.sum(axis=others)
+        got = o.marginal(name, dims[axis])
+        assert np.abs(got - want).max() < 1e-13, name
+        assert abs(got.sum() - o.norm2()) < 1e-12, name
+    # values at or above len are left out
+    assert np.abs(o.marginal("j", 2) - prob.sum(axis=(0, 2, 3, 4, 5))[:2]).max() < 1e-13
+
+
+def test_marginals_after_t_follow_the_rotation(oracle_mod):
+    """After T~|b~> (Alg. T~): the j marginal is |b_j|^2 (T~ acts within row j);
+    b2 = 0 has probability sum_j |b_j|^2 sum_l |a_jl| / s (f^2 = |a|, g^2 = 1 - |a|,
+    Sec. IV); the k marginal is sum over rows j holding column k in a slot of
+    |b_j|^2 / s (the padded list of Sec. II-C, restated by padded_rows)."""
+    w = wl.small_random(24, 8, 13)
+    o = oracle_mod.Oracle(w.matrix, w.s)
+    o.init_b(w.b)
+    o.apply("T")
+    nlen = 1 << o.nb
+    b2 = np.abs(w.b) ** 2
+    assert np.abs(o.marginal("j", nlen)[:w.n] - b2).max() < 1e-14
+    rows = padded_rows(w.matrix, w.s)
+    p0 = sum(b2[j] * np.abs(rows[j][1].astype(np.float64) / 32768.0).sum() / w.s for j in range(w.n))
+    pb2 = o.marginal("b2", 2)
+    assert abs(pb2[0] - p0) < 1e-14 and abs(pb2[1] - (1.0 - p0)) < 1e-14
+    pk = np.zeros(nlen)
+    for j in range(w.n):
+        pk[rows[j][0]] += b2[j] / w.s
+    assert np.abs(o.marginal("k", nlen) - pk).max() < 1e-14
+    for name, ln in (("jc", nlen), ("kc", nlen), ("b1", 2)):
+        p = o.marginal(name, ln)
+        assert abs(p[0] - 1.0) < 1e-14 and np.abs(p[1:]).max() == 0.0, name

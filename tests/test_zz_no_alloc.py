@@ -1,9 +1,10 @@
 """qw_measure_register_noalloc against qw_measure_register, through the C ABI.
 
-The no-allocation entry point serves callers that cannot call cudaMalloc at
-measurement time (code inside a stream capture, or under an allocator with no
-headroom); it accumulates into a fixed scratch array in the library instead
-of a temporary buffer.  It must give the same marginals as the allocating
+The no-allocation entry point serves callers that cannot call cudaMalloc when
+they measure: a runtime whose device memory belongs to another allocator with
+no headroom left, or a loop that must not enter the allocator for latency.  It
+accumulates into a fixed scratch array of the library instead of the
+simulator's own histogram (which qw_measure_register may allocate).  It must give the same marginals as the allocating
 call, also on consecutive calls (the shared scratch is re-zeroed each time),
 and reject lengths above its fixed limit.  This file is collected last so a
 failure here stops a -x run only after every other test has run.
