@@ -48,13 +48,13 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--fp64-steps", type=int, default=1000)
     p.add_argument("--e2e-jobs", type=int, default=10)
-    p.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batched-steps", type=int, default=300)
     p.add_argument("--no-table1", action="store_true")
     p.add_argument("--no-qls", action="store_true")
     p.add_argument("--no-mmax", action="store_true")
+    p.add_argument("--no-configs", action="store_true", help="skip the N=16 and N=1024 walk legs")
     return p.parse_args()
 
 
@@ -188,6 +188,62 @@ def algorithmic_bytes(stats: dict, nb: int, amp_bytes: int) -> tuple[float, floa
     return b_alg, b_min
 
 
+def _canonical(regs, amps):
+    import numpy as np
+    regs = np.ascontiguousarray(regs[:, :7], dtype=np.uint64)
+    order = np.lexsort(tuple(regs[:, c] for c in range(6, -1, -1)))
+    return regs[order], np.asarray(amps)[order]
+
+
+def state_error(gpu, ref) -> dict:
+    """Error of a GPU state against the oracle's, over the union of keys (a
+    key held by one side only counts as amplitude 0 on the other): max |da|,
+    ||da||_2, and how many keys (and the largest |a| among them) one side
+    alone holds."""
+    import numpy as np
+    (kg, ag), (kr, ar) = _canonical(*gpu), _canonical(*ref)
+    both = np.concatenate([kg, kr])
+    _, inv = np.unique(both.view(np.dtype((np.void, 56))).ravel(), return_inverse=True)
+    inv = inv.ravel()
+    m = int(inv.max()) + 1 if inv.size else 0
+    vg, vr = np.zeros(m, complex), np.zeros(m, complex)
+    hg, hr = np.zeros(m, bool), np.zeros(m, bool)
+    vg[inv[:len(kg)]], hg[inv[:len(kg)]] = ag, True
+    vr[inv[len(kg):]], hr[inv[len(kg):]] = ar, True
+    d = vg - vr
+    one = hg ^ hr
+    return {"max_abs": float(np.abs(d).max()) if m else 0.0, "l2": float(np.linalg.norm(d)),
+            "keys": m, "keys_equal": bool(not one.any()), "one_sided": int(one.sum()),
+            "one_sided_max_abs": float((np.abs(vg) + np.abs(vr))[one].max()) if one.any() else 0.0}
+
+
+def gpu_walk_state(w, precision, steps: int, variant: int | None = None):
+    """(regs, amps) of the GPU walk T~ then ``steps`` walk steps (fresh simulator)."""
+    from paper_2303_06890_gb300 import qwalk
+    kw = {} if variant is None else {"walk_variant": variant}
+    sim = qwalk.Sim(w.matrix, s_pad=w.s, precision=precision, **kw)
+    sim.state_init(w.b, apply_T=True)
+    sim.apply_walk_step(steps)
+    keys, amps = sim.state_export(key_words=2 if 4 * sim.nb + 34 <= 128 else 10)
+    regs = sim.unpack(keys)
+    sim.close()
+    return regs, amps
+
+
+def oracle_walk(w, steps: int):
+    """The oracle (plain C, FP64, one thread) on T~ then ``steps`` walk steps:
+    its state and its walk-step rate."""
+    import oracle
+    o = oracle.Oracle(w.matrix, w.s)
+    o.init_b(w.b)
+    o.apply("T")
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.apply("W")
+    dt = time.perf_counter() - t0
+    return o, dt
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -287,9 +343,25 @@ def run_ours(args, rank, world, local_rank):
     qls = None if args.no_qls else qls_leg(torch, barrier, max_over_ranks)
     mmax = None if args.no_mmax else mmax_leg()
 
-    cpu = None
+    cpu, err = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, args.cpu_budget)
+        # the oracle walks the benchmarked workload (T~ + its 20 steps, ~10 s on
+        # one core): its rate is the CPU baseline, its state the reference of
+        # the per-result error of both GPU precisions (fresh walks of 20 steps,
+        # outside every timed region)
+        o, dt = oracle_walk(w, w.steps)
+        cpu = {"value": w.steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the whole {w.steps}-step N=16384 walk after T~ ({dt:.1f} s, {o.size()} branches), "
+                         f"plain C FP64 register-level oracle, one thread"}
+        ref = o.export()
+        err = {"walk_n16384_complex64_20_steps": state_error(gpu_walk_state(w, qwalk.QW_FP32_AMP, w.steps, variant),
+                                                              ref),
+               "walk_n16384_complex128_20_steps": state_error(gpu_walk_state(w, qwalk.QW_FP64, w.steps), ref),
+               "bounds": {"complex128": "keys equal, max |da| <= 1e-12",
+                          "complex64": "max |da| <= 2e-6, ||da||_2 <= 1e-5 over the union of keys"}}
+        del o
+        if not args.no_configs:
+            err.update(configs_leg(torch))
 
     if dist is not None:
         dist.barrier()
@@ -331,6 +403,8 @@ def run_ours(args, rank, world, local_rank):
         line["mmax"] = mmax
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if err is not None:
+        line["error_vs_oracle"] = err
     print(json.dumps(line), flush=True)
 
 
@@ -392,6 +466,20 @@ def batched_leg(args, torch, flush, barrier, max_over_ranks, world, rank) -> dic
 
     t_seq = sequential(qwalk.QW_FP64)
     t_seq32 = sequential(qwalk.QW_FP32_AMP)
+    # error of the complex64 batched walk against each instance's oracle, on
+    # the smallest, a middle and the largest instance (after 50 steps)
+    err = {}
+    if rank == 0:
+        sim = qwalk.Sim([w.matrix for w in ws], s_pad=8, precision=qwalk.QW_FP32_AMP, walk_variant=variant)
+        for i, w in enumerate(ws):
+            sim.state_init(w.b, inst=i)
+        sim.apply_walk_step(50)
+        by_size = sorted(range(len(ws)), key=lambda i: ws[i].n)
+        for i in (by_size[0], by_size[len(ws) // 2], by_size[-1]):
+            keys, amps = sim.state_export(inst=i)
+            o, _ = oracle_walk(ws[i], 50)
+            err[f"instance_{i}_n{ws[i].n}"] = state_error((sim.unpack(keys), amps), o.export())
+        sim.close()
     steps = max(1, stats["steps"])
     return {"workload": "batched_256_n64-4096_s8", "instances": 256,
             "branches_per_step": stats["out"] / steps,
@@ -403,7 +491,8 @@ def batched_leg(args, torch, flush, barrier, max_over_ranks, world, rank) -> dic
             "sequential_fp64_walk_50_steps_ms": 1000.0 * t_seq,
             "speedup_vs_sequential_fp64": t_seq / t_walk,
             "sequential_fp32_walk_50_steps_ms": 1000.0 * t_seq32,
-            "speedup_vs_sequential_same_precision": t_seq32 / t_walk}
+            "speedup_vs_sequential_same_precision": t_seq32 / t_walk,
+            "error_vs_oracle_complex64_50_steps": err}
 
 
 # Table 1: average time per walk step of the paper's simulator on one core of
@@ -493,6 +582,25 @@ def table1_leg(torch, barrier, max_over_ranks) -> dict:
     return out
 
 
+def _cks_theory(w, coeffs):
+    """Y_j = sum_{i<=j} a_i T_{2i+1}(A/s) b and p_j = ||Y_j||^2 in FP64 (the
+    identity before Eq. (fx)), by the three-term recurrence on the sparse A/s."""
+    import numpy as np
+    import scipy.sparse as sp
+    m = w.matrix
+    a = sp.csc_matrix((m.val_q15.astype(np.float64) / 32768.0 / w.s, m.rowidx, m.colptr), shape=(m.n, m.n)).tocsr()
+    t_prev, t_cur = w.b.astype(np.float64), a @ w.b
+    y = coeffs[0] * t_cur
+    p = np.empty(len(coeffs))
+    p[0] = y @ y
+    for j in range(1, len(coeffs)):
+        t_prev, t_cur = t_cur, 2.0 * (a @ t_cur) - t_prev
+        t_prev, t_cur = t_cur, 2.0 * (a @ t_cur) - t_prev
+        y = y + coeffs[j] * t_cur
+        p[j] = y @ y
+    return y, p
+
+
 def qls_leg(torch, barrier, max_over_ranks) -> dict:
     """The CKS solver (Sec. IV, Eq. (fx)) end to end through qw_apply_qls:
     * the cond(A) = 100 N = 1024 system with complex64 amplitudes, at its own
@@ -524,31 +632,48 @@ def qls_leg(torch, barrier, max_over_ranks) -> dict:
         x = np.linalg.solve(w.matrix.dense(), w.b)
         x /= np.linalg.norm(x)
         fid = float(abs(np.vdot(x, y)) ** 2 / np.vdot(y, y).real)
+        # the dense FP64 theory of the same run: Y = sum_j a_j T_{2j+1}(A/s) b
+        # by the Chebyshev recurrence (sparse A/s), p_j = ||Y_j||^2 at every j
+        y_th, p_th = _cks_theory(w, coeffs)
+        fid_th = float(abs(np.vdot(x, y_th)) ** 2 / np.vdot(y_th, y_th).real)
         out[label] = {"n": w.n, "s": w.s, "kappa_walk": w.kappa, "kappa_coefficients": kappa,
                       "j0": j0, "walk_steps": 2 * (j0 + 1),
                       "precision": "complex64" if prec == qwalk.QW_FP32_AMP else "complex128",
                       "seconds": t, "walk_steps_per_s": 2 * (j0 + 1) / t,
                       "fidelity": fid,
-                      "p_succ": float(p[-1] / np.abs(coeffs).sum() ** 2)}
+                      "p_succ": float(p[-1] / np.abs(coeffs).sum() ** 2),
+                      "error_vs_dense_theory": {
+                          "abs_dF": abs(fid - fid_th),
+                          "max_rel_dp_j": float(np.max(np.abs(p - p_th) / p_th)),
+                          "rel_dY": float(np.linalg.norm(y - y_th) / np.linalg.norm(y_th))}}
     return out
 
 
-def cpu_baseline(w, budget: float) -> dict:
-    """The oracle as it stands, single-threaded, on a bounded sample of the
-    same workload: T~ then walk steps until about ``budget`` seconds pass."""
-    import oracle
-
-    o = oracle.Oracle(w.matrix, w.s)
-    o.init_b(w.b)
-    o.apply("T")
-    steps, t0 = 0, time.perf_counter()
-    while steps < 1 or (time.perf_counter() - t0 < budget and steps < 50):
-        o.apply("W")
-        steps += 1
-    dt = time.perf_counter() - t0
-    return {"value": steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} walk steps of the same N=16384 walk after T~ ({dt:.1f} s, "
-                      f"{o.size()} branches), plain C FP64 register-level oracle"}
+def configs_leg(torch) -> dict:
+    """The two small walk workloads: N = 16 (10 steps, complex128) and N = 1024
+    (100 steps, complex128 and complex64).  Per workload and precision: the
+    device time per step of the whole walk issued as graph replays (state
+    resident), and the error of the final state against the oracle's."""
+    from paper_2303_06890_gb300 import qwalk
+    from paper_2303_06890_gb300 import workloads as wl
+    out = {}
+    for w, precs in ((wl.walk_n16(), (qwalk.QW_FP64,)), (wl.walk_n1024(), (qwalk.QW_FP64, qwalk.QW_FP32_AMP))):
+        o, dt = oracle_walk(w, w.steps)
+        ref = o.export()
+        row = {"n": w.n, "s": w.s, "steps": w.steps, "oracle_s_per_step": dt / w.steps}
+        for prec in precs:
+            label = "complex128" if prec == qwalk.QW_FP64 else "complex64"
+            sim = qwalk.Sim(w.matrix, s_pad=w.s, precision=prec)
+            sim.state_init(w.b)
+            sim.apply_walk_step(6)
+            reps = 20
+            t = _events_time(torch, lambda: [sim.enqueue_walk_steps(w.steps) for _ in range(reps)])
+            sim.sync()
+            sim.close()
+            row[label] = {"us_per_step": 1e6 * t / (reps * w.steps),
+                          "error": state_error(gpu_walk_state(w, prec, w.steps), ref)}
+        out[w.name] = row
+    return out
 
 
 def run_reference(args, rank, world):

@@ -6,6 +6,8 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
+import numpy as np  # noqa: E402
+
 import bench  # noqa: E402
 
 
@@ -35,3 +37,19 @@ def test_profiled_traffic_follows_the_kernel_source_hash(tmp_path, monkeypatch):
     stale.write_text(text.replace("kernel_source_sha256_16: `", "kernel_source_sha256_16: `0"))
     monkeypatch.setattr(bench, "PROFILE", str(stale))
     assert bench.profiled_traffic("fp32") is None
+
+
+def test_state_error_over_the_union_of_keys():
+    """The bench's per-result error: equal keys give the amplitude differences;
+    a key held by one side only counts as amplitude 0 on the other."""
+    regs = np.array([[0, 1, 0, 0, 2, 1, 0], [0, 3, 1, 0, 0, 0, 0], [0, 2, 0, 0, 1, 0, 0]], dtype=np.uint64)
+    a = np.array([0.5 + 0.5j, -0.25, 0.1j])
+    st = bench.state_error((regs, a), (regs[::-1], a[::-1]))
+    assert st["max_abs"] == 0.0 and st["keys_equal"] and st["keys"] == 3
+    b = a.copy()
+    b[1] += 1e-7
+    st = bench.state_error((regs, b), (regs[:2], a[:2]))
+    assert not st["keys_equal"] and st["one_sided"] == 1
+    assert abs(st["one_sided_max_abs"] - 0.1) < 1e-15
+    assert abs(st["max_abs"] - 0.1) < 1e-15
+    assert abs(st["l2"] - np.hypot(0.1, 1e-7)) < 1e-15
