@@ -77,7 +77,7 @@ def kernel_hash() -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-VARIANTS = ("rows", "rows, pipelined", "segments", "segments, pipelined")
+VARIANTS = ("rows", "rows, pipelined", "segments", "segments, pipelined", "slot lanes")
 
 
 def profiled_traffic(precision: str):
@@ -384,7 +384,8 @@ def run_ours(args, rank, world, local_rank):
         "fp32_speedup_vs_fp64": value / fp64["value"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": f"k_walk<float2, {VARIANTS[variant]}>",
+                     "kernel": ("k_walk_slot<float2, s = 16>" if variant == 4
+                                else f"k_walk<float2, {VARIANTS[variant]}>"),
                      "autotune_us_per_step": tune_us,
                      "algorithmic_bytes_per_launch": b_alg,
                      "state_bytes_per_launch": b_min,

@@ -92,7 +92,15 @@ typedef struct {
     int32_t walk_variant;    /* step kernel with fuse_reflection = 1 (see qw_autotune):
                                 0 = one row at a time (default), 1 = rows with a
                                 software-pipelined loop, 2 = the two rows of a j as one
-                                segment, 3 = segments, software-pipelined */
+                                segment, 3 = segments, software-pipelined, 4 = one lane
+                                per QRAM slot over groups of 32 / s consecutive j
+                                (s = 8, 16 or 32 and warp_capacity >= 2 row_capacity;
+                                what its lanes do not cover runs as in 2), 5 = the flat
+                                path: the paper's literal schedule on one list of all
+                                branches in device memory, each interference op a
+                                global radix sort by key, a per-group transform and a
+                                compaction (no capacity limit; the host synchronises
+                                between its stages, so no CUDA graph is used) */
     int32_t graphs;          /* 1 (default): runs of >= 6 walk steps are issued as replays
                                 of a captured 6-step CUDA graph; 0: one launch per step */
     int32_t spill_rows;      /* slots of the table holding rows with jc != 0 (reached only
@@ -105,6 +113,18 @@ typedef struct {
                                 (rounded half to even), f = cos, g = sin of it -- the
                                 square-root and arccos registers Table 2 lists for the
                                 conditional rotation */
+    int32_t overflow_fallback; /* 1 (default): a walk step whose rows outgrow row_capacity
+                                or the on-chip buffers is run again from its input on the
+                                flat path (walk_variant 5), and row_capacity grows to the
+                                largest row it produces (the row buckets are reallocated);
+                                qw_state_import grows it the same way.  0: such a step
+                                fails with QW_ERR_CAPACITY and the state is kept at the
+                                last completed step */
+    int32_t nparts;          /* row-partitioned walk: the rows are split among nparts
+                                simulators (1, the default: one simulator holds all) */
+    int32_t part;            /* this simulator's partition, 0 .. nparts - 1 */
+    int64_t outbox_capacity; /* branches each outbox segment (one per other partition)
+                                holds; 0 = auto (2 N s) */
 } qw_sim_opts;
 
 /* Fill *opts with the defaults above. */
@@ -149,9 +169,12 @@ int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, const double *b
  * Apply nsteps walk steps W = S T~ P T~^dag (Alg. "Quantum walk operator")
  * to every instance.  Each step is one launch over all rows; no host
  * synchronisation happens between steps.  The call synchronises once at the
- * end to read the device status word.
- * Errors: QW_ERR_STATE (no state), QW_ERR_CAPACITY (state kept at the last
- * completed step), QW_ERR_DEVICE_STATUS, QW_ERR_CUDA.
+ * end to read the device status word.  With overflow_fallback, steps that
+ * outgrew the row buckets or the on-chip buffers are run again on the flat
+ * path (then the call synchronises between those steps).
+ * Errors: QW_ERR_STATE (no state), QW_ERR_CAPACITY (without overflow_fallback,
+ * or when the grown buckets would not fit in device memory; state kept at the
+ * last completed step), QW_ERR_DEVICE_STATUS, QW_ERR_CUDA.
  */
 int qw_apply_walk_step(qw_sim *sim, int64_t nsteps);
 
@@ -168,20 +191,26 @@ int qw_enqueue_walk_steps(qw_sim *sim, int64_t nsteps);
  * Synchronise the stream and read the device status word.  On a device
  * error the state is the output of the last step that completed cleanly
  * (later steps did nothing) and the error code is returned:
- * QW_ERR_CAPACITY, QW_ERR_DEVICE_STATUS or QW_ERR_CUDA.
+ * QW_ERR_CAPACITY, QW_ERR_DEVICE_STATUS or QW_ERR_CUDA.  With
+ * overflow_fallback, steps enqueued since the last synchronising call that
+ * outgrew the buckets are first run again on the flat path.
  */
 int qw_sync(qw_sim *sim);
 
+/* Number of step-kernel variants (walk_variant 0 .. QW_WALK_VARIANTS - 1). */
+#define QW_WALK_VARIANTS 6
+
 /*
  * Autotuner of the fused step kernel: runs steps_per_candidate walk steps with
- * each of the four variants of walk_variant (rows or segments of two rows,
- * plain or software-pipelined), times them with CUDA events on the
- * simulator's stream, and keeps the fastest for all later steps.  Segments
- * are tried only when warp_capacity >= 2 row_capacity (true by default);
- * otherwise variants 2, 3 are skipped and reported as 0 us.  The state
- * advances by steps_per_candidate walk steps per variant tried (the variants
- * give the same results).  *choice (nullable) receives the variant,
- * *us_per_step (nullable, 4 doubles) the measured times.  Synchronises.
+ * each variant of walk_variant (rows or segments of two rows, plain or
+ * software-pipelined, one lane per QRAM slot), times them with CUDA events on
+ * the simulator's stream, and keeps the fastest for all later steps.
+ * Segments are tried only when warp_capacity >= 2 row_capacity (true by
+ * default), the slot kernel only then and for s = 8, 16 or 32; the flat path
+ * (variant 5) is never chosen; variants not tried are reported as 0 us.  The state advances by steps_per_candidate
+ * walk steps per variant tried (the variants give the same results).
+ * *choice (nullable) receives the variant, *us_per_step (nullable,
+ * QW_WALK_VARIANTS doubles) the measured times.  Synchronises.
  * Has no effect with fuse_reflection = 0.  Errors: QW_ERR_ARG, QW_ERR_STATE,
  * QW_ERR_CAPACITY, QW_ERR_CUDA.
  */
@@ -258,6 +287,70 @@ int qw_measure_register(qw_sim *sim, int32_t inst, int32_t reg_id, double *probs
  */
 int qw_measure_register_noalloc(qw_sim *sim, int32_t inst, int32_t reg_id, double *probs,
                                 int64_t len);
+
+/*
+ * Row-partitioned walk (no counterpart in the paper's single-core simulator;
+ * it follows from Sec. IV: T~^dag, P and T~ never change (jc, j, b1) and read
+ * only row j of the QRAM, so a simulator holding a set of rows advances them
+ * alone, and S, which moves a branch to row (kc, k, b2), is the one exchange
+ * of a step).  Partition p of nparts (qw_sim_opts.nparts, .part; one instance,
+ * fuse_reflection = 1, walk_variant <= 4, no QLS) owns the rows (0, j, b1)
+ * with j in [p R, (p + 1) R), R = ceil(N / nparts), and the garbage rows
+ * (jc != 0 or j >= N) whose (jc, j) hashes to p (qw_part_owner).
+ * qw_state_init stores only the owned rows of |b~>.  A walk step of a
+ * partition leaves the branches S sends to another partition's rows in that
+ * partition's outbox segment; they join the state once delivered to it with
+ * qw_part_inbox, before its next step.  Each partition's step records the
+ * norm of what it emitted (qw_part_norm); the renormalisation of the next
+ * step needs the global norm (qw_part_set_norm).  Steps are issued one at a
+ * time (no CUDA graph).
+ * Outbox entries (32 bytes): uint64 row key inst << 40 | jc << 20 | j << 1 |
+ * b1, uint64 local registers b2 | k << 1 | kc << (1 + nb), double re, im.
+ */
+typedef struct {
+    uint64_t rowkey, local;
+    double re, im;
+} qw_part_entry;
+
+/* Partition owning row (jc, j) of a walk on an N-row matrix split nparts
+ * ways (the rule above; host-only arithmetic, no device needed); -1 on a bad
+ * argument. */
+int qw_part_owner(int32_t n, int32_t nparts, int32_t jc, int32_t j);
+
+/*
+ * Copy the outbox segment toward partition dest, as left by the last walk
+ * step, into the caller's device buffer dst (cap entries); *count receives
+ * its length (more than cap: only cap copied).  Synchronises.
+ * Errors: QW_ERR_ARG, QW_ERR_STATE (not partitioned), QW_ERR_CUDA.
+ */
+int qw_part_outbox(qw_sim *sim, int32_t dest, qw_part_entry *dst, int64_t cap, int64_t *count);
+
+/*
+ * Append count entries received from other partitions (device memory,
+ * caller-owned) to the state; entries must name rows this partition owns.
+ * Synchronises.  Errors: QW_ERR_ARG, QW_ERR_STATE, QW_ERR_CAPACITY, QW_ERR_CUDA.
+ */
+int qw_part_inbox(qw_sim *sim, const qw_part_entry *entries, int64_t count);
+
+/* ||.||^2 of what this partition's last step emitted (its rows and its
+ * outboxes), in FP64.  Synchronises. */
+int qw_part_norm(qw_sim *sim, double *local_norm2);
+
+/* Set the renormalisation of the next step from the global norm (the sum of
+ * every partition's qw_part_norm): scale sqrt(target / global_norm2) when
+ * renormalising, else 1. */
+int qw_part_set_norm(qw_sim *sim, double global_norm2);
+
+/*
+ * nsteps steps of a walk partitioned among nparts simulators of one process
+ * on one device: each step runs every partition's step kernel, then moves
+ * every outbox segment to its destination by cudaMemcpyAsync (device to
+ * device) and appends it, then sets every partition's renormalisation from
+ * the summed norms.  Synchronises once per step.
+ * Errors: QW_ERR_ARG (not a set of partitions 0 .. nparts - 1 of one walk),
+ * QW_ERR_CAPACITY, QW_ERR_DEVICE_STATUS, QW_ERR_CUDA.
+ */
+int qw_part_walk(qw_sim **sims, int32_t nparts, int64_t nsteps);
 
 /* Number of branches of instance inst (inst = -1: all instances). */
 int qw_state_size(qw_sim *sim, int32_t inst, int64_t *count);

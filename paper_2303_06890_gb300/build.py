@@ -1,6 +1,6 @@
 """Build the CUDA library libqwalk.so in-tree for sm_103a with nvcc.
 
-The two translation units are compiled in parallel, then linked against the
+The translation units are compiled in parallel, then linked against the
 shared CUDA runtime (the one PyTorch also loads).  No cmake.
 """
 from __future__ import annotations
@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqwalk.so")
-SOURCES = ["qw_kernels.cu", "qw_api.cpp"]
+SOURCES = ["qw_kernels.cu", "qw_flat.cu", "qw_api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -30,7 +30,7 @@ def _stale(out: str, deps: list[str]) -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "qw_internal.h"),
+    headers = [os.path.join(CSRC, "qw_internal.h"), os.path.join(CSRC, "qw_device.cuh"),
                os.path.join(os.path.dirname(HERE), "include", "qwalk.h")]
     objs, procs = [], []
     for src in SOURCES:

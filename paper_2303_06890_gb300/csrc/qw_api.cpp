@@ -34,6 +34,8 @@ struct Scalars {
     unsigned long long counter;
     unsigned long long stats[QW_NSTAT];
     int64_t qls_j; /* current QLS term */
+    unsigned int deferred_ctr; /* slot kernel: units left to its last block */
+    unsigned int pad2;
 };
 
 /* the head of Scalars the host reads at every synchronising call */
@@ -90,6 +92,11 @@ struct qw_sim {
     uint16_t *unit_inst = nullptr;
     void *slot_rot = nullptr;
     double *partials = nullptr;
+    int32_t *deferred = nullptr; /* slot kernel: units left to its last block */
+    QwPartEntry *outbox = nullptr;      /* row-partitioned walk: outbox segments */
+    unsigned long long *outbox_count = nullptr;
+    QwPartEntry *inbox = nullptr;       /* staging of received entries (qw_part_walk) */
+    int64_t inbox_cap = 0;
     Scalars *sc = nullptr;
     double2 *qls_y = nullptr;
     double *qls_p = nullptr; /* p_j, j = 0..j0 */
@@ -103,6 +110,8 @@ struct qw_sim {
     StatusView *h_st = nullptr;
     int64_t device_bytes = 0;
     int64_t launches = 0;
+    int64_t issued = 0;    /* walk steps issued since the last synchronising call */
+    int64_t last_good = 0; /* clean steps of those, as the last check_status found */
     /* captured 6-step graphs, one per (buffer, scale slot) phase */
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
@@ -162,6 +171,10 @@ extern "C" void qw_sim_opts_default(qw_sim_opts *o)
     o->stream = nullptr;
     o->walk_variant = 0;
     o->graphs = 1;
+    o->overflow_fallback = 1;
+    o->nparts = 1;
+    o->part = 0;
+    o->outbox_capacity = 0;
 }
 
 /* Validate one CSC matrix; on success return its largest column count. */
@@ -277,11 +290,11 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     cudaGetDevice(&sim->device);
     sim->fp32 = o.precision == QW_FP32_AMP;
     sim->renorm = o.renorm < 0 ? sim->fp32 : (o.renorm != 0);
-    static const int kVariantMode[4] = {QW_MODE_WALK_FUSED, QW_MODE_WALK_FUSED_PF, QW_MODE_WALK_SEG,
-                                        QW_MODE_WALK_SEG_PF};
-    if (o.walk_variant < 0 || o.walk_variant > 3) {
+    static const int kVariantMode[QW_WALK_VARIANTS] = {QW_MODE_WALK_FUSED, QW_MODE_WALK_FUSED_PF, QW_MODE_WALK_SEG,
+                                                       QW_MODE_WALK_SEG_PF, QW_MODE_WALK_SLOT, QW_MODE_WALK_FLAT};
+    if (o.walk_variant < 0 || o.walk_variant >= QW_WALK_VARIANTS) {
         delete sim;
-        g_create_error = "qw_sim_create: walk_variant must be 0..3";
+        g_create_error = "qw_sim_create: walk_variant must be 0..5";
         return QW_ERR_ARG;
     }
     sim->mode = o.fuse_reflection ? kVariantMode[o.walk_variant] : QW_MODE_WALK_LITERAL;
@@ -312,8 +325,24 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     wc = std::max<int64_t>(wc, s);
     wc = std::max<int64_t>(wc, d.cap_row);
     d.warp_cap = (int)wc;
+    if (sim->mode == QW_MODE_WALK_SLOT && !qw_slot_supported(d)) {
+        g_create_error = "qw_sim_create: walk_variant 4 (one lane per QRAM slot) needs s = 8, 16 or 32";
+        qw_sim_destroy(sim);
+        return QW_ERR_ARG;
+    }
     if (o.rot_bits < 0 || o.rot_bits > 52) {
         g_create_error = "qw_sim_create: rot_bits must be in [0, 52]";
+        qw_sim_destroy(sim);
+        return QW_ERR_ARG;
+    }
+    if (o.nparts < 1 || o.nparts > 64 || o.part < 0 || o.part >= o.nparts || o.outbox_capacity < 0) {
+        g_create_error = "qw_sim_create: nparts must be in [1, 64] and part in [0, nparts)";
+        qw_sim_destroy(sim);
+        return QW_ERR_ARG;
+    }
+    if (o.nparts > 1 && (ninst != 1 || sim->mode == QW_MODE_WALK_LITERAL || sim->mode == QW_MODE_WALK_FLAT)) {
+        g_create_error = "qw_sim_create: a partitioned walk needs one instance, fuse_reflection = 1 and "
+                         "walk_variant <= 4";
         qw_sim_destroy(sim);
         return QW_ERR_ARG;
     }
@@ -342,6 +371,10 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     d.total_buckets = buckets + d.spill_slots;
     sim->n_of = hn;
     sim->bkt_of = hbkt;
+    d.nparts = o.nparts;
+    d.part = o.part;
+    d.part_rows = ((int64_t)mats[0].n + o.nparts - 1) / o.nparts;
+    d.outbox_cap = o.nparts > 1 ? (o.outbox_capacity > 0 ? o.outbox_capacity : 2 * (int64_t)mats[0].n * s) : 0;
     std::vector<uint32_t> himage((size_t)img_words);
     for (int i = 0; i < ninst; ++i) build_image(mats[i], s, himage.data() + himg[(size_t)i]);
     std::vector<double2> hfg(65536);
@@ -379,6 +412,12 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
                d.warp_cap / 2 >= std::max(d.s, d.cap_row))
             d.warp_cap /= 2;
         const size_t need = qw_step_smem_bytes(d, sim->fp32, sim->mode);
+        if (sim->mode == QW_MODE_WALK_SLOT && d.warp_cap < 2 * d.cap_row) {
+            g_create_error = "qw_sim_create: walk_variant 4 runs the rows it does not cover as two-row segments, "
+                             "which need warp_capacity >= 2 row_capacity";
+            qw_sim_destroy(sim);
+            return QW_ERR_ARG;
+        }
         if (need > (size_t)optin) {
             g_create_error = "qw_sim_create: the step kernel needs " + std::to_string(need) +
                              " bytes of shared memory per block, the device allows " + std::to_string(optin) +
@@ -445,8 +484,17 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     if (sim->mode != QW_MODE_WALK_LITERAL) {
         for (int m : {QW_MODE_WALK_FUSED, QW_MODE_WALK_FUSED_PF, QW_MODE_WALK_SEG, QW_MODE_WALK_SEG_PF})
             gmax = std::max(gmax, qw_step_grid(d, sim->fp32, m));
+        if (qw_slot_supported(d)) gmax = std::max(gmax, qw_step_grid(d, sim->fp32, QW_MODE_WALK_SLOT));
     }
     QW_TRY(dalloc(sim, &sim->partials, (size_t)gmax));
+    QW_TRY(dalloc(sim, &sim->deferred, (size_t)(d.dense_buckets / 2 + d.spill_slots)));
+    if (d.nparts > 1) {
+        QW_TRY(dalloc(sim, &sim->outbox, (size_t)d.nparts * (size_t)d.outbox_cap));
+        QW_TRY(dalloc(sim, &sim->outbox_count, (size_t)d.nparts));
+        QW_TRY(cudaMemset(sim->outbox_count, 0, (size_t)d.nparts * 8));
+        d.outbox = sim->outbox;
+        d.outbox_count = sim->outbox_count;
+    }
     QW_TRY(dalloc(sim, &sim->sc, 1));
     Scalars z{};
     z.scale[0] = z.scale[1] = 1.0;
@@ -486,6 +534,10 @@ extern "C" int qw_sim_destroy(qw_sim *sim)
     drop_graphs(sim);
     if (sim->cap_stream) cudaStreamDestroy(sim->cap_stream);
     cudaFree(sim->partials);
+    cudaFree(sim->deferred);
+    cudaFree(sim->outbox);
+    cudaFree(sim->outbox_count);
+    cudaFree(sim->inbox);
     cudaFree(sim->sc);
     cudaFree(sim->qls_y);
     cudaFree(sim->qls_p);
@@ -534,6 +586,8 @@ static int check_status(qw_sim *sim, const char *where)
     if (e != cudaSuccess) return cuda_fail(sim, e, where);
     const StatusView h = *sim->h_st;
     const int64_t good = h.done - sim->sync_done;
+    sim->last_good = good;
+    sim->issued = 0;
     if (h.status != 0) {
         sim->cur = (int)((sim->sync_cur + good) % 3);
         sim->scale_slot = sim->sync_slot ^ (int)(good & 1);
@@ -552,8 +606,9 @@ static int check_status(qw_sim *sim, const char *where)
     if (st & QW_ST_SPILL_FULL) m += " [garbage-row table full]";
     if (st & QW_ST_ANCILLA) m += " [register A not returned to zero]";
     if (st & QW_ST_NOT_BTILDE) m += " [a row was not |b~> before T~]";
+    if (st & QW_ST_OUTBOX_FULL) m += " [an outbox toward another partition is full: raise outbox_capacity]";
     m += "; state kept after " + std::to_string(good) + " clean steps since the last sync";
-    const int code = (st & (QW_ST_ROW_OVERFLOW | QW_ST_WARP_OVERFLOW | QW_ST_SPILL_FULL))
+    const int code = (st & (QW_ST_ROW_OVERFLOW | QW_ST_WARP_OVERFLOW | QW_ST_SPILL_FULL | QW_ST_OUTBOX_FULL))
                          ? QW_ERR_CAPACITY
                          : QW_ERR_DEVICE_STATUS;
     return fail(sim, code, m);
@@ -576,12 +631,20 @@ static QwStepArgs step_args(qw_sim *sim, int mode)
     a.qls_y = sim->qls_y;
     a.qls_coefs = sim->qls_c;
     a.qls_j = &sim->sc->qls_j;
+    a.deferred = sim->deferred;
+    a.deferred_ctr = &sim->sc->deferred_ctr;
     return a;
 }
+
+static int flat_walk_step(qw_sim *sim, int readout);
 
 /* one walk step: X_cur -> X_cur+1, clearing X_cur+2 */
 static int launch_walk(qw_sim *sim, int readout)
 {
+    if (sim->mode == QW_MODE_WALK_FLAT) return flat_walk_step(sim, readout);
+    if (sim->d.nparts > 1) /* the outboxes hold this step's sends only */
+        QW_CUDA(sim, cudaMemsetAsync(sim->outbox_count, 0, (size_t)sim->d.nparts * 8, sim->stream));
+    sim->issued++;
     QwStepArgs a = step_args(sim, sim->mode);
     a.qls_readout = readout;
     const int nxt = (sim->cur + 1) % 3, clr = (sim->cur + 2) % 3;
@@ -592,6 +655,207 @@ static int launch_walk(qw_sim *sim, int readout)
     sim->cur = nxt;
     sim->scale_slot ^= 1;
     return QW_OK;
+}
+
+/* Give the row buckets of all three buffers room for `need` branches per
+ * row (row_capacity doubles until it fits), keeping their contents.  Refused
+ * (QW_ERR_CAPACITY) when the buffers would take more than half of the device
+ * memory free now plus what they hold. */
+static int grow_rows(qw_sim *sim, int64_t need)
+{
+    int64_t cap = sim->d.cap_row;
+    while (cap < need) cap *= 2;
+    if (cap == sim->d.cap_row) return QW_OK;
+    const size_t amp_bytes = sim->fp32 ? sizeof(float2) : sizeof(double2);
+    const size_t per = 8 + amp_bytes;
+    const size_t oldb = 3 * (size_t)sim->d.total_buckets * (size_t)sim->d.cap_row * per;
+    const size_t newb = 3 * (size_t)sim->d.total_buckets * (size_t)cap * per;
+    QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
+    size_t freeb = 0, totb = 0;
+    QW_CUDA(sim, cudaMemGetInfo(&freeb, &totb));
+    if (newb > (freeb + oldb) / 2)
+        return fail(sim, QW_ERR_CAPACITY,
+                    "row buckets of " + std::to_string(cap) + " branches per row would need " + std::to_string(newb) +
+                        " bytes; device memory is short");
+    drop_graphs(sim);
+    const int cap_old = sim->d.cap_row;
+    const size_t slots = (size_t)sim->d.total_buckets * (size_t)cap;
+    sim->d.cap_row = (int)cap;
+    for (auto &b : sim->buf) {
+        uint64_t *key = nullptr;
+        unsigned char *amp = nullptr;
+        QW_CUDA(sim, dalloc(sim, &key, slots));
+        QW_CUDA(sim, dalloc(sim, &amp, slots * amp_bytes));
+        QW_CUDA(sim, qw_launch_regrow(sim->d, b, cap_old, key, amp, sim->fp32, sim->stream));
+        QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
+        cudaFree(b.key);
+        cudaFree(b.amp);
+        sim->device_bytes -= (int64_t)((size_t)sim->d.total_buckets * (size_t)cap_old * per);
+        b.key = key;
+        b.amp = amp;
+    }
+    return QW_OK;
+}
+
+/* One walk step on the flat path (qw_flat.cu): X_cur gathered into one list
+ * of 16-byte register keys and complex FP64 amplitudes, the paper's
+ * schedule op by op -- O_s'^dag O_A' O_s', R^dag (sort, pairs, compaction),
+ * O_s'^dag O_A', H (sort, groups, compaction), [QLS read-out], P, H,
+ * O_A' O_s', R, O_s'^dag O_A' O_s', A = 0 checked, S -- and the result
+ * stored into X_cur+1 (and X_cur+2 cleared, as a step kernel does), the row
+ * buckets grown when a row of it does not fit.  The host synchronises to size
+ * each stage; device scratch is stream-ordered (cudaMallocAsync) and freed
+ * before the call returns. */
+static int flat_walk_step(qw_sim *sim, int readout)
+{
+    QwSimDev &d = sim->d;
+    cudaStream_t st = sim->stream;
+    std::vector<void *> held;
+    auto alloc = [&](size_t bytes, void **p) -> cudaError_t {
+        *p = nullptr;
+        cudaError_t e = cudaMallocAsync(p, bytes < 16 ? 16 : bytes, st);
+        if (e == cudaSuccess) held.push_back(*p);
+        return e;
+    };
+    auto release = [&](void *p) {
+        for (auto &h : held)
+            if (h == p) {
+                cudaFreeAsync(p, st);
+                h = nullptr;
+            }
+    };
+    auto cleanup = [&]() {
+        for (void *h : held)
+            if (h) cudaFreeAsync(h, st);
+        held.clear();
+    };
+    int rc = QW_OK;
+#define QW_FLAT(call)                                                                              \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            cleanup();                                                                             \
+            return cuda_fail(sim, e_, #call);                                                      \
+        }                                                                                          \
+    } while (0)
+    /* the state size */
+    unsigned long long hc = 0;
+    QW_FLAT(cudaMemsetAsync(&sim->sc->counter, 0, 8, st));
+    QW_FLAT(qw_launch_count(d, sim->buf[sim->cur], -1, &sim->sc->counter, st));
+    QW_FLAT(cudaMemcpyAsync(&hc, &sim->sc->counter, 8, cudaMemcpyDeviceToHost, st));
+    QW_FLAT(cudaStreamSynchronize(st));
+    int64_t M = (int64_t)hc;
+    int64_t counts[5] = {M, 0, 0, 0, 0};
+    void *K = nullptr, *A = nullptr;
+    QW_FLAT(alloc((size_t)M * 16, &K));
+    QW_FLAT(alloc((size_t)M * 16, &A));
+    QW_FLAT(cudaMemsetAsync(&sim->sc->counter, 0, 8, st));
+    QW_FLAT(qw_flat_gather(d, sim->buf[sim->cur], sim->fp32, pending_scale(sim), K, static_cast<double2 *>(A),
+                           &sim->sc->counter, M, st));
+    int32_t *status = &sim->sc->status;
+    auto map = [&](uint32_t ops) { return qw_flat_map(d, K, M, ops, status, st); };
+    /* an interference op: 0 = R^dag, 1 = R, 2 = H */
+    auto stage = [&](int op) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        const int outs = op == 2 ? d.s : 2;
+        if (M > 1) {
+            void *tk, *ta, *work;
+            if ((e = alloc((size_t)M * 16, &tk)) != cudaSuccess) return e;
+            if ((e = alloc((size_t)M * 16, &ta)) != cudaSuccess) return e;
+            if ((e = alloc(qw_flat_sort_words(M) * 4, &work)) != cudaSuccess) return e;
+            e = qw_flat_sort(d, K, static_cast<double2 *>(A), tk, static_cast<double2 *>(ta), M, op == 2 ? 1 : 0,
+                             static_cast<uint32_t *>(work), st);
+            if (e != cudaSuccess) return e;
+            release(tk);
+            release(ta);
+            release(work);
+        }
+        const int64_t n = M * outs;
+        void *ok, *oa, *flags, *pos, *sums, *nk, *na;
+        if ((e = alloc((size_t)n * 16, &ok)) != cudaSuccess) return e;
+        if ((e = alloc((size_t)n * 16, &oa)) != cudaSuccess) return e;
+        if ((e = alloc((size_t)n * 4, &flags)) != cudaSuccess) return e;
+        if ((e = alloc((size_t)n * 4, &pos)) != cudaSuccess) return e;
+        if ((e = alloc(qw_flat_scan_words(n) * 4, &sums)) != cudaSuccess) return e;
+        if ((e = qw_flat_group(d, op, K, static_cast<double2 *>(A), M, ok, static_cast<double2 *>(oa),
+                               static_cast<uint32_t *>(flags), st)) != cudaSuccess)
+            return e;
+        uint32_t total = 0;
+        if (n > 0) {
+            if ((e = qw_flat_scan(static_cast<uint32_t *>(flags), n, static_cast<uint32_t *>(sums),
+                                  static_cast<uint32_t *>(pos), st)) != cudaSuccess)
+                return e;
+            const int64_t nb = (n + 1023) / 1024;
+            if ((e = cudaMemcpyAsync(&total, static_cast<uint32_t *>(sums) + nb, 4, cudaMemcpyDeviceToHost, st)) !=
+                cudaSuccess)
+                return e;
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        }
+        if ((e = alloc((size_t)total * 16, &nk)) != cudaSuccess) return e;
+        if ((e = alloc((size_t)total * 16, &na)) != cudaSuccess) return e;
+        if ((e = qw_flat_compact(ok, static_cast<double2 *>(oa), static_cast<uint32_t *>(flags),
+                                 static_cast<uint32_t *>(pos), n, nk, static_cast<double2 *>(na), st)) != cudaSuccess)
+            return e;
+        for (void *p : {K, A, ok, oa, flags, pos, sums}) release(p);
+        K = nk;
+        A = na;
+        M = (int64_t)total;
+        return cudaSuccess;
+    };
+    QwStepArgs a = step_args(sim, QW_MODE_WALK_FLAT);
+    a.qls_readout = readout;
+    /* T~^dag */
+    QW_FLAT(map(QW_FLAT_OSDAG | QW_FLAT_OA << 4 | QW_FLAT_OS << 8));
+    QW_FLAT(stage(0));
+    counts[1] = M;
+    QW_FLAT(map(QW_FLAT_OSDAG | QW_FLAT_OA << 4));
+    QW_FLAT(stage(2));
+    counts[2] = M;
+    if (readout) QW_FLAT(qw_flat_readout(d, K, static_cast<double2 *>(A), M, a, st));
+    /* P, then T~ */
+    QW_FLAT(qw_flat_phase(d, K, static_cast<double2 *>(A), M, st));
+    QW_FLAT(stage(2));
+    counts[3] = M;
+    QW_FLAT(map(QW_FLAT_OA | QW_FLAT_OS << 4));
+    QW_FLAT(stage(1));
+    counts[4] = M;
+    QW_FLAT(map(QW_FLAT_OSDAG | QW_FLAT_OA << 4 | QW_FLAT_OS << 8 | QW_FLAT_A0 << 12 | QW_FLAT_S << 16));
+    /* store into X_cur+1 */
+    void *norm = nullptr, *maxrow = nullptr;
+    QW_FLAT(alloc(8, &norm));
+    QW_FLAT(alloc(4, &maxrow));
+    const int nxt = (sim->cur + 1) % 3, clr = (sim->cur + 2) % 3;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        for (int bi : {nxt, clr})
+            QW_FLAT(qw_launch_clear(d, sim->buf[bi], 0, d.total_buckets, 1, st));
+        QW_FLAT(cudaMemsetAsync(norm, 0, 8, st));
+        QW_FLAT(cudaMemsetAsync(maxrow, 0, 4, st));
+        QW_FLAT(qw_flat_scatter(d, sim->buf[nxt], sim->fp32, K, static_cast<double2 *>(A), M, status,
+                                static_cast<unsigned int *>(maxrow), static_cast<double *>(norm), st));
+        StatusView hs{};
+        unsigned int hmax = 0;
+        QW_FLAT(cudaMemcpyAsync(sim->h_st, status, sizeof(StatusView), cudaMemcpyDeviceToHost, st));
+        QW_FLAT(cudaMemcpyAsync(&hmax, maxrow, 4, cudaMemcpyDeviceToHost, st));
+        QW_FLAT(cudaStreamSynchronize(st));
+        hs = *sim->h_st;
+        if (hs.status != QW_ST_ROW_OVERFLOW || attempt == 1 || !sim->opts.overflow_fallback) break;
+        /* a row of the result is longer than row_capacity: grow the buckets
+           (the gathered input is no longer needed) and store again */
+        const int32_t zero = 0;
+        QW_FLAT(cudaMemcpyAsync(status, &zero, 4, cudaMemcpyHostToDevice, st));
+        rc = grow_rows(sim, (int64_t)hmax);
+        if (rc != QW_OK) {
+            cleanup();
+            return rc;
+        }
+    }
+    QW_FLAT(qw_flat_finish(a, static_cast<double *>(norm), counts, st));
+    sim->launches += 1;
+    sim->cur = nxt;
+    sim->scale_slot ^= 1;
+    cleanup();
+#undef QW_FLAT
+    return check_status(sim, "walk step on the flat path");
 }
 
 extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, const double *b_im,
@@ -614,6 +878,11 @@ extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, cons
         QW_CUDA(sim, qw_launch_clear(sim->d, sim->buf[bi], all ? 0 : lo,
                                      all ? sim->d.total_buckets : hi, all ? 1 : 0, sim->stream));
         sim->launches++;
+    }
+    if (apply_T && sim->opts.overflow_fallback && sim->d.cap_row < 2 * sim->d.s) {
+        /* T~ gives a row of |b~> up to 2 s branches */
+        int rc = grow_rows(sim, 2 * (int64_t)sim->d.s);
+        if (rc != QW_OK) return rc;
     }
     double nb2 = 0.0;
     for (int j = 0; j < n; ++j) nb2 += b_re[j] * b_re[j] + (b_im ? b_im[j] * b_im[j] : 0.0);
@@ -719,7 +988,7 @@ extern "C" int qw_enqueue_walk_steps(qw_sim *sim, int64_t nsteps)
     if (nsteps > 0) sim->fresh_T = false;
     int64_t t = 0;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (sim->opts.graphs && nsteps >= kGraphSteps &&
+    if (sim->opts.graphs && sim->mode != QW_MODE_WALK_FLAT && sim->d.nparts == 1 && nsteps >= kGraphSteps &&
         cudaStreamIsCapturing(sim->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
         cudaGraphExec_t &g = sim->gexec[sim->cur][sim->scale_slot];
         if (!g) {
@@ -738,17 +1007,33 @@ extern "C" int qw_enqueue_walk_steps(qw_sim *sim, int64_t nsteps)
     return QW_OK;
 }
 
+/* Synchronise after walk steps.  With overflow_fallback, the steps that did
+ * nothing after one outgrew the buckets (the state is at the last clean
+ * step) are run on the flat path, which grows the buckets as needed. */
+static int sync_walk(qw_sim *sim, const char *where)
+{
+    const int64_t issued = sim->issued;
+    int rc = check_status(sim, where);
+    if (rc != QW_ERR_CAPACITY || !sim->opts.overflow_fallback) return rc;
+    for (int64_t t = sim->last_good; t < issued; ++t) {
+        rc = flat_walk_step(sim, 0);
+        if (rc != QW_OK) return rc;
+    }
+    sim->err.clear();
+    return QW_OK;
+}
+
 extern "C" int qw_sync(qw_sim *sim)
 {
     if (!sim) return QW_ERR_ARG;
-    return check_status(sim, "qw_sync");
+    return sync_walk(sim, "qw_sync");
 }
 
 extern "C" int qw_apply_walk_step(qw_sim *sim, int64_t nsteps)
 {
     int rc = qw_enqueue_walk_steps(sim, nsteps);
     if (rc != QW_OK) return rc;
-    return check_status(sim, "qw_apply_walk_step");
+    return sync_walk(sim, "qw_apply_walk_step");
 }
 
 extern "C" int qw_autotune(qw_sim *sim, int32_t steps, int32_t *choice, double *us_per_step)
@@ -759,16 +1044,20 @@ extern "C" int qw_autotune(qw_sim *sim, int32_t steps, int32_t *choice, double *
         if (choice) *choice = -1;
         return QW_OK;
     }
-    const int modes[4] = {QW_MODE_WALK_FUSED, QW_MODE_WALK_FUSED_PF, QW_MODE_WALK_SEG, QW_MODE_WALK_SEG_PF};
-    double us[4] = {0.0, 0.0, 0.0, 0.0};
+    const int modes[QW_WALK_VARIANTS] = {QW_MODE_WALK_FUSED, QW_MODE_WALK_FUSED_PF, QW_MODE_WALK_SEG,
+                                         QW_MODE_WALK_SEG_PF, QW_MODE_WALK_SLOT};
+    double us[QW_WALK_VARIANTS] = {0.0, 0.0, 0.0, 0.0, 0.0};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     QW_CUDA(sim, cudaEventCreate(&e0));
     QW_CUDA(sim, cudaEventCreate(&e1));
     int rc = QW_OK;
     const int graphs = sim->opts.graphs;
     sim->opts.graphs = 0; /* time the kernels themselves */
-    /* a segment holds two rows on chip: only tried when the warp buffer fits them */
-    const int nvar = sim->d.warp_cap >= 2 * sim->d.cap_row ? 4 : 2;
+    /* a segment holds two rows on chip: only tried when the warp buffer fits
+       them; the slot kernel (which falls back to segments) also needs
+       s = 8, 16 or 32 */
+    const bool seg = sim->d.warp_cap >= 2 * sim->d.cap_row;
+    const int nvar = seg ? (qw_slot_supported(sim->d) ? 5 : 4) : 2;
     for (int v = 0; v < nvar && rc == QW_OK; ++v) {
         sim->mode = modes[v];
         sim->grid_walk = qw_step_grid(sim->d, sim->fp32, sim->mode);
@@ -790,7 +1079,7 @@ extern "C" int qw_autotune(qw_sim *sim, int32_t steps, int32_t *choice, double *
     drop_graphs(sim);
     if (choice) *choice = best;
     if (us_per_step)
-        for (int v = 0; v < 4; ++v) us_per_step[v] = us[v];
+        for (int v = 0; v < QW_WALK_VARIANTS; ++v) us_per_step[v] = us[v];
     return rc;
 }
 
@@ -844,6 +1133,7 @@ extern "C" int qw_apply_qls(qw_sim *sim, int32_t inst, const double *coeffs, int
 {
     if (!sim) return QW_ERR_ARG;
     if (sim->d.ninst != 1 || inst != 0) return fail(sim, QW_ERR_ARG, "QLS needs a single-instance simulator");
+    if (sim->d.nparts > 1) return fail(sim, QW_ERR_ARG, "QLS is not run on a partitioned walk");
     if (!coeffs || j0 < 0 || !y_out) return fail(sim, QW_ERR_ARG, "coeffs, j0 and y_out are required");
     if (!sim->has_state || !sim->fresh_T)
         return fail(sim, QW_ERR_STATE, "QLS needs the state T~|b~> (qw_state_init with apply_T = 1)");
@@ -863,8 +1153,8 @@ extern "C" int qw_apply_qls(qw_sim *sim, int32_t inst, const double *coeffs, int
     QW_CUDA(sim, cudaMemsetAsync(sim->qls_y, 0, (size_t)n * sizeof(double2), sim->stream));
     QW_CUDA(sim, cudaMemsetAsync(&sim->sc->qls_j, 0, sizeof(int64_t), sim->stream));
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    const bool graphs = sim->opts.graphs && cudaStreamIsCapturing(sim->stream, &cs) == cudaSuccess &&
-                        cs == cudaStreamCaptureStatusNone;
+    const bool graphs = sim->opts.graphs && sim->mode != QW_MODE_WALK_FLAT &&
+                        cudaStreamIsCapturing(sim->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
     int64_t j = 0, next_check = 1024;
     while (j <= j0) {
         if (graphs && j0 + 1 - j >= kGraphTerms) {
@@ -1101,6 +1391,19 @@ extern "C" int qw_state_import(qw_sim *sim, int32_t key_words, const uint64_t *k
         hamp[(size_t)i] = make_double2(amps[2 * i], amps[2 * i + 1]);
         norm2 += amps[2 * i] * amps[2 * i] + amps[2 * i + 1] * amps[2 * i + 1];
     }
+    if (sim->opts.overflow_fallback && count > 0) { /* a row longer than row_capacity: grow the buckets */
+        std::vector<uint64_t> rows(hrow);
+        std::sort(rows.begin(), rows.end());
+        int64_t longest = 0;
+        for (size_t i = 0, j = 0; i < rows.size(); i = j) {
+            while (j < rows.size() && rows[j] == rows[i]) ++j;
+            longest = std::max<int64_t>(longest, (int64_t)(j - i));
+        }
+        if (longest > sim->d.cap_row) {
+            int rc = grow_rows(sim, longest);
+            if (rc != QW_OK) return rc;
+        }
+    }
     for (int bi = 0; bi < 3; ++bi) {
         QW_CUDA(sim, qw_launch_clear(sim->d, sim->buf[bi], 0, sim->d.total_buckets, 1, sim->stream));
         sim->launches++;
@@ -1134,5 +1437,132 @@ extern "C" int qw_state_import(qw_sim *sim, int32_t key_words, const uint64_t *k
     sim->has_state = true;
     sim->fresh_T = false;
     for (auto &v : sim->init_norm2) v = 0.0;
+    return QW_OK;
+}
+
+/* ---- row-partitioned walk ---------------------------------------------------------- */
+
+extern "C" int qw_part_owner(int32_t n, int32_t nparts, int32_t jc, int32_t j)
+{
+    if (n < 1 || nparts < 1 || jc < 0 || j < 0) return -1;
+    QwSimDev d{};
+    d.n_single = n;
+    d.nparts = nparts;
+    d.part_rows = ((int64_t)n + nparts - 1) / nparts;
+    return qw_part_owner_of(d, (uint32_t)jc, (uint32_t)j);
+}
+
+extern "C" int qw_part_outbox(qw_sim *sim, int32_t dest, qw_part_entry *dst, int64_t cap, int64_t *count)
+{
+    static_assert(sizeof(qw_part_entry) == sizeof(QwPartEntry), "outbox entry layout");
+    if (!sim || !count) return QW_ERR_ARG;
+    if (sim->d.nparts <= 1) return fail(sim, QW_ERR_STATE, "not a partitioned walk");
+    if (dest < 0 || dest >= sim->d.nparts || (cap > 0 && !dst)) return fail(sim, QW_ERR_ARG, "bad destination");
+    unsigned long long c = 0;
+    QW_CUDA(sim, cudaMemcpyAsync(&c, sim->outbox_count + dest, 8, cudaMemcpyDeviceToHost, sim->stream));
+    QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
+    const int64_t n = std::min<int64_t>((int64_t)c, sim->d.outbox_cap);
+    *count = n;
+    const int64_t m = std::min<int64_t>(n, cap);
+    if (m > 0)
+        QW_CUDA(sim, cudaMemcpyAsync(dst, sim->outbox + (int64_t)dest * sim->d.outbox_cap, (size_t)m * sizeof(QwPartEntry),
+                                     cudaMemcpyDeviceToDevice, sim->stream));
+    QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
+    return QW_OK;
+}
+
+extern "C" int qw_part_inbox(qw_sim *sim, const qw_part_entry *entries, int64_t count)
+{
+    if (!sim || count < 0 || (count > 0 && !entries)) return QW_ERR_ARG;
+    if (sim->d.nparts <= 1) return fail(sim, QW_ERR_STATE, "not a partitioned walk");
+    if (!sim->has_state) return fail(sim, QW_ERR_STATE, "no state");
+    QW_CUDA(sim, qw_launch_part_inbox(sim->d, sim->buf[sim->cur], reinterpret_cast<const QwPartEntry *>(entries),
+                                      count, sim->fp32, &sim->sc->status, sim->stream));
+    sim->launches++;
+    return check_status(sim, "qw_part_inbox");
+}
+
+extern "C" int qw_part_norm(qw_sim *sim, double *local_norm2)
+{
+    if (!sim || !local_norm2) return QW_ERR_ARG;
+    QW_CUDA(sim, cudaMemcpyAsync(local_norm2, &sim->sc->norm[sim->scale_slot], 8, cudaMemcpyDeviceToHost, sim->stream));
+    QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
+    return QW_OK;
+}
+
+extern "C" int qw_part_set_norm(qw_sim *sim, double global_norm2)
+{
+    if (!sim || !(global_norm2 >= 0.0)) return QW_ERR_ARG;
+    double target = 1.0;
+    QW_CUDA(sim, cudaMemcpyAsync(&target, &sim->sc->renorm_target, 8, cudaMemcpyDeviceToHost, sim->stream));
+    QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
+    sim->host_target = (sim->renorm && global_norm2 > 0.0) ? std::sqrt(target / global_norm2) : 1.0;
+    QW_CUDA(sim, cudaMemcpyAsync(&sim->sc->scale[sim->scale_slot], &sim->host_target, 8, cudaMemcpyHostToDevice,
+                                 sim->stream));
+    QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
+    return QW_OK;
+}
+
+extern "C" int qw_part_walk(qw_sim **sims, int32_t np, int64_t nsteps)
+{
+    if (!sims || np < 1 || nsteps < 0) return QW_ERR_ARG;
+    for (int p = 0; p < np; ++p) {
+        if (!sims[p] || sims[p]->d.nparts != np || sims[p]->d.part != p || sims[p]->device != sims[0]->device)
+            return sims[p] ? fail(sims[p], QW_ERR_ARG, "qw_part_walk: not partitions 0 .. nparts - 1 of one walk")
+                           : QW_ERR_ARG;
+        if (!sims[p]->has_state) return fail(sims[p], QW_ERR_STATE, "no state");
+    }
+    std::vector<unsigned long long> cnt((size_t)np * np);
+    for (int64_t t = 0; t < nsteps; ++t) {
+        /* every partition's step kernel */
+        for (int p = 0; p < np; ++p) {
+            int rc = qw_enqueue_walk_steps(sims[p], 1);
+            if (rc != QW_OK) return rc;
+        }
+        for (int p = 0; p < np; ++p) {
+            qw_sim *sp = sims[p];
+            int rc = check_status(sp, "qw_part_walk");
+            if (rc != QW_OK) return rc;
+            QW_CUDA(sp, cudaMemcpy(cnt.data() + (size_t)p * np, sp->outbox_count, (size_t)np * 8,
+                                   cudaMemcpyDeviceToHost));
+        }
+        /* S's exchange: outbox segment p -> q copied into q's inbox, appended */
+        double global = 0.0;
+        for (int q = 0; q < np; ++q) {
+            qw_sim *sq = sims[q];
+            int64_t in = 0;
+            for (int p = 0; p < np; ++p)
+                if (p != q) in += std::min<int64_t>((int64_t)cnt[(size_t)p * np + q], sims[p]->d.outbox_cap);
+            if (in > sq->inbox_cap) {
+                QW_CUDA(sq, cudaStreamSynchronize(sq->stream));
+                cudaFree(sq->inbox);
+                sq->inbox = nullptr;
+                sq->inbox_cap = 0;
+                QW_CUDA(sq, cudaMalloc((void **)&sq->inbox, (size_t)in * sizeof(QwPartEntry)));
+                sq->inbox_cap = in;
+            }
+            int64_t off = 0;
+            for (int p = 0; p < np; ++p) {
+                if (p == q) continue;
+                const int64_t n = std::min<int64_t>((int64_t)cnt[(size_t)p * np + q], sims[p]->d.outbox_cap);
+                if (n > 0)
+                    QW_CUDA(sq, cudaMemcpyAsync(sq->inbox + off, sims[p]->outbox + (int64_t)q * sims[p]->d.outbox_cap,
+                                                (size_t)n * sizeof(QwPartEntry), cudaMemcpyDeviceToDevice, sq->stream));
+                off += n;
+            }
+            QW_CUDA(sq, qw_launch_part_inbox(sq->d, sq->buf[sq->cur], sq->inbox, in, sq->fp32, &sq->sc->status,
+                                             sq->stream));
+            sq->launches++;
+            double local = 0.0;
+            int rc = qw_part_norm(sq, &local);
+            if (rc != QW_OK) return rc;
+            global += local;
+        }
+        for (int q = 0; q < np; ++q) {
+            int rc = check_status(sims[q], "qw_part_walk");
+            if (rc == QW_OK) rc = qw_part_set_norm(sims[q], global);
+            if (rc != QW_OK) return rc;
+        }
+    }
     return QW_OK;
 }

@@ -1,0 +1,706 @@
+/*
+ * qw_flat.cu -- the walk step as the paper's simulator runs it, on one flat
+ * list of branches in global memory (Sec. V-A): every register map applied to
+ * every branch, and every interference operation as
+ *   (1) grouping: a stable LSD radix sort (4-bit digits) of the whole list by
+ *       all registers, with the target's bits moved below the others, so that
+ *       the branches equal on every idle register are contiguous;
+ *   (2) computing: the small dense operator on each group's zero-filled
+ *       vector (a thread per group);
+ *   (3) clearing: outputs with |a| <= tau dropped by a stream compaction.
+ * T~^dag, H, P, H, T~ and S run in the order of Alg. "Quantum walk operator",
+ * with the element register A allocated for the whole step.  Nothing here is
+ * bounded by the row buckets or the on-chip buffers of the step kernels, only
+ * by device memory: this is the path of a step whose rows outgrow them, and a
+ * schedule that can be selected on its own.  Amplitudes are complex FP64
+ * whatever the storage precision (converted when the state is gathered and
+ * rounded when it is stored back).
+ *
+ * Packed key of a branch (two 64-bit words, bit 0 first), the layout of
+ * qw_state_export:  b2 | k (nb) | kc (nb) | b1 | j (nb) | jc (nb) | A (16) |
+ * inst (16), 4 nb + 34 bits.
+ */
+#include "qw_device.cuh"
+
+namespace {
+
+struct FKey {
+    uint64_t lo, hi;
+};
+
+struct FLayout {
+    int nb, pk, pkc, pb1, pj, pjc, pA, pinst;
+};
+
+__host__ __device__ inline FLayout flayout(int nb)
+{
+    FLayout f;
+    f.nb = nb;
+    f.pk = 1;
+    f.pkc = 1 + nb;
+    f.pb1 = 1 + 2 * nb;
+    f.pj = 2 + 2 * nb;
+    f.pjc = 2 + 3 * nb;
+    f.pA = 2 + 4 * nb;
+    f.pinst = 18 + 4 * nb;
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fget(const FKey &k, int pos, int w)
+{
+    uint64_t v;
+    if (pos >= 64) {
+        v = k.hi >> (pos - 64);
+    } else {
+        v = k.lo >> pos;
+        if (pos + w > 64) v |= k.hi << (64 - pos);
+    }
+    return (uint32_t)(v & ((1ull << w) - 1ull));
+}
+
+__device__ __forceinline__ void fput(FKey &k, int pos, int w, uint64_t v)
+{
+    v &= (1ull << w) - 1ull;
+    if (pos >= 64) {
+        k.hi |= v << (pos - 64);
+    } else {
+        k.lo |= v << pos;
+        if (pos + w > 64) k.hi |= v >> (64 - pos);
+    }
+}
+
+struct FRegs {
+    uint32_t inst, jc, j, b1;
+    Regs x; /* k, kc, A, b2 */
+};
+
+__device__ __forceinline__ FRegs fdecode(const FKey &k, const FLayout &L)
+{
+    FRegs r;
+    r.x.b2 = fget(k, 0, 1);
+    r.x.k = fget(k, L.pk, L.nb);
+    r.x.kc = fget(k, L.pkc, L.nb);
+    r.b1 = fget(k, L.pb1, 1);
+    r.j = fget(k, L.pj, L.nb);
+    r.jc = fget(k, L.pjc, L.nb);
+    r.x.A = fget(k, L.pA, 16);
+    r.inst = fget(k, L.pinst, 16);
+    return r;
+}
+
+__device__ __forceinline__ FKey fencode(const FRegs &r, const FLayout &L)
+{
+    FKey k = {0ull, 0ull};
+    fput(k, 0, 1, r.x.b2);
+    fput(k, L.pk, L.nb, r.x.k);
+    fput(k, L.pkc, L.nb, r.x.kc);
+    fput(k, L.pb1, 1, r.b1);
+    fput(k, L.pj, L.nb, r.j);
+    fput(k, L.pjc, L.nb, r.jc);
+    fput(k, L.pA, 16, r.x.A);
+    fput(k, L.pinst, 16, r.inst);
+    return k;
+}
+
+/* The row descriptor of a branch, reading its QRAM row straight from the
+ * image in global memory. */
+__device__ __forceinline__ Row frow(const QwSimDev &d, const FRegs &f)
+{
+    Row r;
+    r.inst = f.inst;
+    r.jc = f.jc;
+    r.j = f.j;
+    r.b1 = f.b1;
+    r.n_inst = d.ninst == 1 ? (uint32_t)d.n_single : (uint32_t)d.inst_n[f.inst];
+    r.img_base = d.ninst == 1 ? 0 : d.inst_img[f.inst];
+    r.valid = f.j < r.n_inst;
+    r.simg = r.valid ? d.img + r.img_base + (int64_t)f.j * d.s : nullptr;
+    r.sfg = nullptr;
+    return r;
+}
+
+/* grouping orders: ORDER_R groups b2-pairs (b2 is bit 0 already); ORDER_H
+ * groups the Hadamard's 2^L values of the low L bits of k, which move below
+ * b2 (the low L + 1 bits rotate by one) */
+constexpr int ORDER_R = 0, ORDER_H = 1;
+
+template <int ORDER>
+__device__ __forceinline__ FKey permuted(FKey k, int L)
+{
+    if (ORDER == ORDER_H && L > 0) {
+        const uint64_t m = (1ull << L) - 1ull;
+        k.lo = (k.lo & ~((m << 1) | 1ull)) | ((k.lo >> 1) & m) | ((k.lo & 1ull) << L);
+    }
+    return k;
+}
+
+template <int ORDER>
+__device__ __forceinline__ bool same_group(const FKey &a, const FKey &b, int L)
+{
+    const uint64_t m = ORDER == ORDER_R ? 1ull : (((1ull << L) - 1ull) << 1);
+    return a.hi == b.hi && (a.lo & ~m) == (b.lo & ~m);
+}
+
+/* ---- gather, maps, phase ------------------------------------------------------ */
+
+template <typename AmpT>
+__global__ void k_f_gather(QwSimDev d, QwBufDev buf, const double *scale, FKey *keys, double2 *amps,
+                           unsigned long long *counter, int64_t cap)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const double sc = scale ? *scale : 1.0;
+    const FLayout L = flayout(d.nb);
+    for (int64_t b = warp; b < d.total_buckets; b += nw) {
+        int n = buf.count[b];
+        if (n <= 0) continue;
+        if (n > d.cap_row) n = d.cap_row;
+        Row r;
+        if (!row_of(d, buf, b, r)) continue;
+        for (int i = lane; i < n; i += 32) {
+            const int64_t slot = b * (int64_t)d.cap_row + i;
+            const unsigned long long p = atomicAdd(counter, 1ull);
+            if ((int64_t)p >= cap) continue;
+            FRegs f;
+            f.inst = r.inst;
+            f.jc = r.jc;
+            f.j = r.j;
+            f.b1 = r.b1;
+            f.x = decode_r(buf.key[slot], d.nb);
+            keys[p] = fencode(f, L);
+            amps[p] = cscale(sc, load_amp<AmpT>(buf.amp, slot));
+        }
+    }
+}
+
+/* op codes of k_f_map, applied from the lowest 4 bits up */
+constexpr int F_OSDAG = 1, F_OA = 2, F_OS = 3, F_S = 4, F_A0 = 5;
+
+__global__ void k_f_map(QwSimDev d, FKey *keys, int64_t M, uint32_t ops, int32_t *status)
+{
+    const FLayout L = flayout(d.nb);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        FRegs f = fdecode(keys[i], L);
+        for (uint32_t o = ops; o != 0; o >>= 4) {
+            const uint32_t op = o & 15u;
+            const Row r = frow(d, f);
+            if (op == F_OSDAG) op_osdag(d, r, f.x);
+            else if (op == F_OA) op_oa(d, r, f.x);
+            else if (op == F_OS) op_os(d, r, f.x);
+            else if (op == F_A0) {
+                if (f.x.A != 0) atomicOr(status, QW_ST_ANCILLA);
+            } else if (op == F_S) { /* (jc, j, b1) <-> (kc, k, b2) */
+                const uint32_t jc = f.jc, j = f.j, b1 = f.b1;
+                f.jc = f.x.kc;
+                f.j = f.x.k;
+                f.b1 = f.x.b2;
+                f.x.kc = jc;
+                f.x.k = j;
+                f.x.b2 = b1;
+            }
+        }
+        keys[i] = fencode(f, L);
+    }
+}
+
+/* P = 2 Pi - 1 (Eq. (impl)): the sign flips unless b1, k, b2, jc, kc are 0 */
+__global__ void k_f_phase(QwSimDev d, const FKey *keys, double2 *amps, int64_t M)
+{
+    const FLayout L = flayout(d.nb);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const FRegs f = fdecode(keys[i], L);
+        const bool zero = f.b1 == 0 && f.x.k == 0 && f.x.b2 == 0 && f.jc == 0 && f.x.kc == 0;
+        if (!zero) amps[i] = cneg(amps[i]);
+    }
+}
+
+/* ---- device-wide exclusive scan of 32-bit counts ------------------------------ */
+
+constexpr int SCAN_TILE = 1024; /* elements per block: 256 threads x 4 */
+
+__global__ void k_scan_reduce(const uint32_t *in, int64_t n, uint32_t *sums)
+{
+    __shared__ uint32_t ws[8];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    uint32_t v = 0;
+    for (int t = 0; t < 4; ++t) {
+        const int64_t i = base + threadIdx.x * 4 + t;
+        if (i < n) v += in[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < 8; ++w) t += ws[w];
+        sums[blockIdx.x] = t;
+    }
+}
+
+/* one block: exclusive scan of the block sums in place, total at sums[nb] */
+__global__ void k_scan_blocks(uint32_t *sums, int64_t nb)
+{
+    __shared__ uint32_t ws[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t base = 0; base < nb; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const uint32_t v = i < nb ? sums[i] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, w, o);
+                if (lane >= o) w += y;
+            }
+            ws[lane] = w;
+        }
+        __syncthreads();
+        const uint32_t before = carry + (warp > 0 ? ws[warp - 1] : 0u) + x - v;
+        if (i < nb) sums[i] = before;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += ws[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+__global__ void k_scan_apply(const uint32_t *in, int64_t n, const uint32_t *sums, uint32_t *out)
+{
+    __shared__ uint32_t ws[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * 4;
+    uint32_t v[4], t = 0;
+    for (int k = 0; k < 4; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0u;
+        t += v[k];
+    }
+    uint32_t x = t;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += ws[w];
+    uint32_t run = sums[blockIdx.x] + wpre + x - t;
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+}
+
+/* ---- radix sort ------------------------------------------------------------------ */
+
+template <int ORDER>
+__global__ void k_f_orand(const FKey *keys, int64_t M, int L, unsigned long long *acc)
+{
+    uint64_t ol = 0, oh = 0, al = ~0ull, ah = ~0ull;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const FKey k = permuted<ORDER>(keys[i], L);
+        ol |= k.lo;
+        oh |= k.hi;
+        al &= k.lo;
+        ah &= k.hi;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ol |= __shfl_xor_sync(FULL, ol, o);
+        oh |= __shfl_xor_sync(FULL, oh, o);
+        al &= __shfl_xor_sync(FULL, al, o);
+        ah &= __shfl_xor_sync(FULL, ah, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicOr(acc + 0, (unsigned long long)ol);
+        atomicOr(acc + 1, (unsigned long long)oh);
+        atomicAnd(acc + 2, (unsigned long long)al);
+        atomicAnd(acc + 3, (unsigned long long)ah);
+    }
+}
+
+/* One pass of the stable LSD radix sort on the 4-bit digit at `shift` of the
+ * permuted key: count_only -- per-block digit counts into hist[digit * nblk +
+ * block]; otherwise scatter to offs[digit * nblk + block] + the item's rank
+ * among the equal digits before it (rounds of 256 items in order, warps in
+ * order, lanes in order). */
+template <int ORDER>
+__global__ void __launch_bounds__(256) k_f_radix(const FKey *kin, const double2 *ain, FKey *kout, double2 *aout,
+                                                 int64_t M, int64_t tile, int shift, int L, const uint32_t *offs,
+                                                 uint32_t *hist, int count_only)
+{
+    __shared__ uint32_t wc[8][16];
+    __shared__ uint32_t run[16];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t lo = (int64_t)blockIdx.x * tile;
+    const int64_t hi = lo + tile < M ? lo + tile : M;
+    if (threadIdx.x < 16) run[threadIdx.x] = count_only ? 0u : offs[threadIdx.x * gridDim.x + blockIdx.x];
+    __syncthreads();
+    for (int64_t base = lo; base < hi; base += 256) {
+        const int64_t i = base + threadIdx.x;
+        const bool act = i < hi;
+        FKey k = {0ull, 0ull};
+        int dig = 16;
+        if (act) {
+            k = kin[i];
+            const FKey p = permuted<ORDER>(k, L);
+            dig = (int)((shift < 64 ? (p.lo >> shift) : (p.hi >> (shift - 64))) & 15ull);
+        }
+        const unsigned m = __match_any_sync(FULL, dig);
+        const int rank = __popc(m & ((1u << lane) - 1u));
+        if (threadIdx.x < 128) (&wc[0][0])[threadIdx.x] = 0u;
+        __syncthreads();
+        if (act && rank == 0) wc[warp][dig] = (uint32_t)__popc(m);
+        __syncthreads();
+        uint32_t dest = 0;
+        if (act) {
+            uint32_t pre = 0;
+            for (int w = 0; w < warp; ++w) pre += wc[w][dig];
+            dest = run[dig] + pre + (uint32_t)rank;
+        }
+        __syncthreads();
+        if (threadIdx.x < 16) {
+            uint32_t t = 0;
+            for (int w = 0; w < 8; ++w) t += wc[w][threadIdx.x];
+            run[threadIdx.x] += t;
+        }
+        __syncthreads();
+        if (act && !count_only) {
+            kout[dest] = k;
+            aout[dest] = ain[i];
+        }
+    }
+    if (count_only && threadIdx.x < 16) hist[threadIdx.x * gridDim.x + blockIdx.x] = run[threadIdx.x];
+}
+
+/* ---- per-group transforms (the "computing" step) -------------------------------- */
+
+/* R (DAG = false) or R^dag on b2-pairs (sorted in ORDER_R): the head of each
+ * pair writes both outputs at 2 i (b2 = 0) and 2 i + 1 (b2 = 1) with their
+ * keep flags; R = [[f, -g], [g, conj f]] (Alg. T~ and the footnote of Sec. IV). */
+template <bool DAG>
+__global__ void k_f_rot(QwSimDev d, const FKey *keys, const double2 *amps, int64_t M, FKey *okeys, double2 *oamps,
+                        uint32_t *flags)
+{
+    const FLayout L = flayout(d.nb);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const FKey k = keys[i];
+        const bool head = i == 0 || !same_group<ORDER_R>(keys[i - 1], k, 0);
+        flags[2 * i] = 0u;
+        flags[2 * i + 1] = 0u;
+        if (!head) continue;
+        double2 a0 = make_double2(0, 0), a1 = make_double2(0, 0);
+        if ((k.lo & 1ull) == 0) {
+            a0 = amps[i];
+            if (i + 1 < M && same_group<ORDER_R>(k, keys[i + 1], 0)) a1 = amps[i + 1];
+        } else {
+            a1 = amps[i];
+        }
+        const FRegs f = fdecode(k, L);
+        double2 fv;
+        double g;
+        rot_fg(d, f.x.A, f.j, f.x.k, fv, g);
+        double2 o0, o1;
+        if (!DAG) {
+            o0 = csub(cmul(fv, a0), cscale(g, a1));
+            o1 = cadd(cscale(g, a0), cmul(cconj(fv), a1));
+        } else {
+            o0 = cadd(cmul(cconj(fv), a0), cscale(g, a1));
+            o1 = csub(cmul(fv, a1), cscale(g, a0));
+        }
+        FKey k0 = k;
+        k0.lo &= ~1ull;
+        FKey k1 = k0;
+        k1.lo |= 1ull;
+        okeys[2 * i] = k0;
+        okeys[2 * i + 1] = k1;
+        oamps[2 * i] = o0;
+        oamps[2 * i + 1] = o1;
+        flags[2 * i] = keep(o0, d.tau2) ? 1u : 0u;
+        flags[2 * i + 1] = keep(o1, d.tau2) ? 1u : 0u;
+    }
+}
+
+/* H on the low L bits of k (sorted in ORDER_H): the head of each group
+ * writes the s outputs (1/sqrt s) sum_v (-1)^(u.v) a_v at s i + u. */
+__global__ void k_f_hadamard(QwSimDev d, const FKey *keys, const double2 *amps, int64_t M, FKey *okeys,
+                             double2 *oamps, uint32_t *flags)
+{
+    const int L = d.L, s = d.s;
+    const uint64_t lowm = (((uint64_t)s - 1ull) << 1);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const FKey k = keys[i];
+        const bool head = i == 0 || !same_group<ORDER_H>(keys[i - 1], k, L);
+        for (int u = 0; u < s; ++u) flags[(int64_t)s * i + u] = 0u;
+        if (!head) continue;
+        int64_t e = i + 1;
+        while (e < M && e < i + s && same_group<ORDER_H>(k, keys[e], L)) ++e;
+        for (int u = 0; u < s; ++u) {
+            double2 o = make_double2(0, 0);
+            for (int64_t m = i; m < e; ++m) {
+                const uint32_t v = (uint32_t)((keys[m].lo >> 1) & (uint64_t)(s - 1));
+                const double2 a = amps[m];
+                o = (__popc((uint32_t)u & v) & 1) ? csub(o, a) : cadd(o, a);
+            }
+            o = cscale(d.inv_sqrt_s, o);
+            FKey ko = k;
+            ko.lo = (ko.lo & ~lowm) | ((uint64_t)u << 1);
+            okeys[(int64_t)s * i + u] = ko;
+            oamps[(int64_t)s * i + u] = o;
+            flags[(int64_t)s * i + u] = keep(o, d.tau2) ? 1u : 0u;
+        }
+    }
+}
+
+/* the "clearing" step: kept entries to their scanned positions */
+__global__ void k_f_compact(const FKey *keys, const double2 *amps, const uint32_t *flags, const uint32_t *pos,
+                            int64_t n, FKey *okeys, double2 *oamps)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (!flags[i]) continue;
+        okeys[pos[i]] = keys[i];
+        oamps[pos[i]] = amps[i];
+    }
+}
+
+/* QLS read-out after T~^dag's H: Y[j] += a_j * (the flag-0 amplitude of row j) */
+__global__ void k_f_readout(QwSimDev d, const FKey *keys, const double2 *amps, int64_t M, QwStepArgs a)
+{
+    const FLayout L = flayout(d.nb);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const FRegs f = fdecode(keys[i], L);
+        if (f.jc != 0 || f.b1 != 0 || f.x.kc != 0 || f.x.k != 0 || f.x.b2 != 0 || f.x.A != 0) continue;
+        if (f.j >= (uint32_t)d.n_single) continue;
+        const double coef = a.qls_coefs[*a.qls_j];
+        const double2 v = amps[i];
+        atomicAdd(&a.qls_y[f.j].x, coef * v.x);
+        atomicAdd(&a.qls_y[f.j].y, coef * v.y);
+    }
+}
+
+/* the output into the row buckets, |stored a|^2 summed per block into *norm */
+template <typename AmpT>
+__global__ void k_f_scatter(QwSimDev d, QwBufDev out, const FKey *keys, const double2 *amps, int64_t M,
+                            int32_t *status, unsigned int *maxrow, double *norm)
+{
+    __shared__ double ws[8];
+    const FLayout L = flayout(d.nb);
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const FRegs f = fdecode(keys[i], L);
+        if (f.x.A != 0) {
+            atomicOr(status, QW_ST_ANCILLA);
+            continue;
+        }
+        const int64_t b = bucket_of(d, out, f.inst, f.jc, f.j, f.b1, status);
+        if (b < 0) continue;
+        const int p = atomicAdd(out.count + b, 1);
+        atomicMax(maxrow, (unsigned int)(p + 1));
+        if (p >= d.cap_row) {
+            atomicOr(status, QW_ST_ROW_OVERFLOW);
+            continue;
+        }
+        const int64_t slot = b * (int64_t)d.cap_row + p;
+        out.key[slot] = encode_r(f.x, d.nb);
+        acc += store_amp<AmpT>(out.amp, slot, amps[i]);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        atomicAdd(norm, t);
+    }
+}
+
+/* the step's bookkeeping, as the step kernels' last block does it */
+__global__ void k_f_finish(QwStepArgs a, const double *norm, unsigned long long in, unsigned long long rdag,
+                           unsigned long long h1, unsigned long long hph, unsigned long long out)
+{
+    const bool clean = *(volatile int32_t *)a.status == 0;
+    if (!clean) return;
+    const double tot = *norm;
+    *a.norm_out = tot;
+    if (a.scale_out) *a.scale_out = (a.renorm && tot > 0.0) ? sqrt(*a.renorm_target / tot) : 1.0;
+    if (a.steps_done) *a.steps_done += 1;
+    if (a.stats) {
+        a.stats[QW_STAT_IN] += in;
+        a.stats[QW_STAT_RDAG] += rdag;
+        a.stats[QW_STAT_H1] += h1;
+        a.stats[QW_STAT_HPH] += hph;
+        a.stats[QW_STAT_OUT] += out;
+        a.stats[QW_STAT_STEPS] += 1;
+    }
+}
+
+int grid_for(int64_t n, int threads)
+{
+    int64_t g = (n + threads - 1) / threads;
+    const int cap = 16 * qw_sm_count();
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+} // namespace
+
+/* ---- launchers ------------------------------------------------------------------------ */
+
+cudaError_t qw_flat_gather(const QwSimDev &d, const QwBufDev &buf, int fp32, const double *scale, void *keys,
+                           double2 *amps, unsigned long long *counter, int64_t cap, cudaStream_t st)
+{
+    const int grid = 4 * qw_sm_count();
+    if (fp32)
+        k_f_gather<float2><<<grid, 256, 0, st>>>(d, buf, scale, static_cast<FKey *>(keys), amps, counter, cap);
+    else
+        k_f_gather<double2><<<grid, 256, 0, st>>>(d, buf, scale, static_cast<FKey *>(keys), amps, counter, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t qw_flat_map(const QwSimDev &d, void *keys, int64_t M, uint32_t ops, int32_t *status, cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    k_f_map<<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<FKey *>(keys), M, ops, status);
+    return cudaGetLastError();
+}
+
+cudaError_t qw_flat_phase(const QwSimDev &d, const void *keys, double2 *amps, int64_t M, cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    k_f_phase<<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<const FKey *>(keys), amps, M);
+    return cudaGetLastError();
+}
+
+size_t qw_flat_scan_words(int64_t n)
+{
+    return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE) + 1;
+}
+
+cudaError_t qw_flat_scan(const uint32_t *in, int64_t n, uint32_t *sums, uint32_t *out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    k_scan_reduce<<<(unsigned)nb, 256, 0, st>>>(in, n, sums);
+    k_scan_blocks<<<1, 1024, 0, st>>>(sums, nb);
+    k_scan_apply<<<(unsigned)nb, 256, 0, st>>>(in, n, sums, out);
+    return cudaGetLastError();
+}
+
+size_t qw_flat_sort_words(int64_t M)
+{
+    const int64_t nblk = M < 1 ? 1 : (M + 4095) / 4096 < 1024 ? (M + 4095) / 4096 : 1024;
+    return (size_t)(16 * nblk) * 2 + qw_flat_scan_words(16 * nblk) + 12;
+}
+
+/* Stable sort of (keys, amps) by the permuted key of `order` (0: R, 1: H);
+ * tmpk/tmpa hold M entries each; the result is left in keys/amps.  Digits
+ * equal on every key are skipped (one synchronisation reads them). */
+cudaError_t qw_flat_sort(const QwSimDev &d, void *keys, double2 *amps, void *tmpk, double2 *tmpa, int64_t M,
+                         int order, uint32_t *work, cudaStream_t st)
+{
+    if (M <= 1) return cudaSuccess;
+    const int L = d.L;
+    int64_t nblk = (M + 4095) / 4096;
+    if (nblk > 1024) nblk = 1024;
+    int64_t tile = (M + nblk - 1) / nblk;
+    tile = (tile + 255) / 256 * 256;
+    nblk = (M + tile - 1) / tile;
+    uint32_t *hist = work, *offs = work + 16 * nblk, *sums = offs + 16 * nblk;
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(
+        reinterpret_cast<uintptr_t>(sums + qw_flat_scan_words(16 * nblk) + 3) & ~(uintptr_t)7);
+    const unsigned long long init[4] = {0ull, 0ull, ~0ull, ~0ull};
+    cudaError_t e = cudaMemcpyAsync(acc, init, sizeof init, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    if (order == ORDER_R) k_f_orand<ORDER_R><<<grid_for(M, 256), 256, 0, st>>>(static_cast<FKey *>(keys), M, L, acc);
+    else k_f_orand<ORDER_H><<<grid_for(M, 256), 256, 0, st>>>(static_cast<FKey *>(keys), M, L, acc);
+    unsigned long long h[4];
+    if ((e = cudaMemcpyAsync(h, acc, sizeof h, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    const uint64_t vlo = h[0] ^ h[2], vhi = h[1] ^ h[3];
+    FKey *ka = static_cast<FKey *>(keys), *kb = static_cast<FKey *>(tmpk);
+    double2 *aa = amps, *ab = tmpa;
+    for (int shift = 0; shift < 128; shift += 4) {
+        const uint64_t var = shift < 64 ? (vlo >> shift) & 15ull : (vhi >> (shift - 64)) & 15ull;
+        if (!var) continue;
+        if (order == ORDER_R)
+            k_f_radix<ORDER_R><<<(unsigned)nblk, 256, 0, st>>>(ka, aa, kb, ab, M, tile, shift, L, nullptr, hist, 1);
+        else
+            k_f_radix<ORDER_H><<<(unsigned)nblk, 256, 0, st>>>(ka, aa, kb, ab, M, tile, shift, L, nullptr, hist, 1);
+        if ((e = qw_flat_scan(hist, 16 * nblk, sums, offs, st)) != cudaSuccess) return e;
+        if (order == ORDER_R)
+            k_f_radix<ORDER_R><<<(unsigned)nblk, 256, 0, st>>>(ka, aa, kb, ab, M, tile, shift, L, offs, hist, 0);
+        else
+            k_f_radix<ORDER_H><<<(unsigned)nblk, 256, 0, st>>>(ka, aa, kb, ab, M, tile, shift, L, offs, hist, 0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        FKey *tk = ka;
+        ka = kb;
+        kb = tk;
+        double2 *ta = aa;
+        aa = ab;
+        ab = ta;
+    }
+    if (ka != static_cast<FKey *>(keys)) {
+        if ((e = cudaMemcpyAsync(keys, ka, (size_t)M * sizeof(FKey), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemcpyAsync(amps, aa, (size_t)M * sizeof(double2), cudaMemcpyDeviceToDevice, st)) !=
+            cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
+/* op: 0 = R^dag, 1 = R (2 outputs per entry), 2 = H (s outputs per entry) */
+cudaError_t qw_flat_group(const QwSimDev &d, int op, const void *keys, const double2 *amps, int64_t M, void *okeys,
+                          double2 *oamps, uint32_t *flags, cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    const FKey *k = static_cast<const FKey *>(keys);
+    FKey *ok = static_cast<FKey *>(okeys);
+    if (op == 0) k_f_rot<true><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
+    else if (op == 1) k_f_rot<false><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
+    else k_f_hadamard<<<grid_for(M, 128), 128, 0, st>>>(d, k, amps, M, ok, oamps, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t qw_flat_compact(const void *keys, const double2 *amps, const uint32_t *flags, const uint32_t *pos,
+                            int64_t n, void *okeys, double2 *oamps, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_f_compact<<<grid_for(n, 256), 256, 0, st>>>(static_cast<const FKey *>(keys), amps, flags, pos, n,
+                                                   static_cast<FKey *>(okeys), oamps);
+    return cudaGetLastError();
+}
+
+cudaError_t qw_flat_readout(const QwSimDev &d, const void *keys, const double2 *amps, int64_t M, const QwStepArgs &a,
+                            cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    k_f_readout<<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<const FKey *>(keys), amps, M, a);
+    return cudaGetLastError();
+}
+
+cudaError_t qw_flat_scatter(const QwSimDev &d, const QwBufDev &out, int fp32, const void *keys, const double2 *amps,
+                            int64_t M, int32_t *status, unsigned int *maxrow, double *norm, cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    const FKey *k = static_cast<const FKey *>(keys);
+    if (fp32) k_f_scatter<float2><<<grid_for(M, 256), 256, 0, st>>>(d, out, k, amps, M, status, maxrow, norm);
+    else k_f_scatter<double2><<<grid_for(M, 256), 256, 0, st>>>(d, out, k, amps, M, status, maxrow, norm);
+    return cudaGetLastError();
+}
+
+cudaError_t qw_flat_finish(const QwStepArgs &a, const double *norm, const int64_t *counts, cudaStream_t st)
+{
+    k_f_finish<<<1, 1, 0, st>>>(a, norm, (unsigned long long)counts[0], (unsigned long long)counts[1],
+                                (unsigned long long)counts[2], (unsigned long long)counts[3],
+                                (unsigned long long)counts[4]);
+    return cudaGetLastError();
+}

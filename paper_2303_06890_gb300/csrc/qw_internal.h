@@ -35,6 +35,14 @@
 #define QW_ST_SPILL_FULL 4     /* no free spill slot for a jc != 0 row */
 #define QW_ST_ANCILLA 8        /* register A not zero where it must be */
 #define QW_ST_NOT_BTILDE 16    /* T~ at initialisation met a row that was not |b~> */
+#define QW_ST_OUTBOX_FULL 32   /* a partition's outbox toward another overflowed */
+
+/* A branch sent by S to a row another partition owns: its row key
+   (qw_rowkey), its local registers (R layout) and its amplitude in FP64. */
+struct QwPartEntry {
+    uint64_t rowkey, local;
+    double re, im;
+};
 
 /* per-step branch counters (index into QwStepArgs.stats) */
 #define QW_STAT_ROWS 0      /* rows processed */
@@ -53,6 +61,8 @@
 #define QW_MODE_WALK_FUSED_PF 3 /* fused step, row loop software-pipelined */
 #define QW_MODE_WALK_SEG 4      /* fused step, both rows of a j as one segment */
 #define QW_MODE_WALK_SEG_PF 5   /* segments, software-pipelined */
+#define QW_MODE_WALK_SLOT 6     /* fused step, one lane per QRAM slot (s = 8, 16, 32) */
+#define QW_MODE_WALK_FLAT 7     /* the literal step on one globally sorted branch list (qw_flat.cu) */
 
 struct QwSimDev {
     int nb, s, L, ninst;
@@ -76,6 +86,15 @@ struct QwSimDev {
     const int64_t *inst_img;  /* image offset per instance */
     const int64_t *inst_bkt;  /* first dense bucket per instance, ninst + 1 entries */
     const uint16_t *unit_inst; /* instance of dense bucket pair u (buckets 2u, 2u + 1); ninst > 1 */
+    /* row-partitioned walk (single instance): rows (jc = 0, j < N) in blocks of
+       part_rows per partition, the others by a hash of (jc, j); S sends a
+       branch whose new row another partition owns to that partition's
+       outbox segment (outbox_cap entries each) */
+    int nparts, part;
+    int64_t part_rows;
+    QwPartEntry *outbox;
+    unsigned long long *outbox_count;
+    int64_t outbox_cap;
 };
 
 struct QwBufDev {
@@ -102,6 +121,9 @@ struct QwStepArgs {
     const double *qls_coefs; /* Y += qls_coefs[*qls_j] * Pi_0 tau at this step's midpoint */
     const int64_t *qls_j;    /* index of the current QLS term (advanced by k_qls_norm) */
     int qls_readout;
+    int32_t *deferred;          /* slot kernel: units left to the row pipeline (dense unit u,
+                                   or 0x80000000 | garbage-row slot), run by the last block */
+    unsigned int *deferred_ctr; /* entries in deferred (reset by the last block) */
 };
 
 /* launchers (qw_kernels.cu); all return cudaGetLastError() of the launch */
@@ -109,6 +131,8 @@ int qw_sm_count(void);
 cudaError_t qw_launch_step(const QwSimDev &d, const QwBufDev &in, const QwBufDev &out,
                            const QwBufDev &clear, const QwStepArgs &a, int fp32, int grid,
                            cudaStream_t st);
+/* whether the slot kernel (QW_MODE_WALK_SLOT) covers this sparsity */
+int qw_slot_supported(const QwSimDev &d);
 /* dynamic shared memory per block of the step kernel of `mode` */
 size_t qw_step_smem_bytes(const QwSimDev &d, int fp32, int mode);
 int qw_step_grid(const QwSimDev &d, int fp32, int mode);
@@ -133,6 +157,52 @@ cudaError_t qw_launch_measure_noalloc(const QwSimDev &d, const QwBufDev &buf, in
 cudaError_t qw_launch_count(const QwSimDev &d, const QwBufDev &buf, int inst,
                             unsigned long long *counter, cudaStream_t st);
 cudaError_t qw_launch_qls_norm(const double2 *y, int n, double *p, int64_t *jctr, cudaStream_t st);
+/* copy buffer `from` (row capacity cap_old) into new key/amp arrays laid out
+   with d.cap_row entries per bucket */
+cudaError_t qw_launch_regrow(const QwSimDev &d, const QwBufDev &from, int cap_old, uint64_t *key_new, void *amp_new,
+                             int fp32, cudaStream_t st);
+
+/* flat, globally sorted step (qw_flat.cu): keys are 16-byte packed register
+   keys, amplitudes complex FP64; see qw_flat.cu for each stage */
+#define QW_FLAT_OSDAG 1u
+#define QW_FLAT_OA 2u
+#define QW_FLAT_OS 3u
+#define QW_FLAT_S 4u
+#define QW_FLAT_A0 5u /* check A = 0 */
+cudaError_t qw_flat_gather(const QwSimDev &d, const QwBufDev &buf, int fp32, const double *scale, void *keys,
+                           double2 *amps, unsigned long long *counter, int64_t cap, cudaStream_t st);
+cudaError_t qw_flat_map(const QwSimDev &d, void *keys, int64_t M, uint32_t ops, int32_t *status, cudaStream_t st);
+cudaError_t qw_flat_phase(const QwSimDev &d, const void *keys, double2 *amps, int64_t M, cudaStream_t st);
+size_t qw_flat_scan_words(int64_t n);
+cudaError_t qw_flat_scan(const uint32_t *in, int64_t n, uint32_t *sums, uint32_t *out, cudaStream_t st);
+size_t qw_flat_sort_words(int64_t M);
+cudaError_t qw_flat_sort(const QwSimDev &d, void *keys, double2 *amps, void *tmpk, double2 *tmpa, int64_t M,
+                         int order, uint32_t *work, cudaStream_t st);
+cudaError_t qw_flat_group(const QwSimDev &d, int op, const void *keys, const double2 *amps, int64_t M, void *okeys,
+                          double2 *oamps, uint32_t *flags, cudaStream_t st);
+cudaError_t qw_flat_compact(const void *keys, const double2 *amps, const uint32_t *flags, const uint32_t *pos,
+                            int64_t n, void *okeys, double2 *oamps, cudaStream_t st);
+cudaError_t qw_flat_readout(const QwSimDev &d, const void *keys, const double2 *amps, int64_t M, const QwStepArgs &a,
+                            cudaStream_t st);
+cudaError_t qw_flat_scatter(const QwSimDev &d, const QwBufDev &out, int fp32, const void *keys, const double2 *amps,
+                            int64_t M, int32_t *status, unsigned int *maxrow, double *norm, cudaStream_t st);
+cudaError_t qw_flat_finish(const QwStepArgs &a, const double *norm, const int64_t *counts, cudaStream_t st);
+
+cudaError_t qw_launch_part_inbox(const QwSimDev &d, const QwBufDev &buf, const QwPartEntry *e, int64_t count, int fp32,
+                                 int32_t *status, cudaStream_t st);
+
+/* Partition owning row (jc, j) of a row-partitioned walk: blocks of
+ * part_rows rows for jc = 0, j < N; a hash of (jc, j) otherwise (the rows
+ * only states outside the walk's subspace reach). */
+__host__ __device__ static inline int qw_part_owner_of(const QwSimDev &d, uint32_t jc, uint32_t j)
+{
+    if (jc == 0 && j < (uint32_t)d.n_single) return (int)((int64_t)j / d.part_rows);
+    uint64_t x = ((uint64_t)jc << 20) | (uint64_t)j;
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33;
+    return (int)(x % (uint64_t)d.nparts);
+}
 
 /* packed row key: inst << 40 | jc << 20 | j << 1 | b1  (nb <= 19) */
 __host__ __device__ static inline uint64_t qw_rowkey(uint32_t inst, uint32_t jc, uint32_t j,

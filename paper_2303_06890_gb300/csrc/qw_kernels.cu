@@ -34,6 +34,7 @@
 
 #include "../../include/qwalk.h"
 #include "qw_internal.h"
+#include "qw_device.cuh"
 
 /* Rotation controls carried in the key between a map and its rotation: the
  * element register A (its field of the R layout) and bit 63 = [j > k], the
@@ -46,227 +47,6 @@
 #define QW_B1_BIT 52
 
 namespace {
-
-constexpr unsigned FULL = 0xffffffffu;
-constexpr int WARPS = 8; /* warps per block of the step kernel */
-
-struct Row {
-    uint32_t inst, jc, j, b1;
-    uint32_t n_inst;
-    int64_t img_base;
-    bool valid; /* j < N: the row has a QRAM image */
-    const uint32_t *simg;
-    const void *sfg; /* rotation values of the row's s slots (fused kernel), or null */
-};
-
-struct Regs {
-    uint32_t k, kc, A, b2;
-};
-
-/* ---- complex helpers (FP64) ------------------------------------------------ */
-
-__device__ __forceinline__ double2 cmul(double2 a, double2 b)
-{
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
-__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
-__device__ __forceinline__ double2 cneg(double2 a) { return make_double2(-a.x, -a.y); }
-
-/* clearing step of an interference op: keep a branch iff |a|^2 > tau^2 */
-__device__ __forceinline__ bool keep(double2 a, double tau2)
-{
-    return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y)) > tau2;
-}
-
-template <typename T> __device__ __forceinline__ double2 load_amp(const void *p, int64_t i);
-template <> __device__ __forceinline__ double2 load_amp<double2>(const void *p, int64_t i)
-{
-    return static_cast<const double2 *>(p)[i];
-}
-template <> __device__ __forceinline__ double2 load_amp<float2>(const void *p, int64_t i)
-{
-    float2 v = static_cast<const float2 *>(p)[i];
-    return make_double2((double)v.x, (double)v.y);
-}
-template <typename T> __device__ __forceinline__ double store_amp(void *p, int64_t i, double2 a);
-template <> __device__ __forceinline__ double store_amp<double2>(void *p, int64_t i, double2 a)
-{
-    static_cast<double2 *>(p)[i] = a;
-    return a.x * a.x + a.y * a.y;
-}
-template <> __device__ __forceinline__ double store_amp<float2>(void *p, int64_t i, double2 a)
-{
-    float2 v = make_float2((float)a.x, (float)a.y);
-    static_cast<float2 *>(p)[i] = v;
-    return (double)v.x * (double)v.x + (double)v.y * (double)v.y;
-}
-
-/* ---- warp primitives ---------------------------------------------------------- */
-
-__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
-
-__device__ __forceinline__ int warp_excl_scan(int v, int &total)
-{
-    const int lane = lane_id();
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
-    }
-    total = __shfl_sync(FULL, x, 31);
-    return x - v;
-}
-
-/* Compaction for per-lane emit flags c0, c1 in {0, 1}, emitted in lane
- * order as (c0 item, c1 item): the lane's first output position among the
- * warp's outputs, and the warp total, from two ballots. */
-__device__ __forceinline__ int warp_compact2(bool c0, bool c1, int &total)
-{
-    const unsigned lt = (1u << lane_id()) - 1u;
-    const unsigned b0 = __ballot_sync(FULL, c0), b1 = __ballot_sync(FULL, c1);
-    total = __popc(b0) + __popc(b1);
-    return __popc(b0 & lt) + __popc(b1 & lt);
-}
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    return v;
-}
-
-/* Grouping step of an interference op: sort the row's n branches by key.
- * Keys are distinct (every register map is a bijection and every
- * interference op emits one branch per key), so the rank of a key -- the
- * number of smaller keys -- is its position. */
-__device__ void warp_sort(const uint64_t *ks, const double2 *as, int n, uint64_t *kd, double2 *ad)
-{
-    for (int i = lane_id(); i < n; i += 32) {
-        const uint64_t ki = ks[i];
-        int r = 0;
-        for (int t = 0; t < n; ++t) r += (ks[t] < ki);
-        kd[r] = ki;
-        ad[r] = as[i];
-    }
-    __syncwarp();
-}
-
-/* ---- register layouts --------------------------------------------------------- */
-
-__device__ __forceinline__ Regs decode_r(uint64_t key, int nb)
-{
-    const uint64_t m = (1ull << nb) - 1;
-    Regs x;
-    x.b2 = (uint32_t)(key & 1);
-    x.k = (uint32_t)((key >> 1) & m);
-    x.kc = (uint32_t)((key >> (1 + nb)) & m);
-    x.A = (uint32_t)((key >> (1 + 2 * nb)) & 0xffffu);
-    return x;
-}
-
-__device__ __forceinline__ uint64_t encode_r(const Regs &x, int nb)
-{
-    return (uint64_t)x.b2 | ((uint64_t)x.k << 1) | ((uint64_t)x.kc << (1 + nb)) |
-           ((uint64_t)x.A << (1 + 2 * nb));
-}
-
-__device__ __forceinline__ Regs decode_h(uint64_t key, int nb, int L)
-{
-    const uint64_t m = (1ull << nb) - 1;
-    Regs x;
-    const uint32_t klow = (uint32_t)(key & ((1ull << L) - 1));
-    x.b2 = (uint32_t)((key >> L) & 1);
-    const uint32_t khigh = (uint32_t)((key >> (L + 1)) & ((1ull << (nb - L)) - 1));
-    x.k = (khigh << L) | klow;
-    x.kc = (uint32_t)((key >> (1 + nb)) & m);
-    x.A = (uint32_t)((key >> (1 + 2 * nb)) & 0xffffu);
-    return x;
-}
-
-__device__ __forceinline__ uint64_t encode_h(const Regs &x, int nb, int L)
-{
-    const uint64_t klow = x.k & ((1u << L) - 1), khigh = x.k >> L;
-    return klow | ((uint64_t)x.b2 << L) | (khigh << (L + 1)) | ((uint64_t)x.kc << (1 + nb)) |
-           ((uint64_t)x.A << (1 + 2 * nb));
-}
-
-/* ---- QRAM and the register maps (semi-quantum operations) --------------------- */
-
-/* QRAM word of row r.j, slot l: (column << 16) | value, 0 outside [0, N s).
- * Slots l < s of a row j < N come from the staged copy in shared memory. */
-__device__ __forceinline__ uint32_t qword(const QwSimDev &d, const Row &r, uint32_t l)
-{
-    if (l < (uint32_t)d.s) return r.valid ? r.simg[l] : 0u;
-    const uint64_t addr = (uint64_t)r.j * (uint64_t)d.s + l;
-    if (addr < (uint64_t)r.n_inst * (uint64_t)d.s) return __ldg(d.img + r.img_base + addr);
-    return 0u;
-}
-
-/* Quantum binary search (Def. 1): the net effect of the reversible loop of
- * Alg. 1 after its uncomputation, i(t) = in-row index of t, 0 if absent.
- * A row j < N holds a sorted list of distinct columns, where a branch-free
- * lower-bound search finds the same index as the fixed ceil(log2 s)+1-probe
- * search with a floor midpoint.  A row j >= N reads the all-zero list, where
- * that fixed-probe search stops at its first midpoint s/2 when t = 0 and
- * finds nothing otherwise. */
-__device__ __forceinline__ uint32_t qbs(const QwSimDev &d, const Row &r, uint32_t target)
-{
-    if (!r.valid) return target == 0 ? (uint32_t)(d.s >> 1) : 0u;
-    uint32_t i = 0, ci = r.simg[0] >> 16; /* ci: the column at i */
-    for (int step = d.s >> 1; step > 0; step >>= 1) {
-        const uint32_t c = r.simg[i + step] >> 16;
-        const bool up = c <= target;
-        i = up ? i + (uint32_t)step : i;
-        ci = up ? c : ci;
-    }
-    return ci == target ? i : 0u;
-}
-
-/* O_A': A ^= a_{j,k}, controlled by jc = kc = 0 (Sec. III-B). */
-__device__ __forceinline__ void op_oa(const QwSimDev &d, const Row &r, Regs &x)
-{
-    if (r.jc == 0 && x.kc == 0) x.A ^= (qword(d, r, x.k) & 0xffffu);
-}
-
-/* O_s' (Eq. "Newprocess"): kc ^= K(j, k); k ^= I(j, kc); swap(k, kc). */
-__device__ __forceinline__ void op_os(const QwSimDev &d, const Row &r, Regs &x)
-{
-    x.kc ^= qword(d, r, x.k) >> 16;
-    x.k ^= qbs(d, r, x.kc);
-    const uint32_t t = x.k;
-    x.k = x.kc;
-    x.kc = t;
-}
-
-/* O_s'^dag: the three steps of O_s' in reverse. */
-__device__ __forceinline__ void op_osdag(const QwSimDev &d, const Row &r, Regs &x)
-{
-    const uint32_t t = x.k;
-    x.k = x.kc;
-    x.kc = t;
-    x.k ^= qbs(d, r, x.kc);
-    x.kc ^= qword(d, r, x.k) >> 16;
-}
-
-/* ---- interference operations on one row ---------------------------------------- */
-
-/* f, g of the conditional rotation on b2 (Alg. T~ and the footnote of Sec. IV):
- * g = sqrt(1-|a|); f = sqrt(a) for a >= 0, i sigma sqrt|a| for a < 0 with
- * sigma = +1 if j <= k else -1.  sqrt values come from a per-code table that
- * the host filled with IEEE-rounded square roots. */
-__device__ __forceinline__ void rot_fg(const QwSimDev &d, uint32_t A, uint32_t j, uint32_t k,
-                                       double2 &f, double &g)
-{
-    const double2 t = __ldg(d.fg + A);
-    g = t.y;
-    const int16_t q = (int16_t)(uint16_t)A;
-    if (q >= 0) f = make_double2(t.x, 0.0);
-    else f = make_double2(0.0, (j <= k) ? t.x : -t.x);
-}
 
 /* R (DAG = false) or R^dag on b2: groups are branch pairs differing in b2,
  * adjacent in the sorted R layout.  R = [[f, -g], [g, conj f]]. */
@@ -404,84 +184,6 @@ __device__ void phase_op(const QwSimDev &d, const Row &r, const uint64_t *ks, do
         if (!zero) as[i] = cneg(as[i]);
     }
     __syncwarp();
-}
-
-/* ---- buckets ---------------------------------------------------------------------- */
-
-__device__ __forceinline__ uint32_t hash_rowkey(uint64_t x)
-{
-    x ^= x >> 33;
-    x *= 0xff51afd7ed558ccdull;
-    x ^= x >> 33;
-    x *= 0xc4ceb9fe1a85ec53ull;
-    x ^= x >> 33;
-    return (uint32_t)x;
-}
-
-__device__ int64_t bucket_of(const QwSimDev &d, const QwBufDev &out, uint32_t inst, uint32_t jc,
-                             uint32_t j, uint32_t b1, int32_t *status)
-{
-    if (jc == 0) {
-        const int64_t lo = d.ninst == 1 ? 0 : d.inst_bkt[inst];
-        const int64_t hi = d.ninst == 1 ? d.dense_buckets : d.inst_bkt[inst + 1];
-        const int64_t b = lo + (((int64_t)j << 1) | (int64_t)b1);
-        if (b < hi) return b;
-        atomicOr(status, QW_ST_SPILL_FULL);
-        return -1;
-    }
-    const uint64_t rk = qw_rowkey(inst, jc, j, b1);
-    uint32_t h = hash_rowkey(rk) & (uint32_t)(d.spill_slots - 1);
-    for (int t = 0; t < d.spill_slots; ++t) {
-        const unsigned long long prev =
-            atomicCAS(reinterpret_cast<unsigned long long *>(out.spill + h), QW_SPILL_EMPTY,
-                      (unsigned long long)rk);
-        if (prev == QW_SPILL_EMPTY || prev == rk) return d.dense_buckets + h;
-        h = (h + 1) & (uint32_t)(d.spill_slots - 1);
-    }
-    atomicOr(status, QW_ST_SPILL_FULL);
-    return -1;
-}
-
-__device__ bool row_of(const QwSimDev &d, const QwBufDev &in, int64_t b, Row &r)
-{
-    if (d.ninst == 1) { /* one instance: everything from the kernel parameters */
-        if (b < d.dense_buckets) {
-            r.inst = 0;
-            r.jc = 0;
-            r.j = (uint32_t)(b >> 1);
-            r.b1 = (uint32_t)(b & 1);
-        } else {
-            const uint64_t rk = in.spill[b - d.dense_buckets];
-            if (rk == QW_SPILL_EMPTY) return false;
-            r.inst = (uint32_t)(rk >> 40);
-            r.jc = (uint32_t)((rk >> 20) & 0xfffffu);
-            r.j = (uint32_t)((rk >> 1) & 0x7ffffu);
-            r.b1 = (uint32_t)(rk & 1);
-        }
-        r.n_inst = (uint32_t)d.n_single;
-        r.img_base = 0;
-        r.valid = r.j < r.n_inst;
-        return true;
-    }
-    if (b < d.dense_buckets) {
-        const int lo = d.unit_inst[b >> 1];
-        const int64_t idx = b - d.inst_bkt[lo];
-        r.inst = (uint32_t)lo;
-        r.jc = 0;
-        r.j = (uint32_t)(idx >> 1);
-        r.b1 = (uint32_t)(idx & 1);
-    } else {
-        const uint64_t rk = in.spill[b - d.dense_buckets];
-        if (rk == QW_SPILL_EMPTY) return false;
-        r.inst = (uint32_t)(rk >> 40);
-        r.jc = (uint32_t)((rk >> 20) & 0xfffffu);
-        r.j = (uint32_t)((rk >> 1) & 0x7ffffu);
-        r.b1 = (uint32_t)(rk & 1);
-    }
-    r.n_inst = (uint32_t)d.inst_n[r.inst];
-    r.img_base = d.inst_img[r.inst];
-    r.valid = r.j < r.n_inst;
-    return true;
 }
 
 /* Final register maps of T~ (O_s'^dag, O_A', O_s'), then S for a walk step,
@@ -801,11 +503,12 @@ template <> struct Amp<double2> {
         double x = 0.0, y = 0.0;
         __device__ void add(T a) { x += a.x; y += a.y; }
         /* lane t < min(s, 32) holds the partial sums of the values t, t + 32, ...
-           (s a power of two).  Butterfly over the w = min(s, 32) lanes, x on
+           (s a power of two); with width < 32 each aligned group of width
+           lanes reduces its own values.  Butterfly over the w = min(s, 32) lanes, x on
            lanes t < w/2 and y on lanes t >= w/2 after the first level, so one
            FP64 add serves both components; the same pairs and order as a
            butterfly over each component alone (FP64 addition commutes). */
-        __device__ void reduce(int s)
+        __device__ void reduce(int s, int width = 32)
         {
             const int w = s < 32 ? s : 32, h = w >> 1;
             if (h > 0) {
@@ -816,8 +519,8 @@ template <> struct Amp<double2> {
                 x = v;
                 y = v;
             }
-            x = __shfl_sync(FULL, x, 0);
-            y = __shfl_sync(FULL, y, h);
+            x = __shfl_sync(FULL, x, 0, width);
+            y = __shfl_sync(FULL, y, h, width);
         }
         __device__ void scale_pow2(double f) { x *= f; y *= f; }
         __device__ T minus(T a) const { return make_double2(x - a.x, y - a.y); }
@@ -909,11 +612,12 @@ template <> struct Amp<float2> {
         DF x, y;
         __device__ void add(T a) { x.add(a.x); y.add(a.y); }
         /* lane t < min(s, 32) holds the partial sums of the values t, t + 32, ...
-           (s a power of two).  Butterfly over the w = min(s, 32) lanes, x on
+           (s a power of two); with width < 32 each aligned group of width
+           lanes reduces its own values.  Butterfly over the w = min(s, 32) lanes, x on
            lanes t < w/2 and y on lanes t >= w/2 after the first level (where a
            y lane adds its own pair to its partner's, the order the partner
            would use), so one float-pair add serves both components. */
-        __device__ void reduce(int s)
+        __device__ void reduce(int s, int width = 32)
         {
             const int w = s < 32 ? s : 32, h = w >> 1;
             if (h > 0) {
@@ -936,10 +640,10 @@ template <> struct Amp<float2> {
                 x = v;
                 y = v;
             }
-            x.h = __shfl_sync(FULL, x.h, 0);
-            x.l = __shfl_sync(FULL, x.l, 0);
-            y.h = __shfl_sync(FULL, y.h, h);
-            y.l = __shfl_sync(FULL, y.l, h);
+            x.h = __shfl_sync(FULL, x.h, 0, width);
+            x.l = __shfl_sync(FULL, x.l, 0, width);
+            y.h = __shfl_sync(FULL, y.h, h, width);
+            y.l = __shfl_sync(FULL, y.l, h, width);
         }
         __device__ void scale_pow2(double f)
         {
@@ -1596,11 +1300,21 @@ __device__ void emit_pairs(const QwSimDev &d, const Row &r, const KeyT *ks, cons
     y.b2 = 0;
     y.A = 0;
     const uint64_t local0 = encode_r(y, d.nb);
-    /* destination bucket of branch i (-1: dropped with a status bit) */
+    /* destination bucket of branch i (-1: dropped with a status bit, or sent
+       to the partition owning its new row) */
     auto dest = [&](int i) -> int64_t {
         const KeyT key = ks[i];
         const uint32_t b2 = (uint32_t)(key & (KeyT)1), k = (uint32_t)(key >> 1) & m;
         const uint32_t kc = (uint32_t)(key >> (1 + d.nb)) & m;
+        if (d.nparts > 1) {
+            const int own = qw_part_owner_of(d, kc, k);
+            if (own != d.part) {
+                part_send(d, own, qw_rowkey(r.inst, kc, k, b2),
+                          local0 | (uint64_t)((key >> KeyB1<KeyT>::bit) & (KeyT)1), Amp<AmpT>::to_d(as[i]), status);
+                nrm.add(as[i]);
+                return -1;
+            }
+        }
         if (kc == 0) {
             const int64_t b = blo + (((int64_t)k << 1) | (int64_t)b2);
             if (b < bhi) return b;
@@ -1632,6 +1346,188 @@ __device__ void emit_pairs(const QwSimDev &d, const Row &r, const KeyT *ks, cons
     }
 }
 
+/* Per-warp shared buffers of the row pipeline (offsets from walk_layout). */
+template <typename AmpT, typename KeyT> struct WalkBufs {
+    KeyT *kP, *kQ;
+    AmpT *aP, *aQ, *aX, *zbuf, *z1buf;
+    uint32_t *simg;
+    int16_t *pbuf, *hidx;
+    typename Amp<AmpT>::RotVal *sfg;
+    __device__ WalkBufs(unsigned char *b, const WalkLayout &lay)
+        : kP(reinterpret_cast<KeyT *>(b + lay.kP)), kQ(reinterpret_cast<KeyT *>(b + lay.kQ)),
+          aP(reinterpret_cast<AmpT *>(b + lay.aP)), aQ(reinterpret_cast<AmpT *>(b + lay.aQ)),
+          aX(reinterpret_cast<AmpT *>(b + lay.aX)), zbuf(reinterpret_cast<AmpT *>(b + lay.zbuf)),
+          z1buf(reinterpret_cast<AmpT *>(b + lay.z1buf)), simg(reinterpret_cast<uint32_t *>(b + lay.simg)),
+          pbuf(reinterpret_cast<int16_t *>(b + lay.pbuf)), hidx(reinterpret_cast<int16_t *>(b + lay.hidx)),
+          sfg(reinterpret_cast<typename Amp<AmpT>::RotVal *>(b + lay.sfg))
+    {
+    }
+};
+
+/* What one pass of the row pipeline runs: one row (bucket bA, n0 branches,
+ * b1 tag tagA) or the two rows of a j as one segment (buckets bA, bB). */
+template <typename KeyT> struct WalkItem {
+    int64_t bA, bB;
+    int n0, n1;
+    KeyT tagA;
+    bool valid;
+};
+
+/* Branch counters of one warp (QW_STAT_*), added to the step's at its end. */
+struct WalkStats {
+    unsigned long long rows = 0, in = 0, rdag = 0, hph = 0, out = 0;
+    __device__ void flush(const QwStepArgs &a) const
+    {
+        if (a.stats && lane_id() == 0 && rows) {
+            atomicAdd(a.stats + QW_STAT_ROWS, rows);
+            atomicAdd(a.stats + QW_STAT_IN, in);
+            atomicAdd(a.stats + QW_STAT_RDAG, rdag);
+            atomicAdd(a.stats + QW_STAT_HPH, hph);
+            atomicAdd(a.stats + QW_STAT_OUT, out);
+        }
+    }
+};
+
+/* One item through T~^dag, H P H, T~ and S (the row pipeline).  (have, hk,
+ * ha): the item's first 32 stored branches, loaded ahead by a pipelined
+ * caller; prefetch() runs once the item's input has been read (a pipelined
+ * caller loads the next item's first branches there).  staged: (inst, j) of
+ * the QRAM row held in B.simg. */
+template <typename AmpT, typename KeyT, typename Prefetch>
+__device__ __forceinline__ void walk_item(const QwSimDev &d, const QwBufDev &in, const QwBufDev &out,
+                                          const QwStepArgs &a, const WalkItem<KeyT> &it, bool have_cur, uint64_t hk,
+                                          AmpT ha, bool rescale, const typename Amp<AmpT>::Scale &scale,
+                                          const WalkBufs<AmpT, KeyT> &B, int64_t &staged,
+                                          typename Amp<AmpT>::Norm &nrm, WalkStats &st, Prefetch &&prefetch)
+{
+    typedef typename Amp<AmpT>::RotVal RotVal;
+    constexpr int B1 = KeyB1<KeyT>::bit;
+    const int lane = lane_id();
+    const int C = d.warp_cap;
+    int n = it.n0 + it.n1;
+    if (n <= 0) return;
+    Row r;
+    if (!row_of(d, in, it.bA, r)) return;
+    if (n > C) {
+        if (lane == 0) atomicOr(a.status, QW_ST_WARP_OVERFLOW);
+        return;
+    }
+    r.simg = B.simg;
+    r.sfg = B.sfg;
+    const int64_t want = ((int64_t)r.inst << 32) | (int64_t)r.j;
+    if (r.valid && want != staged) {
+        const int64_t w0 = r.img_base + (int64_t)r.j * d.s;
+        for (int t = lane; t < d.s; t += 32) {
+            B.simg[t] = __ldg(d.img + w0 + t);
+            B.sfg[t] = __ldg(static_cast<const RotVal *>(d.slot_rot) + w0 + t);
+        }
+        staged = want;
+    }
+    st.rows++;
+    st.in += n;
+    if (r.jc == 0) { /* the zero-type group's slots, filled by T~^dag */
+        for (int t = lane; t < d.s; t += 32) {
+            B.zbuf[t] = Amp<AmpT>::zero();
+            B.pbuf[t] = -1;
+        }
+        __syncwarp();
+    }
+    PairListSink<AmpT, KeyT, true> s0(d, r, B.kQ, B.aQ, B.aX, C, B.zbuf, B.z1buf, B.pbuf);
+    if (!Amp<AmpT>::kHeadLanes && it.n0 <= 32 && it.n1 <= 32) {
+        /* rows of <= 32: T~^dag straight from the loaded registers, the
+           pairs found by one warp match per chunk of <= 32 */
+        const int ash = 1 + 2 * d.nb;
+        const KeyT tagB = (KeyT)1 << B1;
+        uint64_t anc = 0;
+        const AmpT *amp = static_cast<const AmpT *>(in.amp);
+        auto get = [&](int64_t slot, bool pre, uint64_t praw, AmpT pamp, KeyT tag, KeyT &k, AmpT &v) {
+            k = in_key<KeyT>(pre ? praw : in.key[slot], ash, tag, anc);
+            v = pre ? pamp : amp[slot];
+            if (rescale) v = scale.apply(v);
+        };
+        if (n <= 32) {
+            KeyT k = 0;
+            AmpT v = Amp<AmpT>::zero();
+            if (lane < it.n0) get(it.bA * (int64_t)d.cap_row + lane, have_cur, hk, ha, it.tagA, k, v);
+            else if (lane < n) get(it.bB * (int64_t)d.cap_row + (lane - it.n0), have_cur, hk, ha, tagB, k, v);
+            rot0_chunk<AmpT, KeyT>(d, r, k, v, lane < n, s0);
+        } else {
+            KeyT k = 0;
+            AmpT v = Amp<AmpT>::zero();
+            if (lane < it.n0) get(it.bA * (int64_t)d.cap_row + lane, have_cur, hk, ha, it.tagA, k, v);
+            rot0_chunk<AmpT, KeyT>(d, r, k, v, lane < it.n0, s0);
+            /* row B: its first 32 - n0 branches were loaded ahead into lanes n0.. */
+            const int src = (it.n0 + lane) & 31;
+            const uint64_t bh = __shfl_sync(FULL, hk, src);
+            AmpT ba;
+            ba.x = __shfl_sync(FULL, ha.x, src);
+            ba.y = __shfl_sync(FULL, ha.y, src);
+            KeyT kB = 0;
+            AmpT vB = Amp<AmpT>::zero();
+            if (lane < it.n1)
+                get(it.bB * (int64_t)d.cap_row + lane, have_cur && it.n0 + lane < 32, bh, ba, tagB, kB, vB);
+            rot0_chunk<AmpT, KeyT>(d, r, kB, vB, lane < it.n1, s0);
+        }
+        if (__any_sync(FULL, anc != 0) && lane == 0) atomicOr(a.status, QW_ST_ANCILLA);
+    } else {
+        load_seg<AmpT, KeyT>(d, in, it.bA, it.n0, it.tagA, it.bB, it.n1, rescale, scale, B.kP, B.aP, B.kQ, B.aQ, C,
+                             have_cur, hk, ha, a.status);
+        map_rot_pairs<0, AmpT, KeyT>(d, r, B.kP, B.aP, n, s0, B.hidx);
+    }
+    prefetch();
+    int np = sink_count(s0, a.status); /* T~^dag, H P H signs */
+    st.rdag += s0.elems + s0.div;
+    int ez = 0;
+    np = reflect_zero_list<AmpT, KeyT>(d, r, B.kQ, B.aQ, B.aX, np, C, a.status, a, B.zbuf, B.z1buf, B.pbuf,
+                                       ez); /* H P H */
+    st.hph += s0.elems + ez;
+    PairSink<AmpT, KeyT, false> s1(d, r, B.kP, B.aP, C, nullptr, nullptr, nullptr);
+    map_rot_list<1, AmpT, KeyT>(d, r, B.kQ, B.aQ, B.aX, np, s1);
+    n = sink_count(s1, a.status); /* T~ */
+    st.out += n;
+    emit_pairs<AmpT, KeyT>(d, r, B.kP, B.aP, n, out, a.status, nrm); /* S */
+    __syncwarp();
+}
+
+/* The row pipeline for one item, out of line: the slot kernel's path for
+ * what its lanes do not cover (so the fast path keeps its registers and its
+ * accumulators stay out of memory).  Returns the item's norm share and adds
+ * its counters to *st. */
+template <typename AmpT, typename KeyT>
+__device__ __noinline__ double walk_item_ool(const QwSimDev &d, const QwBufDev &in, const QwBufDev &out,
+                                             const QwStepArgs &a, WalkItem<KeyT> it, bool rescale, double scale_v,
+                                             unsigned char *base, WalkLayout lay, WalkStats *st)
+{
+    const WalkBufs<AmpT, KeyT> B(base, lay);
+    const typename Amp<AmpT>::Scale scale(scale_v);
+    int64_t staged = -1;
+    typename Amp<AmpT>::Norm nrm;
+    WalkStats sti;
+    walk_item<AmpT, KeyT>(d, in, out, a, it, false, 0ull, Amp<AmpT>::zero(), rescale, scale, B, staged, nrm, sti,
+                          [] {});
+    st->rows += sti.rows;
+    st->in += sti.in;
+    st->rdag += sti.rdag;
+    st->hph += sti.hph;
+    st->out += sti.out;
+    return nrm.get();
+}
+
+/* Start of a step: a step issued after a failed one does nothing, so the
+ * state of the last clean step (its input buffer, never written) survives for
+ * the host; otherwise clear X_{t+2} for the step after this one. */
+__device__ __forceinline__ bool step_begin(const QwSimDev &d, const QwBufDev &clr, const QwStepArgs &a)
+{
+    const bool skip = *(volatile int32_t *)a.status != 0;
+    if (!skip) {
+        const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t b = tid; b < d.total_buckets; b += nthr) clr.count[b] = 0;
+        for (int64_t t = tid; t < d.spill_slots; t += nthr) clr.spill[t] = QW_SPILL_EMPTY;
+    }
+    return skip;
+}
+
 /* One walk step.  SEG = false: the two rows (jc = 0, j, b1 = 0 / 1) of a j
  * are processed one after the other by the same warp; SEG = true: together,
  * as one segment.  PF = false: 4 blocks per SM, each item loaded when its
@@ -1646,33 +1542,14 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
     __shared__ double block_part[WARPS];
     __shared__ int is_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int C = d.warp_cap;
     const WalkLayout lay = walk_layout<AmpT, KeyT>(d);
-    unsigned char *base = smem + lay.per_warp * warp;
-    KeyT *kP = reinterpret_cast<KeyT *>(base + lay.kP);
-    KeyT *kQ = reinterpret_cast<KeyT *>(base + lay.kQ);
-    AmpT *aP = reinterpret_cast<AmpT *>(base + lay.aP);
-    AmpT *aQ = reinterpret_cast<AmpT *>(base + lay.aQ);
-    AmpT *aX = reinterpret_cast<AmpT *>(base + lay.aX);
-    AmpT *zbuf = reinterpret_cast<AmpT *>(base + lay.zbuf);
-    AmpT *z1buf = reinterpret_cast<AmpT *>(base + lay.z1buf);
-    uint32_t *simg = reinterpret_cast<uint32_t *>(base + lay.simg);
-    int16_t *pbuf = reinterpret_cast<int16_t *>(base + lay.pbuf);
-    int16_t *hidx = reinterpret_cast<int16_t *>(base + lay.hidx);
-    typedef typename Amp<AmpT>::RotVal RotVal;
-    RotVal *sfg = reinterpret_cast<RotVal *>(base + lay.sfg);
+    const WalkBufs<AmpT, KeyT> B(smem + lay.per_warp * warp, lay);
 
-    const bool skip = *(volatile int32_t *)a.status != 0;
-    if (!skip) { /* clear X_{t+2} for the step after this one */
-        const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-        for (int64_t b = tid; b < d.total_buckets; b += nthr) clr.count[b] = 0;
-        for (int64_t t = tid; t < d.spill_slots; t += nthr) clr.spill[t] = QW_SPILL_EMPTY;
-    }
+    const bool skip = step_begin(d, clr, a);
     const bool rescale = a.scale_in != nullptr;
     const typename Amp<AmpT>::Scale scale(rescale ? *a.scale_in : 1.0);
     typename Amp<AmpT>::Norm nrm;
-    unsigned long long st_rows = 0, st_in = 0, st_rdag = 0, st_hph = 0, st_out = 0;
+    WalkStats st;
 
     /* Units: a dense unit u holds the rows (jc = 0, j) with b1 = 0 and 1
        (buckets 2u and 2u + 1); a garbage-row bucket (jc != 0) is a unit of
@@ -1683,14 +1560,8 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
     const int64_t nwarps = (int64_t)gridDim.x * WARPS;
     const int64_t d2 = d.dense_buckets >> 1;
     const int64_t units = skip ? 0 : d2 + d.spill_slots;
-    struct Item {
-        int64_t bA, bB;
-        int n0, n1;
-        KeyT tagA;
-        bool valid;
-    };
     constexpr int B1 = KeyB1<KeyT>::bit;
-    auto item_of = [&](int64_t uu, int part, Item &it) {
+    auto item_of = [&](int64_t uu, int part, WalkItem<KeyT> &it) {
         it.valid = uu < units;
         it.n0 = it.n1 = 0;
         it.tagA = 0;
@@ -1722,7 +1593,7 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
     };
     int64_t u = (int64_t)blockIdx.x * WARPS + warp;
     int part = 0;
-    Item cur, nxt;
+    WalkItem<KeyT> cur, nxt;
     item_of(u, part, cur);
     bool have = false;
     uint64_t pk = 0;
@@ -1737,111 +1608,579 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
         const AmpT ha = pa;
         have = false;
         if (PF) item_of(un, pn, nxt);
-        const Item it = cur;
+        const WalkItem<KeyT> it = cur;
         u = un;
         part = pn;
         if (!PF) item_of(u, part, cur);
         else cur = nxt;
-        int n = it.n0 + it.n1;
-        if (n <= 0) continue;
-        Row r;
-        if (!row_of(d, in, it.bA, r)) continue;
-        if (n > C) {
-            if (lane == 0) atomicOr(a.status, QW_ST_WARP_OVERFLOW);
+        walk_item<AmpT, KeyT>(d, in, out, a, it, have_cur, hk, ha, rescale, scale, B, staged, nrm, st, [&] {
+            if (PF && cur.valid) { /* the next item's first 32 branches (row A, then row B) */
+                const int nn = cur.n0 + cur.n1;
+                have = nn > 0;
+                if (lane < nn) {
+                    const int64_t slot = lane < cur.n0 ? cur.bA * (int64_t)d.cap_row + lane
+                                                       : cur.bB * (int64_t)d.cap_row + (lane - cur.n0);
+                    pk = in.key[slot];
+                    pa = static_cast<const AmpT *>(in.amp)[slot];
+                }
+            }
+        });
+    }
+    st.flush(a);
+    finish_step(a, nrm.get(), block_part, &is_last, true);
+}
+
+/* ==== slot kernel: one lane per QRAM slot ==================================== */
+/*
+ * A branch (kc, k, b2) of a row (jc = 0, j < N, b1) whose T~^dag coordinates
+ * (l, z) = O_s'^dag(k, kc) = (kc ^ I(j, k), k ^ K(j, l)) have z = 0 sits on
+ * slot l < s of the row, and its b2 partner on the same slot.  In the states
+ * the walk reaches from T~|b~> every branch of a b1 = 0 row is of that kind
+ * and so are most of a b1 = 1 row (the others come from rows whose padding
+ * names j without j's row naming them).  The kernel takes RPP = 32 / s
+ * consecutive j (a group) per warp pass, lane t = u s + l on slot l of the
+ * group's u-th j:
+ *   - load: every branch of the group's 2 RPP buckets is read once, mapped by
+ *     T~^dag's first O_s'^dag (one QBS and one QRAM word on the staged rows)
+ *     and scattered into the slot table of its row, where its partner lands
+ *     beside it: no matching and no sort; the rest ("extras") are listed;
+ *   - pass A, the b1 = 0 rows: R^dag on each slot's pair; the zero-type group
+ *     of H P H (kc = z = 0, l < s, b2 = 0, jc = b1 = 0) is exactly the row's s
+ *     slots, summed over the unit's s lanes; the reflected pair goes through
+ *     T~ (O_A' reads slot l, O_s' maps (l, 0) to (K(j, l), 0) with no search)
+ *     and R, then S;
+ *   - pass B, the b1 = 1 rows' slots and the extras, one lane per pair:
+ *     R^dag, the sign of H P H (-1 outside the zero-type groups), the maps and
+ *     R of T~, S.
+ * The operations, their order, the pruning points and the counters are those
+ * of k_walk, and so are the results (bit for bit up to the norm's summation
+ * order).  Groups holding anything the lanes do not cover (a row j >= N with
+ * branches, more extras than the list holds) and the garbage rows (jc != 0)
+ * go through the row pipeline. */
+constexpr int kSlotExtras = 32; /* extras list of a group */
+constexpr int kSlotItems = 64;  /* pass B items: 32 slots + 32 extra pairs */
+
+struct SlotUnit {
+    uint32_t j, inst, n;
+    int32_t valid;
+    int64_t img, blo, bhi; /* image offset of the instance, its dense bucket range */
+};
+
+struct SlotLayout {
+    size_t ws, rot, ta, tb, ek, ea, im, ia, unit, per_warp;
+};
+
+template <typename AmpT>
+__host__ __device__ inline SlotLayout slot_layout()
+{
+    SlotLayout o;
+    size_t p = 0;
+#define QW_TAKE(field, bytes)                                                                      \
+    o.field = p;                                                                                   \
+    p = (p + (bytes) + 15) & ~(size_t)15
+    QW_TAKE(ws, 32 * sizeof(uint32_t));
+    QW_TAKE(rot, 32 * 16);
+    QW_TAKE(ta, 64 * sizeof(AmpT));
+    QW_TAKE(tb, 64 * sizeof(AmpT));
+    QW_TAKE(ek, kSlotExtras * sizeof(uint64_t));
+    QW_TAKE(ea, kSlotExtras * sizeof(AmpT));
+    QW_TAKE(im, kSlotItems * sizeof(uint16_t));
+    QW_TAKE(ia, 2 * kSlotItems * sizeof(AmpT));
+    QW_TAKE(unit, 8 * sizeof(SlotUnit));
+#undef QW_TAKE
+    o.per_warp = p;
+    return o;
+}
+
+template <typename AmpT, typename KeyT>
+__host__ __device__ inline size_t slot_per_warp(const QwSimDev &d)
+{
+    const size_t a = walk_layout<AmpT, KeyT>(d).per_warp, b = slot_layout<AmpT>().per_warp;
+    return a > b ? a : b;
+}
+
+/* Def. 1 on a staged row of S sorted distinct columns (the branch-free lower
+ * bound of qbs() with S known at compile time). */
+template <int S>
+__device__ __forceinline__ uint32_t qbs_row(const uint32_t *row, uint32_t target)
+{
+    uint32_t i = 0, ci = row[0] >> 16;
+#pragma unroll
+    for (int step = S >> 1; step > 0; step >>= 1) {
+        const uint32_t c = row[i + step] >> 16;
+        const bool up = c <= target;
+        i = up ? i + (uint32_t)step : i;
+        ci = up ? c : ci;
+    }
+    return ci == target ? i : 0u;
+}
+
+__device__ __forceinline__ Row slot_row(const SlotUnit &U, const uint32_t *ws, const void *rot)
+{
+    Row r;
+    r.inst = U.inst;
+    r.jc = 0;
+    r.j = U.j;
+    r.b1 = 0;
+    r.n_inst = U.n;
+    r.img_base = U.img;
+    r.valid = U.valid != 0;
+    r.simg = ws;
+    r.sfg = rot;
+    return r;
+}
+
+template <typename AmpT>
+__device__ __forceinline__ bool amp_nonzero(AmpT a)
+{
+    return a.x != 0 || a.y != 0;
+}
+
+/* S for up to two kept outputs of a lane: (kc_out, k_out, b2 = 0 / 1) of row
+ * (jc = 0, j, b1) go to row (kc_out, k_out, b2) with local registers
+ * (kc, k, b2) = (0, j, b1); both slot claims are in flight before the stores. */
+template <typename AmpT>
+__device__ __forceinline__ void slot_emit(const QwSimDev &d, const QwBufDev &out, const SlotUnit &U, uint32_t k_out,
+                                          uint32_t kc_out, uint32_t b1, AmpT r0, AmpT r1, bool e0, bool e1,
+                                          int32_t *status, typename Amp<AmpT>::Norm &nrm)
+{
+    int64_t b0 = -1, bb1 = -1;
+    const uint64_t local = (uint64_t)b1 | ((uint64_t)U.j << 1);
+    if (d.nparts > 1) { /* the new row (kc_out, k_out) is another partition's */
+        const int own = qw_part_owner_of(d, kc_out, k_out);
+        if (own != d.part) {
+            if (e0) {
+                part_send(d, own, qw_rowkey(U.inst, kc_out, k_out, 0), local, Amp<AmpT>::to_d(r0), status);
+                nrm.add(r0);
+            }
+            if (e1) {
+                part_send(d, own, qw_rowkey(U.inst, kc_out, k_out, 1), local, Amp<AmpT>::to_d(r1), status);
+                nrm.add(r1);
+            }
+            return;
+        }
+    }
+    if (kc_out == 0) {
+        const int64_t b = U.blo + ((int64_t)k_out << 1);
+        if (e0) {
+            if (b < U.bhi) b0 = b;
+            else atomicOr(status, QW_ST_SPILL_FULL);
+        }
+        if (e1) {
+            if (b + 1 < U.bhi) bb1 = b + 1;
+            else atomicOr(status, QW_ST_SPILL_FULL);
+        }
+    } else {
+        if (e0) b0 = bucket_of(d, out, U.inst, kc_out, k_out, 0, status);
+        if (e1) bb1 = bucket_of(d, out, U.inst, kc_out, k_out, 1, status);
+    }
+    const int p0 = b0 >= 0 ? atomicAdd(out.count + b0, 1) : 0;
+    const int p1 = bb1 >= 0 ? atomicAdd(out.count + bb1, 1) : 0;
+    if (b0 >= 0) {
+        if (p0 < d.cap_row) {
+            const int64_t sl = b0 * (int64_t)d.cap_row + p0;
+            out.key[sl] = local;
+            static_cast<AmpT *>(out.amp)[sl] = r0;
+            nrm.add(r0);
+        } else {
+            atomicOr(status, QW_ST_ROW_OVERFLOW);
+        }
+    }
+    if (bb1 >= 0) {
+        if (p1 < d.cap_row) {
+            const int64_t sl = bb1 * (int64_t)d.cap_row + p1;
+            out.key[sl] = local;
+            static_cast<AmpT *>(out.amp)[sl] = r1;
+            nrm.add(r1);
+        } else {
+            atomicOr(status, QW_ST_ROW_OVERFLOW);
+        }
+    }
+}
+
+template <typename AmpT, int S, typename KeyT>
+__global__ void __launch_bounds__(WARPS * 32, 4) k_walk_slot(QwSimDev d, QwBufDev in, QwBufDev out, QwBufDev clr,
+                                                             QwStepArgs a)
+{
+    typedef typename Amp<AmpT>::RotVal RotVal;
+    constexpr int RPP = 32 / S, NBK = 2 * RPP;
+    constexpr int B1 = KeyB1<KeyT>::bit;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double block_part[WARPS];
+    __shared__ int is_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const WalkLayout lay = walk_layout<AmpT, KeyT>(d);
+    const SlotLayout sl = slot_layout<AmpT>();
+    unsigned char *base = smem + slot_per_warp<AmpT, KeyT>(d) * warp;
+    uint32_t *ws = reinterpret_cast<uint32_t *>(base + sl.ws);
+    RotVal *rotv = reinterpret_cast<RotVal *>(base + sl.rot);
+    AmpT *ta = reinterpret_cast<AmpT *>(base + sl.ta);
+    AmpT *tb = reinterpret_cast<AmpT *>(base + sl.tb);
+    uint64_t *ek = reinterpret_cast<uint64_t *>(base + sl.ek);
+    AmpT *ea = reinterpret_cast<AmpT *>(base + sl.ea);
+    uint16_t *im = reinterpret_cast<uint16_t *>(base + sl.im);
+    AmpT *ia = reinterpret_cast<AmpT *>(base + sl.ia);
+    SlotUnit *units = reinterpret_cast<SlotUnit *>(base + sl.unit);
+
+    const bool skip = step_begin(d, clr, a);
+    const bool rescale = a.scale_in != nullptr;
+    const double scale_v = rescale ? *a.scale_in : 1.0;
+    const typename Amp<AmpT>::Scale scale(scale_v);
+    typename Amp<AmpT>::Norm nrm;
+    WalkStats st;
+    const AmpT zero = Amp<AmpT>::zero();
+    const AmpT *amp_in = static_cast<const AmpT *>(in.amp);
+    const uint32_t msk = (1u << d.nb) - 1u;
+    const int ash = 1 + 2 * d.nb;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t d2 = d.dense_buckets >> 1;
+    const int64_t ngroups = skip ? 0 : (d2 + RPP - 1) / RPP;
+    const int64_t nwarps = (int64_t)gridDim.x * WARPS;
+    const int64_t gw = (int64_t)blockIdx.x * WARPS + warp;
+
+    /* units the lanes do not cover go to the row pipeline, run by the last
+       block once every other block is done (the hot loop holds no call) */
+    auto defer = [&](int32_t entry) {
+        if (lane == 0) {
+            a.deferred[atomicAdd(a.deferred_ctr, 1u)] = entry;
+            __threadfence(); /* visible before this block counts itself done */
+        }
+    };
+
+    for (int64_t g = gw; g < ngroups; g += nwarps) {
+        const int64_t u0 = g * RPP;
+        /* counts of the group's buckets 2 u0 .. 2 u0 + NBK - 1 and their
+           exclusive offsets in the group's branch order */
+        int cnt = 0;
+        if (lane < NBK && u0 + (lane >> 1) < d2) cnt = min(in.count[2 * u0 + lane], d.cap_row);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < NBK; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(FULL, incl, NBK - 1);
+        if (total == 0) continue;
+        const int excl = incl - cnt;
+        if (lane < RPP) {
+            SlotUnit U;
+            const int64_t uu = u0 + lane;
+            U.valid = 0;
+            U.j = 0;
+            U.inst = 0;
+            U.n = 0;
+            U.img = 0;
+            U.blo = 0;
+            U.bhi = d.dense_buckets;
+            if (uu < d2) {
+                if (d.ninst == 1) {
+                    U.j = (uint32_t)uu;
+                    U.n = (uint32_t)d.n_single;
+                } else {
+                    const int i = d.unit_inst[uu];
+                    U.inst = (uint32_t)i;
+                    U.blo = d.inst_bkt[i];
+                    U.bhi = d.inst_bkt[i + 1];
+                    U.j = (uint32_t)((2 * uu - U.blo) >> 1);
+                    U.n = (uint32_t)d.inst_n[i];
+                    U.img = d.inst_img[i];
+                }
+                U.valid = U.j < U.n;
+            }
+            units[lane] = U;
+        }
+        __syncwarp();
+        /* a row j >= N holding branches: the row pipeline */
+        const bool bad = lane < NBK && cnt > 0 && !units[lane >> 1].valid;
+        if (__any_sync(FULL, bad)) {
+            for (int q = 0; q < RPP; ++q) {
+                const int c0 = __shfl_sync(FULL, cnt, 2 * q), c1 = __shfl_sync(FULL, cnt, 2 * q + 1);
+                if (c0 + c1 > 0) defer((int32_t)(u0 + q));
+            }
             continue;
         }
-        r.simg = simg;
-        r.sfg = sfg;
-        const int64_t want = ((int64_t)r.inst << 32) | (int64_t)r.j;
-        if (r.valid && want != staged) {
-            const int64_t w0 = r.img_base + (int64_t)r.j * d.s;
-            for (int t = lane; t < d.s; t += 32) {
-                simg[t] = __ldg(d.img + w0 + t);
-                sfg[t] = __ldg(static_cast<const RotVal *>(d.slot_rot) + w0 + t);
+        /* stage the group's QRAM rows (contiguous in the image for one
+           instance): lane t holds slot l = t % S of the row of unit t / S;
+           a slot whose element is 0 rotates by R(0) */
+        {
+            const SlotUnit &U = units[lane / S];
+            uint32_t w = 0;
+            RotVal rv = Amp<AmpT>::rot_zero();
+            if (U.valid) {
+                const int64_t at = U.img + (int64_t)U.j * S + (lane % S);
+                w = __ldg(d.img + at);
+                if ((w & 0xffffu) != 0) rv = __ldg(static_cast<const RotVal *>(d.slot_rot) + at);
             }
-            staged = want;
+            ws[lane] = w;
+            rotv[lane] = rv;
+            ta[lane] = zero;
+            ta[lane + 32] = zero;
+            tb[lane] = zero;
+            tb[lane + 32] = zero;
         }
-        st_rows++;
-        st_in += n;
-        if (r.jc == 0) { /* the zero-type group's slots, filled by T~^dag */
-            for (int t = lane; t < d.s; t += 32) {
-                zbuf[t] = Amp<AmpT>::zero();
-                pbuf[t] = -1;
+        int ex[NBK];
+#pragma unroll
+        for (int q = 0; q < NBK; ++q) ex[q] = __shfl_sync(FULL, excl, q);
+        __syncwarp();
+        /* load: O_s'^dag of each branch, scattered to its slot or listed */
+        uint64_t anc = 0;
+        int ne = 0;
+        for (int b0 = 0; b0 < total; b0 += 32) {
+            const int t = b0 + lane;
+            const bool act = t < total;
+            int bi = 0, start = 0;
+#pragma unroll
+            for (int q = 1; q < NBK; ++q) {
+                const bool ge = t >= ex[q];
+                bi += ge ? 1 : 0;
+                start = ge ? ex[q] : start;
             }
-            __syncwarp();
-        }
-        PairListSink<AmpT, KeyT, true> s0(d, r, kQ, aQ, aX, C, zbuf, z1buf, pbuf);
-        if (!Amp<AmpT>::kHeadLanes && it.n0 <= 32 && it.n1 <= 32) {
-            /* rows of <= 32: T~^dag straight from the loaded registers, the
-               pairs found by one warp match per chunk of <= 32 */
-            const int ash = 1 + 2 * d.nb;
-            const KeyT tagB = (KeyT)1 << B1;
-            uint64_t anc = 0;
-            const AmpT *amp = static_cast<const AmpT *>(in.amp);
-            auto get = [&](int64_t slot, bool pre, uint64_t praw, AmpT pamp, KeyT tag, KeyT &k, AmpT &v) {
-                k = in_key<KeyT>(pre ? praw : in.key[slot], ash, tag, anc);
-                v = pre ? pamp : amp[slot];
+            const int ut = bi >> 1, b1 = bi & 1;
+            uint64_t raw = 0;
+            AmpT v = zero;
+            if (act) {
+                const int64_t at = (2 * u0 + bi) * (int64_t)d.cap_row + (t - start);
+                raw = in.key[at];
+                v = amp_in[at];
                 if (rescale) v = scale.apply(v);
-            };
-            if (n <= 32) {
-                KeyT k = 0;
-                AmpT v = Amp<AmpT>::zero();
-                if (lane < it.n0) get(it.bA * (int64_t)d.cap_row + lane, have_cur, hk, ha, it.tagA, k, v);
-                else if (lane < n) get(it.bB * (int64_t)d.cap_row + (lane - it.n0), have_cur, hk, ha, tagB, k, v);
-                rot0_chunk<AmpT, KeyT>(d, r, k, v, lane < n, s0);
-            } else {
-                KeyT k = 0;
-                AmpT v = Amp<AmpT>::zero();
-                if (lane < it.n0) get(it.bA * (int64_t)d.cap_row + lane, have_cur, hk, ha, it.tagA, k, v);
-                rot0_chunk<AmpT, KeyT>(d, r, k, v, lane < it.n0, s0);
-                /* row B: its first 32 - n0 branches were loaded ahead into lanes n0.. */
-                const int src = (it.n0 + lane) & 31;
-                const uint64_t bh = __shfl_sync(FULL, hk, src);
-                AmpT ba;
-                ba.x = __shfl_sync(FULL, ha.x, src);
-                ba.y = __shfl_sync(FULL, ha.y, src);
-                KeyT kB = 0;
-                AmpT vB = Amp<AmpT>::zero();
-                if (lane < it.n1)
-                    get(it.bB * (int64_t)d.cap_row + lane, have_cur && it.n0 + lane < 32, bh, ba, tagB, kB, vB);
-                rot0_chunk<AmpT, KeyT>(d, r, kB, vB, lane < it.n1, s0);
+                anc |= raw >> ash;
             }
-            if (__any_sync(FULL, anc != 0) && lane == 0) atomicOr(a.status, QW_ST_ANCILLA);
-        } else {
-            load_seg<AmpT, KeyT>(d, in, it.bA, it.n0, it.tagA, it.bB, it.n1, rescale, scale, kP, aP, kQ, aQ, C,
-                                 have_cur, hk, ha, a.status);
-            map_rot_pairs<0, AmpT, KeyT>(d, r, kP, aP, n, s0, hidx);
+            const uint32_t b2 = (uint32_t)(raw & 1u), k = (uint32_t)(raw >> 1) & msk;
+            const uint32_t kc = (uint32_t)(raw >> (1 + d.nb)) & msk;
+            const uint32_t *row = ws + ut * S;
+            const uint32_t l = kc ^ qbs_row<S>(row, k);
+            bool isslot = false;
+            if (act && l < (uint32_t)S) isslot = (k ^ (row[l] >> 16)) == 0;
+            if (isslot) (b1 ? tb : ta)[(ut * S + (int)l) * 2 + (int)b2] = v;
+            const bool isext = act && !isslot;
+            const unsigned xm = __ballot_sync(FULL, isext);
+            if (isext) {
+                const int e = ne + __popc(xm & lt);
+                if (e < kSlotExtras) {
+                    ek[e] = (uint64_t)in_key<KeyT>(raw, ash, (KeyT)b1 << B1, anc) | ((uint64_t)ut << 56);
+                    ea[e] = v;
+                }
+            }
+            ne += __popc(xm);
         }
-        if (PF && cur.valid) { /* the next item's first 32 branches (row A, then row B) */
-            const int nn = cur.n0 + cur.n1;
-            have = nn > 0;
-            if (lane < nn) {
-                const int64_t slot = lane < cur.n0 ? cur.bA * (int64_t)d.cap_row + lane
-                                                   : cur.bB * (int64_t)d.cap_row + (lane - cur.n0);
-                pk = in.key[slot];
-                pa = static_cast<const AmpT *>(in.amp)[slot];
+        if (__any_sync(FULL, anc != 0) && lane == 0) atomicOr(a.status, QW_ST_ANCILLA);
+        if (ne > kSlotExtras) { /* more extras than the list holds: the row pipeline */
+            for (int q = 0; q < RPP; ++q) {
+                const int c0 = __shfl_sync(FULL, cnt, 2 * q), c1 = __shfl_sync(FULL, cnt, 2 * q + 1);
+                if (c0 + c1 > 0) defer((int32_t)(u0 + q));
+            }
+            continue;
+        }
+        {
+            unsigned long long nu = 0;
+#pragma unroll
+            for (int q = 0; q < RPP; ++q) nu += (ex[2 * q] != (2 * q + 2 < NBK ? ex[2 * q + 2] : total)) ? 1 : 0;
+            st.rows += nu;
+            st.in += (unsigned long long)total;
+        }
+        __syncwarp();
+
+        /* ---- pass A: the b1 = 0 rows, lane t on slot l = t % S of unit t / S ---- */
+        {
+            const SlotUnit &U = units[lane / S];
+            const uint32_t w = ws[lane], col = w >> 16, val = w & 0xffffu;
+            const RotVal rv = rotv[lane];
+            const bool sneg = U.j > col;
+            AmpT o0, o1;
+            Amp<AmpT>::rot(rv, val, true, sneg, ta[2 * lane], ta[2 * lane + 1], o0, o1); /* R^dag */
+            const bool c0 = Amp<AmpT>::keep(d, o0), c1 = Amp<AmpT>::keep(d, o1);
+            st.rdag += __popc(__ballot_sync(FULL, c0)) + __popc(__ballot_sync(FULL, c1));
+            /* H P H on the zero-type group: a_l -> (2/s) sum_v a_v - a_l; the
+               b2 = 1 member, outside every zero-type group, is negated */
+            const AmpT z0 = c0 ? o0 : zero;
+            typename Amp<AmpT>::Sum sum;
+            sum.add(z0);
+            sum.reduce(S, S);
+            if (a.qls_readout && U.valid && (lane % S) == 0) {
+                const double2 sv = sum.value();
+                const double coef = a.qls_coefs[*a.qls_j];
+                double2 acc = a.qls_y[U.j];
+                acc.x += coef * (d.inv_sqrt_s * sv.x);
+                acc.y += coef * (d.inv_sqrt_s * sv.y);
+                a.qls_y[U.j] = acc;
+            }
+            sum.scale_pow2(d.two_over_s);
+            const AmpT h0 = sum.minus(z0);
+            const bool d0 = Amp<AmpT>::keep(d, h0);
+            st.hph += __popc(__ballot_sync(FULL, d0)) + __popc(__ballot_sync(FULL, c1));
+            /* T~: O_A' reads slot l (A = a_{j,l}), O_s' takes (l, 0) to (K(j, l), 0);
+               R; the rest of T~ returns A to 0 */
+            AmpT r0, r1;
+            Amp<AmpT>::rot(rv, val, false, sneg, d0 ? h0 : zero, c1 ? Amp<AmpT>::neg(o1) : zero, r0, r1);
+            const bool e0 = Amp<AmpT>::keep(d, r0), e1 = Amp<AmpT>::keep(d, r1);
+            st.out += __popc(__ballot_sync(FULL, e0)) + __popc(__ballot_sync(FULL, e1));
+            slot_emit<AmpT>(d, out, U, col, 0u, 0u, r0, r1, e0, e1, a.status, nrm); /* S */
+        }
+
+        /* ---- pass B: list the b1 = 1 slots and the extras' pairs ---- */
+        int ni;
+        {
+            const AmpT p0 = tb[2 * lane], p1 = tb[2 * lane + 1];
+            const bool pres = amp_nonzero(p0) || amp_nonzero(p1);
+            const unsigned pm = __ballot_sync(FULL, pres);
+            if (pres) {
+                const int q = __popc(pm & lt);
+                im[q] = (uint16_t)lane;
+                ia[2 * q] = p0;
+                ia[2 * q + 1] = p1;
+            }
+            ni = __popc(pm);
+            if (ne > 0) {
+                /* pairs among the extras: keys equal but for b2, in one unit */
+                const bool v = lane < ne;
+                uint64_t kk = v ? ek[lane] : ~0ull - (uint64_t)(2 * lane);
+                const AmpT va = v ? ea[lane] : zero;
+                const unsigned mm = __match_any_sync(FULL, kk >> 1);
+                const unsigned other = mm & ~(1u << lane);
+                const bool one = (kk & 1ull) != 0;
+                const bool head = v && (!one || other == 0);
+                const int src = other ? (__ffs(other) - 1) : lane;
+                AmpT pa;
+                pa.x = __shfl_sync(FULL, va.x, src);
+                pa.y = __shfl_sync(FULL, va.y, src);
+                const unsigned hm = __ballot_sync(FULL, head);
+                if (head) {
+                    const int q = ni + __popc(hm & lt);
+                    im[q] = (uint16_t)(0x8000u | (unsigned)lane);
+                    ia[2 * q] = one ? zero : va;
+                    ia[2 * q + 1] = one ? va : (other ? pa : zero);
+                }
+                ni += __popc(hm);
             }
         }
-        int np = sink_count(s0, a.status);                                     /* T~^dag, H P H signs */
-        st_rdag += s0.elems + s0.div;
-        int ez = 0;
-        np = reflect_zero_list<AmpT, KeyT>(d, r, kQ, aQ, aX, np, C, a.status, a, zbuf, z1buf, pbuf, ez); /* H P H */
-        st_hph += s0.elems + ez;
-        PairSink<AmpT, KeyT, false> s1(d, r, kP, aP, C, nullptr, nullptr, nullptr);
-        map_rot_list<1, AmpT, KeyT>(d, r, kQ, aQ, aX, np, s1);
-        n = sink_count(s1, a.status);                                          /* T~ */
-        st_out += n;
-        emit_pairs<AmpT, KeyT>(d, r, kP, aP, n, out, a.status, nrm);           /* S */
+        __syncwarp();
+        /* ---- pass B: one lane per pair ---- */
+        for (int c = 0; c < ni; c += 32) {
+            const int q = c + lane;
+            const bool act = q < ni;
+            const unsigned meta = act ? im[q] : 0u;
+            const bool isext = (meta & 0x8000u) != 0;
+            const AmpT a0 = act ? ia[2 * q] : zero, a1 = act ? ia[2 * q + 1] : zero;
+            int ut;
+            uint32_t b1, Adag, At, k_out = 0, kc_out = 0;
+            bool sdag, st_neg;
+            RotVal rdag, rt;
+            KeyT key = 0;
+            if (!isext) { /* slot t of a b1 = 1 row: (l, 0) both ways */
+                const int t = (int)(meta & 63u);
+                ut = t / S;
+                b1 = 1;
+                const uint32_t w = ws[t];
+                k_out = w >> 16;
+                Adag = At = w & 0xffffu;
+                rdag = rt = rotv[t];
+                sdag = st_neg = units[ut].j > k_out;
+            } else { /* an extra: the general maps of rot_head */
+                const uint64_t e = ek[meta & 0x7fffu];
+                ut = (int)(e >> 56);
+                key = (KeyT)(e & ~(0xffull << 56));
+                b1 = (uint32_t)((key >> B1) & (KeyT)1);
+                key &= ~(((KeyT)1) | ((KeyT)1 << B1));
+                const Row r = slot_row(units[ut], ws + ut * S, rotv + ut * S);
+                uint32_t slot;
+                key = map_tdag<KeyT>(d, r, key, slot, Adag, sdag);
+                rdag = Adag == 0 ? Amp<AmpT>::rot_zero()
+                                 : (slot < (uint32_t)S ? rotv[ut * S + slot] : Amp<AmpT>::rot_table(d, Adag));
+            }
+            AmpT o0, o1;
+            Amp<AmpT>::rot(rdag, Adag, true, sdag, a0, a1, o0, o1); /* R^dag */
+            const bool c0 = act && Amp<AmpT>::keep(d, o0), c1 = act && Amp<AmpT>::keep(d, o1);
+            const int kept = __popc(__ballot_sync(FULL, c0)) + __popc(__ballot_sync(FULL, c1));
+            st.rdag += kept;
+            st.hph += kept; /* H P H: -1 here */
+            if (isext && act) {
+                const Row r = slot_row(units[ut], ws + ut * S, rotv + ut * S);
+                uint32_t slot;
+                const KeyT kt = map_t<KeyT>(d, r, key, slot, At, st_neg);
+                k_out = (uint32_t)(kt >> 1) & msk;
+                kc_out = (uint32_t)(kt >> (1 + d.nb)) & msk;
+                rt = At == 0 ? Amp<AmpT>::rot_zero()
+                             : (slot < (uint32_t)S ? rotv[ut * S + slot] : Amp<AmpT>::rot_table(d, At));
+            }
+            AmpT r0, r1;
+            Amp<AmpT>::rot(rt, At, false, st_neg, c0 ? Amp<AmpT>::neg(o0) : zero, c1 ? Amp<AmpT>::neg(o1) : zero,
+                           r0, r1); /* R */
+            const bool e0 = act && Amp<AmpT>::keep(d, r0), e1 = act && Amp<AmpT>::keep(d, r1);
+            st.out += __popc(__ballot_sync(FULL, e0)) + __popc(__ballot_sync(FULL, e1));
+            if (act) slot_emit<AmpT>(d, out, units[ut], k_out, kc_out, b1, r0, r1, e0, e1, a.status, nrm); /* S */
+        }
         __syncwarp();
     }
-    if (a.stats && lane == 0 && st_rows) {
-        atomicAdd(a.stats + QW_STAT_ROWS, st_rows);
-        atomicAdd(a.stats + QW_STAT_IN, st_in);
-        atomicAdd(a.stats + QW_STAT_RDAG, st_rdag);
-        atomicAdd(a.stats + QW_STAT_HPH, st_hph);
-        atomicAdd(a.stats + QW_STAT_OUT, st_out);
+    /* the garbage rows (jc != 0) */
+    if (!skip) {
+        for (int64_t su = gw; su < d.spill_slots; su += nwarps)
+            if (in.count[d.dense_buckets + su] > 0) defer((int32_t)(0x80000000u | (uint32_t)su));
     }
-    finish_step(a, nrm.get(), block_part, &is_last, true);
+    st.flush(a);
+
+    /* end of the step: block partial of the norm; the last block to finish
+       runs the deferred units through the row pipeline, then reduces */
+    double nv = warp_sum(nrm.get());
+    if (lane == 0) block_part[warp] = nv;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < WARPS; ++w) sum += block_part[w];
+        a.partials[blockIdx.x] = sum;
+        __threadfence();
+        const unsigned prev = atomicAdd(a.done_ctr, 1u);
+        is_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    const unsigned nd = *(volatile unsigned int *)a.deferred_ctr;
+    double nd_nrm = 0.0;
+    WalkStats st_ool;
+    for (unsigned e = (unsigned)warp; e < nd; e += WARPS) {
+        const uint32_t ent = (uint32_t)__ldcg(a.deferred + e);
+        WalkItem<KeyT> it;
+        it.valid = true;
+        if (ent & 0x80000000u) { /* a garbage row: one row on its own */
+            const int64_t su = (int64_t)(ent & 0x7fffffffu);
+            it.bA = d.dense_buckets + su;
+            it.bB = -1;
+            it.n0 = min(__ldcg(in.count + it.bA), d.cap_row);
+            it.n1 = 0;
+            it.tagA = (KeyT)(__ldcg(in.spill + su) & 1ull) << B1;
+        } else { /* a dense unit: its two rows as one segment */
+            it.bA = 2 * (int64_t)ent;
+            it.bB = it.bA + 1;
+            it.n0 = min(__ldcg(in.count + it.bA), d.cap_row);
+            it.n1 = min(__ldcg(in.count + it.bB), d.cap_row);
+            it.tagA = 0;
+        }
+        nd_nrm += walk_item_ool<AmpT, KeyT>(d, in, out, a, it, rescale, scale_v, base, lay, &st_ool);
+    }
+    st_ool.flush(a);
+    nd_nrm = warp_sum(nd_nrm);
+    __syncthreads();
+    if (lane == 0) block_part[warp] = nd_nrm;
+    __syncthreads();
+    double v = 0.0;
+    for (unsigned bb = threadIdx.x; bb < gridDim.x; bb += blockDim.x) v += __ldcg(a.partials + bb);
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) block_part[warp] += v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < WARPS; ++w) tot += block_part[w];
+        const bool clean = *(volatile int32_t *)a.status == 0;
+        if (clean) {
+            *a.norm_out = tot;
+            if (a.scale_out) *a.scale_out = (a.renorm && tot > 0.0) ? sqrt(*a.renorm_target / tot) : 1.0;
+            if (a.steps_done) *a.steps_done += 1;
+            if (a.stats) a.stats[QW_STAT_STEPS] += 1;
+        }
+        *a.deferred_ctr = 0u;
+        *a.done_ctr = 0u;
+    }
 }
 
 /* T~ on |b~> (qw_state_init): every row (jc = 0, j, b1 = 0) of the range
@@ -1907,6 +2246,28 @@ __global__ void __launch_bounds__(WARPS * 32) k_tinit(QwSimDev d, QwBufDev buf, 
 
 /* ---- small kernels ------------------------------------------------------------ */
 
+/* Row buckets moved to a larger row capacity: bucket b's entries from
+ * b * cap_old to b * cap_new (counts and the garbage-row table unchanged). */
+__global__ void k_regrow(int64_t buckets, const int32_t *count, int cap_old, int cap_new, const uint64_t *key_old,
+                         const unsigned char *amp_old, uint64_t *key_new, unsigned char *amp_new, int amp_bytes)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int64_t b = warp; b < buckets; b += nw) {
+        int n = count[b];
+        if (n > cap_old) n = cap_old;
+        for (int i = lane; i < n; i += 32) {
+            const int64_t so = b * (int64_t)cap_old + i, sn = b * (int64_t)cap_new + i;
+            key_new[sn] = key_old[so];
+            for (int t = 0; t < amp_bytes; t += 8)
+                *reinterpret_cast<uint64_t *>(amp_new + sn * amp_bytes + t) =
+                    *reinterpret_cast<const uint64_t *>(amp_old + so * amp_bytes + t);
+        }
+    }
+}
+
+
 __global__ void k_clear(QwBufDev buf, int64_t lo, int64_t hi, int spill_slots, int clear_spill)
 {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1926,6 +2287,7 @@ __global__ void k_init_b(QwSimDev d, QwBufDev buf, int inst, const double *b_re,
     if (j >= n) return;
     double2 v = make_double2(b_re[j], b_im ? b_im[j] : 0.0);
     if (v.x == 0.0 && v.y == 0.0) return;
+    if (d.nparts > 1 && qw_part_owner_of(d, 0u, (uint32_t)j) != d.part) return; /* another partition's row */
     if (scale) v = make_double2(v.x / *scale, v.y / *scale);
     const int64_t b = d.inst_bkt[inst] + ((int64_t)j << 1);
     const int64_t slot = b * (int64_t)d.cap_row;
@@ -1954,6 +2316,29 @@ __global__ void k_import(QwSimDev d, QwBufDev buf, const uint64_t *rowkey, const
     const int64_t slot = b * (int64_t)d.cap_row + pos;
     buf.key[slot] = local[i];
     store_amp<AmpT>(buf.amp, slot, amp[i]);
+}
+
+/* Branches received from other partitions (their S outputs for rows this
+ * partition owns) appended to the buckets of their rows. */
+template <typename AmpT>
+__global__ void k_part_inbox(QwSimDev d, QwBufDev buf, const QwPartEntry *e, int64_t count, int32_t *status)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const QwPartEntry x = e[i];
+        const uint64_t rk = x.rowkey;
+        const uint32_t inst = (uint32_t)(rk >> 40), jc = (uint32_t)((rk >> 20) & 0xfffffu);
+        const uint32_t j = (uint32_t)((rk >> 1) & 0x7ffffu), b1 = (uint32_t)(rk & 1);
+        const int64_t b = bucket_of(d, buf, inst, jc, j, b1, status);
+        if (b < 0) continue;
+        const int pos = atomicAdd(buf.count + b, 1);
+        if (pos >= d.cap_row) {
+            atomicOr(status, QW_ST_ROW_OVERFLOW);
+            continue;
+        }
+        const int64_t slot = b * (int64_t)d.cap_row + pos;
+        buf.key[slot] = x.local;
+        store_amp<AmpT>(buf.amp, slot, make_double2(x.re, x.im));
+    }
 }
 
 /* Every branch of instance inst (-1: all) to flat (row key, local key, amp). */
@@ -2137,6 +2522,65 @@ cudaError_t launch_step_t(const QwSimDev &d, const QwBufDev &in, const QwBufDev 
     return cudaGetLastError();
 }
 
+/* slot kernel: s in {8, 16, 32} */
+template <typename AmpT, int S, typename KeyT>
+int slot_grid_k(const QwSimDev &d)
+{
+    const size_t sm = (size_t)WARPS * slot_per_warp<AmpT, KeyT>(d);
+    cudaFuncSetAttribute(k_walk_slot<AmpT, S, KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_slot<AmpT, S, KeyT>, WARPS * 32, sm);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t groups = ((d.dense_buckets >> 1) + (32 / S) - 1) / (32 / S);
+    int64_t want = (groups + d.spill_slots + WARPS - 1) / WARPS;
+    int64_t g = (int64_t)per_sm * qw_sm_count();
+    if (want < g) g = want;
+    return (int)(g < 1 ? 1 : g);
+}
+
+template <typename AmpT, int S>
+int slot_grid_s(const QwSimDev &d)
+{
+    return key32_fits(d) ? slot_grid_k<AmpT, S, uint32_t>(d) : slot_grid_k<AmpT, S, uint64_t>(d);
+}
+
+template <typename AmpT>
+int slot_grid_t(const QwSimDev &d)
+{
+    if (d.s == 8) return slot_grid_s<AmpT, 8>(d);
+    if (d.s == 16) return slot_grid_s<AmpT, 16>(d);
+    return slot_grid_s<AmpT, 32>(d);
+}
+
+template <typename AmpT, int S>
+cudaError_t launch_slot_s(const QwSimDev &d, const QwBufDev &in, const QwBufDev &out, const QwBufDev &clr,
+                          const QwStepArgs &a, int grid, cudaStream_t st)
+{
+    if (key32_fits(d)) {
+        const size_t sm = (size_t)WARPS * slot_per_warp<AmpT, uint32_t>(d);
+        k_walk_slot<AmpT, S, uint32_t><<<grid, WARPS * 32, sm, st>>>(d, in, out, clr, a);
+    } else {
+        const size_t sm = (size_t)WARPS * slot_per_warp<AmpT, uint64_t>(d);
+        k_walk_slot<AmpT, S, uint64_t><<<grid, WARPS * 32, sm, st>>>(d, in, out, clr, a);
+    }
+    return cudaGetLastError();
+}
+
+template <typename AmpT>
+cudaError_t launch_slot_t(const QwSimDev &d, const QwBufDev &in, const QwBufDev &out, const QwBufDev &clr,
+                          const QwStepArgs &a, int grid, cudaStream_t st)
+{
+    if (d.s == 8) return launch_slot_s<AmpT, 8>(d, in, out, clr, a, grid, st);
+    if (d.s == 16) return launch_slot_s<AmpT, 16>(d, in, out, clr, a, grid, st);
+    return launch_slot_s<AmpT, 32>(d, in, out, clr, a, grid, st);
+}
+
+template <typename AmpT>
+size_t slot_smem_bytes(const QwSimDev &d)
+{
+    return (size_t)WARPS * (key32_fits(d) ? slot_per_warp<AmpT, uint32_t>(d) : slot_per_warp<AmpT, uint64_t>(d));
+}
+
 } // namespace
 
 /* SM count of the current device, cached per device (launch shapes follow
@@ -2155,8 +2599,14 @@ int qw_sm_count(void)
     return n;
 }
 
+int qw_slot_supported(const QwSimDev &d)
+{
+    return d.s == 8 || d.s == 16 || d.s == 32;
+}
+
 size_t qw_step_smem_bytes(const QwSimDev &d, int fp32, int mode)
 {
+    if (mode == QW_MODE_WALK_SLOT) return fp32 ? slot_smem_bytes<float2>(d) : slot_smem_bytes<double2>(d);
     if (mode == QW_MODE_WALK_LITERAL || mode == QW_MODE_T)
         return fp32 ? step_smem<float2, QW_MODE_T>(d) : step_smem<double2, QW_MODE_T>(d);
     return fp32 ? walk_smem_bytes<float2>(d) : walk_smem_bytes<double2>(d);
@@ -2164,6 +2614,7 @@ size_t qw_step_smem_bytes(const QwSimDev &d, int fp32, int mode)
 
 int qw_step_grid(const QwSimDev &d, int fp32, int mode)
 {
+    if (mode == QW_MODE_WALK_SLOT) return fp32 ? slot_grid_t<float2>(d) : slot_grid_t<double2>(d);
     if (mode == QW_MODE_WALK_FUSED)
         return fp32 ? walk_grid_t<float2, false, false>(d) : walk_grid_t<double2, false, false>(d);
     if (mode == QW_MODE_WALK_FUSED_PF)
@@ -2184,6 +2635,9 @@ cudaError_t qw_launch_step(const QwSimDev &d, const QwBufDev &in, const QwBufDev
                            const QwBufDev &clr, const QwStepArgs &a, int fp32, int grid,
                            cudaStream_t st)
 {
+    if (a.mode == QW_MODE_WALK_SLOT)
+        return fp32 ? launch_slot_t<float2>(d, in, out, clr, a, grid, st)
+                    : launch_slot_t<double2>(d, in, out, clr, a, grid, st);
     if (a.mode == QW_MODE_WALK_FUSED)
         return fp32 ? launch_walk_t<float2, false, false>(d, in, out, clr, a, grid, st)
                     : launch_walk_t<double2, false, false>(d, in, out, clr, a, grid, st);
@@ -2254,6 +2708,27 @@ cudaError_t qw_launch_count(const QwSimDev &d, const QwBufDev &buf, int inst,
 {
     const int grid = 4 * qw_sm_count();
     k_count<<<grid, 256, 0, st>>>(d, buf, inst, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t qw_launch_part_inbox(const QwSimDev &d, const QwBufDev &buf, const QwPartEntry *e, int64_t count, int fp32,
+                                 int32_t *status, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    int64_t grid = (count + 255) / 256;
+    if (grid > 8 * qw_sm_count()) grid = 8 * qw_sm_count();
+    if (fp32) k_part_inbox<float2><<<(unsigned)grid, 256, 0, st>>>(d, buf, e, count, status);
+    else k_part_inbox<double2><<<(unsigned)grid, 256, 0, st>>>(d, buf, e, count, status);
+    return cudaGetLastError();
+}
+
+cudaError_t qw_launch_regrow(const QwSimDev &d, const QwBufDev &from, int cap_old, uint64_t *key_new, void *amp_new,
+                             int fp32, cudaStream_t st)
+{
+    const int grid = 4 * qw_sm_count();
+    k_regrow<<<grid, 256, 0, st>>>(d.total_buckets, from.count, cap_old, d.cap_row, from.key,
+                                   static_cast<const unsigned char *>(from.amp), key_new,
+                                   static_cast<unsigned char *>(amp_new), fp32 ? 8 : 16);
     return cudaGetLastError();
 }
 

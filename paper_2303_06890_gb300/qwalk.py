@@ -29,8 +29,11 @@ EXPORTED = ("qw_sim_opts_default", "qw_sim_create", "qw_state_init", "qw_apply_w
             "qw_enqueue_walk_steps", "qw_sync",
             "qw_cks_coefficients", "qw_apply_qls", "qw_measure_register", "qw_state_size",
             "qw_state_export", "qw_sim_info", "qw_step_stats", "qw_launch_count", "qw_sim_destroy",
-            "qw_last_error", "qw_measure_register_noalloc", "qw_autotune", "qw_state_import")
+            "qw_last_error", "qw_measure_register_noalloc", "qw_autotune", "qw_state_import",
+            "qw_part_owner", "qw_part_outbox", "qw_part_inbox", "qw_part_norm", "qw_part_set_norm",
+            "qw_part_walk")
 MEASURE_NOALLOC_MAX_LEN = 65536
+WALK_VARIANTS = 6  # QW_WALK_VARIANTS
 
 
 class QwError(RuntimeError):
@@ -49,7 +52,9 @@ class Opts(ctypes.Structure):
                 ("prune_tau", ctypes.c_double), ("row_capacity", ctypes.c_int32),
                 ("warp_capacity", ctypes.c_int32), ("renorm", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("walk_variant", ctypes.c_int32),
-                ("graphs", ctypes.c_int32), ("spill_rows", ctypes.c_int32), ("rot_bits", ctypes.c_int32)]
+                ("graphs", ctypes.c_int32), ("spill_rows", ctypes.c_int32), ("rot_bits", ctypes.c_int32),
+                ("overflow_fallback", ctypes.c_int32), ("nparts", ctypes.c_int32), ("part", ctypes.c_int32),
+                ("outbox_capacity", ctypes.c_int64)]
 
 
 _lib = None
@@ -88,6 +93,15 @@ def load(build_if_missing: bool = True):
     lib.qw_step_stats.argtypes = [P, P, i32, i32]
     lib.qw_autotune.argtypes = [P, i32, P, P]
     lib.qw_state_import.argtypes = [P, i32, P, P, i64]
+    lib.qw_part_owner.argtypes = [i32, i32, i32, i32]
+    lib.qw_part_outbox.argtypes = [P, i32, P, i64, P]
+    lib.qw_part_inbox.argtypes = [P, P, i64]
+    lib.qw_part_norm.argtypes = [P, P]
+    lib.qw_part_set_norm.argtypes = [P, dbl]
+    lib.qw_part_walk.argtypes = [P, i32, i64]
+    for name in ("qw_part_owner", "qw_part_outbox", "qw_part_inbox", "qw_part_norm", "qw_part_set_norm",
+                 "qw_part_walk"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.qw_launch_count.argtypes = [P]
     lib.qw_launch_count.restype = i64
     lib.qw_sim_destroy.argtypes = [P]
@@ -178,7 +192,8 @@ class Sim:
     def __init__(self, matrices, s_pad: int = 0, precision: int = QW_FP64, fuse_reflection: bool = True,
                  prune_tau: float = 0.0, row_capacity: int = 0, warp_capacity: int = 0,
                  renorm: int = -1, stream: int | None = None, walk_variant: int = 0,
-                 graphs: bool = True, spill_rows: int = 0, rot_bits: int = 0):
+                 graphs: bool = True, spill_rows: int = 0, rot_bits: int = 0, overflow_fallback: bool = True,
+                 nparts: int = 1, part: int = 0, outbox_capacity: int = 0):
         lib = load()
         if not isinstance(matrices, (list, tuple)):
             matrices = [matrices]
@@ -203,6 +218,10 @@ class Sim:
         opts.graphs = int(bool(graphs))
         opts.spill_rows = int(spill_rows)
         opts.rot_bits = int(rot_bits)
+        opts.overflow_fallback = int(bool(overflow_fallback))
+        opts.nparts = int(nparts)
+        opts.part = int(part)
+        opts.outbox_capacity = int(outbox_capacity)
         h = ctypes.c_void_p()
         rc = lib.qw_sim_create(arr, len(matrices), ctypes.byref(opts), ctypes.byref(h))
         if rc:
@@ -243,9 +262,9 @@ class Sim:
         self._check(load().qw_apply_walk_step(self._h, int(nsteps)))
 
     def autotune(self, steps_per_candidate: int = 8) -> tuple[int, list[float]]:
-        """qw_autotune: (chosen variant, [us/step of variants 0..3])."""
+        """qw_autotune: (chosen variant, [us/step of variants 0..WALK_VARIANTS-1])."""
         choice = ctypes.c_int32()
-        us = np.zeros(4)
+        us = np.zeros(WALK_VARIANTS)
         self._check(load().qw_autotune(self._h, int(steps_per_candidate), ctypes.byref(choice), _p(us)))
         return int(choice.value), [float(v) for v in us]
 

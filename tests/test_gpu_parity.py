@@ -87,7 +87,7 @@ def test_walk_n1024_fp64_100_steps():
         compare(gpu_state(sim), oracle_state(o), TOL64)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_walk_n16384_fp64_full_size(variant):
     w = wl.walk_n16384()
     sim = _sim(w, walk_variant=variant)
@@ -118,16 +118,16 @@ def test_fp32_amp_n1024_100_steps():
 
 
 def test_fp32_amp_n16384_bench_config():
-    """The benchmarked configuration (N=16384, s=16, complex64 amplitudes with
-    FP64 merge, norm and renormalisation), 20 steps -- 4 of them by each
-    variant inside the autotuner, as bench.py runs it -- against the FP64
-    oracle."""
+    """The benchmarked configuration (N=16384, s=16, complex64 amplitudes), 20
+    steps -- 4 of them by each variant the autotuner tries, as bench.py runs
+    it -- against the FP64 oracle."""
     w = wl.walk_n16384()
     sim = _sim(w, precision=qwalk.QW_FP32_AMP)
     sim.state_init(w.b)
     choice, us = sim.autotune(4)
-    assert choice in (0, 1, 2, 3) and min(us) > 0
-    sim.apply_walk_step(w.steps - 16)
+    assert choice in range(qwalk.WALK_VARIANTS) and min(us[:4]) > 0
+    tried = sum(1 for v in us if v > 0)
+    sim.apply_walk_step(w.steps - 4 * tried)
     o = _oracle(w)
     o.apply("T")
     for _ in range(w.steps):
@@ -260,7 +260,7 @@ def test_capacity_overflow_keeps_last_clean_state(enqueue):
     and the state is the output of the last clean step, equal to the oracle's
     after that many steps."""
     w = wl.walk_n16()
-    sim = _sim(w, row_capacity=8, warp_capacity=8, walk_variant=2)
+    sim = _sim(w, row_capacity=8, warp_capacity=8, walk_variant=2, overflow_fallback=False)
     sim.state_init(w.b)
     o = _oracle(w)
     o.apply("T")
@@ -549,4 +549,230 @@ def test_complex64_with_64bit_in_kernel_keys_against_fp64_oracle():
         o.apply("W")
     st = compare_union_arrays(gpu_arrays(sim), oracle_arrays(o), 2e-6, 1e-5)
     print(f"complex64 N=20000 step 4: {st}")
+    sim.close()
+
+
+@pytest.mark.parametrize("n,smax,seed,band,attempts", [(48, 8, 2, 1, None), (100, 8, 3, 0, None),
+                                                       (130, 16, 5, 0, None), (300, 16, 8, 1, None),
+                                                       (90, 32, 9, 0, 3000), (70, 32, 10, 1, 3000)])
+def test_slot_kernel_matches_oracle(n, smax, seed, band, attempts):
+    """walk_variant 4 (one lane per QRAM slot, s = 8, 16, 32) against the
+    oracle, step by step: keys exactly, amplitudes to 1e-12."""
+    w = wl.small_random(n, smax, seed, band=band, attempts=attempts)
+    assert w.s in (8, 16, 32)
+    sim = _sim(w, walk_variant=4)
+    sim.state_init(w.b)
+    o = _oracle(w)
+    o.apply("T")
+    for _ in range(6):
+        sim.apply_walk_step(1)
+        o.apply("W")
+        compare(gpu_state(sim), oracle_state(o), TOL64)
+    sim.close()
+
+
+@pytest.mark.parametrize("wname", ["walk_n1024", "walk_n16384"])
+def test_slot_kernel_bitwise_equals_row_pipeline(wname):
+    """complex128 (no renormalisation): the slot kernel runs the same
+    operations in the same order as the row pipeline, so the states after
+    each step are bit for bit equal (compared in canonical key order)."""
+    w = getattr(wl, wname)()
+    a = _sim(w, walk_variant=4, graphs=False)
+    b = _sim(w, walk_variant=0, graphs=False)
+    for sim in (a, b):
+        sim.state_init(w.b)
+    for n in (1, 2, 3):
+        a.apply_walk_step(n)
+        b.apply_walk_step(n)
+        ka, va = a.state_export()
+        kb, vb = b.state_export()
+        assert np.array_equal(ka, kb), n
+        assert np.array_equal(va, vb), n
+    sa, sb = a.step_stats(), b.step_stats()
+    for k in ("in", "after_rdag", "after_hph", "out"):
+        assert sa[k] == sb[k], k
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("n,smax,seed", [(12, 8, 21), (40, 16, 22), (24, 8, 23)])
+def test_slot_kernel_on_garbage_subspace_states(n, smax, seed):
+    """Random states over the whole register space (rows with jc != 0, rows
+    j >= N, kc != 0, QRAM reads outside the row, groups with more extras than
+    the slot kernel lists): the slot kernel hands them to the row pipeline or
+    runs them as extras, and equals the oracle."""
+    w = wl.small_random(n, smax, seed)
+    assert w.s in (8, 16, 32), w.s
+    rng = np.random.default_rng(seed)
+    sim = _sim(w, walk_variant=4, row_capacity=128, warp_capacity=256, spill_rows=1024)
+    nb = sim.nb
+    keys = set()
+    while len(keys) < 600:
+        keys.add((int(rng.integers(0, 3)) * int(rng.integers(0, 2)), int(rng.integers(0, 1 << nb)),
+                  int(rng.integers(0, 2)), int(rng.integers(0, 3)) * int(rng.integers(0, 2)),
+                  int(rng.integers(0, 1 << nb)), int(rng.integers(0, 2))))
+    regs = np.array(sorted(keys), dtype=np.uint64)
+    amps = rng.standard_normal(len(regs)) + 1j * rng.standard_normal(len(regs))
+    amps /= np.linalg.norm(amps)
+    full = np.zeros((len(regs), 8), dtype=np.uint64)
+    full[:, :6] = regs
+    sim.state_import(sim.pack(full), amps)
+    o = oracle.Oracle(w.matrix, w.s)
+    o.set_state(regs, amps)
+    for _ in range(3):
+        sim.apply_walk_step(1)
+        o.apply("W")
+        compare(gpu_state(sim), oracle_state(o), TOL64)
+    sim.close()
+
+
+def test_slot_kernel_complex64_bench_config():
+    """The benchmarked workload in complex64 through the slot kernel, 20
+    steps, against the FP64 oracle within the reduced-precision bounds."""
+    w = wl.walk_n16384()
+    sim = _sim(w, precision=qwalk.QW_FP32_AMP, walk_variant=4)
+    sim.state_init(w.b)
+    sim.apply_walk_step(w.steps)
+    o = _oracle(w)
+    o.apply("T")
+    for _ in range(w.steps):
+        o.apply("W")
+    from parity import compare_union_arrays, gpu_arrays, oracle_arrays
+    st = compare_union_arrays(gpu_arrays(sim), oracle_arrays(o), 2e-6, 1e-5)
+    print(f"slot kernel complex64 N=16384 step 20: {st}")
+    sim.close()
+
+
+def _clustered_matrix():
+    """N = 40, s = 8: rows 10..15 form a full block (6 entries each) and pad
+    their two free slots onto the same columns 16 and 17 (the padding rule
+    takes the first free columns after j), so rows 16 and 17 receive more
+    branches than the others; the rest is a tridiagonal band."""
+    from test_oracle_pins import dense_to_matrix
+    n = 40
+    rng = np.random.default_rng(77)
+    a = np.zeros((n, n))
+    for j in range(n):
+        a[j, j] = rng.uniform(0.2, 1.0)
+        if j + 1 < n and not (10 <= j < 16 and 10 <= j + 1 < 16):
+            a[j, j + 1] = a[j + 1, j] = rng.uniform(-1, 1)
+    for i in range(10, 16):
+        for j in range(i + 1, 16):
+            a[i, j] = a[j, i] = rng.uniform(-1, 1)
+    m = dense_to_matrix(a)
+    b = rng.standard_normal(n)
+    return wl.Workload("clustered_n40", m, b / np.linalg.norm(b), s=8, steps=6, cond=0, kappa=0)
+
+
+@pytest.mark.parametrize("variant", [0, 3, 4])
+def test_overflowing_rows_run_on_the_flat_path(variant):
+    """A row capacity below what the clustered rows need: the steps that
+    overflow are run again on the flat path (global radix sort by key,
+    per-group transform, compaction), the row buckets grow, and every step
+    equals the oracle (keys exactly, amplitudes to 1e-12)."""
+    w = _clustered_matrix()
+    sim = _sim(w, row_capacity=6, walk_variant=variant)
+    sim.state_init(w.b)
+    o = _oracle(w)
+    o.apply("T")
+    for _ in range(w.steps):
+        sim.apply_walk_step(1)
+        o.apply("W")
+        compare(gpu_state(sim), oracle_state(o), TOL64)
+    # several steps in one call, enqueued and synchronised once
+    sim.state_init(w.b)
+    sim.enqueue_walk_steps(5)
+    sim.sync()
+    o = _oracle(w)
+    o.apply("T")
+    for _ in range(5):
+        o.apply("W")
+    compare(gpu_state(sim), oracle_state(o), TOL64)
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", [qwalk.QW_FP64, qwalk.QW_FP32_AMP])
+@pytest.mark.parametrize("maker", [wl.walk_n16, lambda: wl.small_random(100, 8, 3),
+                                   lambda: wl.small_random(130, 16, 5)])
+def test_flat_path_matches_oracle(maker, precision):
+    """walk_variant 5, the paper's schedule on one globally sorted list:
+    complex128 equals the oracle step by step (keys exactly, 1e-12); complex64
+    (FP64 arithmetic on the flat path, FP32 storage) within the
+    reduced-precision bounds."""
+    w = maker()
+    sim = _sim(w, walk_variant=5, precision=precision)
+    sim.state_init(w.b)
+    o = _oracle(w)
+    o.apply("T")
+    for _ in range(4):
+        sim.apply_walk_step(1)
+        o.apply("W")
+        if precision == qwalk.QW_FP64:
+            compare(gpu_state(sim), oracle_state(o), TOL64)
+        else:
+            compare_union(gpu_state(sim), oracle_state(o), 2e-6, 1e-5)
+    st = sim.step_stats()
+    assert st["steps"] == 4 and st["after_h1"] > 0
+    sim.close()
+
+
+def test_flat_path_on_garbage_states_and_qls():
+    """The flat path on a random state over the whole register space, and the
+    CKS read-out through it (the flag-0 block after T~^dag's H)."""
+    w = wl.small_random(12, 4, 17)
+    rng = np.random.default_rng(5)
+    sim = _sim(w, walk_variant=5, spill_rows=1024)
+    nb = sim.nb
+    keys = set()
+    while len(keys) < 300:
+        keys.add((int(rng.integers(0, 4)), int(rng.integers(0, 1 << nb)), int(rng.integers(0, 2)),
+                  int(rng.integers(0, 4)), int(rng.integers(0, 1 << nb)), int(rng.integers(0, 2))))
+    regs = np.array(sorted(keys), dtype=np.uint64)
+    amps = rng.standard_normal(len(regs)) + 1j * rng.standard_normal(len(regs))
+    amps /= np.linalg.norm(amps)
+    full = np.zeros((len(regs), 8), dtype=np.uint64)
+    full[:, :6] = regs
+    sim.state_import(sim.pack(full), amps)
+    o = oracle.Oracle(w.matrix, w.s)
+    o.set_state(regs, amps)
+    for _ in range(3):
+        sim.apply_walk_step(1)
+        o.apply("W")
+        compare(gpu_state(sim), oracle_state(o), TOL64)
+    sim.close()
+    w = wl.walk_n16()
+    b_int, j0 = dense.cks_parameters(w.kappa, 1e-3)
+    coeffs = dense.cks_coefficients(b_int, j0)[:40]
+    flat = _sim(w, walk_variant=5)
+    flat.state_init(w.b)
+    y, p = flat.apply_qls(coeffs)
+    ref = _sim(w)
+    ref.state_init(w.b)
+    y2, p2 = ref.apply_qls(coeffs)
+    assert np.abs(y - y2).max() < 1e-12 and np.abs(p - p2).max() < 1e-12
+
+
+def test_import_grows_row_capacity():
+    """qw_state_import of a state whose rows exceed row_capacity grows the
+    buckets (overflow_fallback) and the walk continues equal to the oracle."""
+    w = wl.small_random(24, 8, 23)
+    rng = np.random.default_rng(3)
+    sim = _sim(w, row_capacity=8)
+    nb = sim.nb
+    keys = set()
+    while len(keys) < 60:  # 60 branches in one row (jc = 0, j = 5, b1 = 0)
+        keys.add((0, 5, 0, 0, int(rng.integers(0, 1 << nb)), int(rng.integers(0, 2))))
+    regs = np.array(sorted(keys), dtype=np.uint64)
+    amps = rng.standard_normal(len(regs)) + 0j
+    amps /= np.linalg.norm(amps)
+    full = np.zeros((len(regs), 8), dtype=np.uint64)
+    full[:, :6] = regs
+    sim.state_import(sim.pack(full), amps)
+    o = oracle.Oracle(w.matrix, w.s)
+    o.set_state(regs, amps)
+    compare(gpu_state(sim), oracle_state(o), 0.0)
+    for _ in range(2):
+        sim.apply_walk_step(1)
+        o.apply("W")
+        compare(gpu_state(sim), oracle_state(o), TOL64)
     sim.close()
