@@ -55,6 +55,10 @@ def parse_args():
     p.add_argument("--no-qls", action="store_true")
     p.add_argument("--no-mmax", action="store_true")
     p.add_argument("--no-configs", action="store_true", help="skip the N=16 and N=1024 walk legs")
+    p.add_argument("--no-partition", action="store_true", help="skip the row-partitioned walk leg")
+    p.add_argument("--shard", action="store_true",
+                   help="under torchrun: one N=16384 walk split in row blocks over the ranks (strong scaling), "
+                        "S's sends exchanged by an all-to-all each step, instead of replicas")
     return p.parse_args()
 
 
@@ -244,6 +248,41 @@ def oracle_walk(w, steps: int):
     return o, dt
 
 
+def run_sharded(args, rank, world, local_rank):
+    """--shard under torchrun: one N = 16384 walk split in row blocks over the
+    ranks (one simulator per rank), S's sends exchanged each step by an
+    all-to-all (paper_2303_06890_gb300.partition.walk_partitioned over NCCL);
+    the metric is walk steps/s of the one walk (strong scaling)."""
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_2303_06890_gb300 import partition, qwalk, ranks
+    from paper_2303_06890_gb300 import workloads as wl
+    w = wl.walk_n16384()
+    sim = qwalk.Sim(w.matrix, s_pad=w.s, precision=qwalk.QW_FP32_AMP, walk_variant=4, nparts=world, part=rank)
+    sim.state_init(w.b)
+    eng = partition.SimEngine(sim, world, rank)
+    partition.walk_partitioned(eng, args.warmup)
+    torch.cuda.synchronize()
+    ranks.barrier()
+    t0 = time.perf_counter()
+    partition.walk_partitioned(eng, args.steps)
+    torch.cuda.synchronize()
+    ranks.barrier()
+    t = ranks.max_over_ranks(time.perf_counter() - t0, device="cuda")
+    sim.close()
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "value": args.steps / t, "unit": UNIT, "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps,
+                          "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+                          "data": "synthetic",
+                          "config": {"workload": w.name, "n": w.n, "s": w.s, "parallelism": f"row blocks x{world}",
+                                     "l2": "not flushed (host-clock timing of whole steps with their exchange)"}}),
+              flush=True)
+    dist.destroy_process_group()
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -340,6 +379,7 @@ def run_ours(args, rank, world, local_rank):
                                                        world, rank)
 
     table1 = None if args.no_table1 else table1_leg(torch, barrier, max_over_ranks)
+    part = None if (args.no_partition or world > 1) else partition_leg(torch)
     qls = None if args.no_qls else qls_leg(torch, barrier, max_over_ranks)
     mmax = None if args.no_mmax else mmax_leg()
 
@@ -402,6 +442,8 @@ def run_ours(args, rank, world, local_rank):
         line["qls"] = qls
     if mmax is not None:
         line["mmax"] = mmax
+    if part is not None:
+        line["partitioned"] = part
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if err is not None:
@@ -650,6 +692,36 @@ def qls_leg(torch, barrier, max_over_ranks) -> dict:
     return out
 
 
+def partition_leg(torch, steps: int = 24) -> dict:
+    """The N = 16384 walk split in row blocks among P simulators of this
+    process on one device (qw_part_walk: each step runs every part's step
+    kernel, then moves S's sends between the parts by cudaMemcpyAsync and
+    appends them; one synchronisation per step), complex64: walk steps/s of
+    the whole walk and the branches exchanged per step.  An emulation of the
+    multi-GPU partition on one device: the parts share its SMs."""
+    from paper_2303_06890_gb300 import partition, qwalk
+    from paper_2303_06890_gb300 import workloads as wl
+    w = wl.walk_n16384()
+    out = {"workload": w.name, "precision": "complex64", "steps": steps}
+    for nparts in (2, 4):
+        sims = [qwalk.Sim(w.matrix, s_pad=w.s, precision=qwalk.QW_FP32_AMP, walk_variant=4, nparts=nparts, part=p)
+                for p in range(nparts)]
+        for sim in sims:
+            sim.state_init(w.b)
+        partition.walk_in_process(sims, 2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        partition.walk_in_process(sims, steps)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        sizes = [sim.state_size() for sim in sims]
+        for sim in sims:
+            sim.close()
+        out[f"p{nparts}"] = {"walk_steps_per_s": steps / dt, "ms_per_step": 1000.0 * dt / steps,
+                             "branches_per_part": sizes}
+    return out
+
+
 def configs_leg(torch) -> dict:
     """The two small walk workloads: N = 16 (10 steps, complex128) and N = 1024
     (100 steps, complex128 and complex64).  Per workload and precision: the
@@ -714,6 +786,9 @@ def main():
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.shard and world > 1:
+        run_sharded(args, rank, world, local_rank)
         return
     run_ours(args, rank, world, local_rank)
 

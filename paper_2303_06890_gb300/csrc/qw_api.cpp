@@ -35,7 +35,7 @@ struct Scalars {
     unsigned long long stats[QW_NSTAT];
     int64_t qls_j; /* current QLS term */
     unsigned int deferred_ctr; /* slot kernel: units left to its last block */
-    unsigned int pad2;
+    unsigned int work_ctr;     /* slot kernel: groups claimed */
 };
 
 /* the head of Scalars the host reads at every synchronising call */
@@ -633,6 +633,7 @@ static QwStepArgs step_args(qw_sim *sim, int mode)
     a.qls_j = &sim->sc->qls_j;
     a.deferred = sim->deferred;
     a.deferred_ctr = &sim->sc->deferred_ctr;
+    a.work_ctr = &sim->sc->work_ctr;
     return a;
 }
 

@@ -124,6 +124,8 @@ struct QwStepArgs {
     int32_t *deferred;          /* slot kernel: units left to the row pipeline (dense unit u,
                                    or 0x80000000 | garbage-row slot), run by the last block */
     unsigned int *deferred_ctr; /* entries in deferred (reset by the last block) */
+    unsigned int *work_ctr;     /* slot kernel: groups claimed beyond each warp's first
+                                   (reset by the last block) */
 };
 
 /* launchers (qw_kernels.cu); all return cudaGetLastError() of the launch */

@@ -1736,19 +1736,24 @@ __device__ __forceinline__ bool amp_nonzero(AmpT a)
     return a.x != 0 || a.y != 0;
 }
 
-/* S for up to two kept outputs of a lane: (kc_out, k_out, b2 = 0 / 1) of row
- * (jc = 0, j, b1) go to row (kc_out, k_out, b2) with local registers
- * (kc, k, b2) = (0, j, b1); both slot claims are in flight before the stores. */
+/* S for up to two kept outputs of a lane, in two halves so that a caller
+ * can have the slot claims of several lanes' outputs in flight together:
+ * slot_route finds the buckets of (kc_out, k_out, b2 = 0 / 1), the new rows
+ * of row (jc = 0, j, b1)'s outputs (-1: nothing to store here; a branch whose
+ * new row another partition owns is sent to it), slot_put stores a branch
+ * with local registers (kc, k, b2) = (0, j, b1) at the claimed position. */
 template <typename AmpT>
-__device__ __forceinline__ void slot_emit(const QwSimDev &d, const QwBufDev &out, const SlotUnit &U, uint32_t k_out,
-                                          uint32_t kc_out, uint32_t b1, AmpT r0, AmpT r1, bool e0, bool e1,
-                                          int32_t *status, typename Amp<AmpT>::Norm &nrm)
+__device__ __forceinline__ void slot_route(const QwSimDev &d, const QwBufDev &out, const SlotUnit &U, uint32_t k_out,
+                                           uint32_t kc_out, uint32_t b1, AmpT r0, AmpT r1, bool e0, bool e1,
+                                           int32_t *status, typename Amp<AmpT>::Norm &nrm, int64_t &b0, int64_t &bb1)
 {
-    int64_t b0 = -1, bb1 = -1;
-    const uint64_t local = (uint64_t)b1 | ((uint64_t)U.j << 1);
+    b0 = -1;
+    bb1 = -1;
+    if (!e0 && !e1) return;
     if (d.nparts > 1) { /* the new row (kc_out, k_out) is another partition's */
         const int own = qw_part_owner_of(d, kc_out, k_out);
         if (own != d.part) {
+            const uint64_t local = (uint64_t)b1 | ((uint64_t)U.j << 1);
             if (e0) {
                 part_send(d, own, qw_rowkey(U.inst, kc_out, k_out, 0), local, Amp<AmpT>::to_d(r0), status);
                 nrm.add(r0);
@@ -1774,28 +1779,55 @@ __device__ __forceinline__ void slot_emit(const QwSimDev &d, const QwBufDev &out
         if (e0) b0 = bucket_of(d, out, U.inst, kc_out, k_out, 0, status);
         if (e1) bb1 = bucket_of(d, out, U.inst, kc_out, k_out, 1, status);
     }
-    const int p0 = b0 >= 0 ? atomicAdd(out.count + b0, 1) : 0;
-    const int p1 = bb1 >= 0 ? atomicAdd(out.count + bb1, 1) : 0;
-    if (b0 >= 0) {
-        if (p0 < d.cap_row) {
-            const int64_t sl = b0 * (int64_t)d.cap_row + p0;
-            out.key[sl] = local;
-            static_cast<AmpT *>(out.amp)[sl] = r0;
-            nrm.add(r0);
-        } else {
-            atomicOr(status, QW_ST_ROW_OVERFLOW);
-        }
+}
+
+template <typename AmpT>
+__device__ __forceinline__ void slot_put(const QwSimDev &d, const QwBufDev &out, int64_t b, int p, uint64_t local,
+                                         AmpT r, int32_t *status, typename Amp<AmpT>::Norm &nrm)
+{
+    if (b < 0) return;
+    if (p < d.cap_row) {
+        const int64_t sl = b * (int64_t)d.cap_row + p;
+        out.key[sl] = local;
+        static_cast<AmpT *>(out.amp)[sl] = r;
+        nrm.add(r);
+    } else {
+        atomicOr(status, QW_ST_ROW_OVERFLOW);
     }
-    if (bb1 >= 0) {
-        if (p1 < d.cap_row) {
-            const int64_t sl = bb1 * (int64_t)d.cap_row + p1;
-            out.key[sl] = local;
-            static_cast<AmpT *>(out.amp)[sl] = r1;
-            nrm.add(r1);
-        } else {
-            atomicOr(status, QW_ST_ROW_OVERFLOW);
-        }
-    }
+}
+
+/* One lane's kept outputs waiting for S: the buckets of their new rows, the
+ * local key and the amplitudes. */
+template <typename AmpT> struct SlotOut {
+    int64_t b0, b1;
+    uint64_t local;
+    AmpT r0, r1;
+};
+
+template <typename AmpT>
+__device__ __forceinline__ void slot_out(const QwSimDev &d, const QwBufDev &out, const SlotUnit &U, uint32_t k_out,
+                                         uint32_t kc_out, uint32_t b1, AmpT r0, AmpT r1, bool e0, bool e1,
+                                         int32_t *status, typename Amp<AmpT>::Norm &nrm, SlotOut<AmpT> &o)
+{
+    slot_route<AmpT>(d, out, U, k_out, kc_out, b1, r0, r1, e0, e1, status, nrm, o.b0, o.b1);
+    o.local = (uint64_t)b1 | ((uint64_t)U.j << 1);
+    o.r0 = r0;
+    o.r1 = r1;
+}
+
+/* claims of two lanes' worth of outputs in flight together, then the stores */
+template <typename AmpT>
+__device__ __forceinline__ void slot_store2(const QwSimDev &d, const QwBufDev &out, const SlotOut<AmpT> &x,
+                                            const SlotOut<AmpT> &y, int32_t *status, typename Amp<AmpT>::Norm &nrm)
+{
+    const int px0 = x.b0 >= 0 ? atomicAdd(out.count + x.b0, 1) : 0;
+    const int px1 = x.b1 >= 0 ? atomicAdd(out.count + x.b1, 1) : 0;
+    const int py0 = y.b0 >= 0 ? atomicAdd(out.count + y.b0, 1) : 0;
+    const int py1 = y.b1 >= 0 ? atomicAdd(out.count + y.b1, 1) : 0;
+    slot_put<AmpT>(d, out, x.b0, px0, x.local, x.r0, status, nrm);
+    slot_put<AmpT>(d, out, x.b1, px1, x.local, x.r1, status, nrm);
+    slot_put<AmpT>(d, out, y.b0, py0, y.local, y.r0, status, nrm);
+    slot_put<AmpT>(d, out, y.b1, py1, y.local, y.r1, status, nrm);
 }
 
 template <typename AmpT, int S, typename KeyT>
@@ -1847,12 +1879,29 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_slot(QwSimDev d, QwBufDe
         }
     };
 
-    for (int64_t g = gw; g < ngroups; g += nwarps) {
+    /* groups: each warp's first is its own index.  One instance: then every
+       nwarps-th group (the groups are alike), the next group's counts read
+       one group ahead.  Several instances (groups of very different sizes,
+       empty ones past each N): the rest are claimed from a counter, the claim
+       issued a group ahead so that its latency hides behind the work */
+    const bool dyn = d.ninst > 1;
+    unsigned claim_raw = 0;
+    auto claim = [&]() {
+        if (dyn && lane == 0) claim_raw = atomicAdd(a.work_ctr, 1u);
+    };
+    auto group_counts = [&](int64_t gg) {
+        const int64_t uu0 = gg * RPP;
+        return (gg < ngroups && lane < NBK && uu0 + (lane >> 1) < d2) ? min(in.count[2 * uu0 + lane], d.cap_row) : 0;
+    };
+    int64_t g = gw;
+    int cnt_next = group_counts(g);
+    if (g < ngroups) claim();
+    for (; g < ngroups; g = dyn ? nwarps + (int64_t)__shfl_sync(FULL, claim_raw, 0) : g + nwarps, claim()) {
         const int64_t u0 = g * RPP;
         /* counts of the group's buckets 2 u0 .. 2 u0 + NBK - 1 and their
            exclusive offsets in the group's branch order */
-        int cnt = 0;
-        if (lane < NBK && u0 + (lane >> 1) < d2) cnt = min(in.count[2 * u0 + lane], d.cap_row);
+        const int cnt = dyn ? group_counts(g) : cnt_next;
+        if (!dyn) cnt_next = group_counts(g + nwarps);
         int incl = cnt;
 #pragma unroll
         for (int o = 1; o < NBK; o <<= 1) {
@@ -2014,7 +2063,10 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_slot(QwSimDev d, QwBufDe
             Amp<AmpT>::rot(rv, val, false, sneg, d0 ? h0 : zero, c1 ? Amp<AmpT>::neg(o1) : zero, r0, r1);
             const bool e0 = Amp<AmpT>::keep(d, r0), e1 = Amp<AmpT>::keep(d, r1);
             st.out += __popc(__ballot_sync(FULL, e0)) + __popc(__ballot_sync(FULL, e1));
-            slot_emit<AmpT>(d, out, U, col, 0u, 0u, r0, r1, e0, e1, a.status, nrm); /* S */
+            SlotOut<AmpT> outA, none; /* S */
+            slot_out<AmpT>(d, out, U, col, 0u, 0u, r0, r1, e0, e1, a.status, nrm, outA);
+            none.b0 = none.b1 = -1;
+            slot_store2<AmpT>(d, out, outA, none, a.status, nrm);
         }
 
         /* ---- pass B: list the b1 = 1 slots and the extras' pairs ---- */
@@ -2107,7 +2159,10 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_slot(QwSimDev d, QwBufDe
                            r0, r1); /* R */
             const bool e0 = act && Amp<AmpT>::keep(d, r0), e1 = act && Amp<AmpT>::keep(d, r1);
             st.out += __popc(__ballot_sync(FULL, e0)) + __popc(__ballot_sync(FULL, e1));
-            if (act) slot_emit<AmpT>(d, out, units[ut], k_out, kc_out, b1, r0, r1, e0, e1, a.status, nrm); /* S */
+            SlotOut<AmpT> outB, none;
+            slot_out<AmpT>(d, out, units[ut], k_out, kc_out, b1, r0, r1, e0, e1, a.status, nrm, outB); /* S */
+            none.b0 = none.b1 = -1;
+            slot_store2<AmpT>(d, out, outB, none, a.status, nrm);
         }
         __syncwarp();
     }
@@ -2179,6 +2234,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_slot(QwSimDev d, QwBufDe
             if (a.stats) a.stats[QW_STAT_STEPS] += 1;
         }
         *a.deferred_ctr = 0u;
+        *a.work_ctr = 0u;
         *a.done_ctr = 0u;
     }
 }
