@@ -36,7 +36,8 @@ sys.path.insert(0, ROOT)
 METRIC = "walk steps/s and sparse-state entries/s at n=16384, FP32 vs FP64; HBM GB/s vs peak"
 UNIT = "walk steps/s"
 PROFILE = os.path.join(ROOT, "profiles", "k_walk_n16384_s16.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_2303_06890_gb300", "csrc", "qw_kernels.cu")
+PROFILE_SLOT = os.path.join(ROOT, "profiles", "k_walk_slot_n16384_s16.md")
+KERNEL_SRC = [os.path.join(ROOT, "paper_2303_06890_gb300", "csrc", f) for f in ("qw_kernels.cu", "qw_device.cuh")]
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -56,6 +57,8 @@ def parse_args():
     p.add_argument("--no-mmax", action="store_true")
     p.add_argument("--no-configs", action="store_true", help="skip the N=16 and N=1024 walk legs")
     p.add_argument("--no-partition", action="store_true", help="skip the row-partitioned walk leg")
+    p.add_argument("--variant", type=int, default=-1,
+                   help="step-kernel variant for both precisions instead of the autotuner's choice (profiling)")
     p.add_argument("--shard", action="store_true",
                    help="under torchrun: one N=16384 walk split in row blocks over the ranks (strong scaling), "
                         "S's sends exchanged by an all-to-all each step, instead of replicas")
@@ -77,18 +80,22 @@ def peaks():
 
 
 def kernel_hash() -> str:
-    with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for path in KERNEL_SRC:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 VARIANTS = ("rows", "rows, pipelined", "segments", "segments, pipelined", "slot lanes")
 
 
-def profiled_traffic(precision: str):
-    """DRAM bytes per launch of k_walk from the committed ncu summary, or None
-    when the kernel source changed since the capture."""
+def profiled_traffic(precision: str, variant: int = 0):
+    """DRAM bytes per launch of the step kernel (k_walk_slot for variant 4,
+    else k_walk) from the committed ncu summary, or None when the kernel
+    source changed since the capture."""
     try:
-        text = open(PROFILE).read()
+        text = open(PROFILE_SLOT if variant == 4 else PROFILE).read()
     except OSError:
         return None
     vals = {}
@@ -307,9 +314,19 @@ def run_ours(args, rank, world, local_rank):
         return ranks.max_over_ranks(x, device="cuda")
 
     # --- the benchmarked path: complex64 amplitudes, FP64 merge/norm/renorm ---
-    sim = qwalk.Sim(w.matrix, s_pad=w.s, precision=qwalk.QW_FP32_AMP)
-    sim.state_init(w.b, apply_T=True)
-    variant, tune_us = sim.autotune(max(2, args.warmup // 2))  # warm-up steps, all variants
+    def tuned(precision):
+        """a simulator of the workload in T~|b~> with the autotuner's (or the
+        requested) step-kernel variant"""
+        if args.variant >= 0:
+            sm = qwalk.Sim(w.matrix, s_pad=w.s, precision=precision, walk_variant=args.variant)
+            sm.state_init(w.b, apply_T=True)
+            return sm, args.variant, []
+        sm = qwalk.Sim(w.matrix, s_pad=w.s, precision=precision)
+        sm.state_init(w.b, apply_T=True)
+        v, us = sm.autotune(max(2, args.warmup // 2))  # warm-up steps, all variants
+        return sm, v, us
+
+    sim, variant, tune_us = tuned(qwalk.QW_FP32_AMP)
     sim.apply_walk_step(args.warmup)
     sim.step_stats(reset=True)
     launches0 = sim.launch_count()
@@ -328,14 +345,12 @@ def run_ours(args, rank, world, local_rank):
     mean_step_s = statistics.mean(per_step) / 1000.0
     peak, peak_kind = peaks()
     achieved = b_alg / mean_step_s / 1e9
-    traffic = profiled_traffic("fp32")
+    traffic = profiled_traffic("fp32", variant)
     live_entries = stats["out"] / max(1, stats["steps"])
     sim.close()
 
     # --- the plain FP64 path on the same workload ---
-    sim64 = qwalk.Sim(w.matrix, s_pad=w.s, precision=qwalk.QW_FP64)
-    sim64.state_init(w.b, apply_T=True)
-    variant64, tune64 = sim64.autotune(max(2, args.warmup // 2))
+    sim64, variant64, tune64 = tuned(qwalk.QW_FP64)
     sim64.apply_walk_step(args.warmup)
     sim64.step_stats(reset=True)
     barrier()
@@ -349,7 +364,7 @@ def run_ours(args, rank, world, local_rank):
             "ms_per_step": 1000.0 * t64 / args.fp64_steps,
             "entries_per_s": world * (stats64["in"] + stats64["after_rdag"] + stats64["after_hph"]) / t64,
             "achieved_gbs": b_alg64 / statistics.mean(per64) * 1000.0 / 1e9,
-            "traffic": profiled_traffic("fp64")}
+            "traffic": profiled_traffic("fp64", variant64)}
     sim64.close()
 
     # --- end to end through the C ABI with host buffers ---

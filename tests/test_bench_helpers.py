@@ -29,14 +29,14 @@ def test_algorithmic_bytes_of_a_step():
 
 
 def test_profiled_traffic_follows_the_kernel_source_hash(tmp_path, monkeypatch):
-    text = open(bench.PROFILE).read()
-    committed = bench.profiled_traffic("fp32")
+    text = open(bench.PROFILE_SLOT).read()
+    committed = bench.profiled_traffic("fp32", 4)
     if f"`{bench.kernel_hash()}`" in text:
         assert committed is not None and committed > 0
     stale = tmp_path / "stale.md"
     stale.write_text(text.replace("kernel_source_sha256_16: `", "kernel_source_sha256_16: `0"))
-    monkeypatch.setattr(bench, "PROFILE", str(stale))
-    assert bench.profiled_traffic("fp32") is None
+    monkeypatch.setattr(bench, "PROFILE_SLOT", str(stale))
+    assert bench.profiled_traffic("fp32", 4) is None
 
 
 def test_state_error_over_the_union_of_keys():
