@@ -1373,17 +1373,18 @@ template <typename KeyT> struct WalkItem {
     bool valid;
 };
 
-/* Branch counters of one warp (QW_STAT_*), added to the step's at its end. */
+/* Branch counters of one warp (QW_STAT_*), added to the step's at its end
+ * (32 bits per warp: a warp sees far fewer than 2^32 branches in a step). */
 struct WalkStats {
-    unsigned long long rows = 0, in = 0, rdag = 0, hph = 0, out = 0;
+    unsigned int rows = 0, in = 0, rdag = 0, hph = 0, out = 0;
     __device__ void flush(const QwStepArgs &a) const
     {
         if (a.stats && lane_id() == 0 && rows) {
-            atomicAdd(a.stats + QW_STAT_ROWS, rows);
-            atomicAdd(a.stats + QW_STAT_IN, in);
-            atomicAdd(a.stats + QW_STAT_RDAG, rdag);
-            atomicAdd(a.stats + QW_STAT_HPH, hph);
-            atomicAdd(a.stats + QW_STAT_OUT, out);
+            atomicAdd(a.stats + QW_STAT_ROWS, (unsigned long long)rows);
+            atomicAdd(a.stats + QW_STAT_IN, (unsigned long long)in);
+            atomicAdd(a.stats + QW_STAT_RDAG, (unsigned long long)rdag);
+            atomicAdd(a.stats + QW_STAT_HPH, (unsigned long long)hph);
+            atomicAdd(a.stats + QW_STAT_OUT, (unsigned long long)out);
         }
     }
 };
@@ -1659,6 +1660,29 @@ __global__ void __launch_bounds__(WARPS * 32, PF ? 3 : 4) k_walk(QwSimDev d, QwB
  * go through the row pipeline. */
 constexpr int kSlotExtras = 32; /* extras list of a group */
 constexpr int kSlotItems = 64;  /* pass B items: 32 slots + 32 extra pairs */
+constexpr int kSlotStage = 128; /* a group's first branches, copied to shared memory ahead */
+
+/* Asynchronous copies global -> shared (cp.async, sm_80 and later): the
+ * branch loads of a group are all in flight together, and land without
+ * passing through registers. */
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+template <typename AmpT> __device__ __forceinline__ void cp_async_amp(AmpT *dst, const AmpT *src);
+template <> __device__ __forceinline__ void cp_async_amp<float2>(float2 *dst, const float2 *src) { cp_async8(dst, src); }
+template <> __device__ __forceinline__ void cp_async_amp<double2>(double2 *dst, const double2 *src)
+{
+    cp_async16(dst, src);
+}
 
 struct SlotUnit {
     uint32_t j, inst, n;
@@ -1667,7 +1691,7 @@ struct SlotUnit {
 };
 
 struct SlotLayout {
-    size_t ws, rot, ta, tb, ek, ea, im, ia, unit, per_warp;
+    size_t ws, rot, ta, tb, ek, ea, im, ia, unit, sk, sa, per_warp;
 };
 
 template <typename AmpT>
@@ -1687,6 +1711,8 @@ __host__ __device__ inline SlotLayout slot_layout()
     QW_TAKE(im, kSlotItems * sizeof(uint16_t));
     QW_TAKE(ia, 2 * kSlotItems * sizeof(AmpT));
     QW_TAKE(unit, 8 * sizeof(SlotUnit));
+    QW_TAKE(sk, kSlotStage * sizeof(uint64_t));
+    QW_TAKE(sa, kSlotStage * sizeof(AmpT));
 #undef QW_TAKE
     o.per_warp = p;
     return o;
@@ -1853,6 +1879,8 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_slot(QwSimDev d, QwBufDe
     uint16_t *im = reinterpret_cast<uint16_t *>(base + sl.im);
     AmpT *ia = reinterpret_cast<AmpT *>(base + sl.ia);
     SlotUnit *units = reinterpret_cast<SlotUnit *>(base + sl.unit);
+    uint64_t *sk = reinterpret_cast<uint64_t *>(base + sl.sk);
+    AmpT *sa = reinterpret_cast<AmpT *>(base + sl.sa);
 
     const bool skip = step_begin(d, clr, a);
     const bool rescale = a.scale_in != nullptr;
@@ -1948,6 +1976,31 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_slot(QwSimDev d, QwBufDe
             }
             continue;
         }
+        int ex[NBK];
+#pragma unroll
+        for (int q = 0; q < NBK; ++q) ex[q] = __shfl_sync(FULL, excl, q);
+        /* bucket of the group's t-th branch and its position there */
+        auto locate = [&](int t, int &bi, int64_t &at) {
+            int start = 0;
+            bi = 0;
+#pragma unroll
+            for (int q = 1; q < NBK; ++q) {
+                const bool ge = t >= ex[q];
+                bi += ge ? 1 : 0;
+                start = ge ? ex[q] : start;
+            }
+            at = (2 * u0 + bi) * (int64_t)d.cap_row + (t - start);
+        };
+        /* the group's first kSlotStage branches to shared memory, all in flight
+           while the QRAM rows are staged */
+        for (int t = lane; t < total && t < kSlotStage; t += 32) {
+            int bi;
+            int64_t at;
+            locate(t, bi, at);
+            cp_async8(sk + t, in.key + at);
+            cp_async_amp<AmpT>(sa + t, amp_in + at);
+        }
+        cp_async_commit();
         /* stage the group's QRAM rows (contiguous in the image for one
            instance): lane t holds slot l = t % S of the row of unit t / S;
            a slot whose element is 0 rotates by R(0) */
@@ -1967,9 +2020,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_slot(QwSimDev d, QwBufDe
             tb[lane] = zero;
             tb[lane + 32] = zero;
         }
-        int ex[NBK];
-#pragma unroll
-        for (int q = 0; q < NBK; ++q) ex[q] = __shfl_sync(FULL, excl, q);
+        cp_async_wait_all();
         __syncwarp();
         /* load: O_s'^dag of each branch, scattered to its slot or listed */
         uint64_t anc = 0;
@@ -1977,20 +2028,20 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_slot(QwSimDev d, QwBufDe
         for (int b0 = 0; b0 < total; b0 += 32) {
             const int t = b0 + lane;
             const bool act = t < total;
-            int bi = 0, start = 0;
-#pragma unroll
-            for (int q = 1; q < NBK; ++q) {
-                const bool ge = t >= ex[q];
-                bi += ge ? 1 : 0;
-                start = ge ? ex[q] : start;
-            }
+            int bi;
+            int64_t at;
+            locate(t, bi, at);
             const int ut = bi >> 1, b1 = bi & 1;
             uint64_t raw = 0;
             AmpT v = zero;
             if (act) {
-                const int64_t at = (2 * u0 + bi) * (int64_t)d.cap_row + (t - start);
-                raw = in.key[at];
-                v = amp_in[at];
+                if (t < kSlotStage) {
+                    raw = sk[t];
+                    v = sa[t];
+                } else {
+                    raw = in.key[at];
+                    v = amp_in[at];
+                }
                 if (rescale) v = scale.apply(v);
                 anc |= raw >> ash;
             }
@@ -2021,11 +2072,11 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_slot(QwSimDev d, QwBufDe
             continue;
         }
         {
-            unsigned long long nu = 0;
+            unsigned int nu = 0;
 #pragma unroll
-            for (int q = 0; q < RPP; ++q) nu += (ex[2 * q] != (2 * q + 2 < NBK ? ex[2 * q + 2] : total)) ? 1 : 0;
+            for (int q = 0; q < RPP; ++q) nu += (ex[2 * q] != (2 * q + 2 < NBK ? ex[2 * q + 2] : total)) ? 1u : 0u;
             st.rows += nu;
-            st.in += (unsigned long long)total;
+            st.in += (unsigned int)total;
         }
         __syncwarp();
 
