@@ -57,6 +57,8 @@ def parse_args():
     p.add_argument("--no-mmax", action="store_true")
     p.add_argument("--no-configs", action="store_true", help="skip the N=16 and N=1024 walk legs")
     p.add_argument("--no-partition", action="store_true", help="skip the row-partitioned walk leg")
+    p.add_argument("--no-schedules", action="store_true",
+                   help="skip the flat and register-faithful schedule leg")
     p.add_argument("--variant", type=int, default=-1,
                    help="step-kernel variant for both precisions instead of the autotuner's choice (profiling)")
     p.add_argument("--shard", action="store_true",
@@ -395,6 +397,7 @@ def run_ours(args, rank, world, local_rank):
 
     table1 = None if args.no_table1 else table1_leg(torch, barrier, max_over_ranks)
     part = None if (args.no_partition or world > 1) else partition_leg(torch)
+    sched = None if args.no_schedules else schedules_leg(torch)
     qls = None if args.no_qls else qls_leg(torch, barrier, max_over_ranks)
     mmax = None if args.no_mmax else mmax_leg()
 
@@ -412,6 +415,10 @@ def run_ours(args, rank, world, local_rank):
         err = {"walk_n16384_complex64_20_steps": state_error(gpu_walk_state(w, qwalk.QW_FP32_AMP, w.steps, variant),
                                                               ref),
                "walk_n16384_complex128_20_steps": state_error(gpu_walk_state(w, qwalk.QW_FP64, w.steps), ref),
+               "walk_n16384_flat_complex128_20_steps": state_error(gpu_walk_state(w, qwalk.QW_FP64, w.steps, 5),
+                                                                   ref),
+               "walk_n16384_faithful_complex128_20_steps": state_error(
+                   gpu_walk_state(w, qwalk.QW_FP64, w.steps, 6), ref),
                "bounds": {"complex128": "keys equal, max |da| <= 1e-12",
                           "complex64": "max |da| <= 2e-6, ||da||_2 <= 1e-5 over the union of keys"}}
         del o
@@ -459,6 +466,8 @@ def run_ours(args, rank, world, local_rank):
         line["mmax"] = mmax
     if part is not None:
         line["partitioned"] = part
+    if sched is not None:
+        line["schedules"] = sched
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if err is not None:
@@ -734,6 +743,39 @@ def partition_leg(torch, steps: int = 24) -> dict:
             sim.close()
         out[f"p{nparts}"] = {"walk_steps_per_s": steps / dt, "ms_per_step": 1000.0 * dt / steps,
                              "branches_per_part": sizes}
+    return out
+
+
+def schedules_leg(torch, steps: int = 6) -> dict:
+    """The N = 16384 walk (complex128) on the paper's literal schedule: the
+    flat path (walk_variant 5: one list of 16-byte keys, every interference
+    op a global radix sort, a per-group transform and a compaction) and the
+    register-faithful one (walk_variant 6: 80-byte keys holding the QRAM
+    address and Alg. 1's registers and stack, the 58 sub-operations of W).
+    Wall-clock per step (the host synchronises between stages), branches
+    through the step per second, and the key bytes a branch carries."""
+    from paper_2303_06890_gb300 import qwalk
+    from paper_2303_06890_gb300 import workloads as wl
+    w = wl.walk_n16384()
+    out = {"workload": w.name, "precision": "complex128", "steps": steps}
+    for variant, name, key_bytes in ((5, "flat", 16), (6, "faithful", 80)):
+        sim = qwalk.Sim(w.matrix, s_pad=w.s, walk_variant=variant)
+        sim.state_init(w.b)
+        sim.apply_walk_step(2)
+        sim.step_stats(reset=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.apply_walk_step(steps)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = sim.step_stats(reset=True)
+        row = {"ms_per_step": 1000.0 * dt / steps, "walk_steps_per_s": steps / dt,
+               "branches_per_s": (st["in"] + st["after_rdag"] + st["after_h1"] + st["after_hph"]) / dt,
+               "key_bytes_per_branch": key_bytes}
+        if variant == 6:
+            row.update(sim.faithful_info())
+        sim.close()
+        out[name] = row
     return out
 
 

@@ -100,7 +100,11 @@ typedef struct {
                                 branches in device memory, each interference op a
                                 global radix sort by key, a per-group transform and a
                                 compaction (no capacity limit; the host synchronises
-                                between its stages, so no CUDA graph is used) */
+                                between its stages, so no CUDA graph is used), 6 = the
+                                register-faithful schedule: the flat path with every
+                                working register of O_s', O_A' and Alg. 1 held in the
+                                state between sub-operations (the QW_FQ_STEP sequence
+                                below; any fuse_reflection) */
     int32_t graphs;          /* 1 (default): runs of >= 6 walk steps are issued as replays
                                 of a captured 6-step CUDA graph; 0: one launch per step */
     int32_t spill_rows;      /* slots of the table holding rows with jc != 0 (reached only
@@ -198,7 +202,7 @@ int qw_enqueue_walk_steps(qw_sim *sim, int64_t nsteps);
 int qw_sync(qw_sim *sim);
 
 /* Number of step-kernel variants (walk_variant 0 .. QW_WALK_VARIANTS - 1). */
-#define QW_WALK_VARIANTS 6
+#define QW_WALK_VARIANTS 7
 
 /*
  * Autotuner of the fused step kernel: runs steps_per_candidate walk steps with
@@ -383,6 +387,123 @@ int qw_state_export(qw_sim *sim, int32_t inst, int32_t key_words, uint64_t *keys
  */
 int qw_state_import(qw_sim *sim, int32_t key_words, const uint64_t *keys, const double *amps,
                     int64_t count);
+
+/*
+ * Register-faithful sub-operations (Sec. V-A, the working-qubit count of
+ * Sec. V-C-1, Alg. 1, Eq. "Newprocess").  The paper's simulator keeps every
+ * working register of a semi-quantum operation in the state: the QRAM
+ * address that O_s' and O_A' compute out of place, and the quantum binary
+ * search's left, right, mid, midval, flag and comparison bits with the
+ * push/pop stack of one (mid, midval, cl, ce) frame per probe.  These calls
+ * run the walk at that granularity on one list of all branches in device
+ * memory (the flat path of walk_variant 5) whose keys hold those registers
+ * beside the base ones (QW_FQ_KEY_WORDS 64-bit words per branch).
+ *
+ * QRAM addresses (Fig. 1): the value segment [0, N s) holds A_jl at j s + l,
+ * the column segment [N s, 2 N s) holds the column index of slot l of row j
+ * at N s + j s + l; a read outside its segment gives 0.  Sub-operations:
+ *   QW_FQ_ADDR_COL  addr ^= N s + j s + k
+ *   QW_FQ_QRAM_COL  kc ^= QRAM[addr] (column segment)
+ *   QW_FQ_QBS_FWD   Alg. 1 with target kc on row j's column segment,
+ *                   k ^= the index found; left, right, flag and L + 1 stack
+ *                   frames (L = ceil(log2 s)) stay
+ *   QW_FQ_QBS_BWD   Alg. 1 undone in reverse: the working registers back to
+ *                   0 (k kept)
+ *   QW_FQ_SWAP      swap(k, kc)
+ *   QW_FQ_ADDR_VAL  addr ^= j s + k           (only where jc = kc = 0)
+ *   QW_FQ_QRAM_VAL  A ^= QRAM[addr] (value segment; only where jc = kc = 0)
+ *   QW_FQ_R, QW_FQ_RDAG, QW_FQ_H, QW_FQ_P, QW_FQ_S  the walk's operators
+ *   QW_FQ_ALLOC_A, QW_FQ_FREE_A  A's allocation (FREE_A checks A = 0)
+ * so O_s' = ADDR_COL QRAM_COL ADDR_COL QBS_FWD QBS_BWD SWAP, O_s'^dag =
+ * SWAP QBS_FWD QBS_BWD ADDR_COL QRAM_COL ADDR_COL (the search with its
+ * uncomputation is k ^= index, its own inverse, so that pair keeps its order)
+ * and O_A' = ADDR_VAL QRAM_VAL ADDR_VAL.  The operators
+ * R .. FREE_A act on the base registers and need every working register at 0.
+ * QW_FQ_STEP_LEN codes in QW_FQ_STEP are W = S T~ P T~^dag (Alg. "Quantum
+ * walk operator"); walk_variant 6 runs them as one walk step.
+ */
+#define QW_FQ_ADDR_COL 1
+#define QW_FQ_QRAM_COL 2
+#define QW_FQ_QBS_FWD 3
+#define QW_FQ_QBS_BWD 4
+#define QW_FQ_SWAP 5
+#define QW_FQ_ADDR_VAL 6
+#define QW_FQ_QRAM_VAL 7
+#define QW_FQ_R 8
+#define QW_FQ_RDAG 9
+#define QW_FQ_H 10
+#define QW_FQ_P 11
+#define QW_FQ_S 12
+#define QW_FQ_ALLOC_A 13
+#define QW_FQ_FREE_A 14
+#define QW_FQ_KEY_WORDS 10
+#define QW_FQ_FRAMES 8 /* stack frames in an exported row: s <= 128 */
+#define QW_FQ_COLS (16 + 4 * QW_FQ_FRAMES)
+#define QW_FQ_STEP_LEN 58
+#define QW_FQ_OS_SEQ QW_FQ_ADDR_COL, QW_FQ_QRAM_COL, QW_FQ_ADDR_COL, QW_FQ_QBS_FWD, QW_FQ_QBS_BWD, QW_FQ_SWAP
+#define QW_FQ_OSDAG_SEQ QW_FQ_SWAP, QW_FQ_QBS_FWD, QW_FQ_QBS_BWD, QW_FQ_ADDR_COL, QW_FQ_QRAM_COL, QW_FQ_ADDR_COL
+#define QW_FQ_OA_SEQ QW_FQ_ADDR_VAL, QW_FQ_QRAM_VAL, QW_FQ_ADDR_VAL
+#define QW_FQ_STEP                                                                                               \
+    {QW_FQ_ALLOC_A, QW_FQ_OSDAG_SEQ, QW_FQ_OA_SEQ, QW_FQ_OS_SEQ, QW_FQ_RDAG, QW_FQ_OSDAG_SEQ, QW_FQ_OA_SEQ,        \
+     QW_FQ_H,       QW_FQ_FREE_A,    QW_FQ_P,      QW_FQ_ALLOC_A, QW_FQ_H,   QW_FQ_OA_SEQ,    QW_FQ_OS_SEQ,        \
+     QW_FQ_R,       QW_FQ_OSDAG_SEQ, QW_FQ_OA_SEQ, QW_FQ_OS_SEQ,  QW_FQ_FREE_A, QW_FQ_S}
+
+/*
+ * Layout of the register-faithful keys for this simulator: *addr_bits the
+ * width of the address and of left / right / mid, *key_bits the bits a key
+ * uses (the base registers' 128, the working registers, L + 1 frames),
+ * *live_bits the qubits of the schedule at its widest (inside Alg. 1 with a
+ * full stack: the base registers, A, the address and Alg. 1's registers).
+ * All nullable.  Returns QW_OK when the layout fits QW_FQ_KEY_WORDS words and
+ * QW_FQ_FRAMES frames, QW_ERR_ARG otherwise (the register-faithful calls are
+ * then refused).
+ */
+int qw_faithful_info(const qw_sim *sim, int32_t *addr_bits, int32_t *key_bits, int64_t *live_bits);
+
+/*
+ * Open a register-faithful session: the state (with its pending
+ * renormalisation) becomes a list of branches, every working register 0.
+ * Until qw_faithful_end the row buckets keep the state as it was here, and
+ * walk steps, QLS, qw_state_init and qw_state_import are refused
+ * (QW_ERR_STATE).  Synchronises.  Errors: QW_ERR_ARG (layout too wide, see
+ * qw_faithful_info), QW_ERR_STATE (no state, or a session is open),
+ * QW_ERR_CUDA.
+ */
+int qw_faithful_begin(qw_sim *sim);
+
+/*
+ * Apply nops sub-operations (QW_FQ_* codes) in order to the open session's
+ * list.  R, R^dag and H drop outputs with |a| <= prune_tau, as a walk step
+ * does.  Synchronises.  Errors: QW_ERR_ARG (unknown code), QW_ERR_STATE (no
+ * session), QW_ERR_DEVICE_STATUS (a working register was not 0 where it must
+ * be, or A not 0 at FREE_A; the list is then as after the failing
+ * sub-operation), QW_ERR_CUDA.
+ */
+int qw_faithful_apply(qw_sim *sim, const int32_t *ops, int32_t nops);
+
+/*
+ * The open session's list as a table: *count = its branches; the first
+ * min(count, cap) rows, sorted ascending by their columns, are written to
+ * regs (QW_FQ_COLS uint64 per branch, host memory: inst, jc, j, b1, kc, k, b2,
+ * A, addr, left, right, mid, midval, flag, cl, ce, then QW_FQ_FRAMES frames of
+ * (mid, midval, cl, ce), frames past L + 1 zero) and amps (2 doubles each).
+ * cap = 0 only counts.  Synchronises.  Errors: QW_ERR_ARG, QW_ERR_STATE,
+ * QW_ERR_CUDA.
+ */
+int qw_faithful_export(qw_sim *sim, uint64_t *regs, double *amps, int64_t cap, int64_t *count);
+
+/*
+ * Close the session.  keep != 0: the list becomes the state as the output of
+ * one walk step (the step counter and qw_step_stats advance; with
+ * renormalisation on, the next step rescales it to the target norm); every
+ * working register and A must be 0, and with overflow_fallback the row
+ * buckets grow to the largest row.  keep = 0: the list is dropped and the
+ * state is the one at qw_faithful_begin.  Synchronises.  Errors: QW_ERR_STATE
+ * (no session), QW_ERR_DEVICE_STATUS (a register not 0: the session stays
+ * open), QW_ERR_CAPACITY (a row does not fit and overflow_fallback = 0: the
+ * session is closed, the state is the one at qw_faithful_begin), QW_ERR_CUDA.
+ */
+int qw_faithful_end(qw_sim *sim, int32_t keep);
 
 /* nb, s, number of instances, and the total device bytes held (all nullable). */
 int qw_sim_info(const qw_sim *sim, int32_t *nb, int32_t *s, int32_t *num_instances,

@@ -23,6 +23,18 @@ OP = {"T": 0, "TDAG": 1, "W": 2, "P": 3, "S": 4, "H": 5, "R": 6, "RDAG": 7,
 REGS = ("jc", "j", "b1", "kc", "k", "b2", "A")
 TAU64 = 1e-13
 
+# register-faithful sub-operations (qw_oracle.c): the working registers of
+# O_s', O_A' and Alg. 1 kept per branch between them
+FQ = {"ADDR_COL": 1, "QRAM_COL": 2, "QBS_FWD": 3, "QBS_BWD": 4, "SWAP": 5, "ADDR_VAL": 6, "QRAM_VAL": 7,
+      "R": 8, "RDAG": 9, "H": 10, "P": 11, "S": 12, "ALLOC_A": 13, "FREE_A": 14}
+G_REGS = ("addr", "left", "right", "mid", "midval", "flag", "cl", "ce")  # then 8 frames of (mid, midval, cl, ce)
+FQ_OS = ("ADDR_COL", "QRAM_COL", "ADDR_COL", "QBS_FWD", "QBS_BWD", "SWAP")
+FQ_OSDAG = ("SWAP", "QBS_FWD", "QBS_BWD", "ADDR_COL", "QRAM_COL", "ADDR_COL")
+FQ_OA = ("ADDR_VAL", "QRAM_VAL", "ADDR_VAL")
+# W = S T~ P T~^dag as sub-operations (Alg. T~, Alg. "Quantum walk operator")
+FQ_STEP = (("ALLOC_A",) + FQ_OSDAG + FQ_OA + FQ_OS + ("RDAG",) + FQ_OSDAG + FQ_OA + ("H", "FREE_A", "P", "ALLOC_A", "H")
+           + FQ_OA + FQ_OS + ("R",) + FQ_OSDAG + FQ_OA + FQ_OS + ("FREE_A", "S"))
+
 _lib = None
 
 
@@ -65,6 +77,15 @@ def _load():
     lib.or_qbs.restype = u64
     lib.or_qbs.argtypes = [P, u64, u64]
     lib.or_os_single.argtypes = [P, u64, u64, u64, ctypes.c_int, P, P]
+    lib.or_apply_faithful.argtypes = [P, ctypes.c_int]
+    lib.or_export_faithful.restype = i64
+    lib.or_export_faithful.argtypes = [P, P, P, i64]
+    lib.or_faithful_ng.restype = ctypes.c_int
+    lib.or_faithful_ng.argtypes = []
+    lib.or_faithful_addr_bits.restype = ctypes.c_int
+    lib.or_faithful_addr_bits.argtypes = [P]
+    lib.or_faithful_live_bits.restype = i64
+    lib.or_faithful_live_bits.argtypes = [P]
     _lib = lib
     return lib
 
@@ -136,6 +157,30 @@ class Oracle:
         if _load().or_marginal(self._h, REGS.index(reg), _ptr(p), length):
             raise ValueError(reg)
         return p
+
+    def apply_faithful(self, *ops: str) -> None:
+        """Register-faithful sub-operations (FQ), in order."""
+        for op in ops:
+            if _load().or_apply_faithful(self._h, FQ[op]):
+                raise RuntimeError(f"oracle sub-operation {op} failed")
+
+    def export_faithful(self) -> tuple[np.ndarray, np.ndarray]:
+        """(regs [M, 7 + NG] uint64: jc, j, b1, kc, k, b2, A, then the working
+        registers G_REGS and the stack frames; amps [M]), oracle order."""
+        ng = _load().or_faithful_ng()
+        m = self.size()
+        regs = np.zeros((m, 7 + ng), dtype=np.uint64)
+        a = np.zeros((m, 2), dtype=np.float64)
+        _load().or_export_faithful(self._h, _ptr(regs), _ptr(a), m)
+        return regs, a[:, 0] + 1j * a[:, 1]
+
+    @property
+    def faithful_addr_bits(self) -> int:
+        return int(_load().or_faithful_addr_bits(self._h))
+
+    @property
+    def faithful_live_bits(self) -> int:
+        return int(_load().or_faithful_live_bits(self._h))
 
     def norm2(self) -> float:
         return float(_load().or_norm2(self._h))

@@ -86,6 +86,8 @@ typedef struct oracle {
     reg_meta meta[NREG];
     int64_t live_bits, max_live_bits;
     int64_t violations; /* ancilla-not-zero and other self-check failures */
+    uint64_t *g;        /* register-faithful sub-operations: NG working registers per branch */
+    int64_t gm;         /* rows of g (0: none allocated, all working registers zero) */
 } oracle;
 
 /* ------------------------------------------------------------------------- */
@@ -489,6 +491,187 @@ static int op_w(oracle *o)
 }
 
 /* ------------------------------------------------------------------------- */
+/* Register-faithful sub-operations                                          */
+/*
+ * The paper's simulator holds every working register of a semi-quantum op in
+ * the state (Sec. V-A; the qubit count of Sec. V-C-1): the QRAM address of
+ * O_s' and O_A' (Eq. "Newprocess", computed out of place), and Alg. 1's
+ * left, right, mid, midval and flags with its push/pop garbage stack.  Here
+ * each of those steps is an operation of its own, the working registers kept
+ * per branch between them in g (NG values per branch, zero when idle):
+ *   FQ_ADDR_COL  addr ^= col_base + j s + k
+ *   FQ_QRAM_COL  kc ^= QRAM[addr] over the column segment
+ *   FQ_QBS_FWD   Alg. 1's loop with target kc, output k ^= index: left,
+ *                right, flag and the stack of (mid, midval, cl, ce) frames stay
+ *   FQ_QBS_BWD   Alg. 1's uncomputation: every working register back to 0
+ *   FQ_SWAP      swap(k, kc)
+ *   FQ_ADDR_VAL  addr ^= val_base + j s + k           (controlled by jc = kc = 0)
+ *   FQ_QRAM_VAL  A ^= QRAM[addr] over the value segment (controlled likewise)
+ * so O_s' = ADDR_COL QRAM_COL ADDR_COL QBS_FWD QBS_BWD SWAP, O_s'^dag the same
+ * in reverse, O_A' = ADDR_VAL QRAM_VAL ADDR_VAL.  The interference ops, P and
+ * S act on the base registers; the working registers must be 0 there.
+ */
+enum { G_ADDR = 0, G_LEFT, G_RIGHT, G_MID, G_MIDVAL, G_FLAG, G_CL, G_CE, G_STK, NG = G_STK + 4 * 8 };
+enum {
+    FQ_ADDR_COL = 1, FQ_QRAM_COL, FQ_QBS_FWD, FQ_QBS_BWD, FQ_SWAP, FQ_ADDR_VAL, FQ_QRAM_VAL,
+    FQ_R, FQ_RDAG, FQ_H, FQ_P, FQ_S, FQ_ALLOC_A, FQ_FREE_A
+};
+
+static int g_reserve(oracle *o)
+{
+    if (o->gm == o->m && o->g) return 0;
+    free(o->g);
+    o->g = (uint64_t *)calloc((size_t)(o->m ? o->m : 1) * NG, sizeof(uint64_t));
+    o->gm = o->m;
+    return o->g ? 0 : -1;
+}
+
+/* the working registers are 0 on every branch (an interference op, P and S
+   act on the base registers only) */
+static void g_check_free(oracle *o)
+{
+    if (!o->g) return;
+    for (int64_t i = 0; i < o->gm * NG; ++i) check(o, o->g[i] == 0);
+    free(o->g);
+    o->g = NULL;
+    o->gm = 0;
+}
+
+static void fq_branch(oracle *o, branch *e, uint64_t *g, int op)
+{
+    const uint64_t j = e->r[R_J];
+    const uint64_t offset = (uint64_t)o->col_base + j * (uint64_t)o->s;
+    switch (op) {
+    case FQ_ADDR_COL: g[G_ADDR] ^= offset + e->r[R_K]; break;
+    case FQ_QRAM_COL: e->r[R_KC] ^= qram(o, g[G_ADDR], o->col_base); break;
+    case FQ_ADDR_VAL:
+        if (e->r[R_JC] == 0 && e->r[R_KC] == 0) g[G_ADDR] ^= (uint64_t)o->val_base + j * (uint64_t)o->s + e->r[R_K];
+        break;
+    case FQ_QRAM_VAL:
+        if (e->r[R_JC] == 0 && e->r[R_KC] == 0) e->r[R_A] ^= qram(o, g[G_ADDR], o->val_base);
+        break;
+    case FQ_SWAP: {
+        uint64_t t = e->r[R_K];
+        e->r[R_K] = e->r[R_KC];
+        e->r[R_KC] = t;
+        break;
+    }
+    case FQ_QBS_FWD: { /* Alg. 1, target kc, output into k */
+        const uint64_t target = e->r[R_KC];
+        g[G_LEFT] ^= offset;
+        g[G_RIGHT] ^= g[G_LEFT] + (uint64_t)o->s;
+        g[G_FLAG] ^= 1;
+        for (int it = 0; it <= o->L; ++it) {
+            uint64_t *fr = g + G_STK + 4 * it;
+            if (g[G_FLAG]) g[G_MID] ^= (g[G_LEFT] + g[G_RIGHT]) / 2;
+            if (g[G_FLAG]) g[G_MIDVAL] ^= qram(o, g[G_MID], o->col_base);
+            if (g[G_FLAG]) {
+                g[G_CL] ^= (g[G_MIDVAL] < target);
+                g[G_CE] ^= (g[G_MIDVAL] == target);
+            }
+            if (g[G_CE]) e->r[R_K] ^= g[G_MID] - offset;
+            if (g[G_CE]) g[G_FLAG] ^= 1;
+            if (g[G_FLAG] && g[G_CL]) { uint64_t t = g[G_MID]; g[G_MID] = g[G_LEFT]; g[G_LEFT] = t; }
+            if (g[G_FLAG]) g[G_CL] ^= 1;
+            if (g[G_FLAG] && g[G_CL]) { uint64_t t = g[G_MID]; g[G_MID] = g[G_RIGHT]; g[G_RIGHT] = t; }
+            /* push: the loop registers move into frame it, zeros remain */
+            fr[0] = g[G_MID];
+            fr[1] = g[G_MIDVAL];
+            fr[2] = g[G_CL];
+            fr[3] = g[G_CE];
+            g[G_MID] = g[G_MIDVAL] = g[G_CL] = g[G_CE] = 0;
+        }
+        break;
+    }
+    case FQ_QBS_BWD: { /* the loop undone in reverse, all but the output */
+        const uint64_t target = e->r[R_KC];
+        for (int it = (int)o->L; it >= 0; --it) {
+            uint64_t *fr = g + G_STK + 4 * it;
+            g[G_MID] = fr[0];
+            g[G_MIDVAL] = fr[1];
+            g[G_CL] = fr[2];
+            g[G_CE] = fr[3];
+            fr[0] = fr[1] = fr[2] = fr[3] = 0;
+            if (g[G_FLAG] && g[G_CL]) { uint64_t t = g[G_MID]; g[G_MID] = g[G_RIGHT]; g[G_RIGHT] = t; }
+            if (g[G_FLAG]) g[G_CL] ^= 1;
+            if (g[G_FLAG] && g[G_CL]) { uint64_t t = g[G_MID]; g[G_MID] = g[G_LEFT]; g[G_LEFT] = t; }
+            if (g[G_CE]) g[G_FLAG] ^= 1;
+            if (g[G_FLAG]) {
+                g[G_CL] ^= (g[G_MIDVAL] < target);
+                g[G_CE] ^= (g[G_MIDVAL] == target);
+            }
+            if (g[G_FLAG]) g[G_MIDVAL] ^= qram(o, g[G_MID], o->col_base);
+            if (g[G_FLAG]) g[G_MID] ^= (g[G_LEFT] + g[G_RIGHT]) / 2;
+            check(o, g[G_MID] == 0 && g[G_MIDVAL] == 0 && g[G_CL] == 0 && g[G_CE] == 0);
+        }
+        g[G_FLAG] ^= 1;
+        g[G_RIGHT] ^= g[G_LEFT] + (uint64_t)o->s;
+        g[G_LEFT] ^= offset;
+        check(o, g[G_LEFT] == 0 && g[G_RIGHT] == 0 && g[G_FLAG] == 0);
+        break;
+    }
+    default: break;
+    }
+}
+
+/* address register width of the layout: every address a branch can form */
+static int faithful_addr_bits(const oracle *o)
+{
+    uint64_t top = (uint64_t)o->ns + (((uint64_t)1 << o->nb) * (uint64_t)o->s) + ((uint64_t)1 << o->nb) + 1;
+    int b = 0;
+    while (((uint64_t)1 << b) < top) b++;
+    return b;
+}
+
+/* live bits of the faithful schedule at its widest (inside O_s'): the base
+   registers, A, the address and Alg. 1's registers with a full stack
+   (Sec. V-C-1's count of working qubits, for this register layout) */
+int64_t or_faithful_live_bits(const oracle *o)
+{
+    const int aw = faithful_addr_bits(o);
+    return 4 * o->nb + 2 + o->w + aw + 3 * aw + 16 + 3 + (o->L + 1) * (aw + 16 + 2);
+}
+
+int or_apply_faithful(oracle *o, int op)
+{
+    switch (op) {
+    case FQ_R: g_check_free(o); return op_r(o);
+    case FQ_RDAG: g_check_free(o); return op_rdag(o);
+    case FQ_H: g_check_free(o); return op_h(o);
+    case FQ_P: g_check_free(o); for_each(o, p_branch); return 0;
+    case FQ_S: g_check_free(o); for_each(o, s_branch); return 0;
+    case FQ_ALLOC_A: g_check_free(o); reg_alloc(o, R_A, (int)o->w); return 0;
+    case FQ_FREE_A: g_check_free(o); reg_free(o, R_A); return 0;
+    default: break;
+    }
+    if (op < FQ_ADDR_COL || op > FQ_QRAM_VAL) return -1;
+    if (g_reserve(o)) return -1;
+    if (op == FQ_QBS_FWD) {
+        const int aw = faithful_addr_bits(o);
+        note_transient_bits(o, aw + 3 * aw + 16 + 3 + (o->L + 1) * (aw + 16 + 2));
+    }
+    for (int64_t i = 0; i < o->m; ++i) fq_branch(o, &o->st[i], o->g + i * NG, op);
+    return 0;
+}
+
+/* Export with the working registers: regs m x (7 + NG) (jc, j, b1, kc, k, b2,
+   A, then g), amps m x 2. */
+int64_t or_export_faithful(const oracle *o, uint64_t *regs, double *amps, int64_t cap)
+{
+    int64_t m = o->m < cap ? o->m : cap;
+    for (int64_t i = 0; i < m; ++i) {
+        for (int r = 0; r < NREG; ++r) regs[i * (NREG + NG) + r] = o->st[i].r[r];
+        for (int r = 0; r < NG; ++r) regs[i * (NREG + NG) + NREG + r] = (o->g && i < o->gm) ? o->g[i * NG + r] : 0;
+        amps[2 * i] = creal(o->st[i].a);
+        amps[2 * i + 1] = cimag(o->st[i].a);
+    }
+    return o->m;
+}
+
+int or_faithful_ng(void) { return NG; }
+int or_faithful_addr_bits(const oracle *o) { return faithful_addr_bits(o); }
+
+/* ------------------------------------------------------------------------- */
 /* Public interface (ctypes)                                                 */
 
 enum {
@@ -586,6 +769,7 @@ void or_destroy(oracle *o)
     if (!o) return;
     free(o->mem);
     free(o->st);
+    free(o->g);
     free(o);
 }
 
@@ -606,6 +790,9 @@ void or_image(const oracle *o, int64_t j, int64_t l, uint32_t *val, uint32_t *co
 /* |b~> = sum_j b_j |0, j, 0, 0, 0, 0> (exact zeros are not stored). */
 int or_init_b(oracle *o, const double *b_re, const double *b_im)
 {
+    free(o->g);
+    o->g = NULL;
+    o->gm = 0;
     o->m = 0;
     if (reserve(o, o->n)) return -1;
     for (int64_t j = 0; j < o->n; ++j) {
@@ -623,6 +810,9 @@ int or_init_b(oracle *o, const double *b_re, const double *b_im)
 /* Replace the state: regs is m x 6 (jc, j, b1, kc, k, b2), amps m x 2. */
 int or_import(oracle *o, const uint64_t *regs, const double *amps, int64_t m)
 {
+    free(o->g);
+    o->g = NULL;
+    o->gm = 0;
     if (reserve(o, m)) return -1;
     for (int64_t i = 0; i < m; ++i) {
         branch e;
@@ -649,6 +839,7 @@ int64_t or_export(const oracle *o, uint64_t *regs, double *amps, int64_t cap)
 
 int or_apply(oracle *o, int op)
 {
+    g_check_free(o); /* the whole ops need the working registers idle */
     switch (op) {
     case OR_T: return op_t(o);
     case OR_TDAG: return op_tdag(o);

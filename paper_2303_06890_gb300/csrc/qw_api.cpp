@@ -63,6 +63,23 @@ int ceil_log2(int64_t x)
 
 } // namespace
 
+/* A flat list of branches in device memory (qw_flat.cu): kw-word packed keys
+ * and complex FP64 amplitudes, stream-ordered allocations on the simulator's
+ * stream. */
+struct FlatList {
+    int kw = 2;
+    void *K = nullptr;
+    double2 *A = nullptr;
+    int64_t M = 0;
+};
+
+/* Branch counts of a faithful sequence for qw_step_stats: [0] at the start,
+ * [1] after R^dag, [2] after the first H, [3] after the second, [4] after R. */
+struct FaithCounts {
+    int64_t c[5] = {0, 0, 0, 0, 0};
+    int nh = 0;
+};
+
 struct qw_sim {
     qw_sim_opts opts;
     cudaStream_t stream = nullptr;
@@ -117,8 +134,19 @@ struct qw_sim {
     cudaGraphExec_t gexec[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
     /* captured 3-term QLS graphs (6 walk steps, 3 norms), one per phase */
     cudaGraphExec_t qexec[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    /* an open register-faithful session: its list of branches */
+    FlatList fq;
+    FaithCounts fq_counts;
+    bool fq_open = false;
     std::string err;
 };
+
+/* the flat and register-faithful steps synchronise between their stages:
+   never captured in a graph */
+static bool host_staged(const qw_sim *sim)
+{
+    return sim->mode == QW_MODE_WALK_FLAT || sim->mode == QW_MODE_WALK_FAITHFUL;
+}
 
 static const int kGraphSteps = 6; /* a multiple of the 3-buffer and 2-slot periods */
 static const int kGraphTerms = 3;  /* QLS terms per graph: 2 walk steps each */
@@ -291,13 +319,16 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     sim->fp32 = o.precision == QW_FP32_AMP;
     sim->renorm = o.renorm < 0 ? sim->fp32 : (o.renorm != 0);
     static const int kVariantMode[QW_WALK_VARIANTS] = {QW_MODE_WALK_FUSED, QW_MODE_WALK_FUSED_PF, QW_MODE_WALK_SEG,
-                                                       QW_MODE_WALK_SEG_PF, QW_MODE_WALK_SLOT, QW_MODE_WALK_FLAT};
+                                                       QW_MODE_WALK_SEG_PF, QW_MODE_WALK_SLOT, QW_MODE_WALK_FLAT,
+                                                       QW_MODE_WALK_FAITHFUL};
     if (o.walk_variant < 0 || o.walk_variant >= QW_WALK_VARIANTS) {
         delete sim;
-        g_create_error = "qw_sim_create: walk_variant must be 0..5";
+        g_create_error = "qw_sim_create: walk_variant must be 0..6";
         return QW_ERR_ARG;
     }
-    sim->mode = o.fuse_reflection ? kVariantMode[o.walk_variant] : QW_MODE_WALK_LITERAL;
+    sim->mode = (o.fuse_reflection || kVariantMode[o.walk_variant] == QW_MODE_WALK_FAITHFUL)
+                    ? kVariantMode[o.walk_variant]
+                    : QW_MODE_WALK_LITERAL;
     sim->stream = (cudaStream_t)o.stream;
 
     QwSimDev &d = sim->d;
@@ -340,7 +371,7 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
         qw_sim_destroy(sim);
         return QW_ERR_ARG;
     }
-    if (o.nparts > 1 && (ninst != 1 || sim->mode == QW_MODE_WALK_LITERAL || sim->mode == QW_MODE_WALK_FLAT)) {
+    if (o.nparts > 1 && (ninst != 1 || sim->mode == QW_MODE_WALK_LITERAL || host_staged(sim))) {
         g_create_error = "qw_sim_create: a partitioned walk needs one instance, fuse_reflection = 1 and "
                          "walk_variant <= 4";
         qw_sim_destroy(sim);
@@ -368,6 +399,12 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
                                      : (int)std::min<int64_t>(4096, std::max<int64_t>(256, next_pow2(buckets / 8)));
     d.dense_buckets = buckets;
     d.n_single = ninst == 1 ? mats[0].n : 0;
+    if (sim->mode == QW_MODE_WALK_FAITHFUL && (ninst != 1 || !qw_faithful_layout(d, nullptr, nullptr))) {
+        g_create_error = "qw_sim_create: walk_variant 6 (register-faithful) needs one instance, s <= 128 and "
+                         "working registers that fit 10 key words";
+        qw_sim_destroy(sim);
+        return QW_ERR_ARG;
+    }
     d.total_buckets = buckets + d.spill_slots;
     sim->n_of = hn;
     sim->bkt_of = hbkt;
@@ -517,6 +554,10 @@ extern "C" int qw_sim_destroy(qw_sim *sim)
     if (!sim) return QW_OK;
     if (sim->stream) cudaStreamSynchronize(sim->stream);
     else cudaDeviceSynchronize();
+    if (sim->fq_open) {
+        cudaFree(sim->fq.K);
+        cudaFree(sim->fq.A);
+    }
     cudaFree(sim->img);
     cudaFree(sim->fg);
     cudaFree(sim->fg32);
@@ -638,11 +679,14 @@ static QwStepArgs step_args(qw_sim *sim, int mode)
 }
 
 static int flat_walk_step(qw_sim *sim, int readout);
+static int faithful_walk_step(qw_sim *sim, int readout);
+static int sync_walk(qw_sim *sim, const char *where);
 
 /* one walk step: X_cur -> X_cur+1, clearing X_cur+2 */
 static int launch_walk(qw_sim *sim, int readout)
 {
     if (sim->mode == QW_MODE_WALK_FLAT) return flat_walk_step(sim, readout);
+    if (sim->mode == QW_MODE_WALK_FAITHFUL) return faithful_walk_step(sim, readout);
     if (sim->d.nparts > 1) /* the outboxes hold this step's sends only */
         QW_CUDA(sim, cudaMemsetAsync(sim->outbox_count, 0, (size_t)sim->d.nparts * 8, sim->stream));
     sim->issued++;
@@ -698,171 +742,375 @@ static int grow_rows(qw_sim *sim, int64_t need)
     return QW_OK;
 }
 
+static cudaError_t flat_alloc(qw_sim *sim, size_t bytes, void **p)
+{
+    *p = nullptr;
+    return cudaMallocAsync(p, bytes < 16 ? 16 : bytes, sim->stream);
+}
+
+static void flat_release(qw_sim *sim, FlatList &L)
+{
+    if (L.K) cudaFreeAsync(L.K, sim->stream);
+    if (L.A) cudaFreeAsync(L.A, sim->stream);
+    L.K = nullptr;
+    L.A = nullptr;
+    L.M = 0;
+}
+
+/* Gather the current state (with its pending renormalisation) into L. */
+static cudaError_t flat_gather(qw_sim *sim, FlatList &L, int kw)
+{
+    cudaStream_t st = sim->stream;
+    unsigned long long hc = 0;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(&sim->sc->counter, 0, 8, st)) != cudaSuccess) return e;
+    if ((e = qw_launch_count(sim->d, sim->buf[sim->cur], -1, &sim->sc->counter, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(&hc, &sim->sc->counter, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    flat_release(sim, L);
+    L.kw = kw;
+    L.M = (int64_t)hc;
+    if ((e = flat_alloc(sim, (size_t)L.M * 8 * kw, &L.K)) != cudaSuccess) return e;
+    if ((e = flat_alloc(sim, (size_t)L.M * 16, (void **)&L.A)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(&sim->sc->counter, 0, 8, st)) != cudaSuccess) return e;
+    return qw_flat_gather(sim->d, sim->buf[sim->cur], sim->fp32, pending_scale(sim), L.K, L.A, &sim->sc->counter, L.M,
+                          st, kw);
+}
+
+/* An interference op on the list (0 = R^dag, 1 = R, 2 = H): grouping by a
+ * global radix sort, the per-group transform, the compaction of the kept
+ * outputs; the host synchronises to size the result. */
+static cudaError_t flat_stage(qw_sim *sim, FlatList &L, int op)
+{
+    const QwSimDev &d = sim->d;
+    cudaStream_t st = sim->stream;
+    cudaError_t e = cudaSuccess;
+    const size_t kb = 8 * (size_t)L.kw;
+    const int outs = op == 2 ? d.s : 2;
+    void *tk = nullptr, *ta = nullptr, *work = nullptr;
+    if (L.M > 1) {
+        if ((e = flat_alloc(sim, (size_t)L.M * kb, &tk)) != cudaSuccess) return e;
+        if ((e = flat_alloc(sim, (size_t)L.M * 16, &ta)) != cudaSuccess) return e;
+        if ((e = flat_alloc(sim, qw_flat_sort_words(L.M) * 4, &work)) != cudaSuccess) return e;
+        e = qw_flat_sort(d, L.K, L.A, tk, static_cast<double2 *>(ta), L.M, op == 2 ? 1 : 0,
+                         static_cast<uint32_t *>(work), st, L.kw);
+        cudaFreeAsync(tk, st);
+        cudaFreeAsync(ta, st);
+        cudaFreeAsync(work, st);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t n = L.M * outs;
+    void *ok = nullptr, *oa = nullptr, *flags = nullptr, *pos = nullptr, *sums = nullptr;
+    if ((e = flat_alloc(sim, (size_t)n * kb, &ok)) != cudaSuccess) return e;
+    if ((e = flat_alloc(sim, (size_t)n * 16, &oa)) != cudaSuccess) return e;
+    if ((e = flat_alloc(sim, (size_t)n * 4, &flags)) != cudaSuccess) return e;
+    if ((e = flat_alloc(sim, (size_t)n * 4, &pos)) != cudaSuccess) return e;
+    if ((e = flat_alloc(sim, qw_flat_scan_words(n) * 4, &sums)) != cudaSuccess) return e;
+    uint32_t total = 0;
+    e = qw_flat_group(d, op, L.K, L.A, L.M, ok, static_cast<double2 *>(oa), static_cast<uint32_t *>(flags), st,
+                      L.kw);
+    if (e == cudaSuccess && n > 0) {
+        e = qw_flat_scan(static_cast<uint32_t *>(flags), n, static_cast<uint32_t *>(sums), static_cast<uint32_t *>(pos),
+                         st);
+        const int64_t nb = (n + 1023) / 1024;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&total, static_cast<uint32_t *>(sums) + nb, 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    FlatList R;
+    R.kw = L.kw;
+    R.M = (int64_t)total;
+    if (e == cudaSuccess) e = flat_alloc(sim, (size_t)R.M * kb, &R.K);
+    if (e == cudaSuccess) e = flat_alloc(sim, (size_t)R.M * 16, (void **)&R.A);
+    if (e == cudaSuccess)
+        e = qw_flat_compact(ok, static_cast<double2 *>(oa), static_cast<uint32_t *>(flags),
+                            static_cast<uint32_t *>(pos), n, R.K, R.A, st, L.kw);
+    for (void *p : {ok, oa, flags, pos, sums})
+        if (p) cudaFreeAsync(p, st);
+    flat_release(sim, L);
+    L = R;
+    return e;
+}
+
+/* Store the list as the output of a step: X_cur+1 (and X_cur+2 cleared, as a
+ * step kernel does), the row buckets grown when a row of it does not fit,
+ * then the step's norm, renormalisation and counters; counts are the branch
+ * numbers after each interference op for qw_step_stats. */
+static int flat_store(qw_sim *sim, FlatList &L, const QwStepArgs &a, const int64_t *counts)
+{
+    QwSimDev &d = sim->d;
+    cudaStream_t st = sim->stream;
+    void *norm = nullptr, *maxrow = nullptr;
+    QW_CUDA(sim, flat_alloc(sim, 8, &norm));
+    QW_CUDA(sim, flat_alloc(sim, 4, &maxrow));
+    int32_t *status = &sim->sc->status;
+    const int nxt = (sim->cur + 1) % 3, clr = (sim->cur + 2) % 3;
+    int rc = QW_OK;
+    for (int attempt = 0; attempt < 2 && rc == QW_OK; ++attempt) {
+        for (int bi : {nxt, clr}) QW_CUDA(sim, qw_launch_clear(d, sim->buf[bi], 0, d.total_buckets, 1, st));
+        QW_CUDA(sim, cudaMemsetAsync(norm, 0, 8, st));
+        QW_CUDA(sim, cudaMemsetAsync(maxrow, 0, 4, st));
+        QW_CUDA(sim, qw_flat_scatter(d, sim->buf[nxt], sim->fp32, L.K, L.A, L.M, status,
+                                     static_cast<unsigned int *>(maxrow), static_cast<double *>(norm), st, L.kw));
+        unsigned int hmax = 0;
+        QW_CUDA(sim, cudaMemcpyAsync(sim->h_st, status, sizeof(StatusView), cudaMemcpyDeviceToHost, st));
+        QW_CUDA(sim, cudaMemcpyAsync(&hmax, maxrow, 4, cudaMemcpyDeviceToHost, st));
+        QW_CUDA(sim, cudaStreamSynchronize(st));
+        if (sim->h_st->status != QW_ST_ROW_OVERFLOW || attempt == 1 || !sim->opts.overflow_fallback) break;
+        /* a row of the result is longer than row_capacity: grow the buckets
+           and store again */
+        const int32_t zero = 0;
+        QW_CUDA(sim, cudaMemcpyAsync(status, &zero, 4, cudaMemcpyHostToDevice, st));
+        rc = grow_rows(sim, (int64_t)hmax);
+    }
+    if (rc == QW_OK) {
+        QW_CUDA(sim, qw_flat_finish(a, static_cast<double *>(norm), counts, st));
+        sim->launches += 1;
+        sim->cur = nxt;
+        sim->scale_slot ^= 1;
+    }
+    cudaFreeAsync(norm, st);
+    cudaFreeAsync(maxrow, st);
+    if (rc != QW_OK) return rc;
+    return check_status(sim, "store of the flat list");
+}
+
 /* One walk step on the flat path (qw_flat.cu): X_cur gathered into one list
  * of 16-byte register keys and complex FP64 amplitudes, the paper's
  * schedule op by op -- O_s'^dag O_A' O_s', R^dag (sort, pairs, compaction),
  * O_s'^dag O_A', H (sort, groups, compaction), [QLS read-out], P, H,
  * O_A' O_s', R, O_s'^dag O_A' O_s', A = 0 checked, S -- and the result
- * stored into X_cur+1 (and X_cur+2 cleared, as a step kernel does), the row
- * buckets grown when a row of it does not fit.  The host synchronises to size
- * each stage; device scratch is stream-ordered (cudaMallocAsync) and freed
- * before the call returns. */
+ * stored into X_cur+1.  The host synchronises to size each stage; device
+ * scratch is stream-ordered (cudaMallocAsync) and freed before the call
+ * returns. */
 static int flat_walk_step(qw_sim *sim, int readout)
 {
-    QwSimDev &d = sim->d;
+    const QwSimDev &d = sim->d;
     cudaStream_t st = sim->stream;
-    std::vector<void *> held;
-    auto alloc = [&](size_t bytes, void **p) -> cudaError_t {
-        *p = nullptr;
-        cudaError_t e = cudaMallocAsync(p, bytes < 16 ? 16 : bytes, st);
-        if (e == cudaSuccess) held.push_back(*p);
-        return e;
-    };
-    auto release = [&](void *p) {
-        for (auto &h : held)
-            if (h == p) {
-                cudaFreeAsync(p, st);
-                h = nullptr;
-            }
-    };
-    auto cleanup = [&]() {
-        for (void *h : held)
-            if (h) cudaFreeAsync(h, st);
-        held.clear();
-    };
-    int rc = QW_OK;
+    FlatList L;
+    int32_t *status = &sim->sc->status;
 #define QW_FLAT(call)                                                                              \
     do {                                                                                           \
         cudaError_t e_ = (call);                                                                   \
         if (e_ != cudaSuccess) {                                                                   \
-            cleanup();                                                                             \
+            flat_release(sim, L);                                                                  \
             return cuda_fail(sim, e_, #call);                                                      \
         }                                                                                          \
     } while (0)
-    /* the state size */
-    unsigned long long hc = 0;
-    QW_FLAT(cudaMemsetAsync(&sim->sc->counter, 0, 8, st));
-    QW_FLAT(qw_launch_count(d, sim->buf[sim->cur], -1, &sim->sc->counter, st));
-    QW_FLAT(cudaMemcpyAsync(&hc, &sim->sc->counter, 8, cudaMemcpyDeviceToHost, st));
-    QW_FLAT(cudaStreamSynchronize(st));
-    int64_t M = (int64_t)hc;
-    int64_t counts[5] = {M, 0, 0, 0, 0};
-    void *K = nullptr, *A = nullptr;
-    QW_FLAT(alloc((size_t)M * 16, &K));
-    QW_FLAT(alloc((size_t)M * 16, &A));
-    QW_FLAT(cudaMemsetAsync(&sim->sc->counter, 0, 8, st));
-    QW_FLAT(qw_flat_gather(d, sim->buf[sim->cur], sim->fp32, pending_scale(sim), K, static_cast<double2 *>(A),
-                           &sim->sc->counter, M, st));
-    int32_t *status = &sim->sc->status;
-    auto map = [&](uint32_t ops) { return qw_flat_map(d, K, M, ops, status, st); };
-    /* an interference op: 0 = R^dag, 1 = R, 2 = H */
-    auto stage = [&](int op) -> cudaError_t {
-        cudaError_t e = cudaSuccess;
-        const int outs = op == 2 ? d.s : 2;
-        if (M > 1) {
-            void *tk, *ta, *work;
-            if ((e = alloc((size_t)M * 16, &tk)) != cudaSuccess) return e;
-            if ((e = alloc((size_t)M * 16, &ta)) != cudaSuccess) return e;
-            if ((e = alloc(qw_flat_sort_words(M) * 4, &work)) != cudaSuccess) return e;
-            e = qw_flat_sort(d, K, static_cast<double2 *>(A), tk, static_cast<double2 *>(ta), M, op == 2 ? 1 : 0,
-                             static_cast<uint32_t *>(work), st);
-            if (e != cudaSuccess) return e;
-            release(tk);
-            release(ta);
-            release(work);
-        }
-        const int64_t n = M * outs;
-        void *ok, *oa, *flags, *pos, *sums, *nk, *na;
-        if ((e = alloc((size_t)n * 16, &ok)) != cudaSuccess) return e;
-        if ((e = alloc((size_t)n * 16, &oa)) != cudaSuccess) return e;
-        if ((e = alloc((size_t)n * 4, &flags)) != cudaSuccess) return e;
-        if ((e = alloc((size_t)n * 4, &pos)) != cudaSuccess) return e;
-        if ((e = alloc(qw_flat_scan_words(n) * 4, &sums)) != cudaSuccess) return e;
-        if ((e = qw_flat_group(d, op, K, static_cast<double2 *>(A), M, ok, static_cast<double2 *>(oa),
-                               static_cast<uint32_t *>(flags), st)) != cudaSuccess)
-            return e;
-        uint32_t total = 0;
-        if (n > 0) {
-            if ((e = qw_flat_scan(static_cast<uint32_t *>(flags), n, static_cast<uint32_t *>(sums),
-                                  static_cast<uint32_t *>(pos), st)) != cudaSuccess)
-                return e;
-            const int64_t nb = (n + 1023) / 1024;
-            if ((e = cudaMemcpyAsync(&total, static_cast<uint32_t *>(sums) + nb, 4, cudaMemcpyDeviceToHost, st)) !=
-                cudaSuccess)
-                return e;
-            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-        }
-        if ((e = alloc((size_t)total * 16, &nk)) != cudaSuccess) return e;
-        if ((e = alloc((size_t)total * 16, &na)) != cudaSuccess) return e;
-        if ((e = qw_flat_compact(ok, static_cast<double2 *>(oa), static_cast<uint32_t *>(flags),
-                                 static_cast<uint32_t *>(pos), n, nk, static_cast<double2 *>(na), st)) != cudaSuccess)
-            return e;
-        for (void *p : {K, A, ok, oa, flags, pos, sums}) release(p);
-        K = nk;
-        A = na;
-        M = (int64_t)total;
-        return cudaSuccess;
-    };
+    QW_FLAT(flat_gather(sim, L, 2));
+    int64_t counts[5] = {L.M, 0, 0, 0, 0};
+    auto map = [&](uint32_t ops) { return qw_flat_map(d, L.K, L.M, ops, status, st, 2); };
     QwStepArgs a = step_args(sim, QW_MODE_WALK_FLAT);
     a.qls_readout = readout;
     /* T~^dag */
     QW_FLAT(map(QW_FLAT_OSDAG | QW_FLAT_OA << 4 | QW_FLAT_OS << 8));
-    QW_FLAT(stage(0));
-    counts[1] = M;
+    QW_FLAT(flat_stage(sim, L, 0));
+    counts[1] = L.M;
     QW_FLAT(map(QW_FLAT_OSDAG | QW_FLAT_OA << 4));
-    QW_FLAT(stage(2));
-    counts[2] = M;
-    if (readout) QW_FLAT(qw_flat_readout(d, K, static_cast<double2 *>(A), M, a, st));
+    QW_FLAT(flat_stage(sim, L, 2));
+    counts[2] = L.M;
+    if (readout) QW_FLAT(qw_flat_readout(d, L.K, L.A, L.M, a, st, 2));
     /* P, then T~ */
-    QW_FLAT(qw_flat_phase(d, K, static_cast<double2 *>(A), M, st));
-    QW_FLAT(stage(2));
-    counts[3] = M;
+    QW_FLAT(qw_flat_phase(d, L.K, L.A, L.M, st, 2));
+    QW_FLAT(flat_stage(sim, L, 2));
+    counts[3] = L.M;
     QW_FLAT(map(QW_FLAT_OA | QW_FLAT_OS << 4));
-    QW_FLAT(stage(1));
-    counts[4] = M;
+    QW_FLAT(flat_stage(sim, L, 1));
+    counts[4] = L.M;
     QW_FLAT(map(QW_FLAT_OSDAG | QW_FLAT_OA << 4 | QW_FLAT_OS << 8 | QW_FLAT_A0 << 12 | QW_FLAT_S << 16));
-    /* store into X_cur+1 */
-    void *norm = nullptr, *maxrow = nullptr;
-    QW_FLAT(alloc(8, &norm));
-    QW_FLAT(alloc(4, &maxrow));
-    const int nxt = (sim->cur + 1) % 3, clr = (sim->cur + 2) % 3;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        for (int bi : {nxt, clr})
-            QW_FLAT(qw_launch_clear(d, sim->buf[bi], 0, d.total_buckets, 1, st));
-        QW_FLAT(cudaMemsetAsync(norm, 0, 8, st));
-        QW_FLAT(cudaMemsetAsync(maxrow, 0, 4, st));
-        QW_FLAT(qw_flat_scatter(d, sim->buf[nxt], sim->fp32, K, static_cast<double2 *>(A), M, status,
-                                static_cast<unsigned int *>(maxrow), static_cast<double *>(norm), st));
-        StatusView hs{};
-        unsigned int hmax = 0;
-        QW_FLAT(cudaMemcpyAsync(sim->h_st, status, sizeof(StatusView), cudaMemcpyDeviceToHost, st));
-        QW_FLAT(cudaMemcpyAsync(&hmax, maxrow, 4, cudaMemcpyDeviceToHost, st));
-        QW_FLAT(cudaStreamSynchronize(st));
-        hs = *sim->h_st;
-        if (hs.status != QW_ST_ROW_OVERFLOW || attempt == 1 || !sim->opts.overflow_fallback) break;
-        /* a row of the result is longer than row_capacity: grow the buckets
-           (the gathered input is no longer needed) and store again */
-        const int32_t zero = 0;
-        QW_FLAT(cudaMemcpyAsync(status, &zero, 4, cudaMemcpyHostToDevice, st));
-        rc = grow_rows(sim, (int64_t)hmax);
-        if (rc != QW_OK) {
-            cleanup();
-            return rc;
-        }
-    }
-    QW_FLAT(qw_flat_finish(a, static_cast<double *>(norm), counts, st));
-    sim->launches += 1;
-    sim->cur = nxt;
-    sim->scale_slot ^= 1;
-    cleanup();
 #undef QW_FLAT
-    return check_status(sim, "walk step on the flat path");
+    const int rc = flat_store(sim, L, a, counts);
+    flat_release(sim, L);
+    return rc;
+}
+
+/* ---- register-faithful sub-operations (qw_flat.cu, 10-word keys) ---------- */
+
+/* One sub-operation (QW_FQ_*) on L.  The operators on the base registers are
+ * preceded by the check that every working register is 0. */
+static cudaError_t faithful_op(qw_sim *sim, FlatList &L, int op, FaithCounts &fc)
+{
+    const QwSimDev &d = sim->d;
+    cudaStream_t st = sim->stream;
+    int32_t *status = &sim->sc->status;
+    if (op >= QW_FQ_ADDR_COL && op <= QW_FQ_QRAM_VAL) return qw_faithful_op(d, L.K, L.M, op, status, st);
+    if (op < QW_FQ_R || op > QW_FQ_FREE_A) return cudaErrorInvalidValue;
+    cudaError_t e = qw_faithful_check_idle(d, L.K, L.M, status, st);
+    if (e != cudaSuccess) return e;
+    switch (op) {
+    case QW_FQ_R:
+        e = flat_stage(sim, L, 1);
+        fc.c[4] = L.M;
+        return e;
+    case QW_FQ_RDAG:
+        e = flat_stage(sim, L, 0);
+        fc.c[1] = L.M;
+        return e;
+    case QW_FQ_H:
+        e = flat_stage(sim, L, 2);
+        fc.c[fc.nh < 1 ? 2 : 3] = L.M;
+        fc.nh++;
+        return e;
+    case QW_FQ_P: return qw_flat_phase(d, L.K, L.A, L.M, st, L.kw);
+    case QW_FQ_S: return qw_flat_map(d, L.K, L.M, QW_FLAT_S, status, st, L.kw);
+    case QW_FQ_FREE_A: return qw_flat_map(d, L.K, L.M, QW_FLAT_A0, status, st, L.kw);
+    default: return cudaSuccess; /* QW_FQ_ALLOC_A: A is 0 wherever it is free */
+    }
+}
+
+static bool faithful_fits(const qw_sim *sim)
+{
+    return sim->d.ninst == 1 && qw_faithful_layout(sim->d, nullptr, nullptr) != 0;
+}
+
+/* One walk step in the register-faithful schedule (walk_variant 6): the
+ * QW_FQ_STEP sequence on the gathered list, the QLS read-out after the first
+ * H, the result stored as X_cur+1. */
+static int faithful_walk_step(qw_sim *sim, int readout)
+{
+    static const int32_t kStep[QW_FQ_STEP_LEN] = QW_FQ_STEP;
+    FlatList L;
+    FaithCounts fc;
+    QwStepArgs a = step_args(sim, QW_MODE_WALK_FAITHFUL);
+    a.qls_readout = readout;
+    cudaError_t e = flat_gather(sim, L, QW_FQ_KEY_WORDS);
+    fc.c[0] = L.M;
+    for (int i = 0; i < QW_FQ_STEP_LEN && e == cudaSuccess; ++i) {
+        e = faithful_op(sim, L, kStep[i], fc);
+        if (e == cudaSuccess && readout && kStep[i] == QW_FQ_H && fc.nh == 1)
+            e = qw_flat_readout(sim->d, L.K, L.A, L.M, a, sim->stream, L.kw);
+    }
+    if (e != cudaSuccess) {
+        flat_release(sim, L);
+        return cuda_fail(sim, e, "register-faithful walk step");
+    }
+    const int rc = flat_store(sim, L, a, fc.c);
+    flat_release(sim, L);
+    return rc;
+}
+
+static int faithful_session_closed(qw_sim *sim)
+{
+    return sim->fq_open ? fail(sim, QW_ERR_STATE, "a register-faithful session is open: call qw_faithful_end")
+                        : QW_OK;
+}
+
+extern "C" int qw_faithful_info(const qw_sim *sim, int32_t *addr_bits, int32_t *key_bits, int64_t *live_bits)
+{
+    if (!sim) return QW_ERR_ARG;
+    int aw = 0, bits = 0;
+    const int fits = qw_faithful_layout(sim->d, &aw, &bits);
+    if (addr_bits) *addr_bits = aw;
+    if (key_bits) *key_bits = bits;
+    /* the base registers (jc, j, b1, kc, k, b2: 4 nb + 2), A, the address,
+       left, right, mid, midval, flag, cl, ce and L + 1 frames */
+    if (live_bits)
+        *live_bits = 4 * (int64_t)sim->d.nb + 2 + 16 + aw + 3 * aw + 16 + 3 + (int64_t)(sim->d.L + 1) * (aw + 16 + 2);
+    return fits && sim->d.ninst == 1 ? QW_OK : QW_ERR_ARG;
+}
+
+extern "C" int qw_faithful_begin(qw_sim *sim)
+{
+    if (!sim) return QW_ERR_ARG;
+    if (!sim->has_state) return fail(sim, QW_ERR_STATE, "no state: call qw_state_init first");
+    int rc = faithful_session_closed(sim);
+    if (rc != QW_OK) return rc;
+    if (!faithful_fits(sim))
+        return fail(sim, QW_ERR_ARG, "register-faithful keys: one instance, and the working registers must fit "
+                                     "10 words with s <= 128");
+    rc = sync_walk(sim, "qw_faithful_begin");
+    if (rc != QW_OK) return rc;
+    cudaError_t e = flat_gather(sim, sim->fq, QW_FQ_KEY_WORDS);
+    if (e != cudaSuccess) {
+        flat_release(sim, sim->fq);
+        return cuda_fail(sim, e, "qw_faithful_begin");
+    }
+    sim->launches++;
+    sim->fq_open = true;
+    sim->fq_counts = FaithCounts{};
+    sim->fq_counts.c[0] = sim->fq.M;
+    return QW_OK;
+}
+
+extern "C" int qw_faithful_apply(qw_sim *sim, const int32_t *ops, int32_t nops)
+{
+    if (!sim) return QW_ERR_ARG;
+    if (!sim->fq_open) return fail(sim, QW_ERR_STATE, "no register-faithful session: call qw_faithful_begin");
+    if (nops < 0 || (nops > 0 && !ops)) return fail(sim, QW_ERR_ARG, "bad sub-operation list");
+    for (int32_t i = 0; i < nops; ++i)
+        if (ops[i] < QW_FQ_ADDR_COL || ops[i] > QW_FQ_FREE_A)
+            return fail(sim, QW_ERR_ARG, "unknown sub-operation code " + std::to_string(ops[i]));
+    for (int32_t i = 0; i < nops; ++i) {
+        cudaError_t e = faithful_op(sim, sim->fq, ops[i], sim->fq_counts);
+        if (e != cudaSuccess) return cuda_fail(sim, e, "qw_faithful_apply");
+        sim->launches++;
+    }
+    return check_status(sim, "qw_faithful_apply");
+}
+
+extern "C" int qw_faithful_export(qw_sim *sim, uint64_t *regs, double *amps, int64_t cap, int64_t *count)
+{
+    if (!sim || !count) return QW_ERR_ARG;
+    if (!sim->fq_open) return fail(sim, QW_ERR_STATE, "no register-faithful session: call qw_faithful_begin");
+    if (cap > 0 && (!regs || !amps)) return fail(sim, QW_ERR_ARG, "null output arrays");
+    const int64_t M = sim->fq.M;
+    *count = M;
+    if (M == 0 || cap <= 0) return QW_OK;
+    const size_t C = QW_FQ_COLS;
+    uint64_t *dt = nullptr;
+    QW_CUDA(sim, cudaMallocAsync((void **)&dt, (size_t)M * C * 8, sim->stream));
+    QW_CUDA(sim, qw_faithful_export(sim->d, sim->fq.K, M, dt, sim->stream));
+    sim->launches++;
+    std::vector<uint64_t> t((size_t)M * C);
+    std::vector<double2> a((size_t)M);
+    QW_CUDA(sim, cudaMemcpyAsync(t.data(), dt, (size_t)M * C * 8, cudaMemcpyDeviceToHost, sim->stream));
+    QW_CUDA(sim, cudaMemcpyAsync(a.data(), sim->fq.A, (size_t)M * 16, cudaMemcpyDeviceToHost, sim->stream));
+    QW_CUDA(sim, cudaFreeAsync(dt, sim->stream));
+    QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
+    std::vector<int64_t> order((size_t)M);
+    for (int64_t i = 0; i < M; ++i) order[(size_t)i] = i;
+    std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+        const uint64_t *p = t.data() + (size_t)x * C, *q = t.data() + (size_t)y * C;
+        for (size_t c = 0; c < C; ++c)
+            if (p[c] != q[c]) return p[c] < q[c];
+        return false;
+    });
+    const int64_t nout = std::min(M, cap);
+    for (int64_t i = 0; i < nout; ++i) {
+        const int64_t src = order[(size_t)i];
+        std::memcpy(regs + (size_t)i * C, t.data() + (size_t)src * C, C * 8);
+        amps[2 * i] = a[(size_t)src].x;
+        amps[2 * i + 1] = a[(size_t)src].y;
+    }
+    return QW_OK;
+}
+
+extern "C" int qw_faithful_end(qw_sim *sim, int32_t keep)
+{
+    if (!sim) return QW_ERR_ARG;
+    if (!sim->fq_open) return fail(sim, QW_ERR_STATE, "no register-faithful session: call qw_faithful_begin");
+    if (!keep) {
+        flat_release(sim, sim->fq);
+        sim->fq_open = false;
+        return QW_OK;
+    }
+    FlatList &L = sim->fq;
+    QW_CUDA(sim, qw_faithful_check_idle(sim->d, L.K, L.M, &sim->sc->status, sim->stream));
+    QW_CUDA(sim, qw_flat_map(sim->d, L.K, L.M, QW_FLAT_A0, &sim->sc->status, sim->stream, L.kw));
+    int rc = check_status(sim, "qw_faithful_end");
+    if (rc != QW_OK) return rc;
+    QwStepArgs a = step_args(sim, QW_MODE_WALK_FAITHFUL);
+    rc = flat_store(sim, L, a, sim->fq_counts.c);
+    flat_release(sim, L);
+    sim->fq_open = false;
+    return rc;
 }
 
 extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, const double *b_im,
                              int32_t n, int32_t apply_T)
 {
     if (!sim) return QW_ERR_ARG;
+    if (sim->fq_open) return faithful_session_closed(sim);
     if (inst < 0 || inst >= sim->d.ninst) return fail(sim, QW_ERR_ARG, "instance out of range");
     if (!b_re || n != sim->n_of[(size_t)inst]) return fail(sim, QW_ERR_ARG, "b must hold N values");
     /* |b> goes straight from the caller's arrays to the device (asynchronous
@@ -984,12 +1232,13 @@ static int capture_graph(qw_sim *sim, cudaGraphExec_t *out, bool qls)
 extern "C" int qw_enqueue_walk_steps(qw_sim *sim, int64_t nsteps)
 {
     if (!sim) return QW_ERR_ARG;
+    if (sim->fq_open) return faithful_session_closed(sim);
     if (nsteps < 0) return fail(sim, QW_ERR_ARG, "nsteps < 0");
     if (!sim->has_state) return fail(sim, QW_ERR_STATE, "no state: call qw_state_init first");
     if (nsteps > 0) sim->fresh_T = false;
     int64_t t = 0;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (sim->opts.graphs && sim->mode != QW_MODE_WALK_FLAT && sim->d.nparts == 1 && nsteps >= kGraphSteps &&
+    if (sim->opts.graphs && !host_staged(sim) && sim->d.nparts == 1 && nsteps >= kGraphSteps &&
         cudaStreamIsCapturing(sim->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
         cudaGraphExec_t &g = sim->gexec[sim->cur][sim->scale_slot];
         if (!g) {
@@ -1040,6 +1289,7 @@ extern "C" int qw_apply_walk_step(qw_sim *sim, int64_t nsteps)
 extern "C" int qw_autotune(qw_sim *sim, int32_t steps, int32_t *choice, double *us_per_step)
 {
     if (!sim || steps < 1) return QW_ERR_ARG;
+    if (sim->fq_open) return faithful_session_closed(sim);
     if (!sim->has_state) return fail(sim, QW_ERR_STATE, "no state: call qw_state_init first");
     if (sim->mode == QW_MODE_WALK_LITERAL) {
         if (choice) *choice = -1;
@@ -1133,6 +1383,7 @@ extern "C" int qw_apply_qls(qw_sim *sim, int32_t inst, const double *coeffs, int
                             double *y_out, double *psucc_out)
 {
     if (!sim) return QW_ERR_ARG;
+    if (sim->fq_open) return faithful_session_closed(sim);
     if (sim->d.ninst != 1 || inst != 0) return fail(sim, QW_ERR_ARG, "QLS needs a single-instance simulator");
     if (sim->d.nparts > 1) return fail(sim, QW_ERR_ARG, "QLS is not run on a partitioned walk");
     if (!coeffs || j0 < 0 || !y_out) return fail(sim, QW_ERR_ARG, "coeffs, j0 and y_out are required");
@@ -1154,7 +1405,7 @@ extern "C" int qw_apply_qls(qw_sim *sim, int32_t inst, const double *coeffs, int
     QW_CUDA(sim, cudaMemsetAsync(sim->qls_y, 0, (size_t)n * sizeof(double2), sim->stream));
     QW_CUDA(sim, cudaMemsetAsync(&sim->sc->qls_j, 0, sizeof(int64_t), sim->stream));
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    const bool graphs = sim->opts.graphs && sim->mode != QW_MODE_WALK_FLAT &&
+    const bool graphs = sim->opts.graphs && !host_staged(sim) &&
                         cudaStreamIsCapturing(sim->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
     int64_t j = 0, next_check = 1024;
     while (j <= j0) {
@@ -1352,6 +1603,7 @@ extern "C" int qw_state_import(qw_sim *sim, int32_t key_words, const uint64_t *k
                                int64_t count)
 {
     if (!sim) return QW_ERR_ARG;
+    if (sim->fq_open) return faithful_session_closed(sim);
     const int nb = sim->d.nb;
     if (key_words < 1 || key_words > 10 || key_words * 64 < 4 * nb + 34)
         return fail(sim, QW_ERR_ARG, "key_words too small for the packed register layout");

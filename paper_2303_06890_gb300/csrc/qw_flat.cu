@@ -24,9 +24,14 @@
 
 namespace {
 
-struct FKey {
-    uint64_t lo, hi;
+/* a packed register key of NW 64-bit words (2: the qw_state_export layout;
+   10: the register-faithful layout, the working registers above bit 128) */
+template <int NW> struct FKeyN {
+    uint64_t w[NW];
 };
+typedef FKeyN<2> FKey;
+constexpr int NW_FAITH = 10;
+typedef FKeyN<NW_FAITH> FKeyW;
 
 struct FLayout {
     int nb, pk, pkc, pb1, pj, pjc, pA, pinst;
@@ -46,27 +51,32 @@ __host__ __device__ inline FLayout flayout(int nb)
     return f;
 }
 
-__device__ __forceinline__ uint32_t fget(const FKey &k, int pos, int w)
+template <int NW>
+__device__ __forceinline__ uint64_t fget(const FKeyN<NW> &k, int pos, int w)
 {
-    uint64_t v;
-    if (pos >= 64) {
-        v = k.hi >> (pos - 64);
-    } else {
-        v = k.lo >> pos;
-        if (pos + w > 64) v |= k.hi << (64 - pos);
-    }
-    return (uint32_t)(v & ((1ull << w) - 1ull));
+    const int i = pos >> 6, o = pos & 63;
+    uint64_t v = k.w[i] >> o;
+    if (o + w > 64 && i + 1 < NW) v |= k.w[i + 1] << (64 - o);
+    return v & (w >= 64 ? ~0ull : ((1ull << w) - 1ull));
 }
 
-__device__ __forceinline__ void fput(FKey &k, int pos, int w, uint64_t v)
+/* OR v into a field (the field must be 0) */
+template <int NW>
+__device__ __forceinline__ void fput(FKeyN<NW> &k, int pos, int w, uint64_t v)
 {
-    v &= (1ull << w) - 1ull;
-    if (pos >= 64) {
-        k.hi |= v << (pos - 64);
-    } else {
-        k.lo |= v << pos;
-        if (pos + w > 64) k.hi |= v >> (64 - pos);
-    }
+    v &= (w >= 64 ? ~0ull : ((1ull << w) - 1ull));
+    const int i = pos >> 6, o = pos & 63;
+    k.w[i] |= v << o;
+    if (o + w > 64 && i + 1 < NW) k.w[i + 1] |= v >> (64 - o);
+}
+
+template <int NW>
+__device__ __forceinline__ void fclear(FKeyN<NW> &k, int pos, int w)
+{
+    const uint64_t m = (w >= 64 ? ~0ull : ((1ull << w) - 1ull));
+    const int i = pos >> 6, o = pos & 63;
+    k.w[i] &= ~(m << o);
+    if (o + w > 64 && i + 1 < NW) k.w[i + 1] &= ~(m >> (64 - o));
 }
 
 struct FRegs {
@@ -74,7 +84,8 @@ struct FRegs {
     Regs x; /* k, kc, A, b2 */
 };
 
-__device__ __forceinline__ FRegs fdecode(const FKey &k, const FLayout &L)
+template <int NW>
+__device__ __forceinline__ FRegs fdecode(const FKeyN<NW> &k, const FLayout &L)
 {
     FRegs r;
     r.x.b2 = fget(k, 0, 1);
@@ -88,9 +99,10 @@ __device__ __forceinline__ FRegs fdecode(const FKey &k, const FLayout &L)
     return r;
 }
 
-__device__ __forceinline__ FKey fencode(const FRegs &r, const FLayout &L)
+/* the base registers into k (their fields must be 0) */
+template <int NW>
+__device__ __forceinline__ void fencode_into(FKeyN<NW> &k, const FRegs &r, const FLayout &L)
 {
-    FKey k = {0ull, 0ull};
     fput(k, 0, 1, r.x.b2);
     fput(k, L.pk, L.nb, r.x.k);
     fput(k, L.pkc, L.nb, r.x.kc);
@@ -99,7 +111,26 @@ __device__ __forceinline__ FKey fencode(const FRegs &r, const FLayout &L)
     fput(k, L.pjc, L.nb, r.jc);
     fput(k, L.pA, 16, r.x.A);
     fput(k, L.pinst, 16, r.inst);
+}
+
+__device__ __forceinline__ FKey fencode(const FRegs &r, const FLayout &L)
+{
+    FKey k;
+    k.w[0] = k.w[1] = 0ull;
+    fencode_into(k, r, L);
     return k;
+}
+
+/* the base registers of a wider key rewritten, its other bits kept */
+template <int NW>
+__device__ __forceinline__ void frewrite(FKeyN<NW> &k, const FRegs &r, const FLayout &L)
+{
+    const int bits = L.pinst + 16;
+    for (int i = 0; i < NW && i * 64 < bits; ++i) {
+        const int hi = bits - i * 64;
+        k.w[i] &= hi >= 64 ? 0ull : ~((1ull << hi) - 1ull);
+    }
+    fencode_into(k, r, L);
 }
 
 /* The row descriptor of a branch, reading its QRAM row straight from the
@@ -124,27 +155,31 @@ __device__ __forceinline__ Row frow(const QwSimDev &d, const FRegs &f)
  * b2 (the low L + 1 bits rotate by one) */
 constexpr int ORDER_R = 0, ORDER_H = 1;
 
+/* word 0 of the key with the target's bits moved below the others */
 template <int ORDER>
-__device__ __forceinline__ FKey permuted(FKey k, int L)
+__device__ __forceinline__ uint64_t permuted0(uint64_t w0, int L)
 {
     if (ORDER == ORDER_H && L > 0) {
         const uint64_t m = (1ull << L) - 1ull;
-        k.lo = (k.lo & ~((m << 1) | 1ull)) | ((k.lo >> 1) & m) | ((k.lo & 1ull) << L);
+        w0 = (w0 & ~((m << 1) | 1ull)) | ((w0 >> 1) & m) | ((w0 & 1ull) << L);
     }
-    return k;
+    return w0;
 }
 
-template <int ORDER>
-__device__ __forceinline__ bool same_group(const FKey &a, const FKey &b, int L)
+template <int ORDER, int NW>
+__device__ __forceinline__ bool same_group(const FKeyN<NW> &a, const FKeyN<NW> &b, int L)
 {
     const uint64_t m = ORDER == ORDER_R ? 1ull : (((1ull << L) - 1ull) << 1);
-    return a.hi == b.hi && (a.lo & ~m) == (b.lo & ~m);
+    bool eq = (a.w[0] & ~m) == (b.w[0] & ~m);
+#pragma unroll
+    for (int i = 1; i < NW; ++i) eq = eq && a.w[i] == b.w[i];
+    return eq;
 }
 
 /* ---- gather, maps, phase ------------------------------------------------------ */
 
-template <typename AmpT>
-__global__ void k_f_gather(QwSimDev d, QwBufDev buf, const double *scale, FKey *keys, double2 *amps,
+template <typename AmpT, int NW>
+__global__ void k_f_gather(QwSimDev d, QwBufDev buf, const double *scale, FKeyN<NW> *keys, double2 *amps,
                            unsigned long long *counter, int64_t cap)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -168,7 +203,11 @@ __global__ void k_f_gather(QwSimDev d, QwBufDev buf, const double *scale, FKey *
             f.j = r.j;
             f.b1 = r.b1;
             f.x = decode_r(buf.key[slot], d.nb);
-            keys[p] = fencode(f, L);
+            FKeyN<NW> k;
+#pragma unroll
+            for (int t = 0; t < NW; ++t) k.w[t] = 0ull;
+            fencode_into(k, f, L);
+            keys[p] = k;
             amps[p] = cscale(sc, load_amp<AmpT>(buf.amp, slot));
         }
     }
@@ -177,11 +216,13 @@ __global__ void k_f_gather(QwSimDev d, QwBufDev buf, const double *scale, FKey *
 /* op codes of k_f_map, applied from the lowest 4 bits up */
 constexpr int F_OSDAG = 1, F_OA = 2, F_OS = 3, F_S = 4, F_A0 = 5;
 
-__global__ void k_f_map(QwSimDev d, FKey *keys, int64_t M, uint32_t ops, int32_t *status)
+template <int NW>
+__global__ void k_f_map(QwSimDev d, FKeyN<NW> *keys, int64_t M, uint32_t ops, int32_t *status)
 {
     const FLayout L = flayout(d.nb);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        FRegs f = fdecode(keys[i], L);
+        FKeyN<NW> k = keys[i];
+        FRegs f = fdecode(k, L);
         for (uint32_t o = ops; o != 0; o >>= 4) {
             const uint32_t op = o & 15u;
             const Row r = frow(d, f);
@@ -200,18 +241,227 @@ __global__ void k_f_map(QwSimDev d, FKey *keys, int64_t M, uint32_t ops, int32_t
                 f.x.b2 = b1;
             }
         }
-        keys[i] = fencode(f, L);
+        frewrite(k, f, L);
+        keys[i] = k;
     }
 }
 
 /* P = 2 Pi - 1 (Eq. (impl)): the sign flips unless b1, k, b2, jc, kc are 0 */
-__global__ void k_f_phase(QwSimDev d, const FKey *keys, double2 *amps, int64_t M)
+template <int NW>
+__global__ void k_f_phase(QwSimDev d, const FKeyN<NW> *keys, double2 *amps, int64_t M)
 {
     const FLayout L = flayout(d.nb);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
         const FRegs f = fdecode(keys[i], L);
         const bool zero = f.b1 == 0 && f.x.k == 0 && f.x.b2 == 0 && f.jc == 0 && f.x.kc == 0;
         if (!zero) amps[i] = cneg(amps[i]);
+    }
+}
+
+/* ---- register-faithful sub-operations (10-word keys) -------------------------- */
+/*
+ * The working registers of O_s' (its QRAM address, computed out of place:
+ * Eq. "Newprocess"), of O_A' and of the quantum binary search (Alg. 1: left,
+ * right, mid, midval, the flag and the two comparison bits, and the push/pop
+ * garbage stack of (mid, midval, cl, ce) frames, one per probe) held in each
+ * branch's key between the sub-operations, above bit 128:
+ *   addr, left, right, mid (aw bits each), midval (16), flag, cl, ce (1 each),
+ *   then L + 1 frames of mid (aw), midval (16), cl, ce.
+ * Addresses follow the QRAM of Fig. 1: the value segment [0, N s), the column
+ * segment [N s, 2 N s), row j's slot l at j s + l; a read outside its segment
+ * gives 0.
+ */
+struct FaithLayout {
+    int aw;
+    int p_addr, p_left, p_right, p_mid, p_midval, p_flag, p_cl, p_ce, p_stk, frame;
+};
+
+/* sub-operation codes (the same numbering as the oracle's) */
+constexpr int FQ_ADDR_COL = 1, FQ_QRAM_COL = 2, FQ_QBS_FWD = 3, FQ_QBS_BWD = 4, FQ_SWAP = 5, FQ_ADDR_VAL = 6,
+              FQ_QRAM_VAL = 7;
+
+__device__ __forceinline__ uint64_t fq_qram(const QwSimDev &d, uint64_t addr, bool col_segment)
+{
+    const uint64_t ns = (uint64_t)d.n_single * (uint64_t)d.s;
+    if (col_segment) {
+        if (addr < ns || addr >= 2 * ns) return 0;
+        return (uint64_t)(__ldg(d.img + (addr - ns)) >> 16);
+    }
+    if (addr >= ns) return 0;
+    return (uint64_t)(__ldg(d.img + addr) & 0xffffu);
+}
+
+__global__ void k_fq(QwSimDev d, FKeyW *keys, int64_t M, int op, FaithLayout F, int32_t *status)
+{
+    const FLayout L = flayout(d.nb);
+    const int aw = F.aw;
+    const uint64_t ns = (uint64_t)d.n_single * (uint64_t)d.s;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        FKeyW k = keys[i];
+        FRegs f = fdecode(k, L);
+        uint64_t addr = fget(k, F.p_addr, aw);
+        const uint64_t offset = ns + (uint64_t)f.j * (uint64_t)d.s;
+        if (op == FQ_ADDR_COL) {
+            addr ^= offset + f.x.k;
+        } else if (op == FQ_QRAM_COL) {
+            f.x.kc ^= (uint32_t)fq_qram(d, addr, true);
+        } else if (op == FQ_ADDR_VAL) {
+            if (f.jc == 0 && f.x.kc == 0) addr ^= (uint64_t)f.j * (uint64_t)d.s + f.x.k;
+        } else if (op == FQ_QRAM_VAL) {
+            if (f.jc == 0 && f.x.kc == 0) f.x.A ^= (uint32_t)fq_qram(d, addr, false);
+        } else if (op == FQ_SWAP) {
+            const uint32_t t = f.x.k;
+            f.x.k = f.x.kc;
+            f.x.kc = t;
+        } else if (op == FQ_QBS_FWD || op == FQ_QBS_BWD) {
+            uint64_t left = fget(k, F.p_left, aw), right = fget(k, F.p_right, aw);
+            uint64_t mid = fget(k, F.p_mid, aw), midval = fget(k, F.p_midval, 16);
+            uint32_t flag = (uint32_t)fget(k, F.p_flag, 1), cl = (uint32_t)fget(k, F.p_cl, 1);
+            uint32_t ce = (uint32_t)fget(k, F.p_ce, 1);
+            const uint64_t target = f.x.kc;
+            if (op == FQ_QBS_FWD) { /* Alg. 1's loop, every probe's registers pushed */
+                left ^= offset;
+                right ^= left + (uint64_t)d.s;
+                flag ^= 1u;
+                for (int it = 0; it <= d.L; ++it) {
+                    if (flag) mid ^= (left + right) / 2;
+                    if (flag) midval ^= fq_qram(d, mid, true);
+                    if (flag) {
+                        cl ^= (midval < target) ? 1u : 0u;
+                        ce ^= (midval == target) ? 1u : 0u;
+                    }
+                    if (ce) f.x.k ^= (uint32_t)(mid - offset);
+                    if (ce) flag ^= 1u;
+                    if (flag && cl) {
+                        const uint64_t t = mid;
+                        mid = left;
+                        left = t;
+                    }
+                    if (flag) cl ^= 1u;
+                    if (flag && cl) {
+                        const uint64_t t = mid;
+                        mid = right;
+                        right = t;
+                    }
+                    const int pf = F.p_stk + it * F.frame; /* push: the frame takes them, zeros stay */
+                    fput(k, pf, aw, mid);
+                    fput(k, pf + aw, 16, midval);
+                    fput(k, pf + aw + 16, 1, cl);
+                    fput(k, pf + aw + 17, 1, ce);
+                    mid = midval = 0;
+                    cl = ce = 0u;
+                }
+            } else { /* the loop undone in reverse: pop, then every step inverted */
+                for (int it = d.L; it >= 0; --it) {
+                    const int pf = F.p_stk + it * F.frame;
+                    mid = fget(k, pf, aw);
+                    midval = fget(k, pf + aw, 16);
+                    cl = (uint32_t)fget(k, pf + aw + 16, 1);
+                    ce = (uint32_t)fget(k, pf + aw + 17, 1);
+                    fclear(k, pf, F.frame);
+                    if (flag && cl) {
+                        const uint64_t t = mid;
+                        mid = right;
+                        right = t;
+                    }
+                    if (flag) cl ^= 1u;
+                    if (flag && cl) {
+                        const uint64_t t = mid;
+                        mid = left;
+                        left = t;
+                    }
+                    if (ce) flag ^= 1u;
+                    if (flag) {
+                        cl ^= (midval < target) ? 1u : 0u;
+                        ce ^= (midval == target) ? 1u : 0u;
+                    }
+                    if (flag) midval ^= fq_qram(d, mid, true);
+                    if (flag) mid ^= (left + right) / 2;
+                    if (mid != 0 || midval != 0 || cl != 0 || ce != 0) atomicOr(status, QW_ST_ANCILLA);
+                    mid = midval = 0;
+                    cl = ce = 0u;
+                }
+                flag ^= 1u;
+                right ^= left + (uint64_t)d.s;
+                left ^= offset;
+                if (left != 0 || right != 0 || flag != 0) atomicOr(status, QW_ST_ANCILLA);
+                left = right = 0;
+                flag = 0u;
+            }
+            fclear(k, F.p_left, aw);
+            fclear(k, F.p_right, aw);
+            fclear(k, F.p_mid, aw);
+            fclear(k, F.p_midval, 16);
+            fclear(k, F.p_flag, 3);
+            fput(k, F.p_left, aw, left);
+            fput(k, F.p_right, aw, right);
+            fput(k, F.p_mid, aw, mid);
+            fput(k, F.p_midval, 16, midval);
+            fput(k, F.p_flag, 1, flag);
+            fput(k, F.p_cl, 1, cl);
+            fput(k, F.p_ce, 1, ce);
+        }
+        fclear(k, F.p_addr, aw);
+        fput(k, F.p_addr, aw, addr);
+        frewrite(k, f, L);
+        keys[i] = k;
+    }
+}
+
+/* the working registers must be 0 (an interference op, P, S or the store) */
+__global__ void k_fq_check_idle(const FKeyW *keys, int64_t M, int from_bit, int32_t *status)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const FKeyW k = keys[i];
+        bool any = false;
+        for (int t = from_bit >> 6; t < NW_FAITH; ++t) {
+            uint64_t v = k.w[t];
+            if (t == (from_bit >> 6)) v &= ~((1ull << (from_bit & 63)) - 1ull);
+            any = any || v != 0ull;
+        }
+        if (any) atomicOr(status, QW_ST_ANCILLA);
+    }
+}
+
+/* a list as a table of registers: QW_FQ_COLS values per branch in the order
+   inst, jc, j, b1, kc, k, b2, A, addr, left, right, mid, midval, flag, cl,
+   ce, then QW_FQ_FRAMES frames of (mid, midval, cl, ce) */
+__global__ void k_fq_export(QwSimDev d, const FKeyW *keys, int64_t M, FaithLayout F, uint64_t *table)
+{
+    const FLayout L = flayout(d.nb);
+    const int aw = F.aw;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const FKeyW k = keys[i];
+        const FRegs f = fdecode(k, L);
+        uint64_t *t = table + i * QW_FQ_COLS;
+        t[0] = f.inst;
+        t[1] = f.jc;
+        t[2] = f.j;
+        t[3] = f.b1;
+        t[4] = f.x.kc;
+        t[5] = f.x.k;
+        t[6] = f.x.b2;
+        t[7] = f.x.A;
+        t[8] = fget(k, F.p_addr, aw);
+        t[9] = fget(k, F.p_left, aw);
+        t[10] = fget(k, F.p_right, aw);
+        t[11] = fget(k, F.p_mid, aw);
+        t[12] = fget(k, F.p_midval, 16);
+        t[13] = fget(k, F.p_flag, 1);
+        t[14] = fget(k, F.p_cl, 1);
+        t[15] = fget(k, F.p_ce, 1);
+        for (int it = 0; it < QW_FQ_FRAMES; ++it) {
+            uint64_t *fr = t + 16 + 4 * it;
+            if (it <= d.L) {
+                const int pf = F.p_stk + it * F.frame;
+                fr[0] = fget(k, pf, aw);
+                fr[1] = fget(k, pf + aw, 16);
+                fr[2] = fget(k, pf + aw + 16, 1);
+                fr[3] = fget(k, pf + aw + 17, 1);
+            } else {
+                fr[0] = fr[1] = fr[2] = fr[3] = 0ull;
+            }
+        }
     }
 }
 
@@ -302,28 +552,34 @@ __global__ void k_scan_apply(const uint32_t *in, int64_t n, const uint32_t *sums
 
 /* ---- radix sort ------------------------------------------------------------------ */
 
-template <int ORDER>
-__global__ void k_f_orand(const FKey *keys, int64_t M, int L, unsigned long long *acc)
+template <int ORDER, int NW>
+__global__ void k_f_orand(const FKeyN<NW> *keys, int64_t M, int L, unsigned long long *acc)
 {
-    uint64_t ol = 0, oh = 0, al = ~0ull, ah = ~0ull;
+    uint64_t ov[NW], av[NW];
+#pragma unroll
+    for (int t = 0; t < NW; ++t) {
+        ov[t] = 0ull;
+        av[t] = ~0ull;
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        const FKey k = permuted<ORDER>(keys[i], L);
-        ol |= k.lo;
-        oh |= k.hi;
-        al &= k.lo;
-        ah &= k.hi;
+        FKeyN<NW> k = keys[i];
+        k.w[0] = permuted0<ORDER>(k.w[0], L);
+#pragma unroll
+        for (int t = 0; t < NW; ++t) {
+            ov[t] |= k.w[t];
+            av[t] &= k.w[t];
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        ol |= __shfl_xor_sync(FULL, ol, o);
-        oh |= __shfl_xor_sync(FULL, oh, o);
-        al &= __shfl_xor_sync(FULL, al, o);
-        ah &= __shfl_xor_sync(FULL, ah, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicOr(acc + 0, (unsigned long long)ol);
-        atomicOr(acc + 1, (unsigned long long)oh);
-        atomicAnd(acc + 2, (unsigned long long)al);
-        atomicAnd(acc + 3, (unsigned long long)ah);
+#pragma unroll
+    for (int t = 0; t < NW; ++t) {
+        for (int o = 16; o > 0; o >>= 1) {
+            ov[t] |= __shfl_xor_sync(FULL, ov[t], o);
+            av[t] &= __shfl_xor_sync(FULL, av[t], o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicOr(acc + t, (unsigned long long)ov[t]);
+            atomicAnd(acc + NW + t, (unsigned long long)av[t]);
+        }
     }
 }
 
@@ -332,10 +588,10 @@ __global__ void k_f_orand(const FKey *keys, int64_t M, int L, unsigned long long
  * block]; otherwise scatter to offs[digit * nblk + block] + the item's rank
  * among the equal digits before it (rounds of 256 items in order, warps in
  * order, lanes in order). */
-template <int ORDER>
-__global__ void __launch_bounds__(256) k_f_radix(const FKey *kin, const double2 *ain, FKey *kout, double2 *aout,
-                                                 int64_t M, int64_t tile, int shift, int L, const uint32_t *offs,
-                                                 uint32_t *hist, int count_only)
+template <int ORDER, int NW>
+__global__ void __launch_bounds__(256) k_f_radix(const FKeyN<NW> *kin, const double2 *ain, FKeyN<NW> *kout,
+                                                 double2 *aout, int64_t M, int64_t tile, int shift, int L,
+                                                 const uint32_t *offs, uint32_t *hist, int count_only)
 {
     __shared__ uint32_t wc[8][16];
     __shared__ uint32_t run[16];
@@ -347,12 +603,12 @@ __global__ void __launch_bounds__(256) k_f_radix(const FKey *kin, const double2 
     for (int64_t base = lo; base < hi; base += 256) {
         const int64_t i = base + threadIdx.x;
         const bool act = i < hi;
-        FKey k = {0ull, 0ull};
         int dig = 16;
         if (act) {
-            k = kin[i];
-            const FKey p = permuted<ORDER>(k, L);
-            dig = (int)((shift < 64 ? (p.lo >> shift) : (p.hi >> (shift - 64))) & 15ull);
+            const int wi = shift >> 6;
+            uint64_t wv = kin[i].w[wi];
+            if (wi == 0) wv = permuted0<ORDER>(wv, L);
+            dig = (int)((wv >> (shift & 63)) & 15ull);
         }
         const unsigned m = __match_any_sync(FULL, dig);
         const int rank = __popc(m & ((1u << lane) - 1u));
@@ -374,7 +630,7 @@ __global__ void __launch_bounds__(256) k_f_radix(const FKey *kin, const double2 
         }
         __syncthreads();
         if (act && !count_only) {
-            kout[dest] = k;
+            kout[dest] = kin[i];
             aout[dest] = ain[i];
         }
     }
@@ -386,19 +642,19 @@ __global__ void __launch_bounds__(256) k_f_radix(const FKey *kin, const double2 
 /* R (DAG = false) or R^dag on b2-pairs (sorted in ORDER_R): the head of each
  * pair writes both outputs at 2 i (b2 = 0) and 2 i + 1 (b2 = 1) with their
  * keep flags; R = [[f, -g], [g, conj f]] (Alg. T~ and the footnote of Sec. IV). */
-template <bool DAG>
-__global__ void k_f_rot(QwSimDev d, const FKey *keys, const double2 *amps, int64_t M, FKey *okeys, double2 *oamps,
-                        uint32_t *flags)
+template <bool DAG, int NW>
+__global__ void k_f_rot(QwSimDev d, const FKeyN<NW> *keys, const double2 *amps, int64_t M, FKeyN<NW> *okeys,
+                        double2 *oamps, uint32_t *flags)
 {
     const FLayout L = flayout(d.nb);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        const FKey k = keys[i];
+        const FKeyN<NW> k = keys[i];
         const bool head = i == 0 || !same_group<ORDER_R>(keys[i - 1], k, 0);
         flags[2 * i] = 0u;
         flags[2 * i + 1] = 0u;
         if (!head) continue;
         double2 a0 = make_double2(0, 0), a1 = make_double2(0, 0);
-        if ((k.lo & 1ull) == 0) {
+        if ((k.w[0] & 1ull) == 0) {
             a0 = amps[i];
             if (i + 1 < M && same_group<ORDER_R>(k, keys[i + 1], 0)) a1 = amps[i + 1];
         } else {
@@ -416,10 +672,10 @@ __global__ void k_f_rot(QwSimDev d, const FKey *keys, const double2 *amps, int64
             o0 = cadd(cmul(cconj(fv), a0), cscale(g, a1));
             o1 = csub(cmul(fv, a1), cscale(g, a0));
         }
-        FKey k0 = k;
-        k0.lo &= ~1ull;
-        FKey k1 = k0;
-        k1.lo |= 1ull;
+        FKeyN<NW> k0 = k;
+        k0.w[0] &= ~1ull;
+        FKeyN<NW> k1 = k0;
+        k1.w[0] |= 1ull;
         okeys[2 * i] = k0;
         okeys[2 * i + 1] = k1;
         oamps[2 * i] = o0;
@@ -431,13 +687,14 @@ __global__ void k_f_rot(QwSimDev d, const FKey *keys, const double2 *amps, int64
 
 /* H on the low L bits of k (sorted in ORDER_H): the head of each group
  * writes the s outputs (1/sqrt s) sum_v (-1)^(u.v) a_v at s i + u. */
-__global__ void k_f_hadamard(QwSimDev d, const FKey *keys, const double2 *amps, int64_t M, FKey *okeys,
+template <int NW>
+__global__ void k_f_hadamard(QwSimDev d, const FKeyN<NW> *keys, const double2 *amps, int64_t M, FKeyN<NW> *okeys,
                              double2 *oamps, uint32_t *flags)
 {
     const int L = d.L, s = d.s;
     const uint64_t lowm = (((uint64_t)s - 1ull) << 1);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        const FKey k = keys[i];
+        const FKeyN<NW> k = keys[i];
         const bool head = i == 0 || !same_group<ORDER_H>(keys[i - 1], k, L);
         for (int u = 0; u < s; ++u) flags[(int64_t)s * i + u] = 0u;
         if (!head) continue;
@@ -446,13 +703,13 @@ __global__ void k_f_hadamard(QwSimDev d, const FKey *keys, const double2 *amps, 
         for (int u = 0; u < s; ++u) {
             double2 o = make_double2(0, 0);
             for (int64_t m = i; m < e; ++m) {
-                const uint32_t v = (uint32_t)((keys[m].lo >> 1) & (uint64_t)(s - 1));
+                const uint32_t v = (uint32_t)((keys[m].w[0] >> 1) & (uint64_t)(s - 1));
                 const double2 a = amps[m];
                 o = (__popc((uint32_t)u & v) & 1) ? csub(o, a) : cadd(o, a);
             }
             o = cscale(d.inv_sqrt_s, o);
-            FKey ko = k;
-            ko.lo = (ko.lo & ~lowm) | ((uint64_t)u << 1);
+            FKeyN<NW> ko = k;
+            ko.w[0] = (ko.w[0] & ~lowm) | ((uint64_t)u << 1);
             okeys[(int64_t)s * i + u] = ko;
             oamps[(int64_t)s * i + u] = o;
             flags[(int64_t)s * i + u] = keep(o, d.tau2) ? 1u : 0u;
@@ -461,8 +718,9 @@ __global__ void k_f_hadamard(QwSimDev d, const FKey *keys, const double2 *amps, 
 }
 
 /* the "clearing" step: kept entries to their scanned positions */
-__global__ void k_f_compact(const FKey *keys, const double2 *amps, const uint32_t *flags, const uint32_t *pos,
-                            int64_t n, FKey *okeys, double2 *oamps)
+template <int NW>
+__global__ void k_f_compact(const FKeyN<NW> *keys, const double2 *amps, const uint32_t *flags, const uint32_t *pos,
+                            int64_t n, FKeyN<NW> *okeys, double2 *oamps)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (!flags[i]) continue;
@@ -472,7 +730,8 @@ __global__ void k_f_compact(const FKey *keys, const double2 *amps, const uint32_
 }
 
 /* QLS read-out after T~^dag's H: Y[j] += a_j * (the flag-0 amplitude of row j) */
-__global__ void k_f_readout(QwSimDev d, const FKey *keys, const double2 *amps, int64_t M, QwStepArgs a)
+template <int NW>
+__global__ void k_f_readout(QwSimDev d, const FKeyN<NW> *keys, const double2 *amps, int64_t M, QwStepArgs a)
 {
     const FLayout L = flayout(d.nb);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
@@ -487,8 +746,8 @@ __global__ void k_f_readout(QwSimDev d, const FKey *keys, const double2 *amps, i
 }
 
 /* the output into the row buckets, |stored a|^2 summed per block into *norm */
-template <typename AmpT>
-__global__ void k_f_scatter(QwSimDev d, QwBufDev out, const FKey *keys, const double2 *amps, int64_t M,
+template <typename AmpT, int NW>
+__global__ void k_f_scatter(QwSimDev d, QwBufDev out, const FKeyN<NW> *keys, const double2 *amps, int64_t M,
                             int32_t *status, unsigned int *maxrow, double *norm)
 {
     __shared__ double ws[8];
@@ -550,32 +809,49 @@ int grid_for(int64_t n, int threads)
     return (int)(g < 1 ? 1 : g);
 }
 
+template <int NW>
+cudaError_t flat_sort_t(const QwSimDev &d, void *keys, double2 *amps, void *tmpk, double2 *tmpa, int64_t M, int order,
+                        uint32_t *work, cudaStream_t st);
+
 } // namespace
 
 /* ---- launchers ------------------------------------------------------------------------ */
+/* kw: the key words (2, the export layout; 10, the register-faithful layout) */
 
 cudaError_t qw_flat_gather(const QwSimDev &d, const QwBufDev &buf, int fp32, const double *scale, void *keys,
-                           double2 *amps, unsigned long long *counter, int64_t cap, cudaStream_t st)
+                           double2 *amps, unsigned long long *counter, int64_t cap, cudaStream_t st, int kw)
 {
     const int grid = 4 * qw_sm_count();
-    if (fp32)
-        k_f_gather<float2><<<grid, 256, 0, st>>>(d, buf, scale, static_cast<FKey *>(keys), amps, counter, cap);
-    else
-        k_f_gather<double2><<<grid, 256, 0, st>>>(d, buf, scale, static_cast<FKey *>(keys), amps, counter, cap);
+    if (kw == NW_FAITH) {
+        if (fp32)
+            k_f_gather<float2, NW_FAITH><<<grid, 256, 0, st>>>(d, buf, scale, static_cast<FKeyW *>(keys), amps,
+                                                               counter, cap);
+        else
+            k_f_gather<double2, NW_FAITH><<<grid, 256, 0, st>>>(d, buf, scale, static_cast<FKeyW *>(keys), amps,
+                                                                counter, cap);
+    } else if (fp32) {
+        k_f_gather<float2, 2><<<grid, 256, 0, st>>>(d, buf, scale, static_cast<FKey *>(keys), amps, counter, cap);
+    } else {
+        k_f_gather<double2, 2><<<grid, 256, 0, st>>>(d, buf, scale, static_cast<FKey *>(keys), amps, counter, cap);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t qw_flat_map(const QwSimDev &d, void *keys, int64_t M, uint32_t ops, int32_t *status, cudaStream_t st)
+cudaError_t qw_flat_map(const QwSimDev &d, void *keys, int64_t M, uint32_t ops, int32_t *status, cudaStream_t st,
+                        int kw)
 {
     if (M <= 0) return cudaSuccess;
-    k_f_map<<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<FKey *>(keys), M, ops, status);
+    if (kw == NW_FAITH) k_f_map<NW_FAITH><<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<FKeyW *>(keys), M, ops, status);
+    else k_f_map<2><<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<FKey *>(keys), M, ops, status);
     return cudaGetLastError();
 }
 
-cudaError_t qw_flat_phase(const QwSimDev &d, const void *keys, double2 *amps, int64_t M, cudaStream_t st)
+cudaError_t qw_flat_phase(const QwSimDev &d, const void *keys, double2 *amps, int64_t M, cudaStream_t st, int kw)
 {
     if (M <= 0) return cudaSuccess;
-    k_f_phase<<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<const FKey *>(keys), amps, M);
+    if (kw == NW_FAITH)
+        k_f_phase<NW_FAITH><<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<const FKeyW *>(keys), amps, M);
+    else k_f_phase<2><<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<const FKey *>(keys), amps, M);
     return cudaGetLastError();
 }
 
@@ -597,14 +873,16 @@ cudaError_t qw_flat_scan(const uint32_t *in, int64_t n, uint32_t *sums, uint32_t
 size_t qw_flat_sort_words(int64_t M)
 {
     const int64_t nblk = M < 1 ? 1 : (M + 4095) / 4096 < 1024 ? (M + 4095) / 4096 : 1024;
-    return (size_t)(16 * nblk) * 2 + qw_flat_scan_words(16 * nblk) + 12;
+    return (size_t)(16 * nblk) * 2 + qw_flat_scan_words(16 * nblk) + 4 * NW_FAITH + 8;
 }
 
+namespace {
 /* Stable sort of (keys, amps) by the permuted key of `order` (0: R, 1: H);
  * tmpk/tmpa hold M entries each; the result is left in keys/amps.  Digits
  * equal on every key are skipped (one synchronisation reads them). */
-cudaError_t qw_flat_sort(const QwSimDev &d, void *keys, double2 *amps, void *tmpk, double2 *tmpa, int64_t M,
-                         int order, uint32_t *work, cudaStream_t st)
+template <int NW>
+cudaError_t flat_sort_t(const QwSimDev &d, void *keys, double2 *amps, void *tmpk, double2 *tmpa, int64_t M, int order,
+                        uint32_t *work, cudaStream_t st)
 {
     if (M <= 1) return cudaSuccess;
     const int L = d.L;
@@ -616,39 +894,43 @@ cudaError_t qw_flat_sort(const QwSimDev &d, void *keys, double2 *amps, void *tmp
     uint32_t *hist = work, *offs = work + 16 * nblk, *sums = offs + 16 * nblk;
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(
         reinterpret_cast<uintptr_t>(sums + qw_flat_scan_words(16 * nblk) + 3) & ~(uintptr_t)7);
-    const unsigned long long init[4] = {0ull, 0ull, ~0ull, ~0ull};
+    unsigned long long init[2 * NW];
+    for (int t = 0; t < NW; ++t) {
+        init[t] = 0ull;
+        init[NW + t] = ~0ull;
+    }
     cudaError_t e = cudaMemcpyAsync(acc, init, sizeof init, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
-    if (order == ORDER_R) k_f_orand<ORDER_R><<<grid_for(M, 256), 256, 0, st>>>(static_cast<FKey *>(keys), M, L, acc);
-    else k_f_orand<ORDER_H><<<grid_for(M, 256), 256, 0, st>>>(static_cast<FKey *>(keys), M, L, acc);
-    unsigned long long h[4];
+    FKeyN<NW> *ka = static_cast<FKeyN<NW> *>(keys), *kb = static_cast<FKeyN<NW> *>(tmpk);
+    if (order == ORDER_R) k_f_orand<ORDER_R, NW><<<grid_for(M, 256), 256, 0, st>>>(ka, M, L, acc);
+    else k_f_orand<ORDER_H, NW><<<grid_for(M, 256), 256, 0, st>>>(ka, M, L, acc);
+    unsigned long long h[2 * NW];
     if ((e = cudaMemcpyAsync(h, acc, sizeof h, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-    const uint64_t vlo = h[0] ^ h[2], vhi = h[1] ^ h[3];
-    FKey *ka = static_cast<FKey *>(keys), *kb = static_cast<FKey *>(tmpk);
     double2 *aa = amps, *ab = tmpa;
-    for (int shift = 0; shift < 128; shift += 4) {
-        const uint64_t var = shift < 64 ? (vlo >> shift) & 15ull : (vhi >> (shift - 64)) & 15ull;
+    for (int shift = 0; shift < 64 * NW; shift += 4) {
+        const uint64_t var = ((h[shift >> 6] ^ h[NW + (shift >> 6)]) >> (shift & 63)) & 15ull;
         if (!var) continue;
         if (order == ORDER_R)
-            k_f_radix<ORDER_R><<<(unsigned)nblk, 256, 0, st>>>(ka, aa, kb, ab, M, tile, shift, L, nullptr, hist, 1);
+            k_f_radix<ORDER_R, NW><<<(unsigned)nblk, 256, 0, st>>>(ka, aa, kb, ab, M, tile, shift, L, nullptr, hist, 1);
         else
-            k_f_radix<ORDER_H><<<(unsigned)nblk, 256, 0, st>>>(ka, aa, kb, ab, M, tile, shift, L, nullptr, hist, 1);
+            k_f_radix<ORDER_H, NW><<<(unsigned)nblk, 256, 0, st>>>(ka, aa, kb, ab, M, tile, shift, L, nullptr, hist, 1);
         if ((e = qw_flat_scan(hist, 16 * nblk, sums, offs, st)) != cudaSuccess) return e;
         if (order == ORDER_R)
-            k_f_radix<ORDER_R><<<(unsigned)nblk, 256, 0, st>>>(ka, aa, kb, ab, M, tile, shift, L, offs, hist, 0);
+            k_f_radix<ORDER_R, NW><<<(unsigned)nblk, 256, 0, st>>>(ka, aa, kb, ab, M, tile, shift, L, offs, hist, 0);
         else
-            k_f_radix<ORDER_H><<<(unsigned)nblk, 256, 0, st>>>(ka, aa, kb, ab, M, tile, shift, L, offs, hist, 0);
+            k_f_radix<ORDER_H, NW><<<(unsigned)nblk, 256, 0, st>>>(ka, aa, kb, ab, M, tile, shift, L, offs, hist, 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        FKey *tk = ka;
+        FKeyN<NW> *tk = ka;
         ka = kb;
         kb = tk;
         double2 *ta = aa;
         aa = ab;
         ab = ta;
     }
-    if (ka != static_cast<FKey *>(keys)) {
-        if ((e = cudaMemcpyAsync(keys, ka, (size_t)M * sizeof(FKey), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+    if (ka != static_cast<FKeyN<NW> *>(keys)) {
+        if ((e = cudaMemcpyAsync(keys, ka, (size_t)M * sizeof(FKeyN<NW>), cudaMemcpyDeviceToDevice, st)) !=
+            cudaSuccess)
             return e;
         if ((e = cudaMemcpyAsync(amps, aa, (size_t)M * sizeof(double2), cudaMemcpyDeviceToDevice, st)) !=
             cudaSuccess)
@@ -656,44 +938,74 @@ cudaError_t qw_flat_sort(const QwSimDev &d, void *keys, double2 *amps, void *tmp
     }
     return cudaSuccess;
 }
+} // namespace
+
+cudaError_t qw_flat_sort(const QwSimDev &d, void *keys, double2 *amps, void *tmpk, double2 *tmpa, int64_t M,
+                         int order, uint32_t *work, cudaStream_t st, int kw)
+{
+    if (kw == NW_FAITH) return flat_sort_t<NW_FAITH>(d, keys, amps, tmpk, tmpa, M, order, work, st);
+    return flat_sort_t<2>(d, keys, amps, tmpk, tmpa, M, order, work, st);
+}
 
 /* op: 0 = R^dag, 1 = R (2 outputs per entry), 2 = H (s outputs per entry) */
 cudaError_t qw_flat_group(const QwSimDev &d, int op, const void *keys, const double2 *amps, int64_t M, void *okeys,
-                          double2 *oamps, uint32_t *flags, cudaStream_t st)
+                          double2 *oamps, uint32_t *flags, cudaStream_t st, int kw)
 {
     if (M <= 0) return cudaSuccess;
-    const FKey *k = static_cast<const FKey *>(keys);
-    FKey *ok = static_cast<FKey *>(okeys);
-    if (op == 0) k_f_rot<true><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
-    else if (op == 1) k_f_rot<false><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
-    else k_f_hadamard<<<grid_for(M, 128), 128, 0, st>>>(d, k, amps, M, ok, oamps, flags);
+    if (kw == NW_FAITH) {
+        const FKeyW *k = static_cast<const FKeyW *>(keys);
+        FKeyW *ok = static_cast<FKeyW *>(okeys);
+        if (op == 0) k_f_rot<true, NW_FAITH><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
+        else if (op == 1) k_f_rot<false, NW_FAITH><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
+        else k_f_hadamard<NW_FAITH><<<grid_for(M, 128), 128, 0, st>>>(d, k, amps, M, ok, oamps, flags);
+    } else {
+        const FKey *k = static_cast<const FKey *>(keys);
+        FKey *ok = static_cast<FKey *>(okeys);
+        if (op == 0) k_f_rot<true, 2><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
+        else if (op == 1) k_f_rot<false, 2><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
+        else k_f_hadamard<2><<<grid_for(M, 128), 128, 0, st>>>(d, k, amps, M, ok, oamps, flags);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t qw_flat_compact(const void *keys, const double2 *amps, const uint32_t *flags, const uint32_t *pos,
-                            int64_t n, void *okeys, double2 *oamps, cudaStream_t st)
+                            int64_t n, void *okeys, double2 *oamps, cudaStream_t st, int kw)
 {
     if (n <= 0) return cudaSuccess;
-    k_f_compact<<<grid_for(n, 256), 256, 0, st>>>(static_cast<const FKey *>(keys), amps, flags, pos, n,
-                                                   static_cast<FKey *>(okeys), oamps);
+    if (kw == NW_FAITH)
+        k_f_compact<NW_FAITH><<<grid_for(n, 256), 256, 0, st>>>(static_cast<const FKeyW *>(keys), amps, flags, pos, n,
+                                                                  static_cast<FKeyW *>(okeys), oamps);
+    else
+        k_f_compact<2><<<grid_for(n, 256), 256, 0, st>>>(static_cast<const FKey *>(keys), amps, flags, pos, n,
+                                                           static_cast<FKey *>(okeys), oamps);
     return cudaGetLastError();
 }
 
 cudaError_t qw_flat_readout(const QwSimDev &d, const void *keys, const double2 *amps, int64_t M, const QwStepArgs &a,
-                            cudaStream_t st)
+                            cudaStream_t st, int kw)
 {
     if (M <= 0) return cudaSuccess;
-    k_f_readout<<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<const FKey *>(keys), amps, M, a);
+    if (kw == NW_FAITH)
+        k_f_readout<NW_FAITH><<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<const FKeyW *>(keys), amps, M, a);
+    else k_f_readout<2><<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<const FKey *>(keys), amps, M, a);
     return cudaGetLastError();
 }
 
 cudaError_t qw_flat_scatter(const QwSimDev &d, const QwBufDev &out, int fp32, const void *keys, const double2 *amps,
-                            int64_t M, int32_t *status, unsigned int *maxrow, double *norm, cudaStream_t st)
+                            int64_t M, int32_t *status, unsigned int *maxrow, double *norm, cudaStream_t st, int kw)
 {
     if (M <= 0) return cudaSuccess;
-    const FKey *k = static_cast<const FKey *>(keys);
-    if (fp32) k_f_scatter<float2><<<grid_for(M, 256), 256, 0, st>>>(d, out, k, amps, M, status, maxrow, norm);
-    else k_f_scatter<double2><<<grid_for(M, 256), 256, 0, st>>>(d, out, k, amps, M, status, maxrow, norm);
+    if (kw == NW_FAITH) {
+        const FKeyW *k = static_cast<const FKeyW *>(keys);
+        if (fp32)
+            k_f_scatter<float2, NW_FAITH><<<grid_for(M, 256), 256, 0, st>>>(d, out, k, amps, M, status, maxrow, norm);
+        else
+            k_f_scatter<double2, NW_FAITH><<<grid_for(M, 256), 256, 0, st>>>(d, out, k, amps, M, status, maxrow, norm);
+    } else {
+        const FKey *k = static_cast<const FKey *>(keys);
+        if (fp32) k_f_scatter<float2, 2><<<grid_for(M, 256), 256, 0, st>>>(d, out, k, amps, M, status, maxrow, norm);
+        else k_f_scatter<double2, 2><<<grid_for(M, 256), 256, 0, st>>>(d, out, k, amps, M, status, maxrow, norm);
+    }
     return cudaGetLastError();
 }
 
@@ -702,5 +1014,58 @@ cudaError_t qw_flat_finish(const QwStepArgs &a, const double *norm, const int64_
     k_f_finish<<<1, 1, 0, st>>>(a, norm, (unsigned long long)counts[0], (unsigned long long)counts[1],
                                 (unsigned long long)counts[2], (unsigned long long)counts[3],
                                 (unsigned long long)counts[4]);
+    return cudaGetLastError();
+}
+
+/* register-faithful layout of a simulator: address width and field positions */
+static FaithLayout faith_layout(const QwSimDev &d)
+{
+    FaithLayout F;
+    const uint64_t ns = (uint64_t)d.n_single * (uint64_t)d.s;
+    const uint64_t top = ns + (((uint64_t)1 << d.nb) * (uint64_t)d.s) + ((uint64_t)1 << d.nb) + 1;
+    int b = 0;
+    while (((uint64_t)1 << b) < top) b++;
+    F.aw = b;
+    F.p_addr = 128;
+    F.p_left = F.p_addr + b;
+    F.p_right = F.p_left + b;
+    F.p_mid = F.p_right + b;
+    F.p_midval = F.p_mid + b;
+    F.p_flag = F.p_midval + 16;
+    F.p_cl = F.p_flag + 1;
+    F.p_ce = F.p_cl + 1;
+    F.p_stk = F.p_ce + 1;
+    F.frame = b + 18;
+    return F;
+}
+
+int qw_faithful_layout(const QwSimDev &d, int *addr_bits, int *layout_bits)
+{
+    const FaithLayout F = faith_layout(d);
+    if (addr_bits) *addr_bits = F.aw;
+    const int bits = F.p_stk + (d.L + 1) * F.frame;
+    if (layout_bits) *layout_bits = bits;
+    return bits <= 64 * NW_FAITH && d.L + 1 <= QW_FQ_FRAMES;
+}
+
+cudaError_t qw_faithful_op(const QwSimDev &d, void *keys, int64_t M, int op, int32_t *status, cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    k_fq<<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<FKeyW *>(keys), M, op, faith_layout(d), status);
+    return cudaGetLastError();
+}
+
+cudaError_t qw_faithful_export(const QwSimDev &d, const void *keys, int64_t M, uint64_t *table, cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    k_fq_export<<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<const FKeyW *>(keys), M, faith_layout(d), table);
+    return cudaGetLastError();
+}
+
+cudaError_t qw_faithful_check_idle(const QwSimDev &d, const void *keys, int64_t M, int32_t *status, cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    k_fq_check_idle<<<grid_for(M, 256), 256, 0, st>>>(static_cast<const FKeyW *>(keys), M, faith_layout(d).p_addr,
+                                                       status);
     return cudaGetLastError();
 }

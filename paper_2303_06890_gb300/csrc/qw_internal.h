@@ -27,6 +27,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/qwalk.h"
+
 #define QW_SPILL_EMPTY (~0ull)
 
 /* device status word bits */
@@ -63,6 +65,7 @@ struct QwPartEntry {
 #define QW_MODE_WALK_SEG_PF 5   /* segments, software-pipelined */
 #define QW_MODE_WALK_SLOT 6     /* fused step, one lane per QRAM slot (s = 8, 16, 32) */
 #define QW_MODE_WALK_FLAT 7     /* the literal step on one globally sorted branch list (qw_flat.cu) */
+#define QW_MODE_WALK_FAITHFUL 8 /* the flat step with every working register in a 10-word key */
 
 struct QwSimDev {
     int nb, s, L, ninst;
@@ -164,32 +167,40 @@ cudaError_t qw_launch_qls_norm(const double2 *y, int n, double *p, int64_t *jctr
 cudaError_t qw_launch_regrow(const QwSimDev &d, const QwBufDev &from, int cap_old, uint64_t *key_new, void *amp_new,
                              int fp32, cudaStream_t st);
 
-/* flat, globally sorted step (qw_flat.cu): keys are 16-byte packed register
-   keys, amplitudes complex FP64; see qw_flat.cu for each stage */
+/* flat, globally sorted step (qw_flat.cu): keys are packed register keys of
+   kw 64-bit words (2: the qw_state_export layout; 10: the register-faithful
+   layout with the working registers above bit 128), amplitudes complex FP64;
+   see qw_flat.cu for each stage */
 #define QW_FLAT_OSDAG 1u
 #define QW_FLAT_OA 2u
 #define QW_FLAT_OS 3u
 #define QW_FLAT_S 4u
 #define QW_FLAT_A0 5u /* check A = 0 */
+#define QW_FAITH_WORDS 10
 cudaError_t qw_flat_gather(const QwSimDev &d, const QwBufDev &buf, int fp32, const double *scale, void *keys,
-                           double2 *amps, unsigned long long *counter, int64_t cap, cudaStream_t st);
-cudaError_t qw_flat_map(const QwSimDev &d, void *keys, int64_t M, uint32_t ops, int32_t *status, cudaStream_t st);
-cudaError_t qw_flat_phase(const QwSimDev &d, const void *keys, double2 *amps, int64_t M, cudaStream_t st);
+                           double2 *amps, unsigned long long *counter, int64_t cap, cudaStream_t st, int kw);
+cudaError_t qw_flat_map(const QwSimDev &d, void *keys, int64_t M, uint32_t ops, int32_t *status, cudaStream_t st,
+                        int kw);
+cudaError_t qw_flat_phase(const QwSimDev &d, const void *keys, double2 *amps, int64_t M, cudaStream_t st, int kw);
 size_t qw_flat_scan_words(int64_t n);
 cudaError_t qw_flat_scan(const uint32_t *in, int64_t n, uint32_t *sums, uint32_t *out, cudaStream_t st);
 size_t qw_flat_sort_words(int64_t M);
 cudaError_t qw_flat_sort(const QwSimDev &d, void *keys, double2 *amps, void *tmpk, double2 *tmpa, int64_t M,
-                         int order, uint32_t *work, cudaStream_t st);
+                         int order, uint32_t *work, cudaStream_t st, int kw);
 cudaError_t qw_flat_group(const QwSimDev &d, int op, const void *keys, const double2 *amps, int64_t M, void *okeys,
-                          double2 *oamps, uint32_t *flags, cudaStream_t st);
+                          double2 *oamps, uint32_t *flags, cudaStream_t st, int kw);
 cudaError_t qw_flat_compact(const void *keys, const double2 *amps, const uint32_t *flags, const uint32_t *pos,
-                            int64_t n, void *okeys, double2 *oamps, cudaStream_t st);
+                            int64_t n, void *okeys, double2 *oamps, cudaStream_t st, int kw);
 cudaError_t qw_flat_readout(const QwSimDev &d, const void *keys, const double2 *amps, int64_t M, const QwStepArgs &a,
-                            cudaStream_t st);
+                            cudaStream_t st, int kw);
 cudaError_t qw_flat_scatter(const QwSimDev &d, const QwBufDev &out, int fp32, const void *keys, const double2 *amps,
-                            int64_t M, int32_t *status, unsigned int *maxrow, double *norm, cudaStream_t st);
+                            int64_t M, int32_t *status, unsigned int *maxrow, double *norm, cudaStream_t st, int kw);
 cudaError_t qw_flat_finish(const QwStepArgs &a, const double *norm, const int64_t *counts, cudaStream_t st);
-
+/* register-faithful sub-operations on 10-word keys (op codes QW_FQ_* of qwalk.h) */
+int qw_faithful_layout(const QwSimDev &d, int *addr_bits, int *layout_bits);
+cudaError_t qw_faithful_op(const QwSimDev &d, void *keys, int64_t M, int op, int32_t *status, cudaStream_t st);
+cudaError_t qw_faithful_check_idle(const QwSimDev &d, const void *keys, int64_t M, int32_t *status, cudaStream_t st);
+cudaError_t qw_faithful_export(const QwSimDev &d, const void *keys, int64_t M, uint64_t *table, cudaStream_t st);
 cudaError_t qw_launch_part_inbox(const QwSimDev &d, const QwBufDev &buf, const QwPartEntry *e, int64_t count, int fp32,
                                  int32_t *status, cudaStream_t st);
 

@@ -31,9 +31,24 @@ EXPORTED = ("qw_sim_opts_default", "qw_sim_create", "qw_state_init", "qw_apply_w
             "qw_state_export", "qw_sim_info", "qw_step_stats", "qw_launch_count", "qw_sim_destroy",
             "qw_last_error", "qw_measure_register_noalloc", "qw_autotune", "qw_state_import",
             "qw_part_owner", "qw_part_outbox", "qw_part_inbox", "qw_part_norm", "qw_part_set_norm",
-            "qw_part_walk")
+            "qw_part_walk", "qw_faithful_info", "qw_faithful_begin", "qw_faithful_apply",
+            "qw_faithful_export", "qw_faithful_end")
 MEASURE_NOALLOC_MAX_LEN = 65536
-WALK_VARIANTS = 6  # QW_WALK_VARIANTS
+WALK_VARIANTS = 7  # QW_WALK_VARIANTS
+
+# register-faithful sub-operations (QW_FQ_* of qwalk.h)
+FQ = {"ADDR_COL": 1, "QRAM_COL": 2, "QBS_FWD": 3, "QBS_BWD": 4, "SWAP": 5, "ADDR_VAL": 6, "QRAM_VAL": 7,
+      "R": 8, "RDAG": 9, "H": 10, "P": 11, "S": 12, "ALLOC_A": 13, "FREE_A": 14}
+FQ_FRAMES = 8
+FQ_COLUMNS = (("inst", "jc", "j", "b1", "kc", "k", "b2", "A", "addr", "left", "right", "mid", "midval", "flag",
+               "cl", "ce") + tuple(f"{n}{f}" for f in range(FQ_FRAMES) for n in ("mid", "midval", "cl", "ce")))
+FQ_OS = ("ADDR_COL", "QRAM_COL", "ADDR_COL", "QBS_FWD", "QBS_BWD", "SWAP")
+# Alg. 1 forward then backward is k ^= index, its own inverse: O_s'^dag keeps that pair's order
+FQ_OSDAG = ("SWAP", "QBS_FWD", "QBS_BWD", "ADDR_COL", "QRAM_COL", "ADDR_COL")
+FQ_OA = ("ADDR_VAL", "QRAM_VAL", "ADDR_VAL")
+# W = S T~ P T~^dag (QW_FQ_STEP)
+FQ_STEP = (("ALLOC_A",) + FQ_OSDAG + FQ_OA + FQ_OS + ("RDAG",) + FQ_OSDAG + FQ_OA + ("H", "FREE_A", "P", "ALLOC_A", "H")
+           + FQ_OA + FQ_OS + ("R",) + FQ_OSDAG + FQ_OA + FQ_OS + ("FREE_A", "S"))
 
 
 class QwError(RuntimeError):
@@ -99,6 +114,11 @@ def load(build_if_missing: bool = True):
     lib.qw_part_norm.argtypes = [P, P]
     lib.qw_part_set_norm.argtypes = [P, dbl]
     lib.qw_part_walk.argtypes = [P, i32, i64]
+    lib.qw_faithful_info.argtypes = [P, P, P, P]
+    lib.qw_faithful_begin.argtypes = [P]
+    lib.qw_faithful_apply.argtypes = [P, P, i32]
+    lib.qw_faithful_export.argtypes = [P, P, P, i64, P]
+    lib.qw_faithful_end.argtypes = [P, i32]
     for name in ("qw_part_owner", "qw_part_outbox", "qw_part_inbox", "qw_part_norm", "qw_part_set_norm",
                  "qw_part_walk"):
         getattr(lib, name).restype = ctypes.c_int
@@ -111,7 +131,9 @@ def load(build_if_missing: bool = True):
                  "qw_sync", "qw_cks_coefficients",
                  "qw_apply_qls", "qw_measure_register", "qw_measure_register_noalloc",
                  "qw_state_size", "qw_state_export",
-                 "qw_sim_info", "qw_step_stats", "qw_autotune", "qw_state_import", "qw_sim_destroy"):
+                 "qw_sim_info", "qw_step_stats", "qw_autotune", "qw_state_import", "qw_sim_destroy",
+                 "qw_faithful_info", "qw_faithful_begin", "qw_faithful_apply", "qw_faithful_export",
+                 "qw_faithful_end"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -335,6 +357,38 @@ class Sim:
 
     def launch_count(self) -> int:
         return int(load().qw_launch_count(self._h))
+
+    def faithful_info(self) -> dict:
+        """qw_faithful_info: address width, key bits, live bits at the widest
+        point, and whether the register-faithful layout fits."""
+        aw, kb, live = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        rc = load().qw_faithful_info(self._h, ctypes.byref(aw), ctypes.byref(kb), ctypes.byref(live))
+        return {"addr_bits": aw.value, "key_bits": kb.value, "live_bits": live.value, "fits": rc == QW_OK}
+
+    def faithful_begin(self) -> None:
+        """qw_faithful_begin: open a register-faithful session on the state."""
+        self._check(load().qw_faithful_begin(self._h))
+
+    def faithful_apply(self, *ops: str) -> None:
+        """qw_faithful_apply: sub-operations by name (keys of FQ), in order."""
+        codes = np.array([FQ[o] for o in ops], dtype=np.int32)
+        self._check(load().qw_faithful_apply(self._h, _p(codes) if len(codes) else None, len(codes)))
+
+    def faithful_export(self) -> tuple[np.ndarray, np.ndarray]:
+        """qw_faithful_export: (regs [M, len(FQ_COLUMNS)] uint64, rows ascending;
+        amps [M] complex128)."""
+        c = ctypes.c_int64()
+        self._check(load().qw_faithful_export(self._h, None, None, 0, ctypes.byref(c)))
+        n = int(c.value)
+        regs = np.zeros((max(n, 1), len(FQ_COLUMNS)), dtype=np.uint64)
+        a = np.zeros((max(n, 1), 2))
+        self._check(load().qw_faithful_export(self._h, _p(regs), _p(a), n, ctypes.byref(c)))
+        return regs[:n], a[:n, 0] + 1j * a[:n, 1]
+
+    def faithful_end(self, keep: bool = True) -> None:
+        """qw_faithful_end: store the list as one walk step's output (keep) or
+        drop it."""
+        self._check(load().qw_faithful_end(self._h, int(bool(keep))))
 
     def unpack(self, keys: np.ndarray) -> np.ndarray:
         """Packed keys -> [M, 8] (jc, j, b1, kc, k, b2, A, inst) per the header's layout."""

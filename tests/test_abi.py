@@ -125,3 +125,37 @@ def test_key_pack_unpack_follow_the_header_layout(nb, key_words):
             pos += widths[f]
         assert [int(x) for x in key] == [(v >> (64 * t)) & ((1 << 64) - 1) for t in range(key_words)]
     assert np.array_equal(qwalk.unpack_keys(keys, nb), regs)
+
+
+def _header_defines():
+    text = open(os.path.join(ROOT, "include", "qwalk.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = text.replace("\\\n", " ")
+    return dict(re.findall(r"^#define\s+(QW_\w+)\s+(.*?)\s*$", text, flags=re.M))
+
+
+def test_faithful_codes_and_step_follow_the_header():
+    """The binding's register-faithful codes, table columns and W sequence
+    are the header's, and the oracle's codes and sequence agree with them."""
+    import oracle
+
+    d = _header_defines()
+    for name, code in qwalk.FQ.items():
+        assert int(d["QW_FQ_" + name]) == code
+    assert oracle.FQ == qwalk.FQ
+    assert int(d["QW_FQ_COLS"].replace("(", "").split("+")[0]) + 4 * int(d["QW_FQ_FRAMES"]) == \
+        len(qwalk.FQ_COLUMNS)
+    assert int(d["QW_WALK_VARIANTS"]) == qwalk.WALK_VARIANTS
+
+    def expand(body):
+        out = []
+        for tok in re.findall(r"QW_FQ_\w+", body):
+            if tok.endswith("_SEQ"):
+                out += expand(d[tok])
+            else:
+                out.append(tok[len("QW_FQ_"):])
+        return out
+
+    step = expand(d["QW_FQ_STEP"])
+    assert tuple(step) == qwalk.FQ_STEP == tuple(oracle.FQ_STEP)
+    assert len(step) == int(d["QW_FQ_STEP_LEN"])

@@ -528,3 +528,70 @@ def test_marginals_after_t_follow_the_rotation(oracle_mod):
     for name, ln in (("jc", nlen), ("kc", nlen), ("b1", 2)):
         p = o.marginal(name, ln)
         assert abs(p[0] - 1.0) < 1e-14 and np.abs(p[1:]).max() == 0.0, name
+
+
+# --- register-faithful sub-operations -------------------------------------------------
+
+@pytest.mark.parametrize("maker", [wl.walk_n16, lambda: wl.small_random(40, 8, 3, band=1)])
+def test_faithful_step_composes_to_the_walk_step(oracle_mod, maker):
+    """W = S T~ P T~^dag run as register-faithful sub-operations (the working
+    registers of O_s', O_A' and Alg. 1 kept per branch between them) gives the
+    walk step's state bit for bit, every working register back at 0 and no
+    self-check violated."""
+    w = maker()
+    a = oracle_mod.Oracle(w.matrix, w.s)
+    b = oracle_mod.Oracle(w.matrix, w.s)
+    for o in (a, b):
+        o.init_b(w.b)
+        o.apply("T")
+    for _ in range(3):
+        a.apply("W")
+        b.apply_faithful(*oracle_mod.FQ_STEP)
+        ra, aa = a.export()
+        rb, ab = b.export_faithful()
+        oa_, ob_ = np.lexsort(ra.T[::-1]), np.lexsort(rb[:, :7].T[::-1])
+        assert np.array_equal(ra[oa_], rb[ob_, :7])
+        assert np.array_equal(aa[oa_], ab[ob_])
+        assert not rb[:, 7:].any()
+    assert a.violations == 0 and b.violations == 0
+    assert b.max_live_bits >= b.faithful_live_bits > a.nb * 4
+
+
+def test_faithful_qbs_registers_follow_definition_1(oracle_mod):
+    """Inside O_s' (after Alg. 1's loop, before its uncomputation): register k
+    holds l ^ I(j, kc) with I of Def. 1 (brute force on the padded row), a
+    stack frame holds the equal probe (ce = 1, midval = the target, mid =
+    the row's offset + the index) exactly when the target is in the row, and
+    the uncomputation returns every working register to 0."""
+    w = wl.small_random(24, 8, 9)
+    o = oracle_mod.Oracle(w.matrix, w.s)
+    rows = padded_rows(w.matrix, w.s)
+    nb = o.nb
+    rng = np.random.default_rng(4)
+    regs = []
+    for j in range(w.n):
+        for _ in range(6):
+            regs.append((0, j, 0, int(rng.integers(0, 1 << nb)), int(rng.integers(0, w.s)), 0))
+    regs = np.array(sorted(set(regs)), dtype=np.uint64)
+    amps = np.ones(len(regs)) / np.sqrt(len(regs))
+    o.set_state(regs, amps)
+    o.apply_faithful("ADDR_COL", "QRAM_COL", "ADDR_COL", "QBS_FWD")
+    got, _ = o.export_faithful()
+    offset_base = w.n * w.s  # column segment after the value segment (Fig. 1)
+    L = int(np.log2(w.s))
+    for r in got:
+        j, kc, k = int(r[1]), int(r[3]), int(r[4])
+        cols = list(rows[j][0])
+        want_idx = cols.index(kc) if kc in cols else 0
+        k0 = k ^ want_idx  # the register before the search (the slot index l)
+        assert 0 <= k0 < w.s
+        frames = r[7 + 8:].reshape(-1, 4)[:L + 1]
+        hits = [f for f in frames if f[3] == 1]
+        if kc in cols:
+            assert len(hits) == 1
+            assert int(hits[0][1]) == kc and int(hits[0][0]) == offset_base + j * w.s + want_idx
+        else:
+            assert not hits
+    o.apply_faithful("QBS_BWD")
+    back, _ = o.export_faithful()
+    assert not back[:, 7:].any() and o.violations == 0
