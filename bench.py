@@ -37,6 +37,7 @@ METRIC = "walk steps/s and sparse-state entries/s at n=16384, FP32 vs FP64; HBM 
 UNIT = "walk steps/s"
 PROFILE = os.path.join(ROOT, "profiles", "k_walk_n16384_s16.md")
 PROFILE_SLOT = os.path.join(ROOT, "profiles", "k_walk_slot_n16384_s16.md")
+PROFILE_POS = os.path.join(ROOT, "profiles", "k_walk_pos_n16384_s16.md")
 KERNEL_SRC = [os.path.join(ROOT, "paper_2303_06890_gb300", "csrc", f) for f in ("qw_kernels.cu", "qw_device.cuh")]
 L2_FLUSH_BYTES = 256 << 20
 
@@ -92,12 +93,21 @@ def kernel_hash() -> str:
 VARIANTS = ("rows", "rows, pipelined", "segments", "segments, pipelined", "slot lanes")
 
 
+def kernel_name(variant: int, amp: str = "float2", s: int = 16) -> str:
+    """The step kernel that walk_variant ``variant`` launches."""
+    if variant == 4:
+        return f"k_walk_slot<{amp}, s = {s}>"
+    if variant == 7:
+        return f"k_walk_pos<{amp}, s = {s}>"
+    return f"k_walk<{amp}, {VARIANTS[variant]}>"
+
+
 def profiled_traffic(precision: str, variant: int = 0):
-    """DRAM bytes per launch of the step kernel (k_walk_slot for variant 4,
-    else k_walk) from the committed ncu summary, or None when the kernel
-    source changed since the capture."""
+    """DRAM bytes per launch of the step kernel (k_walk_pos for variant 7,
+    k_walk_slot for variant 4, else k_walk) from the committed ncu summary,
+    or None when the kernel source changed since the capture."""
     try:
-        text = open(PROFILE_SLOT if variant == 4 else PROFILE).read()
+        text = open({4: PROFILE_SLOT, 7: PROFILE_POS}.get(variant, PROFILE)).read()
     except OSError:
         return None
     vals = {}
@@ -446,8 +456,7 @@ def run_ours(args, rank, world, local_rank):
         "fp32_speedup_vs_fp64": value / fp64["value"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": ("k_walk_slot<float2, s = 16>" if variant == 4
-                                else f"k_walk<float2, {VARIANTS[variant]}>"),
+                     "kernel": kernel_name(variant),
                      "autotune_us_per_step": tune_us,
                      "algorithmic_bytes_per_launch": b_alg,
                      "state_bytes_per_launch": b_min,

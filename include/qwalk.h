@@ -104,7 +104,18 @@ typedef struct {
                                 register-faithful schedule: the flat path with every
                                 working register of O_s', O_A' and Alg. 1 held in the
                                 state between sub-operations (the QW_FQ_STEP sequence
-                                below; any fuse_reflection) */
+                                below; any fuse_reflection), 7 = the positional layout:
+                                one instance, s = 8, 16 or 32; every branch the walk
+                                reaches from T~|b~> is held at a fixed position of its
+                                row (no key, no count), one lane per QRAM slot writes
+                                each output to its position, so a step has no search,
+                                atomic or clearing; a state with branches outside those
+                                positions (e.g. from qw_state_import) runs on the
+                                kernel of variant 4.  The state moves into the layout
+                                at the first walk step (a synchronisation) and back
+                                into the row buckets before any call that reads it;
+                                row_capacity grows to 2 s + 2 E (E: the most unpaired
+                                padded columns pointing at one row) */
     int32_t graphs;          /* 1 (default): runs of >= 6 walk steps are issued as replays
                                 of a captured 6-step CUDA graph; 0: one launch per step */
     int32_t spill_rows;      /* slots of the table holding rows with jc != 0 (reached only
@@ -202,21 +213,24 @@ int qw_enqueue_walk_steps(qw_sim *sim, int64_t nsteps);
 int qw_sync(qw_sim *sim);
 
 /* Number of step-kernel variants (walk_variant 0 .. QW_WALK_VARIANTS - 1). */
-#define QW_WALK_VARIANTS 7
+#define QW_WALK_VARIANTS 8
 
 /*
  * Autotuner of the fused step kernel: runs steps_per_candidate walk steps with
  * each variant of walk_variant (rows or segments of two rows, plain or
- * software-pipelined, one lane per QRAM slot), times them with CUDA events on
- * the simulator's stream, and keeps the fastest for all later steps.
- * Segments are tried only when warp_capacity >= 2 row_capacity (true by
- * default), the slot kernel only then and for s = 8, 16 or 32; the flat path
- * (variant 5) is never chosen; variants not tried are reported as 0 us.  The state advances by steps_per_candidate
- * walk steps per variant tried (the variants give the same results).
- * *choice (nullable) receives the variant, *us_per_step (nullable,
- * QW_WALK_VARIANTS doubles) the measured times.  Synchronises.
- * Has no effect with fuse_reflection = 0.  Errors: QW_ERR_ARG, QW_ERR_STATE,
- * QW_ERR_CAPACITY, QW_ERR_CUDA.
+ * software-pipelined, one lane per QRAM slot, the positional layout), times
+ * them with CUDA events on the simulator's stream, and keeps the fastest for
+ * all later steps.  Segments are tried only when warp_capacity >= 2
+ * row_capacity (true by default), the slot kernel only then and for s = 8, 16
+ * or 32, the positional layout (variant 7) for s = 8, 16 or 32 with one
+ * instance and no partitions (its tables are built first, and the move of the
+ * state into it is not timed); the flat path and the register-faithful
+ * schedule (variants 5 and 6) are never chosen; variants not tried are
+ * reported as 0 us.  The state advances by steps_per_candidate walk steps per
+ * variant tried (the variants give the same results).  *choice (nullable)
+ * receives the variant, *us_per_step (nullable, QW_WALK_VARIANTS doubles) the
+ * measured times.  Synchronises.  Has no effect with fuse_reflection = 0.
+ * Errors: QW_ERR_ARG, QW_ERR_STATE, QW_ERR_CAPACITY, QW_ERR_CUDA.
  */
 int qw_autotune(qw_sim *sim, int32_t steps_per_candidate, int32_t *choice, double *us_per_step);
 

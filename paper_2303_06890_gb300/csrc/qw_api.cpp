@@ -138,6 +138,20 @@ struct qw_sim {
     FlatList fq;
     FaithCounts fq_counts;
     bool fq_open = false;
+    /* positional layout (walk_variant 7): tables, the three row arrays that
+       rotate like buf, and whether the state lives there */
+    uint16_t *pos_tp = nullptr;
+    uint32_t *pos_xin = nullptr;
+    uint16_t *pos_xcnt = nullptr;
+    void *pbuf[3] = {nullptr, nullptr, nullptr};
+    size_t pbuf_bytes = 0;
+    bool pos_built = false;
+    bool pos_live = false; /* the state is pbuf[cur], not buf[cur] */
+    bool pos_try = true;   /* the bucket state may have positions (unknown or yes) */
+    int grid_pos = 1;
+    int mode_alt = QW_MODE_WALK_FUSED, grid_alt = 1; /* the bucket kernel for a state without positions */
+    cudaGraphExec_t pexec[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    cudaGraphExec_t pqexec[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
     std::string err;
 };
 
@@ -153,7 +167,7 @@ static const int kGraphTerms = 3;  /* QLS terms per graph: 2 walk steps each */
 
 static void drop_graphs(qw_sim *sim)
 {
-    for (auto *set : {&sim->gexec, &sim->qexec})
+    for (auto *set : {&sim->gexec, &sim->qexec, &sim->pexec, &sim->pqexec})
         for (auto &row : *set)
             for (auto &g : row)
                 if (g) {
@@ -271,6 +285,8 @@ static void build_image(const qw_csc &m, int s, uint32_t *out)
     }
 }
 
+static int pos_build(qw_sim *sim);
+
 extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opts *opts_in,
                              qw_sim **out)
 {
@@ -320,10 +336,10 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     sim->renorm = o.renorm < 0 ? sim->fp32 : (o.renorm != 0);
     static const int kVariantMode[QW_WALK_VARIANTS] = {QW_MODE_WALK_FUSED, QW_MODE_WALK_FUSED_PF, QW_MODE_WALK_SEG,
                                                        QW_MODE_WALK_SEG_PF, QW_MODE_WALK_SLOT, QW_MODE_WALK_FLAT,
-                                                       QW_MODE_WALK_FAITHFUL};
+                                                       QW_MODE_WALK_FAITHFUL, QW_MODE_WALK_POS};
     if (o.walk_variant < 0 || o.walk_variant >= QW_WALK_VARIANTS) {
         delete sim;
-        g_create_error = "qw_sim_create: walk_variant must be 0..6";
+        g_create_error = "qw_sim_create: walk_variant must be 0..7";
         return QW_ERR_ARG;
     }
     sim->mode = (o.fuse_reflection || kVariantMode[o.walk_variant] == QW_MODE_WALK_FAITHFUL)
@@ -356,8 +372,8 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     wc = std::max<int64_t>(wc, s);
     wc = std::max<int64_t>(wc, d.cap_row);
     d.warp_cap = (int)wc;
-    if (sim->mode == QW_MODE_WALK_SLOT && !qw_slot_supported(d)) {
-        g_create_error = "qw_sim_create: walk_variant 4 (one lane per QRAM slot) needs s = 8, 16 or 32";
+    if ((sim->mode == QW_MODE_WALK_SLOT || sim->mode == QW_MODE_WALK_POS) && !qw_slot_supported(d)) {
+        g_create_error = "qw_sim_create: walk_variants 4 and 7 (one lane per QRAM slot) need s = 8, 16 or 32";
         qw_sim_destroy(sim);
         return QW_ERR_ARG;
     }
@@ -371,7 +387,8 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
         qw_sim_destroy(sim);
         return QW_ERR_ARG;
     }
-    if (o.nparts > 1 && (ninst != 1 || sim->mode == QW_MODE_WALK_LITERAL || host_staged(sim))) {
+    if (o.nparts > 1 && (ninst != 1 || sim->mode == QW_MODE_WALK_LITERAL || host_staged(sim) ||
+                         sim->mode == QW_MODE_WALK_POS)) {
         g_create_error = "qw_sim_create: a partitioned walk needs one instance, fuse_reflection = 1 and "
                          "walk_variant <= 4";
         qw_sim_destroy(sim);
@@ -522,6 +539,7 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
         for (int m : {QW_MODE_WALK_FUSED, QW_MODE_WALK_FUSED_PF, QW_MODE_WALK_SEG, QW_MODE_WALK_SEG_PF})
             gmax = std::max(gmax, qw_step_grid(d, sim->fp32, m));
         if (qw_slot_supported(d)) gmax = std::max(gmax, qw_step_grid(d, sim->fp32, QW_MODE_WALK_SLOT));
+        if (qw_slot_supported(d) && ninst == 1) gmax = std::max(gmax, qw_pos_grid(d, sim->fp32));
     }
     QW_TRY(dalloc(sim, &sim->partials, (size_t)gmax));
     QW_TRY(dalloc(sim, &sim->deferred, (size_t)(d.dense_buckets / 2 + d.spill_slots)));
@@ -545,6 +563,15 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     QW_TRY(cudaMallocHost((void **)&sim->h_st, sizeof(StatusView)));
     QW_TRY(cudaDeviceSynchronize());
 #undef QW_TRY
+    if (sim->mode == QW_MODE_WALK_POS) {
+        const int prc = pos_build(sim);
+        if (prc != QW_OK) {
+            g_create_error = "qw_sim_create: " + sim->err;
+            qw_sim_destroy(sim);
+            return prc;
+        }
+        sim->grid_walk = sim->grid_alt;
+    }
     *out = sim;
     return QW_OK;
 }
@@ -558,6 +585,10 @@ extern "C" int qw_sim_destroy(qw_sim *sim)
         cudaFree(sim->fq.K);
         cudaFree(sim->fq.A);
     }
+    cudaFree(sim->pos_tp);
+    cudaFree(sim->pos_xin);
+    cudaFree(sim->pos_xcnt);
+    for (void *p : sim->pbuf) cudaFree(p);
     cudaFree(sim->img);
     cudaFree(sim->fg);
     cudaFree(sim->fg32);
@@ -680,6 +711,7 @@ static QwStepArgs step_args(qw_sim *sim, int mode)
 
 static int flat_walk_step(qw_sim *sim, int readout);
 static int faithful_walk_step(qw_sim *sim, int readout);
+static int pos_unpack(qw_sim *sim);
 static int sync_walk(qw_sim *sim, const char *where);
 
 /* one walk step: X_cur -> X_cur+1, clearing X_cur+2 */
@@ -690,11 +722,20 @@ static int launch_walk(qw_sim *sim, int readout)
     if (sim->d.nparts > 1) /* the outboxes hold this step's sends only */
         QW_CUDA(sim, cudaMemsetAsync(sim->outbox_count, 0, (size_t)sim->d.nparts * 8, sim->stream));
     sim->issued++;
-    QwStepArgs a = step_args(sim, sim->mode);
-    a.qls_readout = readout;
     const int nxt = (sim->cur + 1) % 3, clr = (sim->cur + 2) % 3;
-    cudaError_t e = qw_launch_step(sim->d, sim->buf[sim->cur], sim->buf[nxt], sim->buf[clr], a,
-                                   sim->fp32, sim->grid_walk, sim->stream);
+    cudaError_t e;
+    if (sim->mode == QW_MODE_WALK_POS && sim->pos_live) {
+        QwStepArgs a = step_args(sim, QW_MODE_WALK_POS);
+        a.qls_readout = readout;
+        e = qw_launch_walk_pos(sim->d, sim->pbuf[sim->cur], sim->pbuf[nxt], a, sim->fp32, sim->grid_pos,
+                               sim->stream);
+    } else { /* a positional walk whose state has no positions runs the bucket kernel */
+        const int mode = sim->mode == QW_MODE_WALK_POS ? sim->mode_alt : sim->mode;
+        QwStepArgs a = step_args(sim, mode);
+        a.qls_readout = readout;
+        e = qw_launch_step(sim->d, sim->buf[sim->cur], sim->buf[nxt], sim->buf[clr], a, sim->fp32,
+                           sim->mode == QW_MODE_WALK_POS ? sim->grid_alt : sim->grid_walk, sim->stream);
+    }
     sim->launches++;
     if (e != cudaSuccess) return cuda_fail(sim, e, "walk step launch");
     sim->cur = nxt;
@@ -885,6 +926,10 @@ static int flat_store(qw_sim *sim, FlatList &L, const QwStepArgs &a, const int64
  * returns. */
 static int flat_walk_step(qw_sim *sim, int readout)
 {
+    {
+        const int prc = pos_unpack(sim);
+        if (prc != QW_OK) return prc;
+    }
     const QwSimDev &d = sim->d;
     cudaStream_t st = sim->stream;
     FlatList L;
@@ -921,6 +966,128 @@ static int flat_walk_step(qw_sim *sim, int readout)
 #undef QW_FLAT
     const int rc = flat_store(sim, L, a, counts);
     flat_release(sim, L);
+    return rc;
+}
+
+/* ---- positional layout (walk_variant 7, k_walk_pos) ------------------------ */
+
+/* The tables of the positional layout from the QRAM image: for slot (j, l)
+ * with column c, the position of the branch k = j in row c -- 2 l' when row
+ * c holds column j in slot l', else 2 s + 2 e for the e-th such row x of c
+ * (listed in pos_xin) -- and the three row arrays.  The row buckets grow to
+ * hold a whole positional row (2 s + 2 E branches). */
+static int pos_build(qw_sim *sim)
+{
+    if (sim->pos_built) return QW_OK;
+    QwSimDev &d = sim->d;
+    if (d.ninst != 1 || d.nparts != 1 || !qw_slot_supported(d))
+        return fail(sim, QW_ERR_ARG, "walk_variant 7 (positional) needs one instance, no partitions and s = 8, 16 "
+                                     "or 32");
+    const int64_t n = d.n_single;
+    const int s = d.s;
+    std::vector<uint32_t> img((size_t)n * s);
+    QW_CUDA(sim, cudaMemcpy(img.data(), sim->img, img.size() * 4, cudaMemcpyDeviceToHost));
+    std::vector<uint16_t> tp((size_t)n * s);
+    std::vector<std::vector<uint32_t>> xin((size_t)n);
+    for (int64_t j = 0; j < n; ++j)
+        for (int l = 0; l < s; ++l) {
+            const uint32_t c = img[(size_t)(j * s + l)] >> 16;
+            const uint32_t *row = img.data() + (size_t)c * s;
+            int lo = 0, hi = s;
+            while (lo < hi) {
+                const int m = (lo + hi) >> 1;
+                if ((row[m] >> 16) < (uint32_t)j) lo = m + 1;
+                else hi = m;
+            }
+            if (lo < s && (row[lo] >> 16) == (uint32_t)j) {
+                tp[(size_t)(j * s + l)] = (uint16_t)(2 * lo);
+            } else {
+                tp[(size_t)(j * s + l)] = (uint16_t)(2 * s + 2 * xin[c].size());
+                xin[c].push_back((uint32_t)j << 8 | (uint32_t)l);
+            }
+        }
+    size_t E = 0;
+    for (const auto &v : xin) E = std::max(E, v.size());
+    if (2 * s + 2 * E >= 65535 || n >= (1 << 24))
+        return fail(sim, QW_ERR_ARG, "positional layout: too many unpaired padded columns in a row");
+    std::vector<uint32_t> hx((size_t)n * std::max<size_t>(E, 1), 0u);
+    std::vector<uint16_t> hc((size_t)n);
+    for (int64_t c = 0; c < n; ++c) {
+        hc[(size_t)c] = (uint16_t)xin[(size_t)c].size();
+        for (size_t e = 0; e < xin[(size_t)c].size(); ++e) hx[(size_t)c * E + e] = xin[(size_t)c][e];
+    }
+    const int R = 2 * s + 2 * (int)E;
+    if (d.cap_row < R) {
+        const int rc = grow_rows(sim, R);
+        if (rc != QW_OK) return rc;
+    }
+    QW_CUDA(sim, dalloc(sim, &sim->pos_tp, tp.size()));
+    QW_CUDA(sim, dalloc(sim, &sim->pos_xin, hx.size()));
+    QW_CUDA(sim, dalloc(sim, &sim->pos_xcnt, hc.size()));
+    QW_CUDA(sim, cudaMemcpy(sim->pos_tp, tp.data(), tp.size() * 2, cudaMemcpyHostToDevice));
+    QW_CUDA(sim, cudaMemcpy(sim->pos_xin, hx.data(), hx.size() * 4, cudaMemcpyHostToDevice));
+    QW_CUDA(sim, cudaMemcpy(sim->pos_xcnt, hc.data(), hc.size() * 2, cudaMemcpyHostToDevice));
+    sim->pbuf_bytes = (size_t)2 * (size_t)n * (size_t)R * (sim->fp32 ? sizeof(float2) : sizeof(double2));
+    for (auto &p : sim->pbuf) {
+        unsigned char *b = nullptr;
+        QW_CUDA(sim, dalloc(sim, &b, sim->pbuf_bytes));
+        QW_CUDA(sim, cudaMemset(b, 0, sim->pbuf_bytes));
+        p = b;
+    }
+    d.pos_R = R;
+    d.pos_E = (int)E;
+    d.pos_tp = sim->pos_tp;
+    d.pos_xin = sim->pos_xin;
+    d.pos_xcnt = sim->pos_xcnt;
+    sim->grid_pos = qw_pos_grid(d, sim->fp32);
+    sim->mode_alt = d.warp_cap >= 2 * d.cap_row ? QW_MODE_WALK_SLOT : QW_MODE_WALK_FUSED;
+    sim->grid_alt = qw_step_grid(d, sim->fp32, sim->mode_alt);
+    sim->pos_built = true;
+    return QW_OK;
+}
+
+/* Move the state from the buckets into the positional layout when every
+ * branch has a position (then pos_live); otherwise it stays in the buckets
+ * and pos_try is cleared until the state is replaced.  Synchronises. */
+static int pos_pack(qw_sim *sim)
+{
+    cudaStream_t st = sim->stream;
+    QW_CUDA(sim, cudaMemsetAsync(sim->pbuf[sim->cur], 0, sim->pbuf_bytes, st));
+    QW_CUDA(sim, qw_launch_pos_pack(sim->d, sim->buf[sim->cur], sim->pbuf[sim->cur], sim->fp32, &sim->sc->status, st));
+    sim->launches++;
+    QW_CUDA(sim, cudaMemcpyAsync(sim->h_st, &sim->sc->status, sizeof(StatusView), cudaMemcpyDeviceToHost, st));
+    QW_CUDA(sim, cudaStreamSynchronize(st));
+    if (sim->h_st->status == QW_ST_POS_UNREP) {
+        const int32_t zero = 0;
+        QW_CUDA(sim, cudaMemcpy(&sim->sc->status, &zero, 4, cudaMemcpyHostToDevice));
+        sim->pos_try = false;
+        return QW_OK;
+    }
+    if (sim->h_st->status != 0) return check_status(sim, "positional layout");
+    sim->pos_live = true;
+    return QW_OK;
+}
+
+/* The state back into the row buckets (stream-ordered, no synchronisation). */
+static int pos_unpack(qw_sim *sim)
+{
+    if (!sim->pos_live) return QW_OK;
+    QW_CUDA(sim, qw_launch_clear(sim->d, sim->buf[sim->cur], 0, sim->d.total_buckets, 1, sim->stream));
+    QW_CUDA(sim, qw_launch_pos_unpack(sim->d, sim->pbuf[sim->cur], sim->buf[sim->cur], sim->fp32, &sim->sc->status,
+                                      sim->stream));
+    sim->launches += 2;
+    sim->pos_live = false;
+    return QW_OK;
+}
+
+/* Before a positional walk: the state into the positional layout if it
+ * may fit (synchronises then). */
+static int pos_prepare(qw_sim *sim)
+{
+    if (sim->mode != QW_MODE_WALK_POS || sim->pos_live || !sim->pos_try) return QW_OK;
+    int rc = pos_build(sim);
+    if (rc == QW_OK) rc = sync_walk(sim, "positional layout");
+    if (rc == QW_OK) rc = pos_pack(sim);
     return rc;
 }
 
@@ -968,6 +1135,10 @@ static bool faithful_fits(const qw_sim *sim)
  * H, the result stored as X_cur+1. */
 static int faithful_walk_step(qw_sim *sim, int readout)
 {
+    {
+        const int prc = pos_unpack(sim);
+        if (prc != QW_OK) return prc;
+    }
     static const int32_t kStep[QW_FQ_STEP_LEN] = QW_FQ_STEP;
     FlatList L;
     FaithCounts fc;
@@ -1019,6 +1190,8 @@ extern "C" int qw_faithful_begin(qw_sim *sim)
         return fail(sim, QW_ERR_ARG, "register-faithful keys: one instance, and the working registers must fit "
                                      "10 words with s <= 128");
     rc = sync_walk(sim, "qw_faithful_begin");
+    if (rc != QW_OK) return rc;
+    rc = pos_unpack(sim);
     if (rc != QW_OK) return rc;
     cudaError_t e = flat_gather(sim, sim->fq, QW_FQ_KEY_WORDS);
     if (e != cudaSuccess) {
@@ -1111,6 +1284,8 @@ extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, cons
 {
     if (!sim) return QW_ERR_ARG;
     if (sim->fq_open) return faithful_session_closed(sim);
+    sim->pos_live = false; /* the state is replaced in the row buckets */
+    sim->pos_try = true;
     if (inst < 0 || inst >= sim->d.ninst) return fail(sim, QW_ERR_ARG, "instance out of range");
     if (!b_re || n != sim->n_of[(size_t)inst]) return fail(sim, QW_ERR_ARG, "b must hold N values");
     /* |b> goes straight from the caller's arrays to the device (asynchronous
@@ -1202,7 +1377,7 @@ static int capture_graph(qw_sim *sim, cudaGraphExec_t *out, bool qls)
     if (!sim->cap_stream) QW_CUDA(sim, cudaStreamCreateWithFlags(&sim->cap_stream, cudaStreamNonBlocking));
     cudaStream_t user = sim->stream;
     const int cur = sim->cur, slot = sim->scale_slot;
-    const int64_t launches = sim->launches;
+    const int64_t launches = sim->launches, issued = sim->issued;
     sim->stream = sim->cap_stream;
     cudaError_t e = cudaStreamBeginCapture(sim->cap_stream, cudaStreamCaptureModeThreadLocal);
     int rc = QW_OK;
@@ -1217,6 +1392,7 @@ static int capture_graph(qw_sim *sim, cudaGraphExec_t *out, bool qls)
     sim->cur = cur;
     sim->scale_slot = slot;
     sim->launches = launches;
+    sim->issued = issued;
     if (e != cudaSuccess) return cuda_fail(sim, e, "cudaStreamBeginCapture");
     if (rc != QW_OK) {
         if (g) cudaGraphDestroy(g);
@@ -1238,16 +1414,21 @@ extern "C" int qw_enqueue_walk_steps(qw_sim *sim, int64_t nsteps)
     if (nsteps > 0) sim->fresh_T = false;
     int64_t t = 0;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (sim->opts.graphs && !host_staged(sim) && sim->d.nparts == 1 && nsteps >= kGraphSteps &&
-        cudaStreamIsCapturing(sim->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
-        cudaGraphExec_t &g = sim->gexec[sim->cur][sim->scale_slot];
+    const bool capturing = cudaStreamIsCapturing(sim->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+    if (nsteps > 0 && !capturing) {
+        const int rc = pos_prepare(sim);
+        if (rc != QW_OK) return rc;
+    }
+    if (sim->opts.graphs && !host_staged(sim) && sim->d.nparts == 1 && nsteps >= kGraphSteps && !capturing) {
+        cudaGraphExec_t &g = (sim->pos_live ? sim->pexec : sim->gexec)[sim->cur][sim->scale_slot];
         if (!g) {
             int rc = capture_graph(sim, &g, false);
             if (rc != QW_OK) return rc;
         }
         for (; t + kGraphSteps <= nsteps; t += kGraphSteps) {
             QW_CUDA(sim, cudaGraphLaunch(g, sim->stream));
-            sim->launches += kGraphSteps; /* one k_walk launch per step inside the graph */
+            sim->launches += kGraphSteps; /* one step kernel launch per step inside the graph */
+            sim->issued += kGraphSteps;
         }
     }
     for (; t < nsteps; ++t) {
@@ -1295,23 +1476,43 @@ extern "C" int qw_autotune(qw_sim *sim, int32_t steps, int32_t *choice, double *
         if (choice) *choice = -1;
         return QW_OK;
     }
-    const int modes[QW_WALK_VARIANTS] = {QW_MODE_WALK_FUSED, QW_MODE_WALK_FUSED_PF, QW_MODE_WALK_SEG,
-                                         QW_MODE_WALK_SEG_PF, QW_MODE_WALK_SLOT};
-    double us[QW_WALK_VARIANTS] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    /* candidates: walk_variant -> mode.  A segment holds two rows on chip:
+       tried only when the warp buffer fits them; the slot kernel (which falls
+       back to segments) also needs s = 8, 16 or 32; the positional layout
+       one instance and no partitions (its tables are built first: they may
+       grow row_capacity, which the other kernels' launch shapes follow) */
+    const bool slot = qw_slot_supported(sim->d);
+    const bool pos = slot && sim->d.ninst == 1 && sim->d.nparts == 1;
+    if (pos) {
+        const int rc = pos_build(sim);
+        if (rc != QW_OK) return rc;
+    }
+    const bool seg = sim->d.warp_cap >= 2 * sim->d.cap_row;
+    std::vector<std::pair<int, int>> cand = {{0, QW_MODE_WALK_FUSED}, {1, QW_MODE_WALK_FUSED_PF}};
+    if (seg) {
+        cand.push_back({2, QW_MODE_WALK_SEG});
+        cand.push_back({3, QW_MODE_WALK_SEG_PF});
+        if (slot) cand.push_back({4, QW_MODE_WALK_SLOT});
+    }
+    if (pos) cand.push_back({7, QW_MODE_WALK_POS});
+    double us[QW_WALK_VARIANTS];
+    for (double &u : us) u = 0.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     QW_CUDA(sim, cudaEventCreate(&e0));
     QW_CUDA(sim, cudaEventCreate(&e1));
     int rc = QW_OK;
     const int graphs = sim->opts.graphs;
     sim->opts.graphs = 0; /* time the kernels themselves */
-    /* a segment holds two rows on chip: only tried when the warp buffer fits
-       them; the slot kernel (which falls back to segments) also needs
-       s = 8, 16 or 32 */
-    const bool seg = sim->d.warp_cap >= 2 * sim->d.cap_row;
-    const int nvar = seg ? (qw_slot_supported(sim->d) ? 5 : 4) : 2;
-    for (int v = 0; v < nvar && rc == QW_OK; ++v) {
-        sim->mode = modes[v];
-        sim->grid_walk = qw_step_grid(sim->d, sim->fp32, sim->mode);
+    for (size_t c = 0; c < cand.size() && rc == QW_OK; ++c) {
+        const int v = cand[c].first, mode = cand[c].second;
+        if (mode != QW_MODE_WALK_POS) rc = pos_unpack(sim);
+        if (rc != QW_OK) break;
+        sim->mode = mode;
+        sim->grid_walk = mode == QW_MODE_WALK_POS ? sim->grid_alt : qw_step_grid(sim->d, sim->fp32, mode);
+        if (mode == QW_MODE_WALK_POS) { /* the move into the layout is not timed */
+            rc = pos_prepare(sim);
+            if (rc != QW_OK) break;
+        }
         cudaEventRecord(e0, sim->stream);
         rc = qw_enqueue_walk_steps(sim, steps);
         cudaEventRecord(e1, sim->stream);
@@ -1322,11 +1523,18 @@ extern "C" int qw_autotune(qw_sim *sim, int32_t steps, int32_t *choice, double *
     sim->opts.graphs = graphs;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    int best = 0;
-    for (int v = 1; v < nvar; ++v)
-        if (us[v] > 0.0 && us[v] < us[best]) best = v;
-    sim->mode = modes[best];
-    sim->grid_walk = qw_step_grid(sim->d, sim->fp32, sim->mode);
+    int best = cand[0].first, best_mode = cand[0].second;
+    for (const auto &cv : cand)
+        if (us[cv.first] > 0.0 && (us[best] <= 0.0 || us[cv.first] < us[best])) {
+            best = cv.first;
+            best_mode = cv.second;
+        }
+    if (best_mode != QW_MODE_WALK_POS) {
+        const int urc = pos_unpack(sim);
+        if (rc == QW_OK) rc = urc;
+    }
+    sim->mode = best_mode;
+    sim->grid_walk = best_mode == QW_MODE_WALK_POS ? sim->grid_alt : qw_step_grid(sim->d, sim->fp32, best_mode);
     drop_graphs(sim);
     if (choice) *choice = best;
     if (us_per_step)
@@ -1405,18 +1613,23 @@ extern "C" int qw_apply_qls(qw_sim *sim, int32_t inst, const double *coeffs, int
     QW_CUDA(sim, cudaMemsetAsync(sim->qls_y, 0, (size_t)n * sizeof(double2), sim->stream));
     QW_CUDA(sim, cudaMemsetAsync(&sim->sc->qls_j, 0, sizeof(int64_t), sim->stream));
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    const bool graphs = sim->opts.graphs && !host_staged(sim) &&
-                        cudaStreamIsCapturing(sim->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(sim->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+    if (!capturing) {
+        const int rc = pos_prepare(sim);
+        if (rc != QW_OK) return rc;
+    }
+    const bool graphs = sim->opts.graphs && !host_staged(sim) && !capturing;
     int64_t j = 0, next_check = 1024;
     while (j <= j0) {
         if (graphs && j0 + 1 - j >= kGraphTerms) {
-            cudaGraphExec_t &g = sim->qexec[sim->cur][sim->scale_slot];
+            cudaGraphExec_t &g = (sim->pos_live ? sim->pqexec : sim->qexec)[sim->cur][sim->scale_slot];
             if (!g) {
                 int rc = capture_graph(sim, &g, true);
                 if (rc != QW_OK) return rc;
             }
             QW_CUDA(sim, cudaGraphLaunch(g, sim->stream));
             sim->launches += 3 * kGraphTerms;
+            sim->issued += 2 * kGraphTerms;
             j += kGraphTerms;
         } else {
             int rc = launch_qls_term(sim);
@@ -1451,6 +1664,10 @@ extern "C" int qw_measure_register(qw_sim *sim, int32_t inst, int32_t reg, doubl
     if (inst < 0 || inst >= sim->d.ninst || reg < 0 || reg > 5 || !probs || len < 1)
         return fail(sim, QW_ERR_ARG, "bad instance, register id or output");
     if (!sim->has_state) return fail(sim, QW_ERR_STATE, "no state");
+    {
+        const int prc = pos_unpack(sim); /* the state back into the row buckets */
+        if (prc != QW_OK) return prc;
+    }
     if (sim->meas_cap < len) { /* kept for later calls */
         QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
         cudaFree(sim->meas_dev);
@@ -1485,6 +1702,10 @@ extern "C" int qw_measure_register_noalloc(qw_sim *sim, int32_t inst, int32_t re
                     "qw_measure_register_noalloc: len " + std::to_string(len) + " exceeds the fixed scratch of " +
                         std::to_string(QW_MEASURE_NOALLOC_MAX_LEN) + " bins; use qw_measure_register");
     if (!sim->has_state) return fail(sim, QW_ERR_STATE, "no state");
+    {
+        const int prc = pos_unpack(sim); /* the state back into the row buckets */
+        if (prc != QW_OK) return prc;
+    }
     QW_CUDA(sim, qw_launch_measure_noalloc(sim->d, sim->buf[sim->cur], inst, sim->fp32, pending_scale(sim),
                                            reg, probs, len, sim->device, sim->stream));
     sim->launches++;
@@ -1496,6 +1717,10 @@ extern "C" int qw_state_size(qw_sim *sim, int32_t inst, int64_t *count)
     if (!sim || !count) return QW_ERR_ARG;
     if (inst < -1 || inst >= sim->d.ninst) return fail(sim, QW_ERR_ARG, "instance out of range");
     if (!sim->has_state) return fail(sim, QW_ERR_STATE, "no state");
+    {
+        const int prc = pos_unpack(sim); /* the state back into the row buckets */
+        if (prc != QW_OK) return prc;
+    }
     QW_CUDA(sim, cudaMemsetAsync(&sim->sc->counter, 0, 8, sim->stream));
     QW_CUDA(sim, qw_launch_count(sim->d, sim->buf[sim->cur], inst, &sim->sc->counter, sim->stream));
     sim->launches++;
@@ -1604,6 +1829,11 @@ extern "C" int qw_state_import(qw_sim *sim, int32_t key_words, const uint64_t *k
 {
     if (!sim) return QW_ERR_ARG;
     if (sim->fq_open) return faithful_session_closed(sim);
+    {
+        const int prc = pos_unpack(sim); /* the state back into the row buckets */
+        if (prc != QW_OK) return prc;
+    }
+    sim->pos_try = true;
     const int nb = sim->d.nb;
     if (key_words < 1 || key_words > 10 || key_words * 64 < 4 * nb + 34)
         return fail(sim, QW_ERR_ARG, "key_words too small for the packed register layout");

@@ -38,6 +38,7 @@
 #define QW_ST_ANCILLA 8        /* register A not zero where it must be */
 #define QW_ST_NOT_BTILDE 16    /* T~ at initialisation met a row that was not |b~> */
 #define QW_ST_OUTBOX_FULL 32   /* a partition's outbox toward another overflowed */
+#define QW_ST_POS_UNREP 64     /* a branch the positional layout has no position for */
 
 /* A branch sent by S to a row another partition owns: its row key
    (qw_rowkey), its local registers (R layout) and its amplitude in FP64. */
@@ -66,6 +67,7 @@ struct QwPartEntry {
 #define QW_MODE_WALK_SLOT 6     /* fused step, one lane per QRAM slot (s = 8, 16, 32) */
 #define QW_MODE_WALK_FLAT 7     /* the literal step on one globally sorted branch list (qw_flat.cu) */
 #define QW_MODE_WALK_FAITHFUL 8 /* the flat step with every working register in a 10-word key */
+#define QW_MODE_WALK_POS 9      /* the state held by position, one lane per QRAM slot (s = 8, 16, 32) */
 
 struct QwSimDev {
     int nb, s, L, ninst;
@@ -98,6 +100,15 @@ struct QwSimDev {
     QwPartEntry *outbox;
     unsigned long long *outbox_count;
     int64_t outbox_cap;
+    /* positional layout (single instance): row (jc = 0, j, b1) is pos_R =
+       2 s + 2 pos_E amplitudes at (2 j + b1) pos_R.  pos_tp[j s + l]: the
+       position of the branch k = j in row col(j, l); pos_xin[j pos_E + e] =
+       x << 8 | l for the e-th row x < pos_xcnt[j] whose slot l holds column j
+       while row j holds no column x */
+    int pos_R, pos_E;
+    const uint16_t *pos_tp;
+    const uint32_t *pos_xin;
+    const uint16_t *pos_xcnt;
 };
 
 struct QwBufDev {
@@ -140,6 +151,17 @@ cudaError_t qw_launch_step(const QwSimDev &d, const QwBufDev &in, const QwBufDev
 int qw_slot_supported(const QwSimDev &d);
 /* dynamic shared memory per block of the step kernel of `mode` */
 size_t qw_step_smem_bytes(const QwSimDev &d, int fp32, int mode);
+/* positional layout: one walk step pin -> pout (both pos_R-strided row
+   arrays), the grid of its launch, and the conversions from and to the row
+   buckets (pack: pout zeroed by the caller; a branch without a position sets
+   QW_ST_POS_UNREP; unpack: the buckets cleared by the caller) */
+cudaError_t qw_launch_walk_pos(const QwSimDev &d, const void *pin, void *pout, const QwStepArgs &a, int fp32,
+                               int grid, cudaStream_t st);
+int qw_pos_grid(const QwSimDev &d, int fp32);
+cudaError_t qw_launch_pos_pack(const QwSimDev &d, const QwBufDev &buf, void *pbuf, int fp32, int32_t *status,
+                               cudaStream_t st);
+cudaError_t qw_launch_pos_unpack(const QwSimDev &d, const void *pbuf, const QwBufDev &buf, int fp32,
+                                 int32_t *status, cudaStream_t st);
 int qw_step_grid(const QwSimDev &d, int fp32, int mode);
 cudaError_t qw_launch_clear(const QwSimDev &d, const QwBufDev &buf, int64_t lo, int64_t hi,
                             int clear_spill, cudaStream_t st);

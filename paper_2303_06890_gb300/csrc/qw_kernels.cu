@@ -2290,6 +2290,342 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_slot(QwSimDev d, QwBufDe
     }
 }
 
+/* ==== positional walk step (walk_variant 7) ==================================== */
+/*
+ * The state of a one-instance walk held by position instead of by key.  At a
+ * step boundary every branch that the walk reaches from T~|b~> sits in a row
+ * (jc = 0, j < N, b1) with kc = A = 0, and its k is either a column of row j
+ * (W = S (2 T~ Pi T~^dag - 1): the branches of T~ Pi's range are those of
+ * T~'s rows, the swapped ones have k = a row whose padded column list holds j)
+ * -- position 2 l + b2 for the column in slot l -- or one of the E_j rows x
+ * whose slot l_x holds column j while row j holds no column x (a padded, so
+ * unpaired, entry) -- position 2 s + 2 e + b2.  Row (j, b1) is pos_R = 2 s +
+ * 2 pos_E amplitudes at (2 j + b1) pos_R; an absent branch is 0, so the
+ * position is the key.
+ *
+ * The lane of slot (j, l) runs the slot kernel's arithmetic on the pairs of
+ * both rows of j at positions 2 l, 2 l + 1 (T~^dag's maps take them to (l, 0),
+ * T~'s back to k = col): R^dag, H P H (the zero-type sum over the unit's
+ * lanes for b1 = 0, -1 for b1 = 1), R; S sends its b2 = 0 / 1 outputs to rows
+ * (col, 0) / (col, 1) at position tp(j, l) + b1, where tp is the position of
+ * k = j in row col.  An extra (j, b1, e) is outside every zero-type group and
+ * its maps leave A = 0: R(0) (-R(0)^dag) on its pair, sent to positions
+ * 2 l_x + b1 of rows (x, 0 / 1).  Every position of the output has exactly
+ * one writer, and pruned outputs are written as 0: no counts, atomics,
+ * searches or keys, and nothing to clear between steps.
+ */
+template <typename AmpT> struct PosPair;
+template <> struct PosPair<float2> {
+    __device__ static void load(const float2 *p, float2 &a0, float2 &a1)
+    {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        a0 = make_float2(v.x, v.y);
+        a1 = make_float2(v.z, v.w);
+    }
+    __device__ static void store(float2 *p, float2 a0, float2 a1)
+    {
+        *reinterpret_cast<float4 *>(p) = make_float4(a0.x, a0.y, a1.x, a1.y);
+    }
+};
+template <> struct PosPair<double2> {
+    __device__ static void load(const double2 *p, double2 &a0, double2 &a1)
+    {
+        a0 = __ldg(p);
+        a1 = __ldg(p + 1);
+    }
+    __device__ static void store(double2 *p, double2 a0, double2 a1)
+    {
+        p[0] = a0;
+        p[1] = a1;
+    }
+};
+
+/* per-lane branch counters of the positional step, summed over the warp at
+   the end (the same quantities as WalkStats) */
+struct PosStats {
+    unsigned int rows = 0, in = 0, rdag = 0, hph = 0, out = 0;
+    __device__ void flush(const QwStepArgs &a)
+    {
+        unsigned int v[5] = {rows, in, rdag, hph, out};
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+            for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(FULL, v[i], o);
+        if (a.stats && lane_id() == 0 && v[1]) {
+            atomicAdd(a.stats + QW_STAT_ROWS, (unsigned long long)v[0]);
+            atomicAdd(a.stats + QW_STAT_IN, (unsigned long long)v[1]);
+            atomicAdd(a.stats + QW_STAT_RDAG, (unsigned long long)v[2]);
+            atomicAdd(a.stats + QW_STAT_HPH, (unsigned long long)v[3]);
+            atomicAdd(a.stats + QW_STAT_OUT, (unsigned long long)v[4]);
+        }
+    }
+};
+
+template <typename AmpT>
+__device__ __forceinline__ unsigned int nz(AmpT a)
+{
+    return (a.x != 0 || a.y != 0) ? 1u : 0u;
+}
+
+template <typename AmpT, int S>
+__global__ void __launch_bounds__(WARPS * 32, 4) k_walk_pos(QwSimDev d, const AmpT *__restrict__ pin,
+                                                            AmpT *__restrict__ pout, QwStepArgs a)
+{
+    typedef typename Amp<AmpT>::RotVal RotVal;
+    constexpr int RPP = 32 / S;
+    __shared__ double block_part[WARPS];
+    __shared__ int is_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool skip = *(volatile int32_t *)a.status != 0;
+    const bool rescale = a.scale_in != nullptr;
+    const typename Amp<AmpT>::Scale scale(rescale ? *a.scale_in : 1.0);
+    typename Amp<AmpT>::Norm nrm;
+    PosStats st;
+    const AmpT zero = Amp<AmpT>::zero();
+    const int64_t R = d.pos_R;
+    const int E = d.pos_E;
+    const int64_t n = d.n_single;
+    const int64_t ngroups = skip ? 0 : (n + RPP - 1) / RPP;
+    const int64_t nwarps = (int64_t)gridDim.x * WARPS;
+    const int ul = lane / S, l = lane % S;
+    const int nx = RPP * 2 * E; /* extra items of a group: (unit, b1, e) */
+    for (int64_t g = (int64_t)blockIdx.x * WARPS + warp; g < ngroups; g += nwarps) {
+        const int64_t j = g * RPP + ul;
+        const bool valid = j < n;
+        uint32_t w = 0;
+        RotVal rv = Amp<AmpT>::rot_zero();
+        int64_t tp = 0;
+        AmpT a0 = zero, a1 = zero, q0 = zero, q1 = zero;
+        if (valid) {
+            const int64_t at = j * S + l;
+            w = __ldg(d.img + at);
+            const RotVal t = __ldg(static_cast<const RotVal *>(d.slot_rot) + at);
+            tp = __ldg(d.pos_tp + at);
+            PosPair<AmpT>::load(pin + 2 * j * R + 2 * l, a0, a1);
+            PosPair<AmpT>::load(pin + (2 * j + 1) * R + 2 * l, q0, q1);
+            if ((w & 0xffffu) != 0) rv = t; /* a slot whose element is 0 rotates by R(0) */
+            if (rescale) {
+                a0 = scale.apply(a0);
+                a1 = scale.apply(a1);
+                q0 = scale.apply(q0);
+                q1 = scale.apply(q1);
+            }
+        }
+        const unsigned int nin = nz(a0) + nz(a1) + nz(q0) + nz(q1);
+        st.in += nin;
+        {
+            const unsigned m = __ballot_sync(FULL, nin != 0);
+            const unsigned um = S == 32 ? m : (m >> (ul * S)) & ((1u << (S & 31)) - 1u);
+            if (l == 0 && um != 0) st.rows += 1; /* units holding branches */
+        }
+        const uint32_t col = w >> 16, val = w & 0xffffu;
+        const bool sneg = (uint32_t)j > col;
+
+        /* b1 = 0: R^dag, H P H on the zero-type group (the unit's lanes), R */
+        AmpT rA0, rA1;
+        bool eA0, eA1;
+        {
+            AmpT o0, o1;
+            Amp<AmpT>::rot(rv, val, true, sneg, a0, a1, o0, o1);
+            const bool c0 = Amp<AmpT>::keep(d, o0), c1 = Amp<AmpT>::keep(d, o1);
+            st.rdag += (c0 ? 1u : 0u) + (c1 ? 1u : 0u);
+            const AmpT z0 = c0 ? o0 : zero;
+            typename Amp<AmpT>::Sum sum;
+            sum.add(z0);
+            sum.reduce(S, S);
+            if (a.qls_readout && valid && l == 0) {
+                const double2 sv = sum.value();
+                const double coef = a.qls_coefs[*a.qls_j];
+                double2 acc = a.qls_y[j];
+                acc.x += coef * (d.inv_sqrt_s * sv.x);
+                acc.y += coef * (d.inv_sqrt_s * sv.y);
+                a.qls_y[j] = acc;
+            }
+            sum.scale_pow2(d.two_over_s);
+            const AmpT h0 = sum.minus(z0);
+            const bool d0 = Amp<AmpT>::keep(d, h0);
+            st.hph += (d0 ? 1u : 0u) + (c1 ? 1u : 0u);
+            Amp<AmpT>::rot(rv, val, false, sneg, d0 ? h0 : zero, c1 ? Amp<AmpT>::neg(o1) : zero, rA0, rA1);
+            eA0 = Amp<AmpT>::keep(d, rA0);
+            eA1 = Amp<AmpT>::keep(d, rA1);
+        }
+        /* b1 = 1: R^dag, -1, R */
+        AmpT rB0, rB1;
+        bool eB0, eB1;
+        {
+            AmpT o0, o1;
+            Amp<AmpT>::rot(rv, val, true, sneg, q0, q1, o0, o1);
+            const bool c0 = Amp<AmpT>::keep(d, o0), c1 = Amp<AmpT>::keep(d, o1);
+            const unsigned int kept = (c0 ? 1u : 0u) + (c1 ? 1u : 0u);
+            st.rdag += kept;
+            st.hph += kept;
+            Amp<AmpT>::rot(rv, val, false, sneg, c0 ? Amp<AmpT>::neg(o0) : zero, c1 ? Amp<AmpT>::neg(o1) : zero,
+                           rB0, rB1);
+            eB0 = Amp<AmpT>::keep(d, rB0);
+            eB1 = Amp<AmpT>::keep(d, rB1);
+        }
+        /* S: rows (col, 0) and (col, 1), positions tp (from b1 = 0), tp + 1 */
+        if (valid) {
+            const AmpT s0 = eA0 ? rA0 : zero, s1 = eB0 ? rB0 : zero;
+            const AmpT s2 = eA1 ? rA1 : zero, s3 = eB1 ? rB1 : zero;
+            if (eA0) nrm.add(rA0);
+            if (eB0) nrm.add(rB0);
+            if (eA1) nrm.add(rA1);
+            if (eB1) nrm.add(rB1);
+            st.out += (eA0 ? 1u : 0u) + (eB0 ? 1u : 0u) + (eA1 ? 1u : 0u) + (eB1 ? 1u : 0u);
+            PosPair<AmpT>::store(pout + 2 * (int64_t)col * R + tp, s0, s1);
+            PosPair<AmpT>::store(pout + (2 * (int64_t)col + 1) * R + tp, s2, s3);
+        }
+
+        /* the extras of the group's rows */
+        for (int it = lane; it < nx; it += 32) {
+            const int uu = it / (2 * E), rem = it - uu * 2 * E, xb1 = rem / E, e = rem - xb1 * E;
+            const int64_t jx = g * RPP + uu;
+            if (jx >= n || e >= (int)__ldg(d.pos_xcnt + jx)) continue;
+            const uint32_t xe = __ldg(d.pos_xin + jx * E + e);
+            AmpT x0, x1;
+            PosPair<AmpT>::load(pin + (2 * jx + xb1) * R + 2 * S + 2 * e, x0, x1);
+            if (rescale) {
+                x0 = scale.apply(x0);
+                x1 = scale.apply(x1);
+            }
+            st.in += nz(x0) + nz(x1);
+            AmpT o0, o1;
+            Amp<AmpT>::rot(Amp<AmpT>::rot_zero(), 0u, true, false, x0, x1, o0, o1);
+            const bool c0 = Amp<AmpT>::keep(d, o0), c1 = Amp<AmpT>::keep(d, o1);
+            const unsigned int kept = (c0 ? 1u : 0u) + (c1 ? 1u : 0u);
+            st.rdag += kept;
+            st.hph += kept;
+            AmpT r0, r1;
+            Amp<AmpT>::rot(Amp<AmpT>::rot_zero(), 0u, false, false, c0 ? Amp<AmpT>::neg(o0) : zero,
+                           c1 ? Amp<AmpT>::neg(o1) : zero, r0, r1);
+            const bool e0 = Amp<AmpT>::keep(d, r0), e1 = Amp<AmpT>::keep(d, r1);
+            if (e0) nrm.add(r0);
+            if (e1) nrm.add(r1);
+            st.out += (e0 ? 1u : 0u) + (e1 ? 1u : 0u);
+            const int64_t x = (int64_t)(xe >> 8), px = 2 * (int64_t)(xe & 0xffu) + xb1;
+            pout[2 * x * R + px] = e0 ? r0 : zero;
+            pout[(2 * x + 1) * R + px] = e1 ? r1 : zero;
+        }
+    }
+    st.flush(a);
+
+    /* end of the step: block partial of the norm, the last block reduces */
+    double nv = warp_sum(nrm.get());
+    if (lane == 0) block_part[warp] = nv;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < WARPS; ++w) sum += block_part[w];
+        a.partials[blockIdx.x] = sum;
+        __threadfence();
+        const unsigned prev = atomicAdd(a.done_ctr, 1u);
+        is_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double v = 0.0;
+    for (unsigned bb = threadIdx.x; bb < gridDim.x; bb += blockDim.x) v += __ldcg(a.partials + bb);
+    v = warp_sum(v);
+    if (lane == 0) block_part[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < WARPS; ++w) tot += block_part[w];
+        const bool clean = *(volatile int32_t *)a.status == 0;
+        if (clean) {
+            *a.norm_out = tot;
+            if (a.scale_out) *a.scale_out = (a.renorm && tot > 0.0) ? sqrt(*a.renorm_target / tot) : 1.0;
+            if (a.steps_done) *a.steps_done += 1;
+            if (a.stats) a.stats[QW_STAT_STEPS] += 1;
+        }
+        *a.done_ctr = 0u;
+    }
+}
+
+/* the row buckets into the positional layout (pbuf zeroed by the caller):
+   one thread per bucket slot */
+template <typename AmpT>
+__global__ void k_pos_pack(QwSimDev d, QwBufDev buf, AmpT *pbuf, int32_t *status)
+{
+    const int S = d.s, E = d.pos_E;
+    const int64_t total = d.total_buckets * (int64_t)d.cap_row;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / d.cap_row;
+        const int p = (int)(i - b * d.cap_row);
+        if (p >= buf.count[b]) continue;
+        const int64_t j = b >> 1;
+        if (b >= d.dense_buckets || j >= d.n_single) { /* a row with jc != 0 or j >= N */
+            atomicOr(status, QW_ST_POS_UNREP);
+            continue;
+        }
+        const Regs x = decode_r(buf.key[i], d.nb);
+        int pos = -1;
+        if (x.kc == 0 && x.A == 0) {
+            const uint32_t *row = d.img + j * S;
+            int lo = 0, hi = S; /* lower bound of k among the row's sorted columns */
+            while (lo < hi) {
+                const int m = (lo + hi) >> 1;
+                if ((row[m] >> 16) < x.k) lo = m + 1;
+                else hi = m;
+            }
+            if (lo < S && (row[lo] >> 16) == x.k) {
+                pos = 2 * lo + (int)x.b2;
+            } else {
+                const int ne = d.pos_xcnt[j];
+                for (int e = 0; e < ne; ++e)
+                    if ((d.pos_xin[j * E + e] >> 8) == x.k) {
+                        pos = 2 * S + 2 * e + (int)x.b2;
+                        break;
+                    }
+            }
+        }
+        if (pos < 0) {
+            atomicOr(status, QW_ST_POS_UNREP);
+            continue;
+        }
+        pbuf[(int64_t)b * d.pos_R + pos] = static_cast<const AmpT *>(buf.amp)[i];
+    }
+}
+
+/* the positional layout into the row buckets (cleared by the caller): one
+   thread per position, non-zero amplitudes appended to their row */
+template <typename AmpT>
+__global__ void k_pos_unpack(QwSimDev d, const AmpT *pbuf, QwBufDev buf, int32_t *status)
+{
+    const int S = d.s, E = d.pos_E;
+    const int64_t R = d.pos_R, total = 2 * (int64_t)d.n_single * R;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const AmpT v = pbuf[i];
+        if (v.x == 0 && v.y == 0) continue;
+        const int64_t r = i / R;
+        const int q = (int)(i - r * R);
+        const int64_t j = r >> 1;
+        Regs x;
+        x.kc = 0;
+        x.A = 0;
+        x.b2 = (uint32_t)(q & 1);
+        if (q < 2 * S) {
+            x.k = d.img[j * S + (q >> 1)] >> 16;
+        } else {
+            const int e = (q - 2 * S) >> 1;
+            if (e >= (int)d.pos_xcnt[j]) { /* never written: not a branch */
+                atomicOr(status, QW_ST_POS_UNREP);
+                continue;
+            }
+            x.k = d.pos_xin[j * E + e] >> 8;
+        }
+        const int p = atomicAdd(buf.count + r, 1); /* bucket 2 j + b1 of the one instance */
+        if (p >= d.cap_row) {
+            atomicOr(status, QW_ST_ROW_OVERFLOW);
+            continue;
+        }
+        const int64_t sl = r * d.cap_row + p;
+        buf.key[sl] = encode_r(x, d.nb);
+        static_cast<AmpT *>(buf.amp)[sl] = v;
+    }
+}
+
 /* T~ on |b~> (qw_state_init): every row (jc = 0, j, b1 = 0) of the range
  * holds at most the one branch k = kc = b2 = A = 0.  T~'s Hadamard turns it
  * into the s branches (l, z = 0) with amplitude a / sqrt(s) (a group with a
@@ -2688,6 +3024,39 @@ size_t slot_smem_bytes(const QwSimDev &d)
     return (size_t)WARPS * (key32_fits(d) ? slot_per_warp<AmpT, uint32_t>(d) : slot_per_warp<AmpT, uint64_t>(d));
 }
 
+template <typename AmpT, int S>
+int pos_grid_s(const QwSimDev &d)
+{
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_pos<AmpT, S>, WARPS * 32, 0);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t groups = ((int64_t)d.n_single + (32 / S) - 1) / (32 / S);
+    const int64_t want = (groups + WARPS - 1) / WARPS;
+    int64_t g = (int64_t)per_sm * qw_sm_count();
+    if (want < g) g = want;
+    return (int)(g < 1 ? 1 : g);
+}
+
+template <typename AmpT>
+int pos_grid_t(const QwSimDev &d)
+{
+    if (d.s == 8) return pos_grid_s<AmpT, 8>(d);
+    if (d.s == 16) return pos_grid_s<AmpT, 16>(d);
+    return pos_grid_s<AmpT, 32>(d);
+}
+
+template <typename AmpT>
+cudaError_t launch_pos_t(const QwSimDev &d, const void *pin, void *pout, const QwStepArgs &a, int grid,
+                         cudaStream_t st)
+{
+    const AmpT *i = static_cast<const AmpT *>(pin);
+    AmpT *o = static_cast<AmpT *>(pout);
+    if (d.s == 8) k_walk_pos<AmpT, 8><<<grid, WARPS * 32, 0, st>>>(d, i, o, a);
+    else if (d.s == 16) k_walk_pos<AmpT, 16><<<grid, WARPS * 32, 0, st>>>(d, i, o, a);
+    else k_walk_pos<AmpT, 32><<<grid, WARPS * 32, 0, st>>>(d, i, o, a);
+    return cudaGetLastError();
+}
+
 } // namespace
 
 /* SM count of the current device, cached per device (launch shapes follow
@@ -2776,6 +3145,36 @@ cudaError_t qw_launch_clear(const QwSimDev &d, const QwBufDev &buf, int64_t lo, 
     if (grid < 1) grid = 1;
     if (grid > 4 * qw_sm_count()) grid = 4 * qw_sm_count();
     k_clear<<<grid, 256, 0, st>>>(buf, lo, hi, d.spill_slots, clear_spill);
+    return cudaGetLastError();
+}
+
+int qw_pos_grid(const QwSimDev &d, int fp32)
+{
+    return fp32 ? pos_grid_t<float2>(d) : pos_grid_t<double2>(d);
+}
+
+cudaError_t qw_launch_walk_pos(const QwSimDev &d, const void *pin, void *pout, const QwStepArgs &a, int fp32,
+                               int grid, cudaStream_t st)
+{
+    if (!qw_slot_supported(d)) return cudaErrorInvalidValue;
+    return fp32 ? launch_pos_t<float2>(d, pin, pout, a, grid, st) : launch_pos_t<double2>(d, pin, pout, a, grid, st);
+}
+
+cudaError_t qw_launch_pos_pack(const QwSimDev &d, const QwBufDev &buf, void *pbuf, int fp32, int32_t *status,
+                               cudaStream_t st)
+{
+    const int grid = 4 * qw_sm_count();
+    if (fp32) k_pos_pack<float2><<<grid, 256, 0, st>>>(d, buf, static_cast<float2 *>(pbuf), status);
+    else k_pos_pack<double2><<<grid, 256, 0, st>>>(d, buf, static_cast<double2 *>(pbuf), status);
+    return cudaGetLastError();
+}
+
+cudaError_t qw_launch_pos_unpack(const QwSimDev &d, const void *pbuf, const QwBufDev &buf, int fp32,
+                                 int32_t *status, cudaStream_t st)
+{
+    const int grid = 4 * qw_sm_count();
+    if (fp32) k_pos_unpack<float2><<<grid, 256, 0, st>>>(d, static_cast<const float2 *>(pbuf), buf, status);
+    else k_pos_unpack<double2><<<grid, 256, 0, st>>>(d, static_cast<const double2 *>(pbuf), buf, status);
     return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ EXPORTED = ("qw_sim_opts_default", "qw_sim_create", "qw_state_init", "qw_apply_w
             "qw_part_walk", "qw_faithful_info", "qw_faithful_begin", "qw_faithful_apply",
             "qw_faithful_export", "qw_faithful_end")
 MEASURE_NOALLOC_MAX_LEN = 65536
-WALK_VARIANTS = 7  # QW_WALK_VARIANTS
+WALK_VARIANTS = 8  # QW_WALK_VARIANTS
 
 # register-faithful sub-operations (QW_FQ_* of qwalk.h)
 FQ = {"ADDR_COL": 1, "QRAM_COL": 2, "QBS_FWD": 3, "QBS_BWD": 4, "SWAP": 5, "ADDR_VAL": 6, "QRAM_VAL": 7,
