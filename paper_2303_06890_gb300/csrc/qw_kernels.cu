@@ -497,6 +497,12 @@ template <> struct Amp<double2> {
         double v = 0.0;
         __device__ void add(T a) { v = fma(a.x, a.x, fma(a.y, a.y, v)); }
         __device__ double get() const { return v; }
+        __device__ double warp_total() const
+        {
+            double t = v;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+            return t;
+        }
     };
     /* sum of a zero-type Hadamard group (FP64) */
     struct Sum {
@@ -550,6 +556,9 @@ template <> struct Amp<double2> {
         double s;
         __device__ explicit Scale(double v) : s(v) {}
         __device__ T apply(T a) const { return scale_c128(a, s); }
+        /* staged once per block (the factor in 8 bytes of shared memory) */
+        __device__ static void to_shared(double v, double *buf) { buf[0] = v; }
+        __device__ static Scale from_shared(const double *buf) { return Scale(buf[0]); }
     };
     typedef double2 RotVal; /* (sqrt|a|, sqrt(1-|a|)) */
     __device__ static RotVal rot_table(const QwSimDev &d, uint32_t A) { return __ldg(d.fg + A); }
@@ -576,6 +585,9 @@ template <> struct Amp<float2> {
             hi = s;
         }
         __device__ double get() const { return (double)hi + (double)lo; }
+        /* the warp's sum: a butterfly of float-pair additions, one conversion
+           to FP64 on the lane that returns it (lane 0; the others return 0) */
+        __device__ double warp_total() const;
     };
     /* float-pair (hi + lo) accumulator built from Knuth's TwoSum (the sum and
        its exact rounding error), ~48 significant bits */
@@ -675,7 +687,21 @@ template <> struct Amp<float2> {
     struct Scale { /* the FP64 factor as a float pair, applied with one rounding */
         float sh, sl;
         __device__ explicit Scale(double v) : sh((float)v), sl((float)(v - (double)(float)v)) {}
+        __device__ Scale(float h, float l) : sh(h), sl(l) {}
         __device__ T apply(T a) const { return make_float2(mul_split(a.x, sh, sl), mul_split(a.y, sh, sl)); }
+        /* the split computed once per block (its FP64 conversions would
+           otherwise take a slot of the 1/64-rate FP64 pipe in every thread) */
+        __device__ static void to_shared(double v, double *buf)
+        {
+            float *f = reinterpret_cast<float *>(buf);
+            f[0] = (float)v;
+            f[1] = (float)(v - (double)(float)v);
+        }
+        __device__ static Scale from_shared(const double *buf)
+        {
+            const float *f = reinterpret_cast<const float *>(buf);
+            return Scale(f[0], f[1]);
+        }
     };
     /* round(A x + B y), A = ah + al, B = bh + bl: the products by the FMA-based
        TwoProduct (p = fl(a b), e = fma(a, b, -p) exact), their sum by Knuth's
@@ -698,6 +724,18 @@ template <> struct Amp<float2> {
     __device__ static RotVal rot_zero() { return make_float4(0.f, 0.f, 1.f, 0.f); }
     __device__ static void rot(RotVal t, uint32_t A, bool dag, bool sneg, T a0, T a1, T &o0, T &o1);
 };
+
+__device__ double Amp<float2>::Norm::warp_total() const
+{
+    DF v;
+    v.h = hi;
+    v.l = lo;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(FULL, v.h, o), ol = __shfl_xor_sync(FULL, v.l, o);
+        v.add(oh, ol);
+    }
+    return lane_id() == 0 ? (double)v.h + (double)v.l : 0.0;
+}
 
 /* multiply by 1 (real f) or by i*sigma (imaginary f), sigma = sneg ? -1 : 1:
  * i sigma (x + i y) = -sigma y + i sigma x */
@@ -2309,11 +2347,25 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_slot(QwSimDev d, QwBufDe
  * lanes for b1 = 0, -1 for b1 = 1), R; S sends its b2 = 0 / 1 outputs to rows
  * (col, 0) / (col, 1) at position tp(j, l) + b1, where tp is the position of
  * k = j in row col.  An extra (j, b1, e) is outside every zero-type group and
- * its maps leave A = 0: R(0) (-R(0)^dag) on its pair, sent to positions
- * 2 l_x + b1 of rows (x, 0 / 1).  Every position of the output has exactly
+ * its maps leave A = 0 (kc = x ^ col(j, 0) != 0 after O_s'^dag, so O_A' does
+ * not fire): R(0) (-1) R(0)^dag = -1 on its pair, sent to positions 2 l_x + b1
+ * of rows (x, 0 / 1).  Every position of the output has exactly
  * one writer, and pruned outputs are written as 0: no counts, atomics,
  * searches or keys, and nothing to clear between steps.
  */
+/* launch shape of k_walk_pos per amplitude type (measured on GB300 at
+   N = 16384, s = 16): complex64 runs fastest with 16 warps per SM and up to
+   128 registers a thread (the next group's inputs held in registers while
+   the current one computes), complex128 -- bound by the FP64 pipe -- with
+   blocks of 4 warps, 5 per SM */
+template <typename AmpT> struct PosCfg;
+template <> struct PosCfg<float2> {
+    static constexpr int warps = 8, blocks = 2;
+};
+template <> struct PosCfg<double2> {
+    static constexpr int warps = 4, blocks = 5;
+};
+
 template <typename AmpT> struct PosPair;
 template <> struct PosPair<float2> {
     __device__ static void load(const float2 *p, float2 &a0, float2 &a1)
@@ -2360,24 +2412,32 @@ struct PosStats {
     }
 };
 
-template <typename AmpT>
-__device__ __forceinline__ unsigned int nz(AmpT a)
+/* 1 for a non-zero amplitude (+-0 is zero), tested on the bits: an FP64
+   comparison would take a slot of the FP64 pipe */
+__device__ __forceinline__ unsigned int nz(float2 a)
 {
-    return (a.x != 0 || a.y != 0) ? 1u : 0u;
+    return ((__float_as_uint(a.x) | __float_as_uint(a.y)) << 1) != 0u ? 1u : 0u;
+}
+__device__ __forceinline__ unsigned int nz(double2 a)
+{
+    return (((uint64_t)__double_as_longlong(a.x) | (uint64_t)__double_as_longlong(a.y)) << 1) != 0ull ? 1u : 0u;
 }
 
-template <typename AmpT, int S>
-__global__ void __launch_bounds__(WARPS * 32, 4) k_walk_pos(QwSimDev d, const AmpT *__restrict__ pin,
+template <typename AmpT, int S, int PW>
+__global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSimDev d, const AmpT *__restrict__ pin,
                                                             AmpT *__restrict__ pout, QwStepArgs a)
 {
     typedef typename Amp<AmpT>::RotVal RotVal;
     constexpr int RPP = 32 / S;
-    __shared__ double block_part[WARPS];
+    __shared__ double block_part[PW];
+    __shared__ double scale_sm;
     __shared__ int is_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool skip = *(volatile int32_t *)a.status != 0;
     const bool rescale = a.scale_in != nullptr;
-    const typename Amp<AmpT>::Scale scale(rescale ? *a.scale_in : 1.0);
+    if (threadIdx.x == 0) Amp<AmpT>::Scale::to_shared(rescale ? *a.scale_in : 1.0, &scale_sm);
+    __syncthreads();
+    const typename Amp<AmpT>::Scale scale = Amp<AmpT>::Scale::from_shared(&scale_sm);
     typename Amp<AmpT>::Norm nrm;
     PosStats st;
     const AmpT zero = Amp<AmpT>::zero();
@@ -2385,30 +2445,56 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_pos(QwSimDev d, const Am
     const int E = d.pos_E;
     const int64_t n = d.n_single;
     const int64_t ngroups = skip ? 0 : (n + RPP - 1) / RPP;
-    const int64_t nwarps = (int64_t)gridDim.x * WARPS;
+    const int64_t nwarps = (int64_t)gridDim.x * PW;
     const int ul = lane / S, l = lane % S;
     const int nx = RPP * 2 * E; /* extra items of a group: (unit, b1, e) */
-    for (int64_t g = (int64_t)blockIdx.x * WARPS + warp; g < ngroups; g += nwarps) {
+    /* the lane's first extra item is the same in every group */
+    int x_u = 0, x_b1 = 0, x_e = 0;
+    if (lane < nx) {
+        x_u = lane / (2 * E);
+        const int rem = lane - x_u * 2 * E;
+        x_b1 = rem / E;
+        x_e = rem - x_b1 * E;
+    }
+    /* a group's inputs, loaded one group ahead: the next group's loads are in
+       flight while the current one computes */
+    struct In {
+        uint32_t w;
+        RotVal t;
+        int tp;
+        AmpT a0, a1, q0, q1;
+    };
+    auto fetch = [&](int64_t gg, In &x) {
+        const int64_t jj = gg * RPP + ul;
+        x.w = 0;
+        x.t = Amp<AmpT>::rot_zero();
+        x.tp = 0;
+        x.a0 = x.a1 = x.q0 = x.q1 = zero;
+        if (gg < ngroups && jj < n) {
+            const int64_t at = jj * S + l;
+            x.w = __ldg(d.img + at);
+            x.t = __ldg(static_cast<const RotVal *>(d.slot_rot) + at);
+            x.tp = __ldg(d.pos_tp + at);
+            PosPair<AmpT>::load(pin + 2 * jj * R + 2 * l, x.a0, x.a1);
+            PosPair<AmpT>::load(pin + (2 * jj + 1) * R + 2 * l, x.q0, x.q1);
+        }
+    };
+    In nxt;
+    fetch((int64_t)blockIdx.x * PW + warp, nxt);
+    for (int64_t g = (int64_t)blockIdx.x * PW + warp; g < ngroups; g += nwarps) {
+        const In cur = nxt;
+        fetch(g + nwarps, nxt);
         const int64_t j = g * RPP + ul;
         const bool valid = j < n;
-        uint32_t w = 0;
-        RotVal rv = Amp<AmpT>::rot_zero();
-        int64_t tp = 0;
-        AmpT a0 = zero, a1 = zero, q0 = zero, q1 = zero;
-        if (valid) {
-            const int64_t at = j * S + l;
-            w = __ldg(d.img + at);
-            const RotVal t = __ldg(static_cast<const RotVal *>(d.slot_rot) + at);
-            tp = __ldg(d.pos_tp + at);
-            PosPair<AmpT>::load(pin + 2 * j * R + 2 * l, a0, a1);
-            PosPair<AmpT>::load(pin + (2 * j + 1) * R + 2 * l, q0, q1);
-            if ((w & 0xffffu) != 0) rv = t; /* a slot whose element is 0 rotates by R(0) */
-            if (rescale) {
-                a0 = scale.apply(a0);
-                a1 = scale.apply(a1);
-                q0 = scale.apply(q0);
-                q1 = scale.apply(q1);
-            }
+        const uint32_t w = cur.w;
+        const RotVal rv = (w & 0xffffu) != 0 ? cur.t : Amp<AmpT>::rot_zero(); /* a 0 element rotates by R(0) */
+        const int64_t tp = cur.tp;
+        AmpT a0 = cur.a0, a1 = cur.a1, q0 = cur.q0, q1 = cur.q1;
+        if (valid && rescale) {
+            a0 = scale.apply(a0);
+            a1 = scale.apply(a1);
+            q0 = scale.apply(q0);
+            q1 = scale.apply(q1);
         }
         const unsigned int nin = nz(a0) + nz(a1) + nz(q0) + nz(q1);
         st.in += nin;
@@ -2478,7 +2564,13 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_pos(QwSimDev d, const Am
 
         /* the extras of the group's rows */
         for (int it = lane; it < nx; it += 32) {
-            const int uu = it / (2 * E), rem = it - uu * 2 * E, xb1 = rem / E, e = rem - xb1 * E;
+            int uu = x_u, xb1 = x_b1, e = x_e;
+            if (it != lane) {
+                uu = it / (2 * E);
+                const int rem = it - uu * 2 * E;
+                xb1 = rem / E;
+                e = rem - xb1 * E;
+            }
             const int64_t jx = g * RPP + uu;
             if (jx >= n || e >= (int)__ldg(d.pos_xcnt + jx)) continue;
             const uint32_t xe = __ldg(d.pos_xin + jx * E + e);
@@ -2489,19 +2581,19 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_pos(QwSimDev d, const Am
                 x1 = scale.apply(x1);
             }
             st.in += nz(x0) + nz(x1);
-            AmpT o0, o1;
-            Amp<AmpT>::rot(Amp<AmpT>::rot_zero(), 0u, true, false, x0, x1, o0, o1);
-            const bool c0 = Amp<AmpT>::keep(d, o0), c1 = Amp<AmpT>::keep(d, o1);
-            const unsigned int kept = (c0 ? 1u : 0u) + (c1 ? 1u : 0u);
+            /* R(0) (-1) R(0)^dag with R(0) = [[0, -1], [1, 0]]: R(0)^dag gives
+               (x1, -x0), -1 and R(0) give (-x0, -x1) -- each output the
+               negated input, kept where the input is (every product is by
+               0 or 1, so this is the general rotation's result exactly) */
+            const bool k0 = Amp<AmpT>::keep(d, x0), k1 = Amp<AmpT>::keep(d, x1);
+            const unsigned int kept = (k0 ? 1u : 0u) + (k1 ? 1u : 0u);
             st.rdag += kept;
             st.hph += kept;
-            AmpT r0, r1;
-            Amp<AmpT>::rot(Amp<AmpT>::rot_zero(), 0u, false, false, c0 ? Amp<AmpT>::neg(o0) : zero,
-                           c1 ? Amp<AmpT>::neg(o1) : zero, r0, r1);
-            const bool e0 = Amp<AmpT>::keep(d, r0), e1 = Amp<AmpT>::keep(d, r1);
+            st.out += kept;
+            const AmpT r0 = Amp<AmpT>::neg(x0), r1 = Amp<AmpT>::neg(x1);
+            const bool e0 = k0, e1 = k1;
             if (e0) nrm.add(r0);
             if (e1) nrm.add(r1);
-            st.out += (e0 ? 1u : 0u) + (e1 ? 1u : 0u);
             const int64_t x = (int64_t)(xe >> 8), px = 2 * (int64_t)(xe & 0xffu) + xb1;
             pout[2 * x * R + px] = e0 ? r0 : zero;
             pout[(2 * x + 1) * R + px] = e1 ? r1 : zero;
@@ -2510,12 +2602,12 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_pos(QwSimDev d, const Am
     st.flush(a);
 
     /* end of the step: block partial of the norm, the last block reduces */
-    double nv = warp_sum(nrm.get());
+    const double nv = nrm.warp_total();
     if (lane == 0) block_part[warp] = nv;
     __syncthreads();
     if (threadIdx.x == 0) {
         double sum = 0.0;
-        for (int w = 0; w < WARPS; ++w) sum += block_part[w];
+        for (int w = 0; w < PW; ++w) sum += block_part[w];
         a.partials[blockIdx.x] = sum;
         __threadfence();
         const unsigned prev = atomicAdd(a.done_ctr, 1u);
@@ -2531,7 +2623,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_pos(QwSimDev d, const Am
     __syncthreads();
     if (threadIdx.x == 0) {
         double tot = 0.0;
-        for (int w = 0; w < WARPS; ++w) tot += block_part[w];
+        for (int w = 0; w < PW; ++w) tot += block_part[w];
         const bool clean = *(volatile int32_t *)a.status == 0;
         if (clean) {
             *a.norm_out = tot;
@@ -3027,13 +3119,17 @@ size_t slot_smem_bytes(const QwSimDev &d)
 template <typename AmpT, int S>
 int pos_grid_s(const QwSimDev &d)
 {
+    constexpr int PW = PosCfg<AmpT>::warps;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_pos<AmpT, S>, WARPS * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_pos<AmpT, S, PW>, PW * 32, 0);
     if (per_sm < 1) per_sm = 1;
+    /* as many groups for every warp: with k = ceil(groups / resident warps)
+       groups a warp, the fewest blocks that cover them (a warp with fewer
+       groups than the others would wait for them at the end of the step) */
     const int64_t groups = ((int64_t)d.n_single + (32 / S) - 1) / (32 / S);
-    const int64_t want = (groups + WARPS - 1) / WARPS;
-    int64_t g = (int64_t)per_sm * qw_sm_count();
-    if (want < g) g = want;
+    const int64_t cap = (int64_t)per_sm * qw_sm_count();
+    const int64_t k = (groups + cap * PW - 1) / (cap * PW);
+    const int64_t g = (groups + k * PW - 1) / (k * PW);
     return (int)(g < 1 ? 1 : g);
 }
 
@@ -3051,9 +3147,10 @@ cudaError_t launch_pos_t(const QwSimDev &d, const void *pin, void *pout, const Q
 {
     const AmpT *i = static_cast<const AmpT *>(pin);
     AmpT *o = static_cast<AmpT *>(pout);
-    if (d.s == 8) k_walk_pos<AmpT, 8><<<grid, WARPS * 32, 0, st>>>(d, i, o, a);
-    else if (d.s == 16) k_walk_pos<AmpT, 16><<<grid, WARPS * 32, 0, st>>>(d, i, o, a);
-    else k_walk_pos<AmpT, 32><<<grid, WARPS * 32, 0, st>>>(d, i, o, a);
+    constexpr int PW = PosCfg<AmpT>::warps;
+    if (d.s == 8) k_walk_pos<AmpT, 8, PW><<<grid, PW * 32, 0, st>>>(d, i, o, a);
+    else if (d.s == 16) k_walk_pos<AmpT, 16, PW><<<grid, PW * 32, 0, st>>>(d, i, o, a);
+    else k_walk_pos<AmpT, 32, PW><<<grid, PW * 32, 0, st>>>(d, i, o, a);
     return cudaGetLastError();
 }
 
