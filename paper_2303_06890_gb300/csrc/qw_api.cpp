@@ -1008,8 +1008,8 @@ static int pos_build(qw_sim *sim)
         }
     size_t E = 0;
     for (const auto &v : xin) E = std::max(E, v.size());
-    if (2 * s + 2 * E >= 65535 || n >= (1 << 24))
-        return fail(sim, QW_ERR_ARG, "positional layout: too many unpaired padded columns in a row");
+    if (2 * s + 2 * E >= 65535 || n >= (1 << 24) || 2 * n * (int64_t)(2 * s + 2 * E) >= ((int64_t)1 << 31))
+        return fail(sim, QW_ERR_ARG, "positional layout: too many unpaired padded columns in a row, or rows");
     std::vector<uint32_t> hx((size_t)n * std::max<size_t>(E, 1), 0u);
     std::vector<uint16_t> hc((size_t)n);
     for (int64_t c = 0; c < n; ++c) {

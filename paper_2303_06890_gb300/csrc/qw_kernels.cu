@@ -2363,7 +2363,7 @@ template <> struct PosCfg<float2> {
     static constexpr int warps = 8, blocks = 2;
 };
 template <> struct PosCfg<double2> {
-    static constexpr int warps = 4, blocks = 5;
+    static constexpr int warps = 4, blocks = 4;
 };
 
 template <typename AmpT> struct PosPair;
@@ -2435,17 +2435,15 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool skip = *(volatile int32_t *)a.status != 0;
     const bool rescale = a.scale_in != nullptr;
-    if (threadIdx.x == 0) Amp<AmpT>::Scale::to_shared(rescale ? *a.scale_in : 1.0, &scale_sm);
-    __syncthreads();
-    const typename Amp<AmpT>::Scale scale = Amp<AmpT>::Scale::from_shared(&scale_sm);
     typename Amp<AmpT>::Norm nrm;
     PosStats st;
     const AmpT zero = Amp<AmpT>::zero();
-    const int64_t R = d.pos_R;
+    /* 32-bit indices: the host keeps 2 N pos_R below 2^31 */
+    const uint32_t R = (uint32_t)d.pos_R;
     const int E = d.pos_E;
-    const int64_t n = d.n_single;
-    const int64_t ngroups = skip ? 0 : (n + RPP - 1) / RPP;
-    const int64_t nwarps = (int64_t)gridDim.x * PW;
+    const uint32_t n = (uint32_t)d.n_single;
+    const uint32_t nall = (n + RPP - 1) / RPP, ngroups = skip ? 0u : nall;
+    const uint32_t nwarps = gridDim.x * PW;
     const int ul = lane / S, l = lane % S;
     const int nx = RPP * 2 * E; /* extra items of a group: (unit, b1, e) */
     /* the lane's first extra item is the same in every group */
@@ -2463,32 +2461,53 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
         RotVal t;
         int tp;
         AmpT a0, a1, q0, q1;
+        uint32_t xe; /* the lane's first extra item: x << 8 | l_x, 0xffffffff if none */
+        AmpT x0, x1;
     };
-    auto fetch = [&](int64_t gg, In &x) {
-        const int64_t jj = gg * RPP + ul;
+    /* extra item (u, b1, e) of group gg: its entry and pair (none past the
+       row's extras count) */
+    auto fetch_extra = [&](uint32_t gg, int u, int b1, int e, uint32_t &xe, AmpT &x0, AmpT &x1) {
+        const uint32_t jx = gg * RPP + u;
+        xe = 0xffffffffu;
+        x0 = x1 = zero;
+        if (gg < nall && jx < n && e < (int)__ldg(d.pos_xcnt + jx)) {
+            xe = __ldg(d.pos_xin + jx * (uint32_t)E + e);
+            PosPair<AmpT>::load(pin + (2 * jx + b1) * R + 2 * S + 2 * e, x0, x1);
+        }
+    };
+    auto fetch = [&](uint32_t gg, In &x) {
+        const uint32_t jj = gg * RPP + ul;
         x.w = 0;
         x.t = Amp<AmpT>::rot_zero();
         x.tp = 0;
         x.a0 = x.a1 = x.q0 = x.q1 = zero;
-        if (gg < ngroups && jj < n) {
-            const int64_t at = jj * S + l;
+        if (gg < nall && jj < n) {
+            const uint32_t at = jj * S + l;
             x.w = __ldg(d.img + at);
             x.t = __ldg(static_cast<const RotVal *>(d.slot_rot) + at);
             x.tp = __ldg(d.pos_tp + at);
             PosPair<AmpT>::load(pin + 2 * jj * R + 2 * l, x.a0, x.a1);
             PosPair<AmpT>::load(pin + (2 * jj + 1) * R + 2 * l, x.q0, x.q1);
         }
+        x.xe = 0xffffffffu;
+        x.x0 = x.x1 = zero;
+        if (lane < nx) fetch_extra(gg, x_u, x_b1, x_e, x.xe, x.x0, x.x1);
     };
     In nxt;
-    fetch((int64_t)blockIdx.x * PW + warp, nxt);
-    for (int64_t g = (int64_t)blockIdx.x * PW + warp; g < ngroups; g += nwarps) {
+    fetch(blockIdx.x * PW + warp, nxt);
+    /* the renormalisation factor, staged once per block while the first
+       group's loads are in flight */
+    if (threadIdx.x == 0) Amp<AmpT>::Scale::to_shared(rescale ? *a.scale_in : 1.0, &scale_sm);
+    __syncthreads();
+    const typename Amp<AmpT>::Scale scale = Amp<AmpT>::Scale::from_shared(&scale_sm);
+    for (uint32_t g = blockIdx.x * PW + warp; g < ngroups; g += nwarps) {
         const In cur = nxt;
         fetch(g + nwarps, nxt);
-        const int64_t j = g * RPP + ul;
+        const uint32_t j = g * RPP + ul;
         const bool valid = j < n;
         const uint32_t w = cur.w;
         const RotVal rv = (w & 0xffffu) != 0 ? cur.t : Amp<AmpT>::rot_zero(); /* a 0 element rotates by R(0) */
-        const int64_t tp = cur.tp;
+        const uint32_t tp = (uint32_t)cur.tp;
         AmpT a0 = cur.a0, a1 = cur.a1, q0 = cur.q0, q1 = cur.q1;
         if (valid && rescale) {
             a0 = scale.apply(a0);
@@ -2504,7 +2523,7 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
             if (l == 0 && um != 0) st.rows += 1; /* units holding branches */
         }
         const uint32_t col = w >> 16, val = w & 0xffffu;
-        const bool sneg = (uint32_t)j > col;
+        const bool sneg = j > col;
 
         /* b1 = 0: R^dag, H P H on the zero-type group (the unit's lanes), R */
         AmpT rA0, rA1;
@@ -2558,24 +2577,22 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
             if (eA1) nrm.add(rA1);
             if (eB1) nrm.add(rB1);
             st.out += (eA0 ? 1u : 0u) + (eB0 ? 1u : 0u) + (eA1 ? 1u : 0u) + (eB1 ? 1u : 0u);
-            PosPair<AmpT>::store(pout + 2 * (int64_t)col * R + tp, s0, s1);
-            PosPair<AmpT>::store(pout + (2 * (int64_t)col + 1) * R + tp, s2, s3);
+            PosPair<AmpT>::store(pout + 2 * col * R + tp, s0, s1);
+            PosPair<AmpT>::store(pout + (2 * col + 1) * R + tp, s2, s3);
         }
 
-        /* the extras of the group's rows */
+        /* the extras of the group's rows: the lane's first item prefetched, any
+           further ones (more than 32 per group) loaded here */
         for (int it = lane; it < nx; it += 32) {
-            int uu = x_u, xb1 = x_b1, e = x_e;
+            int xb1 = x_b1;
+            uint32_t xe = cur.xe;
+            AmpT x0 = cur.x0, x1 = cur.x1;
             if (it != lane) {
-                uu = it / (2 * E);
-                const int rem = it - uu * 2 * E;
+                const int uu = it / (2 * E), rem = it - uu * 2 * E;
                 xb1 = rem / E;
-                e = rem - xb1 * E;
+                fetch_extra(g, uu, xb1, rem - xb1 * E, xe, x0, x1);
             }
-            const int64_t jx = g * RPP + uu;
-            if (jx >= n || e >= (int)__ldg(d.pos_xcnt + jx)) continue;
-            const uint32_t xe = __ldg(d.pos_xin + jx * E + e);
-            AmpT x0, x1;
-            PosPair<AmpT>::load(pin + (2 * jx + xb1) * R + 2 * S + 2 * e, x0, x1);
+            if (xe == 0xffffffffu) continue;
             if (rescale) {
                 x0 = scale.apply(x0);
                 x1 = scale.apply(x1);
@@ -2591,12 +2608,11 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
             st.hph += kept;
             st.out += kept;
             const AmpT r0 = Amp<AmpT>::neg(x0), r1 = Amp<AmpT>::neg(x1);
-            const bool e0 = k0, e1 = k1;
-            if (e0) nrm.add(r0);
-            if (e1) nrm.add(r1);
-            const int64_t x = (int64_t)(xe >> 8), px = 2 * (int64_t)(xe & 0xffu) + xb1;
-            pout[2 * x * R + px] = e0 ? r0 : zero;
-            pout[(2 * x + 1) * R + px] = e1 ? r1 : zero;
+            if (k0) nrm.add(r0);
+            if (k1) nrm.add(r1);
+            const uint32_t x = xe >> 8, px = 2 * (xe & 0xffu) + (uint32_t)xb1;
+            pout[2 * x * R + px] = k0 ? r0 : zero;
+            pout[(2 * x + 1) * R + px] = k1 ? r1 : zero;
         }
     }
     st.flush(a);
