@@ -7,6 +7,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
+import pytest  # noqa: E402
 
 import bench  # noqa: E402
 
@@ -28,15 +29,22 @@ def test_algorithmic_bytes_of_a_step():
     assert b_lit == ((200 + 300) + (300 + 900) + (900 + 320) + (320 + 310)) * entry / 2
 
 
-def test_profiled_traffic_follows_the_kernel_source_hash(tmp_path, monkeypatch):
-    text = open(bench.PROFILE_SLOT).read()
-    committed = bench.profiled_traffic("fp32", 4)
+@pytest.mark.parametrize("attr,variant", [("PROFILE_SLOT", 4), ("PROFILE_POS", 7)])
+def test_profiled_traffic_follows_the_kernel_source_hash(tmp_path, monkeypatch, attr, variant):
+    text = open(getattr(bench, attr)).read()
+    committed = bench.profiled_traffic("fp32", variant)
     if f"`{bench.kernel_hash()}`" in text:
         assert committed is not None and committed > 0
     stale = tmp_path / "stale.md"
     stale.write_text(text.replace("kernel_source_sha256_16: `", "kernel_source_sha256_16: `0"))
-    monkeypatch.setattr(bench, "PROFILE_SLOT", str(stale))
-    assert bench.profiled_traffic("fp32", 4) is None
+    monkeypatch.setattr(bench, attr, str(stale))
+    assert bench.profiled_traffic("fp32", variant) is None
+
+
+def test_kernel_names_follow_the_variant():
+    assert bench.kernel_name(7) == "k_walk_pos<float2, s = 16>"
+    assert bench.kernel_name(4) == "k_walk_slot<float2, s = 16>"
+    assert bench.kernel_name(0).startswith("k_walk<float2, rows")
 
 
 def test_state_error_over_the_union_of_keys():
