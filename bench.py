@@ -791,8 +791,9 @@ def schedules_leg(torch, steps: int = 6) -> dict:
 def configs_leg(torch) -> dict:
     """The two small walk workloads: N = 16 (10 steps, complex128) and N = 1024
     (100 steps, complex128 and complex64).  Per workload and precision: the
-    device time per step of the whole walk issued as graph replays (state
-    resident), and the error of the final state against the oracle's."""
+    autotuned step kernel, the device time per step of the whole walk issued
+    as graph replays (state resident), and the error of the final state
+    (a fresh walk on that kernel) against the oracle's."""
     from paper_2303_06890_gb300 import qwalk
     from paper_2303_06890_gb300 import workloads as wl
     out = {}
@@ -804,13 +805,14 @@ def configs_leg(torch) -> dict:
             label = "complex128" if prec == qwalk.QW_FP64 else "complex64"
             sim = qwalk.Sim(w.matrix, s_pad=w.s, precision=prec)
             sim.state_init(w.b)
+            variant, _ = sim.autotune(2)
             sim.apply_walk_step(6)
             reps = 20
             t = _events_time(torch, lambda: [sim.enqueue_walk_steps(w.steps) for _ in range(reps)])
             sim.sync()
             sim.close()
-            row[label] = {"us_per_step": 1e6 * t / (reps * w.steps),
-                          "error": state_error(gpu_walk_state(w, prec, w.steps), ref)}
+            row[label] = {"us_per_step": 1e6 * t / (reps * w.steps), "variant": variant,
+                          "error": state_error(gpu_walk_state(w, prec, w.steps, variant), ref)}
         out[w.name] = row
     return out
 

@@ -105,7 +105,7 @@ typedef struct {
                                 working register of O_s', O_A' and Alg. 1 held in the
                                 state between sub-operations (the QW_FQ_STEP sequence
                                 below; any fuse_reflection), 7 = the positional layout:
-                                one instance, s = 8, 16 or 32; every branch the walk
+                                s = 8, 16 or 32, any number of instances; every branch the walk
                                 reaches from T~|b~> is held at a fixed position of its
                                 row (no key, no count), one lane per QRAM slot writes
                                 each output to its position, so a step has no search,
@@ -222,9 +222,9 @@ int qw_sync(qw_sim *sim);
  * them with CUDA events on the simulator's stream, and keeps the fastest for
  * all later steps.  Segments are tried only when warp_capacity >= 2
  * row_capacity (true by default), the slot kernel only then and for s = 8, 16
- * or 32, the positional layout (variant 7) for s = 8, 16 or 32 with one
- * instance and no partitions (its tables are built first, and the move of the
- * state into it is not timed); the flat path and the register-faithful
+ * or 32, the positional layout (variant 7) for s = 8, 16 or 32 without
+ * partitions (its tables are built first, and the move of the state into it
+ * is not timed); the flat path and the register-faithful
  * schedule (variants 5 and 6) are never chosen; variants not tried are
  * reported as 0 us.  The state advances by steps_per_candidate walk steps per
  * variant tried (the variants give the same results).  *choice (nullable)

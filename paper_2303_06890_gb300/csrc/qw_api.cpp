@@ -109,6 +109,7 @@ struct qw_sim {
     uint16_t *unit_inst = nullptr;
     void *slot_rot = nullptr;
     double *partials = nullptr;
+    int partials_cap = 0;
     int32_t *deferred = nullptr; /* slot kernel: units left to its last block */
     QwPartEntry *outbox = nullptr;      /* row-partitioned walk: outbox segments */
     unsigned long long *outbox_count = nullptr;
@@ -143,6 +144,8 @@ struct qw_sim {
     uint16_t *pos_tp = nullptr;
     uint32_t *pos_xin = nullptr;
     uint16_t *pos_xcnt = nullptr;
+    uint32_t *pos_rowbase = nullptr;
+    uint16_t *pos_rowinst = nullptr;
     void *pbuf[3] = {nullptr, nullptr, nullptr};
     size_t pbuf_bytes = 0;
     bool pos_built = false;
@@ -542,6 +545,7 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
         if (qw_slot_supported(d) && ninst == 1) gmax = std::max(gmax, qw_pos_grid(d, sim->fp32));
     }
     QW_TRY(dalloc(sim, &sim->partials, (size_t)gmax));
+    sim->partials_cap = gmax;
     QW_TRY(dalloc(sim, &sim->deferred, (size_t)(d.dense_buckets / 2 + d.spill_slots)));
     if (d.nparts > 1) {
         QW_TRY(dalloc(sim, &sim->outbox, (size_t)d.nparts * (size_t)d.outbox_cap));
@@ -588,6 +592,8 @@ extern "C" int qw_sim_destroy(qw_sim *sim)
     cudaFree(sim->pos_tp);
     cudaFree(sim->pos_xin);
     cudaFree(sim->pos_xcnt);
+    cudaFree(sim->pos_rowbase);
+    cudaFree(sim->pos_rowinst);
     for (void *p : sim->pbuf) cudaFree(p);
     cudaFree(sim->img);
     cudaFree(sim->fg);
@@ -980,43 +986,60 @@ static int pos_build(qw_sim *sim)
 {
     if (sim->pos_built) return QW_OK;
     QwSimDev &d = sim->d;
-    if (d.ninst != 1 || d.nparts != 1 || !qw_slot_supported(d))
-        return fail(sim, QW_ERR_ARG, "walk_variant 7 (positional) needs one instance, no partitions and s = 8, 16 "
-                                     "or 32");
-    const int64_t n = d.n_single;
+    if (d.nparts != 1 || !qw_slot_supported(d))
+        return fail(sim, QW_ERR_ARG, "walk_variant 7 (positional) needs s = 8, 16 or 32 and no partitions");
     const int s = d.s;
-    std::vector<uint32_t> img((size_t)n * s);
+    const int ninst = d.ninst;
+    /* rows of all instances in order: instance i starts at row inst_img[i] / s */
+    int64_t nrows = 0;
+    std::vector<int64_t> row0((size_t)ninst);
+    for (int i = 0; i < ninst; ++i) {
+        row0[(size_t)i] = nrows;
+        nrows += sim->n_of[(size_t)i];
+    }
+    std::vector<uint32_t> img((size_t)nrows * s);
     QW_CUDA(sim, cudaMemcpy(img.data(), sim->img, img.size() * 4, cudaMemcpyDeviceToHost));
-    std::vector<uint16_t> tp((size_t)n * s);
-    std::vector<std::vector<uint32_t>> xin((size_t)n);
-    for (int64_t j = 0; j < n; ++j)
-        for (int l = 0; l < s; ++l) {
-            const uint32_t c = img[(size_t)(j * s + l)] >> 16;
-            const uint32_t *row = img.data() + (size_t)c * s;
-            int lo = 0, hi = s;
-            while (lo < hi) {
-                const int m = (lo + hi) >> 1;
-                if ((row[m] >> 16) < (uint32_t)j) lo = m + 1;
-                else hi = m;
+    std::vector<uint16_t> tp((size_t)nrows * s);
+    std::vector<std::vector<uint32_t>> xin((size_t)nrows);
+    std::vector<uint32_t> rowbase(ninst > 1 ? (size_t)nrows : 0);
+    std::vector<uint16_t> rowinst(ninst > 1 ? (size_t)nrows : 0);
+    for (int i = 0; i < ninst; ++i) {
+        const int64_t g0 = row0[(size_t)i], n = sim->n_of[(size_t)i];
+        for (int64_t j = 0; j < n; ++j) {
+            if (ninst > 1) {
+                rowbase[(size_t)(g0 + j)] = (uint32_t)g0;
+                rowinst[(size_t)(g0 + j)] = (uint16_t)i;
             }
-            if (lo < s && (row[lo] >> 16) == (uint32_t)j) {
-                tp[(size_t)(j * s + l)] = (uint16_t)(2 * lo);
-            } else {
-                tp[(size_t)(j * s + l)] = (uint16_t)(2 * s + 2 * xin[c].size());
-                xin[c].push_back((uint32_t)j << 8 | (uint32_t)l);
+            for (int l = 0; l < s; ++l) {
+                const uint32_t c = img[(size_t)((g0 + j) * s + l)] >> 16;
+                const uint32_t *row = img.data() + (size_t)(g0 + c) * s;
+                int lo = 0, hi = s;
+                while (lo < hi) {
+                    const int m = (lo + hi) >> 1;
+                    if ((row[m] >> 16) < (uint32_t)j) lo = m + 1;
+                    else hi = m;
+                }
+                auto &xc = xin[(size_t)(g0 + c)];
+                if (lo < s && (row[lo] >> 16) == (uint32_t)j) {
+                    tp[(size_t)((g0 + j) * s + l)] = (uint16_t)(2 * lo);
+                } else {
+                    tp[(size_t)((g0 + j) * s + l)] = (uint16_t)(2 * s + 2 * xc.size());
+                    xc.push_back((uint32_t)(g0 + j) << 8 | (uint32_t)l);
+                }
             }
         }
+    }
     size_t E = 0;
     for (const auto &v : xin) E = std::max(E, v.size());
-    if (2 * s + 2 * E >= 65535 || n >= (1 << 24) || 2 * n * (int64_t)(2 * s + 2 * E) >= ((int64_t)1 << 31))
+    const int64_t R = 2 * s + 2 * (int64_t)E;
+    if (R >= 65535 || nrows >= (1 << 24) || 2 * nrows * R >= ((int64_t)1 << 31))
         return fail(sim, QW_ERR_ARG, "positional layout: too many unpaired padded columns in a row, or rows");
-    std::vector<uint32_t> hx((size_t)n * std::max<size_t>(E, 1), 0u);
-    std::vector<uint16_t> hc((size_t)n);
-    for (int64_t c = 0; c < n; ++c) {
+    std::vector<uint32_t> hx((size_t)nrows * std::max<size_t>(E, 1), 0u);
+    std::vector<uint16_t> hc((size_t)nrows);
+    for (int64_t c = 0; c < nrows; ++c) {
         hc[(size_t)c] = (uint16_t)xin[(size_t)c].size();
         for (size_t e = 0; e < xin[(size_t)c].size(); ++e) hx[(size_t)c * E + e] = xin[(size_t)c][e];
     }
-    const int R = 2 * s + 2 * (int)E;
     if (d.cap_row < R) {
         const int rc = grow_rows(sim, R);
         if (rc != QW_OK) return rc;
@@ -1027,19 +1050,36 @@ static int pos_build(qw_sim *sim)
     QW_CUDA(sim, cudaMemcpy(sim->pos_tp, tp.data(), tp.size() * 2, cudaMemcpyHostToDevice));
     QW_CUDA(sim, cudaMemcpy(sim->pos_xin, hx.data(), hx.size() * 4, cudaMemcpyHostToDevice));
     QW_CUDA(sim, cudaMemcpy(sim->pos_xcnt, hc.data(), hc.size() * 2, cudaMemcpyHostToDevice));
-    sim->pbuf_bytes = (size_t)2 * (size_t)n * (size_t)R * (sim->fp32 ? sizeof(float2) : sizeof(double2));
+    if (ninst > 1) {
+        QW_CUDA(sim, dalloc(sim, &sim->pos_rowbase, rowbase.size()));
+        QW_CUDA(sim, dalloc(sim, &sim->pos_rowinst, rowinst.size()));
+        QW_CUDA(sim, cudaMemcpy(sim->pos_rowbase, rowbase.data(), rowbase.size() * 4, cudaMemcpyHostToDevice));
+        QW_CUDA(sim, cudaMemcpy(sim->pos_rowinst, rowinst.data(), rowinst.size() * 2, cudaMemcpyHostToDevice));
+    }
+    sim->pbuf_bytes = (size_t)2 * (size_t)nrows * (size_t)R * (sim->fp32 ? sizeof(float2) : sizeof(double2));
     for (auto &p : sim->pbuf) {
         unsigned char *b = nullptr;
         QW_CUDA(sim, dalloc(sim, &b, sim->pbuf_bytes));
         QW_CUDA(sim, cudaMemset(b, 0, sim->pbuf_bytes));
         p = b;
     }
-    d.pos_R = R;
+    d.pos_R = (int)R;
     d.pos_E = (int)E;
+    d.pos_rows = nrows;
     d.pos_tp = sim->pos_tp;
     d.pos_xin = sim->pos_xin;
     d.pos_xcnt = sim->pos_xcnt;
+    d.pos_rowbase = sim->pos_rowbase;
+    d.pos_rowinst = sim->pos_rowinst;
     sim->grid_pos = qw_pos_grid(d, sim->fp32);
+    if (sim->grid_pos > sim->partials_cap) { /* one norm partial per block */
+        drop_graphs(sim); /* they hold the old array */
+        cudaFree(sim->partials);
+        sim->partials = nullptr;
+        sim->partials_cap = 0;
+        QW_CUDA(sim, dalloc(sim, &sim->partials, (size_t)sim->grid_pos));
+        sim->partials_cap = sim->grid_pos;
+    }
     sim->mode_alt = d.warp_cap >= 2 * d.cap_row ? QW_MODE_WALK_SLOT : QW_MODE_WALK_FUSED;
     sim->grid_alt = qw_step_grid(d, sim->fp32, sim->mode_alt);
     sim->pos_built = true;
@@ -1284,6 +1324,10 @@ extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, cons
 {
     if (!sim) return QW_ERR_ARG;
     if (sim->fq_open) return faithful_session_closed(sim);
+    if (sim->d.ninst > 1) { /* the other instances keep their state: back into the buckets */
+        const int prc = pos_unpack(sim);
+        if (prc != QW_OK) return prc;
+    }
     sim->pos_live = false; /* the state is replaced in the row buckets */
     sim->pos_try = true;
     if (inst < 0 || inst >= sim->d.ninst) return fail(sim, QW_ERR_ARG, "instance out of range");
@@ -1482,7 +1526,7 @@ extern "C" int qw_autotune(qw_sim *sim, int32_t steps, int32_t *choice, double *
        one instance and no partitions (its tables are built first: they may
        grow row_capacity, which the other kernels' launch shapes follow) */
     const bool slot = qw_slot_supported(sim->d);
-    const bool pos = slot && sim->d.ninst == 1 && sim->d.nparts == 1;
+    const bool pos = slot && sim->d.nparts == 1;
     if (pos) {
         const int rc = pos_build(sim);
         if (rc != QW_OK) return rc;

@@ -100,15 +100,21 @@ struct QwSimDev {
     QwPartEntry *outbox;
     unsigned long long *outbox_count;
     int64_t outbox_cap;
-    /* positional layout (single instance): row (jc = 0, j, b1) is pos_R =
-       2 s + 2 pos_E amplitudes at (2 j + b1) pos_R.  pos_tp[j s + l]: the
-       position of the branch k = j in row col(j, l); pos_xin[j pos_E + e] =
-       x << 8 | l for the e-th row x < pos_xcnt[j] whose slot l holds column j
-       while row j holds no column x */
+    /* positional layout: the rows j < N of all instances in order, row g
+       (instance i, g = inst_img[i] / s + j) of pos_rows; row (g, b1) is
+       pos_R = 2 s + 2 pos_E amplitudes at (2 g + b1) pos_R.  pos_tp[g s + l]:
+       the position of the branch k = j in row col(j, l) of the instance;
+       pos_xin[g pos_E + e] = x << 8 | l for the e-th row x (global) < pos_xcnt[g]
+       whose slot l holds column j while row j holds no column x;
+       pos_rowbase[g] / pos_rowinst[g]: the first row and the instance of
+       row g's instance (null with one instance) */
     int pos_R, pos_E;
+    int64_t pos_rows;
     const uint16_t *pos_tp;
     const uint32_t *pos_xin;
     const uint16_t *pos_xcnt;
+    const uint32_t *pos_rowbase;
+    const uint16_t *pos_rowinst;
 };
 
 struct QwBufDev {

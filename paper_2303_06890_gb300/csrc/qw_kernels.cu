@@ -2441,7 +2441,7 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
     /* 32-bit indices: the host keeps 2 N pos_R below 2^31 */
     const uint32_t R = (uint32_t)d.pos_R;
     const int E = d.pos_E;
-    const uint32_t n = (uint32_t)d.n_single;
+    const uint32_t n = (uint32_t)d.pos_rows; /* rows of all instances */
     const uint32_t nall = (n + RPP - 1) / RPP, ngroups = skip ? 0u : nall;
     const uint32_t nwarps = gridDim.x * PW;
     const int ul = lane / S, l = lane % S;
@@ -2457,7 +2457,7 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
     /* a group's inputs, loaded one group ahead: the next group's loads are in
        flight while the current one computes */
     struct In {
-        uint32_t w;
+        uint32_t w, rb; /* QRAM word, first row of the row's instance */
         RotVal t;
         int tp;
         AmpT a0, a1, q0, q1;
@@ -2478,6 +2478,7 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
     auto fetch = [&](uint32_t gg, In &x) {
         const uint32_t jj = gg * RPP + ul;
         x.w = 0;
+        x.rb = 0;
         x.t = Amp<AmpT>::rot_zero();
         x.tp = 0;
         x.a0 = x.a1 = x.q0 = x.q1 = zero;
@@ -2486,6 +2487,7 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
             x.w = __ldg(d.img + at);
             x.t = __ldg(static_cast<const RotVal *>(d.slot_rot) + at);
             x.tp = __ldg(d.pos_tp + at);
+            if (d.pos_rowbase) x.rb = __ldg(d.pos_rowbase + jj);
             PosPair<AmpT>::load(pin + 2 * jj * R + 2 * l, x.a0, x.a1);
             PosPair<AmpT>::load(pin + (2 * jj + 1) * R + 2 * l, x.q0, x.q1);
         }
@@ -2523,7 +2525,8 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
             if (l == 0 && um != 0) st.rows += 1; /* units holding branches */
         }
         const uint32_t col = w >> 16, val = w & 0xffffu;
-        const bool sneg = j > col;
+        const uint32_t gc = cur.rb + col; /* the column's row among all instances' rows */
+        const bool sneg = j > gc;         /* j > col within the instance */
 
         /* b1 = 0: R^dag, H P H on the zero-type group (the unit's lanes), R */
         AmpT rA0, rA1;
@@ -2577,8 +2580,8 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
             if (eA1) nrm.add(rA1);
             if (eB1) nrm.add(rB1);
             st.out += (eA0 ? 1u : 0u) + (eB0 ? 1u : 0u) + (eA1 ? 1u : 0u) + (eB1 ? 1u : 0u);
-            PosPair<AmpT>::store(pout + 2 * col * R + tp, s0, s1);
-            PosPair<AmpT>::store(pout + (2 * col + 1) * R + tp, s2, s3);
+            PosPair<AmpT>::store(pout + 2 * gc * R + tp, s0, s1);
+            PosPair<AmpT>::store(pout + (2 * gc + 1) * R + tp, s2, s3);
         }
 
         /* the extras of the group's rows: the lane's first item prefetched, any
@@ -2662,15 +2665,26 @@ __global__ void k_pos_pack(QwSimDev d, QwBufDev buf, AmpT *pbuf, int32_t *status
         const int64_t b = i / d.cap_row;
         const int p = (int)(i - b * d.cap_row);
         if (p >= buf.count[b]) continue;
-        const int64_t j = b >> 1;
-        if (b >= d.dense_buckets || j >= d.n_single) { /* a row with jc != 0 or j >= N */
+        if (b >= d.dense_buckets) { /* a row with jc != 0 */
             atomicOr(status, QW_ST_POS_UNREP);
             continue;
         }
+        int64_t j = b >> 1, n = d.n_single, g0 = 0;
+        if (d.ninst > 1) {
+            const int inst = d.unit_inst[b >> 1];
+            j = (b - d.inst_bkt[inst]) >> 1;
+            n = d.inst_n[inst];
+            g0 = d.inst_img[inst] / S;
+        }
+        if (j >= n) { /* a row j >= N */
+            atomicOr(status, QW_ST_POS_UNREP);
+            continue;
+        }
+        const int64_t gr = g0 + j; /* the row among all instances' rows */
         const Regs x = decode_r(buf.key[i], d.nb);
         int pos = -1;
         if (x.kc == 0 && x.A == 0) {
-            const uint32_t *row = d.img + j * S;
+            const uint32_t *row = d.img + gr * S;
             int lo = 0, hi = S; /* lower bound of k among the row's sorted columns */
             while (lo < hi) {
                 const int m = (lo + hi) >> 1;
@@ -2680,9 +2694,9 @@ __global__ void k_pos_pack(QwSimDev d, QwBufDev buf, AmpT *pbuf, int32_t *status
             if (lo < S && (row[lo] >> 16) == x.k) {
                 pos = 2 * lo + (int)x.b2;
             } else {
-                const int ne = d.pos_xcnt[j];
+                const int ne = d.pos_xcnt[gr];
                 for (int e = 0; e < ne; ++e)
-                    if ((d.pos_xin[j * E + e] >> 8) == x.k) {
+                    if ((d.pos_xin[gr * E + e] >> 8) - g0 == x.k) {
                         pos = 2 * S + 2 * e + (int)x.b2;
                         break;
                     }
@@ -2692,7 +2706,7 @@ __global__ void k_pos_pack(QwSimDev d, QwBufDev buf, AmpT *pbuf, int32_t *status
             atomicOr(status, QW_ST_POS_UNREP);
             continue;
         }
-        pbuf[(int64_t)b * d.pos_R + pos] = static_cast<const AmpT *>(buf.amp)[i];
+        pbuf[(2 * gr + (b & 1)) * d.pos_R + pos] = static_cast<const AmpT *>(buf.amp)[i];
     }
 }
 
@@ -2702,33 +2716,40 @@ template <typename AmpT>
 __global__ void k_pos_unpack(QwSimDev d, const AmpT *pbuf, QwBufDev buf, int32_t *status)
 {
     const int S = d.s, E = d.pos_E;
-    const int64_t R = d.pos_R, total = 2 * (int64_t)d.n_single * R;
+    const int64_t R = d.pos_R, total = 2 * d.pos_rows * R;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const AmpT v = pbuf[i];
         if (v.x == 0 && v.y == 0) continue;
         const int64_t r = i / R;
         const int q = (int)(i - r * R);
-        const int64_t j = r >> 1;
+        const int64_t gr = r >> 1; /* the row among all instances' rows */
+        int64_t g0 = 0, bk = r;    /* the instance's first row; the bucket */
+        if (d.ninst > 1) {
+            const int inst = d.pos_rowinst[gr];
+            g0 = d.inst_img[inst] / S;
+            bk = d.inst_bkt[inst] + 2 * (gr - g0) + (r & 1);
+        }
         Regs x;
         x.kc = 0;
         x.A = 0;
         x.b2 = (uint32_t)(q & 1);
         if (q < 2 * S) {
-            x.k = d.img[j * S + (q >> 1)] >> 16;
+            x.k = d.img[gr * S + (q >> 1)] >> 16;
         } else {
             const int e = (q - 2 * S) >> 1;
-            if (e >= (int)d.pos_xcnt[j]) { /* never written: not a branch */
+            if (e >= (int)d.pos_xcnt[gr]) { /* never written: not a branch */
                 atomicOr(status, QW_ST_POS_UNREP);
                 continue;
             }
-            x.k = d.pos_xin[j * E + e] >> 8;
+            x.k = (d.pos_xin[gr * E + e] >> 8) - (uint32_t)g0;
         }
-        const int p = atomicAdd(buf.count + r, 1); /* bucket 2 j + b1 of the one instance */
+        const int64_t r_b = bk;
+        const int p = atomicAdd(buf.count + r_b, 1);
         if (p >= d.cap_row) {
             atomicOr(status, QW_ST_ROW_OVERFLOW);
             continue;
         }
-        const int64_t sl = r * d.cap_row + p;
+        const int64_t sl = r_b * d.cap_row + p;
         buf.key[sl] = encode_r(x, d.nb);
         static_cast<AmpT *>(buf.amp)[sl] = v;
     }
@@ -3142,7 +3163,7 @@ int pos_grid_s(const QwSimDev &d)
     /* as many groups for every warp: with k = ceil(groups / resident warps)
        groups a warp, the fewest blocks that cover them (a warp with fewer
        groups than the others would wait for them at the end of the step) */
-    const int64_t groups = ((int64_t)d.n_single + (32 / S) - 1) / (32 / S);
+    const int64_t groups = (d.pos_rows + (32 / S) - 1) / (32 / S);
     const int64_t cap = (int64_t)per_sm * qw_sm_count();
     const int64_t k = (groups + cap * PW - 1) / (cap * PW);
     const int64_t g = (groups + k * PW - 1) / (k * PW);

@@ -119,15 +119,16 @@ def test_fp32_amp_n1024_100_steps():
 
 def test_fp32_amp_n16384_bench_config():
     """The benchmarked configuration (N=16384, s=16, complex64 amplitudes), 20
-    steps -- 4 of them by each variant the autotuner tries, as bench.py runs
+    steps -- 3 of them by each variant the autotuner tries, as bench.py runs
     it -- against the FP64 oracle."""
     w = wl.walk_n16384()
     sim = _sim(w, precision=qwalk.QW_FP32_AMP)
     sim.state_init(w.b)
-    choice, us = sim.autotune(4)
-    assert choice in range(qwalk.WALK_VARIANTS) and min(us[:4]) > 0
+    choice, us = sim.autotune(3)
+    assert choice in range(qwalk.WALK_VARIANTS) and min(us[:4]) > 0 and us[7] > 0
     tried = sum(1 for v in us if v > 0)
-    sim.apply_walk_step(w.steps - 4 * tried)
+    assert 3 * tried <= w.steps
+    sim.apply_walk_step(w.steps - 3 * tried)
     o = _oracle(w)
     o.apply("T")
     for _ in range(w.steps):

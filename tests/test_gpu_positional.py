@@ -169,3 +169,67 @@ def test_autotune_tries_the_positional_layout():
         o.apply("W")
     compare_union(gpu_state(sim), oracle_state(o), 2e-6, 1e-5)
     sim.close()
+
+
+def test_positional_batched_instances_match_their_oracles():
+    """Several instances of different N in one positional state (rows of all
+    instances in order, each with its own column offset): every instance
+    equals its own oracle after 5 steps, and a re-initialised instance
+    leaves the others' states alone."""
+    sizes = [(64, 1), (100, 2), (37, 3), (256, 4), (64, 5), (500, 6)]
+    ws = [wl.small_random(n, 8, 40 + seed, band=1) for n, seed in sizes]
+    ws = [w for w in ws if w.s == 8]
+    assert len(ws) >= 3
+    sim = qwalk.Sim([w.matrix for w in ws], s_pad=8, walk_variant=7)
+    for i, w in enumerate(ws):
+        sim.state_init(w.b, inst=i)
+    sim.apply_walk_step(5)
+    refs = []
+    for w in ws:
+        o = _oracle(w)
+        o.apply("T")
+        for _ in range(5):
+            o.apply("W")
+        refs.append(o)
+    for i in range(len(ws)):
+        compare(gpu_state(sim, inst=i), oracle_state(refs[i]), TOL64)
+    sim.state_init(ws[1].b, inst=1)  # instance 1 back to T~|b~>, the others at step 5
+    sim.apply_walk_step(2)
+    o1 = _oracle(ws[1])
+    o1.apply("T")
+    for _ in range(2):
+        o1.apply("W")
+    compare(gpu_state(sim, inst=1), oracle_state(o1), TOL64)
+    for i in (0, 2):
+        for _ in range(2):
+            refs[i].apply("W")
+        compare(gpu_state(sim, inst=i), oracle_state(refs[i]), TOL64)
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", [qwalk.QW_FP64, qwalk.QW_FP32_AMP])
+def test_positional_batched_256_bitwise_equals_slot_kernel(precision):
+    """The batched workload (256 walks, N log-uniform in [64, 4096], s = 8):
+    without renormalisation the positional layout's states equal the slot
+    kernel's bit for bit after 12 steps (graph replays), instance by
+    instance on a sample, and the branch counters agree."""
+    ws = wl.batched(256)
+    sims = []
+    for v in (7, 4):
+        sim = qwalk.Sim([w.matrix for w in ws], s_pad=8, precision=precision, walk_variant=v, renorm=0)
+        for i, w in enumerate(ws):
+            sim.state_init(w.b, inst=i)
+        sim.enqueue_walk_steps(12)
+        sim.sync()
+        sims.append(sim)
+    a, b = sims
+    for i in list(range(0, 256, 37)) + [255]:
+        ka, va = a.state_export(inst=i)
+        kb, vb = b.state_export(inst=i)
+        assert np.array_equal(ka, kb), i
+        assert np.array_equal(va, vb), i
+    sa, sb = a.step_stats(), b.step_stats()
+    for k in ("in", "after_rdag", "after_hph", "out", "steps"):
+        assert sa[k] == sb[k], k
+    for sim in sims:
+        sim.close()
