@@ -290,6 +290,22 @@ static void build_image(const qw_csc &m, int s, uint32_t *out)
 
 static int pos_build(qw_sim *sim);
 
+/* (sqrt|a|, sqrt(1 - |a|)) as float pairs (hi, lo) for the Q1.15 code q:
+ * hi the correctly rounded FP32 square root, lo the Newton correction
+ * (x - hi^2) / (2 hi) with the residual exact by FMA, rounded once -- hi + lo
+ * within ~2^-47 relative of the root.  k_walk_pos computes the same bits on
+ * the device from the QRAM value word (IEEE square root, FMA and division are
+ * correctly rounded on both sides). */
+static float4 rot_pair_f32(int16_t q)
+{
+    const float x = (float)(q < 0 ? -(int)q : (int)q) * (1.0f / 32768.0f); /* exact */
+    const float y = 1.0f - x;                                                  /* exact */
+    const float fh = std::sqrt(x), gh = std::sqrt(y);
+    const float fl = fh > 0.0f ? std::fma(-fh, fh, x) / (2.0f * fh) : 0.0f;
+    const float gl = gh > 0.0f ? std::fma(-gh, gh, y) / (2.0f * gh) : 0.0f;
+    return make_float4(fh, fl, gh, gl);
+}
+
 extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opts *opts_in,
                              qw_sim **out)
 {
@@ -364,6 +380,7 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
         std::memcpy(&d.tau_lo_bits, &lo, 8);
         d.tau2f = (float)(tau * tau);
     }
+    d.rot_calc = o.rot_bits == 0;
     d.inv_sqrt_s = 1.0 / std::sqrt((double)s);
     d.two_over_s = 2.0 / (double)s;
     d.cap_row = o.row_capacity > 0 ? o.row_capacity : std::max(8, 4 * s);
@@ -447,8 +464,12 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
             g = std::sin(th);
         }
         hfg[(size_t)c] = make_double2(f, g);
-        const float fh = (float)f, gh = (float)g;
-        hfg32[(size_t)c] = make_float4(fh, (float)(f - (double)fh), gh, (float)(g - (double)gh));
+        if (o.rot_bits > 0) {
+            const float fh = (float)f, gh = (float)g;
+            hfg32[(size_t)c] = make_float4(fh, (float)(f - (double)fh), gh, (float)(g - (double)gh));
+        } else { /* the float pairs the positional kernel derives from the code itself */
+            hfg32[(size_t)c] = rot_pair_f32(q);
+        }
     }
 
     auto bail = [&](cudaError_t e, const char *what) {

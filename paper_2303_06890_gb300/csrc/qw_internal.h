@@ -81,6 +81,7 @@ struct QwSimDev {
     uint64_t tau_hi_bits;     /* bits of tau (1 + 2^-30): |x| above it => kept */
     uint64_t tau_lo_bits;     /* bits of tau sqrt(1/2) (1 - 2^-30): |x|,|y| at most it => pruned */
     float tau2f;              /* tau^2 as float (complex64 path) */
+    int rot_calc;             /* rot_bits == 0: the FP32 rotation pairs follow from the code alone */
     double inv_sqrt_s;        /* 1 / sqrt(s) */
     double two_over_s;        /* 2 / s */
     const uint32_t *img;      /* QRAM words: column << 16 | Q1.15 value */

@@ -563,6 +563,8 @@ template <> struct Amp<double2> {
     typedef double2 RotVal; /* (sqrt|a|, sqrt(1-|a|)) */
     __device__ static RotVal rot_table(const QwSimDev &d, uint32_t A) { return __ldg(d.fg + A); }
     __device__ static RotVal rot_zero() { return make_double2(0.0, 1.0); }
+    static constexpr bool kRotCode = false; /* FP64 square roots: read the table */
+    __device__ static RotVal rot_code(uint32_t) { return rot_zero(); }
     __device__ static void rot(RotVal t, uint32_t A, bool dag, bool sneg, T a0, T a1, T &o0, T &o1);
 };
 
@@ -721,6 +723,20 @@ template <> struct Amp<float2> {
     }
     typedef float4 RotVal; /* (sqrt|a|, sqrt(1-|a|)) as float pairs */
     __device__ static RotVal rot_table(const QwSimDev &d, uint32_t A) { return __ldg(d.fg32 + A); }
+    /* the table entry of code A (rot_bits = 0) computed in place: hi the
+       correctly rounded square root, lo the Newton correction (x - hi^2) /
+       (2 hi) with the residual exact by FMA -- the host builds the table the
+       same way, so the bits agree */
+    static constexpr bool kRotCode = true;
+    __device__ static RotVal rot_code(uint32_t A)
+    {
+        const int q = (int)(int16_t)(uint16_t)A;
+        const float x = (float)(q < 0 ? -q : q) * (1.0f / 32768.0f), y = 1.0f - x;
+        const float fh = __fsqrt_rn(x), gh = __fsqrt_rn(y);
+        const float fl = fh > 0.0f ? __fdiv_rn(__fmaf_rn(-fh, fh, x), 2.0f * fh) : 0.0f;
+        const float gl = gh > 0.0f ? __fdiv_rn(__fmaf_rn(-gh, gh, y), 2.0f * gh) : 0.0f;
+        return make_float4(fh, fl, gh, gl);
+    }
     __device__ static RotVal rot_zero() { return make_float4(0.f, 0.f, 1.f, 0.f); }
     __device__ static void rot(RotVal t, uint32_t A, bool dag, bool sneg, T a0, T a1, T &o0, T &o1);
 };
@@ -2435,6 +2451,7 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool skip = *(volatile int32_t *)a.status != 0;
     const bool rescale = a.scale_in != nullptr;
+    const bool rot_in_place = Amp<AmpT>::kRotCode && d.rot_calc;
     typename Amp<AmpT>::Norm nrm;
     PosStats st;
     const AmpT zero = Amp<AmpT>::zero();
@@ -2485,7 +2502,7 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
         if (gg < nall && jj < n) {
             const uint32_t at = jj * S + l;
             x.w = __ldg(d.img + at);
-            x.t = __ldg(static_cast<const RotVal *>(d.slot_rot) + at);
+            if (!rot_in_place) x.t = __ldg(static_cast<const RotVal *>(d.slot_rot) + at);
             x.tp = __ldg(d.pos_tp + at);
             if (d.pos_rowbase) x.rb = __ldg(d.pos_rowbase + jj);
             PosPair<AmpT>::load(pin + 2 * jj * R + 2 * l, x.a0, x.a1);
@@ -2508,7 +2525,10 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
         const uint32_t j = g * RPP + ul;
         const bool valid = j < n;
         const uint32_t w = cur.w;
-        const RotVal rv = (w & 0xffffu) != 0 ? cur.t : Amp<AmpT>::rot_zero(); /* a 0 element rotates by R(0) */
+        /* a 0 element rotates by R(0); complex64 derives the float pairs from
+           the value word (4 MB less read per step than the per-slot table) */
+        const RotVal rv = (w & 0xffffu) == 0 ? Amp<AmpT>::rot_zero()
+                                             : (rot_in_place ? Amp<AmpT>::rot_code(w & 0xffffu) : cur.t);
         const uint32_t tp = (uint32_t)cur.tp;
         AmpT a0 = cur.a0, a1 = cur.a1, q0 = cur.q0, q1 = cur.q1;
         if (valid && rescale) {
