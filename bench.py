@@ -497,6 +497,7 @@ def batched_leg(args, torch, flush, barrier, max_over_ranks, world, rank) -> dic
 
     ws = wl.batched(256, first=ranks.instance_seed_offset(rank, 256))
     sim = qwalk.Sim([w.matrix for w in ws], s_pad=8, precision=qwalk.QW_FP32_AMP)
+    nb = sim.nb
     for i, w in enumerate(ws):
         sim.state_init(w.b, inst=i)
     variant, tune = sim.autotune(3)
@@ -557,8 +558,12 @@ def batched_leg(args, torch, flush, barrier, max_over_ranks, world, rank) -> dic
             err[f"instance_{i}_n{ws[i].n}"] = state_error((sim.unpack(keys), amps), o.export())
         sim.close()
     steps = max(1, stats["steps"])
+    b_alg, _ = algorithmic_bytes(stats, nb, 8)
+    t_step = t_dev / args.batched_steps
     return {"workload": "batched_256_n64-4096_s8", "instances": 256,
             "branches_per_step": stats["out"] / steps,
+            "entries_per_s": world * (stats["in"] + stats["after_rdag"] + stats["after_hph"]) / steps / t_step,
+            "achieved_gbs": world * b_alg / t_step / 1e9,
             "steps_per_s": world * args.batched_steps / t_dev,
             "instance_steps_per_s": world * 256 * args.batched_steps / t_dev,
             "ms_per_step": 1000.0 * t_dev / args.batched_steps,
@@ -699,11 +704,15 @@ def qls_leg(torch, barrier, max_over_ranks) -> dict:
         kappa = w.kappa if kappa is None else kappa
         coeffs, j0, _ = qwalk.cks_coefficients(kappa, 1e-3)
         sim = qwalk.Sim(w.matrix, s_pad=w.s, precision=prec)
+        sim.state_init(w.b)
+        variant, _ = sim.autotune(2)  # the step kernel the solve runs
+        sim.step_stats(reset=True)
         barrier()
         t0 = time.perf_counter()
         sim.state_init(w.b)
         y, p = sim.apply_qls(coeffs)
         t = max_over_ranks(time.perf_counter() - t0)
+        st = sim.step_stats(reset=True)
         sim.close()
         x = np.linalg.solve(w.matrix.dense(), w.b)
         x /= np.linalg.norm(x)
@@ -715,7 +724,8 @@ def qls_leg(torch, barrier, max_over_ranks) -> dict:
         out[label] = {"n": w.n, "s": w.s, "kappa_walk": w.kappa, "kappa_coefficients": kappa,
                       "j0": j0, "walk_steps": 2 * (j0 + 1),
                       "precision": "complex64" if prec == qwalk.QW_FP32_AMP else "complex128",
-                      "seconds": t, "walk_steps_per_s": 2 * (j0 + 1) / t,
+                      "seconds": t, "walk_steps_per_s": 2 * (j0 + 1) / t, "variant": variant,
+                      "entries_per_s": (st["in"] + st["after_rdag"] + st["after_hph"]) / t,
                       "fidelity": fid,
                       "p_succ": float(p[-1] / np.abs(coeffs).sum() ** 2),
                       "error_vs_dense_theory": {
@@ -807,11 +817,17 @@ def configs_leg(torch) -> dict:
             sim.state_init(w.b)
             variant, _ = sim.autotune(2)
             sim.apply_walk_step(6)
+            sim.step_stats(reset=True)
             reps = 20
             t = _events_time(torch, lambda: [sim.enqueue_walk_steps(w.steps) for _ in range(reps)])
             sim.sync()
+            st = sim.step_stats(reset=True)
+            b_alg, _ = algorithmic_bytes(st, sim.nb, 8 if prec == qwalk.QW_FP32_AMP else 16)
             sim.close()
-            row[label] = {"us_per_step": 1e6 * t / (reps * w.steps), "variant": variant,
+            us = 1e6 * t / (reps * w.steps)
+            row[label] = {"us_per_step": us, "variant": variant,
+                          "entries_per_s": (st["in"] + st["after_rdag"] + st["after_hph"]) / t,
+                          "achieved_gbs": b_alg / us * 1e6 / 1e9,
                           "error": state_error(gpu_walk_state(w, prec, w.steps, variant), ref)}
         out[w.name] = row
     return out
