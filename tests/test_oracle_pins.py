@@ -595,3 +595,39 @@ def test_faithful_qbs_registers_follow_definition_1(oracle_mod):
     o.apply_faithful("QBS_BWD")
     back, _ = o.export_faithful()
     assert not back[:, 7:].any() and o.violations == 0
+
+
+# --- the positional layout's premise -------------------------------------------------
+
+@pytest.mark.parametrize("maker", [wl.walk_n16, lambda: wl.small_random(100, 8, 3),
+                                   lambda: wl.small_random(130, 16, 5),
+                                   lambda: wl.small_random(70, 32, 10, band=1, attempts=3000)])
+def test_reachable_states_have_positions(oracle_mod, maker):
+    """W = S (2 T~ Pi T~^dag - 1) (Sec. IV): from T~|b~> every branch at a step
+    boundary has jc = kc = A = 0, j < N and either k = a column of row j's
+    padded list (T~'s rows) or, with b2 = 0, k = a row whose padded list holds
+    column j (S of them); so it has a fixed position in its row, the premise
+    of the positional layout (walk_variant 7).  Checked on the oracle's states
+    with the padded rows restated here, and both kinds must occur."""
+    w = maker()
+    rows = padded_rows(w.matrix, w.s)
+    cols = [set(int(c) for c in r[0]) for r in rows]
+    into = [set() for _ in range(w.n)]  # rows whose padded list holds column c
+    for j, cs in enumerate(cols):
+        for c in cs:
+            into[c].add(j)
+    o = oracle_mod.Oracle(w.matrix, w.s)
+    o.init_b(w.b)
+    o.apply("T")
+    seen_slot = seen_in = 0
+    for _ in range(6):
+        o.apply("W")
+        regs, _ = o.export()
+        for jc, j, b1, kc, k, b2, a in (tuple(int(v) for v in r) for r in regs):
+            assert jc == 0 and kc == 0 and a == 0 and j < w.n
+            if k in cols[j]:
+                seen_slot += 1
+            else:
+                assert b2 == 0 and k in into[j], (j, b1, k, b2)
+                seen_in += 1
+    assert seen_slot > 0 and (seen_in > 0 or all(j in cols[c] for c in range(w.n) for j in into[c]))
