@@ -197,7 +197,12 @@ int qw_apply_walk_step(qw_sim *sim, int64_t nsteps);
  * Issue nsteps walk steps on the simulator's stream and return without
  * synchronising (for pipelining, timing and stream capture).  Device errors
  * of these steps are reported by the next call that synchronises (qw_sync,
- * qw_apply_walk_step, the measurement and export calls).
+ * qw_apply_walk_step, the measurement and export calls).  Exception: with
+ * walk_variant 7, a call made while the stream is not being captured first
+ * moves a state that is not yet in the positional layout into it, which
+ * synchronises once; during a capture such a state runs on the kernel of
+ * variant 4 instead.  The flat and register-faithful schedules (variants 5
+ * and 6) synchronise between their stages.
  * Errors: QW_ERR_ARG, QW_ERR_STATE, QW_ERR_CUDA (launch failure).
  */
 int qw_enqueue_walk_steps(qw_sim *sim, int64_t nsteps);
