@@ -508,6 +508,7 @@ template <> struct Amp<double2> {
     struct Sum {
         double x = 0.0, y = 0.0;
         __device__ void add(T a) { x += a.x; y += a.y; }
+        __device__ void set(T a) { x = a.x; y = a.y; } /* add() to an empty sum */
         /* lane t < min(s, 32) holds the partial sums of the values t, t + 32, ...
            (s a power of two); with width < 32 each aligned group of width
            lanes reduces its own values.  Butterfly over the w = min(s, 32) lanes, x on
@@ -530,6 +531,9 @@ template <> struct Amp<double2> {
         }
         __device__ void scale_pow2(double f) { x *= f; y *= f; }
         __device__ T minus(T a) const { return make_double2(x - a.x, y - a.y); }
+        /* scale_pow2(f) then minus(a) in one FMA per component: f is a power of
+           two, so f x is exact and the result is the same rounding */
+        __device__ T scaled_minus(double f, T a) const { return make_double2(fma(f, x, -a.x), fma(f, y, -a.y)); }
         __device__ double2 value() const { return make_double2(x, y); }
     };
     __device__ static T zero() { return make_double2(0.0, 0.0); }
@@ -566,6 +570,9 @@ template <> struct Amp<double2> {
     static constexpr bool kRotCode = false; /* FP64 square roots: read the table */
     __device__ static RotVal rot_code(uint32_t) { return rot_zero(); }
     __device__ static void rot(RotVal t, uint32_t A, bool dag, bool sneg, T a0, T a1, T &o0, T &o1);
+    /* rot(t, A, true, sneg, a0, 0): R^dag of a pair whose b2 = 1 member is 0 */
+    __device__ static void rot_dag_b2zero(RotVal t, uint32_t A, bool sneg, T a0, T &o0, T &o1);
+    static constexpr bool kB2ZeroPath = true;
 };
 
 /* complex64 path: amplitudes are float; each rotation output f a0 +- g a1 is
@@ -625,6 +632,13 @@ template <> struct Amp<float2> {
     struct Sum {
         DF x, y;
         __device__ void add(T a) { x.add(a.x); y.add(a.y); }
+        __device__ void set(T a) /* add() to an empty sum: the value, no error term */
+        {
+            x.h = a.x;
+            x.l = 0.f;
+            y.h = a.y;
+            y.l = 0.f;
+        }
         /* lane t < min(s, 32) holds the partial sums of the values t, t + 32, ...
            (s a power of two); with width < 32 each aligned group of width
            lanes reduces its own values.  Butterfly over the w = min(s, 32) lanes, x on
@@ -665,6 +679,11 @@ template <> struct Amp<float2> {
             x.h *= g; x.l *= g; y.h *= g; y.l *= g;
         }
         __device__ T minus(T a) const { return make_float2(x.minus(a.x), y.minus(a.y)); }
+        __device__ T scaled_minus(double f, T a)
+        {
+            scale_pow2(f);
+            return minus(a);
+        }
         __device__ double2 value() const
         {
             return make_double2((double)x.h + (double)x.l, (double)y.h + (double)y.l);
@@ -739,6 +758,16 @@ template <> struct Amp<float2> {
     }
     __device__ static RotVal rot_zero() { return make_float4(0.f, 0.f, 1.f, 0.f); }
     __device__ static void rot(RotVal t, uint32_t A, bool dag, bool sneg, T a0, T a1, T &o0, T &o1);
+    __device__ static void rot_dag_b2zero(RotVal t, uint32_t A, bool sneg, T a0, T &o0, T &o1);
+    static constexpr bool kB2ZeroPath = false;
+    /* dot2 with y = 0: round(A x) -- the same bits (p1 + e1 rounded once) */
+    __device__ static float dot1(float ah, float al, float x)
+    {
+        const float p1 = __fmul_rn(ah, x);
+        float e1 = __fmaf_rn(ah, x, -p1);
+        e1 = __fmaf_rn(al, x, e1);
+        return __fadd_rn(p1, e1);
+    }
 };
 
 __device__ double Amp<float2>::Norm::warp_total() const
@@ -781,6 +810,25 @@ __device__ void Amp<double2>::rot(RotVal t, uint32_t A, bool dag, bool sneg, T a
         o0 = make_double2(fma(fm, x0.x, g * a1.x), fma(fm, x0.y, g * a1.y));
         o1 = make_double2(fma(fm, x1.x, -g * a0.x), fma(fm, x1.y, -g * a0.y));
     }
+}
+
+/* R^dag (a0, 0): o0 = conj(f) a0, o1 = -g a0 -- the general formulas with
+   a1 = 0, whose products by 0 change no rounding */
+__device__ void Amp<double2>::rot_dag_b2zero(RotVal t, uint32_t A, bool sneg, T a0, T &o0, T &o1)
+{
+    const double fm = t.x, g = t.y;
+    const bool imag = (int16_t)(uint16_t)A < 0;
+    const double2 x0 = rho(a0, imag, !sneg);
+    o0 = make_double2(fm * x0.x, fm * x0.y);
+    o1 = make_double2(-g * a0.x, -g * a0.y);
+}
+
+__device__ void Amp<float2>::rot_dag_b2zero(RotVal t, uint32_t A, bool sneg, T a0, T &o0, T &o1)
+{
+    const bool imag = (int16_t)(uint16_t)A < 0;
+    const float2 x0 = rho(a0, imag, !sneg);
+    o0 = make_float2(dot1(t.x, t.y, x0.x), dot1(t.x, t.y, x0.y));
+    o1 = make_float2(dot1(-t.z, -t.w, a0.x), dot1(-t.z, -t.w, a0.y));
 }
 
 __device__ void Amp<float2>::rot(RotVal t, uint32_t A, bool dag, bool sneg, T a0, T a1, T &o0, T &o1)
@@ -2148,7 +2196,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_slot(QwSimDev d, QwBufDe
                b2 = 1 member, outside every zero-type group, is negated */
             const AmpT z0 = c0 ? o0 : zero;
             typename Amp<AmpT>::Sum sum;
-            sum.add(z0);
+            sum.set(z0);
             sum.reduce(S, S);
             if (a.qls_readout && U.valid && (lane % S) == 0) {
                 const double2 sv = sum.value();
@@ -2158,8 +2206,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_walk_slot(QwSimDev d, QwBufDe
                 acc.y += coef * (d.inv_sqrt_s * sv.y);
                 a.qls_y[U.j] = acc;
             }
-            sum.scale_pow2(d.two_over_s);
-            const AmpT h0 = sum.minus(z0);
+            const AmpT h0 = sum.scaled_minus(d.two_over_s, z0);
             const bool d0 = Amp<AmpT>::keep(d, h0);
             st.hph += __popc(__ballot_sync(FULL, d0)) + __popc(__ballot_sync(FULL, c1));
             /* T~: O_A' reads slot l (A = a_{j,l}), O_s' takes (l, 0) to (K(j, l), 0);
@@ -2558,7 +2605,7 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
             st.rdag += (c0 ? 1u : 0u) + (c1 ? 1u : 0u);
             const AmpT z0 = c0 ? o0 : zero;
             typename Amp<AmpT>::Sum sum;
-            sum.add(z0);
+            sum.set(z0);
             sum.reduce(S, S);
             if (a.qls_readout && valid && l == 0) {
                 const double2 sv = sum.value();
@@ -2568,8 +2615,7 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
                 acc.y += coef * (d.inv_sqrt_s * sv.y);
                 a.qls_y[j] = acc;
             }
-            sum.scale_pow2(d.two_over_s);
-            const AmpT h0 = sum.minus(z0);
+            const AmpT h0 = sum.scaled_minus(d.two_over_s, z0);
             const bool d0 = Amp<AmpT>::keep(d, h0);
             st.hph += (d0 ? 1u : 0u) + (c1 ? 1u : 0u);
             Amp<AmpT>::rot(rv, val, false, sneg, d0 ? h0 : zero, c1 ? Amp<AmpT>::neg(o1) : zero, rA0, rA1);
@@ -2581,7 +2627,14 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
         bool eB0, eB1;
         {
             AmpT o0, o1;
-            Amp<AmpT>::rot(rv, val, true, sneg, q0, q1, o0, o1);
+            /* in the walk's reachable states the b2 = 1 member of a b1 = 1 pair
+               is 0: then R^dag takes half the products (same results).  Taken
+               on the FP64-pipe-bound complex128 path only: on complex64 the
+               vote and the second code path cost more than the products */
+            if (Amp<AmpT>::kB2ZeroPath && __all_sync(FULL, nz(q1) == 0u))
+                Amp<AmpT>::rot_dag_b2zero(rv, val, sneg, q0, o0, o1);
+            else
+                Amp<AmpT>::rot(rv, val, true, sneg, q0, q1, o0, o1);
             const bool c0 = Amp<AmpT>::keep(d, o0), c1 = Amp<AmpT>::keep(d, o1);
             const unsigned int kept = (c0 ? 1u : 0u) + (c1 ? 1u : 0u);
             st.rdag += kept;
