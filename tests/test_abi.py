@@ -159,3 +159,20 @@ def test_faithful_codes_and_step_follow_the_header():
     step = expand(d["QW_FQ_STEP"])
     assert tuple(step) == qwalk.FQ_STEP == tuple(oracle.FQ_STEP)
     assert len(step) == int(d["QW_FQ_STEP_LEN"])
+
+
+@pytest.mark.parametrize("variant,words", [(7, "walk_variants 4 and 7"), (4, "walk_variants 4 and 7"),
+                                           (8, "walk_variant must be 0..7"), (-1, "walk_variant must be 0..7")])
+def test_create_rejects_unsupported_walk_variants_before_device_work(variant, words):
+    """The slot kernel and the positional layout need s = 8, 16 or 32 (the
+    N = 16 walk has s = 4); variants outside 0..QW_WALK_VARIANTS - 1 are
+    refused.  Both before any device call."""
+    lib = qwalk.load()
+    csc, keep = _csc(wl.walk_n16().matrix)
+    opts = qwalk.Opts()
+    lib.qw_sim_opts_default(ctypes.byref(opts))
+    opts.walk_variant = variant
+    h = ctypes.c_void_p()
+    rc = lib.qw_sim_create(ctypes.byref(csc), 1, ctypes.byref(opts), ctypes.byref(h))
+    assert rc == qwalk.QW_ERR_ARG
+    assert words in lib.qw_last_error(None).decode()
