@@ -105,13 +105,14 @@ typedef struct {
                                 working register of O_s', O_A' and Alg. 1 held in the
                                 state between sub-operations (the QW_FQ_STEP sequence
                                 below; any fuse_reflection), 7 = the positional layout:
-                                s = 8, 16 or 32, any number of instances; every branch the walk
-                                reaches from T~|b~> is held at a fixed position of its
-                                row (no key, no count), one lane per QRAM slot writes
-                                each output to its position, so a step has no search,
-                                atomic or clearing; a state with branches outside those
-                                positions (e.g. from qw_state_import) runs on the
-                                kernel of variant 4.  The state moves into the layout
+                                s = 8, 16, 32 or 64, any number of instances; every
+                                branch the walk reaches from T~|b~> is held at a fixed
+                                position of its row (no key, no count), one lane per
+                                QRAM slot (two for s = 64) writes each output to its
+                                position, so a step has no search, atomic or clearing;
+                                a state with branches outside those positions (e.g.
+                                from qw_state_import) runs on the kernel of variant 4
+                                (2 for s = 64).  The state moves into the layout
                                 at the first walk step (a synchronisation) and back
                                 into the row buckets before any call that reads it;
                                 row_capacity grows to 2 s + 2 E (E: the most unpaired
@@ -200,8 +201,8 @@ int qw_apply_walk_step(qw_sim *sim, int64_t nsteps);
  * qw_apply_walk_step, the measurement and export calls).  Exception: with
  * walk_variant 7, a call made while the stream is not being captured first
  * moves a state that is not yet in the positional layout into it, which
- * synchronises once; during a capture such a state runs on the kernel of
- * variant 4 instead.  The flat and register-faithful schedules (variants 5
+ * synchronises once; during a capture such a state runs on the bucket
+ * kernel of variant 4 (2 for s = 64) instead.  The flat and register-faithful schedules (variants 5
  * and 6) synchronise between their stages.
  * Errors: QW_ERR_ARG, QW_ERR_STATE, QW_ERR_CUDA (launch failure).
  */
@@ -227,7 +228,7 @@ int qw_sync(qw_sim *sim);
  * them with CUDA events on the simulator's stream, and keeps the fastest for
  * all later steps.  Segments are tried only when warp_capacity >= 2
  * row_capacity (true by default), the slot kernel only then and for s = 8, 16
- * or 32, the positional layout (variant 7) for s = 8, 16 or 32 without
+ * or 32, the positional layout (variant 7) for s = 8, 16, 32 or 64 without
  * partitions (its tables are built first, and the move of the state into it
  * is not timed); the flat path and the register-faithful
  * schedule (variants 5 and 6) are never chosen; variants not tried are

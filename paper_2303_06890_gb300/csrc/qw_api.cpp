@@ -392,8 +392,13 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
     wc = std::max<int64_t>(wc, s);
     wc = std::max<int64_t>(wc, d.cap_row);
     d.warp_cap = (int)wc;
-    if ((sim->mode == QW_MODE_WALK_SLOT || sim->mode == QW_MODE_WALK_POS) && !qw_slot_supported(d)) {
-        g_create_error = "qw_sim_create: walk_variants 4 and 7 (one lane per QRAM slot) need s = 8, 16 or 32";
+    if (sim->mode == QW_MODE_WALK_SLOT && !qw_slot_supported(d)) {
+        g_create_error = "qw_sim_create: walk_variant 4 (one lane per QRAM slot) needs s = 8, 16 or 32";
+        qw_sim_destroy(sim);
+        return QW_ERR_ARG;
+    }
+    if (sim->mode == QW_MODE_WALK_POS && !qw_pos_supported(d)) {
+        g_create_error = "qw_sim_create: walk_variant 7 (positional layout) needs s = 8, 16, 32 or 64";
         qw_sim_destroy(sim);
         return QW_ERR_ARG;
     }
@@ -563,7 +568,7 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
         for (int m : {QW_MODE_WALK_FUSED, QW_MODE_WALK_FUSED_PF, QW_MODE_WALK_SEG, QW_MODE_WALK_SEG_PF})
             gmax = std::max(gmax, qw_step_grid(d, sim->fp32, m));
         if (qw_slot_supported(d)) gmax = std::max(gmax, qw_step_grid(d, sim->fp32, QW_MODE_WALK_SLOT));
-        if (qw_slot_supported(d) && ninst == 1) gmax = std::max(gmax, qw_pos_grid(d, sim->fp32));
+        if (qw_pos_supported(d) && ninst == 1) gmax = std::max(gmax, qw_pos_grid(d, sim->fp32));
     }
     QW_TRY(dalloc(sim, &sim->partials, (size_t)gmax));
     sim->partials_cap = gmax;
@@ -1007,8 +1012,8 @@ static int pos_build(qw_sim *sim)
 {
     if (sim->pos_built) return QW_OK;
     QwSimDev &d = sim->d;
-    if (d.nparts != 1 || !qw_slot_supported(d))
-        return fail(sim, QW_ERR_ARG, "walk_variant 7 (positional) needs s = 8, 16 or 32 and no partitions");
+    if (d.nparts != 1 || !qw_pos_supported(d))
+        return fail(sim, QW_ERR_ARG, "walk_variant 7 (positional) needs s = 8, 16, 32 or 64 and no partitions");
     const int s = d.s;
     const int ninst = d.ninst;
     /* rows of all instances in order: instance i starts at row inst_img[i] / s */
@@ -1101,7 +1106,8 @@ static int pos_build(qw_sim *sim)
         QW_CUDA(sim, dalloc(sim, &sim->partials, (size_t)sim->grid_pos));
         sim->partials_cap = sim->grid_pos;
     }
-    sim->mode_alt = d.warp_cap >= 2 * d.cap_row ? QW_MODE_WALK_SLOT : QW_MODE_WALK_FUSED;
+    sim->mode_alt = d.warp_cap < 2 * d.cap_row ? QW_MODE_WALK_FUSED
+                    : (qw_slot_supported(d) ? QW_MODE_WALK_SLOT : QW_MODE_WALK_SEG);
     sim->grid_alt = qw_step_grid(d, sim->fp32, sim->mode_alt);
     sim->pos_built = true;
     return QW_OK;
@@ -1544,10 +1550,10 @@ extern "C" int qw_autotune(qw_sim *sim, int32_t steps, int32_t *choice, double *
     /* candidates: walk_variant -> mode.  A segment holds two rows on chip:
        tried only when the warp buffer fits them; the slot kernel (which falls
        back to segments) also needs s = 8, 16 or 32; the positional layout
-       one instance and no partitions (its tables are built first: they may
+       s = 8 .. 64 and no partitions (its tables are built first: they may
        grow row_capacity, which the other kernels' launch shapes follow) */
     const bool slot = qw_slot_supported(sim->d);
-    const bool pos = slot && sim->d.nparts == 1;
+    const bool pos = qw_pos_supported(sim->d) && sim->d.nparts == 1;
     if (pos) {
         const int rc = pos_build(sim);
         if (rc != QW_OK) return rc;

@@ -156,6 +156,8 @@ cudaError_t qw_launch_step(const QwSimDev &d, const QwBufDev &in, const QwBufDev
                            cudaStream_t st);
 /* whether the slot kernel (QW_MODE_WALK_SLOT) covers this sparsity */
 int qw_slot_supported(const QwSimDev &d);
+/* whether the positional layout (QW_MODE_WALK_POS) covers this s (8 .. 64) */
+int qw_pos_supported(const QwSimDev &d);
 /* dynamic shared memory per block of the step kernel of `mode` */
 size_t qw_step_smem_bytes(const QwSimDev &d, int fp32, int mode);
 /* positional layout: one walk step pin -> pout (both pos_R-strided row

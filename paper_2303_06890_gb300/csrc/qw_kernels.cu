@@ -679,10 +679,11 @@ template <> struct Amp<float2> {
             x.h *= g; x.l *= g; y.h *= g; y.l *= g;
         }
         __device__ T minus(T a) const { return make_float2(x.minus(a.x), y.minus(a.y)); }
-        __device__ T scaled_minus(double f, T a)
+        __device__ T scaled_minus(double f, T a) const
         {
-            scale_pow2(f);
-            return minus(a);
+            Sum c = *this;
+            c.scale_pow2(f);
+            return c.minus(a);
         }
         __device__ double2 value() const
         {
@@ -2487,11 +2488,13 @@ __device__ __forceinline__ unsigned int nz(double2 a)
 }
 
 template <typename AmpT, int S, int PW>
-__global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSimDev d, const AmpT *__restrict__ pin,
-                                                            AmpT *__restrict__ pout, QwStepArgs a)
+__global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks / (S > 32 ? 2 : 1))
+    k_walk_pos(QwSimDev d, const AmpT *__restrict__ pin, AmpT *__restrict__ pout, QwStepArgs a)
 {
     typedef typename Amp<AmpT>::RotVal RotVal;
-    constexpr int RPP = 32 / S;
+    /* a unit (one j) on SW lanes, each lane holding SPL of its slots (l = lb
+       + 32 k); RPP units per warp */
+    constexpr int SW = S > 32 ? 32 : S, SPL = S / SW, RPP = 32 / SW;
     __shared__ double block_part[PW];
     __shared__ double scale_sm;
     __shared__ int is_last;
@@ -2508,7 +2511,7 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
     const uint32_t n = (uint32_t)d.pos_rows; /* rows of all instances */
     const uint32_t nall = (n + RPP - 1) / RPP, ngroups = skip ? 0u : nall;
     const uint32_t nwarps = gridDim.x * PW;
-    const int ul = lane / S, l = lane % S;
+    const int ul = lane / SW, lb = lane % SW;
     const int nx = RPP * 2 * E; /* extra items of a group: (unit, b1, e) */
     /* the lane's first extra item is the same in every group */
     int x_u = 0, x_b1 = 0, x_e = 0;
@@ -2521,10 +2524,11 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
     /* a group's inputs, loaded one group ahead: the next group's loads are in
        flight while the current one computes */
     struct In {
-        uint32_t w, rb; /* QRAM word, first row of the row's instance */
-        RotVal t;
-        int tp;
-        AmpT a0, a1, q0, q1;
+        uint32_t rb;       /* first row of the row's instance */
+        uint32_t w[SPL];   /* QRAM words */
+        RotVal t[SPL];
+        int tp[SPL];
+        AmpT a0[SPL], a1[SPL], q0[SPL], q1[SPL];
         uint32_t xe; /* the lane's first extra item: x << 8 | l_x, 0xffffffff if none */
         AmpT x0, x1;
     };
@@ -2541,19 +2545,24 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
     };
     auto fetch = [&](uint32_t gg, In &x) {
         const uint32_t jj = gg * RPP + ul;
-        x.w = 0;
+        const bool have = gg < nall && jj < n;
         x.rb = 0;
-        x.t = Amp<AmpT>::rot_zero();
-        x.tp = 0;
-        x.a0 = x.a1 = x.q0 = x.q1 = zero;
-        if (gg < nall && jj < n) {
-            const uint32_t at = jj * S + l;
-            x.w = __ldg(d.img + at);
-            if (!rot_in_place) x.t = __ldg(static_cast<const RotVal *>(d.slot_rot) + at);
-            x.tp = __ldg(d.pos_tp + at);
-            if (d.pos_rowbase) x.rb = __ldg(d.pos_rowbase + jj);
-            PosPair<AmpT>::load(pin + 2 * jj * R + 2 * l, x.a0, x.a1);
-            PosPair<AmpT>::load(pin + (2 * jj + 1) * R + 2 * l, x.q0, x.q1);
+        if (have && d.pos_rowbase) x.rb = __ldg(d.pos_rowbase + jj);
+#pragma unroll
+        for (int k = 0; k < SPL; ++k) {
+            const uint32_t l = lb + 32 * k;
+            x.w[k] = 0;
+            x.t[k] = Amp<AmpT>::rot_zero();
+            x.tp[k] = 0;
+            x.a0[k] = x.a1[k] = x.q0[k] = x.q1[k] = zero;
+            if (have) {
+                const uint32_t at = jj * S + l;
+                x.w[k] = __ldg(d.img + at);
+                if (!rot_in_place) x.t[k] = __ldg(static_cast<const RotVal *>(d.slot_rot) + at);
+                x.tp[k] = __ldg(d.pos_tp + at);
+                PosPair<AmpT>::load(pin + 2 * jj * R + 2 * l, x.a0[k], x.a1[k]);
+                PosPair<AmpT>::load(pin + (2 * jj + 1) * R + 2 * l, x.q0[k], x.q1[k]);
+            }
         }
         x.xe = 0xffffffffu;
         x.x0 = x.x1 = zero;
@@ -2571,43 +2580,61 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
         fetch(g + nwarps, nxt);
         const uint32_t j = g * RPP + ul;
         const bool valid = j < n;
-        const uint32_t w = cur.w;
-        /* a 0 element rotates by R(0); complex64 derives the float pairs from
-           the value word (4 MB less read per step than the per-slot table) */
-        const RotVal rv = (w & 0xffffu) == 0 ? Amp<AmpT>::rot_zero()
-                                             : (rot_in_place ? Amp<AmpT>::rot_code(w & 0xffffu) : cur.t);
-        const uint32_t tp = (uint32_t)cur.tp;
-        AmpT a0 = cur.a0, a1 = cur.a1, q0 = cur.q0, q1 = cur.q1;
-        if (valid && rescale) {
-            a0 = scale.apply(a0);
-            a1 = scale.apply(a1);
-            q0 = scale.apply(q0);
-            q1 = scale.apply(q1);
+        RotVal rv[SPL];
+        uint32_t val[SPL], gc[SPL];
+        bool sneg[SPL];
+        AmpT a0[SPL], a1[SPL], q0[SPL], q1[SPL];
+        unsigned int nin = 0;
+#pragma unroll
+        for (int k = 0; k < SPL; ++k) {
+            const uint32_t w = cur.w[k];
+            val[k] = w & 0xffffu;
+            /* a 0 element rotates by R(0); complex64 derives the float pairs
+               from the value word (4 MB less read per step than the per-slot
+               table at N = 16384, s = 16) */
+            rv[k] = val[k] == 0 ? Amp<AmpT>::rot_zero() : (rot_in_place ? Amp<AmpT>::rot_code(val[k]) : cur.t[k]);
+            gc[k] = cur.rb + (w >> 16); /* the column's row among all instances' rows */
+            sneg[k] = j > gc[k];        /* j > col within the instance */
+            a0[k] = cur.a0[k];
+            a1[k] = cur.a1[k];
+            q0[k] = cur.q0[k];
+            q1[k] = cur.q1[k];
+            if (valid && rescale) {
+                a0[k] = scale.apply(a0[k]);
+                a1[k] = scale.apply(a1[k]);
+                q0[k] = scale.apply(q0[k]);
+                q1[k] = scale.apply(q1[k]);
+            }
+            nin += nz(a0[k]) + nz(a1[k]) + nz(q0[k]) + nz(q1[k]);
         }
-        const unsigned int nin = nz(a0) + nz(a1) + nz(q0) + nz(q1);
         st.in += nin;
         {
             const unsigned m = __ballot_sync(FULL, nin != 0);
-            const unsigned um = S == 32 ? m : (m >> (ul * S)) & ((1u << (S & 31)) - 1u);
-            if (l == 0 && um != 0) st.rows += 1; /* units holding branches */
+            const unsigned um = SW == 32 ? m : (m >> (ul * SW)) & ((1u << (SW & 31)) - 1u);
+            if (lb == 0 && um != 0) st.rows += 1; /* units holding branches */
         }
-        const uint32_t col = w >> 16, val = w & 0xffffu;
-        const uint32_t gc = cur.rb + col; /* the column's row among all instances' rows */
-        const bool sneg = j > gc;         /* j > col within the instance */
 
-        /* b1 = 0: R^dag, H P H on the zero-type group (the unit's lanes), R */
-        AmpT rA0, rA1;
-        bool eA0, eA1;
+        /* b1 = 0: R^dag, H P H on the zero-type group (the unit's slots), R */
+        AmpT rA0[SPL], rA1[SPL];
+        bool eA0[SPL], eA1[SPL];
         {
-            AmpT o0, o1;
-            Amp<AmpT>::rot(rv, val, true, sneg, a0, a1, o0, o1);
-            const bool c0 = Amp<AmpT>::keep(d, o0), c1 = Amp<AmpT>::keep(d, o1);
-            st.rdag += (c0 ? 1u : 0u) + (c1 ? 1u : 0u);
-            const AmpT z0 = c0 ? o0 : zero;
+            AmpT o1[SPL], z0[SPL];
+            bool c1[SPL];
+#pragma unroll
+            for (int k = 0; k < SPL; ++k) {
+                AmpT o0;
+                Amp<AmpT>::rot(rv[k], val[k], true, sneg[k], a0[k], a1[k], o0, o1[k]);
+                const bool c0 = Amp<AmpT>::keep(d, o0);
+                c1[k] = Amp<AmpT>::keep(d, o1[k]);
+                st.rdag += (c0 ? 1u : 0u) + (c1[k] ? 1u : 0u);
+                z0[k] = c0 ? o0 : zero;
+            }
             typename Amp<AmpT>::Sum sum;
-            sum.set(z0);
-            sum.reduce(S, S);
-            if (a.qls_readout && valid && l == 0) {
+            sum.set(z0[0]);
+#pragma unroll
+            for (int k = 1; k < SPL; ++k) sum.add(z0[k]);
+            sum.reduce(SW, SW);
+            if (a.qls_readout && valid && lb == 0) {
                 const double2 sv = sum.value();
                 const double coef = a.qls_coefs[*a.qls_j];
                 double2 acc = a.qls_y[j];
@@ -2615,46 +2642,50 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks) k_walk_pos(QwSi
                 acc.y += coef * (d.inv_sqrt_s * sv.y);
                 a.qls_y[j] = acc;
             }
-            const AmpT h0 = sum.scaled_minus(d.two_over_s, z0);
-            const bool d0 = Amp<AmpT>::keep(d, h0);
-            st.hph += (d0 ? 1u : 0u) + (c1 ? 1u : 0u);
-            Amp<AmpT>::rot(rv, val, false, sneg, d0 ? h0 : zero, c1 ? Amp<AmpT>::neg(o1) : zero, rA0, rA1);
-            eA0 = Amp<AmpT>::keep(d, rA0);
-            eA1 = Amp<AmpT>::keep(d, rA1);
+#pragma unroll
+            for (int k = 0; k < SPL; ++k) {
+                const AmpT h0 = sum.scaled_minus(d.two_over_s, z0[k]);
+                const bool d0 = Amp<AmpT>::keep(d, h0);
+                st.hph += (d0 ? 1u : 0u) + (c1[k] ? 1u : 0u);
+                Amp<AmpT>::rot(rv[k], val[k], false, sneg[k], d0 ? h0 : zero, c1[k] ? Amp<AmpT>::neg(o1[k]) : zero,
+                               rA0[k], rA1[k]);
+                eA0[k] = Amp<AmpT>::keep(d, rA0[k]);
+                eA1[k] = Amp<AmpT>::keep(d, rA1[k]);
+            }
         }
-        /* b1 = 1: R^dag, -1, R */
-        AmpT rB0, rB1;
-        bool eB0, eB1;
-        {
+        /* b1 = 1: R^dag, -1, R, then S: rows (col, 0) and (col, 1), positions
+           tp (from b1 = 0) and tp + 1 (from b1 = 1) */
+#pragma unroll
+        for (int k = 0; k < SPL; ++k) {
+            AmpT rB0, rB1;
             AmpT o0, o1;
             /* in the walk's reachable states the b2 = 1 member of a b1 = 1 pair
                is 0: then R^dag takes half the products (same results).  Taken
                on the FP64-pipe-bound complex128 path only: on complex64 the
                vote and the second code path cost more than the products */
-            if (Amp<AmpT>::kB2ZeroPath && __all_sync(FULL, nz(q1) == 0u))
-                Amp<AmpT>::rot_dag_b2zero(rv, val, sneg, q0, o0, o1);
+            if (Amp<AmpT>::kB2ZeroPath && __all_sync(FULL, nz(q1[k]) == 0u))
+                Amp<AmpT>::rot_dag_b2zero(rv[k], val[k], sneg[k], q0[k], o0, o1);
             else
-                Amp<AmpT>::rot(rv, val, true, sneg, q0, q1, o0, o1);
+                Amp<AmpT>::rot(rv[k], val[k], true, sneg[k], q0[k], q1[k], o0, o1);
             const bool c0 = Amp<AmpT>::keep(d, o0), c1 = Amp<AmpT>::keep(d, o1);
             const unsigned int kept = (c0 ? 1u : 0u) + (c1 ? 1u : 0u);
             st.rdag += kept;
             st.hph += kept;
-            Amp<AmpT>::rot(rv, val, false, sneg, c0 ? Amp<AmpT>::neg(o0) : zero, c1 ? Amp<AmpT>::neg(o1) : zero,
-                           rB0, rB1);
-            eB0 = Amp<AmpT>::keep(d, rB0);
-            eB1 = Amp<AmpT>::keep(d, rB1);
-        }
-        /* S: rows (col, 0) and (col, 1), positions tp (from b1 = 0), tp + 1 */
-        if (valid) {
-            const AmpT s0 = eA0 ? rA0 : zero, s1 = eB0 ? rB0 : zero;
-            const AmpT s2 = eA1 ? rA1 : zero, s3 = eB1 ? rB1 : zero;
-            if (eA0) nrm.add(rA0);
-            if (eB0) nrm.add(rB0);
-            if (eA1) nrm.add(rA1);
-            if (eB1) nrm.add(rB1);
-            st.out += (eA0 ? 1u : 0u) + (eB0 ? 1u : 0u) + (eA1 ? 1u : 0u) + (eB1 ? 1u : 0u);
-            PosPair<AmpT>::store(pout + 2 * gc * R + tp, s0, s1);
-            PosPair<AmpT>::store(pout + (2 * gc + 1) * R + tp, s2, s3);
+            Amp<AmpT>::rot(rv[k], val[k], false, sneg[k], c0 ? Amp<AmpT>::neg(o0) : zero,
+                           c1 ? Amp<AmpT>::neg(o1) : zero, rB0, rB1);
+            const bool eB0 = Amp<AmpT>::keep(d, rB0), eB1 = Amp<AmpT>::keep(d, rB1);
+            if (valid) {
+                const AmpT s0 = eA0[k] ? rA0[k] : zero, s1 = eB0 ? rB0 : zero;
+                const AmpT s2 = eA1[k] ? rA1[k] : zero, s3 = eB1 ? rB1 : zero;
+                if (eA0[k]) nrm.add(rA0[k]);
+                if (eB0) nrm.add(rB0);
+                if (eA1[k]) nrm.add(rA1[k]);
+                if (eB1) nrm.add(rB1);
+                st.out += (eA0[k] ? 1u : 0u) + (eB0 ? 1u : 0u) + (eA1[k] ? 1u : 0u) + (eB1 ? 1u : 0u);
+                const uint32_t tp = (uint32_t)cur.tp[k];
+                PosPair<AmpT>::store(pout + 2 * gc[k] * R + tp, s0, s1);
+                PosPair<AmpT>::store(pout + (2 * gc[k] + 1) * R + tp, s2, s3);
+            }
         }
 
         /* the extras of the group's rows: the lane's first item prefetched, any
@@ -3236,7 +3267,8 @@ int pos_grid_s(const QwSimDev &d)
     /* as many groups for every warp: with k = ceil(groups / resident warps)
        groups a warp, the fewest blocks that cover them (a warp with fewer
        groups than the others would wait for them at the end of the step) */
-    const int64_t groups = (d.pos_rows + (32 / S) - 1) / (32 / S);
+    constexpr int RPP = 32 / (S > 32 ? 32 : S);
+    const int64_t groups = (d.pos_rows + RPP - 1) / RPP;
     const int64_t cap = (int64_t)per_sm * qw_sm_count();
     const int64_t k = (groups + cap * PW - 1) / (cap * PW);
     const int64_t g = (groups + k * PW - 1) / (k * PW);
@@ -3248,7 +3280,8 @@ int pos_grid_t(const QwSimDev &d)
 {
     if (d.s == 8) return pos_grid_s<AmpT, 8>(d);
     if (d.s == 16) return pos_grid_s<AmpT, 16>(d);
-    return pos_grid_s<AmpT, 32>(d);
+    if (d.s == 32) return pos_grid_s<AmpT, 32>(d);
+    return pos_grid_s<AmpT, 64>(d);
 }
 
 template <typename AmpT>
@@ -3260,7 +3293,8 @@ cudaError_t launch_pos_t(const QwSimDev &d, const void *pin, void *pout, const Q
     constexpr int PW = PosCfg<AmpT>::warps;
     if (d.s == 8) k_walk_pos<AmpT, 8, PW><<<grid, PW * 32, 0, st>>>(d, i, o, a);
     else if (d.s == 16) k_walk_pos<AmpT, 16, PW><<<grid, PW * 32, 0, st>>>(d, i, o, a);
-    else k_walk_pos<AmpT, 32, PW><<<grid, PW * 32, 0, st>>>(d, i, o, a);
+    else if (d.s == 32) k_walk_pos<AmpT, 32, PW><<<grid, PW * 32, 0, st>>>(d, i, o, a);
+    else k_walk_pos<AmpT, 64, PW><<<grid, PW * 32, 0, st>>>(d, i, o, a);
     return cudaGetLastError();
 }
 
@@ -3285,6 +3319,11 @@ int qw_sm_count(void)
 int qw_slot_supported(const QwSimDev &d)
 {
     return d.s == 8 || d.s == 16 || d.s == 32;
+}
+
+int qw_pos_supported(const QwSimDev &d)
+{
+    return d.s == 8 || d.s == 16 || d.s == 32 || d.s == 64;
 }
 
 size_t qw_step_smem_bytes(const QwSimDev &d, int fp32, int mode)
@@ -3363,7 +3402,7 @@ int qw_pos_grid(const QwSimDev &d, int fp32)
 cudaError_t qw_launch_walk_pos(const QwSimDev &d, const void *pin, void *pout, const QwStepArgs &a, int fp32,
                                int grid, cudaStream_t st)
 {
-    if (!qw_slot_supported(d)) return cudaErrorInvalidValue;
+    if (!qw_pos_supported(d)) return cudaErrorInvalidValue;
     return fp32 ? launch_pos_t<float2>(d, pin, pout, a, grid, st) : launch_pos_t<double2>(d, pin, pout, a, grid, st);
 }
 

@@ -161,11 +161,11 @@ def test_faithful_codes_and_step_follow_the_header():
     assert len(step) == int(d["QW_FQ_STEP_LEN"])
 
 
-@pytest.mark.parametrize("variant,words", [(7, "walk_variants 4 and 7"), (4, "walk_variants 4 and 7"),
+@pytest.mark.parametrize("variant,words", [(7, "walk_variant 7 (positional layout) needs"), (4, "walk_variant 4 (one lane"),
                                            (8, "walk_variant must be 0..7"), (-1, "walk_variant must be 0..7")])
 def test_create_rejects_unsupported_walk_variants_before_device_work(variant, words):
-    """The slot kernel and the positional layout need s = 8, 16 or 32 (the
-    N = 16 walk has s = 4); variants outside 0..QW_WALK_VARIANTS - 1 are
+    """The slot kernel needs s = 8, 16 or 32, the positional layout s = 8 to
+    64 (the N = 16 walk has s = 4); variants outside 0..QW_WALK_VARIANTS - 1 are
     refused.  Both before any device call."""
     lib = qwalk.load()
     csc, keep = _csc(wl.walk_n16().matrix)

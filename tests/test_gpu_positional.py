@@ -32,13 +32,14 @@ def _oracle(w):
 
 @pytest.mark.parametrize("n,smax,seed,band,attempts", [(48, 8, 2, 1, None), (100, 8, 3, 0, None),
                                                        (130, 16, 5, 0, None), (300, 16, 8, 1, None),
-                                                       (90, 32, 9, 0, 3000), (70, 32, 10, 1, 3000)])
+                                                       (90, 32, 9, 0, 3000), (70, 32, 10, 1, 3000),
+                                                       (150, 64, 11, 0, 8000), (200, 64, 12, 1, 12000)])
 def test_positional_matches_oracle(n, smax, seed, band, attempts):
     """Step by step against the oracle (each read moves the state back into
     the row buckets, each step into the layout again): keys exactly,
     amplitudes to 1e-12."""
     w = wl.small_random(n, smax, seed, band=band, attempts=attempts)
-    assert w.s in (8, 16, 32)
+    assert w.s in (8, 16, 32, 64)
     sim = _sim(w, walk_variant=7)
     sim.state_init(w.b)
     o = _oracle(w)
@@ -233,3 +234,26 @@ def test_positional_batched_256_bitwise_equals_slot_kernel(precision):
         assert sa[k] == sb[k], k
     for sim in sims:
         sim.close()
+
+
+@pytest.mark.parametrize("precision", [qwalk.QW_FP64, qwalk.QW_FP32_AMP])
+def test_positional_table1_e_matches_oracle_and_segments(precision):
+    """Table 1's matrix E (N = 16384, s = 64: two QRAM slots per lane, 3.1 M
+    branches): after 3 steps the positional state equals the segment
+    kernel's (variant 2) -- complex128 to 1e-12 with equal keys (the
+    zero-type sums add in another order), complex64 within the
+    reduced-precision bounds.  (Oracle parity at s = 64 is checked above on
+    smaller matrices.)"""
+    w = wl.table1("E", steps=3)
+    assert w.s == 64
+    out = []
+    for v in (7, 2):
+        sim = _sim(w, walk_variant=v, precision=precision)
+        sim.state_init(w.b)
+        sim.apply_walk_step(3)
+        out.append(gpu_state(sim))
+        sim.close()
+    if precision == qwalk.QW_FP64:
+        compare(out[0], out[1], TOL64)
+    else:
+        compare_union(out[0], out[1], 2e-6, 1e-5)
