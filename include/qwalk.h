@@ -112,11 +112,14 @@ typedef struct {
                                 position, so a step has no search, atomic or clearing;
                                 a state with branches outside those positions (e.g.
                                 from qw_state_import) runs on the kernel of variant 4
-                                (2 for s = 64).  The state moves into the layout
-                                at the first walk step (a synchronisation) and back
-                                into the row buckets before any call that reads it;
-                                row_capacity grows to 2 s + 2 E (E: the most unpaired
-                                padded columns pointing at one row) */
+                                (2 for s = 64).  qw_state_init with apply_T = 1 writes
+                                T~|b~> straight into the layout and the register
+                                marginals read it in place; any other state moves into
+                                it at the first walk step (a synchronisation), and it
+                                moves back into the row buckets before qw_state_size,
+                                qw_state_export, qw_state_import or a register-faithful
+                                session; row_capacity grows to 2 s + 2 E (E: the most
+                                unpaired padded columns pointing at one row) */
     int32_t graphs;          /* 1 (default): runs of >= 6 walk steps are issued as replays
                                 of a captured 6-step CUDA graph; 0: one launch per step */
     int32_t spill_rows;      /* slots of the table holding rows with jc != 0 (reached only

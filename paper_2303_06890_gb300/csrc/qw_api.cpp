@@ -1135,16 +1135,28 @@ static int pos_pack(qw_sim *sim)
     return QW_OK;
 }
 
-/* The state back into the row buckets (stream-ordered, no synchronisation). */
+/* The state back into the row buckets (stream-ordered, no synchronisation).
+ * All three bucket buffers are cleared: a bucket step appends to the next
+ * buffer, which bucket steps run before the positional ones may have left
+ * holding an old state. */
 static int pos_unpack(qw_sim *sim)
 {
     if (!sim->pos_live) return QW_OK;
-    QW_CUDA(sim, qw_launch_clear(sim->d, sim->buf[sim->cur], 0, sim->d.total_buckets, 1, sim->stream));
+    for (const QwBufDev &b : sim->buf)
+        QW_CUDA(sim, qw_launch_clear(sim->d, b, 0, sim->d.total_buckets, 1, sim->stream));
     QW_CUDA(sim, qw_launch_pos_unpack(sim->d, sim->pbuf[sim->cur], sim->buf[sim->cur], sim->fp32, &sim->sc->status,
                                       sim->stream));
-    sim->launches += 2;
+    sim->launches += 4;
     sim->pos_live = false;
     return QW_OK;
+}
+
+/* First row of instance inst among all instances' rows (positional layout). */
+static int64_t pos_row0(const qw_sim *sim, int inst)
+{
+    int64_t g0 = 0;
+    for (int i = 0; i < inst; ++i) g0 += sim->n_of[(size_t)i];
+    return g0;
 }
 
 /* Before a positional walk: the state into the positional layout if it
@@ -1351,14 +1363,20 @@ extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, cons
 {
     if (!sim) return QW_ERR_ARG;
     if (sim->fq_open) return faithful_session_closed(sim);
-    if (sim->d.ninst > 1) { /* the other instances keep their state: back into the buckets */
-        const int prc = pos_unpack(sim);
-        if (prc != QW_OK) return prc;
-    }
-    sim->pos_live = false; /* the state is replaced in the row buckets */
-    sim->pos_try = true;
     if (inst < 0 || inst >= sim->d.ninst) return fail(sim, QW_ERR_ARG, "instance out of range");
     if (!b_re || n != sim->n_of[(size_t)inst]) return fail(sim, QW_ERR_ARG, "b must hold N values");
+    /* T~|b~> of a positional walk is written straight into the layout (one
+       instance, or several already there); otherwise into the row buckets */
+    const bool pos_init = apply_T && sim->mode == QW_MODE_WALK_POS && sim->pos_built &&
+                          (sim->d.ninst == 1 || sim->pos_live);
+    if (!pos_init) {
+        if (sim->d.ninst > 1) { /* the other instances keep their state: back into the buckets */
+            const int prc = pos_unpack(sim);
+            if (prc != QW_OK) return prc;
+        }
+        sim->pos_live = false; /* the state is replaced in the row buckets */
+    }
+    sim->pos_try = true;
     /* |b> goes straight from the caller's arrays to the device (asynchronous
        when they are pinned); the previous call's copies ended at its sync */
     double *dre = sim->b_dev, *dim = b_im ? sim->b_dev + sim->b_stride : nullptr;
@@ -1369,12 +1387,12 @@ extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, cons
     const bool all = sim->d.ninst == 1;
     /* clear the instance's rows in every buffer (the whole state for a single
        instance, garbage-row table included) */
-    for (int bi = 0; bi < 3; ++bi) {
+    for (int bi = 0; bi < 3 && !pos_init; ++bi) {
         QW_CUDA(sim, qw_launch_clear(sim->d, sim->buf[bi], all ? 0 : lo,
                                      all ? sim->d.total_buckets : hi, all ? 1 : 0, sim->stream));
         sim->launches++;
     }
-    if (apply_T && sim->opts.overflow_fallback && sim->d.cap_row < 2 * sim->d.s) {
+    if (apply_T && !pos_init && sim->opts.overflow_fallback && sim->d.cap_row < 2 * sim->d.s) {
         /* T~ gives a row of |b~> up to 2 s branches */
         int rc = grow_rows(sim, 2 * (int64_t)sim->d.s);
         if (rc != QW_OK) return rc;
@@ -1398,10 +1416,19 @@ extern "C" int qw_state_init(qw_sim *sim, int32_t inst, const double *b_re, cons
         QW_CUDA(sim, cudaMemcpyAsync(&sim->sc->renorm_target, &sim->host_target, 8,
                                      cudaMemcpyHostToDevice, sim->stream));
     }
-    QW_CUDA(sim, qw_launch_init_b(sim->d, sim->buf[sim->cur], inst, dre, dim, n, sim->fp32,
-                                  all ? nullptr : pending_scale(sim), sim->stream));
-    sim->launches++;
-    if (apply_T) {
+    if (pos_init) {
+        int64_t g0 = 0;
+        for (int i = 0; i < inst; ++i) g0 += sim->n_of[(size_t)i];
+        QW_CUDA(sim, qw_launch_tinit_pos(sim->d, sim->pbuf[sim->cur], g0, n, dre, dim,
+                                         all ? nullptr : pending_scale(sim), sim->fp32, sim->stream));
+        sim->launches++;
+        sim->pos_live = true;
+    } else {
+        QW_CUDA(sim, qw_launch_init_b(sim->d, sim->buf[sim->cur], inst, dre, dim, n, sim->fp32,
+                                      all ? nullptr : pending_scale(sim), sim->stream));
+        sim->launches++;
+    }
+    if (apply_T && !pos_init) {
         /* T~ on |b~>: the one-branch-per-row kernel (a row that is not |b~>
            sets a status bit), or the literal sort-based schedule when that
            was asked for */
@@ -1735,10 +1762,6 @@ extern "C" int qw_measure_register(qw_sim *sim, int32_t inst, int32_t reg, doubl
     if (inst < 0 || inst >= sim->d.ninst || reg < 0 || reg > 5 || !probs || len < 1)
         return fail(sim, QW_ERR_ARG, "bad instance, register id or output");
     if (!sim->has_state) return fail(sim, QW_ERR_STATE, "no state");
-    {
-        const int prc = pos_unpack(sim); /* the state back into the row buckets */
-        if (prc != QW_OK) return prc;
-    }
     if (sim->meas_cap < len) { /* kept for later calls */
         QW_CUDA(sim, cudaStreamSynchronize(sim->stream));
         cudaFree(sim->meas_dev);
@@ -1749,8 +1772,12 @@ extern "C" int qw_measure_register(qw_sim *sim, int32_t inst, int32_t reg, doubl
     }
     double *dp = sim->meas_dev;
     QW_CUDA(sim, cudaMemsetAsync(dp, 0, (size_t)len * sizeof(double), sim->stream));
-    QW_CUDA(sim, qw_launch_measure(sim->d, sim->buf[sim->cur], inst, sim->fp32, pending_scale(sim), reg,
-                                   dp, len, sim->stream));
+    if (sim->pos_live) /* read the positional layout in place */
+        QW_CUDA(sim, qw_launch_measure_pos(sim->d, sim->pbuf[sim->cur], pos_row0(sim, inst), sim->n_of[(size_t)inst],
+                                           sim->fp32, pending_scale(sim), reg, dp, len, sim->stream));
+    else
+        QW_CUDA(sim, qw_launch_measure(sim->d, sim->buf[sim->cur], inst, sim->fp32, pending_scale(sim), reg,
+                                       dp, len, sim->stream));
     sim->launches++;
     QW_CUDA(sim, cudaMemcpyAsync(probs, dp, (size_t)len * sizeof(double), cudaMemcpyDeviceToHost,
                                  sim->stream));
@@ -1773,12 +1800,10 @@ extern "C" int qw_measure_register_noalloc(qw_sim *sim, int32_t inst, int32_t re
                     "qw_measure_register_noalloc: len " + std::to_string(len) + " exceeds the fixed scratch of " +
                         std::to_string(QW_MEASURE_NOALLOC_MAX_LEN) + " bins; use qw_measure_register");
     if (!sim->has_state) return fail(sim, QW_ERR_STATE, "no state");
-    {
-        const int prc = pos_unpack(sim); /* the state back into the row buckets */
-        if (prc != QW_OK) return prc;
-    }
     QW_CUDA(sim, qw_launch_measure_noalloc(sim->d, sim->buf[sim->cur], inst, sim->fp32, pending_scale(sim),
-                                           reg, probs, len, sim->device, sim->stream));
+                                           reg, probs, len, sim->device, sim->stream,
+                                           sim->pos_live ? sim->pbuf[sim->cur] : nullptr, pos_row0(sim, inst),
+                                           sim->n_of[(size_t)inst]));
     sim->launches++;
     return check_status(sim, "qw_measure_register_noalloc");
 }

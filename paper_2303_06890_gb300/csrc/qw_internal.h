@@ -171,6 +171,13 @@ cudaError_t qw_launch_pos_pack(const QwSimDev &d, const QwBufDev &buf, void *pbu
                                cudaStream_t st);
 cudaError_t qw_launch_pos_unpack(const QwSimDev &d, const void *pbuf, const QwBufDev &buf, int fp32,
                                  int32_t *status, cudaStream_t st);
+/* T~|b~> written straight into rows g0 .. g0 + n of the positional layout
+   (the rest of those rows zeroed); a register marginal read straight from
+   those rows (probs zeroed by the caller, accumulated by atomics) */
+cudaError_t qw_launch_tinit_pos(const QwSimDev &d, void *pbuf, int64_t g0, int64_t n, const double *b_re,
+                                const double *b_im, const double *scale, int fp32, cudaStream_t st);
+cudaError_t qw_launch_measure_pos(const QwSimDev &d, const void *pbuf, int64_t g0, int64_t n, int fp32,
+                                  const double *scale, int reg, double *probs, int64_t len, cudaStream_t st);
 int qw_step_grid(const QwSimDev &d, int fp32, int mode);
 cudaError_t qw_launch_clear(const QwSimDev &d, const QwBufDev &buf, int64_t lo, int64_t hi,
                             int clear_spill, cudaStream_t st);
@@ -187,9 +194,11 @@ cudaError_t qw_launch_export(const QwSimDev &d, const QwBufDev &buf, int inst, i
 cudaError_t qw_launch_measure(const QwSimDev &d, const QwBufDev &buf, int inst, int fp32,
                               const double *scale, int reg, double *probs, int64_t len,
                               cudaStream_t st);
+/* pbuf (nullable): read rows g0 .. g0 + pn of the positional layout instead of buf */
 cudaError_t qw_launch_measure_noalloc(const QwSimDev &d, const QwBufDev &buf, int inst, int fp32,
                                       const double *scale, int reg, double *host_probs,
-                                      int64_t len, int device, cudaStream_t st);
+                                      int64_t len, int device, cudaStream_t st, const void *pbuf = nullptr,
+                                      int64_t g0 = 0, int64_t pn = 0);
 cudaError_t qw_launch_count(const QwSimDev &d, const QwBufDev &buf, int inst,
                             unsigned long long *counter, cudaStream_t st);
 cudaError_t qw_launch_qls_norm(const double2 *y, int n, double *p, int64_t *jctr, cudaStream_t st);

@@ -2760,6 +2760,91 @@ __global__ void __launch_bounds__(PW * 32, PosCfg<AmpT>::blocks / (S > 32 ? 2 : 
     }
 }
 
+/* T~|b~> written straight into the positional layout for rows g0 .. g0 + n
+ * of pbuf (one instance): |b~> holds one branch per row, a = b_j (divided by
+ * the pending renormalisation factor when other instances share the state);
+ * T~'s Hadamard gives (l, z = 0) with a / sqrt(s) for every slot l, its maps
+ * take slot l to k = col(j, l), and R(A_jl) on (a / sqrt(s), 0) gives the
+ * pair at positions 2 l, 2 l + 1 of row (j, b1 = 0) -- the arithmetic of
+ * k_tinit.  Every other position of both rows is written 0.  One thread per
+ * position. */
+template <typename AmpT>
+__global__ void k_tinit_pos(QwSimDev d, AmpT *pbuf, int64_t g0, int64_t n, const double *b_re, const double *b_im,
+                            const double *scale)
+{
+    typedef typename Amp<AmpT>::RotVal RotVal;
+    const int S = d.s;
+    const int64_t R = d.pos_R, total = 2 * n * R;
+    const AmpT zero = Amp<AmpT>::zero();
+    const bool rot_in_place = Amp<AmpT>::kRotCode && d.rot_calc;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / R, j = r >> 1;
+        const int q = (int)(i - r * R);
+        AmpT out = zero;
+        if ((r & 1) == 0 && q < 2 * S) {
+            double2 v = make_double2(b_re[j], b_im ? b_im[j] : 0.0);
+            if (scale) v = make_double2(v.x / *scale, v.y / *scale);
+            const double2 a = Amp<AmpT>::to_d(Amp<AmpT>::from_d(v)); /* as stored by |b~> */
+            const AmpT h = Amp<AmpT>::from_d(make_double2(d.inv_sqrt_s * a.x, d.inv_sqrt_s * a.y));
+            if ((v.x != 0.0 || v.y != 0.0) && Amp<AmpT>::keep(d, h)) {
+                const int64_t at = (g0 + j) * S + (q >> 1);
+                const uint32_t w = __ldg(d.img + at), val = w & 0xffffu;
+                const RotVal rv = val == 0 ? Amp<AmpT>::rot_zero()
+                                           : (rot_in_place ? Amp<AmpT>::rot_code(val)
+                                                           : __ldg(static_cast<const RotVal *>(d.slot_rot) + at));
+                AmpT o0, o1;
+                Amp<AmpT>::rot(rv, val, false, (uint32_t)j > (w >> 16), h, zero, o0, o1); /* R */
+                const AmpT o = (q & 1) ? o1 : o0;
+                if (Amp<AmpT>::keep(d, o)) out = o;
+            }
+        }
+        pbuf[2 * g0 * R + i] = out;
+    }
+}
+
+/* Marginal of one register over instance rows g0 .. g0 + n of the
+ * positional layout (the key of a position: jc = kc = 0, j = its row, b1, k
+ * = the slot's column or the extra's row, b2 = position & 1).  A warp per
+ * row; the row registers (jc, j, b1) add the row's sum once. */
+template <typename AmpT>
+__global__ void k_measure_pos(QwSimDev d, const AmpT *pbuf, int64_t g0, int64_t n, const double *scale, int reg,
+                              double *probs, int64_t len)
+{
+    const int S = d.s, E = d.pos_E;
+    const int64_t R = d.pos_R;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double sc = scale ? *scale : 1.0;
+    const bool row_reg = reg <= 2;
+    for (int64_t rr = warp; rr < 2 * n; rr += nw) {
+        const int64_t j = rr >> 1, g = g0 + j;
+        const int b1 = (int)(rr & 1);
+        const int width = 2 * S + 2 * (int)d.pos_xcnt[g];
+        double acc = 0.0;
+        for (int q = lane; q < width; q += 32) {
+            double2 a = Amp<AmpT>::to_d(pbuf[(2 * g + b1) * R + q]);
+            if (a.x == 0.0 && a.y == 0.0) continue;
+            if (scale) a = make_double2(sc * a.x, sc * a.y);
+            const double p = a.x * a.x + a.y * a.y;
+            if (row_reg) {
+                acc += p;
+                continue;
+            }
+            uint64_t v = 0; /* kc = 0 */
+            if (reg == 4) v = q < 2 * S ? (d.img[g * S + (q >> 1)] >> 16)
+                                        : (uint64_t)((d.pos_xin[g * E + ((q - 2 * S) >> 1)] >> 8) - (uint32_t)g0);
+            else if (reg == 5) v = (uint64_t)(q & 1);
+            if ((int64_t)v < len) atomicAdd(probs + v, p);
+        }
+        if (row_reg) {
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+            const int64_t v = reg == 1 ? j : (reg == 2 ? b1 : 0);
+            if (lane == 0 && acc != 0.0 && v < len) atomicAdd(probs + v, acc);
+        }
+    }
+}
+
 /* the row buckets into the positional layout (pbuf zeroed by the caller):
    one thread per bucket slot */
 template <typename AmpT>
@@ -3415,6 +3500,27 @@ cudaError_t qw_launch_walk_pos(const QwSimDev &d, const void *pin, void *pout, c
     return fp32 ? launch_pos_t<float2>(d, pin, pout, a, grid, st) : launch_pos_t<double2>(d, pin, pout, a, grid, st);
 }
 
+cudaError_t qw_launch_tinit_pos(const QwSimDev &d, void *pbuf, int64_t g0, int64_t n, const double *b_re,
+                                const double *b_im, const double *scale, int fp32, cudaStream_t st)
+{
+    const int grid = 4 * qw_sm_count();
+    if (fp32) k_tinit_pos<float2><<<grid, 256, 0, st>>>(d, static_cast<float2 *>(pbuf), g0, n, b_re, b_im, scale);
+    else k_tinit_pos<double2><<<grid, 256, 0, st>>>(d, static_cast<double2 *>(pbuf), g0, n, b_re, b_im, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t qw_launch_measure_pos(const QwSimDev &d, const void *pbuf, int64_t g0, int64_t n, int fp32,
+                                  const double *scale, int reg, double *probs, int64_t len, cudaStream_t st)
+{
+    const int grid = 4 * qw_sm_count();
+    if (fp32)
+        k_measure_pos<float2><<<grid, 256, 0, st>>>(d, static_cast<const float2 *>(pbuf), g0, n, scale, reg, probs, len);
+    else
+        k_measure_pos<double2><<<grid, 256, 0, st>>>(d, static_cast<const double2 *>(pbuf), g0, n, scale, reg, probs,
+                                                     len);
+    return cudaGetLastError();
+}
+
 cudaError_t qw_launch_pos_pack(const QwSimDev &d, const QwBufDev &buf, void *pbuf, int fp32, int32_t *status,
                                cudaStream_t st)
 {
@@ -3522,7 +3628,8 @@ double *g_scratch_addr[kMaxDevices] = {nullptr};
 
 cudaError_t qw_launch_measure_noalloc(const QwSimDev &d, const QwBufDev &buf, int inst, int fp32,
                                       const double *scale, int reg, double *host_probs,
-                                      int64_t len, int device, cudaStream_t st)
+                                      int64_t len, int device, cudaStream_t st, const void *pbuf, int64_t g0,
+                                      int64_t pn)
 {
     if (device < 0 || device >= kMaxDevices || len < 1 || len > QW_MEASURE_NOALLOC_MAX_LEN)
         return cudaErrorInvalidValue;
@@ -3545,9 +3652,10 @@ cudaError_t qw_launch_measure_noalloc(const QwSimDev &d, const QwBufDev &buf, in
     cudaError_t e = cudaMemsetAsync(scratch, 0, (size_t)len * sizeof(double), st);
     if (e != cudaSuccess) return e;
     const int grid = 4 * qw_sm_count();
-    if (fp32) k_measure<float2><<<grid, 256, 0, st>>>(d, buf, inst, scale, reg, scratch, len);
+    if (pbuf) e = qw_launch_measure_pos(d, pbuf, g0, pn, fp32, scale, reg, scratch, len, st);
+    else if (fp32) k_measure<float2><<<grid, 256, 0, st>>>(d, buf, inst, scale, reg, scratch, len);
     else k_measure<double2><<<grid, 256, 0, st>>>(d, buf, inst, scale, reg, scratch, len);
-    e = cudaGetLastError();
+    if (!pbuf) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(host_probs, scratch, (size_t)len * sizeof(double), cudaMemcpyDeviceToHost, st);
 }

@@ -257,3 +257,28 @@ def test_positional_table1_e_matches_oracle_and_segments(precision):
         compare(out[0], out[1], TOL64)
     else:
         compare_union(out[0], out[1], 2e-6, 1e-5)
+
+
+@pytest.mark.parametrize("precision", [qwalk.QW_FP64, qwalk.QW_FP32_AMP])
+def test_positional_init_and_marginals_in_place(precision):
+    """T~|b~> written straight into the positional layout equals the bucket
+    path's T~ bit for bit, and the register marginals read in place equal
+    the slot kernel's after 7 steps (both measurement entry points)."""
+    w = wl.walk_n1024()
+    a = _sim(w, walk_variant=7, precision=precision, renorm=0)
+    b = _sim(w, walk_variant=4, precision=precision, renorm=0)
+    for sim in (a, b):
+        sim.state_init(w.b)
+    ka, va = a.state_export()
+    kb, vb = b.state_export()
+    assert np.array_equal(ka, kb) and np.array_equal(va, vb)
+    for sim in (a, b):
+        sim.state_init(w.b)  # positional again, the steps from the layout
+        sim.apply_walk_step(7)
+    for reg, length in (("jc", 4), ("j", w.n), ("b1", 2), ("kc", 4), ("k", w.n), ("b2", 2)):
+        pa, pb = a.measure_register(reg, length), b.measure_register(reg, length)
+        assert np.abs(pa - pb).max() < 1e-12, reg
+        na = a.measure_register_noalloc(reg, length)
+        assert np.abs(na - pb).max() < 1e-12, reg
+    a.close()
+    b.close()
