@@ -2804,31 +2804,31 @@ __global__ void k_tinit_pos(QwSimDev d, AmpT *pbuf, int64_t g0, int64_t n, const
 
 /* Marginal of one register over instance rows g0 .. g0 + n of the
  * positional layout (the key of a position: jc = kc = 0, j = its row, b1, k
- * = the slot's column or the extra's row, b2 = position & 1).  A warp per
- * row; the row registers (jc, j, b1) add the row's sum once. */
+ * = the slot's column or the extra's row, b2 = position & 1).  A warp per j
+ * reads both rows whole (positions past a row's extras are 0), all loads in
+ * flight together; the row registers (jc, j, b1) add their sums once. */
 template <typename AmpT>
 __global__ void k_measure_pos(QwSimDev d, const AmpT *pbuf, int64_t g0, int64_t n, const double *scale, int reg,
                               double *probs, int64_t len)
 {
     const int S = d.s, E = d.pos_E;
-    const int64_t R = d.pos_R;
+    const int R = d.pos_R;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const double sc = scale ? *scale : 1.0;
-    const bool row_reg = reg <= 2;
-    for (int64_t rr = warp; rr < 2 * n; rr += nw) {
-        const int64_t j = rr >> 1, g = g0 + j;
-        const int b1 = (int)(rr & 1);
-        const int width = 2 * S + 2 * (int)d.pos_xcnt[g];
-        double acc = 0.0;
-        for (int q = lane; q < width; q += 32) {
-            double2 a = Amp<AmpT>::to_d(pbuf[(2 * g + b1) * R + q]);
+    for (int64_t j = warp; j < n; j += nw) {
+        const int64_t g = g0 + j;
+        const AmpT *rows = pbuf + 2 * g * R; /* rows (j, 0) and (j, 1) */
+        double acc[2] = {0.0, 0.0};
+        for (int q2 = lane; q2 < 2 * R; q2 += 32) {
+            double2 a = Amp<AmpT>::to_d(rows[q2]);
             if (a.x == 0.0 && a.y == 0.0) continue;
             if (scale) a = make_double2(sc * a.x, sc * a.y);
             const double p = a.x * a.x + a.y * a.y;
-            if (row_reg) {
-                acc += p;
+            const int b1 = q2 >= R ? 1 : 0, q = q2 - b1 * R;
+            if (reg <= 2) {
+                acc[reg == 2 ? b1 : 0] += p;
                 continue;
             }
             uint64_t v = 0; /* kc = 0 */
@@ -2837,10 +2837,19 @@ __global__ void k_measure_pos(QwSimDev d, const AmpT *pbuf, int64_t g0, int64_t 
             else if (reg == 5) v = (uint64_t)(q & 1);
             if ((int64_t)v < len) atomicAdd(probs + v, p);
         }
-        if (row_reg) {
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-            const int64_t v = reg == 1 ? j : (reg == 2 ? b1 : 0);
-            if (lane == 0 && acc != 0.0 && v < len) atomicAdd(probs + v, acc);
+        if (reg <= 2) {
+            for (int t = 0; t < 2; ++t)
+                for (int o = 16; o > 0; o >>= 1) acc[t] += __shfl_xor_sync(FULL, acc[t], o);
+            if (lane == 0) {
+                if (reg == 1) {
+                    if (j < len && acc[0] != 0.0) atomicAdd(probs + j, acc[0]);
+                } else {
+                    for (int t = 0; t < 2; ++t) {
+                        const int64_t v = reg == 2 ? t : 0;
+                        if (v < len && acc[t] != 0.0) atomicAdd(probs + v, acc[t]);
+                    }
+                }
+            }
         }
     }
 }
@@ -3512,7 +3521,10 @@ cudaError_t qw_launch_tinit_pos(const QwSimDev &d, void *pbuf, int64_t g0, int64
 cudaError_t qw_launch_measure_pos(const QwSimDev &d, const void *pbuf, int64_t g0, int64_t n, int fp32,
                                   const double *scale, int reg, double *probs, int64_t len, cudaStream_t st)
 {
-    const int grid = 4 * qw_sm_count();
+    /* a warp per j: enough blocks that every j's loads are in flight at once */
+    int64_t want = (n + 7) / 8;
+    const int64_t cap = 32 * (int64_t)qw_sm_count();
+    const int grid = (int)(want < 1 ? 1 : (want < cap ? want : cap));
     if (fp32)
         k_measure_pos<float2><<<grid, 256, 0, st>>>(d, static_cast<const float2 *>(pbuf), g0, n, scale, reg, probs, len);
     else
