@@ -738,9 +738,10 @@ def qls_leg(torch, barrier, max_over_ranks) -> dict:
 def partition_leg(torch, steps: int = 24) -> dict:
     """The N = 16384 walk split in row blocks among P simulators of this
     process on one device (qw_part_walk: each step runs every part's step
-    kernel, then moves S's sends between the parts by cudaMemcpyAsync and
-    appends them; one synchronisation per step), complex64: walk steps/s of
-    the whole walk and the branches exchanged per step.  An emulation of the
+    kernel, then appends S's sends to each part straight from the others'
+    outboxes and sets the renormalisation from the summed norms, all on the
+    device; one synchronisation per call), complex64: walk steps/s of the
+    whole walk and the branches each part holds.  An emulation of the
     multi-GPU partition on one device: the parts share its SMs."""
     from paper_2303_06890_gb300 import partition, qwalk
     from paper_2303_06890_gb300 import workloads as wl

@@ -370,12 +370,18 @@ int qw_part_set_norm(qw_sim *sim, double global_norm2);
 
 /*
  * nsteps steps of a walk partitioned among nparts simulators of one process
- * on one device: each step runs every partition's step kernel, then moves
- * every outbox segment to its destination by cudaMemcpyAsync (device to
- * device) and appends it, then sets every partition's renormalisation from
- * the summed norms.  Synchronises once per step.
+ * on one device: each step runs every partition's step kernel on its stream;
+ * then, on each partition's stream once every step kernel is done (CUDA
+ * events), the entries the others' S sent to it are appended straight from
+ * their outbox segments (the counts read on the device) and its
+ * renormalisation factor is set from the summed norms of all partitions'
+ * outputs; a partition's next step waits for every exchange of the previous
+ * one.  No host synchronisation between steps: the call synchronises once at
+ * the end and reads every partition's device status.  After a device error
+ * (an outbox or a row overflow) the partitions are not at a common step:
+ * initialise them again.
  * Errors: QW_ERR_ARG (not a set of partitions 0 .. nparts - 1 of one walk),
- * QW_ERR_CAPACITY, QW_ERR_DEVICE_STATUS, QW_ERR_CUDA.
+ * QW_ERR_STATE, QW_ERR_CAPACITY, QW_ERR_DEVICE_STATUS, QW_ERR_CUDA.
  */
 int qw_part_walk(qw_sim **sims, int32_t nparts, int64_t nsteps);
 

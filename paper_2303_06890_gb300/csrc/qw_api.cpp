@@ -2084,64 +2084,72 @@ extern "C" int qw_part_set_norm(qw_sim *sim, double global_norm2)
 
 extern "C" int qw_part_walk(qw_sim **sims, int32_t np, int64_t nsteps)
 {
-    if (!sims || np < 1 || nsteps < 0) return QW_ERR_ARG;
+    if (!sims || np < 1 || np > 64 || nsteps < 0) return QW_ERR_ARG;
     for (int p = 0; p < np; ++p) {
         if (!sims[p] || sims[p]->d.nparts != np || sims[p]->d.part != p || sims[p]->device != sims[0]->device)
             return sims[p] ? fail(sims[p], QW_ERR_ARG, "qw_part_walk: not partitions 0 .. nparts - 1 of one walk")
                            : QW_ERR_ARG;
         if (!sims[p]->has_state) return fail(sims[p], QW_ERR_STATE, "no state");
+        if (sims[p]->fq_open) return faithful_session_closed(sims[p]);
     }
-    std::vector<unsigned long long> cnt((size_t)np * np);
-    for (int64_t t = 0; t < nsteps; ++t) {
-        /* every partition's step kernel */
-        for (int p = 0; p < np; ++p) {
-            int rc = qw_enqueue_walk_steps(sims[p], 1);
-            if (rc != QW_OK) return rc;
-        }
-        for (int p = 0; p < np; ++p) {
+    /* Per step, with no host synchronisation: every part's step kernel on
+       its stream; then on each part q's stream, once every step is done, the
+       entries the others' S sent to q are appended straight from their outbox
+       segments (counts read on the device) and q's renormalisation factor is
+       set from the norms of all parts' outputs.  A part's next step waits
+       for every exchange of the previous one (its outbox is read there). */
+    std::vector<cudaEvent_t> ev_step((size_t)np, nullptr), ev_x((size_t)np, nullptr);
+    int rc = QW_OK;
+    for (int p = 0; p < np && rc == QW_OK; ++p) {
+        if (cudaEventCreateWithFlags(&ev_step[(size_t)p], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev_x[(size_t)p], cudaEventDisableTiming) != cudaSuccess)
+            rc = fail(sims[p], QW_ERR_CUDA, "qw_part_walk: cudaEventCreate");
+    }
+    auto cuda = [&](qw_sim *sim, cudaError_t e, const char *what) {
+        if (e != cudaSuccess && rc == QW_OK) rc = cuda_fail(sim, e, what);
+    };
+    for (int64_t t = 0; t < nsteps && rc == QW_OK; ++t) {
+        for (int p = 0; p < np && rc == QW_OK; ++p) {
             qw_sim *sp = sims[p];
-            int rc = check_status(sp, "qw_part_walk");
-            if (rc != QW_OK) return rc;
-            QW_CUDA(sp, cudaMemcpy(cnt.data() + (size_t)p * np, sp->outbox_count, (size_t)np * 8,
-                                   cudaMemcpyDeviceToHost));
+            if (t > 0)
+                for (int q = 0; q < np; ++q)
+                    if (q != p) cuda(sp, cudaStreamWaitEvent(sp->stream, ev_x[(size_t)q], 0), "cudaStreamWaitEvent");
+            if (rc == QW_OK) rc = launch_walk(sp, 0);
+            if (rc == QW_OK) cuda(sp, cudaEventRecord(ev_step[(size_t)p], sp->stream), "cudaEventRecord");
         }
-        /* S's exchange: outbox segment p -> q copied into q's inbox, appended */
-        double global = 0.0;
-        for (int q = 0; q < np; ++q) {
+        for (int q = 0; q < np && rc == QW_OK; ++q) {
             qw_sim *sq = sims[q];
-            int64_t in = 0;
-            for (int p = 0; p < np; ++p)
-                if (p != q) in += std::min<int64_t>((int64_t)cnt[(size_t)p * np + q], sims[p]->d.outbox_cap);
-            if (in > sq->inbox_cap) {
-                QW_CUDA(sq, cudaStreamSynchronize(sq->stream));
-                cudaFree(sq->inbox);
-                sq->inbox = nullptr;
-                sq->inbox_cap = 0;
-                QW_CUDA(sq, cudaMalloc((void **)&sq->inbox, (size_t)in * sizeof(QwPartEntry)));
-                sq->inbox_cap = in;
-            }
-            int64_t off = 0;
+            QwPartSources src{};
+            QwPartNorms nm{};
+            src.cap = sq->d.outbox_cap;
             for (int p = 0; p < np; ++p) {
+                nm.norm[nm.n++] = &sims[p]->sc->norm[sims[p]->scale_slot]; /* the step's output norm */
                 if (p == q) continue;
-                const int64_t n = std::min<int64_t>((int64_t)cnt[(size_t)p * np + q], sims[p]->d.outbox_cap);
-                if (n > 0)
-                    QW_CUDA(sq, cudaMemcpyAsync(sq->inbox + off, sims[p]->outbox + (int64_t)q * sims[p]->d.outbox_cap,
-                                                (size_t)n * sizeof(QwPartEntry), cudaMemcpyDeviceToDevice, sq->stream));
-                off += n;
+                cuda(sq, cudaStreamWaitEvent(sq->stream, ev_step[(size_t)p], 0), "cudaStreamWaitEvent");
+                src.e[src.n] = sims[p]->outbox + (int64_t)q * sims[p]->d.outbox_cap;
+                src.count[src.n] = sims[p]->outbox_count + q;
+                src.n++;
+                if (sims[p]->d.outbox_cap < src.cap) src.cap = sims[p]->d.outbox_cap;
             }
-            QW_CUDA(sq, qw_launch_part_inbox(sq->d, sq->buf[sq->cur], sq->inbox, in, sq->fp32, &sq->sc->status,
-                                             sq->stream));
-            sq->launches++;
-            double local = 0.0;
-            int rc = qw_part_norm(sq, &local);
-            if (rc != QW_OK) return rc;
-            global += local;
-        }
-        for (int q = 0; q < np; ++q) {
-            int rc = check_status(sims[q], "qw_part_walk");
-            if (rc == QW_OK) rc = qw_part_set_norm(sims[q], global);
-            if (rc != QW_OK) return rc;
+            cuda(sq, qw_launch_part_gather(sq->d, sq->buf[sq->cur], src, sq->fp32, &sq->sc->status, sq->stream),
+                 "part gather launch");
+            cuda(sq, qw_launch_part_scale(nm, &sq->sc->renorm_target, &sq->sc->scale[sq->scale_slot], sq->renorm,
+                                          sq->stream),
+                 "part scale launch");
+            sq->launches += 2;
+            cuda(sq, cudaEventRecord(ev_x[(size_t)q], sq->stream), "cudaEventRecord");
         }
     }
-    return QW_OK;
+    /* the device status of every part (outbox or row overflow) */
+    for (int p = 0; p < np; ++p) {
+        if (sims[p]) {
+            const int prc = check_status(sims[p], "qw_part_walk");
+            if (rc == QW_OK) rc = prc;
+        }
+    }
+    for (int p = 0; p < np; ++p) {
+        if (ev_step[(size_t)p]) cudaEventDestroy(ev_step[(size_t)p]);
+        if (ev_x[(size_t)p]) cudaEventDestroy(ev_x[(size_t)p]);
+    }
+    return rc;
 }

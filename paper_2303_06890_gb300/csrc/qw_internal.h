@@ -241,6 +241,22 @@ int qw_faithful_layout(const QwSimDev &d, int *addr_bits, int *layout_bits);
 cudaError_t qw_faithful_op(const QwSimDev &d, void *keys, int64_t M, int op, int32_t *status, cudaStream_t st);
 cudaError_t qw_faithful_check_idle(const QwSimDev &d, const void *keys, int64_t M, int32_t *status, cudaStream_t st);
 cudaError_t qw_faithful_export(const QwSimDev &d, const void *keys, int64_t M, uint64_t *table, cudaStream_t st);
+/* the other partitions' outbox segments toward this one (entries and device
+   counts, cap entries each) and the norm slots of all parts' last step */
+struct QwPartSources {
+    const QwPartEntry *e[64];
+    const unsigned long long *count[64];
+    int n;
+    int64_t cap;
+};
+struct QwPartNorms {
+    const double *norm[64];
+    int n;
+};
+cudaError_t qw_launch_part_gather(const QwSimDev &d, const QwBufDev &buf, const QwPartSources &src, int fp32,
+                                  int32_t *status, cudaStream_t st);
+cudaError_t qw_launch_part_scale(const QwPartNorms &nm, const double *target, double *scale_out, int renorm,
+                                 cudaStream_t st);
 cudaError_t qw_launch_part_inbox(const QwSimDev &d, const QwBufDev &buf, const QwPartEntry *e, int64_t count, int fp32,
                                  int32_t *status, cudaStream_t st);
 

@@ -3092,25 +3092,54 @@ __global__ void k_import(QwSimDev d, QwBufDev buf, const uint64_t *rowkey, const
 
 /* Branches received from other partitions (their S outputs for rows this
  * partition owns) appended to the buckets of their rows. */
+/* one received entry appended to its row */
+template <typename AmpT>
+__device__ __forceinline__ void part_append(const QwSimDev &d, const QwBufDev &buf, const QwPartEntry &x,
+                                            int32_t *status)
+{
+    const uint64_t rk = x.rowkey;
+    const uint32_t inst = (uint32_t)(rk >> 40), jc = (uint32_t)((rk >> 20) & 0xfffffu);
+    const uint32_t j = (uint32_t)((rk >> 1) & 0x7ffffu), b1 = (uint32_t)(rk & 1);
+    const int64_t b = bucket_of(d, buf, inst, jc, j, b1, status);
+    if (b < 0) return;
+    const int pos = atomicAdd(buf.count + b, 1);
+    if (pos >= d.cap_row) {
+        atomicOr(status, QW_ST_ROW_OVERFLOW);
+        return;
+    }
+    const int64_t slot = b * (int64_t)d.cap_row + pos;
+    buf.key[slot] = x.local;
+    store_amp<AmpT>(buf.amp, slot, make_double2(x.re, x.im));
+}
+
 template <typename AmpT>
 __global__ void k_part_inbox(QwSimDev d, QwBufDev buf, const QwPartEntry *e, int64_t count, int32_t *status)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-        const QwPartEntry x = e[i];
-        const uint64_t rk = x.rowkey;
-        const uint32_t inst = (uint32_t)(rk >> 40), jc = (uint32_t)((rk >> 20) & 0xfffffu);
-        const uint32_t j = (uint32_t)((rk >> 1) & 0x7ffffu), b1 = (uint32_t)(rk & 1);
-        const int64_t b = bucket_of(d, buf, inst, jc, j, b1, status);
-        if (b < 0) continue;
-        const int pos = atomicAdd(buf.count + b, 1);
-        if (pos >= d.cap_row) {
-            atomicOr(status, QW_ST_ROW_OVERFLOW);
-            continue;
-        }
-        const int64_t slot = b * (int64_t)d.cap_row + pos;
-        buf.key[slot] = x.local;
-        store_amp<AmpT>(buf.amp, slot, make_double2(x.re, x.im));
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        part_append<AmpT>(d, buf, e[i], status);
+}
+
+/* The entries the other partitions' S sent here, appended straight from
+ * their outbox segments (their counts read on the device: no host round
+ * trip), one thread per entry slot of every source. */
+template <typename AmpT>
+__global__ void k_part_gather(QwSimDev d, QwBufDev buf, QwPartSources src, int32_t *status)
+{
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthr = (int64_t)gridDim.x * blockDim.x;
+    for (int k = 0; k < src.n; ++k) {
+        const unsigned long long c = *src.count[k];
+        const int64_t m = (int64_t)c < src.cap ? (int64_t)c : src.cap;
+        for (int64_t i = tid; i < m; i += nthr) part_append<AmpT>(d, buf, src.e[k][i], status);
     }
+}
+
+/* The renormalisation factor of a partition from the norms of all parts'
+ * outputs of the step: scale = sqrt(target / sum) (1 without renorm). */
+__global__ void k_part_scale(QwPartNorms nm, const double *target, double *scale_out, int renorm)
+{
+    double sum = 0.0;
+    for (int p = 0; p < nm.n; ++p) sum += *nm.norm[p];
+    *scale_out = (renorm && sum > 0.0) ? sqrt(*target / sum) : 1.0;
 }
 
 /* Every branch of instance inst (-1: all) to flat (row key, local key, amp). */
@@ -3598,6 +3627,25 @@ cudaError_t qw_launch_part_inbox(const QwSimDev &d, const QwBufDev &buf, const Q
     if (grid > 8 * qw_sm_count()) grid = 8 * qw_sm_count();
     if (fp32) k_part_inbox<float2><<<(unsigned)grid, 256, 0, st>>>(d, buf, e, count, status);
     else k_part_inbox<double2><<<(unsigned)grid, 256, 0, st>>>(d, buf, e, count, status);
+    return cudaGetLastError();
+}
+
+cudaError_t qw_launch_part_gather(const QwSimDev &d, const QwBufDev &buf, const QwPartSources &src, int fp32,
+                                  int32_t *status, cudaStream_t st)
+{
+    if (src.n <= 0) return cudaSuccess;
+    int64_t grid = (src.cap + 255) / 256;
+    if (grid > 8 * qw_sm_count()) grid = 8 * qw_sm_count();
+    if (grid < 1) grid = 1;
+    if (fp32) k_part_gather<float2><<<(unsigned)grid, 256, 0, st>>>(d, buf, src, status);
+    else k_part_gather<double2><<<(unsigned)grid, 256, 0, st>>>(d, buf, src, status);
+    return cudaGetLastError();
+}
+
+cudaError_t qw_launch_part_scale(const QwPartNorms &nm, const double *target, double *scale_out, int renorm,
+                                 cudaStream_t st)
+{
+    k_part_scale<<<1, 1, 0, st>>>(nm, target, scale_out, renorm);
     return cudaGetLastError();
 }
 
