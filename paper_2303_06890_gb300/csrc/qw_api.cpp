@@ -872,7 +872,33 @@ static cudaError_t flat_stage(qw_sim *sim, FlatList &L, int op)
         cudaFreeAsync(work, st);
         if (e != cudaSuccess) return e;
     }
-    const int64_t n = L.M * outs;
+    /* H: s outputs per group of the sorted list -- count the groups first
+       (head flags and their scan; the host reads the count) */
+    int64_t G = 0;
+    int64_t *starts = nullptr;
+    if (op == 2 && L.M > 0) {
+        void *heads = nullptr, *gidx = nullptr, *hsums = nullptr;
+        uint32_t g32 = 0;
+        if ((e = flat_alloc(sim, (size_t)L.M * 4, &heads)) != cudaSuccess) return e;
+        if ((e = flat_alloc(sim, (size_t)L.M * 4, &gidx)) != cudaSuccess) return e;
+        if ((e = flat_alloc(sim, qw_flat_scan_words(L.M) * 4, &hsums)) != cudaSuccess) return e;
+        e = qw_flat_heads(d, L.K, L.M, static_cast<uint32_t *>(heads), st, L.kw);
+        if (e == cudaSuccess)
+            e = qw_flat_scan(static_cast<uint32_t *>(heads), L.M, static_cast<uint32_t *>(hsums),
+                             static_cast<uint32_t *>(gidx), st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&g32, static_cast<uint32_t *>(hsums) + (L.M + 1023) / 1024, 4, cudaMemcpyDeviceToHost,
+                                st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        G = (int64_t)g32;
+        if (e == cudaSuccess) e = flat_alloc(sim, (size_t)(G + 1) * 8, (void **)&starts);
+        if (e == cudaSuccess)
+            e = qw_flat_starts(static_cast<uint32_t *>(heads), static_cast<uint32_t *>(gidx), L.M, G, starts, st);
+        for (void *p : {heads, gidx, hsums})
+            if (p) cudaFreeAsync(p, st);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t n = op == 2 ? G * outs : L.M * outs;
     void *ok = nullptr, *oa = nullptr, *flags = nullptr, *pos = nullptr, *sums = nullptr;
     if ((e = flat_alloc(sim, (size_t)n * kb, &ok)) != cudaSuccess) return e;
     if ((e = flat_alloc(sim, (size_t)n * 16, &oa)) != cudaSuccess) return e;
@@ -881,7 +907,7 @@ static cudaError_t flat_stage(qw_sim *sim, FlatList &L, int op)
     if ((e = flat_alloc(sim, qw_flat_scan_words(n) * 4, &sums)) != cudaSuccess) return e;
     uint32_t total = 0;
     e = qw_flat_group(d, op, L.K, L.A, L.M, ok, static_cast<double2 *>(oa), static_cast<uint32_t *>(flags), st,
-                      L.kw);
+                      L.kw, starts, G);
     if (e == cudaSuccess && n > 0) {
         e = qw_flat_scan(static_cast<uint32_t *>(flags), n, static_cast<uint32_t *>(sums), static_cast<uint32_t *>(pos),
                          st);
@@ -898,7 +924,7 @@ static cudaError_t flat_stage(qw_sim *sim, FlatList &L, int op)
     if (e == cudaSuccess)
         e = qw_flat_compact(ok, static_cast<double2 *>(oa), static_cast<uint32_t *>(flags),
                             static_cast<uint32_t *>(pos), n, R.K, R.A, st, L.kw);
-    for (void *p : {ok, oa, flags, pos, sums})
+    for (void *p : {ok, oa, flags, pos, sums, (void *)starts})
         if (p) cudaFreeAsync(p, st);
     flat_release(sim, L);
     L = R;

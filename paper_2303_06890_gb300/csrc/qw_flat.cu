@@ -688,32 +688,50 @@ __global__ void k_f_rot(QwSimDev d, const FKeyN<NW> *keys, const double2 *amps, 
 /* H on the low L bits of k (sorted in ORDER_H): the head of each group
  * writes the s outputs (1/sqrt s) sum_v (-1)^(u.v) a_v at s i + u. */
 template <int NW>
-__global__ void k_f_hadamard(QwSimDev d, const FKeyN<NW> *keys, const double2 *amps, int64_t M, FKeyN<NW> *okeys,
-                             double2 *oamps, uint32_t *flags)
+__global__ void k_f_heads(QwSimDev d, const FKeyN<NW> *keys, int64_t M, uint32_t *flags)
 {
-    const int L = d.L, s = d.s;
-    const uint64_t lowm = (((uint64_t)s - 1ull) << 1);
+    const int L = d.L;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
+        flags[i] = (i == 0 || !same_group<ORDER_H>(keys[i - 1], keys[i], L)) ? 1u : 0u;
+}
+
+/* starts[g] = the first member of group g (gidx: the exclusive scan of the
+   head flags), starts[G] = M */
+__global__ void k_f_starts(const uint32_t *heads, const uint32_t *gidx, int64_t M, int64_t G, int64_t *starts)
+{
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        const FKeyN<NW> k = keys[i];
-        const bool head = i == 0 || !same_group<ORDER_H>(keys[i - 1], k, L);
-        for (int u = 0; u < s; ++u) flags[(int64_t)s * i + u] = 0u;
-        if (!head) continue;
-        int64_t e = i + 1;
-        while (e < M && e < i + s && same_group<ORDER_H>(k, keys[e], L)) ++e;
-        for (int u = 0; u < s; ++u) {
-            double2 o = make_double2(0, 0);
-            for (int64_t m = i; m < e; ++m) {
-                const uint32_t v = (uint32_t)((keys[m].w[0] >> 1) & (uint64_t)(s - 1));
-                const double2 a = amps[m];
-                o = (__popc((uint32_t)u & v) & 1) ? csub(o, a) : cadd(o, a);
-            }
-            o = cscale(d.inv_sqrt_s, o);
-            FKeyN<NW> ko = k;
-            ko.w[0] = (ko.w[0] & ~lowm) | ((uint64_t)u << 1);
-            okeys[(int64_t)s * i + u] = ko;
-            oamps[(int64_t)s * i + u] = o;
-            flags[(int64_t)s * i + u] = keep(o, d.tau2) ? 1u : 0u;
+        if (heads[i]) starts[gidx[i]] = i;
+        if (i == 0) starts[G] = M;
+    }
+}
+
+/* The s outputs of every Hadamard group (members equal but for the low L
+ * bits of k, contiguous after the sort): one thread per (group, u), the
+ * group's members read in list order, so each output is the same sum as a
+ * dense s x s product on the zero-filled vector. */
+template <int NW>
+__global__ void k_f_hadamard(QwSimDev d, const FKeyN<NW> *keys, const double2 *amps, const int64_t *starts, int64_t G,
+                             FKeyN<NW> *okeys, double2 *oamps, uint32_t *flags)
+{
+    const int s = d.s;
+    const uint64_t lowm = (((uint64_t)s - 1ull) << 1);
+    const int64_t n = G * s;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = t / s;
+        const int u = (int)(t - g * s);
+        const int64_t b = starts[g], e = starts[g + 1];
+        double2 o = make_double2(0, 0);
+        for (int64_t m = b; m < e; ++m) {
+            const uint32_t v = (uint32_t)((keys[m].w[0] >> 1) & (uint64_t)(s - 1));
+            const double2 a = amps[m];
+            o = (__popc((uint32_t)u & v) & 1) ? csub(o, a) : cadd(o, a);
         }
+        o = cscale(d.inv_sqrt_s, o);
+        FKeyN<NW> ko = keys[b];
+        ko.w[0] = (ko.w[0] & ~lowm) | ((uint64_t)u << 1);
+        okeys[t] = ko;
+        oamps[t] = o;
+        flags[t] = keep(o, d.tau2) ? 1u : 0u;
     }
 }
 
@@ -948,22 +966,41 @@ cudaError_t qw_flat_sort(const QwSimDev &d, void *keys, double2 *amps, void *tmp
 }
 
 /* op: 0 = R^dag, 1 = R (2 outputs per entry), 2 = H (s outputs per entry) */
-cudaError_t qw_flat_group(const QwSimDev &d, int op, const void *keys, const double2 *amps, int64_t M, void *okeys,
-                          double2 *oamps, uint32_t *flags, cudaStream_t st, int kw)
+cudaError_t qw_flat_heads(const QwSimDev &d, const void *keys, int64_t M, uint32_t *flags, cudaStream_t st, int kw)
 {
     if (M <= 0) return cudaSuccess;
+    if (kw == NW_FAITH)
+        k_f_heads<NW_FAITH><<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<const FKeyW *>(keys), M, flags);
+    else k_f_heads<2><<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<const FKey *>(keys), M, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t qw_flat_starts(const uint32_t *heads, const uint32_t *gidx, int64_t M, int64_t G, int64_t *starts,
+                           cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    k_f_starts<<<grid_for(M, 256), 256, 0, st>>>(heads, gidx, M, G, starts);
+    return cudaGetLastError();
+}
+
+cudaError_t qw_flat_group(const QwSimDev &d, int op, const void *keys, const double2 *amps, int64_t M, void *okeys,
+                          double2 *oamps, uint32_t *flags, cudaStream_t st, int kw, const int64_t *starts, int64_t G)
+{
+    if (M <= 0) return cudaSuccess;
+    const int64_t nh = G * d.s;
     if (kw == NW_FAITH) {
         const FKeyW *k = static_cast<const FKeyW *>(keys);
         FKeyW *ok = static_cast<FKeyW *>(okeys);
         if (op == 0) k_f_rot<true, NW_FAITH><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
         else if (op == 1) k_f_rot<false, NW_FAITH><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
-        else k_f_hadamard<NW_FAITH><<<grid_for(M, 128), 128, 0, st>>>(d, k, amps, M, ok, oamps, flags);
+        else if (nh > 0)
+            k_f_hadamard<NW_FAITH><<<grid_for(nh, 128), 128, 0, st>>>(d, k, amps, starts, G, ok, oamps, flags);
     } else {
         const FKey *k = static_cast<const FKey *>(keys);
         FKey *ok = static_cast<FKey *>(okeys);
         if (op == 0) k_f_rot<true, 2><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
         else if (op == 1) k_f_rot<false, 2><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
-        else k_f_hadamard<2><<<grid_for(M, 128), 128, 0, st>>>(d, k, amps, M, ok, oamps, flags);
+        else if (nh > 0) k_f_hadamard<2><<<grid_for(nh, 128), 128, 0, st>>>(d, k, amps, starts, G, ok, oamps, flags);
     }
     return cudaGetLastError();
 }

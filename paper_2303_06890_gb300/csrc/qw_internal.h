@@ -227,8 +227,15 @@ cudaError_t qw_flat_scan(const uint32_t *in, int64_t n, uint32_t *sums, uint32_t
 size_t qw_flat_sort_words(int64_t M);
 cudaError_t qw_flat_sort(const QwSimDev &d, void *keys, double2 *amps, void *tmpk, double2 *tmpa, int64_t M,
                          int order, uint32_t *work, cudaStream_t st, int kw);
+/* the Hadamard stage's groups: head flags of the sorted list, and the first
+   member of each of its G groups (starts[G] = M) from their exclusive scan */
+cudaError_t qw_flat_heads(const QwSimDev &d, const void *keys, int64_t M, uint32_t *flags, cudaStream_t st, int kw);
+cudaError_t qw_flat_starts(const uint32_t *heads, const uint32_t *gidx, int64_t M, int64_t G, int64_t *starts,
+                           cudaStream_t st);
+/* op 0 (R^dag) and 1 (R): 2 M outputs; op 2 (H): s outputs per group (starts, G) */
 cudaError_t qw_flat_group(const QwSimDev &d, int op, const void *keys, const double2 *amps, int64_t M, void *okeys,
-                          double2 *oamps, uint32_t *flags, cudaStream_t st, int kw);
+                          double2 *oamps, uint32_t *flags, cudaStream_t st, int kw, const int64_t *starts = nullptr,
+                          int64_t G = 0);
 cudaError_t qw_flat_compact(const void *keys, const double2 *amps, const uint32_t *flags, const uint32_t *pos,
                             int64_t n, void *okeys, double2 *oamps, cudaStream_t st, int kw);
 cudaError_t qw_flat_readout(const QwSimDev &d, const void *keys, const double2 *amps, int64_t M, const QwStepArgs &a,
