@@ -6,7 +6,8 @@
  *       all registers, with the target's bits moved below the others, so that
  *       the branches equal on every idle register are contiguous;
  *   (2) computing: the small dense operator on each group's zero-filled
- *       vector (a thread per group);
+ *       vector (a thread per output; for H the groups are counted first, so
+ *       that s outputs are formed per group, not per list entry);
  *   (3) clearing: outputs with |a| <= tau dropped by a stream compaction.
  * T~^dag, H, P, H, T~ and S run in the order of Alg. "Quantum walk operator",
  * with the element register A allocated for the whole step.  Nothing here is
