@@ -711,6 +711,7 @@ static int check_status(qw_sim *sim, const char *where)
     if (st & QW_ST_ANCILLA) m += " [register A not returned to zero]";
     if (st & QW_ST_NOT_BTILDE) m += " [a row was not |b~> before T~]";
     if (st & QW_ST_OUTBOX_FULL) m += " [an outbox toward another partition is full: raise outbox_capacity]";
+    if (st & QW_ST_SORT_WAIT) m += " [the flat path's radix sort gave up waiting for a tile's count]";
     m += "; state kept after " + std::to_string(good) + " clean steps since the last sync";
     const int code = (st & (QW_ST_ROW_OVERFLOW | QW_ST_WARP_OVERFLOW | QW_ST_SPILL_FULL | QW_ST_OUTBOX_FULL))
                          ? QW_ERR_CAPACITY
@@ -864,9 +865,17 @@ static cudaError_t flat_stage(qw_sim *sim, FlatList &L, int op)
     if (L.M > 1) {
         if ((e = flat_alloc(sim, (size_t)L.M * kb, &tk)) != cudaSuccess) return e;
         if ((e = flat_alloc(sim, (size_t)L.M * 16, &ta)) != cudaSuccess) return e;
-        if ((e = flat_alloc(sim, qw_flat_sort_words(L.M) * 4, &work)) != cudaSuccess) return e;
-        e = qw_flat_sort(d, L.K, L.A, tk, static_cast<double2 *>(ta), L.M, op == 2 ? 1 : 0,
-                         static_cast<uint32_t *>(work), st, L.kw);
+        if ((e = flat_alloc(sim, qw_flat_sort_bytes(L.M), &work)) != cudaSuccess) return e;
+        int in_tmp = 0;
+        e = qw_flat_sort(d, L.K, L.A, tk, static_cast<double2 *>(ta), L.M, op == 2 ? 1 : 0, work,
+                         &sim->sc->status, st, L.kw, &in_tmp);
+        if (e == cudaSuccess && in_tmp) {
+            /* the sorted list is the one in the scratch arrays: swap them */
+            std::swap(L.K, tk);
+            double2 *sorted = static_cast<double2 *>(ta);
+            ta = L.A;
+            L.A = sorted;
+        }
         cudaFreeAsync(tk, st);
         cudaFreeAsync(ta, st);
         cudaFreeAsync(work, st);

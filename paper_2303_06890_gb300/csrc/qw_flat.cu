@@ -2,9 +2,11 @@
  * qw_flat.cu -- the walk step as the paper's simulator runs it, on one flat
  * list of branches in global memory (Sec. V-A): every register map applied to
  * every branch, and every interference operation as
- *   (1) grouping: a stable LSD radix sort (4-bit digits) of the whole list by
- *       all registers, with the target's bits moved below the others, so that
- *       the branches equal on every idle register are contiguous;
+ *   (1) grouping: a stable LSD radix sort of the whole list by all
+ *       registers, with the target's bits moved below the others, so that
+ *       the branches equal on every idle register are contiguous (8-bit
+ *       digits over the bits that vary between keys, one single-pass
+ *       kernel per digit carrying a permutation, the entries moved once);
  *   (2) computing: the small dense operator on each group's zero-filled
  *       vector (a thread per output; for H the groups are counted first, so
  *       that s outputs are formed per group, not per list entry);
@@ -21,6 +23,8 @@
  * qw_state_export:  b2 | k (nb) | kc (nb) | b1 | j (nb) | jc (nb) | A (16) |
  * inst (16), 4 nb + 34 bits.
  */
+#include <vector>
+
 #include "qw_device.cuh"
 
 namespace {
@@ -553,89 +557,232 @@ __global__ void k_scan_apply(const uint32_t *in, int64_t n, const uint32_t *sums
 
 /* ---- radix sort ------------------------------------------------------------------ */
 
+/* OR and AND of every permuted key, word by word: the bits that differ
+   between keys.  The key array is read as a flat array of 64-bit words; the
+   grid's stride is a multiple of NW, so each thread always sees one word
+   index. */
 template <int ORDER, int NW>
-__global__ void k_f_orand(const FKeyN<NW> *keys, int64_t M, int L, unsigned long long *acc)
+__global__ void k_f_orand(const uint64_t *words, int64_t nwords, int L, unsigned long long *acc)
 {
-    uint64_t ov[NW], av[NW];
-#pragma unroll
-    for (int t = 0; t < NW; ++t) {
-        ov[t] = 0ull;
-        av[t] = ~0ull;
+    __shared__ unsigned long long s_or[NW], s_and[NW];
+    if (threadIdx.x < NW) {
+        s_or[threadIdx.x] = 0ull;
+        s_and[threadIdx.x] = ~0ull;
     }
+    __syncthreads();
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int wi = (int)(g % NW);
+    uint64_t ov = 0ull, av = ~0ull;
+    for (int64_t q = g; q < nwords; q += stride) {
+        uint64_t v = words[q];
+        if (wi == 0) v = permuted0<ORDER>(v, L);
+        ov |= v;
+        av &= v;
+    }
+    atomicOr(&s_or[wi], (unsigned long long)ov);
+    atomicAnd(&s_and[wi], (unsigned long long)av);
+    __syncthreads();
+    if (threadIdx.x < NW) {
+        atomicOr(acc + threadIdx.x, s_or[threadIdx.x]);
+        atomicAnd(acc + NW + threadIdx.x, s_and[threadIdx.x]);
+    }
+}
+
+/* The sort runs on a compacted key: the bits that vary between keys, taken
+ * in order of significance of the permuted key, 64 at a time (a "chunk").
+ * LSD order carries over chunks: chunk 0 is sorted first, chunk c + 1 is
+ * formed from the keys in the order chunk c left. */
+constexpr int CK_MAXRUNS = 64, CK_MAXPASS = 8;
+constexpr int OS_THREADS = 256, OS_IPT = 8, OS_TILE = OS_THREADS * OS_IPT;
+constexpr int OS_SPIN_LIMIT = 1 << 22;
+
+/* the varying bits of one chunk as runs of adjacent bits (key word, first
+   bit, length), lowest first; the chunk's bit b is the b-th of them */
+struct CkRuns {
+    uint8_t word[CK_MAXRUNS], shift[CK_MAXRUNS], len[CK_MAXRUNS];
+    int n, npass;
+};
+
+/* The chunk's compacted key of every entry -- the entry at position i of the
+   current order, i.e. keys[perm[i]] (perm == nullptr: i) -- and the global
+   count of every 8-bit digit of it for each of the chunk's passes
+   (ghist[pass * 256 + digit], zeroed by the caller). */
+template <int ORDER, int NW>
+__global__ void __launch_bounds__(256) k_f_ckey(const FKeyN<NW> *keys, const uint32_t *perm, int64_t M, int L,
+                                                CkRuns runs, uint64_t *ck, uint32_t *ghist)
+{
+    __shared__ uint32_t h[CK_MAXPASS * 256];
+    for (int t = threadIdx.x; t < CK_MAXPASS * 256; t += blockDim.x) h[t] = 0u;
+    __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        FKeyN<NW> k = keys[i];
-        k.w[0] = permuted0<ORDER>(k.w[0], L);
+        int64_t j = perm ? (int64_t)perm[i] : i;
+        if (j >= M) j = 0; /* only after a sort wait gave up */
+        const FKeyN<NW> *k = keys + j;
+        uint64_t c = 0ull, v = 0ull;
+        int dst = 0, cw = -1;
+        for (int r = 0; r < runs.n; ++r) {
+            const int w = runs.word[r];
+            if (w != cw) {
+                v = k->w[w];
+                if (w == 0) v = permuted0<ORDER>(v, L);
+                cw = w;
+            }
+            const int ln = runs.len[r];
+            const uint64_t m = ln >= 64 ? ~0ull : (1ull << ln) - 1ull;
+            c |= ((v >> runs.shift[r]) & m) << dst;
+            dst += ln;
+        }
+        ck[i] = c;
+        for (int p = 0; p < runs.npass; ++p) atomicAdd(&h[p * 256 + (int)((c >> (8 * p)) & 255ull)], 1u);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < runs.npass * 256; t += blockDim.x)
+        if (h[t]) atomicAdd(ghist + t, h[t]);
+}
+
+/* status of a tile in one pass, one 64-bit word per (tile, digit): the pass
+   tag (bits 40..63; a word of another pass reads as not ready), 1 = the
+   tile's own count / 2 = the inclusive prefix over tiles 0..vb (bits 38, 39),
+   the count (bits 0..37) */
+constexpr uint64_t OS_AGG = 1ull << 38, OS_INC = 2ull << 38, OS_CNT = (1ull << 38) - 1ull;
+
+__device__ __forceinline__ uint64_t os_load(const uint64_t *p)
+{
+    return *reinterpret_cast<const volatile uint64_t *>(p);
+}
+
+__device__ __forceinline__ void os_store(uint64_t *p, uint64_t v)
+{
+    *reinterpret_cast<volatile uint64_t *>(p) = v;
+}
+
+/* One stable pass on the 8-bit digit at `shift` of the compacted key.  A
+ * block takes tile vb in the order blocks start (a counter), so every tile
+ * before it belongs to a block already running.  Warp w ranks items vb T +
+ * 256 w + 32 r + lane (r = 0..7) by their digit in that order; the tile's
+ * digit counts are published, then the counts of the tiles before it are
+ * summed by looking back until a tile with its inclusive prefix (single-pass
+ * "decoupled look-back" prefix sum); an item goes to the digit's global
+ * start (the exclusive scan of ghist) + the tiles before + the warps before
+ * + its rank.  A wait that outlasts OS_SPIN_LIMIT polls sets
+ * QW_ST_SORT_WAIT and the block carries on (the sort's result is then
+ * wrong, and the host reports the status). */
+template <bool FIRST, bool WRITE_CK>
+__global__ void __launch_bounds__(OS_THREADS, 4) k_f_onesweep(const uint64_t *ckin, const uint32_t *ixin, uint64_t *ckout,
+                                                           uint32_t *ixout, int64_t M, int shift,
+                                                           const uint32_t *ghist, uint64_t *stat, uint64_t tag,
+                                                           unsigned int *ctr, int32_t *status)
+{
+    __shared__ uint32_t hw[8][256];
+    __shared__ uint32_t sbase[256];
+    __shared__ uint32_t wsum[8];
+    __shared__ unsigned int svb;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (t == 0) svb = atomicAdd(ctr, 1u);
 #pragma unroll
-        for (int t = 0; t < NW; ++t) {
-            ov[t] |= k.w[t];
-            av[t] &= k.w[t];
+    for (int w = 0; w < 8; ++w) hw[w][t] = 0u;
+    __syncthreads();
+    const int64_t vb = svb;
+    const int64_t base = vb * OS_TILE + warp * (32 * OS_IPT) + lane;
+    uint64_t c[OS_IPT];
+    uint32_t ix[OS_IPT], rk[OS_IPT];
+    int dg[OS_IPT];
+#pragma unroll
+    for (int r = 0; r < OS_IPT; ++r) {
+        const int64_t i = base + 32 * r;
+        dg[r] = 256;
+        c[r] = 0ull;
+        ix[r] = 0u;
+        if (i < M) {
+            c[r] = ckin[i];
+            ix[r] = FIRST ? (uint32_t)i : ixin[i];
+            dg[r] = (int)((c[r] >> shift) & 255ull);
         }
     }
+    const unsigned below = (1u << lane) - 1u;
 #pragma unroll
-    for (int t = 0; t < NW; ++t) {
-        for (int o = 16; o > 0; o >>= 1) {
-            ov[t] |= __shfl_xor_sync(FULL, ov[t], o);
-            av[t] &= __shfl_xor_sync(FULL, av[t], o);
+    for (int r = 0; r < OS_IPT; ++r) {
+        const unsigned m = __match_any_sync(FULL, dg[r]);
+        const int d = dg[r];
+        const uint32_t cnt = d < 256 ? hw[warp][d] : 0u;
+        rk[r] = cnt + (uint32_t)__popc(m & below);
+        __syncwarp();
+        if (d < 256 && (m & below) == 0u) hw[warp][d] = cnt + (uint32_t)__popc(m);
+        __syncwarp();
+    }
+    __syncthreads();
+    /* thread t owns digit t: the warps' exclusive prefix, the tile's count */
+    uint32_t run = 0u;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const uint32_t v = hw[w][t];
+        hw[w][t] = run;
+        run += v;
+    }
+    uint64_t *my = stat + vb * 256 + t;
+    os_store(my, (tag << 40) | (vb == 0 ? OS_INC : OS_AGG) | run);
+    /* global start of digit t: exclusive scan of this pass's digit counts */
+    const uint32_t g = ghist[t];
+    uint32_t x = g;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    /* look back over the tiles before */
+    uint64_t excl = 0ull;
+    if (vb > 0) {
+        int64_t p = vb - 1;
+        int spins = 0;
+        while (p >= 0) {
+            const uint64_t v = os_load(stat + p * 256 + t);
+            if ((v >> 40) != tag) {
+                if (++spins > OS_SPIN_LIMIT) {
+                    atomicOr(status, QW_ST_SORT_WAIT);
+                    break;
+                }
+                if (spins > 32) __nanosleep(64);
+                continue;
+            }
+            excl += v & OS_CNT;
+            if (v & OS_INC) break;
+            --p;
         }
-        if ((threadIdx.x & 31) == 0) {
-            atomicOr(acc + t, (unsigned long long)ov[t]);
-            atomicAnd(acc + NW + t, (unsigned long long)av[t]);
+        os_store(my, (tag << 40) | OS_INC | (excl + run));
+    }
+    __syncthreads();
+    uint32_t pre = 0u;
+    for (int w = 0; w < warp; ++w) pre += wsum[w];
+    sbase[t] = pre + x - g + (uint32_t)excl;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < OS_IPT; ++r) {
+        const int d = dg[r];
+        const uint32_t dest = d < 256 ? sbase[d] + hw[warp][d] + rk[r] : 0u;
+        if (d < 256 && (int64_t)dest < M) { /* always, unless a wait gave up */
+            if (WRITE_CK) ckout[dest] = c[r];
+            ixout[dest] = ix[r];
         }
     }
 }
 
-/* One pass of the stable LSD radix sort on the 4-bit digit at `shift` of the
- * permuted key: count_only -- per-block digit counts into hist[digit * nblk +
- * block]; otherwise scatter to offs[digit * nblk + block] + the item's rank
- * among the equal digits before it (rounds of 256 items in order, warps in
- * order, lanes in order). */
-template <int ORDER, int NW>
-__global__ void __launch_bounds__(256) k_f_radix(const FKeyN<NW> *kin, const double2 *ain, FKeyN<NW> *kout,
-                                                 double2 *aout, int64_t M, int64_t tile, int shift, int L,
-                                                 const uint32_t *offs, uint32_t *hist, int count_only)
+/* the sorted list: entry i is the entry perm[i] of the input */
+template <int NW>
+__global__ void k_f_permute(const FKeyN<NW> *kin, const double2 *ain, const uint32_t *perm, FKeyN<NW> *kout,
+                            double2 *aout, int64_t M)
 {
-    __shared__ uint32_t wc[8][16];
-    __shared__ uint32_t run[16];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t lo = (int64_t)blockIdx.x * tile;
-    const int64_t hi = lo + tile < M ? lo + tile : M;
-    if (threadIdx.x < 16) run[threadIdx.x] = count_only ? 0u : offs[threadIdx.x * gridDim.x + blockIdx.x];
-    __syncthreads();
-    for (int64_t base = lo; base < hi; base += 256) {
-        const int64_t i = base + threadIdx.x;
-        const bool act = i < hi;
-        int dig = 16;
-        if (act) {
-            const int wi = shift >> 6;
-            uint64_t wv = kin[i].w[wi];
-            if (wi == 0) wv = permuted0<ORDER>(wv, L);
-            dig = (int)((wv >> (shift & 63)) & 15ull);
-        }
-        const unsigned m = __match_any_sync(FULL, dig);
-        const int rank = __popc(m & ((1u << lane) - 1u));
-        if (threadIdx.x < 128) (&wc[0][0])[threadIdx.x] = 0u;
-        __syncthreads();
-        if (act && rank == 0) wc[warp][dig] = (uint32_t)__popc(m);
-        __syncthreads();
-        uint32_t dest = 0;
-        if (act) {
-            uint32_t pre = 0;
-            for (int w = 0; w < warp; ++w) pre += wc[w][dig];
-            dest = run[dig] + pre + (uint32_t)rank;
-        }
-        __syncthreads();
-        if (threadIdx.x < 16) {
-            uint32_t t = 0;
-            for (int w = 0; w < 8; ++w) t += wc[w][threadIdx.x];
-            run[threadIdx.x] += t;
-        }
-        __syncthreads();
-        if (act && !count_only) {
-            kout[dest] = kin[i];
-            aout[dest] = ain[i];
-        }
+    static_assert(NW % 2 == 0, "keys are copied as 16-byte words");
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = perm[i];
+        if (j >= M) j = 0; /* only after a sort wait gave up */
+        const ulonglong2 *s = reinterpret_cast<const ulonglong2 *>(kin + j);
+        ulonglong2 *o = reinterpret_cast<ulonglong2 *>(kout + i);
+#pragma unroll
+        for (int q = 0; q < NW / 2; ++q) o[q] = s[q];
+        aout[i] = ain[j];
     }
-    if (count_only && threadIdx.x < 16) hist[threadIdx.x * gridDim.x + blockIdx.x] = run[threadIdx.x];
 }
 
 /* ---- per-group transforms (the "computing" step) -------------------------------- */
@@ -889,81 +1036,165 @@ cudaError_t qw_flat_scan(const uint32_t *in, int64_t n, uint32_t *sums, uint32_t
     return cudaGetLastError();
 }
 
-size_t qw_flat_sort_words(int64_t M)
+namespace {
+/* work layout of qw_flat_sort, in bytes: the tiles' status words, the
+   digit counts of every chunk, the block counters of every pass, two
+   compacted-key and two permutation arrays */
+struct SortWork {
+    uint64_t *stat;
+    uint32_t *ghist;
+    unsigned int *ctr;
+    unsigned long long *acc;
+    uint64_t *ck[2];
+    uint32_t *ix[2];
+    size_t zero_bytes, total;
+};
+
+constexpr int SORT_MAXPASSES = 64 * NW_FAITH / 8;
+
+size_t align256(size_t b)
 {
-    const int64_t nblk = M < 1 ? 1 : (M + 4095) / 4096 < 1024 ? (M + 4095) / 4096 : 1024;
-    return (size_t)(16 * nblk) * 2 + qw_flat_scan_words(16 * nblk) + 4 * NW_FAITH + 8;
+    return (b + 255) & ~(size_t)255;
 }
 
-namespace {
-/* Stable sort of (keys, amps) by the permuted key of `order` (0: R, 1: H);
- * tmpk/tmpa hold M entries each; the result is left in keys/amps.  Digits
- * equal on every key are skipped (one synchronisation reads them). */
+SortWork sort_work(void *base, int64_t M)
+{
+    const int64_t n = M < 1 ? 1 : M;
+    const int64_t nblk = (n + OS_TILE - 1) / OS_TILE;
+    char *p = static_cast<char *>(base);
+    SortWork w;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *q = p ? p + off : nullptr;
+        off += align256(bytes);
+        return q;
+    };
+    w.stat = reinterpret_cast<uint64_t *>(take((size_t)nblk * 256 * 8));
+    w.ghist = reinterpret_cast<uint32_t *>(take((size_t)NW_FAITH * CK_MAXPASS * 256 * 4));
+    w.ctr = reinterpret_cast<unsigned int *>(take((size_t)SORT_MAXPASSES * 4));
+    w.zero_bytes = off;
+    w.acc = reinterpret_cast<unsigned long long *>(take(2 * NW_FAITH * 8));
+    w.ck[0] = reinterpret_cast<uint64_t *>(take((size_t)n * 8));
+    w.ck[1] = reinterpret_cast<uint64_t *>(take((size_t)n * 8));
+    w.ix[0] = reinterpret_cast<uint32_t *>(take((size_t)n * 4));
+    w.ix[1] = reinterpret_cast<uint32_t *>(take((size_t)n * 4));
+    w.total = off;
+    return w;
+}
+
+/* Stable sort of (keys, amps) by the permuted key of `order` (0: R, 1: H):
+ * one synchronisation reads which bits vary; they are sorted in chunks of
+ * 64, each by 8-bit passes carrying a permutation; the entries are moved
+ * once at the end, into tmpk / tmpa (*in_tmp = 1).  A list whose keys are
+ * all equal is already sorted (*in_tmp = 0). */
 template <int NW>
 cudaError_t flat_sort_t(const QwSimDev &d, void *keys, double2 *amps, void *tmpk, double2 *tmpa, int64_t M, int order,
-                        uint32_t *work, cudaStream_t st)
+                        void *work, int32_t *status, cudaStream_t st, int *in_tmp)
 {
+    *in_tmp = 0;
     if (M <= 1) return cudaSuccess;
+    if (M > (int64_t)UINT32_MAX) return cudaErrorInvalidValue; /* 32-bit positions */
     const int L = d.L;
-    int64_t nblk = (M + 4095) / 4096;
-    if (nblk > 1024) nblk = 1024;
-    int64_t tile = (M + nblk - 1) / nblk;
-    tile = (tile + 255) / 256 * 256;
-    nblk = (M + tile - 1) / tile;
-    uint32_t *hist = work, *offs = work + 16 * nblk, *sums = offs + 16 * nblk;
-    unsigned long long *acc = reinterpret_cast<unsigned long long *>(
-        reinterpret_cast<uintptr_t>(sums + qw_flat_scan_words(16 * nblk) + 3) & ~(uintptr_t)7);
+    const SortWork w = sort_work(work, M);
     unsigned long long init[2 * NW];
     for (int t = 0; t < NW; ++t) {
         init[t] = 0ull;
         init[NW + t] = ~0ull;
     }
-    cudaError_t e = cudaMemcpyAsync(acc, init, sizeof init, cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(w.acc, init, sizeof init, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
-    FKeyN<NW> *ka = static_cast<FKeyN<NW> *>(keys), *kb = static_cast<FKeyN<NW> *>(tmpk);
-    if (order == ORDER_R) k_f_orand<ORDER_R, NW><<<grid_for(M, 256), 256, 0, st>>>(ka, M, L, acc);
-    else k_f_orand<ORDER_H, NW><<<grid_for(M, 256), 256, 0, st>>>(ka, M, L, acc);
+    const int othreads = 32 * NW;
+    const int ogrid = grid_for(M * NW, othreads);
+    const uint64_t *kwords = static_cast<const uint64_t *>(keys);
+    if (order == ORDER_R) k_f_orand<ORDER_R, NW><<<ogrid, othreads, 0, st>>>(kwords, M * NW, L, w.acc);
+    else k_f_orand<ORDER_H, NW><<<ogrid, othreads, 0, st>>>(kwords, M * NW, L, w.acc);
+    if ((e = cudaMemsetAsync(w.stat, 0, w.zero_bytes, st)) != cudaSuccess) return e;
     unsigned long long h[2 * NW];
-    if ((e = cudaMemcpyAsync(h, acc, sizeof h, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(h, w.acc, sizeof h, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-    double2 *aa = amps, *ab = tmpa;
-    for (int shift = 0; shift < 64 * NW; shift += 4) {
-        const uint64_t var = ((h[shift >> 6] ^ h[NW + (shift >> 6)]) >> (shift & 63)) & 15ull;
-        if (!var) continue;
-        if (order == ORDER_R)
-            k_f_radix<ORDER_R, NW><<<(unsigned)nblk, 256, 0, st>>>(ka, aa, kb, ab, M, tile, shift, L, nullptr, hist, 1);
-        else
-            k_f_radix<ORDER_H, NW><<<(unsigned)nblk, 256, 0, st>>>(ka, aa, kb, ab, M, tile, shift, L, nullptr, hist, 1);
-        if ((e = qw_flat_scan(hist, 16 * nblk, sums, offs, st)) != cudaSuccess) return e;
-        if (order == ORDER_R)
-            k_f_radix<ORDER_R, NW><<<(unsigned)nblk, 256, 0, st>>>(ka, aa, kb, ab, M, tile, shift, L, offs, hist, 0);
-        else
-            k_f_radix<ORDER_H, NW><<<(unsigned)nblk, 256, 0, st>>>(ka, aa, kb, ab, M, tile, shift, L, offs, hist, 0);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        FKeyN<NW> *tk = ka;
-        ka = kb;
-        kb = tk;
-        double2 *ta = aa;
-        aa = ab;
-        ab = ta;
+    /* the varying bits as runs, split into chunks of 64 */
+    std::vector<CkRuns> chunks;
+    CkRuns cur{};
+    int cbits = 0;
+    auto flush = [&]() {
+        if (cbits == 0) return;
+        cur.npass = (cbits + 7) / 8;
+        chunks.push_back(cur);
+        cur = CkRuns{};
+        cbits = 0;
+    };
+    for (int wi = 0; wi < NW; ++wi) {
+        const uint64_t var = h[wi] ^ h[NW + wi];
+        int b = 0;
+        while (b < 64) {
+            if (!((var >> b) & 1ull)) {
+                ++b;
+                continue;
+            }
+            int e2 = b;
+            while (e2 < 64 && ((var >> e2) & 1ull) && cbits + (e2 - b) < 64) ++e2;
+            cur.word[cur.n] = (uint8_t)wi;
+            cur.shift[cur.n] = (uint8_t)b;
+            cur.len[cur.n] = (uint8_t)(e2 - b);
+            ++cur.n;
+            cbits += e2 - b;
+            if (cbits == 64) flush();
+            b = e2;
+        }
     }
-    if (ka != static_cast<FKeyN<NW> *>(keys)) {
-        if ((e = cudaMemcpyAsync(keys, ka, (size_t)M * sizeof(FKeyN<NW>), cudaMemcpyDeviceToDevice, st)) !=
-            cudaSuccess)
-            return e;
-        if ((e = cudaMemcpyAsync(amps, aa, (size_t)M * sizeof(double2), cudaMemcpyDeviceToDevice, st)) !=
-            cudaSuccess)
-            return e;
+    flush();
+    if (chunks.empty()) return cudaSuccess;
+    const int64_t nblk = (M + OS_TILE - 1) / OS_TILE;
+    const int kgrid = grid_for(M, 256);
+    const FKeyN<NW> *kin = static_cast<const FKeyN<NW> *>(keys);
+    int curix = -1, curck = 0;
+    uint64_t tag = 0;
+    for (size_t c = 0; c < chunks.size(); ++c) {
+        const CkRuns &r = chunks[c];
+        uint32_t *gh = w.ghist + c * CK_MAXPASS * 256;
+        const uint32_t *perm = curix < 0 ? nullptr : w.ix[curix];
+        if (order == ORDER_R) k_f_ckey<ORDER_R, NW><<<kgrid, 256, 0, st>>>(kin, perm, M, L, r, w.ck[curck], gh);
+        else k_f_ckey<ORDER_H, NW><<<kgrid, 256, 0, st>>>(kin, perm, M, L, r, w.ck[curck], gh);
+        for (int p = 0; p < r.npass; ++p) {
+            ++tag;
+            const bool wck = p + 1 < r.npass;
+            const int outix = curix == 0 ? 1 : 0;
+            const uint64_t *ci = w.ck[curck];
+            uint64_t *co = w.ck[curck ^ 1];
+            uint32_t *xo = w.ix[outix];
+            unsigned int *ctr = w.ctr + (tag - 1);
+            const uint32_t *ghp = gh + p * 256;
+            const unsigned grid = (unsigned)nblk;
+            if (curix < 0) {
+                if (wck) k_f_onesweep<true, true><<<grid, OS_THREADS, 0, st>>>(ci, nullptr, co, xo, M, 8 * p, ghp, w.stat, tag, ctr, status);
+                else k_f_onesweep<true, false><<<grid, OS_THREADS, 0, st>>>(ci, nullptr, co, xo, M, 8 * p, ghp, w.stat, tag, ctr, status);
+            } else {
+                const uint32_t *xi = w.ix[curix];
+                if (wck) k_f_onesweep<false, true><<<grid, OS_THREADS, 0, st>>>(ci, xi, co, xo, M, 8 * p, ghp, w.stat, tag, ctr, status);
+                else k_f_onesweep<false, false><<<grid, OS_THREADS, 0, st>>>(ci, xi, co, xo, M, 8 * p, ghp, w.stat, tag, ctr, status);
+            }
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            curix = outix;
+            if (wck) curck ^= 1;
+        }
     }
+    k_f_permute<NW><<<kgrid, 256, 0, st>>>(kin, amps, w.ix[curix], static_cast<FKeyN<NW> *>(tmpk), tmpa, M);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    *in_tmp = 1;
     return cudaSuccess;
 }
 } // namespace
 
-cudaError_t qw_flat_sort(const QwSimDev &d, void *keys, double2 *amps, void *tmpk, double2 *tmpa, int64_t M,
-                         int order, uint32_t *work, cudaStream_t st, int kw)
+size_t qw_flat_sort_bytes(int64_t M)
 {
-    if (kw == NW_FAITH) return flat_sort_t<NW_FAITH>(d, keys, amps, tmpk, tmpa, M, order, work, st);
-    return flat_sort_t<2>(d, keys, amps, tmpk, tmpa, M, order, work, st);
+    return sort_work(nullptr, M).total;
+}
+
+cudaError_t qw_flat_sort(const QwSimDev &d, void *keys, double2 *amps, void *tmpk, double2 *tmpa, int64_t M,
+                         int order, void *work, int32_t *status, cudaStream_t st, int kw, int *in_tmp)
+{
+    if (kw == NW_FAITH) return flat_sort_t<NW_FAITH>(d, keys, amps, tmpk, tmpa, M, order, work, status, st, in_tmp);
+    return flat_sort_t<2>(d, keys, amps, tmpk, tmpa, M, order, work, status, st, in_tmp);
 }
 
 /* op: 0 = R^dag, 1 = R (2 outputs per entry), 2 = H (s outputs per entry) */

@@ -39,6 +39,7 @@
 #define QW_ST_NOT_BTILDE 16    /* T~ at initialisation met a row that was not |b~> */
 #define QW_ST_OUTBOX_FULL 32   /* a partition's outbox toward another overflowed */
 #define QW_ST_POS_UNREP 64     /* a branch the positional layout has no position for */
+#define QW_ST_SORT_WAIT 128    /* the flat path's radix sort gave up waiting for a tile's count */
 
 /* A branch sent by S to a row another partition owns: its row key
    (qw_rowkey), its local registers (R layout) and its amplitude in FP64. */
@@ -224,9 +225,11 @@ cudaError_t qw_flat_map(const QwSimDev &d, void *keys, int64_t M, uint32_t ops, 
 cudaError_t qw_flat_phase(const QwSimDev &d, const void *keys, double2 *amps, int64_t M, cudaStream_t st, int kw);
 size_t qw_flat_scan_words(int64_t n);
 cudaError_t qw_flat_scan(const uint32_t *in, int64_t n, uint32_t *sums, uint32_t *out, cudaStream_t st);
-size_t qw_flat_sort_words(int64_t M);
+/* stable sort by the permuted key (order 0: R, 1: H); work holds
+   qw_flat_sort_bytes(M); the result is left in tmpk / tmpa when *in_tmp */
+size_t qw_flat_sort_bytes(int64_t M);
 cudaError_t qw_flat_sort(const QwSimDev &d, void *keys, double2 *amps, void *tmpk, double2 *tmpa, int64_t M,
-                         int order, uint32_t *work, cudaStream_t st, int kw);
+                         int order, void *work, int32_t *status, cudaStream_t st, int kw, int *in_tmp);
 /* the Hadamard stage's groups: head flags of the sorted list, and the first
    member of each of its G groups (starts[G] = M) from their exclusive scan */
 cudaError_t qw_flat_heads(const QwSimDev &d, const void *keys, int64_t M, uint32_t *flags, cudaStream_t st, int kw);
