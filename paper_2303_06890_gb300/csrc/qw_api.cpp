@@ -84,6 +84,7 @@ struct qw_sim {
     qw_sim_opts opts;
     cudaStream_t stream = nullptr;
     int device = 0;                  /* CUDA device current at creation */
+    cudaMemPool_t fpool = nullptr;   /* flat-path scratch (flat_alloc) */
     int fp32 = 0;
     int renorm = 0;
     int mode = QW_MODE_WALK_FUSED;
@@ -609,12 +610,13 @@ extern "C" int qw_sim_create(const qw_csc *mats, int32_t ninst, const qw_sim_opt
 extern "C" int qw_sim_destroy(qw_sim *sim)
 {
     if (!sim) return QW_OK;
+    if (sim->fq_open) {
+        cudaFreeAsync(sim->fq.K, sim->stream);
+        cudaFreeAsync(sim->fq.A, sim->stream);
+    }
     if (sim->stream) cudaStreamSynchronize(sim->stream);
     else cudaDeviceSynchronize();
-    if (sim->fq_open) {
-        cudaFree(sim->fq.K);
-        cudaFree(sim->fq.A);
-    }
+    if (sim->fpool) cudaMemPoolDestroy(sim->fpool);
     cudaFree(sim->pos_tp);
     cudaFree(sim->pos_xin);
     cudaFree(sim->pos_xcnt);
@@ -816,10 +818,28 @@ static int grow_rows(qw_sim *sim, int64_t need)
     return QW_OK;
 }
 
+/* Stream-ordered scratch of the flat path and the register-faithful
+ * sessions, from a pool of the simulator's own that keeps what was freed
+ * (release threshold: no limit), so that a stage's allocations after a
+ * synchronisation reuse memory instead of mapping it again; the pool and
+ * its memory go with qw_sim_destroy. */
 static cudaError_t flat_alloc(qw_sim *sim, size_t bytes, void **p)
 {
     *p = nullptr;
-    return cudaMallocAsync(p, bytes < 16 ? 16 : bytes, sim->stream);
+    if (!sim->fpool) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = sim->device;
+        cudaError_t e = cudaMemPoolCreate(&sim->fpool, &props);
+        if (e != cudaSuccess) {
+            sim->fpool = nullptr;
+            return e;
+        }
+        uint64_t keep = UINT64_MAX;
+        if ((e = cudaMemPoolSetAttribute(sim->fpool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) return e;
+    }
+    return cudaMallocFromPoolAsync(p, bytes < 16 ? 16 : bytes, sim->fpool, sim->stream);
 }
 
 static void flat_release(qw_sim *sim, FlatList &L)
@@ -860,7 +880,6 @@ static cudaError_t flat_stage(qw_sim *sim, FlatList &L, int op)
     cudaStream_t st = sim->stream;
     cudaError_t e = cudaSuccess;
     const size_t kb = 8 * (size_t)L.kw;
-    const int outs = op == 2 ? d.s : 2;
     void *tk = nullptr, *ta = nullptr, *work = nullptr;
     if (L.M > 1) {
         if ((e = flat_alloc(sim, (size_t)L.M * kb, &tk)) != cudaSuccess) return e;
@@ -881,8 +900,8 @@ static cudaError_t flat_stage(qw_sim *sim, FlatList &L, int op)
         cudaFreeAsync(work, st);
         if (e != cudaSuccess) return e;
     }
-    /* H: s outputs per group of the sorted list -- count the groups first
-       (head flags and their scan; the host reads the count) */
+    /* H: the groups of the sorted list counted first (head flags and their
+       scan; the host reads the count) */
     int64_t G = 0;
     int64_t *starts = nullptr;
     if (op == 2 && L.M > 0) {
@@ -907,16 +926,48 @@ static cudaError_t flat_stage(qw_sim *sim, FlatList &L, int op)
             if (p) cudaFreeAsync(p, st);
         if (e != cudaSuccess) return e;
     }
-    const int64_t n = op == 2 ? G * outs : L.M * outs;
+    FlatList R;
+    R.kw = L.kw;
+    uint32_t total = 0;
+    if (op == 2) {
+        /* H: the kept outputs of each group counted, scanned, then written */
+        void *cnt = nullptr, *gpos = nullptr, *sums = nullptr;
+        if (G > 0) {
+            if (e == cudaSuccess) e = flat_alloc(sim, (size_t)G * 4, &cnt);
+            if (e == cudaSuccess) e = flat_alloc(sim, (size_t)G * 4, &gpos);
+            if (e == cudaSuccess) e = flat_alloc(sim, qw_flat_scan_words(G) * 4, &sums);
+            if (e == cudaSuccess)
+                e = qw_flat_hgroups(d, L.K, L.A, starts, G, static_cast<uint32_t *>(cnt), nullptr, nullptr, nullptr, st,
+                                    L.kw);
+            if (e == cudaSuccess)
+                e = qw_flat_scan(static_cast<uint32_t *>(cnt), G, static_cast<uint32_t *>(sums),
+                                 static_cast<uint32_t *>(gpos), st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&total, static_cast<uint32_t *>(sums) + (G + 1023) / 1024, 4,
+                                    cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        }
+        R.M = (int64_t)total;
+        if (e == cudaSuccess) e = flat_alloc(sim, (size_t)R.M * kb, &R.K);
+        if (e == cudaSuccess) e = flat_alloc(sim, (size_t)R.M * 16, (void **)&R.A);
+        if (e == cudaSuccess && total > 0)
+            e = qw_flat_hgroups(d, L.K, L.A, starts, G, static_cast<uint32_t *>(cnt), static_cast<uint32_t *>(gpos),
+                                R.K, R.A, st, L.kw);
+        for (void *p : {cnt, gpos, sums, (void *)starts})
+            if (p) cudaFreeAsync(p, st);
+        flat_release(sim, L);
+        L = R;
+        return e;
+    }
+    const int64_t n = L.M * 2;
     void *ok = nullptr, *oa = nullptr, *flags = nullptr, *pos = nullptr, *sums = nullptr;
     if ((e = flat_alloc(sim, (size_t)n * kb, &ok)) != cudaSuccess) return e;
     if ((e = flat_alloc(sim, (size_t)n * 16, &oa)) != cudaSuccess) return e;
     if ((e = flat_alloc(sim, (size_t)n * 4, &flags)) != cudaSuccess) return e;
     if ((e = flat_alloc(sim, (size_t)n * 4, &pos)) != cudaSuccess) return e;
     if ((e = flat_alloc(sim, qw_flat_scan_words(n) * 4, &sums)) != cudaSuccess) return e;
-    uint32_t total = 0;
     e = qw_flat_group(d, op, L.K, L.A, L.M, ok, static_cast<double2 *>(oa), static_cast<uint32_t *>(flags), st,
-                      L.kw, starts, G);
+                      L.kw);
     if (e == cudaSuccess && n > 0) {
         e = qw_flat_scan(static_cast<uint32_t *>(flags), n, static_cast<uint32_t *>(sums), static_cast<uint32_t *>(pos),
                          st);
@@ -925,15 +976,13 @@ static cudaError_t flat_stage(qw_sim *sim, FlatList &L, int op)
             e = cudaMemcpyAsync(&total, static_cast<uint32_t *>(sums) + nb, 4, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
-    FlatList R;
-    R.kw = L.kw;
     R.M = (int64_t)total;
     if (e == cudaSuccess) e = flat_alloc(sim, (size_t)R.M * kb, &R.K);
     if (e == cudaSuccess) e = flat_alloc(sim, (size_t)R.M * 16, (void **)&R.A);
     if (e == cudaSuccess)
         e = qw_flat_compact(ok, static_cast<double2 *>(oa), static_cast<uint32_t *>(flags),
                             static_cast<uint32_t *>(pos), n, R.K, R.A, st, L.kw);
-    for (void *p : {ok, oa, flags, pos, sums, (void *)starts})
+    for (void *p : {ok, oa, flags, pos, sums})
         if (p) cudaFreeAsync(p, st);
     flat_release(sim, L);
     L = R;

@@ -857,29 +857,85 @@ __global__ void k_f_starts(const uint32_t *heads, const uint32_t *gidx, int64_t 
  * bits of k, contiguous after the sort): one thread per (group, u), the
  * group's members read in list order, so each output is the same sum as a
  * dense s x s product on the zero-filled vector. */
-template <int NW>
-__global__ void k_f_hadamard(QwSimDev d, const FKeyN<NW> *keys, const double2 *amps, const int64_t *starts, int64_t G,
-                             FKeyN<NW> *okeys, double2 *oamps, uint32_t *flags)
+/* H on each group's zero-filled vector of 2^L = s entries (the groups of
+ * the list sorted in ORDER_H, starts[g] .. starts[g + 1]): output u of a group
+ * is s^-1/2 sum_m (-1)^{|u & v_m|} a_m over its members m (v_m: their low L
+ * bits of k).  A warp runs 32 / s groups (s <= 32: lane u of a group holds
+ * entry u of the zero-filled vector, and the L butterfly stages of the fast
+ * Walsh-Hadamard transform (Sylvester order, (x, y) -> (x + y, x - y) on
+ * index bit h) run over shuffles: s L additions per group instead of s^2;
+ * the FP64 pipe is the limit) or one group in s / 32 rounds of 32 outputs,
+ * each the direct sum over the members in list order (a lane loads one
+ * member per round and the warp's shuffles hand them to every output).
+ * COUNT: the kept outputs of each group into cnt[g]; otherwise the kept
+ * outputs are written, in order of u, from gpos[g] (the exclusive scan of
+ * cnt) -- the clearing step without a list of all G s outputs. */
+template <int NW, bool COUNT>
+__global__ void __launch_bounds__(256) k_f_hgroups(QwSimDev d, const FKeyN<NW> *keys, const double2 *amps,
+                                                   const int64_t *starts, int64_t G, uint32_t *cnt,
+                                                   const uint32_t *gpos, FKeyN<NW> *okeys, double2 *oamps)
 {
     const int s = d.s;
-    const uint64_t lowm = (((uint64_t)s - 1ull) << 1);
-    const int64_t n = G * s;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t g = t / s;
-        const int u = (int)(t - g * s);
-        const int64_t b = starts[g], e = starts[g + 1];
-        double2 o = make_double2(0, 0);
-        for (int64_t m = b; m < e; ++m) {
-            const uint32_t v = (uint32_t)((keys[m].w[0] >> 1) & (uint64_t)(s - 1));
-            const double2 a = amps[m];
-            o = (__popc((uint32_t)u & v) & 1) ? csub(o, a) : cadd(o, a);
+    const int sw = s < 32 ? s : 32, gpw = 32 / sw, rounds = s / sw;
+    const int lane = threadIdx.x & 31, sub = lane / sw, ul = lane - sub * sw, first = sub * sw;
+    const unsigned seg = sw == 32 ? FULL : ((1u << sw) - 1u) << first;
+    const unsigned below = (1u << lane) - 1u;
+    const uint64_t lowm = ((uint64_t)s - 1ull) << 1;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    __shared__ double2 zv[8][32];
+    double2 *vec = zv[threadIdx.x >> 5];
+    for (int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wg * gpw < G; wg += nwarps) {
+        const int64_t g = wg * gpw + sub;
+        const bool act = g < G;
+        const int64_t b = act ? starts[g] : 0, nm = act ? starts[g + 1] - b : 0;
+        uint32_t run = 0u;
+        for (int q = 0; q < rounds; ++q) {
+            const uint32_t u = (uint32_t)(q * sw + ul);
+            double2 o = make_double2(0, 0);
+            if (s <= 32) { /* the group's zero-filled vector over its lanes, then the butterflies */
+                vec[lane] = make_double2(0, 0);
+                __syncwarp();
+                if (ul < nm) vec[first + (int)((keys[b + ul].w[0] >> 1) & (uint64_t)(s - 1))] = amps[b + ul];
+                __syncwarp();
+                o = vec[lane];
+                __syncwarp();
+                for (int h = 1; h < sw; h <<= 1) {
+                    const double yx = __shfl_xor_sync(FULL, o.x, h), yy = __shfl_xor_sync(FULL, o.y, h);
+                    o = (ul & h) ? make_double2(yx - o.x, yy - o.y) : make_double2(o.x + yx, o.y + yy);
+                }
+            }
+            for (int q2 = 0; q2 < rounds && s > 32; ++q2) {
+                const int64_t mi = (int64_t)q2 * sw + ul;
+                uint32_t mv = 0u;
+                double2 ma = make_double2(0, 0);
+                if (mi < nm) {
+                    mv = (uint32_t)((keys[b + mi].w[0] >> 1) & (uint64_t)(s - 1));
+                    ma = amps[b + mi];
+                }
+                for (int j = 0; j < sw; ++j) {
+                    const uint32_t v = __shfl_sync(FULL, mv, first + j);
+                    const double ax = __shfl_sync(FULL, ma.x, first + j);
+                    const double ay = __shfl_sync(FULL, ma.y, first + j);
+                    if ((int64_t)q2 * sw + j < nm) {
+                        const double2 a = make_double2(ax, ay);
+                        o = (__popc(u & v) & 1) ? csub(o, a) : cadd(o, a);
+                    }
+                }
+            }
+            o = cscale(d.inv_sqrt_s, o);
+            const bool kept = act && keep(o, d.tau2);
+            const unsigned bal = __ballot_sync(FULL, kept) & seg;
+            const uint32_t rank = run + (uint32_t)__popc(bal & below);
+            if (!COUNT && kept && rank < cnt[g]) { /* the count pass made the same decisions */
+                const int64_t dst = (int64_t)gpos[g] + rank;
+                FKeyN<NW> ko = keys[b];
+                ko.w[0] = (ko.w[0] & ~lowm) | ((uint64_t)u << 1);
+                okeys[dst] = ko;
+                oamps[dst] = o;
+            }
+            run += (uint32_t)__popc(bal);
         }
-        o = cscale(d.inv_sqrt_s, o);
-        FKeyN<NW> ko = keys[b];
-        ko.w[0] = (ko.w[0] & ~lowm) | ((uint64_t)u << 1);
-        okeys[t] = ko;
-        oamps[t] = o;
-        flags[t] = keep(o, d.tau2) ? 1u : 0u;
+        if (COUNT && act && ul == 0) cnt[g] = run;
     }
 }
 
@@ -1216,23 +1272,40 @@ cudaError_t qw_flat_starts(const uint32_t *heads, const uint32_t *gidx, int64_t 
 }
 
 cudaError_t qw_flat_group(const QwSimDev &d, int op, const void *keys, const double2 *amps, int64_t M, void *okeys,
-                          double2 *oamps, uint32_t *flags, cudaStream_t st, int kw, const int64_t *starts, int64_t G)
+                          double2 *oamps, uint32_t *flags, cudaStream_t st, int kw)
 {
     if (M <= 0) return cudaSuccess;
-    const int64_t nh = G * d.s;
     if (kw == NW_FAITH) {
         const FKeyW *k = static_cast<const FKeyW *>(keys);
         FKeyW *ok = static_cast<FKeyW *>(okeys);
         if (op == 0) k_f_rot<true, NW_FAITH><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
-        else if (op == 1) k_f_rot<false, NW_FAITH><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
-        else if (nh > 0)
-            k_f_hadamard<NW_FAITH><<<grid_for(nh, 128), 128, 0, st>>>(d, k, amps, starts, G, ok, oamps, flags);
+        else k_f_rot<false, NW_FAITH><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
     } else {
         const FKey *k = static_cast<const FKey *>(keys);
         FKey *ok = static_cast<FKey *>(okeys);
         if (op == 0) k_f_rot<true, 2><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
-        else if (op == 1) k_f_rot<false, 2><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
-        else if (nh > 0) k_f_hadamard<2><<<grid_for(nh, 128), 128, 0, st>>>(d, k, amps, starts, G, ok, oamps, flags);
+        else k_f_rot<false, 2><<<grid_for(M, 256), 256, 0, st>>>(d, k, amps, M, ok, oamps, flags);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t qw_flat_hgroups(const QwSimDev &d, const void *keys, const double2 *amps, const int64_t *starts, int64_t G,
+                            uint32_t *cnt, const uint32_t *gpos, void *okeys, double2 *oamps, cudaStream_t st, int kw)
+{
+    if (G <= 0) return cudaSuccess;
+    const int gpw = d.s < 32 ? 32 / d.s : 1;
+    const int grid = grid_for((G + gpw - 1) / gpw * 32, 256);
+    const bool count = gpos == nullptr;
+    if (kw == NW_FAITH) {
+        const FKeyW *k = static_cast<const FKeyW *>(keys);
+        if (count) k_f_hgroups<NW_FAITH, true><<<grid, 256, 0, st>>>(d, k, amps, starts, G, cnt, nullptr, nullptr, nullptr);
+        else
+            k_f_hgroups<NW_FAITH, false><<<grid, 256, 0, st>>>(d, k, amps, starts, G, cnt, gpos,
+                                                                static_cast<FKeyW *>(okeys), oamps);
+    } else {
+        const FKey *k = static_cast<const FKey *>(keys);
+        if (count) k_f_hgroups<2, true><<<grid, 256, 0, st>>>(d, k, amps, starts, G, cnt, nullptr, nullptr, nullptr);
+        else k_f_hgroups<2, false><<<grid, 256, 0, st>>>(d, k, amps, starts, G, cnt, gpos, static_cast<FKey *>(okeys), oamps);
     }
     return cudaGetLastError();
 }

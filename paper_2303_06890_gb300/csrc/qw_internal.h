@@ -235,10 +235,13 @@ cudaError_t qw_flat_sort(const QwSimDev &d, void *keys, double2 *amps, void *tmp
 cudaError_t qw_flat_heads(const QwSimDev &d, const void *keys, int64_t M, uint32_t *flags, cudaStream_t st, int kw);
 cudaError_t qw_flat_starts(const uint32_t *heads, const uint32_t *gidx, int64_t M, int64_t G, int64_t *starts,
                            cudaStream_t st);
-/* op 0 (R^dag) and 1 (R): 2 M outputs; op 2 (H): s outputs per group (starts, G) */
+/* op 0 (R^dag) and 1 (R): 2 M outputs with their keep flags */
 cudaError_t qw_flat_group(const QwSimDev &d, int op, const void *keys, const double2 *amps, int64_t M, void *okeys,
-                          double2 *oamps, uint32_t *flags, cudaStream_t st, int kw, const int64_t *starts = nullptr,
-                          int64_t G = 0);
+                          double2 *oamps, uint32_t *flags, cudaStream_t st, int kw);
+/* H on the G groups (starts): gpos == nullptr -- the kept outputs of each
+   group into cnt; otherwise the kept outputs written from gpos[g] on */
+cudaError_t qw_flat_hgroups(const QwSimDev &d, const void *keys, const double2 *amps, const int64_t *starts, int64_t G,
+                            uint32_t *cnt, const uint32_t *gpos, void *okeys, double2 *oamps, cudaStream_t st, int kw);
 cudaError_t qw_flat_compact(const void *keys, const double2 *amps, const uint32_t *flags, const uint32_t *pos,
                             int64_t n, void *okeys, double2 *oamps, cudaStream_t st, int kw);
 cudaError_t qw_flat_readout(const QwSimDev &d, const void *keys, const double2 *amps, int64_t M, const QwStepArgs &a,
