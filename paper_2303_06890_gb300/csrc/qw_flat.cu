@@ -413,6 +413,47 @@ __global__ void k_fq(QwSimDev d, FKeyW *keys, int64_t M, int op, FaithLayout F, 
     }
 }
 
+/* The sub-operations that touch only the base registers and the address
+ * register (ADDR_COL, QRAM_COL, SWAP, ADDR_VAL, QRAM_VAL), as k_fq runs them,
+ * reading words 0..2 of the 80-byte key (the address lies at bits 128 ..
+ * 128 + aw - 1, in word 2 for aw <= 64) and writing back only the words the
+ * operation changes: the address word, or the base registers' two. */
+__global__ void k_fq_light(QwSimDev d, FKeyW *keys, int64_t M, int op, int aw)
+{
+    const FLayout L = flayout(d.nb);
+    const uint64_t ns = (uint64_t)d.n_single * (uint64_t)d.s;
+    const uint64_t am = aw >= 64 ? ~0ull : (1ull << aw) - 1ull;
+    const bool addr_op = op == FQ_ADDR_COL || op == FQ_ADDR_VAL;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        ulonglong2 *base = reinterpret_cast<ulonglong2 *>(keys + i);
+        uint64_t *w2p = keys[i].w + 2;
+        const ulonglong2 b01 = *base;
+        FKey b;
+        b.w[0] = b01.x;
+        b.w[1] = b01.y;
+        FRegs f = fdecode(b, L);
+        const uint64_t w2 = op == FQ_SWAP ? 0ull : *w2p;
+        uint64_t addr = w2 & am;
+        if (addr_op) {
+            if (op == FQ_ADDR_COL) addr ^= ns + (uint64_t)f.j * (uint64_t)d.s + f.x.k;
+            else if (f.jc == 0 && f.x.kc == 0) addr ^= (uint64_t)f.j * (uint64_t)d.s + f.x.k;
+            *w2p = (w2 & ~am) | (addr & am);
+            continue;
+        }
+        if (op == FQ_QRAM_COL) {
+            f.x.kc ^= (uint32_t)fq_qram(d, addr, true);
+        } else if (op == FQ_QRAM_VAL) {
+            if (f.jc == 0 && f.x.kc == 0) f.x.A ^= (uint32_t)fq_qram(d, addr, false);
+        } else {
+            const uint32_t t = f.x.k;
+            f.x.k = f.x.kc;
+            f.x.kc = t;
+        }
+        frewrite(b, f, L);
+        *base = make_ulonglong2(b.w[0], b.w[1]);
+    }
+}
+
 /* the working registers must be 0 (an interference op, P, S or the store) */
 __global__ void k_fq_check_idle(const FKeyW *keys, int64_t M, int from_bit, int32_t *status)
 {
@@ -1393,7 +1434,12 @@ int qw_faithful_layout(const QwSimDev &d, int *addr_bits, int *layout_bits)
 cudaError_t qw_faithful_op(const QwSimDev &d, void *keys, int64_t M, int op, int32_t *status, cudaStream_t st)
 {
     if (M <= 0) return cudaSuccess;
-    k_fq<<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<FKeyW *>(keys), M, op, faith_layout(d), status);
+    const FaithLayout F = faith_layout(d);
+    const bool light = op == FQ_ADDR_COL || op == FQ_QRAM_COL || op == FQ_SWAP || op == FQ_ADDR_VAL ||
+                       op == FQ_QRAM_VAL;
+    if (light && F.p_addr == 128 && F.aw <= 64)
+        k_fq_light<<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<FKeyW *>(keys), M, op, F.aw);
+    else k_fq<<<grid_for(M, 256), 256, 0, st>>>(d, static_cast<FKeyW *>(keys), M, op, F, status);
     return cudaGetLastError();
 }
 

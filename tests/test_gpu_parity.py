@@ -753,6 +753,37 @@ def test_flat_path_on_garbage_states_and_qls():
     assert np.abs(y - y2).max() < 1e-12 and np.abs(p - p2).max() < 1e-12
 
 
+@pytest.mark.parametrize("variant", [5, 6])
+def test_flat_sort_spans_two_key_chunks(variant):
+    """A random state whose branches differ in 66 register bits (nb = 16:
+    jc, j, kc, k over their whole ranges, b1, b2): the flat path's radix sort
+    takes the varying bits in two 64-bit chunks (the second formed in the
+    order the first left); three steps on the flat path and on the
+    register-faithful schedule equal the oracle's."""
+    w = wl.small_random(40000, 4, 29)
+    rng = np.random.default_rng(7)
+    sim = _sim(w, walk_variant=variant, spill_rows=1024)
+    nb = sim.nb
+    assert 4 * nb + 2 > 64
+    keys = set()
+    while len(keys) < 300:
+        keys.add((int(rng.integers(0, 1 << nb)), int(rng.integers(0, 1 << nb)), int(rng.integers(0, 2)),
+                  int(rng.integers(0, 1 << nb)), int(rng.integers(0, 1 << nb)), int(rng.integers(0, 2))))
+    regs = np.array(sorted(keys), dtype=np.uint64)
+    amps = rng.standard_normal(len(regs)) + 1j * rng.standard_normal(len(regs))
+    amps /= np.linalg.norm(amps)
+    full = np.zeros((len(regs), 8), dtype=np.uint64)
+    full[:, :6] = regs
+    sim.state_import(sim.pack(full), amps)
+    o = oracle.Oracle(w.matrix, w.s)
+    o.set_state(regs, amps)
+    for _ in range(3):
+        sim.apply_walk_step(1)
+        o.apply("W")
+        compare(gpu_state(sim), oracle_state(o), TOL64)
+    sim.close()
+
+
 def test_import_grows_row_capacity():
     """qw_state_import of a state whose rows exceed row_capacity grows the
     buckets (overflow_fallback) and the walk continues equal to the oracle."""
