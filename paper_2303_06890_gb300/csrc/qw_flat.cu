@@ -56,12 +56,23 @@ __host__ __device__ inline FLayout flayout(int nb)
     return f;
 }
 
+/* word i of a key by selection over its words, so that the key stays in
+   registers whatever i is (an indexed access moves it to local memory) */
+template <int NW>
+__device__ __forceinline__ uint64_t fword(const FKeyN<NW> &k, int i)
+{
+    uint64_t v = k.w[0];
+#pragma unroll
+    for (int t = 1; t < NW; ++t) v = t == i ? k.w[t] : v;
+    return v;
+}
+
 template <int NW>
 __device__ __forceinline__ uint64_t fget(const FKeyN<NW> &k, int pos, int w)
 {
     const int i = pos >> 6, o = pos & 63;
-    uint64_t v = k.w[i] >> o;
-    if (o + w > 64 && i + 1 < NW) v |= k.w[i + 1] << (64 - o);
+    uint64_t v = fword(k, i) >> o;
+    if (o + w > 64 && i + 1 < NW) v |= fword(k, i + 1) << (64 - o);
     return v & (w >= 64 ? ~0ull : ((1ull << w) - 1ull));
 }
 
@@ -71,8 +82,11 @@ __device__ __forceinline__ void fput(FKeyN<NW> &k, int pos, int w, uint64_t v)
 {
     v &= (w >= 64 ? ~0ull : ((1ull << w) - 1ull));
     const int i = pos >> 6, o = pos & 63;
-    k.w[i] |= v << o;
-    if (o + w > 64 && i + 1 < NW) k.w[i + 1] |= v >> (64 - o);
+#pragma unroll
+    for (int t = 0; t < NW; ++t) {
+        if (t == i) k.w[t] |= v << o;
+        if (t == i + 1 && o + w > 64) k.w[t] |= v >> (64 - o);
+    }
 }
 
 template <int NW>
@@ -80,8 +94,11 @@ __device__ __forceinline__ void fclear(FKeyN<NW> &k, int pos, int w)
 {
     const uint64_t m = (w >= 64 ? ~0ull : ((1ull << w) - 1ull));
     const int i = pos >> 6, o = pos & 63;
-    k.w[i] &= ~(m << o);
-    if (o + w > 64 && i + 1 < NW) k.w[i + 1] &= ~(m >> (64 - o));
+#pragma unroll
+    for (int t = 0; t < NW; ++t) {
+        if (t == i) k.w[t] &= ~(m << o);
+        if (t == i + 1 && o + w > 64) k.w[t] &= ~(m >> (64 - o));
+    }
 }
 
 struct FRegs {
@@ -89,9 +106,32 @@ struct FRegs {
     Regs x; /* k, kc, A, b2 */
 };
 
+/* the base registers (4 nb + 34 bits) lie in words 0 and 1 of any key
+   width: they are decoded from and encoded into those two words */
 template <int NW>
-__device__ __forceinline__ FRegs fdecode(const FKeyN<NW> &k, const FLayout &L)
+__device__ __forceinline__ FKeyN<2> fbase(const FKeyN<NW> &k)
 {
+    FKeyN<2> b;
+    b.w[0] = k.w[0];
+    b.w[1] = k.w[1];
+    return b;
+}
+
+/* words 0 and 1 of a key in global memory, as one 16-byte load */
+template <int NW>
+__device__ __forceinline__ FKeyN<2> fbase_load(const FKeyN<NW> *k)
+{
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(k);
+    FKeyN<2> b;
+    b.w[0] = v.x;
+    b.w[1] = v.y;
+    return b;
+}
+
+template <int NW>
+__device__ __forceinline__ FRegs fdecode(const FKeyN<NW> &key, const FLayout &L)
+{
+    const FKeyN<2> k = fbase(key);
     FRegs r;
     r.x.b2 = fget(k, 0, 1);
     r.x.k = fget(k, L.pk, L.nb);
@@ -106,8 +146,9 @@ __device__ __forceinline__ FRegs fdecode(const FKeyN<NW> &k, const FLayout &L)
 
 /* the base registers into k (their fields must be 0) */
 template <int NW>
-__device__ __forceinline__ void fencode_into(FKeyN<NW> &k, const FRegs &r, const FLayout &L)
+__device__ __forceinline__ void fencode_into(FKeyN<NW> &key, const FRegs &r, const FLayout &L)
 {
+    FKeyN<2> k = fbase(key);
     fput(k, 0, 1, r.x.b2);
     fput(k, L.pk, L.nb, r.x.k);
     fput(k, L.pkc, L.nb, r.x.kc);
@@ -116,6 +157,8 @@ __device__ __forceinline__ void fencode_into(FKeyN<NW> &k, const FRegs &r, const
     fput(k, L.pjc, L.nb, r.jc);
     fput(k, L.pA, 16, r.x.A);
     fput(k, L.pinst, 16, r.inst);
+    key.w[0] = k.w[0];
+    key.w[1] = k.w[1];
 }
 
 __device__ __forceinline__ FKey fencode(const FRegs &r, const FLayout &L)
@@ -131,10 +174,8 @@ template <int NW>
 __device__ __forceinline__ void frewrite(FKeyN<NW> &k, const FRegs &r, const FLayout &L)
 {
     const int bits = L.pinst + 16;
-    for (int i = 0; i < NW && i * 64 < bits; ++i) {
-        const int hi = bits - i * 64;
-        k.w[i] &= hi >= 64 ? 0ull : ~((1ull << hi) - 1ull);
-    }
+    k.w[0] &= bits >= 64 ? 0ull : ~((1ull << bits) - 1ull);
+    if (bits > 64) k.w[1] &= bits >= 128 ? 0ull : ~((1ull << (bits - 64)) - 1ull);
     fencode_into(k, r, L);
 }
 
@@ -226,7 +267,13 @@ __global__ void k_f_map(QwSimDev d, FKeyN<NW> *keys, int64_t M, uint32_t ops, in
 {
     const FLayout L = flayout(d.nb);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        FKeyN<NW> k = keys[i];
+        /* the base registers are words 0 and 1 of any key width: only they
+           are read and written */
+        ulonglong2 *base = reinterpret_cast<ulonglong2 *>(keys + i);
+        const ulonglong2 b01 = *base;
+        FKey k;
+        k.w[0] = b01.x;
+        k.w[1] = b01.y;
         FRegs f = fdecode(k, L);
         for (uint32_t o = ops; o != 0; o >>= 4) {
             const uint32_t op = o & 15u;
@@ -247,7 +294,7 @@ __global__ void k_f_map(QwSimDev d, FKeyN<NW> *keys, int64_t M, uint32_t ops, in
             }
         }
         frewrite(k, f, L);
-        keys[i] = k;
+        *base = make_ulonglong2(k.w[0], k.w[1]);
     }
 }
 
@@ -257,7 +304,7 @@ __global__ void k_f_phase(QwSimDev d, const FKeyN<NW> *keys, double2 *amps, int6
 {
     const FLayout L = flayout(d.nb);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        const FRegs f = fdecode(keys[i], L);
+        const FRegs f = fdecode(fbase_load(keys + i), L);
         const bool zero = f.b1 == 0 && f.x.k == 0 && f.x.b2 == 0 && f.jc == 0 && f.x.kc == 0;
         if (!zero) amps[i] = cneg(amps[i]);
     }
@@ -281,6 +328,32 @@ struct FaithLayout {
     int p_addr, p_left, p_right, p_mid, p_midval, p_flag, p_cl, p_ce, p_stk, frame;
 };
 
+/* field access on a key held in shared memory (k_fq: one key per thread,
+   indexed by the field's word) */
+__device__ __forceinline__ uint64_t sget(const uint64_t *w, int pos, int n)
+{
+    const int i = pos >> 6, o = pos & 63;
+    uint64_t v = w[i] >> o;
+    if (o + n > 64 && i + 1 < NW_FAITH) v |= w[i + 1] << (64 - o);
+    return v & (n >= 64 ? ~0ull : ((1ull << n) - 1ull));
+}
+
+__device__ __forceinline__ void sput(uint64_t *w, int pos, int n, uint64_t v)
+{
+    v &= (n >= 64 ? ~0ull : ((1ull << n) - 1ull));
+    const int i = pos >> 6, o = pos & 63;
+    w[i] |= v << o;
+    if (o + n > 64 && i + 1 < NW_FAITH) w[i + 1] |= v >> (64 - o);
+}
+
+__device__ __forceinline__ void sclear(uint64_t *w, int pos, int n)
+{
+    const uint64_t m = (n >= 64 ? ~0ull : ((1ull << n) - 1ull));
+    const int i = pos >> 6, o = pos & 63;
+    w[i] &= ~(m << o);
+    if (o + n > 64 && i + 1 < NW_FAITH) w[i + 1] &= ~(m >> (64 - o));
+}
+
 /* sub-operation codes (the same numbering as the oracle's) */
 constexpr int FQ_ADDR_COL = 1, FQ_QRAM_COL = 2, FQ_QBS_FWD = 3, FQ_QBS_BWD = 4, FQ_SWAP = 5, FQ_ADDR_VAL = 6,
               FQ_QRAM_VAL = 7;
@@ -296,15 +369,18 @@ __device__ __forceinline__ uint64_t fq_qram(const QwSimDev &d, uint64_t addr, bo
     return (uint64_t)(__ldg(d.img + addr) & 0xffffu);
 }
 
-__global__ void k_fq(QwSimDev d, FKeyW *keys, int64_t M, int op, FaithLayout F, int32_t *status)
+__global__ void __launch_bounds__(256) k_fq(QwSimDev d, FKeyW *keys, int64_t M, int op, FaithLayout F, int32_t *status)
 {
     const FLayout L = flayout(d.nb);
     const int aw = F.aw;
     const uint64_t ns = (uint64_t)d.n_single * (uint64_t)d.s;
+    __shared__ FKeyW sk[256];
+    uint64_t *kw = sk[threadIdx.x].w;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        FKeyW k = keys[i];
-        FRegs f = fdecode(k, L);
-        uint64_t addr = fget(k, F.p_addr, aw);
+        sk[threadIdx.x] = keys[i];
+        FKey b = fbase(sk[threadIdx.x]);
+        FRegs f = fdecode(b, L);
+        uint64_t addr = sget(kw, F.p_addr, aw);
         const uint64_t offset = ns + (uint64_t)f.j * (uint64_t)d.s;
         if (op == FQ_ADDR_COL) {
             addr ^= offset + f.x.k;
@@ -319,10 +395,10 @@ __global__ void k_fq(QwSimDev d, FKeyW *keys, int64_t M, int op, FaithLayout F, 
             f.x.k = f.x.kc;
             f.x.kc = t;
         } else if (op == FQ_QBS_FWD || op == FQ_QBS_BWD) {
-            uint64_t left = fget(k, F.p_left, aw), right = fget(k, F.p_right, aw);
-            uint64_t mid = fget(k, F.p_mid, aw), midval = fget(k, F.p_midval, 16);
-            uint32_t flag = (uint32_t)fget(k, F.p_flag, 1), cl = (uint32_t)fget(k, F.p_cl, 1);
-            uint32_t ce = (uint32_t)fget(k, F.p_ce, 1);
+            uint64_t left = sget(kw, F.p_left, aw), right = sget(kw, F.p_right, aw);
+            uint64_t mid = sget(kw, F.p_mid, aw), midval = sget(kw, F.p_midval, 16);
+            uint32_t flag = (uint32_t)sget(kw, F.p_flag, 1), cl = (uint32_t)sget(kw, F.p_cl, 1);
+            uint32_t ce = (uint32_t)sget(kw, F.p_ce, 1);
             const uint64_t target = f.x.kc;
             if (op == FQ_QBS_FWD) { /* Alg. 1's loop, every probe's registers pushed */
                 left ^= offset;
@@ -349,21 +425,21 @@ __global__ void k_fq(QwSimDev d, FKeyW *keys, int64_t M, int op, FaithLayout F, 
                         right = t;
                     }
                     const int pf = F.p_stk + it * F.frame; /* push: the frame takes them, zeros stay */
-                    fput(k, pf, aw, mid);
-                    fput(k, pf + aw, 16, midval);
-                    fput(k, pf + aw + 16, 1, cl);
-                    fput(k, pf + aw + 17, 1, ce);
+                    sput(kw, pf, aw, mid);
+                    sput(kw, pf + aw, 16, midval);
+                    sput(kw, pf + aw + 16, 1, cl);
+                    sput(kw, pf + aw + 17, 1, ce);
                     mid = midval = 0;
                     cl = ce = 0u;
                 }
             } else { /* the loop undone in reverse: pop, then every step inverted */
                 for (int it = d.L; it >= 0; --it) {
                     const int pf = F.p_stk + it * F.frame;
-                    mid = fget(k, pf, aw);
-                    midval = fget(k, pf + aw, 16);
-                    cl = (uint32_t)fget(k, pf + aw + 16, 1);
-                    ce = (uint32_t)fget(k, pf + aw + 17, 1);
-                    fclear(k, pf, F.frame);
+                    mid = sget(kw, pf, aw);
+                    midval = sget(kw, pf + aw, 16);
+                    cl = (uint32_t)sget(kw, pf + aw + 16, 1);
+                    ce = (uint32_t)sget(kw, pf + aw + 17, 1);
+                    sclear(kw, pf, F.frame);
                     if (flag && cl) {
                         const uint64_t t = mid;
                         mid = right;
@@ -393,23 +469,25 @@ __global__ void k_fq(QwSimDev d, FKeyW *keys, int64_t M, int op, FaithLayout F, 
                 left = right = 0;
                 flag = 0u;
             }
-            fclear(k, F.p_left, aw);
-            fclear(k, F.p_right, aw);
-            fclear(k, F.p_mid, aw);
-            fclear(k, F.p_midval, 16);
-            fclear(k, F.p_flag, 3);
-            fput(k, F.p_left, aw, left);
-            fput(k, F.p_right, aw, right);
-            fput(k, F.p_mid, aw, mid);
-            fput(k, F.p_midval, 16, midval);
-            fput(k, F.p_flag, 1, flag);
-            fput(k, F.p_cl, 1, cl);
-            fput(k, F.p_ce, 1, ce);
+            sclear(kw, F.p_left, aw);
+            sclear(kw, F.p_right, aw);
+            sclear(kw, F.p_mid, aw);
+            sclear(kw, F.p_midval, 16);
+            sclear(kw, F.p_flag, 3);
+            sput(kw, F.p_left, aw, left);
+            sput(kw, F.p_right, aw, right);
+            sput(kw, F.p_mid, aw, mid);
+            sput(kw, F.p_midval, 16, midval);
+            sput(kw, F.p_flag, 1, flag);
+            sput(kw, F.p_cl, 1, cl);
+            sput(kw, F.p_ce, 1, ce);
         }
-        fclear(k, F.p_addr, aw);
-        fput(k, F.p_addr, aw, addr);
-        frewrite(k, f, L);
-        keys[i] = k;
+        sclear(kw, F.p_addr, aw);
+        sput(kw, F.p_addr, aw, addr);
+        frewrite(b, f, L);
+        kw[0] = b.w[0];
+        kw[1] = b.w[1];
+        keys[i] = sk[threadIdx.x];
     }
 }
 
@@ -998,7 +1076,7 @@ __global__ void k_f_readout(QwSimDev d, const FKeyN<NW> *keys, const double2 *am
 {
     const FLayout L = flayout(d.nb);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        const FRegs f = fdecode(keys[i], L);
+        const FRegs f = fdecode(fbase_load(keys + i), L);
         if (f.jc != 0 || f.b1 != 0 || f.x.kc != 0 || f.x.k != 0 || f.x.b2 != 0 || f.x.A != 0) continue;
         if (f.j >= (uint32_t)d.n_single) continue;
         const double coef = a.qls_coefs[*a.qls_j];
@@ -1017,7 +1095,7 @@ __global__ void k_f_scatter(QwSimDev d, QwBufDev out, const FKeyN<NW> *keys, con
     const FLayout L = flayout(d.nb);
     double acc = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        const FRegs f = fdecode(keys[i], L);
+        const FRegs f = fdecode(fbase_load(keys + i), L);
         if (f.x.A != 0) {
             atomicOr(status, QW_ST_ANCILLA);
             continue;
