@@ -628,7 +628,8 @@ template <> struct Amp<float2> {
             return __fadd_rn(s, __fadd_rn(e, l));
         }
     };
-    /* sum of a zero-type Hadamard group, exact to ~2^-46 relative */
+    /* sum of a zero-type Hadamard group of FP32 terms in a float pair: its
+       error is of order 2^-46 times the sum of the terms' magnitudes */
     struct Sum {
         DF x, y;
         __device__ void add(T a) { x.add(a.x); y.add(a.y); }
