@@ -100,7 +100,10 @@ typedef struct {
                                 branches in device memory, each interference op a
                                 global radix sort by key, a per-group transform and a
                                 compaction (no capacity limit; the host synchronises
-                                between its stages, so no CUDA graph is used), 6 = the
+                                between its stages, so no CUDA graph is used; its
+                                scratch comes from a device memory pool of the
+                                simulator's own, which keeps the memory once used
+                                until qw_sim_destroy), 6 = the
                                 register-faithful schedule: the flat path with every
                                 working register of O_s', O_A' and Alg. 1 held in the
                                 state between sub-operations (the QW_FQ_STEP sequence

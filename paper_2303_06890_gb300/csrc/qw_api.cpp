@@ -1038,8 +1038,8 @@ static int flat_store(qw_sim *sim, FlatList &L, const QwStepArgs &a, const int64
  * O_s'^dag O_A', H (sort, groups, compaction), [QLS read-out], P, H,
  * O_A' O_s', R, O_s'^dag O_A' O_s', A = 0 checked, S -- and the result
  * stored into X_cur+1.  The host synchronises to size each stage; device
- * scratch is stream-ordered (cudaMallocAsync) and freed before the call
- * returns. */
+ * scratch is stream-ordered (flat_alloc: the simulator's pool) and returned
+ * to the pool before the call returns. */
 static int flat_walk_step(qw_sim *sim, int readout)
 {
     {
