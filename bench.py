@@ -634,7 +634,9 @@ def table1_leg(torch, barrier, max_over_ranks) -> dict:
     """Walk steps on the band matrices shaped like Table 1 (A..E, Sec. V-B),
     complex128 and complex64, autotuned, steps issued back to back as graph
     replays (the state stays resident; no L2 flush: consecutive steps of one
-    walk), beside the paper's single-core time per step."""
+    walk), beside the paper's single-core time per step; and the same walk on
+    the paper's literal schedule (flat path and register-faithful, complex128,
+    wall clock per step)."""
     from paper_2303_06890_gb300 import qwalk
     from paper_2303_06890_gb300 import workloads as wl
 
@@ -659,6 +661,26 @@ def table1_leg(torch, barrier, max_over_ranks) -> dict:
                           "branches_per_step": st["out"] / max(1, st["steps"]),
                           "entries_per_s": (st["in"] + st["after_rdag"] + st["after_hph"]) / t}
         row["paper_over_fp64"] = row["paper_s_per_step"] / (row["fp64"]["us_per_step"] * 1e-6)
+        # the paper's own schedule (complex128): the flat path and the
+        # register-faithful one, whose keys hold Alg. 1's registers and stack
+        # as the paper's simulator does; wall clock (the host synchronises
+        # between their stages)
+        for label, variant in (("flat", 5), ("faithful", 6)):
+            sim = qwalk.Sim(w.matrix, s_pad=w.s, walk_variant=variant)
+            sim.state_init(w.b)
+            sim.apply_walk_step(2)
+            sim.step_stats(reset=True)
+            nst = 4
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.apply_walk_step(nst)
+            torch.cuda.synchronize()
+            dt = max_over_ranks(time.perf_counter() - t0)
+            st = sim.step_stats(reset=True)
+            sim.close()
+            row[label] = {"ms_per_step": 1e3 * dt / nst, "branches_per_step": st["out"] / max(1, st["steps"])}
+        row["paper_over_faithful"] = row["paper_s_per_step"] / (row["faithful"]["ms_per_step"] * 1e-3)
         out[name] = row
     return out
 

@@ -979,16 +979,20 @@ __global__ void k_f_starts(const uint32_t *heads, const uint32_t *gidx, int64_t 
 /* H on each group's zero-filled vector of 2^L = s entries (the groups of
  * the list sorted in ORDER_H, starts[g] .. starts[g + 1]): output u of a group
  * is s^-1/2 sum_m (-1)^{|u & v_m|} a_m over its members m (v_m: their low L
- * bits of k).  A warp runs 32 / s groups (s <= 32: lane u of a group holds
- * entry u of the zero-filled vector, and the L butterfly stages of the fast
- * Walsh-Hadamard transform (Sylvester order, (x, y) -> (x + y, x - y) on
- * index bit h) run over shuffles: s L additions per group instead of s^2;
- * the FP64 pipe is the limit) or one group in s / 32 rounds of 32 outputs,
- * each the direct sum over the members in list order (a lane loads one
- * member per round and the warp's shuffles hand them to every output).
+ * bits of k).  A warp runs 32 / s groups (s < 32) or one group (s >= 32).
+ * For s <= 128 lane t of a group holds entries t, t + 32, ... of the
+ * zero-filled vector, and the L butterfly stages of the fast Walsh-Hadamard
+ * transform (Sylvester order, (x, y) -> (x + y, x - y) on index bit h) run
+ * over shuffles (bits below 32) and between the lane's registers (bits
+ * above): s L additions per group instead of s^2; the FP64 pipe is the
+ * limit.  Larger s: s / 32 rounds of 32 outputs, each the direct sum over
+ * the members in list order (a lane loads one member per round and the
+ * warp's shuffles hand them to every output).
  * COUNT: the kept outputs of each group into cnt[g]; otherwise the kept
  * outputs are written, in order of u, from gpos[g] (the exclusive scan of
  * cnt) -- the clearing step without a list of all G s outputs. */
+constexpr int FWHT_ROUNDS = 4; /* the fast transform for s <= 128 */
+
 template <int NW, bool COUNT>
 __global__ void __launch_bounds__(256) k_f_hgroups(QwSimDev d, const FKeyN<NW> *keys, const double2 *amps,
                                                    const int64_t *starts, int64_t G, uint32_t *cnt,
@@ -1001,29 +1005,63 @@ __global__ void __launch_bounds__(256) k_f_hgroups(QwSimDev d, const FKeyN<NW> *
     const unsigned below = (1u << lane) - 1u;
     const uint64_t lowm = ((uint64_t)s - 1ull) << 1;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    __shared__ double2 zv[8][32];
+    const bool fwht = s <= 32 * FWHT_ROUNDS;
+    __shared__ double2 zv[8][32 * FWHT_ROUNDS];
     double2 *vec = zv[threadIdx.x >> 5];
     for (int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wg * gpw < G; wg += nwarps) {
         const int64_t g = wg * gpw + sub;
         const bool act = g < G;
         const int64_t b = act ? starts[g] : 0, nm = act ? starts[g + 1] - b : 0;
+        /* fast transform: entry q sw + ul of the group's zero-filled vector
+           in x[q], the butterflies of index bits below sw over shuffles, the
+           ones above between the lane's registers; x[q] is then output
+           u = q sw + ul */
+        double2 x[FWHT_ROUNDS];
+        if (fwht) {
+#pragma unroll
+            for (int q = 0; q < FWHT_ROUNDS; ++q)
+                if (q < rounds) vec[first + q * sw + ul] = make_double2(0, 0);
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < FWHT_ROUNDS; ++q) {
+                const int64_t mi = (int64_t)q * sw + ul;
+                if (q < rounds && mi < nm)
+                    vec[first + (int)((keys[b + mi].w[0] >> 1) & (uint64_t)(s - 1))] = amps[b + mi];
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < FWHT_ROUNDS; ++q) x[q] = q < rounds ? vec[first + q * sw + ul] : make_double2(0, 0);
+            __syncwarp();
+            for (int h = 1; h < sw; h <<= 1) {
+#pragma unroll
+                for (int q = 0; q < FWHT_ROUNDS; ++q) {
+                    if (q >= rounds) continue;
+                    const double yx = __shfl_xor_sync(FULL, x[q].x, h), yy = __shfl_xor_sync(FULL, x[q].y, h);
+                    x[q] = (ul & h) ? make_double2(yx - x[q].x, yy - x[q].y)
+                                    : make_double2(x[q].x + yx, x[q].y + yy);
+                }
+            }
+#pragma unroll
+            for (int hq = 1; hq < FWHT_ROUNDS; hq <<= 1) {
+#pragma unroll
+                for (int q = 0; q < FWHT_ROUNDS; ++q) {
+                    if ((q & hq) || (q | hq) >= rounds) continue;
+                    const double2 lo = x[q], hi = x[q | hq];
+                    x[q] = make_double2(lo.x + hi.x, lo.y + hi.y);
+                    x[q | hq] = make_double2(lo.x - hi.x, lo.y - hi.y);
+                }
+            }
+        }
         uint32_t run = 0u;
         for (int q = 0; q < rounds; ++q) {
             const uint32_t u = (uint32_t)(q * sw + ul);
             double2 o = make_double2(0, 0);
-            if (s <= 32) { /* the group's zero-filled vector over its lanes, then the butterflies */
-                vec[lane] = make_double2(0, 0);
-                __syncwarp();
-                if (ul < nm) vec[first + (int)((keys[b + ul].w[0] >> 1) & (uint64_t)(s - 1))] = amps[b + ul];
-                __syncwarp();
-                o = vec[lane];
-                __syncwarp();
-                for (int h = 1; h < sw; h <<= 1) {
-                    const double yx = __shfl_xor_sync(FULL, o.x, h), yy = __shfl_xor_sync(FULL, o.y, h);
-                    o = (ul & h) ? make_double2(yx - o.x, yy - o.y) : make_double2(o.x + yx, o.y + yy);
-                }
+            if (fwht) {
+#pragma unroll
+                for (int t = 0; t < FWHT_ROUNDS; ++t)
+                    if (t == q) o = x[t];
             }
-            for (int q2 = 0; q2 < rounds && s > 32; ++q2) {
+            for (int q2 = 0; q2 < rounds && !fwht; ++q2) {
                 const int64_t mi = (int64_t)q2 * sw + ul;
                 uint32_t mv = 0u;
                 double2 ma = make_double2(0, 0);

@@ -717,6 +717,36 @@ def test_flat_path_matches_oracle(maker, precision):
     sim.close()
 
 
+@pytest.mark.parametrize("variant, n, smax, seed, tries", [(5, 160, 64, 9, 40), (6, 160, 64, 9, 40),
+                                                           (5, 300, 128, 11, 80), (6, 300, 128, 11, 80),
+                                                           (5, 600, 256, 13, 160)])
+def test_flat_path_large_s(variant, n, smax, seed, tries):
+    """The flat path's Hadamard stage at s = 64 and 128 (the fast transform
+    with 2 and 4 vector entries a lane, the butterflies above bit 5 between a
+    lane's registers) and at s = 256 (the direct sums), on the flat path and
+    the register-faithful schedule: three complex128 steps equal the
+    oracle's."""
+    w = wl.small_random(n, smax, seed, attempts=n * tries)
+    assert w.s == smax
+    # row buckets of s entries (grown by the store where a row needs more), so
+    # that the bucket kernels' per-block buffers fit at creation
+    sim = _sim(w, walk_variant=variant, row_capacity=smax)
+    o = _oracle(w)
+    o.apply("T")
+    if smax <= 128:
+        sim.state_init(w.b)
+    else:  # T~|b~> (rows of 2 s branches) imported: beyond the initialisation kernel's row buffers
+        regs, amps = o.export()
+        full = np.zeros((len(regs), 8), dtype=np.uint64)
+        full[:, :7] = regs
+        sim.state_import(sim.pack(full), amps)
+    for _ in range(3):
+        sim.apply_walk_step(1)
+        o.apply("W")
+        compare(gpu_state(sim), oracle_state(o), TOL64)
+    sim.close()
+
+
 def test_flat_path_on_garbage_states_and_qls():
     """The flat path on a random state over the whole register space, and the
     CKS read-out through it (the flag-0 block after T~^dag's H)."""
@@ -756,17 +786,18 @@ def test_flat_path_on_garbage_states_and_qls():
 @pytest.mark.parametrize("variant", [5, 6])
 def test_flat_sort_spans_two_key_chunks(variant):
     """A random state whose branches differ in 66 register bits (nb = 16:
-    jc, j, kc, k over their whole ranges, b1, b2): the flat path's radix sort
-    takes the varying bits in two 64-bit chunks (the second formed in the
-    order the first left); three steps on the flat path and on the
-    register-faithful schedule equal the oracle's."""
+    jc, j, kc, k over their whole ranges, b1, b2; 5000 branches, several
+    2048-entry tiles of the sort's passes with a ragged last one): the flat
+    path's radix sort takes the varying bits in two 64-bit chunks (the second
+    formed in the order the first left); three steps on the flat path and on
+    the register-faithful schedule equal the oracle's."""
     w = wl.small_random(40000, 4, 29)
     rng = np.random.default_rng(7)
-    sim = _sim(w, walk_variant=variant, spill_rows=1024)
+    sim = _sim(w, walk_variant=variant, spill_rows=1 << 15)  # rows with jc != 0
     nb = sim.nb
     assert 4 * nb + 2 > 64
     keys = set()
-    while len(keys) < 300:
+    while len(keys) < 5000:
         keys.add((int(rng.integers(0, 1 << nb)), int(rng.integers(0, 1 << nb)), int(rng.integers(0, 2)),
                   int(rng.integers(0, 1 << nb)), int(rng.integers(0, 1 << nb)), int(rng.integers(0, 2))))
     regs = np.array(sorted(keys), dtype=np.uint64)
