@@ -991,9 +991,7 @@ __global__ void k_f_starts(const uint32_t *heads, const uint32_t *gidx, int64_t 
  * COUNT: the kept outputs of each group into cnt[g]; otherwise the kept
  * outputs are written, in order of u, from gpos[g] (the exclusive scan of
  * cnt) -- the clearing step without a list of all G s outputs. */
-constexpr int FWHT_ROUNDS = 4; /* the fast transform for s <= 128 */
-
-template <int NW, bool COUNT>
+template <int NW, bool COUNT, int FWHT_ROUNDS>
 __global__ void __launch_bounds__(256) k_f_hgroups(QwSimDev d, const FKeyN<NW> *keys, const double2 *amps,
                                                    const int64_t *starts, int64_t G, uint32_t *cnt,
                                                    const uint32_t *gpos, FKeyN<NW> *okeys, double2 *oamps)
@@ -1005,8 +1003,9 @@ __global__ void __launch_bounds__(256) k_f_hgroups(QwSimDev d, const FKeyN<NW> *
     const unsigned below = (1u << lane) - 1u;
     const uint64_t lowm = ((uint64_t)s - 1ull) << 1;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const bool fwht = s <= 32 * FWHT_ROUNDS;
-    __shared__ double2 zv[8][32 * FWHT_ROUNDS];
+    constexpr int ZR = FWHT_ROUNDS > 0 ? FWHT_ROUNDS : 1;
+    const bool fwht = FWHT_ROUNDS > 0;
+    __shared__ double2 zv[8][32 * ZR];
     double2 *vec = zv[threadIdx.x >> 5];
     for (int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wg * gpw < G; wg += nwarps) {
         const int64_t g = wg * gpw + sub;
@@ -1016,25 +1015,25 @@ __global__ void __launch_bounds__(256) k_f_hgroups(QwSimDev d, const FKeyN<NW> *
            in x[q], the butterflies of index bits below sw over shuffles, the
            ones above between the lane's registers; x[q] is then output
            u = q sw + ul */
-        double2 x[FWHT_ROUNDS];
+        double2 x[ZR];
         if (fwht) {
 #pragma unroll
-            for (int q = 0; q < FWHT_ROUNDS; ++q)
+            for (int q = 0; q < ZR; ++q)
                 if (q < rounds) vec[first + q * sw + ul] = make_double2(0, 0);
             __syncwarp();
 #pragma unroll
-            for (int q = 0; q < FWHT_ROUNDS; ++q) {
+            for (int q = 0; q < ZR; ++q) {
                 const int64_t mi = (int64_t)q * sw + ul;
                 if (q < rounds && mi < nm)
                     vec[first + (int)((keys[b + mi].w[0] >> 1) & (uint64_t)(s - 1))] = amps[b + mi];
             }
             __syncwarp();
 #pragma unroll
-            for (int q = 0; q < FWHT_ROUNDS; ++q) x[q] = q < rounds ? vec[first + q * sw + ul] : make_double2(0, 0);
+            for (int q = 0; q < ZR; ++q) x[q] = q < rounds ? vec[first + q * sw + ul] : make_double2(0, 0);
             __syncwarp();
             for (int h = 1; h < sw; h <<= 1) {
 #pragma unroll
-                for (int q = 0; q < FWHT_ROUNDS; ++q) {
+                for (int q = 0; q < ZR; ++q) {
                     if (q >= rounds) continue;
                     const double yx = __shfl_xor_sync(FULL, x[q].x, h), yy = __shfl_xor_sync(FULL, x[q].y, h);
                     x[q] = (ul & h) ? make_double2(yx - x[q].x, yy - x[q].y)
@@ -1042,9 +1041,9 @@ __global__ void __launch_bounds__(256) k_f_hgroups(QwSimDev d, const FKeyN<NW> *
                 }
             }
 #pragma unroll
-            for (int hq = 1; hq < FWHT_ROUNDS; hq <<= 1) {
+            for (int hq = 1; hq < ZR; hq <<= 1) {
 #pragma unroll
-                for (int q = 0; q < FWHT_ROUNDS; ++q) {
+                for (int q = 0; q < ZR; ++q) {
                     if ((q & hq) || (q | hq) >= rounds) continue;
                     const double2 lo = x[q], hi = x[q | hq];
                     x[q] = make_double2(lo.x + hi.x, lo.y + hi.y);
@@ -1058,7 +1057,7 @@ __global__ void __launch_bounds__(256) k_f_hgroups(QwSimDev d, const FKeyN<NW> *
             double2 o = make_double2(0, 0);
             if (fwht) {
 #pragma unroll
-                for (int t = 0; t < FWHT_ROUNDS; ++t)
+                for (int t = 0; t < ZR; ++t)
                     if (t == q) o = x[t];
             }
             for (int q2 = 0; q2 < rounds && !fwht; ++q2) {
@@ -1446,24 +1445,38 @@ cudaError_t qw_flat_group(const QwSimDev &d, int op, const void *keys, const dou
     return cudaGetLastError();
 }
 
+namespace {
+template <int NW, int R>
+void launch_hgroups(const QwSimDev &d, const FKeyN<NW> *k, const double2 *amps, const int64_t *starts, int64_t G,
+                    uint32_t *cnt, const uint32_t *gpos, FKeyN<NW> *ok, double2 *oamps, int grid, cudaStream_t st)
+{
+    if (gpos == nullptr) k_f_hgroups<NW, true, R><<<grid, 256, 0, st>>>(d, k, amps, starts, G, cnt, nullptr, nullptr, nullptr);
+    else k_f_hgroups<NW, false, R><<<grid, 256, 0, st>>>(d, k, amps, starts, G, cnt, gpos, ok, oamps);
+}
+
+/* the fast transform's vector entries a lane: 1 (s <= 32), 2 (64), 4 (128);
+   0: the direct sums (s > 128) */
+template <int NW>
+void launch_hgroups_s(const QwSimDev &d, const void *keys, const double2 *amps, const int64_t *starts, int64_t G,
+                      uint32_t *cnt, const uint32_t *gpos, void *okeys, double2 *oamps, int grid, cudaStream_t st)
+{
+    const FKeyN<NW> *k = static_cast<const FKeyN<NW> *>(keys);
+    FKeyN<NW> *ok = static_cast<FKeyN<NW> *>(okeys);
+    if (d.s <= 32) launch_hgroups<NW, 1>(d, k, amps, starts, G, cnt, gpos, ok, oamps, grid, st);
+    else if (d.s == 64) launch_hgroups<NW, 2>(d, k, amps, starts, G, cnt, gpos, ok, oamps, grid, st);
+    else if (d.s == 128) launch_hgroups<NW, 4>(d, k, amps, starts, G, cnt, gpos, ok, oamps, grid, st);
+    else launch_hgroups<NW, 0>(d, k, amps, starts, G, cnt, gpos, ok, oamps, grid, st);
+}
+} // namespace
+
 cudaError_t qw_flat_hgroups(const QwSimDev &d, const void *keys, const double2 *amps, const int64_t *starts, int64_t G,
                             uint32_t *cnt, const uint32_t *gpos, void *okeys, double2 *oamps, cudaStream_t st, int kw)
 {
     if (G <= 0) return cudaSuccess;
     const int gpw = d.s < 32 ? 32 / d.s : 1;
     const int grid = grid_for((G + gpw - 1) / gpw * 32, 256);
-    const bool count = gpos == nullptr;
-    if (kw == NW_FAITH) {
-        const FKeyW *k = static_cast<const FKeyW *>(keys);
-        if (count) k_f_hgroups<NW_FAITH, true><<<grid, 256, 0, st>>>(d, k, amps, starts, G, cnt, nullptr, nullptr, nullptr);
-        else
-            k_f_hgroups<NW_FAITH, false><<<grid, 256, 0, st>>>(d, k, amps, starts, G, cnt, gpos,
-                                                                static_cast<FKeyW *>(okeys), oamps);
-    } else {
-        const FKey *k = static_cast<const FKey *>(keys);
-        if (count) k_f_hgroups<2, true><<<grid, 256, 0, st>>>(d, k, amps, starts, G, cnt, nullptr, nullptr, nullptr);
-        else k_f_hgroups<2, false><<<grid, 256, 0, st>>>(d, k, amps, starts, G, cnt, gpos, static_cast<FKey *>(okeys), oamps);
-    }
+    if (kw == NW_FAITH) launch_hgroups_s<NW_FAITH>(d, keys, amps, starts, G, cnt, gpos, okeys, oamps, grid, st);
+    else launch_hgroups_s<2>(d, keys, amps, starts, G, cnt, gpos, okeys, oamps, grid, st);
     return cudaGetLastError();
 }
 
