@@ -89,18 +89,6 @@ __device__ __forceinline__ void fput(FKeyN<NW> &k, int pos, int w, uint64_t v)
     }
 }
 
-template <int NW>
-__device__ __forceinline__ void fclear(FKeyN<NW> &k, int pos, int w)
-{
-    const uint64_t m = (w >= 64 ? ~0ull : ((1ull << w) - 1ull));
-    const int i = pos >> 6, o = pos & 63;
-#pragma unroll
-    for (int t = 0; t < NW; ++t) {
-        if (t == i) k.w[t] &= ~(m << o);
-        if (t == i + 1 && o + w > 64) k.w[t] &= ~(m >> (64 - o));
-    }
-}
-
 struct FRegs {
     uint32_t inst, jc, j, b1;
     Regs x; /* k, kc, A, b2 */
@@ -159,14 +147,6 @@ __device__ __forceinline__ void fencode_into(FKeyN<NW> &key, const FRegs &r, con
     fput(k, L.pinst, 16, r.inst);
     key.w[0] = k.w[0];
     key.w[1] = k.w[1];
-}
-
-__device__ __forceinline__ FKey fencode(const FRegs &r, const FLayout &L)
-{
-    FKey k;
-    k.w[0] = k.w[1] = 0ull;
-    fencode_into(k, r, L);
-    return k;
 }
 
 /* the base registers of a wider key rewritten, its other bits kept */
