@@ -53,7 +53,9 @@
  * and the paper's printed examples.  Parity unpinned: the amplitudes of
  * garbage branches (jc or kc != 0, rows j >= N) follow only from the readings
  * above -- no closed form of the paper reaches them -- and are compared with
- * the CUDA path as they stand.
+ * the CUDA path as they stand; what pins them is an invariant only: on random
+ * states over the whole register space each op of W is undone by its
+ * inverse, and W by T~ P T~^dag S.
  */
 #include <complex.h>
 #include <math.h>

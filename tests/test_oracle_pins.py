@@ -631,3 +631,58 @@ def test_reachable_states_have_positions(oracle_mod, maker):
                 assert b2 == 0 and k in into[j], (j, b1, k, b2)
                 seen_in += 1
     assert seen_slot > 0 and (seen_in > 0 or all(j in cols[c] for c in range(w.n) for j in into[c]))
+
+
+def _garbage_state(nb, rng, count=400):
+    """Random branches over the whole register space: half with jc = kc = 0
+    (where O_A' writes A), half with every register random (jc, kc != 0, rows
+    j >= N, k outside the row)."""
+    keys = set()
+    while len(keys) < count:
+        z = len(keys) % 2 == 0
+        keys.add((0 if z else int(rng.integers(0, 1 << nb)), int(rng.integers(0, 1 << nb)), int(rng.integers(0, 2)),
+                  0 if z else int(rng.integers(0, 1 << nb)), int(rng.integers(0, 1 << nb)), int(rng.integers(0, 2))))
+    regs = np.array(sorted(keys), dtype=np.uint64)
+    amps = rng.standard_normal(len(regs)) + 1j * rng.standard_normal(len(regs))
+    return regs, amps / np.linalg.norm(amps)
+
+
+@pytest.mark.parametrize("maker", [lambda: wl.small_random(12, 4, 17), lambda: wl.small_random(40, 8, 5),
+                                   lambda: wl.small_random(100, 16, 3)])
+def test_garbage_subspace_ops_undo_each_other(oracle_mod, maker):
+    """The branches no closed form of the paper reaches (jc or kc != 0, rows
+    j >= N of a non-power-of-two N, k outside the row): on random states over
+    the whole register space each op of W is undone by its inverse -- O_s' by
+    O_s'^dag and back, O_A', H, P and S by themselves, R by R^dag and back
+    (A set by O_A' first on the jc = kc = 0 half), T~ by T~^dag and back, and
+    W by T~ P T~^dag S -- keys exactly and amplitudes to 1e-14, each op
+    keeping the norm.  A garbage branch dropped or duplicated, or mapped by
+    one op of a pair differently from how its inverse maps it back, fails."""
+    w = maker()
+
+    def state(o):
+        regs, amps = o.export()
+        return {tuple(int(v) for v in r): complex(a) for r, a in zip(regs, amps)}
+
+    rng = np.random.default_rng(11)
+    nb = oracle_mod.Oracle(w.matrix, w.s).nb
+    regs, amps = _garbage_state(nb, rng)
+    assert any(int(j) >= w.n for j in regs[:, 1]) and any(int(r[0]) and int(r[3]) for r in regs)
+    runs = [((), a, b) for a, b in (("OS", ("OSDAG",)), ("OSDAG", ("OS",)), ("OA", ("OA",)), ("R", ("RDAG",)),
+                                    ("RDAG", ("R",)), ("H", ("H",)), ("P", ("P",)), ("S", ("S",)),
+                                    ("T", ("TDAG",)), ("TDAG", ("T",)), ("W", ("S", "TDAG", "P", "T")))]
+    runs += [(("ALLOC_A", "OA"), a, b) for a, b in (("R", ("RDAG",)), ("RDAG", ("R",)), ("OS", ("OSDAG",)))]
+    for prefix, a, b in runs:
+        o = oracle_mod.Oracle(w.matrix, w.s)
+        o.set_state(regs, amps)
+        o.apply(*prefix)
+        s0 = state(o)
+        if prefix:
+            assert sum(1 for k in s0 if k[6] != 0) > 0  # A is set on some branches
+        o.apply(a)
+        assert abs(o.norm2() - 1.0) < 1e-12, a
+        o.apply(*b)
+        s1 = state(o)
+        assert set(s1) == set(s0), (prefix, a)
+        assert max(abs(s1[k] - s0[k]) for k in s0) <= 1e-14, (prefix, a)
+        assert o.violations == 0, (prefix, a)
