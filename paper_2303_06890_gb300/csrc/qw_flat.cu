@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "qw_device.cuh"
+#include "qw_sort_chunks.h"
 
 namespace {
 
@@ -688,20 +689,11 @@ __global__ void k_f_orand(const uint64_t *words, int64_t nwords, int L, unsigned
     }
 }
 
-/* The sort runs on a compacted key: the bits that vary between keys, taken
- * in order of significance of the permuted key, 64 at a time (a "chunk").
- * LSD order carries over chunks: chunk 0 is sorted first, chunk c + 1 is
- * formed from the keys in the order chunk c left. */
-constexpr int CK_MAXRUNS = 64, CK_MAXPASS = 8;
+/* The sort runs on a compacted key (the chunks of qw_sort_chunks.h).  LSD
+ * order carries over chunks: chunk 0 is sorted first, chunk c + 1 is formed
+ * from the keys in the order chunk c left. */
 constexpr int OS_THREADS = 256, OS_IPT = 8, OS_TILE = OS_THREADS * OS_IPT;
 constexpr int OS_SPIN_LIMIT = 1 << 22;
-
-/* the varying bits of one chunk as runs of adjacent bits (key word, first
-   bit, length), lowest first; the chunk's bit b is the b-th of them */
-struct CkRuns {
-    uint8_t word[CK_MAXRUNS], shift[CK_MAXRUNS], len[CK_MAXRUNS];
-    int n, npass;
-};
 
 /* The chunk's compacted key of every entry -- the entry at position i of the
    current order, i.e. keys[perm[i]] (perm == nullptr: i) -- and the global
@@ -1305,36 +1297,10 @@ cudaError_t flat_sort_t(const QwSimDev &d, void *keys, double2 *amps, void *tmpk
     if ((e = cudaMemcpyAsync(h, w.acc, sizeof h, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
     /* the varying bits as runs, split into chunks of 64 */
-    std::vector<CkRuns> chunks;
-    CkRuns cur{};
-    int cbits = 0;
-    auto flush = [&]() {
-        if (cbits == 0) return;
-        cur.npass = (cbits + 7) / 8;
-        chunks.push_back(cur);
-        cur = CkRuns{};
-        cbits = 0;
-    };
-    for (int wi = 0; wi < NW; ++wi) {
-        const uint64_t var = h[wi] ^ h[NW + wi];
-        int b = 0;
-        while (b < 64) {
-            if (!((var >> b) & 1ull)) {
-                ++b;
-                continue;
-            }
-            int e2 = b;
-            while (e2 < 64 && ((var >> e2) & 1ull) && cbits + (e2 - b) < 64) ++e2;
-            cur.word[cur.n] = (uint8_t)wi;
-            cur.shift[cur.n] = (uint8_t)b;
-            cur.len[cur.n] = (uint8_t)(e2 - b);
-            ++cur.n;
-            cbits += e2 - b;
-            if (cbits == 64) flush();
-            b = e2;
-        }
-    }
-    flush();
+    uint64_t var[NW];
+    for (int wi = 0; wi < NW; ++wi) var[wi] = h[wi] ^ h[NW + wi];
+    std::vector<CkRuns> chunks(NW);
+    chunks.resize((size_t)qw_sort_chunks(var, NW, chunks.data()));
     if (chunks.empty()) return cudaSuccess;
     const int64_t nblk = (M + OS_TILE - 1) / OS_TILE;
     const int kgrid = grid_for(M, 256);
